@@ -1,0 +1,716 @@
+/*
+ * hjb_oracle.c -- plain, slow, FP64 CPU oracle for semi-Lagrangian value
+ * iteration and the independent sub-domain method of Festa,
+ * "Reconstruction of independent sub-domains for a class of Hamilton Jacobi
+ * equations and its application to parallel computing" (arXiv:1405.3521).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; it is written from the
+ * paper's definitions, in the paper's order, with no blocking or fusion.
+ *
+ * Every function names the passage it follows.  Where the paper is
+ * garbled or silent the reading used is stated beside the code:
+ *   R1  operator form  [T(V)]_i = beta * min_a I[V](x_i + h f(x_i,a)) + gamma * l_i,
+ *       beta = exp(-lambda h), gamma = (1 - beta)/lambda  (Sec. 3, eq. Tdef,
+ *       with the sign convention of the dynamics y' = f of Sec. 2).
+ *   R2  ghost value: a foot strictly outside the closed box (beyond 1e-6
+ *       grid cells) takes the value v_out (the Kruzhkov image of the paper's
+ *       +infinity on ghost nodes); feet within that tolerance are clamped
+ *       onto the face.  Ghost NODES of a restricted problem carry v_out.
+ *   R3  ISA step 3: the sub-problem on sub-domain k keeps every target node
+ *       inside it as a target; nodes outside it are ghosts.
+ *   R4  projection: Kuhn (Freudenthal) triangulation of each coarse cell; a
+ *       fine node belongs to sub-domain k iff every vertex carrying a
+ *       non-zero barycentric weight is labelled k.
+ *   R10 ties in the control minimum go to the lowest control index.
+ *
+ * Parity unpinned: none of the functions below is unpinned; the pins live in
+ * tests/test_oracle_pins.py (brute force, BFS graph case, closed forms,
+ * invariants, the restricted-solve property).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OHJB_FACE_TOL 1e-6 /* R2: grid-cell tolerance for "on the face" */
+
+/* Problem statement of Sec. 2 discretised as in Sec. 3.  Arrays are node
+ * fields in row-major order with x fastest; controls are [ncontrols][cdim]. */
+typedef struct {
+    int ndim;            /* 2 or 3 */
+    int n[3];            /* nodes per dimension */
+    double lo[3], hi[3]; /* box; a periodic dimension has period hi-lo */
+    int periodic[3];
+    int dyn;             /* 0: f = s(x) a + c(x);  1: Dubins f = (v cos th, v sin th, u) */
+    const double *speed;   /* [N] or NULL (s = 1) */
+    const double *current; /* [N][2] or NULL (c = 0) */
+    double dubins_v;
+    const double *cost;    /* [N] or NULL (l = cost_const) */
+    double cost_const;
+    double h;              /* fictitious time step */
+    double lambda;         /* discount rate */
+    int ncontrols, cdim;
+    const double *controls;
+    const int32_t *target; /* [N] 0 free, k >= 1 target component k */
+    int ntargets;
+    double v_out;          /* value of ghost nodes / feet outside the box */
+} ohjb_problem;
+
+static long long node_count(const ohjb_problem *p) {
+    long long N = 1;
+    for (int d = 0; d < p->ndim; ++d) N *= p->n[d];
+    return N;
+}
+
+/* Grid spacing: n nodes on [lo,hi], or n nodes on a period (periodic). */
+static double spacing(const ohjb_problem *p, int d) {
+    return p->periodic[d] ? (p->hi[d] - p->lo[d]) / p->n[d]
+                          : (p->hi[d] - p->lo[d]) / (p->n[d] - 1);
+}
+
+static void unflatten(const ohjb_problem *p, long long i, int idx[3]) {
+    idx[0] = (int)(i % p->n[0]);
+    long long r = i / p->n[0];
+    idx[1] = (int)(r % p->n[1]);
+    idx[2] = p->ndim > 2 ? (int)(r / p->n[1]) : 0;
+}
+
+static long long flatten(const ohjb_problem *p, const int idx[3]) {
+    long long i = idx[0] + (long long)p->n[0] * idx[1];
+    if (p->ndim > 2) i += (long long)p->n[0] * p->n[1] * idx[2];
+    return i;
+}
+
+/* Q1 (multilinear) interpolation I[V] at grid coordinate g (Sec. 3, the
+ * "linear n-dimensional interpolation" of the scheme).  Non-periodic
+ * coordinates must already lie in [0, n-1]; the cell is floor(g) clamped to
+ * [0, n-2].  Periodic coordinates wrap modulo n.  If grad != NULL the
+ * gradient with respect to the grid coordinates is written there. */
+static double q1_at(const ohjb_problem *p, const double *V, const double *g,
+                    double *grad) {
+    int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+    double t[3] = {0, 0, 0};
+    for (int d = 0; d < p->ndim; ++d) {
+        int n = p->n[d];
+        if (p->periodic[d]) {
+            double gg = fmod(g[d], (double)n);
+            if (gg < 0) gg += n;
+            int c = (int)floor(gg);
+            if (c >= n) c = n - 1;
+            t[d] = gg - c;
+            c0[d] = c;
+            c1[d] = (c + 1) % n;
+        } else {
+            int c = (int)floor(g[d]);
+            if (c < 0) c = 0;
+            if (c > n - 2) c = n - 2;
+            t[d] = g[d] - c;
+            c0[d] = c;
+            c1[d] = c + 1;
+        }
+    }
+    double acc = 0.0;
+    double gacc[3] = {0, 0, 0};
+    int corners = 1 << p->ndim;
+    for (int m = 0; m < corners; ++m) {
+        int idx[3] = {0, 0, 0};
+        double w = 1.0;
+        double dw[3] = {1, 1, 1};
+        for (int d = 0; d < p->ndim; ++d) {
+            int up = (m >> d) & 1;
+            idx[d] = up ? c1[d] : c0[d];
+            double wd = up ? t[d] : 1.0 - t[d];
+            double dd = up ? 1.0 : -1.0;
+            for (int e = 0; e < p->ndim; ++e) dw[e] *= (e == d) ? dd : wd;
+            w *= wd;
+        }
+        double v = V[flatten(p, idx)];
+        acc += w * v;
+        for (int e = 0; e < p->ndim; ++e) gacc[e] += dw[e] * v;
+    }
+    if (grad)
+        for (int e = 0; e < p->ndim; ++e) grad[e] = gacc[e];
+    return acc;
+}
+
+/* Interpolate at a physical point y (clamped into the box). */
+double ohjb_interp(const ohjb_problem *p, const double *V, const double *y) {
+    double g[3] = {0, 0, 0};
+    for (int d = 0; d < p->ndim; ++d) {
+        g[d] = (y[d] - p->lo[d]) / spacing(p, d);
+        if (!p->periodic[d]) {
+            if (g[d] < 0) g[d] = 0;
+            if (g[d] > p->n[d] - 1) g[d] = p->n[d] - 1;
+        }
+    }
+    return q1_at(p, V, g, NULL);
+}
+
+/* Dynamics f(x_i, a_j) of Sec. 2 for the two families. */
+static void dynamics(const ohjb_problem *p, long long i, const int idx[3], int j,
+                     double f[3]) {
+    const double *a = p->controls + (long long)j * p->cdim;
+    if (p->dyn == 0) {
+        double s = p->speed ? p->speed[i] : 1.0;
+        double cx = p->current ? p->current[2 * i] : 0.0;
+        double cy = p->current ? p->current[2 * i + 1] : 0.0;
+        f[0] = s * a[0] + cx;
+        f[1] = s * a[1] + cy;
+        f[2] = 0.0;
+    } else {
+        double th = p->lo[2] + idx[2] * spacing(p, 2);
+        f[0] = p->dubins_v * cos(th);
+        f[1] = p->dubins_v * sin(th);
+        f[2] = a[0];
+    }
+}
+
+/* Foot of the characteristic y = x_i + h f(x_i, a_j) in grid coordinates.
+ * Returns 0 when the foot is strictly outside the closed box (reading R2). */
+static int foot(const ohjb_problem *p, long long i, const int idx[3], int j,
+                double g[3], double off[3]) {
+    double f[3];
+    dynamics(p, i, idx, j, f);
+    int inside = 1;
+    for (int d = 0; d < p->ndim; ++d) {
+        double o = p->h * f[d] / spacing(p, d);
+        off[d] = o;
+        g[d] = idx[d] + o;
+        if (!p->periodic[d]) {
+            if (o < -(double)idx[d] - OHJB_FACE_TOL ||
+                o > (double)(p->n[d] - 1 - idx[d]) + OHJB_FACE_TOL)
+                inside = 0;
+            if (g[d] < 0) g[d] = 0;
+            if (g[d] > p->n[d] - 1) g[d] = p->n[d] - 1;
+        }
+    }
+    return inside;
+}
+
+/* Node classes of Sec. 3: ghost (Phi), boundary/target (dG), interior (G).
+ * mask/bit select a restricted problem (ISA step 3, reading R3);
+ * only_target = k keeps only target component k (RA step 1: dG := X_k). */
+enum { NODE_FREE = 0, NODE_TARGET = 1, NODE_GHOST = 2 };
+static int node_class(const ohjb_problem *p, long long i, const uint32_t *mask,
+                      int bit, int only_target) {
+    if (mask && !((mask[i] >> bit) & 1u)) return NODE_GHOST;
+    int32_t lab = p->target[i];
+    if (lab != 0 && (only_target == 0 || lab == only_target)) return NODE_TARGET;
+    return NODE_FREE;
+}
+
+static double beta_of(const ohjb_problem *p) { return exp(-p->lambda * p->h); }
+static double gamma_of(const ohjb_problem *p) {
+    return (1.0 - exp(-p->lambda * p->h)) / p->lambda;
+}
+
+/* One application of the operator T of Sec. 3, eq. (Tdef), under readings
+ * R1-R3, at one node.  Writes the minimising control index (R10). */
+static double apply_node(const ohjb_problem *p, const double *V, long long i,
+                         const uint32_t *mask, int bit, int only_target,
+                         int32_t *arg) {
+    int cls = node_class(p, i, mask, bit, only_target);
+    if (arg) *arg = -1;
+    if (cls == NODE_GHOST) return p->v_out;
+    if (cls == NODE_TARGET) return 0.0; /* g = 0 on the target */
+    int idx[3];
+    unflatten(p, i, idx);
+    double best = INFINITY;
+    int32_t barg = -1;
+    for (int j = 0; j < p->ncontrols; ++j) {
+        double g[3], off[3];
+        double q = foot(p, i, idx, j, g, off) ? q1_at(p, V, g, NULL) : p->v_out;
+        if (q < best) {
+            best = q;
+            barg = j;
+        }
+    }
+    if (arg) *arg = barg;
+    double l = p->cost ? p->cost[i] : p->cost_const;
+    return beta_of(p) * best + gamma_of(p) * l;
+}
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* One Jacobi application Vn = T(V) over all nodes; returns ||Vn - V||_inf
+ * (the quantity of the stopping Remark of Sec. 3). */
+double ohjb_apply(const ohjb_problem *p, const double *V, double *Vn,
+                  int32_t *policy, const uint32_t *mask, int bit,
+                  int only_target, int nthreads) {
+    long long N = node_count(p);
+    double r = 0.0;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static) reduction(max : r)
+    for (long long i = 0; i < N; ++i) {
+        int32_t a;
+        double v = apply_node(p, V, i, mask, bit, only_target, &a);
+        Vn[i] = v;
+        if (policy) policy[i] = a;
+        double dv = fabs(v - V[i]);
+        if (dv > r) r = dv;
+    }
+    return r;
+}
+
+/* Starting point of the iteration: v_out on free and ghost nodes, 0 on the
+ * target -- a supersolution, so the iteration decreases monotonically. */
+void ohjb_initial(const ohjb_problem *p, double *V, const uint32_t *mask, int bit,
+                  int only_target) {
+    long long N = node_count(p);
+    for (long long i = 0; i < N; ++i)
+        V[i] = node_class(p, i, mask, bit, only_target) == NODE_TARGET ? 0.0
+                                                                        : p->v_out;
+}
+
+/* Value iteration V^{n+1} = T(V^n) (Sec. 3) until ||V^{n+1}-V^n||_inf <= tol.
+ * V holds the start on entry (see ohjb_initial) and the result on exit.
+ * Returns the number of applications of T. */
+int ohjb_solve(const ohjb_problem *p, double tol, int max_iters, double *V,
+               const uint32_t *mask, int bit, int only_target, int nthreads,
+               double *final_res) {
+    long long N = node_count(p);
+    double *W = (double *)malloc(sizeof(double) * N);
+    if (!W) return -1;
+    double r = INFINITY;
+    int it = 0;
+    while (it < max_iters) {
+        r = ohjb_apply(p, V, W, NULL, mask, bit, only_target, nthreads);
+        ++it;
+        memcpy(V, W, sizeof(double) * N);
+        if (r <= tol) break;
+    }
+    free(W);
+    if (final_res) *final_res = r;
+    return it;
+}
+
+/* Gauss-Seidel variant with alternating orderings: the same operator and the
+ * same unique fixed point (T is a contraction), used only to reach tight
+ * tolerances quickly on large reference grids.  Stops when one strict Jacobi
+ * application changes V by at most tol. */
+int ohjb_solve_gs(const ohjb_problem *p, double tol, int max_sweeps, double *V,
+                  const uint32_t *mask, int bit, int only_target,
+                  double *final_res) {
+    long long N = node_count(p);
+    double *W = (double *)malloc(sizeof(double) * N);
+    if (!W) return -1;
+    int sweeps = 0;
+    double r = INFINITY;
+    int nord = 1 << p->ndim;
+    while (sweeps < max_sweeps) {
+        int ord = sweeps % nord;
+        double ch = 0.0;
+        int nz = p->ndim > 2 ? p->n[2] : 1;
+        for (int zz = 0; zz < nz; ++zz)
+            for (int yy = 0; yy < p->n[1]; ++yy)
+                for (int xx = 0; xx < p->n[0]; ++xx) {
+                    int idx[3];
+                    idx[0] = (ord & 1) ? p->n[0] - 1 - xx : xx;
+                    idx[1] = (ord & 2) ? p->n[1] - 1 - yy : yy;
+                    idx[2] = (ord & 4) ? nz - 1 - zz : zz;
+                    long long i = flatten(p, idx);
+                    double v = apply_node(p, V, i, mask, bit, only_target, NULL);
+                    double dv = fabs(v - V[i]);
+                    if (dv > ch) ch = dv;
+                    V[i] = v;
+                }
+        ++sweeps;
+        if (ch <= tol) {
+            r = ohjb_apply(p, V, W, NULL, mask, bit, only_target, 1);
+            if (r <= tol) break;
+        }
+    }
+    free(W);
+    if (final_res) *final_res = r;
+    return sweeps;
+}
+
+/* ---------------------------------------------------------------------- */
+/* RA: reconstruction algorithm (Sec. 3, algorithm "RA", steps 1-3).       */
+
+/* Coarse grid K: every stride-th fine node (the superimposed grids of the
+ * projection remark in Sec. 4).  Builds the coarse problem in *q, with
+ * freshly allocated field arrays owned by the caller (ohjb_free_coarse). */
+static int make_coarse(const ohjb_problem *p, const int stride[3], double h_coarse,
+                       ohjb_problem *q) {
+    *q = *p;
+    for (int d = 0; d < p->ndim; ++d) {
+        int r = stride[d];
+        if (r < 1) return -1;
+        if (p->periodic[d]) {
+            if (p->n[d] % r) return -1;
+            q->n[d] = p->n[d] / r;
+        } else {
+            if ((p->n[d] - 1) % r) return -1;
+            q->n[d] = (p->n[d] - 1) / r + 1;
+        }
+    }
+    q->h = h_coarse;
+    long long NK = node_count(q);
+    double *sp = p->speed ? (double *)malloc(sizeof(double) * NK) : NULL;
+    double *cu = p->current ? (double *)malloc(sizeof(double) * 2 * NK) : NULL;
+    double *co = p->cost ? (double *)malloc(sizeof(double) * NK) : NULL;
+    int32_t *ta = (int32_t *)malloc(sizeof(int32_t) * NK);
+    for (long long k = 0; k < NK; ++k) {
+        int ik[3], ifn[3] = {0, 0, 0};
+        unflatten(q, k, ik);
+        for (int d = 0; d < p->ndim; ++d) ifn[d] = ik[d] * stride[d];
+        long long i = flatten(p, ifn);
+        if (sp) sp[k] = p->speed[i];
+        if (cu) {
+            cu[2 * k] = p->current[2 * i];
+            cu[2 * k + 1] = p->current[2 * i + 1];
+        }
+        if (co) co[k] = p->cost[i];
+        ta[k] = p->target[i];
+    }
+    q->speed = sp;
+    q->current = cu;
+    q->cost = co;
+    q->target = ta;
+    return 0;
+}
+
+static void free_coarse(ohjb_problem *q) {
+    free((void *)q->speed);
+    free((void *)q->current);
+    free((void *)q->cost);
+    free((void *)q->target);
+}
+
+/* Coarse grid sizes for a stride (for the Python side to size buffers). */
+int ohjb_coarse_shape(const ohjb_problem *p, const int stride[3], int nK[3]) {
+    ohjb_problem q;
+    if (make_coarse(p, stride, p->h, &q)) return -1;
+    for (int d = 0; d < 3; ++d) nK[d] = d < p->ndim ? q.n[d] : 1;
+    free_coarse(&q);
+    return 0;
+}
+
+/* RA steps 2-3 on given auxiliary solutions Vaux[m][NK]:
+ * V = min_k V_k;  bit (k-1) of labels[j] set iff j in X_k or
+ * |V_k(j) - V(j)| <= delta (eq. rep of Prop. 3.1).  Counts the (j,k) pairs
+ * whose deciding quantity lies within tie_eps of the threshold (R10). */
+long long ohjb_label(long long NK, int m, const double *Vaux, const int32_t *target,
+                     double delta, double tie_eps, double *Vmin, uint32_t *labels) {
+    long long ties = 0;
+    for (long long j = 0; j < NK; ++j) {
+        double v = INFINITY;
+        for (int k = 0; k < m; ++k)
+            if (Vaux[(long long)k * NK + j] < v) v = Vaux[(long long)k * NK + j];
+        if (Vmin) Vmin[j] = v;
+        uint32_t bits = 0;
+        for (int k = 0; k < m; ++k) {
+            double diff = fabs(Vaux[(long long)k * NK + j] - v);
+            if (target[j] == k + 1 || diff <= delta) bits |= 1u << k;
+            if (fabs(diff - delta) <= tie_eps) ++ties;
+        }
+        labels[j] = bits;
+    }
+    return ties;
+}
+
+/* RA (all three steps) on the coarse grid of the given stride.
+ * Step 1 solves the m auxiliary problems V_k = T_k(V_k) whose target is
+ * component k only (dG := X_k); Vaux receives them as [m][NK].  labels
+ * receives the coarse bitmasks.  Returns the number of ties (R10), or -1. */
+long long ohjb_ra(const ohjb_problem *p, const int stride[3], double h_coarse,
+                  double delta, double tol, int max_iters, double *Vaux,
+                  uint32_t *labels, int nthreads) {
+    ohjb_problem q;
+    if (make_coarse(p, stride, h_coarse, &q)) return -1;
+    long long NK = node_count(&q);
+    int m = p->ntargets;
+    for (int k = 1; k <= m; ++k) {
+        double *Vk = Vaux + (long long)(k - 1) * NK;
+        ohjb_initial(&q, Vk, NULL, 0, k);
+        ohjb_solve(&q, tol, max_iters, Vk, NULL, 0, k, nthreads, NULL);
+    }
+    long long ties = ohjb_label(NK, m, Vaux, q.target, delta, 1e-6, NULL, labels);
+    free_coarse(&q);
+    return ties;
+}
+
+/* ---------------------------------------------------------------------- */
+/* ISA step 2: projection of coarse labels onto the fine grid through the  */
+/* concave hull Con (Sec. 4, second observation after the algorithm),      */
+/* reading R4 (Kuhn triangulation, integer local coordinates).            */
+
+void ohjb_project(const ohjb_problem *p, const int stride[3], const uint32_t *coarse,
+                  uint32_t *fine) {
+    int nK[3] = {1, 1, 1};
+    for (int d = 0; d < p->ndim; ++d)
+        nK[d] = p->periodic[d] ? p->n[d] / stride[d] : (p->n[d] - 1) / stride[d] + 1;
+    long long N = node_count(p);
+    for (long long i = 0; i < N; ++i) {
+        int idx[3];
+        unflatten(p, i, idx);
+        int cell[3] = {0, 0, 0}, loc[3] = {0, 0, 0};
+        for (int d = 0; d < p->ndim; ++d) {
+            int c = idx[d] / stride[d];
+            if (!p->periodic[d] && c > nK[d] - 2) c = nK[d] - 2;
+            cell[d] = c;
+            loc[d] = idx[d] - c * stride[d]; /* 0..stride */
+        }
+        /* Kuhn simplex: order the dimensions by decreasing local coordinate
+         * t_d = loc_d / stride_d (compared exactly by cross-multiplication).
+         * The vertices are v_0 = cell origin, v_k = v_{k-1} + e_{sigma(k)}.
+         * Barycentric weights: 1 - t_s1, t_s1 - t_s2, ..., t_sD. */
+        int ord[3] = {0, 1, 2};
+        for (int a = 0; a < p->ndim; ++a)
+            for (int b = a + 1; b < p->ndim; ++b) {
+                long long ta = (long long)loc[ord[a]] * stride[ord[b]];
+                long long tb = (long long)loc[ord[b]] * stride[ord[a]];
+                if (tb > ta) {
+                    int t = ord[a];
+                    ord[a] = ord[b];
+                    ord[b] = t;
+                }
+            }
+        uint32_t acc = 0xffffffffu;
+        int vtx[3] = {cell[0], cell[1], cell[2]};
+        for (int k = 0; k <= p->ndim; ++k) {
+            /* weight of vertex k is non-zero iff t_{s_k} > t_{s_{k+1}}
+             * (with t_{s_0} := 1 and t_{s_{D+1}} := 0) */
+            long long num_hi, den_hi, num_lo, den_lo;
+            if (k == 0) {
+                num_hi = 1;
+                den_hi = 1;
+            } else {
+                num_hi = loc[ord[k - 1]];
+                den_hi = stride[ord[k - 1]];
+            }
+            if (k == p->ndim) {
+                num_lo = 0;
+                den_lo = 1;
+            } else {
+                num_lo = loc[ord[k]];
+                den_lo = stride[ord[k]];
+            }
+            int nonzero = num_hi * den_lo > num_lo * den_hi;
+            if (k > 0) vtx[ord[k - 1]] += 1;
+            if (nonzero) {
+                int w[3] = {0, 0, 0};
+                for (int d = 0; d < p->ndim; ++d)
+                    w[d] = p->periodic[d] ? vtx[d] % nK[d] : vtx[d];
+                long long ci = w[0] + (long long)nK[0] * w[1];
+                if (p->ndim > 2) ci += (long long)nK[0] * nK[1] * w[2];
+                acc &= coarse[ci];
+            }
+        }
+        fine[i] = acc;
+    }
+}
+
+/* ISA steps 3-4 (Sec. 4): restricted solves on every sub-domain given by
+ * fine_mask (reading R3), then Vbar(j) = min{ V_k(j) : j in Sigma_k }.
+ * Vk (optional) receives [m][N].  Returns the number of uncovered nodes
+ * (nodes in no sub-domain; they receive v_out). */
+long long ohjb_isa(const ohjb_problem *p, const uint32_t *fine_mask, double tol,
+                   int max_iters, int use_gs, double *Vk, double *Vbar,
+                   int *iters, int nthreads) {
+    long long N = node_count(p);
+    int m = p->ntargets;
+    double *tmp = (double *)malloc(sizeof(double) * N);
+    for (long long i = 0; i < N; ++i) Vbar[i] = INFINITY;
+    for (int k = 0; k < m; ++k) {
+        ohjb_initial(p, tmp, fine_mask, k, 0);
+        int it;
+        if (use_gs)
+            it = ohjb_solve_gs(p, tol, max_iters, tmp, fine_mask, k, 0, NULL);
+        else
+            it = ohjb_solve(p, tol, max_iters, tmp, fine_mask, k, 0, nthreads, NULL);
+        if (iters) iters[k] = it;
+        if (Vk) memcpy(Vk + (long long)k * N, tmp, sizeof(double) * N);
+        for (long long i = 0; i < N; ++i)
+            if (((fine_mask[i] >> k) & 1u) && tmp[i] < Vbar[i]) Vbar[i] = tmp[i];
+    }
+    long long unc = 0;
+    for (long long i = 0; i < N; ++i)
+        if (Vbar[i] == INFINITY) {
+            Vbar[i] = p->v_out;
+            ++unc;
+        }
+    free(tmp);
+    return unc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Adjoint of the converged fixed point with the optimal policy frozen.    */
+/* (The paper has no adjoint; this is the plain linear algebra of          */
+/* V = beta P_pi V + b: the transposed system (I - beta P_pi)^T lam = g.)  */
+
+/* Q1 weights of the foot of node i under control j: up to 2^ndim corner
+ * indices and weights; returns 0 when the foot is outside (row of zeros). */
+static int row_weights(const ohjb_problem *p, long long i, int j, long long *cidx,
+                       double *cw, double *gradw_dir, const double *V) {
+    int idx[3];
+    unflatten(p, i, idx);
+    double g[3], off[3];
+    if (!foot(p, i, idx, j, g, off)) return 0;
+    int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+    double t[3] = {0, 0, 0};
+    for (int d = 0; d < p->ndim; ++d) {
+        int n = p->n[d];
+        if (p->periodic[d]) {
+            double gg = fmod(g[d], (double)n);
+            if (gg < 0) gg += n;
+            int c = (int)floor(gg);
+            if (c >= n) c = n - 1;
+            t[d] = gg - c;
+            c0[d] = c;
+            c1[d] = (c + 1) % n;
+        } else {
+            int c = (int)floor(g[d]);
+            if (c < 0) c = 0;
+            if (c > n - 2) c = n - 2;
+            t[d] = g[d] - c;
+            c0[d] = c;
+            c1[d] = c + 1;
+        }
+    }
+    int corners = 1 << p->ndim;
+    for (int m = 0; m < corners; ++m) {
+        int id[3] = {0, 0, 0};
+        double w = 1.0;
+        for (int d = 0; d < p->ndim; ++d) {
+            int up = (m >> d) & 1;
+            id[d] = up ? c1[d] : c0[d];
+            w *= up ? t[d] : 1.0 - t[d];
+        }
+        cidx[m] = flatten(p, id);
+        cw[m] = w;
+    }
+    if (gradw_dir) { /* grid-coordinate gradient of I[V] at the foot */
+        double gr[3];
+        q1_at(p, V, g, gr);
+        for (int d = 0; d < p->ndim; ++d) gradw_dir[d] = gr[d];
+    }
+    return corners;
+}
+
+/* Optimal policy pi_i = argmin_j Q_j (lowest index on ties, R10); -1 on
+ * targets.  Returns ||T(V) - V||_inf. */
+double ohjb_policy(const ohjb_problem *p, const double *V, int32_t *policy,
+                   int nthreads) {
+    long long N = node_count(p);
+    double *W = (double *)malloc(sizeof(double) * N);
+    double r = ohjb_apply(p, V, W, policy, NULL, 0, 0, nthreads);
+    free(W);
+    return r;
+}
+
+/* lam = g + beta P_pi^T lam, Jacobi iteration until ||dlam||_inf <= tol.
+ * Rows of target nodes and rows whose foot is outside the box are zero. */
+int ohjb_adjoint(const ohjb_problem *p, const int32_t *policy, const double *g,
+                 double tol, int max_iters, double *lam, double *final_res) {
+    long long N = node_count(p);
+    double beta = beta_of(p);
+    double *nx = (double *)malloc(sizeof(double) * N);
+    memcpy(lam, g, sizeof(double) * N);
+    int it = 0;
+    double r = INFINITY;
+    while (it < max_iters) {
+        memcpy(nx, g, sizeof(double) * N);
+        for (long long i = 0; i < N; ++i) {
+            if (policy[i] < 0 || p->target[i] != 0) continue;
+            long long ci[8];
+            double cw[8];
+            int nc = row_weights(p, i, policy[i], ci, cw, NULL, NULL);
+            for (int m = 0; m < nc; ++m) nx[ci[m]] += beta * cw[m] * lam[i];
+        }
+        r = 0.0;
+        for (long long i = 0; i < N; ++i) {
+            double d = fabs(nx[i] - lam[i]);
+            if (d > r) r = d;
+        }
+        memcpy(lam, nx, sizeof(double) * N);
+        ++it;
+        if (r <= tol) break;
+    }
+    free(nx);
+    if (final_res) *final_res = r;
+    return it;
+}
+
+/* dL/dtheta_i for s = exp(theta), f = s a + c:
+ *   lam_i * beta * h * s_i * (grad_y I[V](y_i) . a_pi(i)),
+ * and dL/dl_i = lam_i * gamma.  Zero on targets and for outside feet (theta)
+ * and on targets (cost). */
+void ohjb_grad(const ohjb_problem *p, const double *V, const int32_t *policy,
+               const double *lam, double *grad_theta, double *grad_cost) {
+    long long N = node_count(p);
+    double beta = beta_of(p), gam = gamma_of(p);
+    for (long long i = 0; i < N; ++i) {
+        if (grad_theta) grad_theta[i] = 0.0;
+        if (grad_cost) grad_cost[i] = 0.0;
+        if (policy[i] < 0 || p->target[i] != 0) continue;
+        if (grad_cost) grad_cost[i] = lam[i] * gam;
+        if (!grad_theta || p->dyn != 0) continue;
+        long long ci[8];
+        double cw[8], gr[3];
+        int nc = row_weights(p, i, policy[i], ci, cw, gr, V);
+        if (!nc) continue;
+        const double *a = p->controls + (long long)policy[i] * p->cdim;
+        double s = p->speed ? p->speed[i] : 1.0;
+        double dot = 0.0;
+        for (int d = 0; d < 2; ++d) dot += gr[d] / spacing(p, d) * a[d];
+        grad_theta[i] = lam[i] * beta * p->h * s * dot;
+    }
+}
+
+/* Loss L = (1/P) sum_p I[V](pts_p): values at the points, and the gradient
+ * g = dL/dV (the Q1 weights divided by P, accumulated per node). */
+void ohjb_points(const ohjb_problem *p, const double *V, const double *pts, int P,
+                 double *vals, double *g) {
+    long long N = node_count(p);
+    if (g)
+        for (long long i = 0; i < N; ++i) g[i] = 0.0;
+    for (int k = 0; k < P; ++k) {
+        const double *y = pts + (long long)k * p->ndim;
+        if (vals) vals[k] = ohjb_interp(p, V, y);
+        if (!g) continue;
+        double gg[3];
+        int c0[3] = {0, 0, 0};
+        double t[3] = {0, 0, 0};
+        for (int d = 0; d < p->ndim; ++d) {
+            gg[d] = (y[d] - p->lo[d]) / spacing(p, d);
+            if (gg[d] < 0) gg[d] = 0;
+            if (gg[d] > p->n[d] - 1) gg[d] = p->n[d] - 1;
+            int c = (int)floor(gg[d]);
+            if (c > p->n[d] - 2) c = p->n[d] - 2;
+            c0[d] = c;
+            t[d] = gg[d] - c;
+        }
+        for (int m = 0; m < (1 << p->ndim); ++m) {
+            int id[3] = {0, 0, 0};
+            double w = 1.0;
+            for (int d = 0; d < p->ndim; ++d) {
+                int up = (m >> d) & 1;
+                id[d] = c0[d] + up;
+                w *= up ? t[d] : 1.0 - t[d];
+            }
+            g[flatten(p, id)] += w / P;
+        }
+    }
+}
+
+/* Number of OpenMP threads the library would use (1 without OpenMP). */
+int ohjb_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

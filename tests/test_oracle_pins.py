@@ -1,0 +1,722 @@
+"""Pins of the FP64 oracle to things other than itself.
+
+Each test checks the oracle against what the paper or the mathematics fixes:
+exactness of Q1 interpolation on multilinear functions, brute-force policy
+enumeration with exact linear solves, graph shortest paths where every foot
+lands on a node, closed-form solutions (distance to disks, constant drift,
+the strip of Example 3.1, the box-boundary distance of Sec. 4.1), the
+invariants of the iteration and of the reconstruction (Sec. 3), the defining
+property of independent sub-domains (a restricted solve reproduces the full
+values on policy-closed sets), the concave-hull projection against a direct
+enumeration of labelled simplices, Table 1 of the paper, and central finite
+differences for the adjoint gradient.
+"""
+import itertools
+import json
+import math
+import os
+from collections import deque
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Q1 interpolation (Sec. 3, linear n-dimensional interpolation)
+
+def test_q1_exact_on_bilinear(orc):
+    g = np.random.default_rng(1)
+    nx, ny = 7, 5
+    lo, hi = (-1.0, 0.5), (2.0, 3.0)
+    x = np.linspace(lo[0], hi[0], nx)
+    y = np.linspace(lo[1], hi[1], ny)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    a, b, c, d = g.normal(size=4)
+    F = a + b * X + c * Y + d * X * Y
+    p = orc.Problem((nx, ny), lo, hi, [[1.0, 0.0]], np.zeros((ny, nx)), h=0.1)
+    for _ in range(200):
+        q = g.uniform(lo, hi)
+        exact = a + b * q[0] + c * q[1] + d * q[0] * q[1]
+        assert abs(orc.interp(p, F, q) - exact) < 1e-12
+
+
+def test_q1_exact_on_trilinear_and_periodic_wrap(orc):
+    g = np.random.default_rng(2)
+    n = (4, 6, 5)
+    lo, hi = (0.0, -1.0, 2.0), (1.5, 1.0, 3.0)
+    ax = [np.linspace(lo[d], hi[d], n[d]) for d in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    cf = g.normal(size=8)
+
+    def f(x, y, z):
+        return (cf[0] + cf[1] * x + cf[2] * y + cf[3] * z + cf[4] * x * y + cf[5] * y * z
+                + cf[6] * x * z + cf[7] * x * y * z)
+
+    F = f(X, Y, Z)
+    p = orc.Problem(n, lo, hi, [[0.0]], np.zeros(F.shape), h=0.1, dyn=1)
+    for _ in range(200):
+        q = g.uniform(lo, hi)
+        assert abs(orc.interp(p, F, q) - f(*q)) < 1e-12
+    # periodic third dimension: n nodes on a period; the last cell wraps to node 0
+    pp = orc.Problem(n, lo, hi, [[0.0]], np.zeros(F.shape), h=0.1, dyn=1, periodic=(0, 0, 1))
+    V = g.normal(size=F.shape)
+    dz = (hi[2] - lo[2]) / n[2]
+    xq, yq = ax[0][1], ax[1][2]
+    for t in (0.0, 0.25, 0.5, 0.9):
+        zq = lo[2] + (n[2] - 1 + t) * dz
+        want = (1 - t) * V[n[2] - 1, 2, 1] + t * V[0, 2, 1]
+        assert abs(orc.interp(pp, V, (xq, yq, zq)) - want) < 1e-12
+        assert abs(orc.interp(pp, V, (xq, yq, zq + (hi[2] - lo[2]))) - want) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Brute force: the optimal value of a discounted problem with finitely many
+# states is the componentwise minimum over deterministic stationary policies
+# of the policy values, each the solution of a linear system.
+
+def _grid_index(shape, idx):
+    out, mul = 0, 1
+    for d in range(len(shape)):
+        out += idx[d] * mul
+        mul *= shape[d]
+    return out
+
+
+def _stencil(shape, spacing, periodic, idx, off):
+    """Independent restatement of the foot rule: returns None when the foot
+    is outside the closed box (beyond 1e-6 cells), else [(flat, weight)]."""
+    nd = len(shape)
+    cells = []
+    for d in range(nd):
+        o = off[d] / spacing[d]
+        gd = idx[d] + o
+        n = shape[d]
+        if periodic[d]:
+            gd = gd % n
+            c = min(int(math.floor(gd)), n - 1)
+            cells.append((c, (c + 1) % n, gd - c))
+        else:
+            if o < -idx[d] - 1e-6 or o > (n - 1 - idx[d]) + 1e-6:
+                return None
+            gd = min(max(gd, 0.0), n - 1.0)
+            c = min(max(int(math.floor(gd)), 0), n - 2)
+            cells.append((c, c + 1, gd - c))
+    out = []
+    for bits in itertools.product((0, 1), repeat=nd):
+        w, ii = 1.0, []
+        for d, bt in enumerate(bits):
+            c0, c1, t = cells[d]
+            ii.append(c1 if bt else c0)
+            w *= t if bt else 1.0 - t
+        out.append((_grid_index(shape, ii), w))
+    return out
+
+
+def _brute_force(shape, spacing, periodic, target, feet, cost, lam, h, v_out):
+    """feet[i][j] = physical offset h f(x_i, a_j).  Returns the optimal V."""
+    N = int(np.prod(shape))
+    beta = math.exp(-lam * h)
+    gam = (1 - beta) / lam
+    free = [i for i in range(N) if target[i] == 0]
+    pos = {i: k for k, i in enumerate(free)}
+    F, A = len(free), len(feet[free[0]])
+    R = np.zeros((F, A, F))
+    b = np.zeros((F, A))
+    for k, i in enumerate(free):
+        idx = []
+        r = i
+        for d in range(len(shape)):
+            idx.append(r % shape[d])
+            r //= shape[d]
+        for j in range(A):
+            st = _stencil(shape, spacing, periodic, idx, feet[i][j])
+            b[k, j] = gam * cost[i]
+            if st is None:
+                b[k, j] += beta * v_out
+                continue
+            for flat, w in st:
+                if target[flat] == 0:
+                    R[k, j, pos[flat]] += w
+    pols = np.array(list(itertools.product(range(A), repeat=F)), dtype=np.int64)
+    ar = np.arange(F)
+    M = np.eye(F)[None] - beta * R[ar[None, :], pols]
+    rhs = b[ar[None, :], pols]
+    vals = np.linalg.solve(M, rhs[..., None])[..., 0]
+    vstar = vals.min(axis=0)
+    # a single policy attains the minimum in every component
+    assert np.abs(vals - vstar[None]).max(axis=1).min() < 1e-12
+    V = np.zeros(N)
+    V[free] = vstar
+    return V
+
+
+def test_brute_force_speed_current_cost(orc):
+    g = np.random.default_rng(3)
+    shape = (4, 3)
+    lo, hi = (0.0, 0.0), (3.0, 1.0)  # dx = 1, dy = 0.5: anisotropic cells
+    spacing = (1.0, 0.5)
+    N = 12
+    target = np.zeros(N, dtype=np.int32)
+    target[[0, 7, 9, 10]] = [1, 2, 1, 3]
+    ang = 0.3 + np.pi / 2 * np.arange(4)
+    ctr = np.stack([np.cos(ang), np.sin(ang)], 1)
+    s = g.uniform(0.5, 1.5, N)
+    cur = g.uniform(-0.2, 0.2, (N, 2))
+    cost = g.uniform(0.5, 2.0, N)
+    lam, h, v_out = 0.7, 0.8, 3.0
+    feet = [[h * (s[i] * ctr[j] + cur[i]) for j in range(4)] for i in range(N)]
+    Vb = _brute_force(shape, spacing, (0, 0), target, feet, cost, lam, h, v_out)
+    p = orc.Problem(shape, lo, hi, ctr, target, h=h, lam=lam, speed=s, current=cur, cost=cost,
+                    v_out=v_out)
+    V, it, r = orc.solve(p, tol=1e-15, max_iters=100000)
+    assert np.abs(V - Vb).max() < 1e-12
+
+
+def test_brute_force_long_feet_constant_drift(orc):
+    shape = (3, 3)
+    lo, hi = (-1.0, -1.0), (1.0, 1.0)
+    target = np.zeros(9, dtype=np.int32)
+    target[4] = 1
+    ang = 0.1 + np.pi / 2 * np.arange(4)
+    ctr = np.stack([np.cos(ang), np.sin(ang)], 1)
+    cur = np.tile([0.2, -0.1], (9, 1))
+    h = 1.3
+    feet = [[h * (ctr[j] + cur[i]) for j in range(4)] for i in range(9)]
+    Vb = _brute_force(shape, (1.0, 1.0), (0, 0), target, feet, np.ones(9), 1.0, h, 1.0)
+    p = orc.Problem(shape, lo, hi, ctr, target, h=h, current=cur)
+    V, _, _ = orc.solve(p, tol=1e-15)
+    assert np.abs(V - Vb).max() < 1e-12
+
+
+def test_brute_force_dubins_periodic(orc):
+    shape = (2, 2, 3)
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 2 * np.pi)
+    N = 12
+    target = np.zeros(N, dtype=np.int32)
+    for t in range(3):
+        target[_grid_index(shape, (0, 0, t))] = 1
+    ctr = np.array([[-1.0], [0.0], [1.0]])
+    h = 0.7
+    dth = 2 * np.pi / 3
+    feet = []
+    for i in range(N):
+        th = (i // 4) * dth
+        feet.append([np.array([h * np.cos(th), h * np.sin(th), h * u]) for u in (-1.0, 0.0, 1.0)])
+    Vb = _brute_force(shape, (1.0, 1.0, dth), (0, 0, 1), target, feet, np.ones(N), 1.0, h, 1.0)
+    p = orc.Problem(shape, lo, hi, ctr, target, h=h, dyn=1, periodic=(0, 0, 1))
+    V, _, _ = orc.solve(p, tol=1e-15)
+    assert np.abs(V - Vb).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Graph special case: every foot lands on a node, so V = 1 - beta^k with k
+# the graph distance to the target set (lambda = 1, l = 1).
+
+def _bfs(n_nodes, sources, neighbours):
+    dist = np.full(n_nodes, -1)
+    q = deque()
+    for s in sources:
+        dist[s] = 0
+        q.append(s)
+    while q:
+        u = q.popleft()
+        for v in neighbours(u):
+            if dist[v] < 0:
+                dist[v] = dist[u] + 1
+                q.append(v)
+    return dist
+
+
+@pytest.mark.parametrize("moves", ["axis", "king"])
+def test_graph_distance_2d(orc, moves):
+    nx, ny = 13, 9
+    g = np.random.default_rng(4)
+    target = np.zeros(nx * ny, dtype=np.int32)
+    target[g.choice(nx * ny, 3, replace=False)] = [1, 2, 3]
+    ctr = S.axis_controls() if moves == "axis" else S.king_controls()
+    h = 1.0
+    p = orc.Problem((nx, ny), (0.0, 0.0), (nx - 1.0, ny - 1.0), ctr, target, h=h)
+    V, _, _ = orc.solve(p, tol=1e-15)
+    steps = [tuple(int(v) for v in c) for c in ctr]
+
+    def nb(u):  # reversed edges: v -> u whenever u = v + step
+        x, y = u % nx, u // nx
+        out = []
+        for dx, dy in steps:
+            vx, vy = x - dx, y - dy
+            if 0 <= vx < nx and 0 <= vy < ny and target[vy * nx + vx] == 0:
+                out.append(vy * nx + vx)
+        return out
+
+    k = _bfs(nx * ny, np.nonzero(target)[0], nb)
+    assert (k >= 0).all()
+    want = 1.0 - np.exp(-h) ** k
+    assert np.abs(V - want).max() < 1e-12
+
+
+def test_graph_distance_dubins(orc):
+    # heading grid of 4 angles; h = dx = dtheta = pi/2: a step moves one node
+    # along the heading and turns by u * 90 degrees.
+    nx, ny, nt = 7, 6, 4
+    d = np.pi / 2
+    shape = (nx, ny, nt)
+    N = nx * ny * nt
+    g = np.random.default_rng(5)
+    cells = g.choice(nx * ny, 2, replace=False)
+    target = np.zeros(N, dtype=np.int32)
+    for t in range(nt):
+        target[cells + t * nx * ny] = [1, 2]
+    p = orc.Problem(shape, (0.0, 0.0, 0.0), ((nx - 1) * d, (ny - 1) * d, 2 * np.pi),
+                    [[-1.0], [0.0], [1.0]], target, h=d, dyn=1, periodic=(0, 0, 1))
+    V, _, _ = orc.solve(p, tol=1e-15)
+    head = [(1, 0), (0, 1), (-1, 0), (0, -1)]
+    fwd = {}
+    for v in range(N):
+        x, y, t = v % nx, (v // nx) % ny, v // (nx * ny)
+        for u in (-1, 0, 1):
+            X, Y, Tn = x + head[t][0], y + head[t][1], (t + u) % nt
+            if 0 <= X < nx and 0 <= Y < ny:
+                fwd.setdefault(X + Y * nx + Tn * nx * ny, []).append(v)
+
+    def nb(u):
+        return [v for v in fwd.get(u, []) if target[v] == 0]
+
+    k = _bfs(N, np.nonzero(target)[0], nb)
+    want = np.where(k >= 0, 1.0 - np.exp(-d) ** np.maximum(k, 0), 1.0)
+    assert np.abs(V - want).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Closed forms
+
+def test_disk_distance_convergence(orc):
+    """f = a, |a| = 1: v = 1 - exp(-dist) (Kruzhkov transform, Sec. 4.1)."""
+    errs = []
+    for n in (51, 101, 201):
+        d = S.c1(n=n)
+        p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"])
+        V, _, _ = orc.solve(p, tol=1e-12, nthreads=4)
+        X, Y = S.mesh2(n, n)
+        dist = np.min([np.maximum(np.hypot(X - c[0], Y - c[1]) - 0.1, 0) for c in d["centers"]], 0)
+        errs.append(np.abs(V.reshape(n, n) - (1 - np.exp(-dist))).max())
+    assert errs[1] < 0.025
+    assert errs[0] / errs[1] > 1.6 and errs[1] / errs[2] > 1.6
+
+
+def _drift_time(X, Y, q, rho, c):
+    dxx, dyy = q[0] - X, q[1] - Y
+    dc = dxx * c[0] + dyy * c[1]
+    c2 = c[0] ** 2 + c[1] ** 2
+    dd = dxx ** 2 + dyy ** 2
+    T = (-(dc + rho) + np.sqrt((dc + rho) ** 2 + (1 - c2) * (dd - rho ** 2))) / (1 - c2)
+    return np.where(dd <= rho ** 2, 0.0, T)
+
+
+def test_constant_drift_closed_form(orc):
+    """f = a + c with constant c: the reachable set at time T is the disk of
+    radius T around x + cT, so the arrival time at a disk solves a quadratic.
+    Pins the sign of the foot (x + h f) and the x/y order of the current."""
+    c = (0.3, -0.15)
+    cen = [(-0.5, 0.4), (0.45, -0.3)]
+    rho = 0.15
+    errs = []
+    for n in (51, 101, 201):
+        X, Y = S.mesh2(n, n)
+        lab = S.disk_labels(X, Y, np.array(cen), rho)
+        cur = np.tile(c, (n * n, 1))
+        p = orc.Problem((n, n), (-1, -1), (1, 1), S.circle_controls(64), lab, 2 / (n - 1),
+                        current=cur)
+        V, _, _ = orc.solve(p, tol=1e-12, nthreads=4)
+        T = np.minimum(*[_drift_time(X, Y, q, rho, c) for q in cen])
+        errs.append(np.abs(V.reshape(n, n) - (1 - np.exp(-T))).max())
+    assert errs[1] < 0.03
+    assert errs[0] > errs[1] > errs[2]
+    # the mirrored current must give a clearly different answer
+    n = 101
+    X, Y = S.mesh2(n, n)
+    T_wrong = np.minimum(*[_drift_time(X, Y, q, rho, (c[1], c[0])) for q in cen])
+    assert np.abs(V.reshape(201, 201)[::2, ::2] - (1 - np.exp(-T_wrong))).max() > 0.05
+
+
+@pytest.mark.parametrize("delta", [1.0, 0.5])
+def test_strip_example_exact(orc, delta):
+    """Example 3.1 (Sec. 3): strip, f = a_1, lambda = delta, l = 1, exits at
+    x1 = +-1 with g = 0.  Corrected closed form (the printed one is garbled):
+    v = (1 - exp(-delta (1 - |x1|)))/delta.  With axis controls and h = dx the
+    scheme is exact at the nodes."""
+    nx, ny = 41, 8
+    target = np.zeros((ny, nx), dtype=np.int32)
+    target[:, 0] = 2
+    target[:, -1] = 1
+    h = 2.0 / (nx - 1)
+    p = orc.Problem((nx, ny), (-1.0, 0.0), (1.0, 1.0), S.axis_controls(), target, h=h,
+                    lam=delta, periodic=(0, 1), v_out=1.0 / delta)
+    V, _, _ = orc.solve(p, tol=1e-15)
+    x = np.linspace(-1, 1, nx)
+    want = (1 - np.exp(-delta * (1 - np.abs(x)))) / delta
+    assert np.abs(V.reshape(ny, nx) - want[None, :]).max() < 1e-12
+    # off-node feet (32 controls, h = dx/2) converge to the same closed form
+    errs = []
+    for m in (41, 81):
+        tg = np.zeros((ny, m), dtype=np.int32)
+        tg[:, 0] = 2
+        tg[:, -1] = 1
+        p2 = orc.Problem((m, ny), (-1.0, 0.0), (1.0, 1.0), S.circle_controls(32), tg,
+                         h=1.0 / (m - 1), lam=delta, periodic=(0, 1), v_out=1.0 / delta)
+        V2, _, _ = orc.solve(p2, tol=1e-13)
+        xm = np.linspace(-1, 1, m)
+        wm = (1 - np.exp(-delta * (1 - np.abs(xm)))) / delta
+        errs.append(np.abs(V2.reshape(ny, m) - wm[None, :]).max())
+    assert errs[0] < 6e-3 and errs[0] / errs[1] > 1.8
+
+
+def _box_labels(n):
+    lab = np.zeros((n, n), dtype=np.int32)
+    lab[0, :] = 1      # y = -1
+    lab[:, n - 1] = 2  # x = +1
+    lab[n - 1, :] = 3  # y = +1
+    lab[:, 0] = 4      # x = -1
+    return lab
+
+
+def test_box_boundary_distance_exact(orc):
+    """Sec. 4.1: distance to the boundary of (-1,1)^2, lambda = 1:
+    v = 1 - exp(-(1 - max(|x1|, |x2|))) (the printed 'min' is a misprint)."""
+    n = 81
+    p = orc.Problem((n, n), (-1, -1), (1, 1), S.circle_controls(32), _box_labels(n), 2 / (n - 1))
+    V, _, _ = orc.solve(p, tol=1e-14)
+    X, Y = S.mesh2(n, n)
+    want = 1 - np.exp(-(1 - np.maximum(np.abs(X), np.abs(Y))))
+    assert np.abs(V.reshape(n, n) - want).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Invariants (Sec. 3)
+
+def test_iteration_invariants(orc):
+    d = S.c2(n=65)
+    p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"],
+                    speed=d["speed"], current=d["current"])
+    V = orc.initial(p)
+    for _ in range(60):
+        Vn, r = orc.apply(p, V)
+        assert (Vn <= V + 1e-15).all()  # monotone from the supersolution start
+        assert (Vn >= 0).all() and (Vn <= 1).all()
+        V = Vn
+    Vs, it, r = orc.solve(p, tol=1e-13)
+    assert r <= 1e-13
+    assert (Vs <= V + 1e-15).all()
+    # contraction bound of the stopping remark: ||V^n - V*|| <= beta/(1-beta) r_n
+    V = orc.initial(p)
+    for _ in range(40):
+        Vn, r = orc.apply(p, V)
+        V = Vn
+    Vn, r = orc.apply(p, V)
+    beta = p.beta
+    assert np.abs(Vn - Vs).max() <= beta / (1 - beta) * r + 1e-12
+    # Gauss-Seidel reaches the same fixed point
+    Vg, _, _ = orc.solve(p, tol=1e-13, gs=True)
+    assert np.abs(Vg - Vs).max() < 1e-11
+
+
+def test_ra_invariants_and_exact_quarters(orc):
+    """RA (Sec. 3): every node carries a label, X_k is in Sigma_k, V <= V_k,
+    and for the 4-split of the box boundary the sets tend to the exact
+    quarters (25 %, Table 1)."""
+    fr = []
+    for n in (41, 81):
+        p = orc.Problem((n, n), (-1, -1), (1, 1), S.circle_controls(32), _box_labels(n),
+                        2 / (n - 1))
+        Vaux, lab, ties = orc.ra(p, (1, 1), 1e-9)
+        Vfull, _, _ = orc.solve(p, tol=1e-14)
+        assert (lab != 0).all()
+        tl = _box_labels(n).reshape(-1)
+        for k in range(4):
+            assert ((lab >> k) & 1)[tl == k + 1].all()
+            assert (Vfull <= Vaux[k] + 1e-12).all()
+        fr.append(max(((lab >> k) & 1).mean() for k in range(4)))
+    assert 0.25 <= fr[1] < fr[0] <= 0.25 + 1.5 / 41
+
+
+def test_table1_shape(orc):
+    """Table 1 of Sec. 4.1: the largest reconstructed sub-domain shrinks as
+    the coarse grid is refined (eq. incap) towards the exact 25 %.  With the
+    threshold delta = dx_K the finer rows agree with the paper within 0.05."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_table1_distance.json")))
+    prev = 2.0
+    for n, _, paper in gold["rows"]:
+        dx = 2.0 / (n - 1)
+        p = orc.Problem((n, n), (-1, -1), (1, 1), S.circle_controls(32), _box_labels(n), dx)
+        _, lab, _ = orc.ra(p, (1, 1), dx)
+        f = max(((lab >> k) & 1).mean() for k in range(4))
+        assert f < prev and f >= gold["exact_max_fraction"]
+        prev = f
+        if n >= 15:
+            assert abs(f - paper) < 0.05, (n, f, paper)
+
+
+def test_nesting_in_threshold(orc):
+    d = S.c1(n=41)
+    p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"])
+    Vaux, lab_small, _ = orc.ra(p, (1, 1), 0.02)
+    _, lab_big, _ = orc.ra(p, (1, 1), 0.08)
+    assert ((lab_small & ~lab_big) == 0).all()
+    vmin, lab2, _ = orc.label(Vaux, d["labels"], 0.02)
+    assert (lab2 == lab_small).all()
+    assert np.allclose(vmin, Vaux.min(0))
+
+
+# --------------------------------------------------------------------------
+# Defining property of independent sub-domains (Def. and Prop. 2.1; Prop. 4.1)
+
+def _policy_closed(p, pol, member, shape):
+    """Largest subset of `member` closed under the policy stencils."""
+    nx, ny = shape
+    dxs = [p.spacing(0), p.spacing(1)]
+    keep = member.copy()
+    st = {}
+    sp = p.speed if p.speed is not None else np.ones(p.N)
+    cu = p.current if p.current is not None else np.zeros((p.N, 2))
+    for i in np.nonzero(member)[0]:
+        if p.target[i] != 0 or pol[i] < 0:
+            continue
+        a = p.controls[pol[i]]
+        off = p.h * (sp[i] * a + cu[i])
+        s = _stencil(shape, dxs, (0, 0), (i % nx, i // nx), off)
+        st[i] = [] if s is None else [f for f, w in s if w > 0]
+    changed = True
+    while changed:
+        changed = False
+        for i, nbrs in st.items():
+            if keep[i] and any(not keep[j] for j in nbrs):
+                keep[i] = False
+                changed = True
+    return keep
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_restricted_solve_reproduces_full(orc, which):
+    """Prop. 2.1 / Prop. 4.1: a solve restricted to a reconstructed
+    sub-domain reproduces the full-domain values on every subset closed under
+    the optimal policy; elsewhere (next to switching curves, where the
+    discrete union-of-targets value mixes both basins) the assembled ISA value
+    can only be larger, by at most the discretisation error."""
+    if which == "c1":
+        d = S.c1(n=81)
+        stride = (4, 4)
+    else:
+        d = S.c2(n=97, ntargets=6)
+        stride = (4, 4)
+    n = d["shape"][0]
+    p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"],
+                    speed=d["speed"], current=d["current"])
+    V, _, _ = orc.solve(p, tol=1e-13)
+    pol, _ = orc.policy(p, V)
+    # threshold of eq. (rep) with the Lipschitz constant M estimated by the
+    # largest discrete gradient of the coarse V = min_k V_k (C dx^q dropped)
+    Vaux, _, _ = orc.ra(p, stride, 0.0, tol=1e-13)
+    nk = orc.coarse_shape(p, stride)
+    dxk = 2.0 / (nk[0] - 1)
+    gy, gx = np.gradient(Vaux.min(0).reshape(nk[1], nk[0]), dxk)
+    delta = 2 * np.sqrt(gx ** 2 + gy ** 2).max() * dxk
+    vmin, lab, _ = orc.label(Vaux, p.target.reshape(n, n)[::stride[1], ::stride[0]], delta)
+    fine = orc.project(p, stride, lab)
+    Vbar, unc, its, Vk = orc.isa(p, fine, tol=1e-13, keep_vk=True)
+    assert unc == 0
+    covered = np.zeros(p.N, dtype=bool)
+    for k in range(p.ntargets):
+        member = ((fine >> k) & 1).astype(bool)
+        Dk = _policy_closed(p, pol, member, d["shape"])
+        assert (Vk[k][member] >= V[member] - 1e-12).all()  # restriction cannot help
+        assert np.abs(Vk[k][Dk] - V[Dk]).max(initial=0) < 1e-10
+        covered |= Dk
+    assert covered.mean() > 0.8
+    assert np.abs(Vbar - V)[covered].max() < 1e-10
+    assert (Vbar >= V - 1e-12).all()
+    assert (Vbar - V).max() < 2 * d["h"]
+    # a restriction to the whole grid is the full problem
+    Vall, _, _ = orc.solve(p, tol=1e-13, mask=np.ones(p.N, dtype=np.uint32), bit=0)
+    assert np.abs(Vall - V).max() < 1e-12
+
+
+def test_isa_error_bound_distance(orc):
+    """Prop. 4.1 and Table 3 (Sec. 4.1): the ISA value converges to the exact
+    solution at the rate of the full solve, and is no farther from it."""
+    errs_full, errs_isa = [], []
+    for n, st in ((41, 4), (81, 4)):
+        d = S.c1(n=n)
+        p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"])
+        V, _, _ = orc.solve(p, tol=1e-13)
+        Vaux, lab, _ = orc.ra(p, (st, st), 0.25, tol=1e-13)
+        fine = orc.project(p, (st, st), lab)
+        Vbar, unc, _, _ = orc.isa(p, fine, tol=1e-13)
+        assert unc == 0
+        X, Y = S.mesh2(n, n)
+        dist = np.min([np.maximum(np.hypot(X - c[0], Y - c[1]) - 0.1, 0) for c in d["centers"]], 0)
+        ex = (1 - np.exp(-dist)).reshape(-1)
+        errs_full.append(np.abs(V - ex).max())
+        errs_isa.append(np.abs(Vbar - ex).max())
+    assert errs_isa[1] <= errs_full[1] + 1e-12
+    assert errs_isa[0] / errs_isa[1] > 1.5
+
+
+# --------------------------------------------------------------------------
+# Projection through the concave hull Con (Sec. 4): direct enumeration of
+# every face of the Kuhn triangulation whose vertices are all labelled.
+
+def _con_2d(nK, r, coarse):
+    n = (nK - 1) * r + 1
+    fine = np.zeros((n, n), dtype=np.uint32)
+    cl = coarse.reshape(nK, nK)
+    for cy in range(nK - 1):
+        for cx in range(nK - 1):
+            tris = [[(0, 0), (1, 0), (1, 1)], [(0, 0), (0, 1), (1, 1)]]
+            for tri in tris:
+                for k in range(1, len(tri) + 1):
+                    for face in itertools.combinations(tri, k):
+                        bits = np.uint32(0xFFFFFFFF)
+                        for vx, vy in face:
+                            bits &= cl[cy + vy, cx + vx]
+                        if bits == 0:
+                            continue
+                        # fine nodes in the closed face: convex hull test via
+                        # barycentric coordinates on the lattice
+                        P = np.array(face, dtype=float) * r
+                        for py in range(r + 1):
+                            for px in range(r + 1):
+                                if _in_hull((px, py), P):
+                                    fine[cy * r + py, cx * r + px] |= bits
+    return fine.reshape(-1)
+
+
+def _in_hull(q, P):
+    q = np.array(q, dtype=float)
+    if len(P) == 1:
+        return np.allclose(q, P[0])
+    if len(P) == 2:
+        a, b = P
+        ab, aq = b - a, q - a
+        cross = ab[0] * aq[1] - ab[1] * aq[0]
+        t = aq @ ab / (ab @ ab)
+        return abs(cross) < 1e-9 and -1e-9 <= t <= 1 + 1e-9
+    a, b, c = P
+    M = np.array([b - a, c - a]).T
+    l1, l2 = np.linalg.solve(M, q - a)
+    return l1 >= -1e-9 and l2 >= -1e-9 and l1 + l2 <= 1 + 1e-9
+
+
+def test_projection_matches_concave_hull(orc):
+    g = np.random.default_rng(6)
+    nK, r = 6, 4
+    coarse = g.integers(0, 8, size=nK * nK).astype(np.uint32)
+    n = (nK - 1) * r + 1
+    p = orc.Problem((n, n), (-1, -1), (1, 1), [[1.0, 0.0]], np.zeros(n * n), 0.1)
+    got = orc.project(p, (r, r), coarse)
+    assert (got == _con_2d(nK, r, coarse)).all()
+    # coarse nodes map exactly
+    assert (got.reshape(n, n)[::r, ::r].reshape(-1) == coarse).all()
+
+
+def test_projection_3d_periodic(orc):
+    """Kuhn tetrahedra: a fine node inside a coarse cell whose 8 corners all
+    carry bit k carries bit k; a node on a coarse edge needs only the edge's
+    two end points; theta wraps."""
+    nKx, r = 4, 2
+    nKt, rt = 3, 2
+    n = ((nKx - 1) * r + 1, (nKx - 1) * r + 1, nKt * rt)
+    coarse = np.zeros((nKt, nKx, nKx), dtype=np.uint32)
+    coarse[...] = 1
+    coarse[0, 0, 0] = 0
+    p = orc.Problem(n, (0, 0, 0), (1, 1, 2 * np.pi), [[0.0]], np.zeros(int(np.prod(n))), 0.1,
+                    dyn=1, periodic=(0, 0, 1))
+    fine = orc.project(p, (r, r, rt), coarse.reshape(-1)).reshape(n[2], n[1], n[0])
+    assert fine[0, 0, 0] == 0                 # the unlabelled coarse node
+    assert fine[0, 0, 1] == 0                 # on the edge to it
+    assert fine[0, 2, 2] == 1                 # a labelled coarse node
+    assert fine[1, 1, 1] == 0                 # interior of a cell touching it
+    assert fine[3, 3, 3] == 1                 # interior of a fully labelled cell
+    assert fine[5, 3, 3] == 1                 # the wrapped last layer (theta -> 0)
+    assert fine[5, 0, 0] == 0                 # wrapped edge ending at the unlabelled node
+    assert fine[5, 0, 1] == 1                 # wrapped diagonal edge that avoids it
+
+
+# --------------------------------------------------------------------------
+# Adjoint: central finite differences with the policy frozen
+
+def _c5_small(n=21, A=16):
+    X, Y = S.mesh2(n, n)
+    g = np.random.default_rng(7)
+    th = 0.3 * np.sin(2.1 * X + 0.7) * np.cos(1.3 * Y - 0.2) + 0.1 * g.normal(size=X.shape)
+    cen = np.array([[-0.5, -0.4], [0.5, 0.45]])
+    lab = S.disk_labels(X, Y, cen, 0.2)
+    pts = g.uniform(-0.9, 0.9, size=(64, 2))
+    return X, Y, th, lab, pts
+
+
+def test_adjoint_matches_finite_differences(orc):
+    n, A = 21, 16
+    X, Y, th, lab, pts = _c5_small(n, A)
+    ctr = S.circle_controls(A)
+    h = 2.0 / (n - 1)
+
+    def prob(theta, cost=None):
+        return orc.Problem((n, n), (-1, -1), (1, 1), ctr, lab, h, speed=np.exp(theta),
+                           cost=cost)
+
+    def loss(theta, cost=None):
+        p = prob(theta, cost)
+        V, _, _ = orc.solve(p, tol=1e-15, max_iters=200000)
+        vals, _ = orc.points(p, V, pts, with_grad=False)
+        pol, _ = orc.policy(p, V)
+        return vals.mean(), pol
+
+    p = prob(th)
+    V, _, _ = orc.solve(p, tol=1e-15, max_iters=200000)
+    pol, _ = orc.policy(p, V)
+    _, gV = orc.points(p, V, pts)
+    lam, it, r = orc.adjoint(p, pol, gV, tol=1e-15)
+    gt, gc = orc.grad(p, V, pol, lam)
+    g = np.random.default_rng(8)
+    free = np.nonzero(lab.reshape(-1) == 0)[0]
+    idx = g.choice(free, 16, replace=False)
+    eps = 1e-6
+    checked = 0
+    for i in idx:
+        tp = th.reshape(-1).copy()
+        tm = tp.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        Lp, pp = loss(tp.reshape(n, n))
+        Lm, pm = loss(tm.reshape(n, n))
+        if (pp != pol).any() or (pm != pol).any():
+            continue  # kink: the policy changes inside the stencil
+        fd = (Lp - Lm) / (2 * eps)
+        assert abs(fd - gt[i]) <= 1e-6 * max(1e-3, abs(gt[i])) + 1e-9, (i, fd, gt[i])
+        checked += 1
+    assert checked >= 12
+    # cost field: L is affine in l with the policy frozen
+    cost = np.ones(n * n)
+    for i in idx[:6]:
+        cp = cost.copy()
+        cp[i] += 1e-3
+        Lp, pp = loss(th, cp)
+        L0, _ = loss(th, cost)
+        if (pp != pol).any():
+            continue
+        assert abs((Lp - L0) / 1e-3 - gc[i]) < 1e-8 + 1e-6 * abs(gc[i])
+
+
+def test_points_loss_gradient_is_interpolation_weights(orc):
+    n = 9
+    p = orc.Problem((n, n), (-1, -1), (1, 1), [[1.0, 0.0]], np.zeros(n * n), 0.1)
+    g = np.random.default_rng(9)
+    V = g.normal(size=n * n)
+    pts = g.uniform(-1, 1, size=(5, 2))
+    vals, gr = orc.points(p, V, pts)
+    # L is linear in V: L(V) = gr . V
+    assert abs(vals.mean() - gr @ V) < 1e-12
+    assert abs(gr.sum() - 1.0) < 1e-12
