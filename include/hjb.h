@@ -1,0 +1,250 @@
+/*
+ * hjb.h -- C ABI of the GB300 semi-Lagrangian HJB library.
+ *
+ * The library solves the discrete Hamilton-Jacobi-Bellman fixed point
+ * V = T(V) of Festa, "Reconstruction of independent sub-domains for a class
+ * of Hamilton Jacobi equations and its application to parallel computing"
+ * (arXiv:1405.3521), Sec. 3, eq. (SL)/(Tdef), for discounted optimal control
+ * (the Kruzhkov-transformed minimum-time problem when lambda = 1, l = 1):
+ *
+ *   [T(V)]_i = beta * min_{a in A} I[V](x_i + h f(x_i, a)) + gamma * l_i   (x_i free)
+ *   [T(V)]_i = 0                                                           (x_i target)
+ *   beta = exp(-lambda h),  gamma = (1 - beta) / lambda,
+ *
+ * with I the multilinear (Q1) interpolation on a structured grid, a foot
+ * strictly outside the closed box taking the value `value_out` (the image of
+ * the paper's +infinity on ghost nodes), and the reconstruction (RA, Sec. 3)
+ * and decomposed solve (ISA, Sec. 4) of independent sub-domains.
+ *
+ * Conventions for every entry point:
+ *  - Return value: HJB_OK (0) or a negative HJB_ERR_* code.  The message of
+ *    the last failure on the calling thread is returned by hjb_last_error().
+ *  - Arrays are node fields in row-major order with x fastest:
+ *    2D [ny][nx], 3D [nz][ny][nx].
+ *  - Array arguments may be device memory or host memory; the library
+ *    classifies each pointer (cudaPointerGetAttributes).  Host inputs are
+ *    copied to device workspaces and host outputs are copied back, on the
+ *    given stream, inside the call.  Device inputs are read in place.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *    call enqueues its work on that stream and returns after the stream has
+ *    completed it, so outputs and statistics are valid on return.
+ *  - The caller owns every array it passes.  A problem keeps the field
+ *    pointers given to hjb_create and reads them at every call: they must
+ *    stay valid and unchanged in meaning until hjb_destroy.  The library owns
+ *    only its workspaces (iteration buffers, work lists, graphs).
+ *  - Calls on one problem are not thread-safe; distinct problems are
+ *    independent.
+ */
+#ifndef HJB_H
+#define HJB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HJB_OK 0
+#define HJB_ERR_INVALID_ARG (-1)   /* bad descriptor, size or pointer */
+#define HJB_ERR_CUDA (-2)          /* a CUDA call failed (message says which) */
+#define HJB_ERR_OOM (-3)           /* device allocation failed */
+#define HJB_ERR_NOT_CONVERGED (-4) /* max_iters reached; outputs and stats are valid */
+#define HJB_ERR_UNSUPPORTED (-5)   /* valid but not supported combination */
+#define HJB_ERR_TIMEOUT (-6)       /* a bounded device wait gave up; outputs invalid */
+
+#define HJB_MAX_CONTROLS 128
+#define HJB_MAX_TARGETS 32
+
+/* Structured grid of Sec. 3 (the "regular mesh" case).  Non-periodic
+ * dimension d has n[d] >= 2 nodes x = lo + i (hi-lo)/(n-1); a periodic
+ * dimension has n[d] nodes on the period [lo, hi): x = lo + i (hi-lo)/n. */
+typedef struct {
+    int ndim;          /* 2 or 3 */
+    int n[3];          /* nodes per dimension, x first */
+    double lo[3];
+    double hi[3];
+    int periodic[3];   /* 0/1 per dimension */
+} hjb_grid;
+
+/* Dynamics f(x, a) of Sec. 2 ("y' = f(y, a)").
+ *  HJB_DYN_SPEED_CURRENT (2D): f = s(x) a + c(x), a in R^2 a control.
+ *     speed: node field s [N] (device or host), NULL means s = 1;
+ *     log_speed: node field theta [N] with s = exp(theta) (use one of the two);
+ *     current: node field c [N][2], NULL means c = 0.
+ *  HJB_DYN_DUBINS (3D, dimension 2 is the heading theta, periodic):
+ *     f = (v cos theta, v sin theta, u), u a scalar control; v = dubins_v. */
+#define HJB_DYN_SPEED_CURRENT 0
+#define HJB_DYN_DUBINS 1
+typedef struct {
+    int kind;
+    const float *speed;
+    const float *current;
+    const float *log_speed;
+    double dubins_v;
+} hjb_dynamics;
+
+/* Running cost l > 0 (hypothesis H0): a node field [N], or the constant
+ * l_const when l == NULL.  A constant cost lets the solver iterate on
+ * W = l/lambda - V (a pure max-plus-scaling form, see hjb_solve_opts). */
+typedef struct {
+    const float *l;
+    double l_const;
+} hjb_cost;
+
+/* Fictitious time step h and discount rate lambda > 0 (Sec. 3). */
+typedef struct {
+    double h;
+    double lambda;
+} hjb_discount;
+
+/* Discrete control set A (Sec. 3: "a discrete version of the control
+ * space"), host memory [count][dim], copied at hjb_create.  dim = 2 for
+ * HJB_DYN_SPEED_CURRENT, 1 for HJB_DYN_DUBINS.  count <= HJB_MAX_CONTROLS. */
+typedef struct {
+    int count;
+    int dim;
+    const float *a;
+} hjb_controls;
+
+/* Target (the boundary set Gamma / dG of Sec. 3, with exit cost g = 0),
+ * split into components Gamma_1..Gamma_m (Sec. 2, eq. HJD): labels [N],
+ * 0 = free node, k in 1..n_targets = node of component k.
+ * value_out: value of a foot outside the box and of ghost nodes; the
+ * natural choice is l/lambda (the cost of never arriving), 1 for the
+ * Kruzhkov transform. */
+typedef struct {
+    const uint8_t *labels;
+    int n_targets; /* m <= HJB_MAX_TARGETS */
+    double value_out;
+} hjb_target;
+
+typedef struct hjb_problem hjb_problem;
+
+/* Create a problem.  Validates every descriptor, classifies the field
+ * pointers, copies the control set, and sizes (but does not yet allocate)
+ * the workspaces.  On success *out receives the handle.
+ * Errors: HJB_ERR_INVALID_ARG (bad sizes, NULL required pointers, controls
+ * whose feet move more than 3 cells per step), HJB_ERR_UNSUPPORTED. */
+int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *cost,
+               const hjb_discount *disc, const hjb_controls *controls,
+               const hjb_target *target, hjb_problem **out);
+
+/* Free the problem and all its workspaces.  NULL is accepted. */
+int hjb_destroy(hjb_problem *p);
+
+/* Options of an iterative solve.
+ *  tol: stop when ||V^{n+1} - V^n||_inf <= tol (the stopping remark of
+ *       Sec. 3); by the contraction bound the distance to the fixed point is
+ *       then at most beta/(1-beta) tol.  tol <= 0 selects 0.5e-4 (1 - beta),
+ *       which guarantees 1e-4 in exact arithmetic.
+ *  max_iters: cap on applications of T (<= 0: 100,000).
+ *  use_w_form: 1 = iterate on W = l/lambda - V (constant cost only),
+ *       0 = iterate on V, -1 = automatic (W form when the cost is constant).
+ *  v_init: optional warm start [N] (a previous solution), NULL = start from
+ *       value_out on free nodes and 0 on targets (a supersolution).
+ *  sweeps_per_check: sweeps between two convergence tests in the device loop
+ *       (<= 0: library default). */
+typedef struct {
+    double tol;
+    int max_iters;
+    int use_w_form;
+    const float *v_init;
+    int sweeps_per_check;
+} hjb_solve_opts;
+
+/* Statistics of one solve (per problem or per sub-domain). */
+typedef struct {
+    int iterations;        /* applications of T */
+    int converged;         /* 1 if the residual reached tol */
+    long long node_updates;/* evaluations of T at free nodes (all controls) */
+    double final_residual; /* last ||V^{n+1} - V^n||_inf */
+    double ms;             /* device time of the call, milliseconds */
+    long long ties;        /* label decisions within 1e-6 of the threshold */
+    long long labelled;    /* sum over sub-domains of their node counts */
+    long long launches;    /* CUDA kernels the call launched */
+} hjb_stats;
+
+/* Full-domain solve of V = T(V) by value iteration V^{n+1} = T(V^n)
+ * (Sec. 3, eq. SL and the iteration following it).  v_out [N] receives V.
+ * Returns HJB_ERR_NOT_CONVERGED (outputs valid) when max_iters is hit. */
+int hjb_solve(hjb_problem *p, const hjb_solve_opts *opts, float *v_out, hjb_stats *stats,
+              void *stream);
+
+/* Options of the reconstruction (RA, Sec. 3, and ISA steps 1-2, Sec. 4).
+ *  coarse_stride[d]: the coarse grid K is every stride-th fine node (the
+ *       superimposed grids of the projection remark); (n-1) % stride == 0
+ *       for non-periodic dimensions, n % stride == 0 for periodic ones.
+ *  h_coarse: time step on K (<= 0: h * coarse_stride[0]).
+ *  delta: threshold of eq. (rep), |V_k - V| <= delta (Prop. 3.1);
+ *       delta < 0 selects 2 (C dx_K^q + M dx_K) with the C, M, q below.
+ *  tol / max_iters: stopping rule of the auxiliary solves (RA step 1). */
+typedef struct {
+    int coarse_stride[3];
+    double h_coarse;
+    double delta;
+    double C, M, q;
+    double tol;
+    int max_iters;
+} hjb_ra_opts;
+
+/* RA (Sec. 3, steps 1-3) on the coarse grid followed by ISA step 2
+ * (projection through the concave hull Con, Sec. 4).
+ *  fine_mask_out [N]: bit k-1 set iff the fine node lies in the projected
+ *       sub-domain of target component k.
+ *  coarse_labels_out [N_K] (optional): the coarse labels (same bit layout).
+ *  v_aux_out [m][N_K] (optional): the auxiliary solutions V_k of step 1.
+ *  stats (optional): iterations = max over the auxiliary solves,
+ *       node_updates = their sum, ties = label decisions within 1e-6 of
+ *       delta, labelled = sum over k of |Sigma_k| on the fine grid. */
+int hjb_subdomains(hjb_problem *p, const hjb_ra_opts *ra, uint32_t *fine_mask_out,
+                   uint32_t *coarse_labels_out, float *v_aux_out, hjb_stats *stats,
+                   void *stream);
+
+/* ISA steps 3-4 (Sec. 4): for every k, iterate V_k = T(V_k) restricted to
+ * the nodes with bit k-1 of fine_mask (every target node inside is kept as
+ * a target, nodes outside are ghosts with value value_out), all sub-domains
+ * in one persistent launch with per-sub-domain convergence; then
+ * Vbar(j) = min{ V_k(j) : bit k-1 of fine_mask[j] }.  Nodes in no
+ * sub-domain receive value_out.
+ *  per_subdomain (optional): [n_targets] statistics; total (optional). */
+int hjb_solve_decomposed(hjb_problem *p, const uint32_t *fine_mask, const hjb_solve_opts *opts,
+                         float *v_out, hjb_stats *per_subdomain, hjb_stats *total,
+                         void *stream);
+
+/* Many independent problems (uneven grids allowed) in one persistent,
+ * graph-captured launch with per-problem convergence.  All problems must use
+ * the same dynamics kind, control set size and cost form.
+ *  v_out[i] [N_i] receives problem i's V; per_problem (optional) [count]. */
+int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opts *opts,
+                    float *const *v_out, hjb_stats *per_problem, void *stream);
+
+/* Adjoint of the converged fixed point with respect to a node field theta
+ * (not in the paper: the transposed linear system of V = beta P_pi V + b
+ * with the optimal policy pi frozen and recomputed from v):
+ *     (I - beta P_pi)^T lambda = grad_v,
+ *  wrt = 0: grad_out = dL/dtheta for the log-speed field (s = exp(theta),
+ *           HJB_DYN_SPEED_CURRENT):  lambda_i beta h s_i grad I[V](y_i) . a_pi(i)
+ *  wrt = 1: grad_out = dL/dl for the cost field: lambda_i gamma.
+ *  v [N]: the converged solution; grad_v [N]: dL/dV.  opts->tol bounds
+ *  ||lambda^{n+1} - lambda^n||_inf.  stats (optional). */
+int hjb_backward(hjb_problem *p, const float *v, const float *grad_v, int wrt,
+                 const hjb_solve_opts *opts, float *grad_out, hjb_stats *stats, void *stream);
+
+/* Values of I[V] at P points [P][ndim] (physical coordinates, clamped into
+ * the box) and, if grad_v != NULL, the gradient of the loss
+ * L = (1/P) sum_p I[V](points_p) with respect to V, written to grad_v [N]. */
+int hjb_point_values(hjb_problem *p, const float *v, const float *points, int P, float *values,
+                     float *grad_v, void *stream);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *hjb_last_error(void);
+
+/* Library version string. */
+const char *hjb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HJB_H */

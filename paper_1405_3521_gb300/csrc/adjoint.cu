@@ -1,0 +1,313 @@
+// adjoint.cu -- gradient of a loss on the converged value function with
+// respect to a node field (log-speed theta or running cost l).
+//
+// The paper (Festa, arXiv:1405.3521) stops at the forward solve; with the
+// optimal policy pi frozen, the converged fixed point of Sec. 3 is the linear
+// system V = beta P_pi V + b, so for a loss L(V):
+//     (I - beta P_pi)^T lambda = dL/dV,
+//     dL/dtheta_i = lambda_i beta h s_i grad I[V](y_i) . a_pi(i)   (s = e^theta)
+//     dL/dl_i     = lambda_i gamma.
+// pi is recomputed from V (no per-control data is stored), the transposed
+// iteration lambda <- g + beta P_pi^T lambda scatters the Q1 weights of each
+// node's foot with atomics, and its L-infinity residual is reduced in the
+// same pass that re-arms the next target buffer; the last CTA of that pass
+// takes the stopping decision and drives the CUDA-graph loop.
+#include <math.h>
+
+#include "hjb_internal.cuh"
+
+using namespace hjbk;
+using hjbh::AdjArgs;
+using hjbh::AdjCtl;
+using hjbh::AdjProblem;
+
+namespace {
+
+// Foot of node (gx, gy) under control (ax, ay): the same arithmetic as the
+// boundary path of the sweep (cell offsets in FP32, 1e-6-cell tolerance,
+// clamping onto the face), returning the cell and the fractions.
+struct Foot {
+    bool inside;
+    int cx, cy;
+    float tx, ty;
+};
+
+__device__ __forceinline__ Foot foot_of(const AdjProblem &ap, int gx, int gy, float sx, float sy,
+                                        float ox0, float oy0, float ax, float ay) {
+    Foot f;
+    float ox = fmaf(sx, ax, ox0), oy = fmaf(sy, ay, oy0);
+    const float lox = -static_cast<float>(gx), hix = static_cast<float>(ap.nx - 1 - gx);
+    const float loy = -static_cast<float>(gy), hiy = static_cast<float>(ap.ny - 1 - gy);
+    f.inside = !((ox < lox - 1e-6f) | (ox > hix + 1e-6f) | (oy < loy - 1e-6f) | (oy > hiy + 1e-6f));
+    ox = fminf(fmaxf(ox, lox), hix);
+    oy = fminf(fmaxf(oy, loy), hiy);
+    const float kx = floorf(ox), ky = floorf(oy);
+    int cx = gx + static_cast<int>(kx), cy = gy + static_cast<int>(ky);
+    float tx = ox - kx, ty = oy - ky;
+    if (cx > ap.nx - 2) {
+        cx = ap.nx - 2;
+        tx = 1.0f;
+    }
+    if (cy > ap.ny - 2) {
+        cy = ap.ny - 2;
+        ty = 1.0f;
+    }
+    f.cx = cx;
+    f.cy = cy;
+    f.tx = tx;
+    f.ty = ty;
+    return f;
+}
+
+__device__ __forceinline__ float interp(const float *V, int nx, const Foot &f) {
+    const long long i = static_cast<long long>(f.cy) * nx + f.cx;
+    const float a = fmaf(f.tx, V[i + 1], (1.0f - f.tx) * V[i]);
+    const float b = fmaf(f.tx, V[i + nx + 1], (1.0f - f.tx) * V[i + nx]);
+    return fmaf(f.ty, b, (1.0f - f.ty) * a);
+}
+
+struct NodeDyn {
+    float sx, sy, ox0, oy0, s;
+};
+
+__device__ __forceinline__ NodeDyn node_dyn(const AdjProblem &ap, long long i) {
+    NodeDyn d;
+    d.s = ap.speed ? ap.speed[i] : 1.0f;
+    float cx = 0.0f, cy = 0.0f;
+    if (ap.current) {
+        const float2 c = reinterpret_cast<const float2 *>(ap.current)[i];
+        cx = c.x;
+        cy = c.y;
+    }
+    d.sx = d.s * ap.hx;
+    d.sy = d.s * ap.hy;
+    d.ox0 = cx * ap.hx;
+    d.oy0 = cy * ap.hy;
+    return d;
+}
+
+#define GRID_STRIDE(i, n)                                                                  \
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < (n); \
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+
+__global__ void policy_kernel(AdjProblem ap, const __grid_constant__ ControlTable C, const float *V,
+                              int8_t *policy, unsigned *ties) {
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    unsigned nt = 0;
+    GRID_STRIDE(i, N) {
+        if (ap.labels[i] != 0) {
+            policy[i] = -1;
+            continue;
+        }
+        const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
+        const NodeDyn d = node_dyn(ap, i);
+        float best = INFINITY, second = INFINITY;
+        int arg = 0;
+        bool arg_inside = false;
+        for (int j = 0; j < C.count; ++j) {
+            const Foot f = foot_of(ap, gx, gy, d.sx, d.sy, d.ox0, d.oy0, C.ax[j], C.ay[j]);
+            const float q = f.inside ? interp(V, ap.nx, f) : ap.vout;
+            if (q < best) {
+                second = best;
+                best = q;
+                arg = j;
+                arg_inside = f.inside;
+            } else if (q < second) {
+                second = q;
+            }
+        }
+        if (second - best <= 1e-6f) ++nt;
+        policy[i] = arg_inside ? static_cast<int8_t>(arg) : static_cast<int8_t>(-2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nt += __shfl_xor_sync(0xffffffffu, nt, o);
+    if ((threadIdx.x & 31) == 0 && nt) atomicAdd(ties, nt);
+}
+
+// lambda_dst += beta P_pi^T lambda_src (dst pre-armed with g).
+__device__ __forceinline__ void scatter_body(const AdjArgs &A) {
+    const AdjProblem &ap = A.ap;
+    const int par = A.ctl->parity;
+    const float *src = A.L[par];
+    float *dst = A.L[par ^ 1];
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    GRID_STRIDE(i, N) {
+        const int p = A.policy[i];
+        if (p < 0) continue;
+        const float lam = src[i];
+        if (lam == 0.0f) continue;
+        const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
+        const NodeDyn d = node_dyn(ap, i);
+        const Foot f = foot_of(ap, gx, gy, d.sx, d.sy, d.ox0, d.oy0, A.ctrl.ax[p], A.ctrl.ay[p]);
+        const float bl = ap.beta * lam;
+        const long long c = static_cast<long long>(f.cy) * ap.nx + f.cx;
+        atomicAdd(dst + c, bl * (1.0f - f.tx) * (1.0f - f.ty));
+        atomicAdd(dst + c + 1, bl * f.tx * (1.0f - f.ty));
+        atomicAdd(dst + c + ap.nx, bl * (1.0f - f.tx) * f.ty);
+        atomicAdd(dst + c + ap.nx + 1, bl * f.tx * f.ty);
+    }
+}
+
+// Residual ||lambda_dst - lambda_src||_inf, re-arming src with g for the
+// next iteration; the last CTA decides convergence.
+__global__ void adj_resid(const __grid_constant__ AdjArgs A) {
+    AdjCtl *ctl = A.ctl;
+    // a finished loop may still run the rest of its body: leave the result
+    if (ctl->converged) return;
+    const int par = ctl->parity;
+    float *src = A.L[par];
+    const float *dst = A.L[par ^ 1];
+    const long long N = static_cast<long long>(A.ap.nx) * A.ap.ny;
+    float r = 0.0f;
+    GRID_STRIDE(i, N) {
+        r = fmaxf(r, fabsf(dst[i] - src[i]));
+        src[i] = A.g[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    __shared__ float s_r[THREADS / 32];
+    __shared__ int s_last;
+    if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = s_r[0];
+        for (int w = 1; w < THREADS / 32; ++w) m = fmaxf(m, s_r[w]);
+        atomicMax(&ctl->res_bits, __float_as_uint(m));
+        __threadfence();
+        s_last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const float res = __uint_as_float(ctl->res_bits);
+        ctl->res_bits = 0u;
+        ctl->iters += 1;
+        ctl->final_res = res;
+        ctl->parity = par ^ 1;
+        ctl->done_ctas = 0u;
+        int go = 1;
+        if (res <= ctl->tol) {
+            ctl->converged = 1;
+            go = 0;
+        } else if (ctl->iters >= ctl->max_iters) {
+            ctl->converged = 2;
+            go = 0;
+        }
+        __threadfence();
+        if (A.use_handle) cudaGraphSetConditional(A.handle, go ? 1u : 0u);
+    }
+}
+
+// A finished loop may still run the rest of its body: the scatter and
+// residual kernels return at once when ctl->converged is set.
+__global__ void adj_scatter_guarded(const __grid_constant__ AdjArgs A) {
+    if (A.ctl->converged) return;
+    scatter_body(A);
+}
+
+__global__ void adj_init_kernel(const float *g, float *L0, float *L1, long long n, AdjCtl *ctl,
+                                float tol, int max_iters) {
+    GRID_STRIDE(i, n) {
+        L0[i] = g[i];
+        L1[i] = g[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->done_ctas = 0u;
+        ctl->res_bits = 0u;
+        ctl->iters = 0;
+        ctl->parity = 0;
+        ctl->converged = 0;
+        ctl->final_res = 0.0f;
+        ctl->tol = tol;
+        ctl->max_iters = max_iters;
+        ctl->error = 0;
+    }
+}
+
+__global__ void adj_grad_kernel(AdjProblem ap, const __grid_constant__ ControlTable C, const float *V,
+                                const int8_t *policy, const float *lam, int wrt, float *out) {
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    GRID_STRIDE(i, N) {
+        const int p = policy[i];
+        float g = 0.0f;
+        if (wrt == 1) {
+            if (p != -1) g = lam[i] * ap.gamma;  // every free node
+        } else if (p >= 0) {
+            const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
+            const NodeDyn d = node_dyn(ap, i);
+            const Foot f = foot_of(ap, gx, gy, d.sx, d.sy, d.ox0, d.oy0, C.ax[p], C.ay[p]);
+            const long long c = static_cast<long long>(f.cy) * ap.nx + f.cx;
+            const float v00 = V[c], v10 = V[c + 1], v01 = V[c + ap.nx], v11 = V[c + ap.nx + 1];
+            const float dgx = (1.0f - f.ty) * (v10 - v00) + f.ty * (v11 - v01);
+            const float dgy = (1.0f - f.tx) * (v01 - v00) + f.tx * (v11 - v10);
+            const float dot = dgx / ap.dx * C.ax[p] + dgy / ap.dy * C.ay[p];
+            g = lam[i] * ap.beta * ap.h * d.s * dot;
+        }
+        out[i] = g;
+    }
+}
+
+__global__ void points_kernel(int nx, int ny, float lo0, float lo1, float idx0, float idx1,
+                              const float *V, const float *pts, int P, float *vals, float *grad) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    float gx = (pts[2 * k] - lo0) * idx0;
+    float gy = (pts[2 * k + 1] - lo1) * idx1;
+    gx = fminf(fmaxf(gx, 0.0f), static_cast<float>(nx - 1));
+    gy = fminf(fmaxf(gy, 0.0f), static_cast<float>(ny - 1));
+    int cx = static_cast<int>(floorf(gx)), cy = static_cast<int>(floorf(gy));
+    cx = cx > nx - 2 ? nx - 2 : cx;
+    cy = cy > ny - 2 ? ny - 2 : cy;
+    const float tx = gx - cx, ty = gy - cy;
+    const long long c = static_cast<long long>(cy) * nx + cx;
+    const float w00 = (1.0f - tx) * (1.0f - ty), w10 = tx * (1.0f - ty), w01 = (1.0f - tx) * ty,
+                w11 = tx * ty;
+    if (vals) vals[k] = w00 * V[c] + w10 * V[c + 1] + w01 * V[c + nx] + w11 * V[c + nx + 1];
+    if (grad) {
+        const float s = 1.0f / static_cast<float>(P);
+        atomicAdd(grad + c, w00 * s);
+        atomicAdd(grad + c + 1, w10 * s);
+        atomicAdd(grad + c + nx, w01 * s);
+        atomicAdd(grad + c + nx + 1, w11 * s);
+    }
+}
+
+int blocks_for(long long n) {
+    long long b = (n + THREADS - 1) / THREADS;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return static_cast<int>(b);
+}
+
+}  // namespace
+
+namespace hjbh {
+
+void launch_policy(const AdjProblem &ap, const ControlTable &C, const float *V, int8_t *policy,
+                   unsigned *ties_out, cudaStream_t st) {
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    policy_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, policy, ties_out);
+}
+
+const void *adj_scatter_kernel() { return reinterpret_cast<const void *>(&adj_scatter_guarded); }
+const void *adj_resid_kernel() { return reinterpret_cast<const void *>(&adj_resid); }
+
+void launch_adj_init(const float *g, float *L0, float *L1, long long n, AdjCtl *ctl, float tol,
+                     int max_iters, cudaStream_t st) {
+    adj_init_kernel<<<blocks_for(n), THREADS, 0, st>>>(g, L0, L1, n, ctl, tol, max_iters);
+}
+
+void launch_adj_grad(const AdjProblem &ap, const ControlTable &C, const float *V,
+                     const int8_t *policy, const float *lam, int wrt, float *out, cudaStream_t st) {
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    adj_grad_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, policy, lam, wrt, out);
+}
+
+void launch_points(int nx, int ny, double lo0, double lo1, double dx0, double dx1, const float *V,
+                   const float *pts, int P, float *vals, float *grad, cudaStream_t st) {
+    points_kernel<<<(P + THREADS - 1) / THREADS, THREADS, 0, st>>>(
+        nx, ny, static_cast<float>(lo0), static_cast<float>(lo1), static_cast<float>(1.0 / dx0),
+        static_cast<float>(1.0 / dx1), V, pts, P, vals, grad);
+}
+
+}  // namespace hjbh

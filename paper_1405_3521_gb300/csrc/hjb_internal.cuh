@@ -1,0 +1,232 @@
+// hjb_internal.cuh -- device-side data structures shared by the kernels and
+// the host runtime of the GB300 HJB library.  Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hjbk {
+
+// 2D tile: 32 x 8 nodes, one node per thread (256 threads).
+constexpr int TX = 32;
+constexpr int TY = 8;
+// 3D tile: 32 x 8 x TZ nodes, each thread walks TZ layers.
+constexpr int TZ = 4;
+// x halo padding in shared memory: TMA boxes must start at x coordinates
+// whose byte offset is a multiple of 16, so the x halo is widened to 4 floats.
+constexpr int XPAD = 4;
+constexpr int TW = TX + 2 * XPAD;  // shared-memory row width (floats)
+constexpr int THREADS = 256;
+constexpr int MAX_SLOTS = 1024;
+constexpr int MAX_CTRL = 128;
+#define HJB_MAX_TARGETS_DEV 32
+// Bounded waits: a TMA transaction that has not completed after this many
+// nanoseconds is treated as lost; the kernel records an error and returns.
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+// Discrete control set, passed by value in the kernel parameters so that a
+// fully unrolled loop reads the components as constant-bank operands.
+struct ControlTable {
+    float ax[MAX_CTRL];
+    float ay[MAX_CTRL];
+    int count;
+};
+
+// One independent fixed-point problem ("slot") of a launch: the full grid,
+// an auxiliary problem of the reconstruction, a sub-domain of the decomposed
+// solve, or one problem of a batch.
+struct alignas(128) SlotDesc {
+    CUtensorMap tmap[2];        // TMA maps of the two iteration buffers
+    float *V[2];                // pitched iteration buffers [nzl][ny][pitch]
+    const float *speed;         // node field s (or null: s = 1)
+    const float *current;       // node field c [N][2] (or null)
+    const float *cost;          // node field l (or null: constant)
+    const uint8_t *labels;      // target labels [N]
+    const uint32_t *mask;       // sub-domain bitmask [N] (or null)
+    const int *tile_list;       // tiles of this slot (or null: all tiles)
+    const float2 *trig;         // Dubins: per heading layer (v h cos/dx, v h sin/dy)
+    long long zstride;          // floats between layers of V
+    int nx, ny, nz, pitch;
+    int tiles_x, tiles_y, tiles_z, ntiles;
+    int mask_bit, only_target;  // restricted problem / auxiliary problem selectors
+    int zdup;                   // duplicated heading layers on each side (periodic z)
+    int halo;                   // interpolation halo in x, y (cells)
+    float hx, hy, hz;           // h / spacing per dimension
+    float beta;                 // exp(-lambda h)
+    float gl;                   // gamma * l_const (V form)
+    float gamma;                // (1 - beta)/lambda (V form with a cost field)
+    float vout;                 // ghost / outside value in the iterated variable
+    float vtarget;              // target value in the iterated variable
+    float tol;
+    int max_iters;
+    int pad_[2];
+};
+
+// Convergence state of a slot.
+struct SlotState {
+    unsigned res_bits;           // atomicMax target: residual of the running sweep
+    int iters;
+    int done;
+    int converged;               // 1 tol reached, 2 stagnated at rounding level
+    int final_parity;            // buffer holding the latest iterate
+    int stall;
+    float best_res;
+    float final_res;
+    unsigned long long updates;  // free-node evaluations of T
+    unsigned long long changed;  // (reserved)
+};
+
+// Launch-wide control block.
+struct Ctl {
+    unsigned done_ctas;
+    unsigned sweep;      // number of sweeps so far (parity of the source buffer)
+    int nactive;
+    int total_items;
+    int error;           // non-zero: a bounded wait gave up
+    unsigned launches;   // sweep kernels run (including empty ones at the loop's end)
+    int pad_[2];
+    int act_slot[MAX_SLOTS];
+    int act_prefix[MAX_SLOTS + 1];
+};
+
+struct SweepArgs {
+    const SlotDesc *slots;
+    SlotState *state;
+    Ctl *ctl;
+    int nslots;
+    int use_handle;
+    cudaGraphConditionalHandle handle;
+    float stall_tol;
+    ControlTable ctrl;
+};
+
+}  // namespace hjbk
+
+// Host-side entry points of the kernels (defined in the .cu files).
+namespace hjbh {
+
+// Kernel selection key for the sweep.
+struct SweepKey {
+    int dubins;  // 0: 2D speed/current, 1: 3D Dubins
+    int wform;   // iterate on W (max form) instead of V (min form)
+    int na;      // number of controls
+    int halo;    // 2 or 4 (2D), 2 (3D)
+};
+
+// Returns the kernel function for a key (nullptr if unsupported) and the
+// dynamic shared memory it needs.
+const void *sweep_kernel(const SweepKey &k, size_t *smem);
+// Occupancy-derived persistent grid size for the kernel.
+int sweep_grid(const SweepKey &k);
+
+// Kernels used around the loop (see their definitions for the contracts).
+void launch_loop_init(const hjbk::SlotDesc *slots, hjbk::SlotState *state, hjbk::Ctl *ctl,
+                      int nslots, const int *ntiles_dev, cudaStream_t st);
+void launch_init_values(const hjbk::SlotDesc *slots, int nslots, int max_nodes, int wform,
+                        float c_over, const float *v_init, cudaStream_t st);
+void launch_extract(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int slot,
+                    float *out, int wform, float c_over, cudaStream_t st);
+
+// Grid geometry shared by the reconstruction kernels.
+struct GridDims {
+    int ndim;
+    int n[3];
+    int periodic[3];
+};
+
+// Fine -> coarse gather of node fields at the coarse stride (any pointer may
+// be null).
+void launch_gather_coarse(const GridDims &fine, const GridDims &coarse, const int stride[3],
+                          const float *speed, const float *current, const float *cost,
+                          const uint8_t *labels, float *c_speed, float *c_current,
+                          float *c_cost, uint8_t *c_labels, cudaStream_t st);
+// RA steps 2-3: labels of the coarse nodes from the m auxiliary solutions
+// held by slots[0..m) (min property + threshold of eq. rep).  ties_out is an
+// unsigned long long counter (accumulated); vmin_out optional.
+void launch_label(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int m,
+                  const GridDims &coarse, const uint8_t *labels, float delta, int wform,
+                  uint32_t *labels_out, float *vmin_out, unsigned long long *ties_out,
+                  cudaStream_t st);
+// Largest centred-difference gradient norm of min_k V_k over the coarse grid
+// (physical units, dx per dimension); result as float bits in *out (atomicMax).
+void launch_grad_max(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int m,
+                     int wform, const GridDims &coarse, const float dx[3], unsigned *out,
+                     cudaStream_t st);
+// ISA step 2: fine bitmask from coarse labels through the Kuhn simplices.
+void launch_project(const GridDims &fine, const GridDims &coarse, const int stride[3],
+                    const uint32_t *coarse_labels, uint32_t *fine_mask, cudaStream_t st);
+// Work lists of the decomposed solve: for every sub-domain k < m, the tiles
+// containing at least one node of it; writes slots[k].ntiles on the device.
+void launch_tile_lists(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z,
+                       const uint32_t *mask, int m, uint32_t *tile_bits, int *lists,
+                       hjbk::SlotDesc *slots, cudaStream_t st);
+// ISA step 4: Vbar = min over the sub-domains containing each node.
+void launch_assemble(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int m,
+                     const GridDims &fine, const uint32_t *mask, int wform, float c_over,
+                     float vout_v, float *out, cudaStream_t st);
+// Largest |value| of a node field (float bits, atomicMax) -- used for the
+// interpolation halo.
+void launch_absmax(const float *x, long long n, int stride, int offset, unsigned *out,
+                   cudaStream_t st);
+// s = exp(theta) elementwise.
+void launch_exp(const float *theta, float *s, long long n, cudaStream_t st);
+// Count of bits per sub-domain (sum over k of |Sigma_k|) into *out.
+void launch_popcount(const uint32_t *mask, long long n, unsigned long long *out, cudaStream_t st);
+
+// ----- adjoint (adjoint.cu) -------------------------------------------------
+
+// Geometry and coefficients of a 2D speed/current problem for the adjoint.
+struct AdjProblem {
+    int nx, ny;
+    float hx, hy;        // h / dx, h / dy
+    float dx, dy;
+    float beta, gamma, h;
+    float vout;          // value of feet outside the box (V form)
+    const float *speed;  // s (or null)
+    const float *current;
+    const uint8_t *labels;
+};
+
+struct AdjCtl {
+    unsigned done_ctas;
+    unsigned res_bits;
+    int iters;
+    int parity;
+    int converged;
+    float final_res;
+    float tol;
+    int max_iters;
+    int error;
+    int pad_[7];
+};
+
+// pi_i = argmin_j I[V](foot_j) (lowest index on ties), -1 on targets, -2
+// when the minimising foot is outside the box (a zero row of P_pi).
+void launch_policy(const AdjProblem &ap, const hjbk::ControlTable &C, const float *V,
+                   int8_t *policy, unsigned *ties_out, cudaStream_t st);
+// Graph-able adjoint iteration kernels.
+const void *adj_scatter_kernel();
+const void *adj_resid_kernel();
+struct AdjArgs {
+    AdjProblem ap;
+    hjbk::ControlTable ctrl;
+    const int8_t *policy;
+    const float *g;
+    float *L[2];
+    AdjCtl *ctl;
+    int use_handle;
+    cudaGraphConditionalHandle handle;
+};
+void launch_adj_init(const float *g, float *L0, float *L1, long long n, AdjCtl *ctl, float tol,
+                     int max_iters, cudaStream_t st);
+// dL/dtheta (wrt = 0) or dL/dl (wrt = 1) from lambda.
+void launch_adj_grad(const AdjProblem &ap, const hjbk::ControlTable &C, const float *V,
+                     const int8_t *policy, const float *lam, int wrt, float *out, cudaStream_t st);
+// Values of Q1 interpolation at points and (optionally) the gradient of
+// their mean with respect to V (grad must be zeroed by the caller).
+void launch_points(int nx, int ny, double lo0, double lo1, double dx0, double dx1,
+                   const float *V, const float *pts, int P, float *vals, float *grad,
+                   cudaStream_t st);
+
+}  // namespace hjbh

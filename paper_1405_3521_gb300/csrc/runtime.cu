@@ -1,0 +1,1339 @@
+// runtime.cu -- host runtime behind the C ABI of include/hjb.h: problem
+// objects, workspaces, TMA descriptors, the CUDA-graph convergence loop and
+// the entry points hjb_create ... hjb_point_values.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hjb.h"
+#include "hjb_internal.cuh"
+
+using hjbk::Ctl;
+using hjbk::SlotDesc;
+using hjbk::SlotState;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? HJB_ERR_OOM : HJB_ERR_CUDA,       \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                          \
+    } while (0)
+
+#define TRY(expr)                \
+    do {                         \
+        int rc_ = (expr);        \
+        if (rc_ != HJB_OK) return rc_; \
+    } while (0)
+
+// ----- TMA descriptor encoder from the driver (no link-time libcuda) --------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A caller-owned node field, read in place on the device or mirrored from
+// host memory at every call.
+struct Field {
+    const void *user = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+    void *mirror = nullptr;
+
+    void set(const void *p, size_t b) {
+        user = p;
+        bytes = b;
+        host = p && !is_device_ptr(p);
+    }
+    const void *dev() const { return host ? mirror : user; }
+    int refresh(cudaStream_t st) {
+        if (!user || !host) return HJB_OK;
+        if (!mirror) CK(cudaMalloc(&mirror, bytes));
+        CK(cudaMemcpyAsync(mirror, user, bytes, cudaMemcpyHostToDevice, st));
+        return HJB_OK;
+    }
+    void release() {
+        if (mirror) cudaFree(mirror);
+        mirror = nullptr;
+    }
+};
+
+// Growable device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t b) {
+        if (b <= bytes && p) return HJB_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        CK(cudaMalloc(&p, b));
+        bytes = b;
+        return HJB_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T>
+    T *as() const {
+        return static_cast<T *>(p);
+    }
+};
+
+// An output array: written in place when it is device memory, otherwise
+// produced in a device staging buffer and copied back at the end.
+struct OutArr {
+    void *user = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+    DevBuf *stage = nullptr;
+    int init(void *u, size_t b, DevBuf *s) {
+        user = u;
+        bytes = b;
+        host = u && !is_device_ptr(u);
+        stage = s;
+        if (host) TRY(stage->ensure(b));
+        return HJB_OK;
+    }
+    void *dev() const { return host ? stage->p : user; }
+    int finish(cudaStream_t st) {
+        if (user && host) CK(cudaMemcpyAsync(user, stage->p, bytes, cudaMemcpyDeviceToHost, st));
+        return HJB_OK;
+    }
+};
+
+// One launch of the convergence loop over a set of slots.
+struct RunCtx {
+    std::vector<SlotDesc> slots;
+    DevBuf d_slots, d_state, d_ctl, vbuf, h_state_pinned;
+    SlotState *h_state = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    hjbh::SweepKey key{-1, -1, -1, -1};
+    int spb = 0;
+    const void *graph_slots = nullptr;
+    int graph_nslots = -1;
+    hjbk::ControlTable ctrl_in_graph;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        d_slots.release();
+        d_state.release();
+        d_ctl.release();
+        vbuf.release();
+        if (h_state) cudaFreeHost(h_state);
+        h_state = nullptr;
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        ev0 = ev1 = nullptr;
+    }
+};
+
+}  // namespace
+
+struct hjb_problem {
+    hjb_grid grid;
+    int kind;
+    double dubins_v;
+    Field speed, current, log_speed, cost, labels;
+    double l_const, h, lambda, value_out;
+    int na, cdim;
+    float ax[hjbk::MAX_CTRL], ay[hjbk::MAX_CTRL];
+    int ntargets;
+    long long N;
+    double dx[3];
+    DevBuf speed_exp, trig;
+    // coarse problem of the reconstruction
+    DevBuf c_speed, c_current, c_cost, c_labels, c_trig, c_mask, c_vstage, c_grad;
+    DevBuf tile_bits, tile_lists, fine_mask_dev, scratch_u64;
+    DevBuf out_stage, out_stage2, out_stage3, in_stage;
+    RunCtx full, ra, dec;
+    RunCtx *batch = nullptr;
+    // adjoint workspaces
+    DevBuf adj_policy, adj_g, adj_L, adj_ctl, adj_v;
+    cudaGraph_t adj_graph = nullptr;
+    cudaGraphExec_t adj_exec = nullptr;
+    hjbh::AdjArgs adj_args_in_graph;
+    std::vector<const hjb_problem *> batch_key;
+};
+
+namespace {
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------
+// Geometry of one slot's iteration buffers.
+
+struct SlotGeo {
+    int nx, ny, nz, pitch, zdup, nzl;
+    long long zstride;
+};
+
+SlotGeo geo_of(int ndim, const int n[3], int periodic_z) {
+    SlotGeo g;
+    g.nx = n[0];
+    g.ny = n[1];
+    g.nz = ndim > 2 ? n[2] : 1;
+    g.pitch = round_up(g.nx, 32);
+    g.zdup = (ndim > 2 && periodic_z) ? 1 : 0;
+    g.nzl = g.nz + 2 * g.zdup;
+    g.zstride = static_cast<long long>(g.pitch) * g.ny;
+    return g;
+}
+
+int encode_maps(SlotDesc &S, int ndim, int halo) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(HJB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    for (int b = 0; b < 2; ++b) {
+        CUresult r;
+        if (ndim == 2) {
+            cuuint64_t dims[2] = {static_cast<cuuint64_t>(S.nx), static_cast<cuuint64_t>(S.ny)};
+            cuuint64_t strides[1] = {static_cast<cuuint64_t>(S.pitch) * 4};
+            cuuint32_t box[2] = {static_cast<cuuint32_t>(hjbk::TW),
+                                 static_cast<cuuint32_t>(hjbk::TY + 2 * halo)};
+            cuuint32_t es[2] = {1, 1};
+            r = enc(&S.tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, S.V[b], dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        } else {
+            cuuint64_t dims[3] = {static_cast<cuuint64_t>(S.nx), static_cast<cuuint64_t>(S.ny),
+                                  static_cast<cuuint64_t>(S.nz + 2 * S.zdup)};
+            cuuint64_t strides[2] = {static_cast<cuuint64_t>(S.pitch) * 4,
+                                     static_cast<cuuint64_t>(S.zstride) * 4};
+            cuuint32_t box[3] = {static_cast<cuuint32_t>(hjbk::TW),
+                                 static_cast<cuuint32_t>(hjbk::TY + 2 * halo),
+                                 static_cast<cuuint32_t>(hjbk::TZ + 2)};
+            cuuint32_t es[3] = {1, 1, 1};
+            r = enc(&S.tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S.V[b], dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
+        if (r != CUDA_SUCCESS) return fail(HJB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return HJB_OK;
+}
+
+// Per-call problem preparation: refresh host mirrors, exp(theta), and the
+// largest foot displacement in cells (which selects the halo).
+struct Prep {
+    const float *speed = nullptr;
+    const float *current = nullptr;
+    const float *cost = nullptr;
+    const uint8_t *labels = nullptr;
+    double max_off_xy = 0.0;  // cells
+    double max_off_z = 0.0;
+    int launches = 0;         // kernels launched by prepare()
+};
+
+int prepare(hjb_problem *P, cudaStream_t st, Prep &out) {
+    TRY(P->speed.refresh(st));
+    TRY(P->current.refresh(st));
+    TRY(P->log_speed.refresh(st));
+    TRY(P->cost.refresh(st));
+    TRY(P->labels.refresh(st));
+    out.labels = static_cast<const uint8_t *>(P->labels.dev());
+    out.cost = static_cast<const float *>(P->cost.dev());
+    out.current = static_cast<const float *>(P->current.dev());
+    if (P->log_speed.user) {
+        TRY(P->speed_exp.ensure(P->N * sizeof(float)));
+        hjbh::launch_exp(static_cast<const float *>(P->log_speed.dev()), P->speed_exp.as<float>(),
+                         P->N, st);
+        out.launches += 1;
+        out.speed = P->speed_exp.as<float>();
+    } else {
+        out.speed = static_cast<const float *>(P->speed.dev());
+    }
+    if (P->kind == HJB_DYN_SPEED_CURRENT) {
+        double amax_x = 0, amax_y = 0;
+        for (int j = 0; j < P->na; ++j) {
+            amax_x = std::fmax(amax_x, std::fabs(P->ax[j]));
+            amax_y = std::fmax(amax_y, std::fabs(P->ay[j]));
+        }
+        double smax = 1.0, cx = 0.0, cy = 0.0;
+        if (out.speed || out.current) {
+            TRY(P->scratch_u64.ensure(64));
+            unsigned *d = P->scratch_u64.as<unsigned>();
+            CK(cudaMemsetAsync(d, 0, 3 * sizeof(unsigned), st));
+            if (out.speed) {
+                hjbh::launch_absmax(out.speed, P->N, 1, 0, d, st);
+                out.launches += 1;
+            }
+            if (out.current) {
+                hjbh::launch_absmax(out.current, P->N, 2, 0, d + 1, st);
+                hjbh::launch_absmax(out.current, P->N, 2, 1, d + 2, st);
+                out.launches += 2;
+            }
+            unsigned h[3];
+            CK(cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            float f[3];
+            std::memcpy(f, h, sizeof f);
+            if (out.speed) smax = f[0];
+            cx = f[1];
+            cy = f[2];
+        }
+        const double ox = (smax * amax_x + cx) * P->h / P->dx[0];
+        const double oy = (smax * amax_y + cy) * P->h / P->dx[1];
+        out.max_off_xy = std::fmax(ox, oy);
+    } else {
+        out.max_off_xy = std::fabs(P->dubins_v) * P->h / std::fmin(P->dx[0], P->dx[1]);
+        double umax = 0;
+        for (int j = 0; j < P->na; ++j) umax = std::fmax(umax, std::fabs(P->ax[j]));
+        out.max_off_z = umax * P->h / P->dx[2];
+    }
+    return HJB_OK;
+}
+
+int halo_for(const hjb_problem *P, double max_off, double max_off_z, int *halo) {
+    if (!std::isfinite(max_off) || !std::isfinite(max_off_z))
+        return fail(HJB_ERR_INVALID_ARG, "a speed, log-speed or current field is not finite");
+    // the cells reached by a foot displaced by up to M cells lie within
+    // floor(M) + 1 nodes of the node
+    const int need = static_cast<int>(std::floor(max_off)) + 1;
+    if (P->kind == HJB_DYN_DUBINS) {
+        if (need > 2 || max_off_z >= 1.0)
+            return fail(HJB_ERR_UNSUPPORTED,
+                        "Dubins feet move %.3f cells in (x,y) and %.3f in theta per step; the "
+                        "3D sweep supports < 2 and < 1",
+                        max_off, max_off_z);
+        *halo = 2;
+        return HJB_OK;
+    }
+    if (need <= 2)
+        *halo = 2;
+    else if (need <= 4)
+        *halo = 4;
+    else
+        return fail(HJB_ERR_UNSUPPORTED,
+                    "feet move up to %.3f cells per step; the sweep supports fewer than 4 (reduce h)",
+                    max_off);
+    return HJB_OK;
+}
+
+// Fill the fields of a slot that depend on the problem statement.
+void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &pr, bool wform,
+               double h, const double dx[3], int halo, double tol, int max_iters) {
+    const double beta = std::exp(-P->lambda * h);
+    const double gamma = -std::expm1(-P->lambda * h) / P->lambda;
+    const double c = P->l_const / P->lambda;
+    S.nx = g.nx;
+    S.ny = g.ny;
+    S.nz = g.nz;
+    S.pitch = g.pitch;
+    S.zdup = g.zdup;
+    S.zstride = g.zstride;
+    S.tiles_x = (g.nx + hjbk::TX - 1) / hjbk::TX;
+    S.tiles_y = (g.ny + hjbk::TY - 1) / hjbk::TY;
+    S.tiles_z = P->grid.ndim > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
+    S.ntiles = S.tiles_x * S.tiles_y * S.tiles_z;
+    S.halo = halo;
+    S.hx = static_cast<float>(h / dx[0]);
+    S.hy = static_cast<float>(h / dx[1]);
+    S.hz = P->grid.ndim > 2 ? static_cast<float>(h / dx[2]) : 0.0f;
+    S.beta = static_cast<float>(beta);
+    S.gamma = static_cast<float>(gamma);
+    S.gl = static_cast<float>(gamma * P->l_const);
+    S.speed = pr.speed;
+    S.current = pr.current;
+    S.cost = wform ? nullptr : pr.cost;
+    S.labels = pr.labels;
+    S.mask = nullptr;
+    S.mask_bit = 0;
+    S.only_target = 0;
+    S.tile_list = nullptr;
+    S.trig = nullptr;
+    if (wform) {
+        S.vout = static_cast<float>(c - P->value_out);
+        S.vtarget = static_cast<float>(c);
+    } else {
+        S.vout = static_cast<float>(P->value_out);
+        S.vtarget = 0.0f;
+    }
+    S.tol = static_cast<float>(tol);
+    S.max_iters = max_iters;
+}
+
+int resolve_form(const hjb_problem *P, int use_w, bool *wform) {
+    const bool const_cost = P->cost.user == nullptr;
+    if (use_w < 0)
+        *wform = const_cost;
+    else if (use_w > 0) {
+        if (!const_cost)
+            return fail(HJB_ERR_INVALID_ARG, "use_w_form = 1 requires a constant cost (l == NULL)");
+        *wform = true;
+    } else
+        *wform = false;
+    return HJB_OK;
+}
+
+double default_tol(const hjb_problem *P, double h) {
+    return 0.5e-4 * (-std::expm1(-P->lambda * h));
+}
+
+// Dubins per-layer foot offsets (v h cos(th)/dx, v h sin(th)/dy) in FP64.
+int dubins_trig(const hjb_problem *P, DevBuf &buf, int nz, double h, const double dx[3], double th0,
+                double dth, cudaStream_t st) {
+    std::vector<float2> t(nz);
+    for (int k = 0; k < nz; ++k) {
+        const double th = th0 + k * dth;
+        t[k].x = static_cast<float>(P->dubins_v * h * std::cos(th) / dx[0]);
+        t[k].y = static_cast<float>(P->dubins_v * h * std::sin(th) / dx[1]);
+    }
+    TRY(buf.ensure(nz * sizeof(float2)));
+    CK(cudaMemcpyAsync(buf.p, t.data(), nz * sizeof(float2), cudaMemcpyHostToDevice, st));
+    // the host vector dies at return: wait for the copy
+    CK(cudaStreamSynchronize(st));
+    return HJB_OK;
+}
+
+hjbk::ControlTable control_table(const hjb_problem *P) {
+    hjbk::ControlTable c;
+    std::memset(&c, 0, sizeof c);
+    c.count = P->na;
+    for (int j = 0; j < P->na; ++j) {
+        c.ax[j] = P->ax[j];
+        c.ay[j] = P->ay[j];
+    }
+    return c;
+}
+
+// Allocate iteration buffers for the slots (laid out back to back, each
+// 256-byte aligned) and encode their TMA maps.
+int alloc_slot_buffers(RunCtx &R, int ndim, int halo) {
+    size_t total = 0;
+    std::vector<size_t> off(R.slots.size());
+    for (size_t i = 0; i < R.slots.size(); ++i) {
+        const SlotDesc &S = R.slots[i];
+        const size_t fl = static_cast<size_t>(S.nz + 2 * S.zdup) * S.zstride;
+        off[i] = total;
+        total += 2 * ((fl + 63) / 64 * 64);
+    }
+    TRY(R.vbuf.ensure(total * sizeof(float)));
+    for (size_t i = 0; i < R.slots.size(); ++i) {
+        SlotDesc &S = R.slots[i];
+        const size_t fl = static_cast<size_t>(S.nz + 2 * S.zdup) * S.zstride;
+        const size_t fl64 = (fl + 63) / 64 * 64;
+        S.V[0] = R.vbuf.as<float>() + off[i];
+        S.V[1] = R.vbuf.as<float>() + off[i] + fl64;
+        TRY(encode_maps(S, ndim, halo));
+    }
+    return HJB_OK;
+}
+
+// Build (or reuse) the graph: a WHILE conditional node whose body runs
+// `spb` sweeps; the last CTA of each sweep sets the loop condition.
+int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlTable &ctrl,
+                 float stall_tol) {
+    const int n = static_cast<int>(R.slots.size());
+    if (R.exec && R.key.dubins == key.dubins && R.key.wform == key.wform && R.key.na == key.na &&
+        R.key.halo == key.halo && R.spb == spb && R.graph_slots == R.d_slots.p &&
+        R.graph_nslots == n && std::memcmp(&R.ctrl_in_graph, &ctrl, sizeof ctrl) == 0)
+        return HJB_OK;
+    if (R.exec) cudaGraphExecDestroy(R.exec);
+    if (R.graph) cudaGraphDestroy(R.graph);
+    R.exec = nullptr;
+    R.graph = nullptr;
+    const void *fn = hjbh::sweep_kernel(key, nullptr);
+    if (!fn) return fail(HJB_ERR_UNSUPPORTED, "no sweep kernel for this configuration");
+    const int grid = hjbh::sweep_grid(key);
+    CK(cudaGraphCreate(&R.graph, 0));
+    cudaGraphConditionalHandle handle;
+    CK(cudaGraphConditionalHandleCreate(&handle, R.graph, 1, cudaGraphCondAssignDefault));
+    // (the params struct holds a union with non-trivial members: zeroed raw storage)
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof cp_raw);
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, R.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    hjbk::SweepArgs args;
+    std::memset(&args, 0, sizeof args);
+    args.slots = R.d_slots.as<SlotDesc>();
+    args.state = R.d_state.as<SlotState>();
+    args.ctl = R.d_ctl.as<Ctl>();
+    args.nslots = n;
+    args.use_handle = 1;
+    args.handle = handle;
+    args.stall_tol = stall_tol;
+    args.ctrl = ctrl;
+    cudaGraphNode_t prev = nullptr;
+    for (int k = 0; k < spb; ++k) {
+        cudaKernelNodeParams kp;
+        std::memset(&kp, 0, sizeof kp);
+        kp.func = const_cast<void *>(fn);
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(hjbk::THREADS);
+        kp.sharedMemBytes = 0;
+        void *argv[1] = {&args};
+        kp.kernelParams = argv;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        prev = node;
+    }
+    CK(cudaGraphInstantiate(&R.exec, R.graph, 0));
+    R.key = key;
+    R.spb = spb;
+    R.graph_slots = R.d_slots.p;
+    R.graph_nslots = n;
+    R.ctrl_in_graph = ctrl;
+    return HJB_OK;
+}
+
+int sweeps_per_body(const hjb_solve_opts *o) {
+    if (o && o->sweeps_per_check > 0) return o->sweeps_per_check > 64 ? 64 : o->sweeps_per_check;
+    return 2;
+}
+
+// Upload the slot table and allocate the state/control blocks.
+int upload_slots(RunCtx &R, cudaStream_t st) {
+    const size_t n = R.slots.size();
+    TRY(R.d_slots.ensure(n * sizeof(SlotDesc)));
+    TRY(R.d_state.ensure(n * sizeof(SlotState)));
+    TRY(R.d_ctl.ensure(sizeof(Ctl)));
+    if (!R.ev0) {
+        CK(cudaEventCreate(&R.ev0));
+        CK(cudaEventCreate(&R.ev1));
+    }
+    CK(cudaMemcpyAsync(R.d_slots.p, R.slots.data(), n * sizeof(SlotDesc), cudaMemcpyHostToDevice,
+                       st));
+    return HJB_OK;
+}
+
+// Run the convergence loop (graph), after init values and loop init.
+int run_loop(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlTable &ctrl,
+             cudaStream_t st) {
+    const int n = static_cast<int>(R.slots.size());
+    hjbh::launch_loop_init(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), R.d_ctl.as<Ctl>(),
+                           n, nullptr, st);
+    CK(cudaGetLastError());
+    const float stall_tol = 8.0f * 1.1920929e-7f;
+    const char *ng = std::getenv("HJB_NO_GRAPH");
+    if (ng && ng[0] == '1') {
+        // host-driven loop (debugging aid): spb sweeps, then read nactive
+        const void *fn = hjbh::sweep_kernel(key, nullptr);
+        if (!fn) return fail(HJB_ERR_UNSUPPORTED, "no sweep kernel for this configuration");
+        const int grid = hjbh::sweep_grid(key);
+        hjbk::SweepArgs args;
+        std::memset(&args, 0, sizeof args);
+        args.slots = R.d_slots.as<SlotDesc>();
+        args.state = R.d_state.as<SlotState>();
+        args.ctl = R.d_ctl.as<Ctl>();
+        args.nslots = n;
+        args.use_handle = 0;
+        args.stall_tol = stall_tol;
+        args.ctrl = ctrl;
+        for (;;) {
+            for (int k = 0; k < spb; ++k) {
+                void *argv[1] = {&args};
+                CK(cudaLaunchKernel(fn, dim3(grid), dim3(hjbk::THREADS), argv, 0, st));
+            }
+            int nact = 0, err = 0;
+            CK(cudaMemcpyAsync(&nact, &R.d_ctl.as<Ctl>()->nactive, sizeof(int),
+                               cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&err, &R.d_ctl.as<Ctl>()->error, sizeof(int), cudaMemcpyDeviceToHost,
+                               st));
+            CK(cudaStreamSynchronize(st));
+            if (nact == 0 || err) break;
+        }
+        return HJB_OK;
+    }
+    TRY(ensure_graph(R, key, spb, ctrl, stall_tol));
+    CK(cudaGraphLaunch(R.exec, st));
+    return HJB_OK;
+}
+
+// Read back the slot states, the error flag and the number of sweep
+// launches (synchronises the stream).
+int read_state(RunCtx &R, cudaStream_t st, int *err, long long *launches = nullptr) {
+    const size_t n = R.slots.size();
+    if (!R.h_state || R.h_state_pinned.bytes < n * sizeof(SlotState)) {
+        if (R.h_state) cudaFreeHost(R.h_state);
+        R.h_state = nullptr;
+        CK(cudaMallocHost(reinterpret_cast<void **>(&R.h_state), (n + 1) * sizeof(SlotState)));
+        R.h_state_pinned.bytes = n * sizeof(SlotState);
+    }
+    CK(cudaMemcpyAsync(R.h_state, R.d_state.p, n * sizeof(SlotState), cudaMemcpyDeviceToHost, st));
+    int *herr = reinterpret_cast<int *>(R.h_state + n);
+    CK(cudaMemcpyAsync(herr, &R.d_ctl.as<Ctl>()->error, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    *err = herr[0];
+    if (launches) *launches = static_cast<unsigned>(herr[1]);
+    return HJB_OK;
+}
+
+void fill_stats(hjb_stats *s, const SlotState &st) {
+    if (!s) return;
+    std::memset(s, 0, sizeof *s);
+    s->iterations = st.iters;
+    s->converged = st.converged ? 1 : 0;
+    s->node_updates = static_cast<long long>(st.updates);
+    s->final_residual = st.final_res;
+}
+
+hjbh::GridDims dims_of(const hjb_problem *P) {
+    hjbh::GridDims g;
+    g.ndim = P->grid.ndim;
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = d < g.ndim ? P->grid.n[d] : 1;
+        g.periodic[d] = d < g.ndim ? P->grid.periodic[d] : 0;
+    }
+    return g;
+}
+
+int check_opts(const hjb_solve_opts *o) {
+    if (o && o->max_iters < 0) return fail(HJB_ERR_INVALID_ARG, "max_iters < 0");
+    return HJB_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+const char *hjb_last_error(void) { return g_err.c_str(); }
+
+const char *hjb_version(void) { return "hjb-gb300 0.1 (sm_103a)"; }
+
+int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *cost,
+               const hjb_discount *disc, const hjb_controls *controls, const hjb_target *target,
+               hjb_problem **out) {
+    g_err.clear();
+    if (!grid || !dyn || !cost || !disc || !controls || !target || !out)
+        return fail(HJB_ERR_INVALID_ARG, "NULL descriptor");
+    *out = nullptr;
+    if (grid->ndim != 2 && grid->ndim != 3) return fail(HJB_ERR_INVALID_ARG, "ndim must be 2 or 3");
+    long long N = 1;
+    for (int d = 0; d < grid->ndim; ++d) {
+        const int n = grid->n[d];
+        if (n < 2) return fail(HJB_ERR_INVALID_ARG, "n[%d] = %d < 2", d, n);
+        if (!(grid->hi[d] > grid->lo[d])) return fail(HJB_ERR_INVALID_ARG, "hi[%d] <= lo[%d]", d, d);
+        N *= n;
+    }
+    if (grid->n[0] > 65536 || grid->n[1] > 65536 || (grid->ndim > 2 && grid->n[2] > 65536))
+        return fail(HJB_ERR_INVALID_ARG, "grid too large");
+    if (N > (1LL << 31)) return fail(HJB_ERR_INVALID_ARG, "more than 2^31 nodes");
+    if (dyn->kind == HJB_DYN_SPEED_CURRENT) {
+        if (grid->ndim != 2) return fail(HJB_ERR_UNSUPPORTED, "speed/current dynamics are 2D");
+        if (grid->periodic[0] || grid->periodic[1])
+            return fail(HJB_ERR_UNSUPPORTED, "periodic dimensions are supported for theta (Dubins) only");
+        if (controls->dim != 2) return fail(HJB_ERR_INVALID_ARG, "controls must be 2D vectors");
+        if (dyn->speed && dyn->log_speed)
+            return fail(HJB_ERR_INVALID_ARG, "give either speed or log_speed");
+    } else if (dyn->kind == HJB_DYN_DUBINS) {
+        if (grid->ndim != 3 || !grid->periodic[2] || grid->periodic[0] || grid->periodic[1])
+            return fail(HJB_ERR_INVALID_ARG, "Dubins needs a 3D grid, periodic in dimension 2 only");
+        if (controls->dim != 1) return fail(HJB_ERR_INVALID_ARG, "Dubins controls are scalars");
+        if (dyn->speed || dyn->current || dyn->log_speed)
+            return fail(HJB_ERR_UNSUPPORTED, "Dubins takes no node fields");
+    } else {
+        return fail(HJB_ERR_INVALID_ARG, "unknown dynamics kind %d", dyn->kind);
+    }
+    if (controls->count < 1 || controls->count > HJB_MAX_CONTROLS || !controls->a)
+        return fail(HJB_ERR_INVALID_ARG, "control count must be in [1, %d]", HJB_MAX_CONTROLS);
+    for (int j = 0; j < controls->count * controls->dim; ++j)
+        if (!std::isfinite(controls->a[j]) || std::fabs(controls->a[j]) > 1e6f)
+            return fail(HJB_ERR_INVALID_ARG, "control component %d is not a finite value", j);
+    if (!std::isfinite(dyn->dubins_v) || !std::isfinite(disc->h) || !std::isfinite(disc->lambda) ||
+        !std::isfinite(target->value_out) || !std::isfinite(cost->l_const))
+        return fail(HJB_ERR_INVALID_ARG, "non-finite scalar parameter");
+    if (!(disc->h > 0) || !(disc->lambda > 0))
+        return fail(HJB_ERR_INVALID_ARG, "h and lambda must be positive");
+    if (!target->labels) return fail(HJB_ERR_INVALID_ARG, "target labels are required");
+    if (target->n_targets < 1 || target->n_targets > HJB_MAX_TARGETS)
+        return fail(HJB_ERR_INVALID_ARG, "n_targets must be in [1, %d]", HJB_MAX_TARGETS);
+    if (!cost->l && !(cost->l_const > 0))
+        return fail(HJB_ERR_INVALID_ARG, "constant running cost must be positive");
+    hjb_problem *P = new hjb_problem();
+    P->grid = *grid;
+    for (int d = grid->ndim; d < 3; ++d) {
+        P->grid.n[d] = 1;
+        P->grid.periodic[d] = 0;
+        P->grid.lo[d] = 0;
+        P->grid.hi[d] = 1;
+    }
+    P->kind = dyn->kind;
+    P->dubins_v = dyn->dubins_v;
+    P->N = N;
+    P->speed.set(dyn->speed, N * sizeof(float));
+    P->current.set(dyn->current, 2 * N * sizeof(float));
+    P->log_speed.set(dyn->log_speed, N * sizeof(float));
+    P->cost.set(cost->l, N * sizeof(float));
+    P->labels.set(target->labels, N);
+    P->l_const = cost->l ? 1.0 : cost->l_const;
+    P->h = disc->h;
+    P->lambda = disc->lambda;
+    P->value_out = target->value_out;
+    P->ntargets = target->n_targets;
+    P->na = controls->count;
+    P->cdim = controls->dim;
+    for (int j = 0; j < P->na; ++j) {
+        P->ax[j] = controls->a[j * controls->dim];
+        P->ay[j] = controls->dim > 1 ? controls->a[j * controls->dim + 1] : 0.0f;
+    }
+    for (int d = 0; d < 3; ++d)
+        P->dx[d] = P->grid.periodic[d] ? (P->grid.hi[d] - P->grid.lo[d]) / P->grid.n[d]
+                                       : (P->grid.hi[d] - P->grid.lo[d]) / (P->grid.n[d] - 1);
+    *out = P;
+    return HJB_OK;
+}
+
+int hjb_destroy(hjb_problem *P) {
+    if (!P) return HJB_OK;
+    P->full.release();
+    P->ra.release();
+    P->dec.release();
+    if (P->batch) {
+        P->batch->release();
+        delete P->batch;
+    }
+    if (P->adj_exec) cudaGraphExecDestroy(P->adj_exec);
+    if (P->adj_graph) cudaGraphDestroy(P->adj_graph);
+    P->adj_policy.release();
+    P->adj_g.release();
+    P->adj_L.release();
+    P->adj_ctl.release();
+    P->adj_v.release();
+    DevBuf *bufs[] = {&P->speed_exp, &P->trig,     &P->c_speed,      &P->c_current,
+                      &P->c_cost,    &P->c_labels, &P->c_trig,       &P->c_mask,
+                      &P->c_vstage,  &P->c_grad,   &P->tile_bits,    &P->tile_lists,
+                      &P->fine_mask_dev, &P->scratch_u64, &P->out_stage, &P->out_stage2,
+                      &P->out_stage3, &P->in_stage};
+    for (DevBuf *b : bufs) b->release();
+    P->speed.release();
+    P->current.release();
+    P->log_speed.release();
+    P->cost.release();
+    P->labels.release();
+    delete P;
+    return HJB_OK;
+}
+
+int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stats *stats,
+              void *stream) {
+    g_err.clear();
+    if (!P || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL problem or output");
+    TRY(check_opts(opts));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool wform;
+    TRY(resolve_form(P, opts ? opts->use_w_form : -1, &wform));
+    Prep pr;
+    TRY(prepare(P, st, pr));
+    int halo;
+    TRY(halo_for(P, pr.max_off_xy, pr.max_off_z, &halo));
+    const double tol = (opts && opts->tol > 0) ? opts->tol : default_tol(P, P->h);
+    const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
+    RunCtx &R = P->full;
+    const SlotGeo g = geo_of(P->grid.ndim, P->grid.n, P->grid.periodic[2]);
+    R.slots.assign(1, SlotDesc());
+    std::memset(R.slots.data(), 0, sizeof(SlotDesc));
+    fill_slot(R.slots[0], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters);
+    if (P->kind == HJB_DYN_DUBINS) {
+        TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
+        R.slots[0].trig = P->trig.as<float2>();
+    }
+    TRY(alloc_slot_buffers(R, P->grid.ndim, halo));
+    TRY(upload_slots(R, st));
+    OutArr out;
+    TRY(out.init(v_out, P->N * sizeof(float), &P->out_stage));
+    const float *vinit = nullptr;
+    if (opts && opts->v_init) {
+        if (is_device_ptr(opts->v_init)) {
+            vinit = opts->v_init;
+        } else {
+            TRY(P->in_stage.ensure(P->N * sizeof(float)));
+            CK(cudaMemcpyAsync(P->in_stage.p, opts->v_init, P->N * sizeof(float),
+                               cudaMemcpyHostToDevice, st));
+            vinit = P->in_stage.as<float>();
+        }
+    }
+    const float c_over = static_cast<float>(P->l_const / P->lambda);
+    CK(cudaEventRecord(R.ev0, st));
+    hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), 1, static_cast<int>(P->N), wform, c_over,
+                             vinit, st);
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo};
+    const hjbk::ControlTable ctrl = control_table(P);
+    TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st));
+    hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
+                         static_cast<float *>(out.dev()), wform, c_over, st);
+    CK(cudaEventRecord(R.ev1, st));
+    TRY(out.finish(st));
+    int err = 0;
+    long long sweeps = 0;
+    TRY(read_state(R, st, &err, &sweeps));
+    CK(cudaGetLastError());
+    float ms = 0;
+    cudaEventElapsedTime(&ms, R.ev0, R.ev1);
+    if (stats) {
+        fill_stats(stats, R.h_state[0]);
+        stats->ms = ms;
+        stats->launches = pr.launches + 3 + sweeps;
+    }
+    if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
+    if (!R.h_state[0].converged)
+        return fail(HJB_ERR_NOT_CONVERGED, "not converged after %d iterations (residual %g)",
+                    R.h_state[0].iters, R.h_state[0].final_res);
+    return HJB_OK;
+}
+
+int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_out,
+                   uint32_t *coarse_labels_out, float *v_aux_out, hjb_stats *stats,
+                   void *stream) {
+    g_err.clear();
+    if (!P || !ra || !fine_mask_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nd = P->grid.ndim;
+    hjbh::GridDims fine = dims_of(P), coarse = fine;
+    int stride[3] = {1, 1, 1};
+    for (int d = 0; d < nd; ++d) {
+        const int r = ra->coarse_stride[d];
+        if (r < 1) return fail(HJB_ERR_INVALID_ARG, "coarse_stride[%d] < 1", d);
+        stride[d] = r;
+        if (fine.periodic[d]) {
+            if (fine.n[d] % r) return fail(HJB_ERR_INVALID_ARG, "stride %d does not divide n[%d]", r, d);
+            coarse.n[d] = fine.n[d] / r;
+        } else {
+            if ((fine.n[d] - 1) % r)
+                return fail(HJB_ERR_INVALID_ARG, "stride %d does not divide n[%d]-1", r, d);
+            coarse.n[d] = (fine.n[d] - 1) / r + 1;
+        }
+        if (coarse.n[d] < 2) return fail(HJB_ERR_INVALID_ARG, "coarse grid has < 2 nodes in dim %d", d);
+    }
+    const long long NK = static_cast<long long>(coarse.n[0]) * coarse.n[1] * coarse.n[2];
+    const double hK = ra->h_coarse > 0 ? ra->h_coarse : P->h * stride[0];
+    double dxK[3];
+    for (int d = 0; d < 3; ++d) dxK[d] = P->dx[d] * stride[d];
+    bool wform;
+    TRY(resolve_form(P, -1, &wform));
+    Prep pr;
+    TRY(prepare(P, st, pr));
+    // coarse fields
+    TRY(P->c_labels.ensure(NK));
+    if (pr.speed) TRY(P->c_speed.ensure(NK * sizeof(float)));
+    if (pr.current) TRY(P->c_current.ensure(2 * NK * sizeof(float)));
+    if (pr.cost) TRY(P->c_cost.ensure(NK * sizeof(float)));
+    hjbh::launch_gather_coarse(fine, coarse, stride, pr.speed, pr.current, pr.cost, pr.labels,
+                               P->c_speed.as<float>(), P->c_current.as<float>(),
+                               P->c_cost.as<float>(), P->c_labels.as<uint8_t>(), st);
+    Prep cp = pr;
+    cp.speed = pr.speed ? P->c_speed.as<float>() : nullptr;
+    cp.current = pr.current ? P->c_current.as<float>() : nullptr;
+    cp.cost = pr.cost ? P->c_cost.as<float>() : nullptr;
+    cp.labels = P->c_labels.as<uint8_t>();
+    // the displacement in cells scales with h_K / dx_K
+    const double scale = (hK / dxK[0]) / (P->h / P->dx[0]);
+    int halo;
+    TRY(halo_for(P, pr.max_off_xy * scale, pr.max_off_z * (hK / dxK[2 < nd ? 2 : 0]) /
+                                               (P->h / P->dx[2 < nd ? 2 : 0]),
+                 &halo));
+    const double tol = ra->tol > 0 ? ra->tol : default_tol(P, hK);
+    const int max_iters = ra->max_iters > 0 ? ra->max_iters : 100000;
+    const int m = P->ntargets;
+    RunCtx &R = P->ra;
+    const SlotGeo g = geo_of(nd, coarse.n, coarse.periodic[2]);
+    R.slots.assign(m, SlotDesc());
+    std::memset(R.slots.data(), 0, m * sizeof(SlotDesc));
+    if (P->kind == HJB_DYN_DUBINS)
+        TRY(dubins_trig(P, P->c_trig, g.nz, hK, dxK, P->grid.lo[2], dxK[2], st));
+    for (int k = 0; k < m; ++k) {
+        fill_slot(R.slots[k], P, g, cp, wform, hK, dxK, halo, tol, max_iters);
+        R.slots[k].only_target = k + 1;  // RA step 1: dG := X_k
+        if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->c_trig.as<float2>();
+    }
+    TRY(alloc_slot_buffers(R, nd, halo));
+    TRY(upload_slots(R, st));
+    const float c_over = static_cast<float>(P->l_const / P->lambda);
+    CK(cudaEventRecord(R.ev0, st));
+    hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform, c_over,
+                             nullptr, st);
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo};
+    TRY(run_loop(R, key, 2, control_table(P), st));
+    // threshold of eq. (rep)
+    double delta = ra->delta;
+    TRY(P->scratch_u64.ensure(64));
+    unsigned long long *d_u64 = P->scratch_u64.as<unsigned long long>();
+    CK(cudaMemsetAsync(d_u64, 0, 64, st));
+    if (delta < 0) {
+        double M = ra->M;
+        if (M < 0) {
+            const float dxf[3] = {static_cast<float>(dxK[0]), static_cast<float>(dxK[1]),
+                                  static_cast<float>(dxK[2])};
+            unsigned *gm = reinterpret_cast<unsigned *>(d_u64 + 4);
+            hjbh::launch_grad_max(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m,
+                                  wform ? 1 : 0, coarse, dxf, gm, st);
+            unsigned hb = 0;
+            CK(cudaMemcpyAsync(&hb, gm, sizeof hb, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            float f;
+            std::memcpy(&f, &hb, sizeof f);
+            M = f;
+        }
+        const double C = ra->C > 0 ? ra->C : 0.0;
+        const double q = ra->q > 0 ? ra->q : 1.0;
+        delta = 2.0 * (C * std::pow(dxK[0], q) + M * dxK[0]);
+    }
+    OutArr cl;
+    TRY(cl.init(coarse_labels_out, NK * sizeof(uint32_t), &P->c_mask));
+    uint32_t *cl_dev = coarse_labels_out ? static_cast<uint32_t *>(cl.dev()) : nullptr;
+    if (!cl_dev) {
+        TRY(P->c_mask.ensure(NK * sizeof(uint32_t)));
+        cl_dev = P->c_mask.as<uint32_t>();
+    }
+    hjbh::launch_label(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, coarse,
+                       P->c_labels.as<uint8_t>(), static_cast<float>(delta), wform ? 1 : 0, cl_dev,
+                       nullptr, d_u64, st);
+    OutArr fm;
+    TRY(fm.init(fine_mask_out, P->N * sizeof(uint32_t), &P->out_stage2));
+    hjbh::launch_project(fine, coarse, stride, cl_dev, static_cast<uint32_t *>(fm.dev()), st);
+    hjbh::launch_popcount(static_cast<const uint32_t *>(fm.dev()), P->N, d_u64 + 1, st);
+    if (v_aux_out) {
+        OutArr va;
+        TRY(va.init(v_aux_out, static_cast<size_t>(m) * NK * sizeof(float), &P->c_vstage));
+        for (int k = 0; k < m; ++k)
+            hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), k,
+                                 static_cast<float *>(va.dev()) + static_cast<size_t>(k) * NK,
+                                 wform, c_over, st);
+        TRY(va.finish(st));
+    }
+    CK(cudaEventRecord(R.ev1, st));
+    TRY(cl.finish(st));
+    TRY(fm.finish(st));
+    unsigned long long hc[2];
+    CK(cudaMemcpyAsync(hc, d_u64, sizeof hc, cudaMemcpyDeviceToHost, st));
+    int err = 0;
+    long long sweeps = 0;
+    TRY(read_state(R, st, &err, &sweeps));
+    CK(cudaGetLastError());
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        int conv = 1;
+        for (int k = 0; k < m; ++k) {
+            const SlotState &s = R.h_state[k];
+            stats->iterations = s.iters > stats->iterations ? s.iters : stats->iterations;
+            stats->node_updates += static_cast<long long>(s.updates);
+            stats->final_residual = std::fmax(stats->final_residual, s.final_res);
+            conv &= s.converged ? 1 : 0;
+        }
+        stats->converged = conv;
+        stats->ties = static_cast<long long>(hc[0]);
+        stats->labelled = static_cast<long long>(hc[1]);
+        stats->launches = pr.launches + 7 + sweeps + (ra->delta < 0 && ra->M < 0 ? 1 : 0) +
+                          (v_aux_out ? m : 0);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, R.ev0, R.ev1);
+        stats->ms = ms;
+    }
+    if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
+    for (int k = 0; k < m; ++k)
+        if (!R.h_state[k].converged)
+            return fail(HJB_ERR_NOT_CONVERGED, "auxiliary problem %d did not converge", k + 1);
+    return HJB_OK;
+}
+
+int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *opts,
+                         float *v_out, hjb_stats *per_subdomain, hjb_stats *total, void *stream) {
+    g_err.clear();
+    if (!P || !fine_mask || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    TRY(check_opts(opts));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool wform;
+    TRY(resolve_form(P, opts ? opts->use_w_form : -1, &wform));
+    Prep pr;
+    TRY(prepare(P, st, pr));
+    int halo;
+    TRY(halo_for(P, pr.max_off_xy, pr.max_off_z, &halo));
+    const double tol = (opts && opts->tol > 0) ? opts->tol : default_tol(P, P->h);
+    const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
+    const int m = P->ntargets;
+    const int nd = P->grid.ndim;
+    const hjbh::GridDims fine = dims_of(P);
+    const uint32_t *mask = fine_mask;
+    if (!is_device_ptr(fine_mask)) {
+        TRY(P->fine_mask_dev.ensure(P->N * sizeof(uint32_t)));
+        CK(cudaMemcpyAsync(P->fine_mask_dev.p, fine_mask, P->N * sizeof(uint32_t),
+                           cudaMemcpyHostToDevice, st));
+        mask = P->fine_mask_dev.as<uint32_t>();
+    }
+    RunCtx &R = P->dec;
+    const SlotGeo g = geo_of(nd, P->grid.n, P->grid.periodic[2]);
+    R.slots.assign(m, SlotDesc());
+    std::memset(R.slots.data(), 0, m * sizeof(SlotDesc));
+    if (P->kind == HJB_DYN_DUBINS)
+        TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
+    const int tiles_x = (g.nx + hjbk::TX - 1) / hjbk::TX;
+    const int tiles_y = (g.ny + hjbk::TY - 1) / hjbk::TY;
+    const int tiles_z = nd > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
+    const int nt = tiles_x * tiles_y * tiles_z;
+    TRY(P->tile_bits.ensure(nt * sizeof(uint32_t)));
+    TRY(P->tile_lists.ensure(static_cast<size_t>(m) * nt * sizeof(int)));
+    for (int k = 0; k < m; ++k) {
+        fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters);
+        R.slots[k].mask = mask;
+        R.slots[k].mask_bit = k;
+        R.slots[k].tile_list = P->tile_lists.as<int>() + static_cast<size_t>(k) * nt;
+        if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->trig.as<float2>();
+    }
+    TRY(alloc_slot_buffers(R, nd, halo));
+    TRY(upload_slots(R, st));
+    OutArr out;
+    TRY(out.init(v_out, P->N * sizeof(float), &P->out_stage));
+    const float c_over = static_cast<float>(P->l_const / P->lambda);
+    CK(cudaEventRecord(R.ev0, st));
+    hjbh::launch_tile_lists(fine, tiles_x, tiles_y, tiles_z, mask, m, P->tile_bits.as<uint32_t>(),
+                            P->tile_lists.as<int>(), R.d_slots.as<SlotDesc>(), st);
+    hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
+                             nullptr, st);
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo};
+    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P), st));
+    hjbh::launch_assemble(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, fine, mask,
+                          wform ? 1 : 0, c_over, static_cast<float>(P->value_out),
+                          static_cast<float *>(out.dev()), st);
+    CK(cudaEventRecord(R.ev1, st));
+    TRY(out.finish(st));
+    int err = 0;
+    long long sweeps = 0;
+    TRY(read_state(R, st, &err, &sweeps));
+    CK(cudaGetLastError());
+    float ms = 0;
+    cudaEventElapsedTime(&ms, R.ev0, R.ev1);
+    int conv = 1;
+    hjb_stats tot;
+    std::memset(&tot, 0, sizeof tot);
+    for (int k = 0; k < m; ++k) {
+        const SlotState &s = R.h_state[k];
+        if (per_subdomain) {
+            fill_stats(&per_subdomain[k], s);
+            per_subdomain[k].ms = ms;
+        }
+        tot.iterations = s.iters > tot.iterations ? s.iters : tot.iterations;
+        tot.node_updates += static_cast<long long>(s.updates);
+        tot.final_residual = std::fmax(tot.final_residual, s.final_res);
+        conv &= s.converged ? 1 : 0;
+    }
+    tot.converged = conv;
+    tot.ms = ms;
+    tot.launches = pr.launches + 5 + sweeps;
+    if (total) *total = tot;
+    if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
+    if (!conv) return fail(HJB_ERR_NOT_CONVERGED, "a sub-domain did not converge");
+    return HJB_OK;
+}
+
+int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opts *opts,
+                    float *const *v_out, hjb_stats *per_problem, void *stream) {
+    g_err.clear();
+    if (!problems || count < 1 || !v_out) return fail(HJB_ERR_INVALID_ARG, "empty batch");
+    if (count > hjbk::MAX_SLOTS)
+        return fail(HJB_ERR_INVALID_ARG, "at most %d problems per batch", hjbk::MAX_SLOTS);
+    TRY(check_opts(opts));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    hjb_problem *P0 = problems[0];
+    if (!P0) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
+    bool wform;
+    TRY(resolve_form(P0, opts ? opts->use_w_form : -1, &wform));
+    std::vector<Prep> preps(count);
+    int halo = 2;
+    for (int i = 0; i < count; ++i) {
+        hjb_problem *P = problems[i];
+        if (!P || !v_out[i]) return fail(HJB_ERR_INVALID_ARG, "NULL problem or output %d", i);
+        if (P->kind != P0->kind || P->na != P0->na || P->grid.ndim != P0->grid.ndim ||
+            (P->cost.user == nullptr) != (P0->cost.user == nullptr) ||
+            std::memcmp(P->ax, P0->ax, P->na * sizeof(float)) ||
+            std::memcmp(P->ay, P0->ay, P->na * sizeof(float)) || P->l_const != P0->l_const ||
+            P->lambda != P0->lambda)
+            return fail(HJB_ERR_INVALID_ARG,
+                        "problem %d differs from problem 0 in dynamics kind, controls, cost form "
+                        "or discount rate",
+                        i);
+        TRY(prepare(P, st, preps[i]));
+        int hh;
+        TRY(halo_for(P, preps[i].max_off_xy, preps[i].max_off_z, &hh));
+        halo = hh > halo ? hh : halo;
+    }
+    if (!P0->batch) P0->batch = new RunCtx();
+    RunCtx &R = *P0->batch;
+    R.slots.assign(count, SlotDesc());
+    std::memset(R.slots.data(), 0, count * sizeof(SlotDesc));
+    long long maxN = 0;
+    for (int i = 0; i < count; ++i) {
+        hjb_problem *P = problems[i];
+        const SlotGeo g = geo_of(P->grid.ndim, P->grid.n, P->grid.periodic[2]);
+        const double tol = (opts && opts->tol > 0) ? opts->tol : default_tol(P, P->h);
+        const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
+        fill_slot(R.slots[i], P, g, preps[i], wform, P->h, P->dx, halo, tol, max_iters);
+        if (P->kind == HJB_DYN_DUBINS) {
+            TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
+            R.slots[i].trig = P->trig.as<float2>();
+        }
+        maxN = P->N > maxN ? P->N : maxN;
+    }
+    TRY(alloc_slot_buffers(R, P0->grid.ndim, halo));
+    TRY(upload_slots(R, st));
+    const float c_over = static_cast<float>(P0->l_const / P0->lambda);
+    std::vector<OutArr> outs(count);
+    CK(cudaEventRecord(R.ev0, st));
+    hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), count, static_cast<int>(maxN), wform, c_over,
+                             nullptr, st);
+    const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P0->na, halo};
+    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st));
+    for (int i = 0; i < count; ++i) {
+        TRY(outs[i].init(v_out[i], problems[i]->N * sizeof(float), &problems[i]->out_stage));
+        hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), i,
+                             static_cast<float *>(outs[i].dev()), wform, c_over, st);
+    }
+    CK(cudaEventRecord(R.ev1, st));
+    for (int i = 0; i < count; ++i) TRY(outs[i].finish(st));
+    int err = 0;
+    long long sweeps = 0;
+    TRY(read_state(R, st, &err, &sweeps));
+    long long nl = 2 + sweeps + count;
+    for (int i = 0; i < count; ++i) nl += preps[i].launches;
+    CK(cudaGetLastError());
+    float ms = 0;
+    cudaEventElapsedTime(&ms, R.ev0, R.ev1);
+    int conv = 1;
+    for (int i = 0; i < count; ++i) {
+        if (per_problem) {
+            fill_stats(&per_problem[i], R.h_state[i]);
+            per_problem[i].ms = ms;
+            per_problem[i].launches = nl;
+        }
+        conv &= R.h_state[i].converged ? 1 : 0;
+    }
+    if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
+    if (!conv) return fail(HJB_ERR_NOT_CONVERGED, "a problem of the batch did not converge");
+    return HJB_OK;
+}
+
+int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
+                 const hjb_solve_opts *opts, float *grad_out, hjb_stats *stats, void *stream) {
+    g_err.clear();
+    if (!P || !v || !grad_v || !grad_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (wrt != 0 && wrt != 1) return fail(HJB_ERR_INVALID_ARG, "wrt must be 0 (log-speed) or 1 (cost)");
+    if (P->kind != HJB_DYN_SPEED_CURRENT)
+        return fail(HJB_ERR_UNSUPPORTED, "the adjoint is implemented for 2D speed/current dynamics");
+    TRY(check_opts(opts));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Prep pr;
+    TRY(prepare(P, st, pr));
+    const long long N = P->N;
+    // inputs into problem-owned buffers (the graph's arguments stay fixed)
+    TRY(P->adj_v.ensure(N * sizeof(float)));
+    TRY(P->adj_g.ensure(N * sizeof(float)));
+    CK(cudaMemcpyAsync(P->adj_v.p, v, N * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(P->adj_g.p, grad_v, N * sizeof(float), cudaMemcpyDefault, st));
+    TRY(P->adj_policy.ensure(N));
+    TRY(P->adj_L.ensure(2 * N * sizeof(float)));
+    TRY(P->adj_ctl.ensure(sizeof(hjbh::AdjCtl)));
+    TRY(P->scratch_u64.ensure(64));
+    unsigned *d_ties = P->scratch_u64.as<unsigned>();
+    CK(cudaMemsetAsync(d_ties, 0, sizeof(unsigned), st));
+    hjbh::AdjProblem ap;
+    ap.nx = P->grid.n[0];
+    ap.ny = P->grid.n[1];
+    ap.hx = static_cast<float>(P->h / P->dx[0]);
+    ap.hy = static_cast<float>(P->h / P->dx[1]);
+    ap.dx = static_cast<float>(P->dx[0]);
+    ap.dy = static_cast<float>(P->dx[1]);
+    ap.beta = static_cast<float>(std::exp(-P->lambda * P->h));
+    ap.gamma = static_cast<float>(-std::expm1(-P->lambda * P->h) / P->lambda);
+    ap.h = static_cast<float>(P->h);
+    ap.vout = static_cast<float>(P->value_out);
+    ap.speed = pr.speed;
+    ap.current = pr.current;
+    ap.labels = pr.labels;
+    const hjbk::ControlTable ctrl = control_table(P);
+    const double tol = (opts && opts->tol > 0) ? opts->tol : 1e-7;
+    const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
+    float *L0 = P->adj_L.as<float>(), *L1 = L0 + N;
+    hjbh::AdjCtl *ctl = P->adj_ctl.as<hjbh::AdjCtl>();
+    RunCtx &R = P->full;
+    if (!R.ev0) {
+        CK(cudaEventCreate(&R.ev0));
+        CK(cudaEventCreate(&R.ev1));
+    }
+    OutArr out;
+    TRY(out.init(grad_out, N * sizeof(float), &P->out_stage));
+    CK(cudaEventRecord(R.ev0, st));
+    hjbh::launch_policy(ap, ctrl, P->adj_v.as<float>(), P->adj_policy.as<int8_t>(), d_ties, st);
+    hjbh::launch_adj_init(P->adj_g.as<float>(), L0, L1, N, ctl, static_cast<float>(tol), max_iters,
+                          st);
+    // graph: WHILE { scatter; residual } x 2
+    hjbh::AdjArgs args;
+    std::memset(&args, 0, sizeof args);
+    args.ap = ap;
+    args.ctrl = ctrl;
+    args.policy = P->adj_policy.as<int8_t>();
+    args.g = P->adj_g.as<float>();
+    args.L[0] = L0;
+    args.L[1] = L1;
+    args.ctl = ctl;
+    args.use_handle = 1;
+    if (!P->adj_exec || std::memcmp(&P->adj_args_in_graph.ap, &args.ap, sizeof args.ap) ||
+        std::memcmp(&P->adj_args_in_graph.ctrl, &args.ctrl, sizeof args.ctrl) ||
+        P->adj_args_in_graph.L[0] != L0 || P->adj_args_in_graph.policy != args.policy ||
+        P->adj_args_in_graph.g != args.g || P->adj_args_in_graph.ctl != ctl) {
+        if (P->adj_exec) cudaGraphExecDestroy(P->adj_exec);
+        if (P->adj_graph) cudaGraphDestroy(P->adj_graph);
+        P->adj_exec = nullptr;
+        P->adj_graph = nullptr;
+        CK(cudaGraphCreate(&P->adj_graph, 0));
+        cudaGraphConditionalHandle handle;
+        CK(cudaGraphConditionalHandleCreate(&handle, P->adj_graph, 1, cudaGraphCondAssignDefault));
+        alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+        std::memset(cp_raw, 0, sizeof cp_raw);
+        cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        CK(cudaGraphAddNode(&cnode, P->adj_graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        args.handle = handle;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const void *fns[2] = {hjbh::adj_scatter_kernel(), hjbh::adj_resid_kernel()};
+        cudaGraphNode_t prev = nullptr;
+        for (int rep = 0; rep < 2; ++rep)
+            for (int k = 0; k < 2; ++k) {
+                cudaKernelNodeParams kp;
+                std::memset(&kp, 0, sizeof kp);
+                kp.func = const_cast<void *>(fns[k]);
+                kp.gridDim = dim3(sms * 8);
+                kp.blockDim = dim3(hjbk::THREADS);
+                void *argv[1] = {&args};
+                kp.kernelParams = argv;
+                cudaGraphNode_t node;
+                CK(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+                prev = node;
+            }
+        CK(cudaGraphInstantiate(&P->adj_exec, P->adj_graph, 0));
+        P->adj_args_in_graph = args;
+    }
+    CK(cudaGraphLaunch(P->adj_exec, st));
+    hjbh::AdjCtl hc;
+    CK(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const float *lam = hc.parity ? L1 : L0;
+    hjbh::launch_adj_grad(ap, ctrl, P->adj_v.as<float>(), P->adj_policy.as<int8_t>(), lam, wrt,
+                          static_cast<float *>(out.dev()), st);
+    CK(cudaEventRecord(R.ev1, st));
+    TRY(out.finish(st));
+    unsigned ties = 0;
+    CK(cudaMemcpyAsync(&ties, d_ties, sizeof ties, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->iterations = hc.iters;
+        stats->converged = hc.converged == 1;
+        stats->final_residual = hc.final_res;
+        stats->node_updates = static_cast<long long>(hc.iters) * N;
+        stats->ties = ties;
+        stats->launches = pr.launches + 3 + 4LL * ((hc.iters + 1) / 2);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, R.ev0, R.ev1);
+        stats->ms = ms;
+    }
+    if (hc.converged != 1)
+        return fail(HJB_ERR_NOT_CONVERGED, "adjoint not converged after %d iterations (residual %g)",
+                    hc.iters, hc.final_res);
+    return HJB_OK;
+}
+
+int hjb_point_values(hjb_problem *P, const float *v, const float *points, int npts, float *values,
+                     float *grad_v, void *stream) {
+    g_err.clear();
+    if (!P || !v || !points || npts < 0) return fail(HJB_ERR_INVALID_ARG, "bad argument");
+    if (P->grid.ndim != 2) return fail(HJB_ERR_UNSUPPORTED, "point values are implemented in 2D");
+    if (npts == 0) return HJB_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long N = P->N;
+    const float *vd = v;
+    if (!is_device_ptr(v)) {
+        TRY(P->in_stage.ensure(N * sizeof(float)));
+        CK(cudaMemcpyAsync(P->in_stage.p, v, N * sizeof(float), cudaMemcpyHostToDevice, st));
+        vd = P->in_stage.as<float>();
+    }
+    const float *pd = points;
+    DevBuf pts_stage;
+    if (!is_device_ptr(points)) {
+        TRY(pts_stage.ensure(static_cast<size_t>(npts) * 2 * sizeof(float)));
+        CK(cudaMemcpyAsync(pts_stage.p, points, static_cast<size_t>(npts) * 2 * sizeof(float),
+                           cudaMemcpyHostToDevice, st));
+        pd = pts_stage.as<float>();
+    }
+    OutArr ov, og;
+    TRY(ov.init(values, static_cast<size_t>(npts) * sizeof(float), &P->out_stage2));
+    TRY(og.init(grad_v, N * sizeof(float), &P->out_stage3));
+    if (grad_v) CK(cudaMemsetAsync(og.dev(), 0, N * sizeof(float), st));
+    hjbh::launch_points(P->grid.n[0], P->grid.n[1], P->grid.lo[0], P->grid.lo[1], P->dx[0],
+                        P->dx[1], vd, pd, npts, values ? static_cast<float *>(ov.dev()) : nullptr,
+                        grad_v ? static_cast<float *>(og.dev()) : nullptr, st);
+    TRY(ov.finish(st));
+    TRY(og.finish(st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    pts_stage.release();
+    return HJB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,387 @@
+// subdomain.cu -- kernels of the reconstruction of independent sub-domains
+// (RA, Sec. 3 of Festa, arXiv:1405.3521) and of the decomposed solve (ISA,
+// Sec. 4): coarse-grid gather, labelling (RA steps 2-3), projection through
+// the concave hull (ISA step 2), per-sub-domain tile work lists, assembly
+// (ISA step 4), and small reductions used by the runtime.
+#include <math.h>
+
+#include "hjb_internal.cuh"
+
+using namespace hjbk;
+
+namespace {
+
+__device__ __forceinline__ void unflat(const hjbh::GridDims &g, long long i, int idx[3]) {
+    idx[0] = static_cast<int>(i % g.n[0]);
+    const long long r = i / g.n[0];
+    idx[1] = static_cast<int>(r % g.n[1]);
+    idx[2] = g.ndim > 2 ? static_cast<int>(r / g.n[1]) : 0;
+}
+
+__device__ __forceinline__ long long flat(const hjbh::GridDims &g, int x, int y, int z) {
+    return (static_cast<long long>(z) * g.n[1] + y) * g.n[0] + x;
+}
+
+__device__ __forceinline__ long long count(const hjbh::GridDims &g) {
+    return static_cast<long long>(g.n[0]) * g.n[1] * (g.ndim > 2 ? g.n[2] : 1);
+}
+
+#define GRID_STRIDE(i, n)                                                                  \
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < (n); \
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+
+__global__ void gather_coarse_kernel(hjbh::GridDims fine, hjbh::GridDims coarse, int r0, int r1,
+                                     int r2, const float *speed, const float *current,
+                                     const float *cost, const uint8_t *labels, float *c_speed,
+                                     float *c_current, float *c_cost, uint8_t *c_labels) {
+    const long long NK = count(coarse);
+    GRID_STRIDE(k, NK) {
+        int c[3];
+        unflat(coarse, k, c);
+        const long long i = flat(fine, c[0] * r0, c[1] * r1, c[2] * r2);
+        if (c_speed) c_speed[k] = speed[i];
+        if (c_current) {
+            c_current[2 * k] = current[2 * i];
+            c_current[2 * k + 1] = current[2 * i + 1];
+        }
+        if (c_cost) c_cost[k] = cost[i];
+        c_labels[k] = labels[i];
+    }
+}
+
+// Value of slot k's latest iterate at node (x, y, z).
+__device__ __forceinline__ float slot_value(const SlotDesc &S, const SlotState &st, int x, int y,
+                                            int z) {
+    const float *V = S.V[st.final_parity];
+    return V[static_cast<long long>(z + S.zdup) * S.zstride + static_cast<long long>(y) * S.pitch + x];
+}
+
+// RA step 2 (V = min_k V_k) and step 3 (threshold of eq. rep) at every
+// coarse node.  In the W form W = c - V, so min over V is max over W and the
+// differences |V_k - V| = |W_k - W| are computed on W directly.
+__global__ void label_kernel(const SlotDesc *slots, const SlotState *state, int m,
+                             hjbh::GridDims coarse, const uint8_t *labels, float delta, int wform,
+                             uint32_t *labels_out, float *vmin_out, unsigned long long *ties_out) {
+    const long long NK = count(coarse);
+    unsigned long long ties = 0;
+    GRID_STRIDE(j, NK) {
+        int c[3];
+        unflat(coarse, j, c);
+        float vk[HJB_MAX_TARGETS_DEV];
+        float best = wform ? -INFINITY : INFINITY;
+        for (int k = 0; k < m; ++k) {
+            vk[k] = slot_value(slots[k], state[k], c[0], c[1], c[2]);
+            best = wform ? fmaxf(best, vk[k]) : fminf(best, vk[k]);
+        }
+        const int lab = labels[j];
+        uint32_t bits = 0u;
+        for (int k = 0; k < m; ++k) {
+            const float diff = fabsf(vk[k] - best);
+            if (lab == k + 1 || diff <= delta) bits |= 1u << k;
+            if (fabsf(diff - delta) <= 1e-6f) ++ties;
+        }
+        labels_out[j] = bits;
+        if (vmin_out) vmin_out[j] = best;
+    }
+    if (ties) atomicAdd(ties_out, ties);
+}
+
+__device__ __forceinline__ float vmin_at(const SlotDesc *slots, const SlotState *state, int m,
+                                         int wform, int x, int y, int z) {
+    float best = wform ? -INFINITY : INFINITY;
+    for (int k = 0; k < m; ++k) {
+        const float v = slot_value(slots[k], state[k], x, y, z);
+        best = wform ? fmaxf(best, v) : fminf(best, v);
+    }
+    return best;
+}
+
+// Largest discrete gradient norm of V = min_k V_k (centred differences,
+// one-sided at non-periodic edges), an estimate of the Lipschitz constant M
+// of Prop. 3.1.
+__global__ void grad_max_kernel(const SlotDesc *slots, const SlotState *state, int m, int wform,
+                                hjbh::GridDims g, float dx0, float dx1, float dx2, unsigned *out) {
+    const long long NK = count(g);
+    const float dx[3] = {dx0, dx1, dx2};
+    float mx = 0.0f;
+    GRID_STRIDE(j, NK) {
+        int c[3];
+        unflat(g, j, c);
+        float s2 = 0.0f;
+        for (int d = 0; d < g.ndim; ++d) {
+            int a[3] = {c[0], c[1], c[2]}, b[3] = {c[0], c[1], c[2]};
+            const int n = g.n[d];
+            float span = 2.0f * dx[d];
+            if (g.periodic[d]) {
+                a[d] = (c[d] + n - 1) % n;
+                b[d] = (c[d] + 1) % n;
+            } else if (c[d] == 0) {
+                b[d] = 1;
+                span = dx[d];
+            } else if (c[d] == n - 1) {
+                a[d] = n - 2;
+                span = dx[d];
+            } else {
+                a[d] = c[d] - 1;
+                b[d] = c[d] + 1;
+            }
+            const float va = vmin_at(slots, state, m, wform, a[0], a[1], a[2]);
+            const float vb = vmin_at(slots, state, m, wform, b[0], b[1], b[2]);
+            const float gd = (vb - va) / span;
+            s2 += gd * gd;
+        }
+        mx = fmaxf(mx, sqrtf(s2));
+    }
+    atomicMax(out, __float_as_uint(mx));
+}
+
+// ISA step 2 (projection remark of Sec. 4): x_j belongs to the projected
+// sub-domain k iff it lies in Con, the union of the simplices of the coarse
+// triangulation whose vertices all carry label k.  The coarse cells are split
+// into Kuhn simplices; the fine node lies in the closed simplex selected by
+// the ordering of its local coordinates t_d = loc_d / r_d, and belongs to
+// Con iff every vertex with a non-zero barycentric weight is labelled.
+// Everything is integer: coordinates are compared by cross-multiplication.
+__global__ void project_kernel(hjbh::GridDims fine, hjbh::GridDims coarse, int r0, int r1, int r2,
+                               const uint32_t *cl, uint32_t *out) {
+    const long long N = count(fine);
+    const int r[3] = {r0, r1, r2};
+    GRID_STRIDE(i, N) {
+        int idx[3];
+        unflat(fine, i, idx);
+        int cell[3] = {0, 0, 0}, loc[3] = {0, 0, 0};
+        for (int d = 0; d < fine.ndim; ++d) {
+            int c = idx[d] / r[d];
+            if (!coarse.periodic[d] && c > coarse.n[d] - 2) c = coarse.n[d] - 2;
+            cell[d] = c;
+            loc[d] = idx[d] - c * r[d];
+        }
+        // sort dimensions by decreasing t_d (stable: lower dimension first on ties)
+        int ord[3] = {0, 1, 2};
+        for (int a = 1; a < fine.ndim; ++a) {
+            for (int b = a; b > 0; --b) {
+                const int p = ord[b - 1], q = ord[b];
+                // t_q > t_p  <=>  loc_q r_p > loc_p r_q
+                if (static_cast<long long>(loc[q]) * r[p] > static_cast<long long>(loc[p]) * r[q]) {
+                    ord[b - 1] = q;
+                    ord[b] = p;
+                } else {
+                    break;
+                }
+            }
+        }
+        uint32_t acc = 0xffffffffu;
+        int v[3] = {cell[0], cell[1], cell[2]};
+        for (int k = 0; k <= fine.ndim; ++k) {
+            if (k > 0) v[ord[k - 1]] += 1;
+            // weight of vertex k: t_{ord[k-1]} - t_{ord[k]} (t_{ord[-1]} = 1, t_{ord[D]} = 0)
+            long long nh, dh, nl, dl;
+            if (k == 0) {
+                nh = 1;
+                dh = 1;
+            } else {
+                nh = loc[ord[k - 1]];
+                dh = r[ord[k - 1]];
+            }
+            if (k == fine.ndim) {
+                nl = 0;
+                dl = 1;
+            } else {
+                nl = loc[ord[k]];
+                dl = r[ord[k]];
+            }
+            if (nh * dl > nl * dh) {
+                int w[3] = {v[0], v[1], v[2]};
+                for (int d = 0; d < fine.ndim; ++d)
+                    if (coarse.periodic[d]) w[d] %= coarse.n[d];
+                acc &= cl[flat(coarse, w[0], w[1], fine.ndim > 2 ? w[2] : 0)];
+            }
+        }
+        out[i] = acc;
+    }
+}
+
+// OR of the sub-domain bits over the nodes of each tile (one block per tile).
+__global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, const uint32_t *mask,
+                                 uint32_t *tile_bits) {
+    const int t = blockIdx.x;
+    const int txy = tiles_x * tiles_y;
+    const int tz = t / txy, rem = t - tz * txy;
+    const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
+    const int x = tx * TX + (threadIdx.x & 31), y = ty * TY + (threadIdx.x >> 5);
+    uint32_t bits = 0u;
+    const int zn = g.ndim > 2 ? TZ : 1;
+    for (int lz = 0; lz < zn; ++lz) {
+        const int z = g.ndim > 2 ? tz * TZ + lz : 0;
+        if (x < g.n[0] && y < g.n[1] && (g.ndim < 3 || z < g.n[2])) bits |= mask[flat(g, x, y, z)];
+    }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    __shared__ uint32_t s[THREADS / 32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t b = 0u;
+        for (int w = 0; w < THREADS / 32; ++w) b |= s[w];
+        tile_bits[t] = b;
+    }
+}
+
+// Stream compaction of the tiles carrying bit k (one block per sub-domain):
+// lists + k * ntiles_total receives them, slots[k].ntiles their count.
+__global__ void tile_lists_kernel(int ntiles, const uint32_t *tile_bits, int *lists, SlotDesc *slots) {
+    const int k = blockIdx.x;
+    int *L = lists + static_cast<long long>(k) * ntiles;
+    __shared__ int s_w[THREADS / 32];
+    __shared__ int s_base;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < ntiles; t0 += THREADS) {
+        const int t = t0 + threadIdx.x;
+        const int f = (t < ntiles && ((tile_bits[t] >> k) & 1u)) ? 1 : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int wpre = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) s_w[warp] = __popc(bal);
+        __syncthreads();
+        int off = s_base;
+        for (int w = 0; w < warp; ++w) off += s_w[w];
+        if (f) L[off + wpre] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < THREADS / 32; ++w) tot += s_w[w];
+            s_base += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) slots[k].ntiles = s_base;
+}
+
+// ISA step 4: Vbar(j) = min{ V_k(j) : bit k of mask[j] } (max of W in the
+// W form), value_out on nodes that belong to no sub-domain.
+__global__ void assemble_kernel(const SlotDesc *slots, const SlotState *state, int m,
+                                hjbh::GridDims g, const uint32_t *mask, int wform, float c_over,
+                                float vout_v, float *out) {
+    const long long N = count(g);
+    GRID_STRIDE(i, N) {
+        int c[3];
+        unflat(g, i, c);
+        uint32_t bits = mask[i];
+        if (m < 32) bits &= (1u << m) - 1u;
+        float best = wform ? -INFINITY : INFINITY;
+        while (bits) {
+            const int k = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const float v = slot_value(slots[k], state[k], c[0], c[1], c[2]);
+            best = wform ? fmaxf(best, v) : fminf(best, v);
+        }
+        float res;
+        if (isinf(best))
+            res = vout_v;
+        else
+            res = wform ? c_over - best : best;
+        out[i] = res;
+    }
+}
+
+// Largest |x| over a strided field; a non-finite entry yields +inf so that
+// the caller rejects the field.
+__global__ void absmax_kernel(const float *x, long long n, int stride, int offset, unsigned *out) {
+    float m = 0.0f;
+    GRID_STRIDE(i, n) {
+        float a = fabsf(x[i * stride + offset]);
+        if (!(a <= 3.402823466e38f)) a = INFINITY;
+        m = fmaxf(m, a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+__global__ void exp_kernel(const float *th, float *s, long long n) {
+    GRID_STRIDE(i, n) s[i] = expf(th[i]);
+}
+
+__global__ void popcount_kernel(const uint32_t *mask, long long n, unsigned long long *out) {
+    unsigned long long c = 0;
+    GRID_STRIDE(i, n) c += __popc(mask[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+int blocks_for(long long n) {
+    long long b = (n + THREADS - 1) / THREADS;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return static_cast<int>(b);
+}
+
+}  // namespace
+
+namespace hjbh {
+
+void launch_gather_coarse(const GridDims &fine, const GridDims &coarse, const int stride[3],
+                          const float *speed, const float *current, const float *cost,
+                          const uint8_t *labels, float *c_speed, float *c_current, float *c_cost,
+                          uint8_t *c_labels, cudaStream_t st) {
+    long long NK = static_cast<long long>(coarse.n[0]) * coarse.n[1] * (coarse.ndim > 2 ? coarse.n[2] : 1);
+    gather_coarse_kernel<<<blocks_for(NK), THREADS, 0, st>>>(
+        fine, coarse, stride[0], stride[1], coarse.ndim > 2 ? stride[2] : 1, speed, current, cost,
+        labels, speed ? c_speed : nullptr, current ? c_current : nullptr, cost ? c_cost : nullptr,
+        c_labels);
+}
+
+void launch_label(const SlotDesc *slots, const SlotState *state, int m, const GridDims &coarse,
+                  const uint8_t *labels, float delta, int wform, uint32_t *labels_out,
+                  float *vmin_out, unsigned long long *ties_out, cudaStream_t st) {
+    long long NK = static_cast<long long>(coarse.n[0]) * coarse.n[1] * (coarse.ndim > 2 ? coarse.n[2] : 1);
+    label_kernel<<<blocks_for(NK), THREADS, 0, st>>>(slots, state, m, coarse, labels, delta, wform,
+                                                    labels_out, vmin_out, ties_out);
+}
+
+void launch_grad_max(const SlotDesc *slots, const SlotState *state, int m, int wform,
+                     const GridDims &coarse, const float dx[3], unsigned *out, cudaStream_t st) {
+    long long NK = static_cast<long long>(coarse.n[0]) * coarse.n[1] * (coarse.ndim > 2 ? coarse.n[2] : 1);
+    grad_max_kernel<<<blocks_for(NK), THREADS, 0, st>>>(slots, state, m, wform,
+                                                       coarse, dx[0], dx[1], dx[2], out);
+}
+
+void launch_project(const GridDims &fine, const GridDims &coarse, const int stride[3],
+                    const uint32_t *coarse_labels, uint32_t *fine_mask, cudaStream_t st) {
+    long long N = static_cast<long long>(fine.n[0]) * fine.n[1] * (fine.ndim > 2 ? fine.n[2] : 1);
+    project_kernel<<<blocks_for(N), THREADS, 0, st>>>(fine, coarse, stride[0], stride[1],
+                                                     fine.ndim > 2 ? stride[2] : 1, coarse_labels,
+                                                     fine_mask);
+}
+
+void launch_tile_lists(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z,
+                       const uint32_t *mask, int m, uint32_t *tile_bits, int *lists,
+                       SlotDesc *slots, cudaStream_t st) {
+    const int nt = tiles_x * tiles_y * tiles_z;
+    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, mask, tile_bits);
+    tile_lists_kernel<<<m, THREADS, 0, st>>>(nt, tile_bits, lists, slots);
+}
+
+void launch_assemble(const SlotDesc *slots, const SlotState *state, int m, const GridDims &fine,
+                     const uint32_t *mask, int wform, float c_over, float vout_v, float *out,
+                     cudaStream_t st) {
+    long long N = static_cast<long long>(fine.n[0]) * fine.n[1] * (fine.ndim > 2 ? fine.n[2] : 1);
+    assemble_kernel<<<blocks_for(N), THREADS, 0, st>>>(slots, state, m, fine, mask, wform, c_over,
+                                                      vout_v, out);
+}
+
+void launch_absmax(const float *x, long long n, int stride, int offset, unsigned *out,
+                   cudaStream_t st) {
+    absmax_kernel<<<blocks_for(n), THREADS, 0, st>>>(x, n, stride, offset, out);
+}
+
+void launch_exp(const float *theta, float *s, long long n, cudaStream_t st) {
+    exp_kernel<<<blocks_for(n), THREADS, 0, st>>>(theta, s, n);
+}
+
+void launch_popcount(const uint32_t *mask, long long n, unsigned long long *out, cudaStream_t st) {
+    popcount_kernel<<<blocks_for(n), THREADS, 0, st>>>(mask, n, out);
+}
+
+}  // namespace hjbh

@@ -1,0 +1,804 @@
+// sweep.cu -- the value-iteration sweep: one Jacobi application of the
+// semi-Lagrangian operator T of Festa (arXiv:1405.3521), Sec. 3, eq. (Tdef),
+//
+//   [T(V)]_i = beta * min_a I[V](x_i + h f(x_i, a)) + gamma * l_i   (free node)
+//
+// to every free node of every active problem ("slot") of a launch, with the
+// L-infinity residual ||T(V) - V|| of the stopping remark of Sec. 3 fused
+// into the same kernel, and the convergence decision taken by the last CTA
+// to finish (which also drives the CUDA-graph WHILE loop around the sweep).
+//
+// Design for sm_103a:
+//  * persistent grid (SMs x resident CTAs), items = (slot, tile) pulled from a
+//    compacted list of active slots, so converged problems cost nothing;
+//  * each tile of V plus its interpolation halo is staged in shared memory by
+//    a TMA tensor load (cp.async.bulk.tensor) completing on an mbarrier, with
+//    the next item's tile prefetched while the current one is computed;
+//  * per node, the foot of every control is located with two FP32 adds
+//    against a 2^23 magic constant (cell index and fraction without
+//    float-to-int conversions), and interpolated with a monotone two-product
+//    lerp, so that in the W = l/lambda - V form the FP32 iteration is itself
+//    monotone and ends at an exact FP32 fixed point;
+//  * feet are tested against the box only in tiles that touch the boundary.
+#include <math.h>
+
+#include "hjb_internal.cuh"
+
+using namespace hjbk;
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `phase` of an mbarrier, giving up after WAIT_NS.
+__device__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (global_ns() - t0 > WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Node classes of Sec. 3 for one slot: ghost (outside a restricted
+// sub-domain), target (the slot's part of dG) or free (G).
+enum { CLS_FREE = 0, CLS_TARGET = 1, CLS_GHOST = 2 };
+__device__ __forceinline__ int node_class(const SlotDesc &S, long long gi) {
+    if (S.mask != nullptr && !((S.mask[gi] >> S.mask_bit) & 1u)) return CLS_GHOST;
+    const int lab = S.labels[gi];
+    if (lab != 0 && (S.only_target == 0 || lab == S.only_target)) return CLS_TARGET;
+    return CLS_FREE;
+}
+
+// Magic constant 2^23 - 1/2: for p in [1/2, 2^22), p + M rounds to
+// 2^23 + rn(p - 1/2), so the float's low mantissa bits hold the cell index
+// k in {floor(p) - 1, floor(p)} with p - k in [0, 1].
+constexpr float MAGIC = 8388607.5f;
+constexpr float TWO23 = 8388608.0f;
+constexpr int TWO23_BITS = 0x4B000000;
+
+// Bilinear interpolation in a shared-memory tile with row width TW.
+// (px, py) are tile-local coordinates; py carries a +1 shift so that it is
+// >= 1/2 for every foot (the row index is corrected below).  The lerp uses
+// the two-product form (1-f) a + f b, which is monotone in a and b under
+// FP32 rounding.
+__device__ __forceinline__ float q1_tile(const float *T, float px, float py) {
+    const float mx = px + MAGIC;
+    const float my = py + MAGIC;
+    const float kx = mx - TWO23;
+    const float ky = my - TWO23;
+    const float fx = px - kx;
+    const float fy = py - ky;
+    const float ex = 1.0f - fx;
+    const float ey = 1.0f - fy;
+    const int idx = (__float_as_int(my) - (TWO23_BITS + 1)) * TW + (__float_as_int(mx) - TWO23_BITS);
+    const float v00 = T[idx];
+    const float v10 = T[idx + 1];
+    const float v01 = T[idx + TW];
+    const float v11 = T[idx + TW + 1];
+    const float a = fmaf(fx, v10, ex * v00);
+    const float b = fmaf(fx, v11, ex * v01);
+    return fmaf(fy, b, ey * a);
+}
+
+template <bool WFORM>
+__device__ __forceinline__ float pick(float best, float q) {
+    return WFORM ? fmaxf(best, q) : fminf(best, q);
+}
+
+// Evaluation of all controls at one node of a tile that does not touch the
+// box boundary (no foot can leave the box).
+template <int NA, bool WFORM>
+__device__ __forceinline__ float controls_interior(const ControlTable &C, const float *T, float sx,
+                                                   float sy, float bx, float by, float best) {
+    if constexpr (NA > 0) {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const float px = fmaf(sx, C.ax[j], bx);
+            const float py = fmaf(sy, C.ay[j], by);
+            best = pick<WFORM>(best, q1_tile(T, px, py));
+        }
+    } else {
+        const int na = C.count;
+#pragma unroll 4
+        for (int j = 0; j < na; ++j) {
+            const float px = fmaf(sx, C.ax[j], bx);
+            const float py = fmaf(sy, C.ay[j], by);
+            best = pick<WFORM>(best, q1_tile(T, px, py));
+        }
+    }
+    return best;
+}
+
+// Node bounds in cell offsets: a foot with offset o is outside the closed
+// box when o < lo - 1e-6 or o > hi + 1e-6 (reading R2: 1e-6 grid cells of
+// tolerance, in-tolerance feet clamped onto the face).
+struct EdgeBounds {
+    float lox, hix, loy, hiy;
+};
+
+template <bool WFORM>
+__device__ __forceinline__ float one_control_edge(const float *T, float ox, float oy,
+                                                  const EdgeBounds &eb, float basex, float basey,
+                                                  float vout, float best) {
+    const bool out = (ox < eb.lox - 1e-6f) | (ox > eb.hix + 1e-6f) | (oy < eb.loy - 1e-6f) |
+                     (oy > eb.hiy + 1e-6f);
+    ox = fminf(fmaxf(ox, eb.lox), eb.hix);
+    oy = fminf(fmaxf(oy, eb.loy), eb.hiy);
+    const float q = q1_tile(T, basex + ox, basey + oy);
+    return pick<WFORM>(best, out ? vout : q);
+}
+
+template <int NA, bool WFORM>
+__device__ __forceinline__ float controls_edge(const ControlTable &C, const float *T, float sx,
+                                               float sy, float ox0, float oy0, const EdgeBounds &eb,
+                                               float basex, float basey, float vout, float best) {
+    if constexpr (NA > 0) {
+#pragma unroll
+        for (int j = 0; j < NA; ++j)
+            best = one_control_edge<WFORM>(T, fmaf(sx, C.ax[j], ox0), fmaf(sy, C.ay[j], oy0), eb,
+                                           basex, basey, vout, best);
+    } else {
+        const int na = C.count;
+#pragma unroll 4
+        for (int j = 0; j < na; ++j)
+            best = one_control_edge<WFORM>(T, fmaf(sx, C.ax[j], ox0), fmaf(sy, C.ay[j], oy0), eb,
+                                           basex, basey, vout, best);
+    }
+    return best;
+}
+
+// Active item v -> (slot, index of the item inside the slot).
+__device__ __forceinline__ void map_item(const Ctl *ctl, int nact, int v, int &slot, int &local) {
+    int lo = 0, hi = nact - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ctl->act_prefix[mid] <= v)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    slot = ctl->act_slot[lo];
+    local = v - ctl->act_prefix[lo];
+}
+
+// Block-wide exclusive scan of two ints (256 threads).
+__device__ __forceinline__ void block_scan2(int a, int b, int &ea, int &eb, int &ta, int &tb,
+                                            int *sa, int *sb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int xa = __shfl_up_sync(0xffffffffu, ia, o);
+        const int xb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += xa;
+            ib += xb;
+        }
+    }
+    if (lane == 31) {
+        sa[warp] = ia;
+        sb[warp] = ib;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int va = lane < THREADS / 32 ? sa[lane] : 0;
+        int vb = lane < THREADS / 32 ? sb[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int xa = __shfl_up_sync(0xffffffffu, va, o);
+            const int xb = __shfl_up_sync(0xffffffffu, vb, o);
+            if (lane >= o) {
+                va += xa;
+                vb += xb;
+            }
+        }
+        if (lane < THREADS / 32) {
+            sa[lane] = va;
+            sb[lane] = vb;
+        }
+    }
+    __syncthreads();
+    const int wa = warp ? sa[warp - 1] : 0;
+    const int wb = warp ? sb[warp - 1] : 0;
+    ea = wa + ia - a;
+    eb = wb + ib - b;
+    ta = sa[THREADS / 32 - 1];
+    tb = sb[THREADS / 32 - 1];
+    __syncthreads();
+}
+
+// Convergence step, run by the last CTA of a sweep: read and reset each
+// active slot's residual, apply the stopping rule (residual <= tol, the
+// iteration cap, or stagnation at rounding level), compact the active list
+// and set the graph loop condition.
+__device__ void finish_sweep(const SweepArgs &args) {
+    Ctl *ctl = args.ctl;
+    __shared__ int s_sa[THREADS / 32], s_sb[THREADS / 32];
+    const int n = ctl->nactive;
+    const int dst_parity = static_cast<int>((ctl->sweep & 1u) ^ 1u);
+    const int err = ctl->error;
+    constexpr int PER = MAX_SLOTS / THREADS;
+    int sid[PER], keep[PER];
+    int cnt = 0, tiles = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x * PER + k;
+        keep[k] = 0;
+        sid[k] = -1;
+        if (i >= n) continue;
+        const int s = ctl->act_slot[i];
+        sid[k] = s;
+        SlotState &st = args.state[s];
+        const SlotDesc &S = args.slots[s];
+        const float r = __uint_as_float(st.res_bits);
+        st.res_bits = 0u;
+        st.iters += 1;
+        st.final_res = r;
+        st.final_parity = dst_parity;
+        int kp = 1;
+        if (r <= S.tol) {
+            st.converged = 1;
+            kp = 0;
+        } else if (st.iters >= S.max_iters || err) {
+            kp = 0;
+        } else {
+            if (r < st.best_res) {
+                st.best_res = r;
+                st.stall = 0;
+            } else if (++st.stall >= 64 && r <= args.stall_tol) {
+                st.converged = 2;
+                kp = 0;
+            }
+        }
+        if (!kp) st.done = 1;
+        keep[k] = kp;
+        cnt += kp;
+        tiles += kp ? S.ntiles : 0;
+    }
+    // every thread has read its entries of the active list before the scan's
+    // barriers, so the list can be compacted in place afterwards
+    int ec, et, tc, tt;
+    block_scan2(cnt, tiles, ec, et, tc, tt, s_sa, s_sb);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (keep[k]) {
+            ctl->act_slot[ec] = sid[k];
+            ctl->act_prefix[ec] = et;
+            ++ec;
+            et += args.slots[sid[k]].ntiles;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->act_prefix[tc] = tt;
+        ctl->nactive = tc;
+        ctl->total_items = tt;
+        if (n > 0) ctl->sweep += 1u;
+        ctl->launches += 1u;
+        ctl->done_ctas = 0u;
+        __threadfence();
+        if (args.use_handle) cudaGraphSetConditional(args.handle, (tc > 0 && !err) ? 1u : 0u);
+    }
+}
+
+// Count this CTA as finished; the last one runs finish_sweep.
+__device__ __forceinline__ void cta_done(const SweepArgs &args, bool failed) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (failed) atomicExch(&args.ctl->error, 1);
+        __threadfence();
+        const unsigned t = atomicAdd(&args.ctl->done_ctas, 1u);
+        s_last = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finish_sweep(args);
+    }
+}
+
+// --------------------------------------------------------------------------
+// 2D sweep: f = s(x) a + c(x).  Tile 32 x 8, halo H (cells) in x and y.
+
+template <int NA, bool WFORM, int H>
+__global__ void __launch_bounds__(THREADS) sweep2d_kernel(const __grid_constant__ SweepArgs args) {
+    constexpr int ROWS = TY + 2 * H;
+    constexpr int TILE = ROWS * TW;
+    __shared__ alignas(128) float s_tile[2][TILE];
+    __shared__ alignas(8) uint64_t s_bar[2];
+    __shared__ int s_item[2][2];
+    __shared__ float s_red[THREADS / 32];
+
+    const Ctl *ctl = args.ctl;
+    const int tid = threadIdx.x;
+    const int lx = tid & 31, ly = tid >> 5;
+    const unsigned sweep = ctl->sweep;
+    const int src = static_cast<int>(sweep & 1u), dst = src ^ 1;
+    const int nitems = ctl->total_items;
+    const int nact = ctl->nactive;
+
+    auto issue = [&](int v, int b) {
+        int slot, local;
+        map_item(ctl, nact, v, slot, local);
+        const SlotDesc *S = args.slots + slot;
+        const int tile = S->tile_list ? S->tile_list[local] : local;
+        s_item[b][0] = slot;
+        s_item[b][1] = tile;
+        const int tx = tile % S->tiles_x, ty = tile / S->tiles_x;
+        mbar_expect_tx(&s_bar[b], TILE * 4);
+        tma_load_2d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H, &s_bar[b]);
+    };
+
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int v = blockIdx.x;
+    if (tid == 0 && v < nitems) issue(v, 0);
+    __syncthreads();
+    bool failed = false;
+    for (int it = 0; v < nitems; ++it, v += gridDim.x) {
+        const int b = it & 1;
+        const int vn = v + gridDim.x;
+        if (tid == 0 && vn < nitems) issue(vn, b ^ 1);
+        const bool ok = mbar_wait_bounded(&s_bar[b], (it >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            // let the prefetch of the next item (if any) land before leaving
+            if (vn < nitems) mbar_wait_bounded(&s_bar[b ^ 1], ((it + 1) >> 1) & 1);
+            break;
+        }
+        const int slot = s_item[b][0], tile = s_item[b][1];
+        const SlotDesc &S = args.slots[slot];
+        const int nx = S.nx, ny = S.ny;
+        const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
+        const int gx = tx * TX + lx, gy = ty * TY + ly;
+        const float *T = s_tile[b];
+        const float vold = T[(ly + H) * TW + lx + XPAD];
+        const long long gi = static_cast<long long>(gy) * nx + gx;
+        const bool isfree = (gx < nx) && (gy < ny) && node_class(S, gi) == CLS_FREE;
+        float vnew = vold;
+        if (isfree) {
+            const float s = S.speed ? S.speed[gi] : 1.0f;
+            float cx = 0.0f, cy = 0.0f;
+            if (S.current) {
+                const float2 c = reinterpret_cast<const float2 *>(S.current)[gi];
+                cx = c.x;
+                cy = c.y;
+            }
+            const float sx = s * S.hx, sy = s * S.hy;
+            const float ox0 = cx * S.hx, oy0 = cy * S.hy;
+            const float basex = static_cast<float>(lx + XPAD);
+            const float basey = static_cast<float>(ly + H + 1);
+            const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
+                                  (ty * TY >= H) && (ty * TY + TY - 1 + H <= ny - 1);
+            float best = WFORM ? -INFINITY : INFINITY;
+            if (interior) {
+                best = controls_interior<NA, WFORM>(args.ctrl, T, sx, sy, basex + ox0, basey + oy0,
+                                                    best);
+            } else {
+                EdgeBounds eb;
+                eb.lox = -static_cast<float>(gx);
+                eb.hix = static_cast<float>(nx - 1 - gx);
+                eb.loy = -static_cast<float>(gy);
+                eb.hiy = static_cast<float>(ny - 1 - gy);
+                best = controls_edge<NA, WFORM>(args.ctrl, T, sx, sy, ox0, oy0, eb, basex, basey,
+                                                S.vout, best);
+            }
+            if (WFORM)
+                vnew = S.beta * best;
+            else
+                vnew = fmaf(S.beta, best, S.cost ? S.gamma * S.cost[gi] : S.gl);
+            S.V[dst][static_cast<long long>(gy) * S.pitch + gx] = vnew;
+        }
+        const float r = warp_max(isfree ? fabsf(vnew - vold) : 0.0f);
+        if (lx == 0) s_red[ly] = r;
+        const int cnt = __syncthreads_count(isfree);
+        if (tid == 0) {
+            float m = s_red[0];
+#pragma unroll
+            for (int w = 1; w < THREADS / 32; ++w) m = fmaxf(m, s_red[w]);
+            atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
+            atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(cnt));
+        }
+        __syncthreads();
+    }
+    cta_done(args, failed);
+}
+
+// --------------------------------------------------------------------------
+// 3D Dubins sweep: f = (v cos th, v sin th, u), th = dimension 2 (periodic).
+// Tile 32 x 8 x TZ, halo 2 in x, y and 1 in th.  The (x, y) part of the foot
+// does not depend on the control, so the bilinear values at the three
+// heading layers a foot can reach are computed once per node and each
+// control only interpolates in th.
+
+template <bool WFORM>
+__global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant__ SweepArgs args) {
+    constexpr int H = 2, HZ = 1;
+    constexpr int ROWS = TY + 2 * H;
+    constexpr int LAYER = ROWS * TW;
+    constexpr int TILE = (TZ + 2 * HZ) * LAYER;
+    __shared__ alignas(128) float s_tile[2][TILE];
+    __shared__ alignas(8) uint64_t s_bar[2];
+    __shared__ int s_item[2][2];
+    __shared__ float s_red[THREADS / 32];
+    __shared__ int s_cnt[THREADS / 32];
+
+    const Ctl *ctl = args.ctl;
+    const int tid = threadIdx.x;
+    const int lx = tid & 31, ly = tid >> 5;
+    const unsigned sweep = ctl->sweep;
+    const int src = static_cast<int>(sweep & 1u), dst = src ^ 1;
+    const int nitems = ctl->total_items;
+    const int nact = ctl->nactive;
+
+    auto issue = [&](int v, int b) {
+        int slot, local;
+        map_item(ctl, nact, v, slot, local);
+        const SlotDesc *S = args.slots + slot;
+        const int tile = S->tile_list ? S->tile_list[local] : local;
+        s_item[b][0] = slot;
+        s_item[b][1] = tile;
+        const int txy = S->tiles_x * S->tiles_y;
+        const int tz = tile / txy, rem = tile - tz * txy;
+        const int ty = rem / S->tiles_x, tx = rem - ty * S->tiles_x;
+        mbar_expect_tx(&s_bar[b], TILE * 4);
+        tma_load_3d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H, tz * TZ - HZ + S->zdup,
+                    &s_bar[b]);
+    };
+
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int v = blockIdx.x;
+    if (tid == 0 && v < nitems) issue(v, 0);
+    __syncthreads();
+    bool failed = false;
+    for (int it = 0; v < nitems; ++it, v += gridDim.x) {
+        const int b = it & 1;
+        const int vn = v + gridDim.x;
+        if (tid == 0 && vn < nitems) issue(vn, b ^ 1);
+        const bool ok = mbar_wait_bounded(&s_bar[b], (it >> 1) & 1);
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            if (vn < nitems) mbar_wait_bounded(&s_bar[b ^ 1], ((it + 1) >> 1) & 1);
+            break;
+        }
+        const int slot = s_item[b][0], tile = s_item[b][1];
+        const SlotDesc &S = args.slots[slot];
+        const int nx = S.nx, ny = S.ny, nz = S.nz;
+        const int txy = S.tiles_x * S.tiles_y;
+        const int tz = tile / txy, rem = tile - tz * txy;
+        const int ty = rem / S.tiles_x, tx = rem - ty * S.tiles_x;
+        const int gx = tx * TX + lx, gy = ty * TY + ly;
+        const float *T = s_tile[b];
+        const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
+                              (ty * TY >= H) && (ty * TY + TY - 1 + H <= ny - 1);
+        float rmax = 0.0f;
+        int cnt = 0;
+#pragma unroll 1
+        for (int lz = 0; lz < TZ; ++lz) {
+            const int gz = tz * TZ + lz;
+            const float *L = T + (lz + HZ) * LAYER;  // layer of this node
+            const float vold = L[(ly + H) * TW + lx + XPAD];
+            const long long gi = (static_cast<long long>(gz) * ny + gy) * nx + gx;
+            const bool isfree = (gx < nx) && (gy < ny) && (gz < nz) && node_class(S, gi) == CLS_FREE;
+            if (!isfree) continue;
+            const float2 tr = S.trig[gz];
+            float ox = tr.x, oy = tr.y;
+            bool out = false;
+            if (!interior) {
+                const float lox = -static_cast<float>(gx), hix = static_cast<float>(nx - 1 - gx);
+                const float loy = -static_cast<float>(gy), hiy = static_cast<float>(ny - 1 - gy);
+                out = (ox < lox - 1e-6f) | (ox > hix + 1e-6f) | (oy < loy - 1e-6f) |
+                      (oy > hiy + 1e-6f);
+                ox = fminf(fmaxf(ox, lox), hix);
+                oy = fminf(fmaxf(oy, loy), hiy);
+            }
+            float best;
+            if (out) {
+                best = S.vout;
+            } else {
+                // bilinear (x, y) values at layers lz-1, lz, lz+1 of the tile
+                const float px = static_cast<float>(lx + XPAD) + ox;
+                const float py = static_cast<float>(ly + H + 1) + oy;
+                const float mx = px + MAGIC, my = py + MAGIC;
+                const float fx = px - (mx - TWO23), fy = py - (my - TWO23);
+                const float ex = 1.0f - fx, ey = 1.0f - fy;
+                const int idx = (__float_as_int(my) - (TWO23_BITS + 1)) * TW +
+                                (__float_as_int(mx) - TWO23_BITS);
+                float B[3];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const float *P = T + (lz + HZ - 1 + t) * LAYER + idx;
+                    const float a = fmaf(fx, P[1], ex * P[0]);
+                    const float c = fmaf(fx, P[TW + 1], ex * P[TW]);
+                    B[t] = fmaf(fy, c, ey * a);
+                }
+                // heading: local coordinate of the node is lz + HZ + 1 (+1 shift)
+                const float bz = static_cast<float>(lz + HZ + 1);
+                const int kz0 = lz + HZ + 1;
+                best = WFORM ? -INFINITY : INFINITY;
+                const int na = args.ctrl.count;
+#pragma unroll 4
+                for (int j = 0; j < na; ++j) {
+                    const float pz = fmaf(S.hz, args.ctrl.ax[j], bz);
+                    const float mz = pz + MAGIC;
+                    const float fz = pz - (mz - TWO23);
+                    const int d = (__float_as_int(mz) - TWO23_BITS) - kz0;  // -1 or 0
+                    const float lo = d < 0 ? B[0] : B[1];
+                    const float hi = d < 0 ? B[1] : B[2];
+                    const float q = fmaf(fz, hi, (1.0f - fz) * lo);
+                    best = pick<WFORM>(best, q);
+                }
+            }
+            float vnew;
+            if (WFORM)
+                vnew = S.beta * best;
+            else
+                vnew = fmaf(S.beta, best, S.cost ? S.gamma * S.cost[gi] : S.gl);
+            float *D = S.V[dst];
+            const long long row = static_cast<long long>(gy) * S.pitch + gx;
+            D[static_cast<long long>(gz + S.zdup) * S.zstride + row] = vnew;
+            if (gz < S.zdup) D[static_cast<long long>(gz + nz + S.zdup) * S.zstride + row] = vnew;
+            if (gz >= nz - S.zdup)
+                D[static_cast<long long>(gz - nz + S.zdup) * S.zstride + row] = vnew;
+            rmax = fmaxf(rmax, fabsf(vnew - vold));
+            ++cnt;
+        }
+        const float r = warp_max(rmax);
+        if (lx == 0) s_red[ly] = r;
+        int c = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lx == 0) s_cnt[ly] = c;
+        __syncthreads();
+        if (tid == 0) {
+            float m = s_red[0];
+            int tot = s_cnt[0];
+#pragma unroll
+            for (int w = 1; w < THREADS / 32; ++w) {
+                m = fmaxf(m, s_red[w]);
+                tot += s_cnt[w];
+            }
+            atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
+            atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot));
+        }
+        __syncthreads();
+    }
+    cta_done(args, failed);
+}
+
+// --------------------------------------------------------------------------
+// Helpers around the loop.
+
+__global__ void loop_init_kernel(const SlotDesc *slots, SlotState *state, Ctl *ctl, int nslots) {
+    __shared__ int s_sa[THREADS / 32], s_sb[THREADS / 32];
+    constexpr int PER = MAX_SLOTS / THREADS;
+    int tiles = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x * PER + k;
+        if (i < nslots) {
+            tiles += slots[i].ntiles;
+            SlotState &st = state[i];
+            st.res_bits = 0u;
+            st.iters = 0;
+            st.done = 0;
+            st.converged = 0;
+            st.final_parity = 0;
+            st.stall = 0;
+            st.best_res = INFINITY;
+            st.final_res = 0.0f;
+            st.updates = 0ull;
+            st.changed = 0ull;
+        }
+    }
+    int ec, et, tc, tt;
+    block_scan2(0, tiles, ec, et, tc, tt, s_sa, s_sb);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x * PER + k;
+        if (i < nslots) {
+            ctl->act_slot[i] = i;
+            ctl->act_prefix[i] = et;
+            et += slots[i].ntiles;
+        }
+    }
+    if (threadIdx.x == 0) {
+        ctl->act_prefix[nslots] = tt;
+        ctl->nactive = nslots;
+        ctl->total_items = tt;
+        ctl->sweep = 0u;
+        ctl->done_ctas = 0u;
+        ctl->error = 0;
+        ctl->launches = 0u;
+    }
+}
+
+// Starting iterate of every slot, written to both buffers (and the
+// duplicated heading layers): targets take vtarget, ghosts and free nodes
+// vout, or the warm start converted to the iterated variable.
+__global__ void init_values_kernel(const SlotDesc *slots, int wform, float c_over,
+                                   const float *v_init) {
+    const SlotDesc &S = slots[blockIdx.y];
+    const long long N = static_cast<long long>(S.nx) * S.ny * S.nz;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int cls = node_class(S, i);
+        float v;
+        if (cls == CLS_TARGET)
+            v = S.vtarget;
+        else if (cls == CLS_GHOST || v_init == nullptr)
+            v = S.vout;
+        else
+            v = wform ? c_over - v_init[i] : v_init[i];
+        const long long gx = i % S.nx;
+        const long long r = i / S.nx;
+        const long long gy = r % S.ny;
+        const long long gz = r / S.ny;
+        const long long row = gy * S.pitch + gx;
+        for (int b = 0; b < 2; ++b) {
+            float *D = S.V[b];
+            D[(gz + S.zdup) * S.zstride + row] = v;
+            if (gz < S.zdup) D[(gz + S.nz + S.zdup) * S.zstride + row] = v;
+            if (gz >= S.nz - S.zdup) D[(gz - S.nz + S.zdup) * S.zstride + row] = v;
+        }
+    }
+}
+
+// Copy the latest iterate of one slot to a dense [N] array, converting
+// W back to V = c_over - W in the W form.
+__global__ void extract_kernel(const SlotDesc *slots, const SlotState *state, int slot, float *out,
+                               int wform, float c_over) {
+    const SlotDesc &S = slots[slot];
+    const float *Vb = S.V[state[slot].final_parity];
+    const long long N = static_cast<long long>(S.nx) * S.ny * S.nz;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long gx = i % S.nx;
+        const long long r = i / S.nx;
+        const long long gy = r % S.ny;
+        const long long gz = r / S.ny;
+        const float w = Vb[(gz + S.zdup) * S.zstride + gy * S.pitch + gx];
+        out[i] = wform ? c_over - w : w;
+    }
+}
+
+}  // namespace
+
+namespace hjbh {
+
+const void *sweep_kernel(const SweepKey &k, size_t *smem) {
+    if (smem) *smem = 0;
+    if (k.dubins) {
+        if (k.halo != 2) return nullptr;
+        return k.wform ? reinterpret_cast<const void *>(&sweep3d_kernel<true>)
+                       : reinterpret_cast<const void *>(&sweep3d_kernel<false>);
+    }
+#define HJB_PICK(NA_, H_)                                                          \
+    if (k.halo == H_) {                                                            \
+        return k.wform ? reinterpret_cast<const void *>(&sweep2d_kernel<NA_, true, H_>) \
+                       : reinterpret_cast<const void *>(&sweep2d_kernel<NA_, false, H_>); \
+    }
+    switch (k.na) {
+        case 64:
+            HJB_PICK(64, 2)
+            HJB_PICK(64, 4)
+            break;
+        case 32:
+            HJB_PICK(32, 2)
+            HJB_PICK(32, 4)
+            break;
+        case 16:
+            HJB_PICK(16, 2)
+            HJB_PICK(16, 4)
+            break;
+        default:
+            HJB_PICK(0, 2)
+            HJB_PICK(0, 4)
+            break;
+    }
+#undef HJB_PICK
+    return nullptr;
+}
+
+int sweep_grid(const SweepKey &k) {
+    const void *f = sweep_kernel(k, nullptr);
+    if (!f) return 0;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, THREADS, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+void launch_loop_init(const SlotDesc *slots, SlotState *state, Ctl *ctl, int nslots,
+                      const int * /*ntiles_dev*/, cudaStream_t st) {
+    loop_init_kernel<<<1, THREADS, 0, st>>>(slots, state, ctl, nslots);
+}
+
+void launch_init_values(const SlotDesc *slots, int nslots, int max_nodes, int wform, float c_over,
+                        const float *v_init, cudaStream_t st) {
+    int bx = (max_nodes + THREADS - 1) / THREADS;
+    if (bx > 4096) bx = 4096;
+    if (bx < 1) bx = 1;
+    dim3 grid(bx, nslots);
+    init_values_kernel<<<grid, THREADS, 0, st>>>(slots, wform, c_over, v_init);
+}
+
+void launch_extract(const SlotDesc *slots, const SlotState *state, int slot, float *out, int wform,
+                    float c_over, cudaStream_t st) {
+    extract_kernel<<<1184, THREADS, 0, st>>>(slots, state, slot, out, wform, c_over);
+}
+
+}  // namespace hjbh

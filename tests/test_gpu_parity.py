@@ -1,0 +1,267 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  Tolerance: 1e-4 in L-infinity on V (the Kruzhkov
+value); labels bit-exact except decisions within 1e-6 of the threshold;
+gradients 1e-3 relative."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from _cases import gpu_problem, oracle_problem, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL_V = 1e-4
+
+
+@pytest.fixture(scope="module")
+def hjb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1405_3521_gb300 as h
+    h._capi.lib()  # fails loudly when the library is missing
+    return h
+
+
+def _ref(orc, d, tol=1e-12, **kw):
+    p = oracle_problem(orc, d)
+    V, it, r = orc.solve(p, tol=tol, nthreads=8, **kw)
+    return p, V
+
+
+@pytest.mark.parametrize("wform", [1, 0])
+def test_c1_full_solve(hjb, orc, wform):
+    d = S.c1()
+    _, Vo = _ref(orc, d, tol=1e-10)
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p, use_w_form=wform)
+    err = np.abs(to_np(V) - Vo).max()
+    assert st["converged"] == 1
+    assert err < TOL_V, err
+    assert st["node_updates"] == st["iterations"] * int((d["labels"] == 0).sum())
+
+
+@pytest.mark.parametrize("nx,ny,A,cur", [(67, 45, 16, True), (33, 97, 7, False),
+                                          (130, 9, 32, True), (257, 129, 64, True)])
+def test_ragged_speed_current(hjb, orc, nx, ny, A, cur):
+    """Grids that are not multiples of the 32 x 8 tile, generic and
+    specialised control counts, speed and current fields."""
+    X, Y = S.mesh2(nx, ny)
+    g = S.rng("misc", nx * 1000 + ny)
+    cen = S.disk_centers(g, 3, 0.12)
+    lab = S.disk_labels(X, Y, cen, 0.12)
+    d = dict(shape=(nx, ny), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=S.f32(S.circle_controls(A)), labels=lab, ntargets=3,
+             speed=S.f32(S.speed_field(g, X, Y)),
+             current=S.f32(S.current_field(g, X, Y)) if cur else None,
+             h=min(2.0 / (nx - 1), 2.0 / (ny - 1)), lam=1.0, v_out=1.0)
+    _, Vo = _ref(orc, d, tol=1e-11)
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p)
+    assert np.abs(to_np(V) - Vo).max() < TOL_V
+
+
+def test_halo4_long_steps(hjb, orc):
+    """Feet travelling 2-4 cells per step select the wider-halo kernel."""
+    n = 61
+    X, Y = S.mesh2(n, n)
+    g = S.rng("misc", 77)
+    lab = S.disk_labels(X, Y, S.disk_centers(g, 2, 0.15), 0.15)
+    d = dict(shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=S.f32(S.circle_controls(32)), labels=lab, ntargets=2,
+             speed=S.f32(S.speed_field(g, X, Y)), current=None, h=2.3 * 2.0 / (n - 1), lam=1.0,
+             v_out=1.0)
+    _, Vo = _ref(orc, d, tol=1e-11)
+    V, st = hjb.solve(gpu_problem(hjb, d))
+    assert np.abs(to_np(V) - Vo).max() < TOL_V
+
+
+def test_cost_field_vform(hjb, orc):
+    """A running-cost field forces the V (min) form; lambda != 1."""
+    n = 73
+    X, Y = S.mesh2(n, n)
+    g = S.rng("misc", 5)
+    lab = S.disk_labels(X, Y, S.disk_centers(g, 2, 0.1), 0.1)
+    cost = S.f32(0.5 + X * X + Y * Y)
+    d = dict(shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=S.f32(S.circle_controls(32)), labels=lab, ntargets=2, speed=None,
+             current=None, cost=cost, h=2.0 / (n - 1), lam=0.7, v_out=2.5 / 0.7)
+    _, Vo = _ref(orc, d, tol=1e-11)
+    V, st = hjb.solve(gpu_problem(hjb, d))
+    assert np.abs(to_np(V) - Vo).max() < TOL_V
+
+
+def test_host_buffers_match_device(hjb, orc):
+    d = S.c2(n=129, ntargets=5)
+    pd = gpu_problem(hjb, d)
+    ph = gpu_problem(hjb, d, host=True)
+    Vd, _ = hjb.solve(pd)
+    Vh, _ = hjb.solve(ph)
+    assert isinstance(Vh, np.ndarray)
+    assert np.array_equal(to_np(Vd), Vh)
+
+
+def test_warm_start_and_degenerate(hjb, orc):
+    d = S.c1(n=41)
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p)
+    V2, st2 = hjb.solve(p, v_init=V)
+    assert st2["iterations"] <= 2
+    assert np.abs(to_np(V2) - to_np(V)).max() < 1e-6
+    # no target node at all: every node keeps the "never arrives" value
+    d0 = dict(d)
+    d0["labels"] = np.zeros_like(d["labels"])
+    V0, st0 = hjb.solve(gpu_problem(hjb, d0))
+    assert np.abs(to_np(V0) - 1.0).max() < 1e-6
+    # every node a target: nothing to iterate
+    d1 = dict(d)
+    d1["labels"] = np.ones_like(d["labels"])
+    d1["ntargets"] = 1
+    V1, st1 = hjb.solve(gpu_problem(hjb, d1))
+    assert np.abs(to_np(V1)).max() == 0.0 and st1["node_updates"] == 0
+    # smallest grid: 2 x 2
+    d2 = dict(shape=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+              controls=S.f32(S.axis_controls()), labels=np.array([[1, 0], [0, 0]], np.uint8),
+              ntargets=1, speed=None, current=None, h=1.0, lam=1.0, v_out=1.0)
+    _, Vo = _ref(orc, d2)
+    V2, _ = hjb.solve(gpu_problem(hjb, d2))
+    assert np.abs(to_np(V2) - Vo).max() < 1e-6
+
+
+def test_not_converged_reports(hjb):
+    d = S.c1(n=61)
+    p = gpu_problem(hjb, d)
+    with pytest.raises(hjb.NotConverged):
+        hjb.solve(p, max_iters=3)
+    V, st = hjb.solve(p, max_iters=3, allow_not_converged=True)
+    assert st["iterations"] == 3 and st["converged"] == 0
+
+
+def test_dubins_3d(hjb, orc):
+    d = S.c3(nxy=41, nth=16, ntargets=3, stride=(5, 5, 4))
+    _, Vo = _ref(orc, d, tol=1e-11)
+    V, st = hjb.solve(gpu_problem(hjb, d))
+    assert np.abs(to_np(V) - Vo).max() < TOL_V
+
+
+def test_ra_labels_and_projection(hjb, orc):
+    """RA on the coarse grid (Sec. 3) and the projection (Sec. 4): coarse
+    labels bit-exact except near-threshold decisions; the fine mask is the
+    projection of the coarse labels (integer, exact)."""
+    d = S.c2(n=129, ntargets=6, stride=8)
+    po = oracle_problem(orc, d)
+    stride = (8, 8)
+    delta = 0.12
+    Vaux_o, lab_o, _ = orc.ra(po, stride, delta, tol=1e-11)
+    p = gpu_problem(hjb, d)
+    fine, coarse, aux, st = hjb.subdomains(p, stride, delta=delta, want_aux=True)
+    coarse = to_np(coarse).astype(np.uint32)
+    fine = to_np(fine).astype(np.uint32)
+    aux = to_np(aux).reshape(Vaux_o.shape)
+    assert np.abs(aux - Vaux_o).max() < TOL_V
+    vmin = Vaux_o.min(0)
+    diff = coarse ^ lab_o
+    near = np.zeros_like(diff, dtype=bool)
+    for k in range(d["ntargets"]):
+        close = np.abs(np.abs(Vaux_o[k] - vmin) - delta) <= TOL_V
+        near |= close & (((diff >> k) & 1) == 1)
+    bad = (diff != 0) & ~near
+    assert bad.sum() == 0
+    assert np.array_equal(fine, orc.project(po, stride, coarse))
+    assert st["labelled"] == sum(int(((fine >> k) & 1).sum()) for k in range(6))
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_decomposed_matches_oracle_isa(hjb, orc, which):
+    if which == "c1":
+        d = S.c1(n=81)
+        stride = (4, 4)
+    else:
+        d = S.c2(n=129, ntargets=6, stride=8)
+        stride = (8, 8)
+    po = oracle_problem(orc, d)
+    _, lab_o, _ = orc.ra(po, stride, 0.15, tol=1e-11)
+    fine = orc.project(po, stride, lab_o)
+    Vbar_o, unc, _, _ = orc.isa(po, fine, tol=1e-11, nthreads=8)
+    p = gpu_problem(hjb, d)
+    import torch
+    fm = torch.as_tensor(fine.astype(np.int32)).cuda()
+    Vbar, per, tot = hjb.solve_decomposed(p, fm)
+    assert np.abs(to_np(Vbar) - Vbar_o).max() < TOL_V
+    assert tot["converged"] == 1
+    # host mask path
+    Vbar_h, _, _ = hjb.solve_decomposed(p, fine)
+    assert np.array_equal(to_np(Vbar_h), to_np(Vbar))
+
+
+def test_batch_uneven(hjb, orc):
+    sides = [64, 97, 130, 71]
+    ds = [S.c4_problem(i, n) for i, n in enumerate(sides)]
+    ps = [gpu_problem(hjb, d) for d in ds]
+    Vs, sts = hjb.solve_batch(ps)
+    for d, V, st in zip(ds, Vs, sts):
+        _, Vo = _ref(orc, d, tol=1e-11)
+        assert np.abs(to_np(V) - Vo).max() < TOL_V
+        assert st["converged"] == 1
+    # batch result equals the single solves
+    V0, _ = hjb.solve(ps[1])
+    assert np.abs(to_np(V0) - to_np(Vs[1])).max() < 1e-6
+
+
+def test_point_values(hjb, orc):
+    d = S.c1(n=51)
+    po, Vo = _ref(orc, d)
+    p = gpu_problem(hjb, d)
+    import torch
+    g = np.random.default_rng(3)
+    pts = S.f32(g.uniform(-1, 1, size=(300, 2)))
+    vals_o, gr_o = orc.points(po, Vo, pts)
+    vals, gr = hjb.point_values(p, torch.as_tensor(Vo.astype(np.float32)).cuda(),
+                                torch.as_tensor(pts.astype(np.float32)).cuda())
+    assert np.abs(to_np(vals) - vals_o).max() < 1e-5
+    assert np.abs(to_np(gr) - gr_o).max() < 1e-6
+
+
+def test_adjoint_gradient(hjb, orc):
+    """hjb_backward against the FP64 adjoint of the oracle (1e-3 relative),
+    with both solves from the same seeded inputs."""
+    n, A = 65, 16
+    d = S.c5(n=n, A=A, ntargets=3, P=256)
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-14, nthreads=8)
+    pol, _ = orc.policy(po, Vo)
+    vals, gV = orc.points(po, Vo, d["points"])
+    lam, _, _ = orc.adjoint(po, pol, gV, tol=1e-14)
+    gt_o, gc_o = orc.grad(po, Vo, pol, lam)
+    import torch
+    p = gpu_problem(hjb, d)
+    V, _ = hjb.solve(p)
+    pts = torch.as_tensor(d["points"].astype(np.float32)).cuda()
+    _, gV_gpu = hjb.point_values(p, V, pts)
+    gt, st = hjb.backward(p, V, gV_gpu, wrt=0, tol=1e-9)
+    gc, _ = hjb.backward(p, V, gV_gpu, wrt=1, tol=1e-9)
+    rel_t = np.abs(to_np(gt) - gt_o).max() / np.abs(gt_o).max()
+    rel_c = np.abs(to_np(gc) - gc_o).max() / np.abs(gc_o).max()
+    assert rel_c < 1e-3, rel_c
+    assert rel_t < 1e-3, rel_t
+
+
+def test_autograd_function(hjb, orc):
+    import torch
+    n, A = 49, 16
+    d = S.c5(n=n, A=A, ntargets=2, P=128)
+    spec = dict(shape=d["shape"], lo=d["lo"], hi=d["hi"], controls=d["controls"],
+                labels=torch.as_tensor(d["labels"]).cuda(), h=d["h"], n_targets=2)
+    theta = torch.as_tensor(d["log_speed"].astype(np.float32)).cuda().requires_grad_(True)
+    v = hjb.HJBSolve.apply(theta, spec)
+    prob = hjb.Problem(log_speed=theta.detach(), **spec)
+    loss = hjb.point_loss(v, prob, torch.as_tensor(d["points"].astype(np.float32)).cuda())
+    loss.backward()
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-14)
+    pol, _ = orc.policy(po, Vo)
+    _, gV = orc.points(po, Vo, d["points"])
+    lam, _, _ = orc.adjoint(po, pol, gV, tol=1e-14)
+    gt_o, _ = orc.grad(po, Vo, pol, lam)
+    g = theta.grad.detach().cpu().numpy().reshape(-1)
+    assert np.abs(g - gt_o).max() / np.abs(gt_o).max() < 1e-3

@@ -1,0 +1,140 @@
+"""Host-side checks that need no GPU: the C library builds, loads and exports
+every entry point declared in include/hjb.h; descriptor validation; the
+seeded inputs; the separation of the oracle from the library; the
+multi-rank aggregation of the benchmark (gloo, world size 2)."""
+import ctypes as C
+import os
+import re
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hjb.h")).read()
+    return re.findall(r"^(?:int|const char \*)\s*(hjb_\w+)\(", src, flags=re.M)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1405_3521_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = set(_declared())
+    for n in ["hjb_create", "hjb_destroy", "hjb_solve", "hjb_subdomains", "hjb_solve_decomposed",
+              "hjb_solve_batch", "hjb_backward", "hjb_point_values", "hjb_last_error",
+              "hjb_version"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = C.CDLL(libpath)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True).stdout
+    for name in _declared():
+        assert re.search(r" T %s$" % name, out, flags=re.M), name
+
+
+def test_create_validates_without_touching_the_gpu(libpath):
+    import paper_1405_3521_gb300 as hjb
+    from paper_1405_3521_gb300 import _capi
+    L = _capi.lib()
+    g = _capi.hjb_grid()
+    g.ndim = 4
+    dy, co, di, ct, tg = (_capi.hjb_dynamics(), _capi.hjb_cost(), _capi.hjb_discount(),
+                          _capi.hjb_controls(), _capi.hjb_target())
+    h = C.c_void_p()
+    rc = L.hjb_create(C.byref(g), C.byref(dy), C.byref(co), C.byref(di), C.byref(ct), C.byref(tg),
+                      C.byref(h))
+    assert rc == _capi.HJB_ERR_INVALID_ARG
+    assert b"ndim" in L.hjb_last_error()
+    # a valid grid with a bad control set
+    lab = np.zeros(16, dtype=np.uint8)
+    with pytest.raises(hjb.HJBError):
+        hjb.Problem((4, 4), (0, 0), (1, 1), np.full((2, 2), np.nan, np.float32), lab, 0.1,
+                    n_targets=1)
+    with pytest.raises(hjb.HJBError):
+        hjb.Problem((4, 4), (0, 0), (1, 1), S.circle_controls(4), lab, -0.1, n_targets=1)
+    with pytest.raises(hjb.HJBError):
+        hjb.Problem((4, 4), (0, 0), (1, 1), S.circle_controls(4), lab, 0.1, n_targets=40)
+    p = hjb.Problem((4, 4), (0, 0), (1, 1), S.circle_controls(4), lab, 0.1, n_targets=1)
+    p.close()
+    assert L.hjb_destroy(None) == 0
+
+
+def test_package_never_reaches_the_oracle():
+    """The library path and the oracle share no code and the package never
+    imports, loads or runs anything under oracle/."""
+    pkg = os.path.join(ROOT, "paper_1405_3521_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\boracle\b|ohjb_|liboracle", txt), f
+    src = open(os.path.join(ROOT, "oracle", "hjb_oracle.c")).read()
+    assert "hjb_internal" not in src and "include/hjb.h" not in src
+
+
+def test_synthetic_inputs_are_seeded_and_shaped():
+    d1, d2 = S.c2(n=65), S.c2(n=65)
+    assert np.array_equal(d1["speed"], d2["speed"])
+    assert d1["speed"].min() >= 0.5 - 1e-6 and d1["speed"].max() <= 1.5 + 1e-6
+    c = d1["current"]
+    assert np.sqrt((c ** 2).sum(-1)).max() <= 0.4 + 1e-6
+    cen = d1["centers"]
+    for i in range(len(cen)):
+        for j in range(i):
+            assert np.hypot(*(cen[i] - cen[j])) >= 0.3
+    assert set(np.unique(d1["labels"])) <= set(range(17))
+    # the current is divergence-free (analytic curl of a stream function)
+    X, Y = S.mesh2(257, 257)
+    cf = S.current_field(S.rng("current", 2), X, Y)
+    h = 2.0 / 256
+    div = np.gradient(cf[..., 0], h, axis=1) + np.gradient(cf[..., 1], h, axis=0)
+    assert np.abs(div[2:-2, 2:-2]).max() < 0.05 * np.abs(cf).max() / h * h * 50
+    sides = S.c4_sides()
+    assert len(sides) == 512 and sides.min() >= 64 and sides.max() <= 512
+    th = S.grf_logspeed(S.rng("theta", 1), 65)
+    assert abs(th.min() - np.log(0.5)) < 1e-12 and abs(th.max() - np.log(1.5)) < 1e-12
+
+
+def _agg_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import bench
+    ms, total = bench.aggregate(step_ms=10.0 + rank, units_per_rank=1000.0, dist=dist,
+                                device="cpu")
+    q.put((rank, ms, total))
+    dist.destroy_process_group()
+
+
+def test_bench_aggregation_two_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_agg_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, ms, total in res:
+        assert ms == 11.0  # the slowest rank sets the time
+        assert abs(total - 2000.0 / 11.0e-3) < 1e-6 * total  # units of all ranks / that time
