@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1025, help="grid side (default: the 1025^2 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile", choices=["full", "decomposed", "ra"], default=None,
+                    help="run one solve of that path (after one warm-up) for a profiler; "
+                         "prints per-solve statistics instead of the JSON line")
     return ap.parse_args()
 
 
@@ -242,6 +245,23 @@ def main():
         fine, coarse, _, rst = hjb.subdomains(prob, stride, delta=-1.0, C_=0.0, M=-1.0)
         Vbar, per, tot = hjb.solve_decomposed(prob, fine)
         return Vbar, fine, rst, tot
+
+    if args.profile:
+        for rep in range(2):
+            if args.profile == "full":
+                _, st = hjb.solve(p)
+                info = st
+            else:
+                fine, _, _, rst = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
+                info = rst
+                if args.profile == "decomposed":
+                    _, per, tot = hjb.solve_decomposed(p, fine)
+                    f = fine.cpu().numpy().astype(np.uint32)
+                    info = {"total": tot, "per": [(s_["iterations"], int(((f >> k) & 1).sum()))
+                                                  for k, s_ in enumerate(per)]}
+            torch.cuda.synchronize()
+        print(json.dumps(info))
+        return
 
     # full-domain reference solve on the same GPU (sweeps to the same stopping rule)
     for _ in range(max(1, args.warmup)):

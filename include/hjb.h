@@ -156,7 +156,8 @@ typedef struct {
 /* Statistics of one solve (per problem or per sub-domain). */
 typedef struct {
     int iterations;        /* applications of T */
-    int converged;         /* 1 if the residual reached tol */
+    int converged;         /* 1: the residual reached tol; 2: it stopped decreasing at the
+                              FP32 rounding floor (accepted); 0: not converged */
     long long node_updates;/* evaluations of T at free nodes (all controls) */
     double final_residual; /* last ||V^{n+1} - V^n||_inf */
     double ms;             /* device time of the call, milliseconds */

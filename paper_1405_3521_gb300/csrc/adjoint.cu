@@ -185,12 +185,25 @@ __global__ void adj_resid(const __grid_constant__ AdjArgs A) {
         ctl->final_res = res;
         ctl->parity = par ^ 1;
         ctl->done_ctas = 0u;
+        // stopping: residual <= tol (1); or no decrease over 64 iterations,
+        // i.e. the FP32 rounding floor of the atomic accumulation, after at
+        // least a 1e3-fold reduction (2); otherwise the iteration cap (3)
+        if (ctl->iters == 1) ctl->first_res = res;
+        if (res < ctl->best_res) {
+            ctl->best_res = res;
+            ctl->stall = 0;
+        } else {
+            ctl->stall += 1;
+        }
         int go = 1;
         if (res <= ctl->tol) {
             ctl->converged = 1;
             go = 0;
+        } else if (ctl->stall >= 64) {
+            ctl->converged = ctl->best_res <= 1e-3f * ctl->first_res ? 2 : 3;
+            go = 0;
         } else if (ctl->iters >= ctl->max_iters) {
-            ctl->converged = 2;
+            ctl->converged = 3;
             go = 0;
         }
         __threadfence();
@@ -221,6 +234,9 @@ __global__ void adj_init_kernel(const float *g, float *L0, float *L1, long long 
         ctl->tol = tol;
         ctl->max_iters = max_iters;
         ctl->error = 0;
+        ctl->best_res = INFINITY;
+        ctl->first_res = INFINITY;
+        ctl->stall = 0;
     }
 }
 

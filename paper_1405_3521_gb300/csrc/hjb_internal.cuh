@@ -198,7 +198,10 @@ struct AdjCtl {
     float tol;
     int max_iters;
     int error;
-    int pad_[7];
+    float best_res;
+    float first_res;
+    int stall;
+    int pad_[4];
 };
 
 // pi_i = argmin_j I[V](foot_j) (lowest index on ties), -1 on targets, -2

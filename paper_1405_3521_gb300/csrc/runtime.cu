@@ -620,7 +620,7 @@ void fill_stats(hjb_stats *s, const SlotState &st) {
     if (!s) return;
     std::memset(s, 0, sizeof *s);
     s->iterations = st.iters;
-    s->converged = st.converged ? 1 : 0;
+    s->converged = st.converged;
     s->node_updates = static_cast<long long>(st.updates);
     s->final_residual = st.final_res;
 }
@@ -1284,7 +1284,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     if (stats) {
         std::memset(stats, 0, sizeof *stats);
         stats->iterations = hc.iters;
-        stats->converged = hc.converged == 1;
+        stats->converged = (hc.converged == 1 || hc.converged == 2) ? hc.converged : 0;
         stats->final_residual = hc.final_res;
         stats->node_updates = static_cast<long long>(hc.iters) * N;
         stats->ties = ties;
@@ -1293,7 +1293,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
         cudaEventElapsedTime(&ms, R.ev0, R.ev1);
         stats->ms = ms;
     }
-    if (hc.converged != 1)
+    if (hc.converged != 1 && hc.converged != 2)
         return fail(HJB_ERR_NOT_CONVERGED, "adjoint not converged after %d iterations (residual %g)",
                     hc.iters, hc.final_res);
     return HJB_OK;
