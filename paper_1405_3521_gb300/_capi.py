@@ -12,7 +12,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libhjb.so")
+# HJB_LIBRARY may point at another build of the same library (for A/B
+# comparisons of compile-time tuning); the default is the in-tree build.
+LIB_PATH = os.environ.get("HJB_LIBRARY") or os.path.join(_HERE, "_build", "libhjb.so")
 
 HJB_OK = 0
 HJB_ERR_INVALID_ARG = -1

@@ -28,10 +28,14 @@ constexpr unsigned long long WAIT_NS = 2000000000ull;
 // Discrete control set, passed by value in the kernel parameters so that a
 // fully unrolled loop reads the components as constant-bank operands.
 struct ControlTable {
+    float2 a2[MAX_CTRL];  // (ax, ay) pairs for the packed FP32x2 path
     float ax[MAX_CTRL];
     float ay[MAX_CTRL];
     int count;
 };
+// Shared-memory pair layout of the 2D sweep: row r, column c holds
+// (V[r][c], V[r][c+1]) as a float2; rows are PW float2 (512 bytes) apart.
+constexpr int PW = 64;
 
 // One independent fixed-point problem ("slot") of a launch: the full grid,
 // an auxiliary problem of the reconstruction, a sub-domain of the decomposed

@@ -443,6 +443,7 @@ hjbk::ControlTable control_table(const hjb_problem *P) {
     for (int j = 0; j < P->na; ++j) {
         c.ax[j] = P->ax[j];
         c.ay[j] = P->ay[j];
+        c.a2[j] = make_float2(P->ax[j], P->ay[j]);
     }
     return c;
 }

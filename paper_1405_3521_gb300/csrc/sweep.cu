@@ -14,17 +14,24 @@
 //  * each tile of V plus its interpolation halo is staged in shared memory by
 //    a TMA tensor load (cp.async.bulk.tensor) completing on an mbarrier, with
 //    the next item's tile prefetched while the current one is computed;
-//  * per node, the foot of every control is located with two FP32 adds
+//  * per node, the foot of every control is located with packed FP32x2 adds
 //    against a 2^23 magic constant (cell index and fraction without
-//    float-to-int conversions), and interpolated with a monotone two-product
-//    lerp, so that in the W = l/lambda - V form the FP32 iteration is itself
-//    monotone and ends at an exact FP32 fixed point;
+//    float-to-int conversions), the four corner values come from two 64-bit
+//    shared loads of a (V[c], V[c+1]) pair layout addressed with shifts, and
+//    the interpolation uses a monotone two-product lerp, so that in the
+//    W = l/lambda - V form the FP32 iteration is itself monotone and ends at
+//    an exact FP32 fixed point;
 //  * feet are tested against the box only in tiles that touch the boundary.
 #include <math.h>
 
 #include "hjb_internal.cuh"
 
 using namespace hjbk;
+
+// Resident CTAs per SM the 2D sweep is compiled for (register budget).
+#ifndef HJB_SWEEP2D_MINB
+#define HJB_SWEEP2D_MINB 8
+#endif
 
 namespace {
 
@@ -117,28 +124,26 @@ constexpr float MAGIC = 8388607.5f;
 constexpr float TWO23 = 8388608.0f;
 constexpr int TWO23_BITS = 0x4B000000;
 
-// Bilinear interpolation in a shared-memory tile with row width TW.
-// (px, py) are tile-local coordinates; py carries a +1 shift so that it is
-// >= 1/2 for every foot (the row index is corrected below).  The lerp uses
-// the two-product form (1-f) a + f b, which is monotone in a and b under
-// FP32 rounding.
-__device__ __forceinline__ float q1_tile(const float *T, float px, float py) {
-    const float mx = px + MAGIC;
-    const float my = py + MAGIC;
-    const float kx = mx - TWO23;
-    const float ky = my - TWO23;
-    const float fx = px - kx;
-    const float fy = py - ky;
-    const float ex = 1.0f - fx;
-    const float ey = 1.0f - fy;
-    const int idx = (__float_as_int(my) - (TWO23_BITS + 1)) * TW + (__float_as_int(mx) - TWO23_BITS);
-    const float v00 = T[idx];
-    const float v10 = T[idx + 1];
-    const float v01 = T[idx + TW];
-    const float v11 = T[idx + TW + 1];
-    const float a = fmaf(fx, v10, ex * v00);
-    const float b = fmaf(fx, v11, ex * v01);
-    return fmaf(fy, b, ey * a);
+// Bilinear interpolation of the pair layout at the tile-local foot
+// P2 = (px, py) (py carries a +1 row shift so that it is >= 1/2).  The
+// foot arithmetic runs on packed FP32x2 instructions; K is the shared
+// address of the pair array minus the magic-constant bias, so that the byte
+// address of pair (ky, kx) is (bits(my) << 9) + (bits(mx) << 3) + K.  The
+// lerps use the two-product form (1-f) a + f b, which is monotone in a and b
+// under FP32 rounding.
+__device__ __forceinline__ float q1_pairs(float2 P2, uint32_t K) {
+    const float2 M2 = __fadd2_rn(P2, make_float2(MAGIC, MAGIC));
+    const float2 Kn = __ffma2_rn(M2, make_float2(-1.0f, -1.0f), make_float2(TWO23, TWO23));
+    const float2 F2 = __fadd2_rn(P2, Kn);  // (fx, fy) = p - k
+    const float2 E2 = __ffma2_rn(F2, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+    const uint32_t addr = (__float_as_uint(M2.y) << 9) + (__float_as_uint(M2.x) << 3) + K;
+    float lo0, lo1, hi0, hi1;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(lo0), "=f"(lo1) : "r"(addr));
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+512];" : "=f"(hi0), "=f"(hi1) : "r"(addr));
+    // lo = (v00, v10), hi = (v01, v11): lerp in y, then in x
+    const float a = fmaf(F2.y, hi0, E2.y * lo0);
+    const float b = fmaf(F2.y, hi1, E2.y * lo1);
+    return fmaf(F2.x, b, E2.x * a);
 }
 
 template <bool WFORM>
@@ -147,25 +152,18 @@ __device__ __forceinline__ float pick(float best, float q) {
 }
 
 // Evaluation of all controls at one node of a tile that does not touch the
-// box boundary (no foot can leave the box).
+// box boundary (no foot can leave the box).  S2 = (s hx, s hy), B2 = the
+// node's tile-local position plus the current's displacement.
 template <int NA, bool WFORM>
-__device__ __forceinline__ float controls_interior(const ControlTable &C, const float *T, float sx,
-                                                   float sy, float bx, float by, float best) {
+__device__ __forceinline__ float controls_interior(const ControlTable &C, uint32_t K, float2 S2,
+                                                   float2 B2, float best) {
     if constexpr (NA > 0) {
 #pragma unroll
-        for (int j = 0; j < NA; ++j) {
-            const float px = fmaf(sx, C.ax[j], bx);
-            const float py = fmaf(sy, C.ay[j], by);
-            best = pick<WFORM>(best, q1_tile(T, px, py));
-        }
+        for (int j = 0; j < NA; ++j) best = pick<WFORM>(best, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
     } else {
         const int na = C.count;
 #pragma unroll 4
-        for (int j = 0; j < na; ++j) {
-            const float px = fmaf(sx, C.ax[j], bx);
-            const float py = fmaf(sy, C.ay[j], by);
-            best = pick<WFORM>(best, q1_tile(T, px, py));
-        }
+        for (int j = 0; j < na; ++j) best = pick<WFORM>(best, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
     }
     return best;
 }
@@ -178,32 +176,29 @@ struct EdgeBounds {
 };
 
 template <bool WFORM>
-__device__ __forceinline__ float one_control_edge(const float *T, float ox, float oy,
-                                                  const EdgeBounds &eb, float basex, float basey,
-                                                  float vout, float best) {
-    const bool out = (ox < eb.lox - 1e-6f) | (ox > eb.hix + 1e-6f) | (oy < eb.loy - 1e-6f) |
-                     (oy > eb.hiy + 1e-6f);
-    ox = fminf(fmaxf(ox, eb.lox), eb.hix);
-    oy = fminf(fmaxf(oy, eb.loy), eb.hiy);
-    const float q = q1_tile(T, basex + ox, basey + oy);
+__device__ __forceinline__ float one_control_edge(uint32_t K, float2 O2, const EdgeBounds &eb,
+                                                  float2 BASE2, float vout, float best) {
+    const bool out = (O2.x < eb.lox - 1e-6f) | (O2.x > eb.hix + 1e-6f) | (O2.y < eb.loy - 1e-6f) |
+                     (O2.y > eb.hiy + 1e-6f);
+    O2.x = fminf(fmaxf(O2.x, eb.lox), eb.hix);
+    O2.y = fminf(fmaxf(O2.y, eb.loy), eb.hiy);
+    const float q = q1_pairs(__fadd2_rn(O2, BASE2), K);
     return pick<WFORM>(best, out ? vout : q);
 }
 
 template <int NA, bool WFORM>
-__device__ __forceinline__ float controls_edge(const ControlTable &C, const float *T, float sx,
-                                               float sy, float ox0, float oy0, const EdgeBounds &eb,
-                                               float basex, float basey, float vout, float best) {
+__device__ __forceinline__ float controls_edge(const ControlTable &C, uint32_t K, float2 S2,
+                                               float2 O02, const EdgeBounds &eb, float2 BASE2,
+                                               float vout, float best) {
     if constexpr (NA > 0) {
 #pragma unroll
         for (int j = 0; j < NA; ++j)
-            best = one_control_edge<WFORM>(T, fmaf(sx, C.ax[j], ox0), fmaf(sy, C.ay[j], oy0), eb,
-                                           basex, basey, vout, best);
+            best = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2, vout, best);
     } else {
         const int na = C.count;
 #pragma unroll 4
         for (int j = 0; j < na; ++j)
-            best = one_control_edge<WFORM>(T, fmaf(sx, C.ax[j], ox0), fmaf(sy, C.ay[j], oy0), eb,
-                                           basex, basey, vout, best);
+            best = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2, vout, best);
     }
     return best;
 }
@@ -363,10 +358,11 @@ __device__ __forceinline__ void cta_done(const SweepArgs &args, bool failed) {
 // 2D sweep: f = s(x) a + c(x).  Tile 32 x 8, halo H (cells) in x and y.
 
 template <int NA, bool WFORM, int H>
-__global__ void __launch_bounds__(THREADS) sweep2d_kernel(const __grid_constant__ SweepArgs args) {
+__global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(const __grid_constant__ SweepArgs args) {
     constexpr int ROWS = TY + 2 * H;
     constexpr int TILE = ROWS * TW;
     __shared__ alignas(128) float s_tile[2][TILE];
+    __shared__ alignas(16) float2 s_pair[ROWS * PW];
     __shared__ alignas(8) uint64_t s_bar[2];
     __shared__ int s_item[2][2];
     __shared__ float s_red[THREADS / 32];
@@ -378,6 +374,10 @@ __global__ void __launch_bounds__(THREADS) sweep2d_kernel(const __grid_constant_
     const int src = static_cast<int>(sweep & 1u), dst = src ^ 1;
     const int nitems = ctl->total_items;
     const int nact = ctl->nactive;
+    // pair (ky, kx) sits at byte (ky - 1) * 512 + kx * 8 of s_pair, with
+    // kx = bits(mx) - 2^23 bits and ky = bits(my) - 2^23 bits (see q1_pairs)
+    const uint32_t K = smem_u32(s_pair) - (static_cast<uint32_t>(TWO23_BITS) << 9) -
+                       (static_cast<uint32_t>(TWO23_BITS) << 3) - 512u;
 
     auto issue = [&](int v, int b) {
         int slot, local;
@@ -412,15 +412,21 @@ __global__ void __launch_bounds__(THREADS) sweep2d_kernel(const __grid_constant_
             if (vn < nitems) mbar_wait_bounded(&s_bar[b ^ 1], ((it + 1) >> 1) & 1);
             break;
         }
+        // pair layout: (raw[r][c], raw[r][c+1]) for the TW-1 columns a foot can use
+        const float *T = s_tile[b];
+        for (int i = tid; i < ROWS * (TW - 1); i += THREADS) {
+            const int r = i / (TW - 1), c = i - r * (TW - 1);
+            s_pair[r * PW + c] = make_float2(T[r * TW + c], T[r * TW + c + 1]);
+        }
         const int slot = s_item[b][0], tile = s_item[b][1];
         const SlotDesc &S = args.slots[slot];
         const int nx = S.nx, ny = S.ny;
         const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
         const int gx = tx * TX + lx, gy = ty * TY + ly;
-        const float *T = s_tile[b];
         const float vold = T[(ly + H) * TW + lx + XPAD];
         const long long gi = static_cast<long long>(gy) * nx + gx;
         const bool isfree = (gx < nx) && (gy < ny) && node_class(S, gi) == CLS_FREE;
+        __syncthreads();
         float vnew = vold;
         if (isfree) {
             const float s = S.speed ? S.speed[gi] : 1.0f;
@@ -430,24 +436,22 @@ __global__ void __launch_bounds__(THREADS) sweep2d_kernel(const __grid_constant_
                 cx = c.x;
                 cy = c.y;
             }
-            const float sx = s * S.hx, sy = s * S.hy;
-            const float ox0 = cx * S.hx, oy0 = cy * S.hy;
-            const float basex = static_cast<float>(lx + XPAD);
-            const float basey = static_cast<float>(ly + H + 1);
+            const float2 S2 = make_float2(s * S.hx, s * S.hy);
+            const float2 O02 = make_float2(cx * S.hx, cy * S.hy);
+            const float2 BASE2 = make_float2(static_cast<float>(lx + XPAD),
+                                             static_cast<float>(ly + H + 1));
             const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
                                   (ty * TY >= H) && (ty * TY + TY - 1 + H <= ny - 1);
             float best = WFORM ? -INFINITY : INFINITY;
             if (interior) {
-                best = controls_interior<NA, WFORM>(args.ctrl, T, sx, sy, basex + ox0, basey + oy0,
-                                                    best);
+                best = controls_interior<NA, WFORM>(args.ctrl, K, S2, __fadd2_rn(BASE2, O02), best);
             } else {
                 EdgeBounds eb;
                 eb.lox = -static_cast<float>(gx);
                 eb.hix = static_cast<float>(nx - 1 - gx);
                 eb.loy = -static_cast<float>(gy);
                 eb.hiy = static_cast<float>(ny - 1 - gy);
-                best = controls_edge<NA, WFORM>(args.ctrl, T, sx, sy, ox0, oy0, eb, basex, basey,
-                                                S.vout, best);
+                best = controls_edge<NA, WFORM>(args.ctrl, K, S2, O02, eb, BASE2, S.vout, best);
             }
             if (WFORM)
                 vnew = S.beta * best;
