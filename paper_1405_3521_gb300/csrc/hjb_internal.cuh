@@ -48,11 +48,12 @@ struct alignas(128) SlotDesc {
     const float *cost;          // node field l (or null: constant)
     const uint8_t *labels;      // target labels [N]
     const uint32_t *mask;       // sub-domain bitmask [N] (or null)
-    const int *tile_list;       // tiles of this slot (or null: all tiles)
+    const uint32_t *tile_bits;  // per-tile OR of the sub-domain bits (masked slots), or null
     const float2 *trig;         // Dubins: per heading layer (v h cos/dx, v h sin/dy)
     long long zstride;          // floats between layers of V
     int nx, ny, nz, pitch;
-    int tiles_x, tiles_y, tiles_z, ntiles;
+    int tiles_x, tiles_y, tiles_z, ntiles;  // ntiles = tiles_x * tiles_y * tiles_z
+    int qbase;                  // offset of this slot's tiles in the queue flag arrays
     int mask_bit, only_target;  // restricted problem / auxiliary problem selectors
     int zdup;                   // duplicated heading layers on each side (periodic z)
     int halo;                   // interpolation halo in x, y (cells)
@@ -89,15 +90,18 @@ struct Ctl {
     int total_items;
     int error;           // non-zero: a bounded wait gave up
     unsigned launches;   // sweep kernels run (including empty ones at the loop's end)
-    int pad_[2];
+    int qcount[2];       // entries of the two tile queues (parity = sweep parity)
     int act_slot[MAX_SLOTS];
-    int act_prefix[MAX_SLOTS + 1];
 };
 
+// Work queue of a sweep: the tiles whose 3x3 (3x3x3) tile neighbourhood
+// changed in the previous sweep.  Entries pack (slot << 22) | tile.
 struct SweepArgs {
     const SlotDesc *slots;
     SlotState *state;
     Ctl *ctl;
+    int *qlist[2];
+    uint8_t *qflag[2];
     int nslots;
     int use_handle;
     cudaGraphConditionalHandle handle;
@@ -126,7 +130,11 @@ int sweep_grid(const SweepKey &k);
 
 // Kernels used around the loop (see their definitions for the contracts).
 void launch_loop_init(const hjbk::SlotDesc *slots, hjbk::SlotState *state, hjbk::Ctl *ctl,
-                      int nslots, const int *ntiles_dev, cudaStream_t st);
+                      int nslots, cudaStream_t st);
+// Queue of the first sweep: every tile of every slot that holds a node of it
+// (for masked slots: tile_bits carries the slot's bit); both flag arrays set.
+void launch_queue_init(const hjbk::SlotDesc *slots, int nslots, int max_tiles, hjbk::Ctl *ctl,
+                       int *qlist0, uint8_t *qflag0, uint8_t *qflag1, cudaStream_t st);
 void launch_init_values(const hjbk::SlotDesc *slots, int nslots, int max_nodes, int wform,
                         float c_over, const float *v_init, cudaStream_t st);
 void launch_extract(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int slot,
@@ -160,11 +168,9 @@ void launch_grad_max(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, 
 // ISA step 2: fine bitmask from coarse labels through the Kuhn simplices.
 void launch_project(const GridDims &fine, const GridDims &coarse, const int stride[3],
                     const uint32_t *coarse_labels, uint32_t *fine_mask, cudaStream_t st);
-// Work lists of the decomposed solve: for every sub-domain k < m, the tiles
-// containing at least one node of it; writes slots[k].ntiles on the device.
-void launch_tile_lists(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z,
-                       const uint32_t *mask, int m, uint32_t *tile_bits, int *lists,
-                       hjbk::SlotDesc *slots, cudaStream_t st);
+// Per-tile OR of the sub-domain bits of the decomposed solve.
+void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z,
+                      const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st);
 // ISA step 4: Vbar = min over the sub-domains containing each node.
 void launch_assemble(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int m,
                      const GridDims &fine, const uint32_t *mask, int wform, float c_over,

@@ -151,13 +151,17 @@ struct OutArr {
 // One launch of the convergence loop over a set of slots.
 struct RunCtx {
     std::vector<SlotDesc> slots;
-    DevBuf d_slots, d_state, d_ctl, vbuf, h_state_pinned;
+    DevBuf d_slots, d_state, d_ctl, vbuf, h_state_pinned, qlist, qflag;
+    int qtiles = 0;  // tiles of all slots (queue capacity)
+    int max_tiles = 0;
     SlotState *h_state = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     hjbh::SweepKey key{-1, -1, -1, -1};
     int spb = 0;
     const void *graph_slots = nullptr;
+    const void *graph_q = nullptr;
+    const void *graph_f = nullptr;
     int graph_nslots = -1;
     hjbk::ControlTable ctrl_in_graph;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -171,6 +175,8 @@ struct RunCtx {
         d_state.release();
         d_ctl.release();
         vbuf.release();
+        qlist.release();
+        qflag.release();
         if (h_state) cudaFreeHost(h_state);
         h_state = nullptr;
         if (ev0) cudaEventDestroy(ev0);
@@ -195,7 +201,7 @@ struct hjb_problem {
     DevBuf speed_exp, trig;
     // coarse problem of the reconstruction
     DevBuf c_speed, c_current, c_cost, c_labels, c_trig, c_mask, c_vstage, c_grad;
-    DevBuf tile_bits, tile_lists, fine_mask_dev, scratch_u64;
+    DevBuf tile_bits, fine_mask_dev, scratch_u64;
     DevBuf out_stage, out_stage2, out_stage3, in_stage;
     RunCtx full, ra, dec;
     RunCtx *batch = nullptr;
@@ -376,6 +382,8 @@ void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &
     S.tiles_y = (g.ny + hjbk::TY - 1) / hjbk::TY;
     S.tiles_z = P->grid.ndim > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
     S.ntiles = S.tiles_x * S.tiles_y * S.tiles_z;
+    S.tile_bits = nullptr;
+    S.qbase = 0;
     S.halo = halo;
     S.hx = static_cast<float>(h / dx[0]);
     S.hy = static_cast<float>(h / dx[1]);
@@ -390,7 +398,6 @@ void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &
     S.mask = nullptr;
     S.mask_bit = 0;
     S.only_target = 0;
-    S.tile_list = nullptr;
     S.trig = nullptr;
     if (wform) {
         S.vout = static_cast<float>(c - P->value_out);
@@ -451,6 +458,19 @@ hjbk::ControlTable control_table(const hjb_problem *P) {
 // Allocate iteration buffers for the slots (laid out back to back, each
 // 256-byte aligned) and encode their TMA maps.
 int alloc_slot_buffers(RunCtx &R, int ndim, int halo) {
+    // tile queues: one flag byte per tile per parity, lists of packed items
+    int qt = 0, mt = 0;
+    for (SlotDesc &S : R.slots) {
+        S.qbase = qt;
+        qt += S.ntiles;
+        mt = S.ntiles > mt ? S.ntiles : mt;
+    }
+    if (qt >= (1 << 30)) return fail(HJB_ERR_INVALID_ARG, "too many tiles in one launch");
+    R.qtiles = qt;
+    R.max_tiles = mt;
+    const size_t fb = (static_cast<size_t>(qt) + 3) / 4 * 4;
+    TRY(R.qlist.ensure(2 * static_cast<size_t>(qt) * sizeof(int)));
+    TRY(R.qflag.ensure(2 * fb));
     size_t total = 0;
     std::vector<size_t> off(R.slots.size());
     for (size_t i = 0; i < R.slots.size(); ++i) {
@@ -471,6 +491,14 @@ int alloc_slot_buffers(RunCtx &R, int ndim, int halo) {
     return HJB_OK;
 }
 
+void set_queue_args(const RunCtx &R, hjbk::SweepArgs &a) {
+    const size_t fb = (static_cast<size_t>(R.qtiles) + 3) / 4 * 4;
+    a.qlist[0] = R.qlist.as<int>();
+    a.qlist[1] = R.qlist.as<int>() + R.qtiles;
+    a.qflag[0] = R.qflag.as<uint8_t>();
+    a.qflag[1] = R.qflag.as<uint8_t>() + fb;
+}
+
 // Build (or reuse) the graph: a WHILE conditional node whose body runs
 // `spb` sweeps; the last CTA of each sweep sets the loop condition.
 int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlTable &ctrl,
@@ -478,6 +506,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     const int n = static_cast<int>(R.slots.size());
     if (R.exec && R.key.dubins == key.dubins && R.key.wform == key.wform && R.key.na == key.na &&
         R.key.halo == key.halo && R.spb == spb && R.graph_slots == R.d_slots.p &&
+        R.graph_q == R.qlist.p && R.graph_f == R.qflag.p &&
         R.graph_nslots == n && std::memcmp(&R.ctrl_in_graph, &ctrl, sizeof ctrl) == 0)
         return HJB_OK;
     if (R.exec) cudaGraphExecDestroy(R.exec);
@@ -506,6 +535,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     args.slots = R.d_slots.as<SlotDesc>();
     args.state = R.d_state.as<SlotState>();
     args.ctl = R.d_ctl.as<Ctl>();
+    set_queue_args(R, args);
     args.nslots = n;
     args.use_handle = 1;
     args.handle = handle;
@@ -529,6 +559,8 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     R.key = key;
     R.spb = spb;
     R.graph_slots = R.d_slots.p;
+    R.graph_q = R.qlist.p;
+    R.graph_f = R.qflag.p;
     R.graph_nslots = n;
     R.ctrl_in_graph = ctrl;
     return HJB_OK;
@@ -559,7 +591,13 @@ int run_loop(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlT
              cudaStream_t st) {
     const int n = static_cast<int>(R.slots.size());
     hjbh::launch_loop_init(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), R.d_ctl.as<Ctl>(),
-                           n, nullptr, st);
+                           n, st);
+    {
+        hjbk::SweepArgs qa;
+        set_queue_args(R, qa);
+        hjbh::launch_queue_init(R.d_slots.as<SlotDesc>(), n, R.max_tiles, R.d_ctl.as<Ctl>(),
+                                qa.qlist[0], qa.qflag[0], qa.qflag[1], st);
+    }
     CK(cudaGetLastError());
     const float stall_tol = 8.0f * 1.1920929e-7f;
     const char *ng = std::getenv("HJB_NO_GRAPH");
@@ -573,6 +611,7 @@ int run_loop(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlT
         args.slots = R.d_slots.as<SlotDesc>();
         args.state = R.d_state.as<SlotState>();
         args.ctl = R.d_ctl.as<Ctl>();
+        set_queue_args(R, args);
         args.nslots = n;
         args.use_handle = 0;
         args.stall_tol = stall_tol;
@@ -753,7 +792,7 @@ int hjb_destroy(hjb_problem *P) {
     P->adj_v.release();
     DevBuf *bufs[] = {&P->speed_exp, &P->trig,     &P->c_speed,      &P->c_current,
                       &P->c_cost,    &P->c_labels, &P->c_trig,       &P->c_mask,
-                      &P->c_vstage,  &P->c_grad,   &P->tile_bits,    &P->tile_lists,
+                      &P->c_vstage,  &P->c_grad,   &P->tile_bits,
                       &P->fine_mask_dev, &P->scratch_u64, &P->out_stage, &P->out_stage2,
                       &P->out_stage3, &P->in_stage};
     for (DevBuf *b : bufs) b->release();
@@ -824,7 +863,7 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
     if (stats) {
         fill_stats(stats, R.h_state[0]);
         stats->ms = ms;
-        stats->launches = pr.launches + 3 + sweeps;
+        stats->launches = pr.launches + 4 + sweeps;
     }
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
     if (!R.h_state[0].converged)
@@ -974,7 +1013,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
         stats->converged = conv;
         stats->ties = static_cast<long long>(hc[0]);
         stats->labelled = static_cast<long long>(hc[1]);
-        stats->launches = pr.launches + 7 + sweeps + (ra->delta < 0 && ra->M < 0 ? 1 : 0) +
+        stats->launches = pr.launches + 8 + sweeps + (ra->delta < 0 && ra->M < 0 ? 1 : 0) +
                           (v_aux_out ? m : 0);
         float ms = 0;
         cudaEventElapsedTime(&ms, R.ev0, R.ev1);
@@ -1022,12 +1061,11 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     const int tiles_z = nd > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
     const int nt = tiles_x * tiles_y * tiles_z;
     TRY(P->tile_bits.ensure(nt * sizeof(uint32_t)));
-    TRY(P->tile_lists.ensure(static_cast<size_t>(m) * nt * sizeof(int)));
     for (int k = 0; k < m; ++k) {
         fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters);
         R.slots[k].mask = mask;
         R.slots[k].mask_bit = k;
-        R.slots[k].tile_list = P->tile_lists.as<int>() + static_cast<size_t>(k) * nt;
+        R.slots[k].tile_bits = P->tile_bits.as<uint32_t>();
         if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->trig.as<float2>();
     }
     TRY(alloc_slot_buffers(R, nd, halo));
@@ -1036,8 +1074,7 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     TRY(out.init(v_out, P->N * sizeof(float), &P->out_stage));
     const float c_over = static_cast<float>(P->l_const / P->lambda);
     CK(cudaEventRecord(R.ev0, st));
-    hjbh::launch_tile_lists(fine, tiles_x, tiles_y, tiles_z, mask, m, P->tile_bits.as<uint32_t>(),
-                            P->tile_lists.as<int>(), R.d_slots.as<SlotDesc>(), st);
+    hjbh::launch_tile_bits(fine, tiles_x, tiles_y, tiles_z, mask, P->tile_bits.as<uint32_t>(), st);
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo};
@@ -1143,7 +1180,7 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
     int err = 0;
     long long sweeps = 0;
     TRY(read_state(R, st, &err, &sweeps));
-    long long nl = 2 + sweeps + count;
+    long long nl = 3 + sweeps + count;
     for (int i = 0; i < count; ++i) nl += preps[i].launches;
     CK(cudaGetLastError());
     float ms = 0;

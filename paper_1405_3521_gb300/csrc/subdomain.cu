@@ -226,37 +226,6 @@ __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, con
     }
 }
 
-// Stream compaction of the tiles carrying bit k (one block per sub-domain):
-// lists + k * ntiles_total receives them, slots[k].ntiles their count.
-__global__ void tile_lists_kernel(int ntiles, const uint32_t *tile_bits, int *lists, SlotDesc *slots) {
-    const int k = blockIdx.x;
-    int *L = lists + static_cast<long long>(k) * ntiles;
-    __shared__ int s_w[THREADS / 32];
-    __shared__ int s_base;
-    if (threadIdx.x == 0) s_base = 0;
-    __syncthreads();
-    for (int t0 = 0; t0 < ntiles; t0 += THREADS) {
-        const int t = t0 + threadIdx.x;
-        const int f = (t < ntiles && ((tile_bits[t] >> k) & 1u)) ? 1 : 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int wpre = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) s_w[warp] = __popc(bal);
-        __syncthreads();
-        int off = s_base;
-        for (int w = 0; w < warp; ++w) off += s_w[w];
-        if (f) L[off + wpre] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < THREADS / 32; ++w) tot += s_w[w];
-            s_base += tot;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) slots[k].ntiles = s_base;
-}
-
 // ISA step 4: Vbar(j) = min{ V_k(j) : bit k of mask[j] } (max of W in the
 // W form), value_out on nodes that belong to no sub-domain.
 __global__ void assemble_kernel(const SlotDesc *slots, const SlotState *state, int m,
@@ -355,12 +324,10 @@ void launch_project(const GridDims &fine, const GridDims &coarse, const int stri
                                                      fine_mask);
 }
 
-void launch_tile_lists(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z,
-                       const uint32_t *mask, int m, uint32_t *tile_bits, int *lists,
-                       SlotDesc *slots, cudaStream_t st) {
+void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z,
+                      const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st) {
     const int nt = tiles_x * tiles_y * tiles_z;
     tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, mask, tile_bits);
-    tile_lists_kernel<<<m, THREADS, 0, st>>>(nt, tile_bits, lists, slots);
 }
 
 void launch_assemble(const SlotDesc *slots, const SlotState *state, int m, const GridDims &fine,

@@ -9,8 +9,13 @@
 // to finish (which also drives the CUDA-graph WHILE loop around the sweep).
 //
 // Design for sm_103a:
-//  * persistent grid (SMs x resident CTAs), items = (slot, tile) pulled from a
-//    compacted list of active slots, so converged problems cost nothing;
+//  * persistent grid (SMs x resident CTAs) over a device work queue of
+//    (slot, tile) items: a tile is queued for the next sweep only when a tile
+//    of its 3x3 (3x3x3) neighbourhood changed bitwise in this sweep, since
+//    otherwise its inputs, and hence its outputs, are those of the previous
+//    sweep -- the iteration stays exactly Jacobi while quiescent regions
+//    (ahead of the front, and behind it once converged) cost nothing; tiles
+//    of converged slots drop out of the queue;
 //  * each tile of V plus its interpolation halo is staged in shared memory by
 //    a TMA tensor load (cp.async.bulk.tensor) completing on an mbarrier, with
 //    the next item's tile prefetched while the current one is computed;
@@ -203,79 +208,48 @@ __device__ __forceinline__ float controls_edge(const ControlTable &C, uint32_t K
     return best;
 }
 
-// Active item v -> (slot, index of the item inside the slot).
-__device__ __forceinline__ void map_item(const Ctl *ctl, int nact, int v, int &slot, int &local) {
-    int lo = 0, hi = nact - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ctl->act_prefix[mid] <= v)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    slot = ctl->act_slot[lo];
-    local = v - ctl->act_prefix[lo];
-}
-
-// Block-wide exclusive scan of two ints (256 threads).
-__device__ __forceinline__ void block_scan2(int a, int b, int &ea, int &eb, int &ta, int &tb,
-                                            int *sa, int *sb) {
+// Block-wide exclusive scan of an int (256 threads); returns the total.
+__device__ __forceinline__ int block_scan(int a, int &ea, int *sa) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int ia = a, ib = b;
+    int ia = a;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int xa = __shfl_up_sync(0xffffffffu, ia, o);
-        const int xb = __shfl_up_sync(0xffffffffu, ib, o);
-        if (lane >= o) {
-            ia += xa;
-            ib += xb;
-        }
+        if (lane >= o) ia += xa;
     }
-    if (lane == 31) {
-        sa[warp] = ia;
-        sb[warp] = ib;
-    }
+    if (lane == 31) sa[warp] = ia;
     __syncthreads();
     if (warp == 0) {
         int va = lane < THREADS / 32 ? sa[lane] : 0;
-        int vb = lane < THREADS / 32 ? sb[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int xa = __shfl_up_sync(0xffffffffu, va, o);
-            const int xb = __shfl_up_sync(0xffffffffu, vb, o);
-            if (lane >= o) {
-                va += xa;
-                vb += xb;
-            }
+            if (lane >= o) va += xa;
         }
-        if (lane < THREADS / 32) {
-            sa[lane] = va;
-            sb[lane] = vb;
-        }
+        if (lane < THREADS / 32) sa[lane] = va;
     }
     __syncthreads();
-    const int wa = warp ? sa[warp - 1] : 0;
-    const int wb = warp ? sb[warp - 1] : 0;
-    ea = wa + ia - a;
-    eb = wb + ib - b;
-    ta = sa[THREADS / 32 - 1];
-    tb = sb[THREADS / 32 - 1];
+    ea = (warp ? sa[warp - 1] : 0) + ia - a;
+    const int total = sa[THREADS / 32 - 1];
     __syncthreads();
+    return total;
 }
 
 // Convergence step, run by the last CTA of a sweep: read and reset each
 // active slot's residual, apply the stopping rule (residual <= tol, the
-// iteration cap, or stagnation at rounding level), compact the active list
-// and set the graph loop condition.
+// iteration cap, or stagnation at rounding level), compact the active slot
+// list, empty the tile queue this sweep consumed, and set the graph loop
+// condition.
 __device__ void finish_sweep(const SweepArgs &args) {
     Ctl *ctl = args.ctl;
-    __shared__ int s_sa[THREADS / 32], s_sb[THREADS / 32];
+    __shared__ int s_sa[THREADS / 32];
     const int n = ctl->nactive;
-    const int dst_parity = static_cast<int>((ctl->sweep & 1u) ^ 1u);
+    const int p = static_cast<int>(ctl->sweep & 1u);
+    const int dst_parity = p ^ 1;
     const int err = ctl->error;
     constexpr int PER = MAX_SLOTS / THREADS;
     int sid[PER], keep[PER];
-    int cnt = 0, tiles = 0;
+    int cnt = 0;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int i = threadIdx.x * PER + k;
@@ -309,26 +283,18 @@ __device__ void finish_sweep(const SweepArgs &args) {
         if (!kp) st.done = 1;
         keep[k] = kp;
         cnt += kp;
-        tiles += kp ? S.ntiles : 0;
     }
     // every thread has read its entries of the active list before the scan's
     // barriers, so the list can be compacted in place afterwards
-    int ec, et, tc, tt;
-    block_scan2(cnt, tiles, ec, et, tc, tt, s_sa, s_sb);
+    int ec;
+    const int tc = block_scan(cnt, ec, s_sa);
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        if (keep[k]) {
-            ctl->act_slot[ec] = sid[k];
-            ctl->act_prefix[ec] = et;
-            ++ec;
-            et += args.slots[sid[k]].ntiles;
-        }
-    }
+    for (int k = 0; k < PER; ++k)
+        if (keep[k]) ctl->act_slot[ec++] = sid[k];
     __syncthreads();
     if (threadIdx.x == 0) {
-        ctl->act_prefix[tc] = tt;
         ctl->nactive = tc;
-        ctl->total_items = tt;
+        ctl->qcount[p] = 0;  // every entry of this sweep's queue was consumed
         if (n > 0) ctl->sweep += 1u;
         ctl->launches += 1u;
         ctl->done_ctas = 0u;
@@ -354,6 +320,52 @@ __device__ __forceinline__ void cta_done(const SweepArgs &args, bool failed) {
     }
 }
 
+// Tile queue of the next sweep: called by warp 0 of a CTA whose tile changed
+// (bitwise) in this sweep; lane t < NB considers neighbour t of the 3x3
+// (3x3x3) tile neighbourhood, skips tiles outside the grid or holding no node
+// of the slot, claims the neighbour's flag, and the claimed neighbours are
+// appended with one atomic per warp.  A tile none of whose neighbours
+// changed would reproduce its previous values exactly, so it is not queued.
+template <bool THREE_D>
+__device__ __forceinline__ void enqueue_neighbours(const SweepArgs &args, const SlotDesc &S,
+                                                   int slot, int tx, int ty, int tz, int p) {
+    const int lane = threadIdx.x & 31;
+    int nb = -1;
+    constexpr int NB = THREE_D ? 27 : 9;
+    if (lane < NB) {
+        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = THREE_D ? lane / 9 - 1 : 0;
+        const int x = tx + dx, y = ty + dy;
+        int z = tz + dz;
+        if (THREE_D) z = (z + S.tiles_z) % S.tiles_z;  // periodic heading
+        if (x >= 0 && x < S.tiles_x && y >= 0 && y < S.tiles_y) {
+            const int t = (z * S.tiles_y + y) * S.tiles_x + x;
+            const bool member = S.tile_bits == nullptr || ((S.tile_bits[t] >> S.mask_bit) & 1u);
+            if (member) {
+                // byte flags: claim with an atomic OR on the containing word
+                uint8_t *f = args.qflag[p ^ 1] + S.qbase + t;
+                unsigned *w = reinterpret_cast<unsigned *>(reinterpret_cast<size_t>(f) & ~size_t(3));
+                const unsigned bit = 1u << ((reinterpret_cast<size_t>(f) & 3u) * 8u);
+                if ((atomicOr(w, bit) & bit) == 0u) nb = t;
+            }
+        }
+    }
+    const unsigned need = __ballot_sync(0xffffffffu, nb >= 0);
+    if (need) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&args.ctl->qcount[p ^ 1], __popc(need));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (nb >= 0) args.qlist[p ^ 1][base + __popc(need & ((1u << lane) - 1u))] = (slot << 22) | nb;
+    }
+}
+
+// Clear this sweep's queued flag of a tile (byte flag inside a word).
+__device__ __forceinline__ void unflag(const SweepArgs &args, const SlotDesc &S, int tile, int p) {
+    uint8_t *f = args.qflag[p] + S.qbase + tile;
+    unsigned *w = reinterpret_cast<unsigned *>(reinterpret_cast<size_t>(f) & ~size_t(3));
+    const unsigned sh = static_cast<unsigned>(reinterpret_cast<size_t>(f) & 3u) * 8u;
+    atomicAnd(w, ~(0xffu << sh));
+}
+
 // --------------------------------------------------------------------------
 // 2D sweep: f = s(x) a + c(x).  Tile 32 x 8, halo H (cells) in x and y.
 
@@ -364,31 +376,36 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
     __shared__ alignas(128) float s_tile[2][TILE];
     __shared__ alignas(16) float2 s_pair[ROWS * PW];
     __shared__ alignas(8) uint64_t s_bar[2];
-    __shared__ int s_item[2][2];
+    __shared__ int s_item[2][3];
     __shared__ float s_red[THREADS / 32];
+    __shared__ int s_cnt[THREADS / 32];
 
     const Ctl *ctl = args.ctl;
     const int tid = threadIdx.x;
     const int lx = tid & 31, ly = tid >> 5;
-    const unsigned sweep = ctl->sweep;
-    const int src = static_cast<int>(sweep & 1u), dst = src ^ 1;
-    const int nitems = ctl->total_items;
-    const int nact = ctl->nactive;
+    const int p = static_cast<int>(ctl->sweep & 1u);
+    const int src = p, dst = p ^ 1;
+    const int nitems = ctl->qcount[p];
+    const int *qlist = args.qlist[p];
     // pair (ky, kx) sits at byte (ky - 1) * 512 + kx * 8 of s_pair, with
     // kx = bits(mx) - 2^23 bits and ky = bits(my) - 2^23 bits (see q1_pairs)
     const uint32_t K = smem_u32(s_pair) - (static_cast<uint32_t>(TWO23_BITS) << 9) -
                        (static_cast<uint32_t>(TWO23_BITS) << 3) - 512u;
 
+    // thread 0: stage item v into buffer b (no copy for a finished slot)
     auto issue = [&](int v, int b) {
-        int slot, local;
-        map_item(ctl, nact, v, slot, local);
+        const int e = qlist[v];
+        const int slot = e >> 22, tile = e & 0x3FFFFF;
         const SlotDesc *S = args.slots + slot;
-        const int tile = S->tile_list ? S->tile_list[local] : local;
+        const int live = args.state[slot].done ? 0 : 1;
         s_item[b][0] = slot;
         s_item[b][1] = tile;
-        const int tx = tile % S->tiles_x, ty = tile / S->tiles_x;
-        mbar_expect_tx(&s_bar[b], TILE * 4);
-        tma_load_2d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H, &s_bar[b]);
+        s_item[b][2] = live;
+        if (live) {
+            const int tx = tile % S->tiles_x, ty = tile / S->tiles_x;
+            mbar_expect_tx(&s_bar[b], TILE * 4);
+            tma_load_2d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H, &s_bar[b]);
+        }
     };
 
     if (tid == 0) {
@@ -401,15 +418,26 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
     if (tid == 0 && v < nitems) issue(v, 0);
     __syncthreads();
     bool failed = false;
+    unsigned uses[2] = {0u, 0u};  // completed TMA phases consumed per buffer
     for (int it = 0; v < nitems; ++it, v += gridDim.x) {
         const int b = it & 1;
         const int vn = v + gridDim.x;
+        const int slot = s_item[b][0], tile = s_item[b][1], live = s_item[b][2];
+        __syncthreads();  // everyone has read s_item[b]; buffer b ^ 1 is free
         if (tid == 0 && vn < nitems) issue(vn, b ^ 1);
-        const bool ok = mbar_wait_bounded(&s_bar[b], (it >> 1) & 1);
+        const SlotDesc &S = args.slots[slot];
+        if (!live) {
+            if (tid == 0) unflag(args, S, tile, p);
+            __syncthreads();  // s_item[b ^ 1] written by the issue above
+            continue;
+        }
+        const bool ok = mbar_wait_bounded(&s_bar[b], uses[b] & 1u);
+        uses[b] += 1u;
         if (!__syncthreads_and(ok)) {
             failed = true;
             // let the prefetch of the next item (if any) land before leaving
-            if (vn < nitems) mbar_wait_bounded(&s_bar[b ^ 1], ((it + 1) >> 1) & 1);
+            if (tid == 0 && vn < nitems && s_item[b ^ 1][2])
+                mbar_wait_bounded(&s_bar[b ^ 1], uses[b ^ 1] & 1u);
             break;
         }
         // pair layout: (raw[r][c], raw[r][c+1]) for the TW-1 columns a foot can use
@@ -418,8 +446,6 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
             const int r = i / (TW - 1), c = i - r * (TW - 1);
             s_pair[r * PW + c] = make_float2(T[r * TW + c], T[r * TW + c + 1]);
         }
-        const int slot = s_item[b][0], tile = s_item[b][1];
-        const SlotDesc &S = args.slots[slot];
         const int nx = S.nx, ny = S.ny;
         const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
         const int gx = tx * TX + lx, gy = ty * TY + ly;
@@ -460,16 +486,29 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
             S.V[dst][static_cast<long long>(gy) * S.pitch + gx] = vnew;
         }
         const float r = warp_max(isfree ? fabsf(vnew - vold) : 0.0f);
-        if (lx == 0) s_red[ly] = r;
-        const int cnt = __syncthreads_count(isfree);
-        if (tid == 0) {
-            float m = s_red[0];
-#pragma unroll
-            for (int w = 1; w < THREADS / 32; ++w) m = fmaxf(m, s_red[w]);
-            atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
-            atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(cnt));
+        const unsigned fm = __ballot_sync(0xffffffffu, isfree);
+        const unsigned cm = __ballot_sync(0xffffffffu, isfree && (vnew != vold));
+        if (lx == 0) {
+            s_red[ly] = r;
+            s_cnt[ly] = __popc(fm) | (cm ? 0x10000 : 0);
         }
         __syncthreads();
+        if (tid < 32) {
+            float m = 0.0f;
+            int tot = 0, chg = 0;
+#pragma unroll
+            for (int w = 0; w < THREADS / 32; ++w) {
+                m = fmaxf(m, s_red[w]);
+                tot += s_cnt[w] & 0xffff;
+                chg |= s_cnt[w] >> 16;
+            }
+            if (tid == 0) {
+                if (m > 0.0f) atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
+                atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot));
+                unflag(args, S, tile, p);
+            }
+            if (chg) enqueue_neighbours<false>(args, S, slot, tx, ty, 0, p);
+        }
     }
     cta_done(args, failed);
 }
@@ -489,31 +528,34 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
     constexpr int TILE = (TZ + 2 * HZ) * LAYER;
     __shared__ alignas(128) float s_tile[2][TILE];
     __shared__ alignas(8) uint64_t s_bar[2];
-    __shared__ int s_item[2][2];
+    __shared__ int s_item[2][3];
     __shared__ float s_red[THREADS / 32];
     __shared__ int s_cnt[THREADS / 32];
 
     const Ctl *ctl = args.ctl;
     const int tid = threadIdx.x;
     const int lx = tid & 31, ly = tid >> 5;
-    const unsigned sweep = ctl->sweep;
-    const int src = static_cast<int>(sweep & 1u), dst = src ^ 1;
-    const int nitems = ctl->total_items;
-    const int nact = ctl->nactive;
+    const int p = static_cast<int>(ctl->sweep & 1u);
+    const int src = p, dst = p ^ 1;
+    const int nitems = ctl->qcount[p];
+    const int *qlist = args.qlist[p];
 
     auto issue = [&](int v, int b) {
-        int slot, local;
-        map_item(ctl, nact, v, slot, local);
+        const int e = qlist[v];
+        const int slot = e >> 22, tile = e & 0x3FFFFF;
         const SlotDesc *S = args.slots + slot;
-        const int tile = S->tile_list ? S->tile_list[local] : local;
+        const int live = args.state[slot].done ? 0 : 1;
         s_item[b][0] = slot;
         s_item[b][1] = tile;
-        const int txy = S->tiles_x * S->tiles_y;
-        const int tz = tile / txy, rem = tile - tz * txy;
-        const int ty = rem / S->tiles_x, tx = rem - ty * S->tiles_x;
-        mbar_expect_tx(&s_bar[b], TILE * 4);
-        tma_load_3d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H, tz * TZ - HZ + S->zdup,
-                    &s_bar[b]);
+        s_item[b][2] = live;
+        if (live) {
+            const int txy = S->tiles_x * S->tiles_y;
+            const int tz = tile / txy, rem = tile - tz * txy;
+            const int ty = rem / S->tiles_x, tx = rem - ty * S->tiles_x;
+            mbar_expect_tx(&s_bar[b], TILE * 4);
+            tma_load_3d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H,
+                        tz * TZ - HZ + S->zdup, &s_bar[b]);
+        }
     };
 
     if (tid == 0) {
@@ -526,18 +568,27 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
     if (tid == 0 && v < nitems) issue(v, 0);
     __syncthreads();
     bool failed = false;
+    unsigned uses[2] = {0u, 0u};
     for (int it = 0; v < nitems; ++it, v += gridDim.x) {
         const int b = it & 1;
         const int vn = v + gridDim.x;
+        const int slot = s_item[b][0], tile = s_item[b][1], live = s_item[b][2];
+        __syncthreads();
         if (tid == 0 && vn < nitems) issue(vn, b ^ 1);
-        const bool ok = mbar_wait_bounded(&s_bar[b], (it >> 1) & 1);
+        const SlotDesc &S = args.slots[slot];
+        if (!live) {
+            if (tid == 0) unflag(args, S, tile, p);
+            __syncthreads();  // s_item[b ^ 1] written by the issue above
+            continue;
+        }
+        const bool ok = mbar_wait_bounded(&s_bar[b], uses[b] & 1u);
+        uses[b] += 1u;
         if (!__syncthreads_and(ok)) {
             failed = true;
-            if (vn < nitems) mbar_wait_bounded(&s_bar[b ^ 1], ((it + 1) >> 1) & 1);
+            if (tid == 0 && vn < nitems && s_item[b ^ 1][2])
+                mbar_wait_bounded(&s_bar[b ^ 1], uses[b ^ 1] & 1u);
             break;
         }
-        const int slot = s_item[b][0], tile = s_item[b][1];
-        const SlotDesc &S = args.slots[slot];
         const int nx = S.nx, ny = S.ny, nz = S.nz;
         const int txy = S.tiles_x * S.tiles_y;
         const int tz = tile / txy, rem = tile - tz * txy;
@@ -548,6 +599,7 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
                               (ty * TY >= H) && (ty * TY + TY - 1 + H <= ny - 1);
         float rmax = 0.0f;
         int cnt = 0;
+        bool chg = false;
 #pragma unroll 1
         for (int lz = 0; lz < TZ; ++lz) {
             const int gz = tz * TZ + lz;
@@ -616,27 +668,35 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
             if (gz >= nz - S.zdup)
                 D[static_cast<long long>(gz - nz + S.zdup) * S.zstride + row] = vnew;
             rmax = fmaxf(rmax, fabsf(vnew - vold));
+            chg |= (vnew != vold);
             ++cnt;
         }
         const float r = warp_max(rmax);
-        if (lx == 0) s_red[ly] = r;
         int c = cnt;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lx == 0) s_cnt[ly] = c;
-        __syncthreads();
-        if (tid == 0) {
-            float m = s_red[0];
-            int tot = s_cnt[0];
-#pragma unroll
-            for (int w = 1; w < THREADS / 32; ++w) {
-                m = fmaxf(m, s_red[w]);
-                tot += s_cnt[w];
-            }
-            atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
-            atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot));
+        const unsigned cm = __ballot_sync(0xffffffffu, chg);
+        if (lx == 0) {
+            s_red[ly] = r;
+            s_cnt[ly] = c | (cm ? 0x10000 : 0);
         }
         __syncthreads();
+        if (tid < 32) {
+            float m = 0.0f;
+            int tot = 0, any = 0;
+#pragma unroll
+            for (int w = 0; w < THREADS / 32; ++w) {
+                m = fmaxf(m, s_red[w]);
+                tot += s_cnt[w] & 0xffff;
+                any |= s_cnt[w] >> 16;
+            }
+            if (tid == 0) {
+                if (m > 0.0f) atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
+                atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot));
+                unflag(args, S, tile, p);
+            }
+            if (any) enqueue_neighbours<true>(args, S, slot, tx, ty, tz, p);
+        }
     }
     cta_done(args, failed);
 }
@@ -644,47 +704,52 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
 // --------------------------------------------------------------------------
 // Helpers around the loop.
 
-__global__ void loop_init_kernel(const SlotDesc *slots, SlotState *state, Ctl *ctl, int nslots) {
-    __shared__ int s_sa[THREADS / 32], s_sb[THREADS / 32];
-    constexpr int PER = MAX_SLOTS / THREADS;
-    int tiles = 0;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x * PER + k;
-        if (i < nslots) {
-            tiles += slots[i].ntiles;
-            SlotState &st = state[i];
-            st.res_bits = 0u;
-            st.iters = 0;
-            st.done = 0;
-            st.converged = 0;
-            st.final_parity = 0;
-            st.stall = 0;
-            st.best_res = INFINITY;
-            st.final_res = 0.0f;
-            st.updates = 0ull;
-            st.changed = 0ull;
-        }
-    }
-    int ec, et, tc, tt;
-    block_scan2(0, tiles, ec, et, tc, tt, s_sa, s_sb);
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x * PER + k;
-        if (i < nslots) {
-            ctl->act_slot[i] = i;
-            ctl->act_prefix[i] = et;
-            et += slots[i].ntiles;
-        }
+__global__ void loop_init_kernel(SlotState *state, Ctl *ctl, int nslots) {
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+        SlotState &st = state[i];
+        st.res_bits = 0u;
+        st.iters = 0;
+        st.done = 0;
+        st.converged = 0;
+        st.final_parity = 0;
+        st.stall = 0;
+        st.best_res = INFINITY;
+        st.final_res = 0.0f;
+        st.updates = 0ull;
+        st.changed = 0ull;
+        ctl->act_slot[i] = i;
     }
     if (threadIdx.x == 0) {
-        ctl->act_prefix[nslots] = tt;
         ctl->nactive = nslots;
-        ctl->total_items = tt;
         ctl->sweep = 0u;
         ctl->done_ctas = 0u;
         ctl->error = 0;
         ctl->launches = 0u;
+        ctl->qcount[0] = 0;
+        ctl->qcount[1] = 0;
+    }
+}
+
+// First queue: every member tile of every slot, both flag arrays written
+// (blockIdx.y = slot, threads over the slot's tiles).
+__global__ void queue_init_kernel(const SlotDesc *slots, Ctl *ctl, int *qlist0, uint8_t *qflag0,
+                                  uint8_t *qflag1) {
+    const int slot = blockIdx.y;
+    const SlotDesc &S = slots[slot];
+    const int lane = threadIdx.x & 31;
+    for (int t0 = blockIdx.x * blockDim.x; t0 < S.ntiles; t0 += gridDim.x * blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        bool member = false;
+        if (t < S.ntiles) {
+            member = S.tile_bits == nullptr || ((S.tile_bits[t] >> S.mask_bit) & 1u);
+            qflag0[S.qbase + t] = member ? 1 : 0;
+            qflag1[S.qbase + t] = 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, member);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&ctl->qcount[0], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (member) qlist0[base + __popc(m & ((1u << lane) - 1u))] = (slot << 22) | t;
     }
 }
 
@@ -786,9 +851,17 @@ int sweep_grid(const SweepKey &k) {
     return sms * per;
 }
 
-void launch_loop_init(const SlotDesc *slots, SlotState *state, Ctl *ctl, int nslots,
-                      const int * /*ntiles_dev*/, cudaStream_t st) {
-    loop_init_kernel<<<1, THREADS, 0, st>>>(slots, state, ctl, nslots);
+void launch_loop_init(const SlotDesc * /*slots*/, SlotState *state, Ctl *ctl, int nslots,
+                      cudaStream_t st) {
+    loop_init_kernel<<<1, THREADS, 0, st>>>(state, ctl, nslots);
+}
+
+void launch_queue_init(const SlotDesc *slots, int nslots, int max_tiles, Ctl *ctl, int *qlist0,
+                       uint8_t *qflag0, uint8_t *qflag1, cudaStream_t st) {
+    int bx = (max_tiles + THREADS - 1) / THREADS;
+    if (bx > 1024) bx = 1024;
+    if (bx < 1) bx = 1;
+    queue_init_kernel<<<dim3(bx, nslots), THREADS, 0, st>>>(slots, ctl, qlist0, qflag0, qflag1);
 }
 
 void launch_init_values(const SlotDesc *slots, int nslots, int max_nodes, int wform, float c_over,
