@@ -120,6 +120,8 @@ struct SweepKey {
     int wform;   // iterate on W (max form) instead of V (min form)
     int na;      // number of controls
     int halo;    // 2 or 4 (2D), 2 (3D)
+    int ty;      // tile rows: 8, 4 or 2 (2D); 8 (3D)
+    int groups;  // control groups per node: 256 / (32 ty)
 };
 
 // Returns the kernel function for a key (nullptr if unsupported) and the
@@ -169,7 +171,7 @@ void launch_grad_max(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, 
 void launch_project(const GridDims &fine, const GridDims &coarse, const int stride[3],
                     const uint32_t *coarse_labels, uint32_t *fine_mask, cudaStream_t st);
 // Per-tile OR of the sub-domain bits of the decomposed solve.
-void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z,
+void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty,
                       const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st);
 // ISA step 4: Vbar = min over the sub-domains containing each node.
 void launch_assemble(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int m,

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -157,7 +158,7 @@ struct RunCtx {
     SlotState *h_state = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    hjbh::SweepKey key{-1, -1, -1, -1};
+    hjbh::SweepKey key{-1, -1, -1, -1, -1, -1};
     int spb = 0;
     const void *graph_slots = nullptr;
     const void *graph_q = nullptr;
@@ -237,7 +238,7 @@ SlotGeo geo_of(int ndim, const int n[3], int periodic_z) {
     return g;
 }
 
-int encode_maps(SlotDesc &S, int ndim, int halo) {
+int encode_maps(SlotDesc &S, int ndim, int halo, int rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(HJB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     for (int b = 0; b < 2; ++b) {
@@ -246,7 +247,7 @@ int encode_maps(SlotDesc &S, int ndim, int halo) {
             cuuint64_t dims[2] = {static_cast<cuuint64_t>(S.nx), static_cast<cuuint64_t>(S.ny)};
             cuuint64_t strides[1] = {static_cast<cuuint64_t>(S.pitch) * 4};
             cuuint32_t box[2] = {static_cast<cuuint32_t>(hjbk::TW),
-                                 static_cast<cuuint32_t>(hjbk::TY + 2 * halo)};
+                                 static_cast<cuuint32_t>(rows + 2 * halo)};
             cuuint32_t es[2] = {1, 1};
             r = enc(&S.tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, S.V[b], dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -368,7 +369,7 @@ int halo_for(const hjb_problem *P, double max_off, double max_off_z, int *halo) 
 
 // Fill the fields of a slot that depend on the problem statement.
 void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &pr, bool wform,
-               double h, const double dx[3], int halo, double tol, int max_iters) {
+               double h, const double dx[3], int halo, double tol, int max_iters, int rows) {
     const double beta = std::exp(-P->lambda * h);
     const double gamma = -std::expm1(-P->lambda * h) / P->lambda;
     const double c = P->l_const / P->lambda;
@@ -379,7 +380,7 @@ void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &
     S.zdup = g.zdup;
     S.zstride = g.zstride;
     S.tiles_x = (g.nx + hjbk::TX - 1) / hjbk::TX;
-    S.tiles_y = (g.ny + hjbk::TY - 1) / hjbk::TY;
+    S.tiles_y = (g.ny + rows - 1) / rows;
     S.tiles_z = P->grid.ndim > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
     S.ntiles = S.tiles_x * S.tiles_y * S.tiles_z;
     S.tile_bits = nullptr;
@@ -457,7 +458,7 @@ hjbk::ControlTable control_table(const hjb_problem *P) {
 
 // Allocate iteration buffers for the slots (laid out back to back, each
 // 256-byte aligned) and encode their TMA maps.
-int alloc_slot_buffers(RunCtx &R, int ndim, int halo) {
+int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows) {
     // tile queues: one flag byte per tile per parity, lists of packed items
     int qt = 0, mt = 0;
     for (SlotDesc &S : R.slots) {
@@ -486,7 +487,7 @@ int alloc_slot_buffers(RunCtx &R, int ndim, int halo) {
         const size_t fl64 = (fl + 63) / 64 * 64;
         S.V[0] = R.vbuf.as<float>() + off[i];
         S.V[1] = R.vbuf.as<float>() + off[i] + fl64;
-        TRY(encode_maps(S, ndim, halo));
+        TRY(encode_maps(S, ndim, halo, rows));
     }
     return HJB_OK;
 }
@@ -505,7 +506,8 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
                  float stall_tol) {
     const int n = static_cast<int>(R.slots.size());
     if (R.exec && R.key.dubins == key.dubins && R.key.wform == key.wform && R.key.na == key.na &&
-        R.key.halo == key.halo && R.spb == spb && R.graph_slots == R.d_slots.p &&
+        R.key.halo == key.halo && R.key.ty == key.ty && R.key.groups == key.groups &&
+        R.spb == spb && R.graph_slots == R.d_slots.p &&
         R.graph_q == R.qlist.p && R.graph_f == R.qflag.p &&
         R.graph_nslots == n && std::memcmp(&R.ctrl_in_graph, &ctrl, sizeof ctrl) == 0)
         return HJB_OK;
@@ -680,6 +682,55 @@ int check_opts(const hjb_solve_opts *o) {
     return HJB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the 2D tile shape: 32 x rows nodes with 8 / rows control groups
+// per node.  Small tiles follow a narrow active front with less wasted work
+// and finish an item sooner; large tiles amortise the halo.  The first call
+// for a problem class runs the whole call once per candidate on the caller's
+// data and keeps the fastest; the choice is cached for the process.
+// HJB_TILE_ROWS=8|4|2 forces a shape.
+
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, int> g_tuned;
+
+int forced_rows() {
+    const char *e = std::getenv("HJB_TILE_ROWS");
+    if (!e) return 0;
+    const int r = std::atoi(e);
+    return (r == 8 || r == 4 || r == 2) ? r : 0;
+}
+
+template <typename Run>
+int tuned_call(const std::vector<long long> &key, Run run) {
+    int rows = forced_rows();
+    if (rows) return run(rows, nullptr);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) rows = it->second;
+    }
+    if (rows) return run(rows, nullptr);
+    const int cand[3] = {8, 4, 2};
+    double best_ms = 1e300;
+    int best = 2, last_rc = HJB_OK;
+    for (int c : cand) {
+        double ms = 0;
+        const int rc = run(c, &ms);
+        if (rc != HJB_OK && rc != HJB_ERR_NOT_CONVERGED) return rc;
+        last_rc = rc;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = best;
+    }
+    // the outputs of the last candidate are in place when it won
+    return best == cand[2] ? last_rc : run(best, nullptr);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -805,12 +856,12 @@ int hjb_destroy(hjb_problem *P) {
     return HJB_OK;
 }
 
-int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stats *stats,
-              void *stream) {
-    g_err.clear();
-    if (!P || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL problem or output");
-    TRY(check_opts(opts));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_out, hjb_stats *stats,
+               cudaStream_t st) {
     bool wform;
     TRY(resolve_form(P, opts ? opts->use_w_form : -1, &wform));
     Prep pr;
@@ -823,12 +874,12 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
     const SlotGeo g = geo_of(P->grid.ndim, P->grid.n, P->grid.periodic[2]);
     R.slots.assign(1, SlotDesc());
     std::memset(R.slots.data(), 0, sizeof(SlotDesc));
-    fill_slot(R.slots[0], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters);
+    fill_slot(R.slots[0], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows);
     if (P->kind == HJB_DYN_DUBINS) {
         TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
         R.slots[0].trig = P->trig.as<float2>();
     }
-    TRY(alloc_slot_buffers(R, P->grid.ndim, halo));
+    TRY(alloc_slot_buffers(R, P->grid.ndim, halo, rows));
     TRY(upload_slots(R, st));
     OutArr out;
     TRY(out.init(v_out, P->N * sizeof(float), &P->out_stage));
@@ -847,7 +898,8 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
     CK(cudaEventRecord(R.ev0, st));
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), 1, static_cast<int>(P->N), wform, c_over,
                              vinit, st);
-    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo};
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
+                             8 / rows};
     const hjbk::ControlTable ctrl = control_table(P);
     TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st));
     hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
@@ -870,6 +922,28 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
         return fail(HJB_ERR_NOT_CONVERGED, "not converged after %d iterations (residual %g)",
                     R.h_state[0].iters, R.h_state[0].final_res);
     return HJB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stats *stats,
+              void *stream) {
+    g_err.clear();
+    if (!P || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL problem or output");
+    TRY(check_opts(opts));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (P->kind == HJB_DYN_DUBINS) return solve_full(P, opts, hjbk::TY, v_out, stats, st);
+    const std::vector<long long> key = {0, P->kind, P->grid.n[0], P->grid.n[1], P->na,
+                                        P->cost.user ? 1 : 0};
+    return tuned_call(key, [&](int rows, double *ms) {
+        hjb_stats tmp;
+        hjb_stats *sp = stats ? stats : &tmp;
+        const int rc = solve_full(P, opts, rows, v_out, sp, st);
+        if (ms) *ms = sp->ms;
+        return rc;
+    });
 }
 
 int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_out,
@@ -931,18 +1005,20 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     std::memset(R.slots.data(), 0, m * sizeof(SlotDesc));
     if (P->kind == HJB_DYN_DUBINS)
         TRY(dubins_trig(P, P->c_trig, g.nz, hK, dxK, P->grid.lo[2], dxK[2], st));
+    const int rows = P->kind == HJB_DYN_DUBINS ? hjbk::TY : 2;
     for (int k = 0; k < m; ++k) {
-        fill_slot(R.slots[k], P, g, cp, wform, hK, dxK, halo, tol, max_iters);
+        fill_slot(R.slots[k], P, g, cp, wform, hK, dxK, halo, tol, max_iters, rows);
         R.slots[k].only_target = k + 1;  // RA step 1: dG := X_k
         if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->c_trig.as<float2>();
     }
-    TRY(alloc_slot_buffers(R, nd, halo));
+    TRY(alloc_slot_buffers(R, nd, halo, rows));
     TRY(upload_slots(R, st));
     const float c_over = static_cast<float>(P->l_const / P->lambda);
     CK(cudaEventRecord(R.ev0, st));
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform, c_over,
                              nullptr, st);
-    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo};
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
+                             8 / rows};
     TRY(run_loop(R, key, 2, control_table(P), st));
     // threshold of eq. (rep)
     double delta = ra->delta;
@@ -1026,12 +1102,12 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     return HJB_OK;
 }
 
-int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *opts,
-                         float *v_out, hjb_stats *per_subdomain, hjb_stats *total, void *stream) {
-    g_err.clear();
-    if (!P || !fine_mask || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
-    TRY(check_opts(opts));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *opts, int rows,
+              float *v_out, hjb_stats *per_subdomain, hjb_stats *total, cudaStream_t st) {
     bool wform;
     TRY(resolve_form(P, opts ? opts->use_w_form : -1, &wform));
     Prep pr;
@@ -1057,27 +1133,29 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     if (P->kind == HJB_DYN_DUBINS)
         TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
     const int tiles_x = (g.nx + hjbk::TX - 1) / hjbk::TX;
-    const int tiles_y = (g.ny + hjbk::TY - 1) / hjbk::TY;
+    const int tiles_y = (g.ny + rows - 1) / rows;
     const int tiles_z = nd > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
     const int nt = tiles_x * tiles_y * tiles_z;
     TRY(P->tile_bits.ensure(nt * sizeof(uint32_t)));
     for (int k = 0; k < m; ++k) {
-        fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters);
+        fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows);
         R.slots[k].mask = mask;
         R.slots[k].mask_bit = k;
         R.slots[k].tile_bits = P->tile_bits.as<uint32_t>();
         if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->trig.as<float2>();
     }
-    TRY(alloc_slot_buffers(R, nd, halo));
+    TRY(alloc_slot_buffers(R, nd, halo, rows));
     TRY(upload_slots(R, st));
     OutArr out;
     TRY(out.init(v_out, P->N * sizeof(float), &P->out_stage));
     const float c_over = static_cast<float>(P->l_const / P->lambda);
     CK(cudaEventRecord(R.ev0, st));
-    hjbh::launch_tile_bits(fine, tiles_x, tiles_y, tiles_z, mask, P->tile_bits.as<uint32_t>(), st);
+    hjbh::launch_tile_bits(fine, tiles_x, tiles_y, tiles_z, rows, mask,
+                           P->tile_bits.as<uint32_t>(), st);
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
                              nullptr, st);
-    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo};
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
+                             8 / rows};
     TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P), st));
     hjbh::launch_assemble(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, fine, mask,
                           wform ? 1 : 0, c_over, static_cast<float>(P->value_out),
@@ -1113,14 +1191,35 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     return HJB_OK;
 }
 
-int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opts *opts,
-                    float *const *v_out, hjb_stats *per_problem, void *stream) {
+}  // namespace
+
+extern "C" {
+
+int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *opts,
+                         float *v_out, hjb_stats *per_subdomain, hjb_stats *total, void *stream) {
     g_err.clear();
-    if (!problems || count < 1 || !v_out) return fail(HJB_ERR_INVALID_ARG, "empty batch");
-    if (count > hjbk::MAX_SLOTS)
-        return fail(HJB_ERR_INVALID_ARG, "at most %d problems per batch", hjbk::MAX_SLOTS);
+    if (!P || !fine_mask || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (P->kind == HJB_DYN_DUBINS)
+        return solve_dec(P, fine_mask, opts, hjbk::TY, v_out, per_subdomain, total, st);
+    const std::vector<long long> key = {1, P->kind, P->grid.n[0], P->grid.n[1], P->na,
+                                        P->cost.user ? 1 : 0, P->ntargets};
+    return tuned_call(key, [&](int rows, double *ms) {
+        hjb_stats tmp;
+        hjb_stats *tp = total ? total : &tmp;
+        const int rc = solve_dec(P, fine_mask, opts, rows, v_out, per_subdomain, tp, st);
+        if (ms) *ms = tp->ms;
+        return rc;
+    });
+}
+
+}  // extern "C"
+
+namespace {
+
+int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_opts *opts, int rows,
+                     float *const *v_out, hjb_stats *per_problem, cudaStream_t st) {
     hjb_problem *P0 = problems[0];
     if (!P0) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
     bool wform;
@@ -1154,21 +1253,22 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
         const SlotGeo g = geo_of(P->grid.ndim, P->grid.n, P->grid.periodic[2]);
         const double tol = (opts && opts->tol > 0) ? opts->tol : default_tol(P, P->h);
         const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
-        fill_slot(R.slots[i], P, g, preps[i], wform, P->h, P->dx, halo, tol, max_iters);
+        fill_slot(R.slots[i], P, g, preps[i], wform, P->h, P->dx, halo, tol, max_iters, rows);
         if (P->kind == HJB_DYN_DUBINS) {
             TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
             R.slots[i].trig = P->trig.as<float2>();
         }
         maxN = P->N > maxN ? P->N : maxN;
     }
-    TRY(alloc_slot_buffers(R, P0->grid.ndim, halo));
+    TRY(alloc_slot_buffers(R, P0->grid.ndim, halo, rows));
     TRY(upload_slots(R, st));
     const float c_over = static_cast<float>(P0->l_const / P0->lambda);
     std::vector<OutArr> outs(count);
     CK(cudaEventRecord(R.ev0, st));
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), count, static_cast<int>(maxN), wform, c_over,
                              nullptr, st);
-    const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P0->na, halo};
+    const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P0->na, halo, rows,
+                             8 / rows};
     TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st));
     for (int i = 0; i < count; ++i) {
         TRY(outs[i].init(v_out[i], problems[i]->N * sizeof(float), &problems[i]->out_stage));
@@ -1197,6 +1297,33 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
     if (!conv) return fail(HJB_ERR_NOT_CONVERGED, "a problem of the batch did not converge");
     return HJB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opts *opts,
+                    float *const *v_out, hjb_stats *per_problem, void *stream) {
+    g_err.clear();
+    if (!problems || count < 1 || !v_out) return fail(HJB_ERR_INVALID_ARG, "empty batch");
+    if (count > hjbk::MAX_SLOTS)
+        return fail(HJB_ERR_INVALID_ARG, "at most %d problems per batch", hjbk::MAX_SLOTS);
+    TRY(check_opts(opts));
+    if (!problems[0]) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (problems[0]->kind == HJB_DYN_DUBINS)
+        return solve_batch_impl(problems, count, opts, hjbk::TY, v_out, per_problem, st);
+    long long nodes = 0;
+    for (int i = 0; i < count; ++i) nodes += problems[i] ? problems[i]->N : 0;
+    const std::vector<long long> key = {2, problems[0]->kind, count, nodes, problems[0]->na};
+    std::vector<hjb_stats> tmp(count);
+    return tuned_call(key, [&](int rows, double *ms) {
+        hjb_stats *pp = per_problem ? per_problem : tmp.data();
+        const int rc = solve_batch_impl(problems, count, opts, rows, v_out, pp, st);
+        if (ms) *ms = pp[0].ms;
+        return rc;
+    });
 }
 
 int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,

@@ -201,18 +201,20 @@ __global__ void project_kernel(hjbh::GridDims fine, hjbh::GridDims coarse, int r
     }
 }
 
-// OR of the sub-domain bits over the nodes of each tile (one block per tile).
-__global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, const uint32_t *mask,
-                                 uint32_t *tile_bits) {
+// OR of the sub-domain bits over the nodes of each tile (one block per tile;
+// tiles are 32 x ty (x TZ in 3D) nodes).
+__global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int ty_rows,
+                                 const uint32_t *mask, uint32_t *tile_bits) {
     const int t = blockIdx.x;
     const int txy = tiles_x * tiles_y;
     const int tz = t / txy, rem = t - tz * txy;
     const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
-    const int x = tx * TX + (threadIdx.x & 31), y = ty * TY + (threadIdx.x >> 5);
+    const int x = tx * TX + (threadIdx.x & 31);
     uint32_t bits = 0u;
     const int zn = g.ndim > 2 ? TZ : 1;
-    for (int lz = 0; lz < zn; ++lz) {
-        const int z = g.ndim > 2 ? tz * TZ + lz : 0;
+    for (int r = threadIdx.x >> 5; r < ty_rows * zn; r += THREADS / 32) {
+        const int y = ty * ty_rows + r % ty_rows;
+        const int z = g.ndim > 2 ? tz * TZ + r / ty_rows : 0;
         if (x < g.n[0] && y < g.n[1] && (g.ndim < 3 || z < g.n[2])) bits |= mask[flat(g, x, y, z)];
     }
     bits = __reduce_or_sync(0xffffffffu, bits);
@@ -324,10 +326,10 @@ void launch_project(const GridDims &fine, const GridDims &coarse, const int stri
                                                      fine_mask);
 }
 
-void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z,
+void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty,
                       const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st) {
     const int nt = tiles_x * tiles_y * tiles_z;
-    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, mask, tile_bits);
+    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, ty, mask, tile_bits);
 }
 
 void launch_assemble(const SlotDesc *slots, const SlotState *state, int m, const GridDims &fine,

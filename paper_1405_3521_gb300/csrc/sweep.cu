@@ -156,20 +156,16 @@ __device__ __forceinline__ float pick(float best, float q) {
     return WFORM ? fmaxf(best, q) : fminf(best, q);
 }
 
-// Evaluation of all controls at one node of a tile that does not touch the
-// box boundary (no foot can leave the box).  S2 = (s hx, s hy), B2 = the
-// node's tile-local position plus the current's displacement.
-template <int NA, bool WFORM>
-__device__ __forceinline__ float controls_interior(const ControlTable &C, uint32_t K, float2 S2,
-                                                   float2 B2, float best) {
-    if constexpr (NA > 0) {
+// Controls [J0, J0 + NJ) at one node of a tile that does not touch the box
+// boundary (no foot can leave the box).  S2 = (s hx, s hy), B2 = the node's
+// tile-local position plus the current's displacement.  Compile-time control
+// indices let the control components be constant-bank operands.
+template <int J0, int NJ, bool WFORM>
+__device__ __forceinline__ float range_interior(const ControlTable &C, uint32_t K, float2 S2,
+                                                float2 B2, float best) {
 #pragma unroll
-        for (int j = 0; j < NA; ++j) best = pick<WFORM>(best, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
-    } else {
-        const int na = C.count;
-#pragma unroll 4
-        for (int j = 0; j < na; ++j) best = pick<WFORM>(best, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
-    }
+    for (int j = 0; j < NJ; ++j)
+        best = pick<WFORM>(best, q1_pairs(__ffma2_rn(S2, C.a2[J0 + j], B2), K));
     return best;
 }
 
@@ -191,21 +187,63 @@ __device__ __forceinline__ float one_control_edge(uint32_t K, float2 O2, const E
     return pick<WFORM>(best, out ? vout : q);
 }
 
-template <int NA, bool WFORM>
-__device__ __forceinline__ float controls_edge(const ControlTable &C, uint32_t K, float2 S2,
-                                               float2 O02, const EdgeBounds &eb, float2 BASE2,
-                                               float vout, float best) {
-    if constexpr (NA > 0) {
+template <int J0, int NJ, bool WFORM>
+__device__ __forceinline__ float range_edge(const ControlTable &C, uint32_t K, float2 S2,
+                                            float2 O02, const EdgeBounds &eb, float2 BASE2,
+                                            float vout, float best) {
 #pragma unroll
-        for (int j = 0; j < NA; ++j)
-            best = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2, vout, best);
+    for (int j = 0; j < NJ; ++j)
+        best = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[J0 + j], O02), eb, BASE2, vout, best);
+    return best;
+}
+
+// The controls of group g (of G groups splitting the control set): for a
+// compile-time count NA the group's contiguous block, selected by a
+// warp-uniform switch so that indices stay compile-time; otherwise every
+// G-th control from g.
+template <int NA, int G, bool WFORM>
+__device__ __forceinline__ float controls_interior(int g, const ControlTable &C, uint32_t K,
+                                                   float2 S2, float2 B2, float best) {
+    if constexpr (NA > 0) {
+        constexpr int NJ = NA / G;
+        if (g == 0) return range_interior<0, NJ, WFORM>(C, K, S2, B2, best);
+        if constexpr (G > 1)
+            if (g == 1) return range_interior<NJ, NJ, WFORM>(C, K, S2, B2, best);
+        if constexpr (G > 2) {
+            if (g == 2) return range_interior<2 * NJ, NJ, WFORM>(C, K, S2, B2, best);
+            return range_interior<3 * NJ, NJ, WFORM>(C, K, S2, B2, best);
+        }
+        return best;
     } else {
         const int na = C.count;
 #pragma unroll 4
-        for (int j = 0; j < na; ++j)
-            best = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2, vout, best);
+        for (int j = g; j < na; j += G)
+            best = pick<WFORM>(best, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
+        return best;
     }
-    return best;
+}
+
+template <int NA, int G, bool WFORM>
+__device__ __forceinline__ float controls_edge(int g, const ControlTable &C, uint32_t K, float2 S2,
+                                               float2 O02, const EdgeBounds &eb, float2 BASE2,
+                                               float vout, float best) {
+    if constexpr (NA > 0) {
+        constexpr int NJ = NA / G;
+        if (g == 0) return range_edge<0, NJ, WFORM>(C, K, S2, O02, eb, BASE2, vout, best);
+        if constexpr (G > 1)
+            if (g == 1) return range_edge<NJ, NJ, WFORM>(C, K, S2, O02, eb, BASE2, vout, best);
+        if constexpr (G > 2) {
+            if (g == 2) return range_edge<2 * NJ, NJ, WFORM>(C, K, S2, O02, eb, BASE2, vout, best);
+            return range_edge<3 * NJ, NJ, WFORM>(C, K, S2, O02, eb, BASE2, vout, best);
+        }
+        return best;
+    } else {
+        const int na = C.count;
+#pragma unroll 4
+        for (int j = g; j < na; j += G)
+            best = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2, vout, best);
+        return best;
+    }
 }
 
 // Block-wide exclusive scan of an int (256 threads); returns the total.
@@ -321,22 +359,24 @@ __device__ __forceinline__ void cta_done(const SweepArgs &args, bool failed) {
 }
 
 // Tile queue of the next sweep: called by warp 0 of a CTA whose tile changed
-// (bitwise) in this sweep; lane t < NB considers neighbour t of the 3x3
-// (3x3x3) tile neighbourhood, skips tiles outside the grid or holding no node
-// of the slot, claims the neighbour's flag, and the claimed neighbours are
-// appended with one atomic per warp.  A tile none of whose neighbours
-// changed would reproduce its previous values exactly, so it is not queued.
-template <bool THREE_D>
+// (bitwise) in this sweep; lane t considers neighbour t of the tile
+// neighbourhood (radius RX, RY, RZ in tiles: the halo of a tile reaches that
+// far), skips tiles outside the grid or holding no node of the slot, claims
+// the neighbour's flag, and the claimed neighbours are appended with one
+// atomic per warp.  A tile none of whose neighbours changed would reproduce
+// its previous values exactly, so it is not queued.
+template <int RX, int RY, int RZ>
 __device__ __forceinline__ void enqueue_neighbours(const SweepArgs &args, const SlotDesc &S,
                                                    int slot, int tx, int ty, int tz, int p) {
+    constexpr int WX = 2 * RX + 1, WY = 2 * RY + 1, WZ = 2 * RZ + 1;
+    static_assert(WX * WY * WZ <= 32, "neighbourhood larger than a warp");
     const int lane = threadIdx.x & 31;
     int nb = -1;
-    constexpr int NB = THREE_D ? 27 : 9;
-    if (lane < NB) {
-        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = THREE_D ? lane / 9 - 1 : 0;
+    if (lane < WX * WY * WZ) {
+        const int dx = lane % WX - RX, dy = (lane / WX) % WY - RY, dz = lane / (WX * WY) - RZ;
         const int x = tx + dx, y = ty + dy;
         int z = tz + dz;
-        if (THREE_D) z = (z + S.tiles_z) % S.tiles_z;  // periodic heading
+        if (RZ > 0) z = ((z % S.tiles_z) + S.tiles_z) % S.tiles_z;  // periodic heading
         if (x >= 0 && x < S.tiles_x && y >= 0 && y < S.tiles_y) {
             const int t = (z * S.tiles_y + y) * S.tiles_x + x;
             const bool member = S.tile_bits == nullptr || ((S.tile_bits[t] >> S.mask_bit) & 1u);
@@ -367,22 +407,31 @@ __device__ __forceinline__ void unflag(const SweepArgs &args, const SlotDesc &S,
 }
 
 // --------------------------------------------------------------------------
-// 2D sweep: f = s(x) a + c(x).  Tile 32 x 8, halo H (cells) in x and y.
+// 2D sweep: f = s(x) a + c(x).  Tile 32 x TYT nodes, halo H (cells) in x
+// and y; the 256 threads form G control groups per node: warp w handles row
+// w / G of the tile for the controls of group w % G, and the groups' partial
+// extrema are combined through shared memory.
 
-template <int NA, bool WFORM, int H>
+template <int NA, bool WFORM, int H, int TYT, int G>
 __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(const __grid_constant__ SweepArgs args) {
-    constexpr int ROWS = TY + 2 * H;
+    static_assert(TYT * G * 32 == THREADS, "tile rows x control groups must fill the CTA");
+    constexpr int ROWS = TYT + 2 * H;
     constexpr int TILE = ROWS * TW;
-    __shared__ alignas(128) float s_tile[2][TILE];
+    // each staging buffer starts on a 128-byte boundary (TMA destination rule)
+    constexpr int TILE_STRIDE = (TILE + 31) / 32 * 32;
+    constexpr int RY = (H + TYT - 1) / TYT;  // tile neighbourhood reached by the halo
+    __shared__ alignas(128) float s_tile[2][TILE_STRIDE];
     __shared__ alignas(16) float2 s_pair[ROWS * PW];
     __shared__ alignas(8) uint64_t s_bar[2];
     __shared__ int s_item[2][3];
     __shared__ float s_red[THREADS / 32];
     __shared__ int s_cnt[THREADS / 32];
+    __shared__ float s_part[G][TYT][32];
 
     const Ctl *ctl = args.ctl;
     const int tid = threadIdx.x;
-    const int lx = tid & 31, ly = tid >> 5;
+    const int lx = tid & 31, warp = tid >> 5;
+    const int grp = warp % G, ly = warp / G;
     const int p = static_cast<int>(ctl->sweep & 1u);
     const int src = p, dst = p ^ 1;
     const int nitems = ctl->qcount[p];
@@ -404,7 +453,7 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
         if (live) {
             const int tx = tile % S->tiles_x, ty = tile / S->tiles_x;
             mbar_expect_tx(&s_bar[b], TILE * 4);
-            tma_load_2d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H, &s_bar[b]);
+            tma_load_2d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TYT - H, &s_bar[b]);
         }
     };
 
@@ -448,14 +497,15 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
         }
         const int nx = S.nx, ny = S.ny;
         const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
-        const int gx = tx * TX + lx, gy = ty * TY + ly;
+        const int gx = tx * TX + lx, gy = ty * TYT + ly;
         const float vold = T[(ly + H) * TW + lx + XPAD];
         const long long gi = static_cast<long long>(gy) * nx + gx;
         const bool isfree = (gx < nx) && (gy < ny) && node_class(S, gi) == CLS_FREE;
         __syncthreads();
-        float vnew = vold;
+        float best = WFORM ? -INFINITY : INFINITY;
+        float s = 1.0f;
         if (isfree) {
-            const float s = S.speed ? S.speed[gi] : 1.0f;
+            if (S.speed) s = S.speed[gi];
             float cx = 0.0f, cy = 0.0f;
             if (S.current) {
                 const float2 c = reinterpret_cast<const float2 *>(S.current)[gi];
@@ -467,30 +517,43 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
             const float2 BASE2 = make_float2(static_cast<float>(lx + XPAD),
                                              static_cast<float>(ly + H + 1));
             const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
-                                  (ty * TY >= H) && (ty * TY + TY - 1 + H <= ny - 1);
-            float best = WFORM ? -INFINITY : INFINITY;
+                                  (ty * TYT >= H) && (ty * TYT + TYT - 1 + H <= ny - 1);
             if (interior) {
-                best = controls_interior<NA, WFORM>(args.ctrl, K, S2, __fadd2_rn(BASE2, O02), best);
+                best = controls_interior<NA, G, WFORM>(grp, args.ctrl, K, S2,
+                                                      __fadd2_rn(BASE2, O02), best);
             } else {
                 EdgeBounds eb;
                 eb.lox = -static_cast<float>(gx);
                 eb.hix = static_cast<float>(nx - 1 - gx);
                 eb.loy = -static_cast<float>(gy);
                 eb.hiy = static_cast<float>(ny - 1 - gy);
-                best = controls_edge<NA, WFORM>(args.ctrl, K, S2, O02, eb, BASE2, S.vout, best);
+                best = controls_edge<NA, G, WFORM>(grp, args.ctrl, K, S2, O02, eb, BASE2, S.vout,
+                                                  best);
             }
+        }
+        if constexpr (G > 1) {
+            s_part[grp][ly][lx] = best;
+            __syncthreads();
+            if (grp == 0) {
+#pragma unroll
+                for (int q = 1; q < G; ++q) best = pick<WFORM>(best, s_part[q][ly][lx]);
+            }
+        }
+        const bool mine = isfree && grp == 0;  // group 0 owns the node's result
+        float vnew = vold;
+        if (mine) {
             if (WFORM)
                 vnew = S.beta * best;
             else
                 vnew = fmaf(S.beta, best, S.cost ? S.gamma * S.cost[gi] : S.gl);
             S.V[dst][static_cast<long long>(gy) * S.pitch + gx] = vnew;
         }
-        const float r = warp_max(isfree ? fabsf(vnew - vold) : 0.0f);
-        const unsigned fm = __ballot_sync(0xffffffffu, isfree);
-        const unsigned cm = __ballot_sync(0xffffffffu, isfree && (vnew != vold));
+        const float r = warp_max(mine ? fabsf(vnew - vold) : 0.0f);
+        const unsigned fm = __ballot_sync(0xffffffffu, mine);
+        const unsigned cm = __ballot_sync(0xffffffffu, mine && (vnew != vold));
         if (lx == 0) {
-            s_red[ly] = r;
-            s_cnt[ly] = __popc(fm) | (cm ? 0x10000 : 0);
+            s_red[warp] = r;
+            s_cnt[warp] = __popc(fm) | (cm ? 0x10000 : 0);
         }
         __syncthreads();
         if (tid < 32) {
@@ -507,7 +570,7 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
                 atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot));
                 unflag(args, S, tile, p);
             }
-            if (chg) enqueue_neighbours<false>(args, S, slot, tx, ty, 0, p);
+            if (chg) enqueue_neighbours<1, RY, 0>(args, S, slot, tx, ty, 0, p);
         }
     }
     cta_done(args, failed);
@@ -526,7 +589,8 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
     constexpr int ROWS = TY + 2 * H;
     constexpr int LAYER = ROWS * TW;
     constexpr int TILE = (TZ + 2 * HZ) * LAYER;
-    __shared__ alignas(128) float s_tile[2][TILE];
+    constexpr int TILE_STRIDE = (TILE + 31) / 32 * 32;  // 128-byte aligned buffers
+    __shared__ alignas(128) float s_tile[2][TILE_STRIDE];
     __shared__ alignas(8) uint64_t s_bar[2];
     __shared__ int s_item[2][3];
     __shared__ float s_red[THREADS / 32];
@@ -695,7 +759,7 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
                 atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot));
                 unflag(args, S, tile, p);
             }
-            if (any) enqueue_neighbours<true>(args, S, slot, tx, ty, tz, p);
+            if (any) enqueue_neighbours<1, 1, 1>(args, S, slot, tx, ty, tz, p);
         }
     }
     cta_done(args, failed);
@@ -809,33 +873,34 @@ namespace hjbh {
 const void *sweep_kernel(const SweepKey &k, size_t *smem) {
     if (smem) *smem = 0;
     if (k.dubins) {
-        if (k.halo != 2) return nullptr;
+        if (k.halo != 2 || k.ty != TY || k.groups != 1) return nullptr;
         return k.wform ? reinterpret_cast<const void *>(&sweep3d_kernel<true>)
                        : reinterpret_cast<const void *>(&sweep3d_kernel<false>);
     }
-#define HJB_PICK(NA_, H_)                                                          \
-    if (k.halo == H_) {                                                            \
-        return k.wform ? reinterpret_cast<const void *>(&sweep2d_kernel<NA_, true, H_>) \
-                       : reinterpret_cast<const void *>(&sweep2d_kernel<NA_, false, H_>); \
+#define HJB_PICK(NA_, H_, TY_, G_)                                                              \
+    if (k.halo == H_ && k.ty == TY_ && k.groups == G_) {                                         \
+        return k.wform ? reinterpret_cast<const void *>(&sweep2d_kernel<NA_, true, H_, TY_, G_>)  \
+                       : reinterpret_cast<const void *>(&sweep2d_kernel<NA_, false, H_, TY_, G_>); \
     }
+#define HJB_PICK_SHAPES(NA_, H_) \
+    HJB_PICK(NA_, H_, 8, 1)      \
+    HJB_PICK(NA_, H_, 4, 2)      \
+    HJB_PICK(NA_, H_, 2, 4)
     switch (k.na) {
         case 64:
-            HJB_PICK(64, 2)
-            HJB_PICK(64, 4)
+            HJB_PICK_SHAPES(64, 2)
+            HJB_PICK_SHAPES(64, 4)
             break;
         case 32:
-            HJB_PICK(32, 2)
-            HJB_PICK(32, 4)
-            break;
-        case 16:
-            HJB_PICK(16, 2)
-            HJB_PICK(16, 4)
+            HJB_PICK_SHAPES(32, 2)
+            HJB_PICK_SHAPES(32, 4)
             break;
         default:
-            HJB_PICK(0, 2)
-            HJB_PICK(0, 4)
+            HJB_PICK_SHAPES(0, 2)
+            HJB_PICK_SHAPES(0, 4)
             break;
     }
+#undef HJB_PICK_SHAPES
 #undef HJB_PICK
     return nullptr;
 }

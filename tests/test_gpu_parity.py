@@ -38,7 +38,9 @@ def test_c1_full_solve(hjb, orc, wform):
     err = np.abs(to_np(V) - Vo).max()
     assert st["converged"] == 1
     assert err < TOL_V, err
-    assert st["node_updates"] == st["iterations"] * int((d["labels"] == 0).sum())
+    # quiescent tiles are skipped (exactly), so at most every free node per sweep
+    nfree = int((d["labels"] == 0).sum())
+    assert 0 < st["node_updates"] <= st["iterations"] * nfree
 
 
 @pytest.mark.parametrize("nx,ny,A,cur", [(67, 45, 16, True), (33, 97, 7, False),
@@ -265,3 +267,34 @@ def test_autograd_function(hjb, orc):
     gt_o, _ = orc.grad(po, Vo, pol, lam)
     g = theta.grad.detach().cpu().numpy().reshape(-1)
     assert np.abs(g - gt_o).max() / np.abs(gt_o).max() < 1e-3
+
+
+def test_tile_shapes_agree_bitwise(hjb, orc, monkeypatch):
+    """Every tile shape (32 x 8 / 4 / 2 nodes with 1 / 2 / 4 control groups)
+    computes the same Jacobi iterates, so the results agree bit for bit; the
+    grid holds more tiles than resident CTAs, so every CTA stages several
+    items through both shared-memory buffers."""
+    n, A = 577, 16
+    X, Y = S.mesh2(n, n)
+    g = S.rng("misc", 31)
+    lab = S.disk_labels(X, Y, S.disk_centers(g, 5, 0.1), 0.1)
+    d = dict(shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=S.f32(S.circle_controls(A)), labels=lab, ntargets=5,
+             speed=S.f32(S.speed_field(g, X, Y)), current=S.f32(S.current_field(g, X, Y)),
+             h=2.0 / (n - 1), lam=1.0, v_out=1.0)
+    p = gpu_problem(hjb, d)
+    outs = []
+    for rows in ("8", "4", "2"):
+        monkeypatch.setenv("HJB_TILE_ROWS", rows)
+        V, st = hjb.solve(p)
+        outs.append(to_np(V))
+        fine, _, _, _ = hjb.subdomains(p, (16, 16), delta=0.2)
+        Vb, _, _ = hjb.solve_decomposed(p, fine)
+        outs.append(to_np(Vb))
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[0], outs[4])
+    assert np.array_equal(outs[1], outs[3]) and np.array_equal(outs[1], outs[5])
+    # one sampled check against the oracle's operator at full size: the FP64
+    # residual of the GPU fixed point bounds its distance to the oracle's
+    po = oracle_problem(orc, d)
+    Tv, r = orc.apply(po, outs[0].astype(np.float64), nthreads=8)
+    assert r / (1 - po.beta) < TOL_V
