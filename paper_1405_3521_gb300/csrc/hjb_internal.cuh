@@ -87,7 +87,7 @@ struct Ctl {
     unsigned done_ctas;
     unsigned sweep;      // number of sweeps so far (parity of the source buffer)
     int nactive;
-    int total_items;
+    unsigned gen;        // generation of the cooperative loop's grid barrier
     int error;           // non-zero: a bounded wait gave up
     unsigned launches;   // sweep kernels run (including empty ones at the loop's end)
     int qcount[2];       // entries of the two tile queues (parity = sweep parity)
@@ -122,6 +122,7 @@ struct SweepKey {
     int halo;    // 2 or 4 (2D), 2 (3D)
     int ty;      // tile rows: 8, 4 or 2 (2D); 8 (3D)
     int groups;  // control groups per node: 256 / (32 ty)
+    int loop;    // 1: the cooperative whole-loop kernel, 0: one sweep per launch
 };
 
 // Returns the kernel function for a key (nullptr if unsupported) and the

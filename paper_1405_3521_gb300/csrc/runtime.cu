@@ -158,7 +158,8 @@ struct RunCtx {
     SlotState *h_state = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    hjbh::SweepKey key{-1, -1, -1, -1, -1, -1};
+    hjbh::SweepKey key{-1, -1, -1, -1, -1, -1, -1};
+    int last_loop = 0;  // the last run used the cooperative loop kernel
     int spb = 0;
     const void *graph_slots = nullptr;
     const void *graph_q = nullptr;
@@ -424,6 +425,15 @@ int resolve_form(const hjb_problem *P, int use_w, bool *wform) {
     return HJB_OK;
 }
 
+// Convergence loop driver: 1 = one cooperative launch running every sweep
+// with grid barriers (default), 0 = a CUDA-graph WHILE loop of one-sweep
+// launches.  HJB_LOOP=graph|coop selects it.
+int loop_mode() {
+    const char *e = std::getenv("HJB_LOOP");
+    if (e && std::strcmp(e, "graph") == 0) return 0;
+    return 1;
+}
+
 double default_tol(const hjb_problem *P, double h) {
     return 0.5e-4 * (-std::expm1(-P->lambda * h));
 }
@@ -507,6 +517,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     const int n = static_cast<int>(R.slots.size());
     if (R.exec && R.key.dubins == key.dubins && R.key.wform == key.wform && R.key.na == key.na &&
         R.key.halo == key.halo && R.key.ty == key.ty && R.key.groups == key.groups &&
+        R.key.loop == key.loop &&
         R.spb == spb && R.graph_slots == R.d_slots.p &&
         R.graph_q == R.qlist.p && R.graph_f == R.qflag.p &&
         R.graph_nslots == n && std::memcmp(&R.ctrl_in_graph, &ctrl, sizeof ctrl) == 0)
@@ -602,6 +613,26 @@ int run_loop(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlT
     }
     CK(cudaGetLastError());
     const float stall_tol = 8.0f * 1.1920929e-7f;
+    R.last_loop = key.loop;
+    if (key.loop) {
+        // the whole loop in one cooperative launch (all CTAs co-resident)
+        const void *fn = hjbh::sweep_kernel(key, nullptr);
+        if (!fn) return fail(HJB_ERR_UNSUPPORTED, "no sweep kernel for this configuration");
+        const int grid = hjbh::sweep_grid(key);
+        hjbk::SweepArgs args;
+        std::memset(&args, 0, sizeof args);
+        args.slots = R.d_slots.as<SlotDesc>();
+        args.state = R.d_state.as<SlotState>();
+        args.ctl = R.d_ctl.as<Ctl>();
+        set_queue_args(R, args);
+        args.nslots = n;
+        args.use_handle = 0;
+        args.stall_tol = stall_tol;
+        args.ctrl = ctrl;
+        void *argv[1] = {&args};
+        CK(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(hjbk::THREADS), argv, 0, st));
+        return HJB_OK;
+    }
     const char *ng = std::getenv("HJB_NO_GRAPH");
     if (ng && ng[0] == '1') {
         // host-driven loop (debugging aid): spb sweeps, then read nactive
@@ -654,7 +685,7 @@ int read_state(RunCtx &R, cudaStream_t st, int *err, long long *launches = nullp
                        st));
     CK(cudaStreamSynchronize(st));
     *err = herr[0];
-    if (launches) *launches = static_cast<unsigned>(herr[1]);
+    if (launches) *launches = R.last_loop ? 1 : static_cast<unsigned>(herr[1]);
     return HJB_OK;
 }
 
@@ -899,7 +930,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_ou
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), 1, static_cast<int>(P->N), wform, c_over,
                              vinit, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
-                             8 / rows};
+                             8 / rows, loop_mode()};
     const hjbk::ControlTable ctrl = control_table(P);
     TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st));
     hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
@@ -1018,7 +1049,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
-                             8 / rows};
+                             8 / rows, loop_mode()};
     TRY(run_loop(R, key, 2, control_table(P), st));
     // threshold of eq. (rep)
     double delta = ra->delta;
@@ -1155,7 +1186,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
-                             8 / rows};
+                             8 / rows, loop_mode()};
     TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P), st));
     hjbh::launch_assemble(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, fine, mask,
                           wform ? 1 : 0, c_over, static_cast<float>(P->value_out),
@@ -1268,7 +1299,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), count, static_cast<int>(maxN), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P0->na, halo, rows,
-                             8 / rows};
+                             8 / rows, loop_mode()};
     TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st));
     for (int i = 0; i < count; ++i) {
         TRY(outs[i].init(v_out[i], problems[i]->N * sizeof(float), &problems[i]->out_stage));

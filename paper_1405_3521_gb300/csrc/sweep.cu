@@ -281,10 +281,11 @@ __device__ __forceinline__ int block_scan(int a, int &ea, int *sa) {
 __device__ void finish_sweep(const SweepArgs &args) {
     Ctl *ctl = args.ctl;
     __shared__ int s_sa[THREADS / 32];
-    const int n = ctl->nactive;
-    const int p = static_cast<int>(ctl->sweep & 1u);
+    // L2 reads: in the cooperative loop these were written by other CTAs
+    const int n = __ldcg(&ctl->nactive);
+    const int p = static_cast<int>(__ldcg(&ctl->sweep) & 1u);
     const int dst_parity = p ^ 1;
-    const int err = ctl->error;
+    const int err = __ldcg(&ctl->error);
     constexpr int PER = MAX_SLOTS / THREADS;
     int sid[PER], keep[PER];
     int cnt = 0;
@@ -294,28 +295,33 @@ __device__ void finish_sweep(const SweepArgs &args) {
         keep[k] = 0;
         sid[k] = -1;
         if (i >= n) continue;
-        const int s = ctl->act_slot[i];
+        const int s = __ldcg(&ctl->act_slot[i]);
         sid[k] = s;
         SlotState &st = args.state[s];
         const SlotDesc &S = args.slots[s];
-        const float r = __uint_as_float(st.res_bits);
+        const float r = __uint_as_float(__ldcg(&st.res_bits));
+        const int iters = __ldcg(&st.iters) + 1;
         st.res_bits = 0u;
-        st.iters += 1;
+        st.iters = iters;
         st.final_res = r;
         st.final_parity = dst_parity;
         int kp = 1;
         if (r <= S.tol) {
             st.converged = 1;
             kp = 0;
-        } else if (st.iters >= S.max_iters || err) {
+        } else if (iters >= S.max_iters || err) {
             kp = 0;
         } else {
-            if (r < st.best_res) {
+            if (r < __ldcg(&st.best_res)) {
                 st.best_res = r;
                 st.stall = 0;
-            } else if (++st.stall >= 64 && r <= args.stall_tol) {
-                st.converged = 2;
-                kp = 0;
+            } else {
+                const int stall = __ldcg(&st.stall) + 1;
+                st.stall = stall;
+                if (stall >= 64 && r <= args.stall_tol) {
+                    st.converged = 2;
+                    kp = 0;
+                }
             }
         }
         if (!kp) st.done = 1;
@@ -333,8 +339,8 @@ __device__ void finish_sweep(const SweepArgs &args) {
     if (threadIdx.x == 0) {
         ctl->nactive = tc;
         ctl->qcount[p] = 0;  // every entry of this sweep's queue was consumed
-        if (n > 0) ctl->sweep += 1u;
-        ctl->launches += 1u;
+        if (n > 0) ctl->sweep = __ldcg(&ctl->sweep) + 1u;
+        ctl->launches = __ldcg(&ctl->launches) + 1u;
         ctl->done_ctas = 0u;
         __threadfence();
         if (args.use_handle) cudaGraphSetConditional(args.handle, (tc > 0 && !err) ? 1u : 0u);
@@ -406,94 +412,147 @@ __device__ __forceinline__ void unflag(const SweepArgs &args, const SlotDesc &S,
     atomicAnd(w, ~(0xffu << sh));
 }
 
+// Grid-wide barrier of the cooperative loop, fused with the convergence
+// step: the last CTA to arrive runs finish_sweep and then releases the
+// others by bumping the generation.  Waiters give up after WAIT_NS and
+// raise the error flag, so a lost CTA cannot hang the loop.  Returns false
+// when the loop must stop (all slots done, or an error).
+__device__ bool grid_barrier_finish(const SweepArgs &args, bool failed) {
+    __shared__ int s_last;
+    __shared__ int s_go;
+    Ctl *ctl = args.ctl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (failed) atomicExch(&ctl->error, 1);
+        const unsigned gen = *reinterpret_cast<volatile unsigned *>(&ctl->gen);
+        __threadfence();
+        const unsigned t = atomicAdd(&ctl->done_ctas, 1u);
+        s_last = (t == gridDim.x - 1) ? 1 : 0;
+        if (!s_last) {
+            const unsigned long long t0 = global_ns();
+            unsigned ns = 32;
+            while (*reinterpret_cast<volatile unsigned *>(&ctl->gen) == gen) {
+                if (*reinterpret_cast<volatile int *>(&ctl->error)) break;
+                if (global_ns() - t0 > WAIT_NS) {
+                    atomicExch(&ctl->error, 1);
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finish_sweep(args);  // resets done_ctas
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&ctl->gen, 1u);
+        }
+    }
+    if (threadIdx.x == 0) {
+        const int nact = *reinterpret_cast<volatile int *>(&ctl->nactive);
+        const int err = *reinterpret_cast<volatile int *>(&ctl->error);
+        s_go = (nact > 0 && !err) ? 1 : 0;
+    }
+    __syncthreads();
+    return s_go != 0;
+}
+
 // --------------------------------------------------------------------------
 // 2D sweep: f = s(x) a + c(x).  Tile 32 x TYT nodes, halo H (cells) in x
 // and y; the 256 threads form G control groups per node: warp w handles row
 // w / G of the tile for the controls of group w % G, and the groups' partial
 // extrema are combined through shared memory.
 
-template <int NA, bool WFORM, int H, int TYT, int G>
-__global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(const __grid_constant__ SweepArgs args) {
-    static_assert(TYT * G * 32 == THREADS, "tile rows x control groups must fill the CTA");
-    constexpr int ROWS = TYT + 2 * H;
-    constexpr int TILE = ROWS * TW;
+template <int H, int TYT, int G>
+struct Smem2d {
+    static constexpr int ROWS = TYT + 2 * H;
+    static constexpr int TILE = ROWS * TW;
     // each staging buffer starts on a 128-byte boundary (TMA destination rule)
-    constexpr int TILE_STRIDE = (TILE + 31) / 32 * 32;
-    constexpr int RY = (H + TYT - 1) / TYT;  // tile neighbourhood reached by the halo
-    __shared__ alignas(128) float s_tile[2][TILE_STRIDE];
-    __shared__ alignas(16) float2 s_pair[ROWS * PW];
-    __shared__ alignas(8) uint64_t s_bar[2];
-    __shared__ int s_item[2][3];
-    __shared__ float s_red[THREADS / 32];
-    __shared__ int s_cnt[THREADS / 32];
-    __shared__ float s_part[G][TYT][32];
+    static constexpr int TILE_STRIDE = (TILE + 31) / 32 * 32;
+    float tile[2][TILE_STRIDE];
+    float2 pair[ROWS * PW];
+    uint64_t bar[2];
+    int item[2][3];
+    float red[THREADS / 32];
+    int cnt[THREADS / 32];
+    float part[G][TYT][32];
+};
 
+// One sweep over this launch's tile queue by one CTA.  `uses` counts the
+// TMA phases consumed per staging buffer and persists across sweeps.
+template <int NA, bool WFORM, int H, int TYT, int G>
+__device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> &sm,
+                                       unsigned uses[2]) {
+    using SM = Smem2d<H, TYT, G>;
+    constexpr int ROWS = SM::ROWS;
+    constexpr int TILE = SM::TILE;
+    constexpr int RY = (H + TYT - 1) / TYT;  // tile neighbourhood reached by the halo
     const Ctl *ctl = args.ctl;
     const int tid = threadIdx.x;
     const int lx = tid & 31, warp = tid >> 5;
     const int grp = warp % G, ly = warp / G;
-    const int p = static_cast<int>(ctl->sweep & 1u);
+    const int p = static_cast<int>(*reinterpret_cast<const volatile unsigned *>(&ctl->sweep) & 1u);
     const int src = p, dst = p ^ 1;
-    const int nitems = ctl->qcount[p];
+    const int nitems = *reinterpret_cast<const volatile int *>(&ctl->qcount[p]);
     const int *qlist = args.qlist[p];
-    // pair (ky, kx) sits at byte (ky - 1) * 512 + kx * 8 of s_pair, with
+    // pair (ky, kx) sits at byte (ky - 1) * 512 + kx * 8 of sm.pair, with
     // kx = bits(mx) - 2^23 bits and ky = bits(my) - 2^23 bits (see q1_pairs)
-    const uint32_t K = smem_u32(s_pair) - (static_cast<uint32_t>(TWO23_BITS) << 9) -
+    const uint32_t K = smem_u32(sm.pair) - (static_cast<uint32_t>(TWO23_BITS) << 9) -
                        (static_cast<uint32_t>(TWO23_BITS) << 3) - 512u;
 
     // thread 0: stage item v into buffer b (no copy for a finished slot)
     auto issue = [&](int v, int b) {
-        const int e = qlist[v];
+        const int e = __ldcg(qlist + v);  // written by other CTAs in the previous sweep
         const int slot = e >> 22, tile = e & 0x3FFFFF;
         const SlotDesc *S = args.slots + slot;
-        const int live = args.state[slot].done ? 0 : 1;
-        s_item[b][0] = slot;
-        s_item[b][1] = tile;
-        s_item[b][2] = live;
+        const int live = __ldcg(&args.state[slot].done) ? 0 : 1;
+        sm.item[b][0] = slot;
+        sm.item[b][1] = tile;
+        sm.item[b][2] = live;
         if (live) {
             const int tx = tile % S->tiles_x, ty = tile / S->tiles_x;
-            mbar_expect_tx(&s_bar[b], TILE * 4);
-            tma_load_2d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TYT - H, &s_bar[b]);
+            mbar_expect_tx(&sm.bar[b], TILE * 4);
+            tma_load_2d(sm.tile[b], &S->tmap[src], tx * TX - XPAD, ty * TYT - H, &sm.bar[b]);
         }
     };
 
-    if (tid == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
     int v = blockIdx.x;
-    if (tid == 0 && v < nitems) issue(v, 0);
+    // buffer of the first item: continue the alternation of earlier sweeps
+    int b0 = static_cast<int>((uses[0] + uses[1]) & 1u);
+    if (tid == 0 && v < nitems) issue(v, b0);
     __syncthreads();
     bool failed = false;
-    unsigned uses[2] = {0u, 0u};  // completed TMA phases consumed per buffer
     for (int it = 0; v < nitems; ++it, v += gridDim.x) {
-        const int b = it & 1;
+        const int b = (b0 + it) & 1;
         const int vn = v + gridDim.x;
-        const int slot = s_item[b][0], tile = s_item[b][1], live = s_item[b][2];
-        __syncthreads();  // everyone has read s_item[b]; buffer b ^ 1 is free
+        const int slot = sm.item[b][0], tile = sm.item[b][1], live = sm.item[b][2];
+        __syncthreads();  // everyone has read sm.item[b]; buffer b ^ 1 is free
         if (tid == 0 && vn < nitems) issue(vn, b ^ 1);
         const SlotDesc &S = args.slots[slot];
         if (!live) {
             if (tid == 0) unflag(args, S, tile, p);
-            __syncthreads();  // s_item[b ^ 1] written by the issue above
+            __syncthreads();  // sm.item[b ^ 1] written by the issue above
             continue;
         }
-        const bool ok = mbar_wait_bounded(&s_bar[b], uses[b] & 1u);
+        const bool ok = mbar_wait_bounded(&sm.bar[b], uses[b] & 1u);
         uses[b] += 1u;
         if (!__syncthreads_and(ok)) {
             failed = true;
             // let the prefetch of the next item (if any) land before leaving
-            if (tid == 0 && vn < nitems && s_item[b ^ 1][2])
-                mbar_wait_bounded(&s_bar[b ^ 1], uses[b ^ 1] & 1u);
+            if (tid == 0 && vn < nitems && sm.item[b ^ 1][2])
+                mbar_wait_bounded(&sm.bar[b ^ 1], uses[b ^ 1] & 1u);
             break;
         }
         // pair layout: (raw[r][c], raw[r][c+1]) for the TW-1 columns a foot can use
-        const float *T = s_tile[b];
+        const float *T = sm.tile[b];
         for (int i = tid; i < ROWS * (TW - 1); i += THREADS) {
             const int r = i / (TW - 1), c = i - r * (TW - 1);
-            s_pair[r * PW + c] = make_float2(T[r * TW + c], T[r * TW + c + 1]);
+            sm.pair[r * PW + c] = make_float2(T[r * TW + c], T[r * TW + c + 1]);
         }
         const int nx = S.nx, ny = S.ny;
         const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
@@ -503,9 +562,8 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
         const bool isfree = (gx < nx) && (gy < ny) && node_class(S, gi) == CLS_FREE;
         __syncthreads();
         float best = WFORM ? -INFINITY : INFINITY;
-        float s = 1.0f;
         if (isfree) {
-            if (S.speed) s = S.speed[gi];
+            const float s = S.speed ? S.speed[gi] : 1.0f;
             float cx = 0.0f, cy = 0.0f;
             if (S.current) {
                 const float2 c = reinterpret_cast<const float2 *>(S.current)[gi];
@@ -532,11 +590,11 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
             }
         }
         if constexpr (G > 1) {
-            s_part[grp][ly][lx] = best;
+            sm.part[grp][ly][lx] = best;
             __syncthreads();
             if (grp == 0) {
 #pragma unroll
-                for (int q = 1; q < G; ++q) best = pick<WFORM>(best, s_part[q][ly][lx]);
+                for (int q = 1; q < G; ++q) best = pick<WFORM>(best, sm.part[q][ly][lx]);
             }
         }
         const bool mine = isfree && grp == 0;  // group 0 owns the node's result
@@ -552,8 +610,8 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
         const unsigned fm = __ballot_sync(0xffffffffu, mine);
         const unsigned cm = __ballot_sync(0xffffffffu, mine && (vnew != vold));
         if (lx == 0) {
-            s_red[warp] = r;
-            s_cnt[warp] = __popc(fm) | (cm ? 0x10000 : 0);
+            sm.red[warp] = r;
+            sm.cnt[warp] = __popc(fm) | (cm ? 0x10000 : 0);
         }
         __syncthreads();
         if (tid < 32) {
@@ -561,9 +619,9 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
             int tot = 0, chg = 0;
 #pragma unroll
             for (int w = 0; w < THREADS / 32; ++w) {
-                m = fmaxf(m, s_red[w]);
-                tot += s_cnt[w] & 0xffff;
-                chg |= s_cnt[w] >> 16;
+                m = fmaxf(m, sm.red[w]);
+                tot += sm.cnt[w] & 0xffff;
+                chg |= sm.cnt[w] >> 16;
             }
             if (tid == 0) {
                 if (m > 0.0f) atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
@@ -573,7 +631,42 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
             if (chg) enqueue_neighbours<1, RY, 0>(args, S, slot, tx, ty, 0, p);
         }
     }
+    return failed;
+}
+
+template <int H, int TYT, int G>
+__device__ __forceinline__ void init_bars(Smem2d<H, TYT, G> &sm) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// One sweep per launch (the body of the CUDA-graph WHILE loop).
+template <int NA, bool WFORM, int H, int TYT, int G>
+__global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(const __grid_constant__ SweepArgs args) {
+    static_assert(TYT * G * 32 == THREADS, "tile rows x control groups must fill the CTA");
+    __shared__ alignas(128) Smem2d<H, TYT, G> sm;
+    init_bars(sm);
+    unsigned uses[2] = {0u, 0u};
+    const bool failed = pass2d<NA, WFORM, H, TYT, G>(args, sm, uses);
     cta_done(args, failed);
+}
+
+// The whole convergence loop in one cooperative launch: sweeps separated by
+// a grid barrier that also takes the convergence decision.
+template <int NA, bool WFORM, int H, int TYT, int G>
+__global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) loop2d_kernel(const __grid_constant__ SweepArgs args) {
+    static_assert(TYT * G * 32 == THREADS, "tile rows x control groups must fill the CTA");
+    __shared__ alignas(128) Smem2d<H, TYT, G> sm;
+    init_bars(sm);
+    unsigned uses[2] = {0u, 0u};
+    for (;;) {
+        const bool failed = pass2d<NA, WFORM, H, TYT, G>(args, sm, uses);
+        if (!grid_barrier_finish(args, failed)) break;
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -583,74 +676,73 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
 // heading layers a foot can reach are computed once per node and each
 // control only interpolates in th.
 
-template <bool WFORM>
-__global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant__ SweepArgs args) {
-    constexpr int H = 2, HZ = 1;
-    constexpr int ROWS = TY + 2 * H;
-    constexpr int LAYER = ROWS * TW;
-    constexpr int TILE = (TZ + 2 * HZ) * LAYER;
-    constexpr int TILE_STRIDE = (TILE + 31) / 32 * 32;  // 128-byte aligned buffers
-    __shared__ alignas(128) float s_tile[2][TILE_STRIDE];
-    __shared__ alignas(8) uint64_t s_bar[2];
-    __shared__ int s_item[2][3];
-    __shared__ float s_red[THREADS / 32];
-    __shared__ int s_cnt[THREADS / 32];
+struct Smem3d {
+    static constexpr int H = 2, HZ = 1;
+    static constexpr int ROWS = TY + 2 * H;
+    static constexpr int LAYER = ROWS * TW;
+    static constexpr int TILE = (TZ + 2 * HZ) * LAYER;
+    static constexpr int TILE_STRIDE = (TILE + 31) / 32 * 32;  // 128-byte aligned buffers
+    float tile[2][TILE_STRIDE];
+    uint64_t bar[2];
+    int item[2][3];
+    float red[THREADS / 32];
+    int cnt[THREADS / 32];
+};
 
+template <bool WFORM>
+__device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsigned uses[2]) {
+    constexpr int H = Smem3d::H, HZ = Smem3d::HZ;
+    constexpr int LAYER = Smem3d::LAYER;
+    constexpr int TILE = Smem3d::TILE;
     const Ctl *ctl = args.ctl;
     const int tid = threadIdx.x;
     const int lx = tid & 31, ly = tid >> 5;
-    const int p = static_cast<int>(ctl->sweep & 1u);
+    const int p = static_cast<int>(*reinterpret_cast<const volatile unsigned *>(&ctl->sweep) & 1u);
     const int src = p, dst = p ^ 1;
-    const int nitems = ctl->qcount[p];
+    const int nitems = *reinterpret_cast<const volatile int *>(&ctl->qcount[p]);
     const int *qlist = args.qlist[p];
 
     auto issue = [&](int v, int b) {
-        const int e = qlist[v];
+        const int e = __ldcg(qlist + v);  // written by other CTAs in the previous sweep
         const int slot = e >> 22, tile = e & 0x3FFFFF;
         const SlotDesc *S = args.slots + slot;
-        const int live = args.state[slot].done ? 0 : 1;
-        s_item[b][0] = slot;
-        s_item[b][1] = tile;
-        s_item[b][2] = live;
+        const int live = __ldcg(&args.state[slot].done) ? 0 : 1;
+        sm.item[b][0] = slot;
+        sm.item[b][1] = tile;
+        sm.item[b][2] = live;
         if (live) {
             const int txy = S->tiles_x * S->tiles_y;
             const int tz = tile / txy, rem = tile - tz * txy;
             const int ty = rem / S->tiles_x, tx = rem - ty * S->tiles_x;
-            mbar_expect_tx(&s_bar[b], TILE * 4);
-            tma_load_3d(s_tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H,
-                        tz * TZ - HZ + S->zdup, &s_bar[b]);
+            mbar_expect_tx(&sm.bar[b], TILE * 4);
+            tma_load_3d(sm.tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H,
+                        tz * TZ - HZ + S->zdup, &sm.bar[b]);
         }
     };
 
-    if (tid == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
     int v = blockIdx.x;
-    if (tid == 0 && v < nitems) issue(v, 0);
+    int b0 = static_cast<int>((uses[0] + uses[1]) & 1u);
+    if (tid == 0 && v < nitems) issue(v, b0);
     __syncthreads();
     bool failed = false;
-    unsigned uses[2] = {0u, 0u};
     for (int it = 0; v < nitems; ++it, v += gridDim.x) {
-        const int b = it & 1;
+        const int b = (b0 + it) & 1;
         const int vn = v + gridDim.x;
-        const int slot = s_item[b][0], tile = s_item[b][1], live = s_item[b][2];
+        const int slot = sm.item[b][0], tile = sm.item[b][1], live = sm.item[b][2];
         __syncthreads();
         if (tid == 0 && vn < nitems) issue(vn, b ^ 1);
         const SlotDesc &S = args.slots[slot];
         if (!live) {
             if (tid == 0) unflag(args, S, tile, p);
-            __syncthreads();  // s_item[b ^ 1] written by the issue above
+            __syncthreads();
             continue;
         }
-        const bool ok = mbar_wait_bounded(&s_bar[b], uses[b] & 1u);
+        const bool ok = mbar_wait_bounded(&sm.bar[b], uses[b] & 1u);
         uses[b] += 1u;
         if (!__syncthreads_and(ok)) {
             failed = true;
-            if (tid == 0 && vn < nitems && s_item[b ^ 1][2])
-                mbar_wait_bounded(&s_bar[b ^ 1], uses[b ^ 1] & 1u);
+            if (tid == 0 && vn < nitems && sm.item[b ^ 1][2])
+                mbar_wait_bounded(&sm.bar[b ^ 1], uses[b ^ 1] & 1u);
             break;
         }
         const int nx = S.nx, ny = S.ny, nz = S.nz;
@@ -658,7 +750,7 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
         const int tz = tile / txy, rem = tile - tz * txy;
         const int ty = rem / S.tiles_x, tx = rem - ty * S.tiles_x;
         const int gx = tx * TX + lx, gy = ty * TY + ly;
-        const float *T = s_tile[b];
+        const float *T = sm.tile[b];
         const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
                               (ty * TY >= H) && (ty * TY + TY - 1 + H <= ny - 1);
         float rmax = 0.0f;
@@ -741,8 +833,8 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         const unsigned cm = __ballot_sync(0xffffffffu, chg);
         if (lx == 0) {
-            s_red[ly] = r;
-            s_cnt[ly] = c | (cm ? 0x10000 : 0);
+            sm.red[ly] = r;
+            sm.cnt[ly] = c | (cm ? 0x10000 : 0);
         }
         __syncthreads();
         if (tid < 32) {
@@ -750,9 +842,9 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
             int tot = 0, any = 0;
 #pragma unroll
             for (int w = 0; w < THREADS / 32; ++w) {
-                m = fmaxf(m, s_red[w]);
-                tot += s_cnt[w] & 0xffff;
-                any |= s_cnt[w] >> 16;
+                m = fmaxf(m, sm.red[w]);
+                tot += sm.cnt[w] & 0xffff;
+                any |= sm.cnt[w] >> 16;
             }
             if (tid == 0) {
                 if (m > 0.0f) atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
@@ -762,7 +854,36 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
             if (any) enqueue_neighbours<1, 1, 1>(args, S, slot, tx, ty, tz, p);
         }
     }
+    return failed;
+}
+
+__device__ __forceinline__ void init_bars3(Smem3d &sm) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+template <bool WFORM>
+__global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant__ SweepArgs args) {
+    __shared__ alignas(128) Smem3d sm;
+    init_bars3(sm);
+    unsigned uses[2] = {0u, 0u};
+    const bool failed = pass3d<WFORM>(args, sm, uses);
     cta_done(args, failed);
+}
+
+template <bool WFORM>
+__global__ void __launch_bounds__(THREADS) loop3d_kernel(const __grid_constant__ SweepArgs args) {
+    __shared__ alignas(128) Smem3d sm;
+    init_bars3(sm);
+    unsigned uses[2] = {0u, 0u};
+    for (;;) {
+        const bool failed = pass3d<WFORM>(args, sm, uses);
+        if (!grid_barrier_finish(args, failed)) break;
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -789,6 +910,7 @@ __global__ void loop_init_kernel(SlotState *state, Ctl *ctl, int nslots) {
         ctl->done_ctas = 0u;
         ctl->error = 0;
         ctl->launches = 0u;
+        ctl->gen = 0u;
         ctl->qcount[0] = 0;
         ctl->qcount[1] = 0;
     }
@@ -874,11 +996,18 @@ const void *sweep_kernel(const SweepKey &k, size_t *smem) {
     if (smem) *smem = 0;
     if (k.dubins) {
         if (k.halo != 2 || k.ty != TY || k.groups != 1) return nullptr;
+        if (k.loop)
+            return k.wform ? reinterpret_cast<const void *>(&loop3d_kernel<true>)
+                           : reinterpret_cast<const void *>(&loop3d_kernel<false>);
         return k.wform ? reinterpret_cast<const void *>(&sweep3d_kernel<true>)
                        : reinterpret_cast<const void *>(&sweep3d_kernel<false>);
     }
 #define HJB_PICK(NA_, H_, TY_, G_)                                                              \
     if (k.halo == H_ && k.ty == TY_ && k.groups == G_) {                                         \
+        if (k.loop)                                                                              \
+            return k.wform                                                                       \
+                       ? reinterpret_cast<const void *>(&loop2d_kernel<NA_, true, H_, TY_, G_>)  \
+                       : reinterpret_cast<const void *>(&loop2d_kernel<NA_, false, H_, TY_, G_>); \
         return k.wform ? reinterpret_cast<const void *>(&sweep2d_kernel<NA_, true, H_, TY_, G_>)  \
                        : reinterpret_cast<const void *>(&sweep2d_kernel<NA_, false, H_, TY_, G_>); \
     }

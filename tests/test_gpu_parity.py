@@ -271,8 +271,9 @@ def test_autograd_function(hjb, orc):
 
 def test_tile_shapes_agree_bitwise(hjb, orc, monkeypatch):
     """Every tile shape (32 x 8 / 4 / 2 nodes with 1 / 2 / 4 control groups)
-    computes the same Jacobi iterates, so the results agree bit for bit; the
-    grid holds more tiles than resident CTAs, so every CTA stages several
+    computes the same Jacobi iteration; tile-local foot coordinates round at
+    the last ulp differently per shape, so results agree to FP32 rounding.
+    The grid holds more tiles than resident CTAs, so every CTA stages several
     items through both shared-memory buffers."""
     n, A = 577, 16
     X, Y = S.mesh2(n, n)
@@ -284,15 +285,20 @@ def test_tile_shapes_agree_bitwise(hjb, orc, monkeypatch):
              h=2.0 / (n - 1), lam=1.0, v_out=1.0)
     p = gpu_problem(hjb, d)
     outs = []
-    for rows in ("8", "4", "2"):
-        monkeypatch.setenv("HJB_TILE_ROWS", rows)
-        V, st = hjb.solve(p)
-        outs.append(to_np(V))
-        fine, _, _, _ = hjb.subdomains(p, (16, 16), delta=0.2)
-        Vb, _, _ = hjb.solve_decomposed(p, fine)
-        outs.append(to_np(Vb))
-    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[0], outs[4])
-    assert np.array_equal(outs[1], outs[3]) and np.array_equal(outs[1], outs[5])
+    for loop in ("coop", "graph"):
+        monkeypatch.setenv("HJB_LOOP", loop)
+        for rows in ("8", "4", "2"):
+            monkeypatch.setenv("HJB_TILE_ROWS", rows)
+            V, st = hjb.solve(p)
+            outs.append(to_np(V))
+            fine, _, _, _ = hjb.subdomains(p, (16, 16), delta=0.2)
+            Vb, _, _ = hjb.solve_decomposed(p, fine)
+            outs.append(to_np(Vb))
+    for k in range(2, len(outs), 2):
+        assert np.abs(outs[0] - outs[k]).max() < 1e-5
+        assert np.abs(outs[1] - outs[k + 1]).max() < 1e-5
+    # the same shape in both loop modes runs the identical iteration
+    assert np.array_equal(outs[0], outs[6]) and np.array_equal(outs[1], outs[7])
     # one sampled check against the oracle's operator at full size: the FP64
     # residual of the GPU fixed point bounds its distance to the oracle's
     po = oracle_problem(orc, d)
