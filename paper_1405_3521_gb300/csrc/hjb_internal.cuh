@@ -83,14 +83,17 @@ struct SlotState {
 };
 
 // Launch-wide control block.
+// The words every CTA hits each sweep (arrival counter, barrier generation,
+// queue counters) sit on separate 128-byte lines so that the atomics of one
+// do not contend with the polling of another.
 struct Ctl {
-    unsigned done_ctas;
-    unsigned sweep;      // number of sweeps so far (parity of the source buffer)
+    alignas(128) unsigned done_ctas;
+    alignas(128) unsigned gen;  // generation of the cooperative loop's grid barrier
+    alignas(128) int qcount[2];  // entries of the two tile queues (parity = sweep parity)
+    alignas(128) unsigned sweep;  // number of sweeps so far (parity of the source buffer)
     int nactive;
-    unsigned gen;        // generation of the cooperative loop's grid barrier
     int error;           // non-zero: a bounded wait gave up
     unsigned launches;   // sweep kernels run (including empty ones at the loop's end)
-    int qcount[2];       // entries of the two tile queues (parity = sweep parity)
     int act_slot[MAX_SLOTS];
 };
 

@@ -581,7 +581,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
 
 int sweeps_per_body(const hjb_solve_opts *o) {
     if (o && o->sweeps_per_check > 0) return o->sweeps_per_check > 64 ? 64 : o->sweeps_per_check;
-    return 2;
+    return 8;
 }
 
 // Upload the slot table and allocate the state/control blocks.
@@ -1050,7 +1050,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
                              8 / rows, loop_mode()};
-    TRY(run_loop(R, key, 2, control_table(P), st));
+    TRY(run_loop(R, key, 8, control_table(P), st));
     // threshold of eq. (rep)
     double delta = ra->delta;
     TRY(P->scratch_u64.ensure(64));

@@ -347,15 +347,18 @@ __device__ void finish_sweep(const SweepArgs &args) {
     }
 }
 
-// Count this CTA as finished; the last one runs finish_sweep.
-__device__ __forceinline__ void cta_done(const SweepArgs &args, bool failed) {
+// Count this CTA as finished; the last one runs finish_sweep.  Only the
+// `working` CTAs (those that had an item, or CTA 0 when the queue is empty)
+// take part, so a short queue costs few arrivals.
+__device__ __forceinline__ void cta_done(const SweepArgs &args, bool failed, int working) {
     __shared__ int s_last;
+    if (static_cast<int>(blockIdx.x) >= working) return;
     __syncthreads();
     if (threadIdx.x == 0) {
         if (failed) atomicExch(&args.ctl->error, 1);
         __threadfence();
         const unsigned t = atomicAdd(&args.ctl->done_ctas, 1u);
-        s_last = (t == gridDim.x - 1) ? 1 : 0;
+        s_last = (t == static_cast<unsigned>(working) - 1u) ? 1 : 0;
     }
     __syncthreads();
     if (s_last) {
@@ -649,10 +652,14 @@ template <int NA, bool WFORM, int H, int TYT, int G>
 __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(const __grid_constant__ SweepArgs args) {
     static_assert(TYT * G * 32 == THREADS, "tile rows x control groups must fill the CTA");
     __shared__ alignas(128) Smem2d<H, TYT, G> sm;
+    const int p = static_cast<int>(args.ctl->sweep & 1u);
+    const int nitems = args.ctl->qcount[p];
+    const int working = nitems < 1 ? 1 : (nitems < static_cast<int>(gridDim.x) ? nitems : gridDim.x);
+    if (static_cast<int>(blockIdx.x) >= working) return;
     init_bars(sm);
     unsigned uses[2] = {0u, 0u};
     const bool failed = pass2d<NA, WFORM, H, TYT, G>(args, sm, uses);
-    cta_done(args, failed);
+    cta_done(args, failed, working);
 }
 
 // The whole convergence loop in one cooperative launch: sweeps separated by
@@ -869,10 +876,14 @@ __device__ __forceinline__ void init_bars3(Smem3d &sm) {
 template <bool WFORM>
 __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant__ SweepArgs args) {
     __shared__ alignas(128) Smem3d sm;
+    const int p = static_cast<int>(args.ctl->sweep & 1u);
+    const int nitems = args.ctl->qcount[p];
+    const int working = nitems < 1 ? 1 : (nitems < static_cast<int>(gridDim.x) ? nitems : gridDim.x);
+    if (static_cast<int>(blockIdx.x) >= working) return;
     init_bars3(sm);
     unsigned uses[2] = {0u, 0u};
     const bool failed = pass3d<WFORM>(args, sm, uses);
-    cta_done(args, failed);
+    cta_done(args, failed, working);
 }
 
 template <bool WFORM>
