@@ -425,13 +425,13 @@ int resolve_form(const hjb_problem *P, int use_w, bool *wform) {
     return HJB_OK;
 }
 
-// Convergence loop driver: 1 = one cooperative launch running every sweep
-// with grid barriers (default), 0 = a CUDA-graph WHILE loop of one-sweep
-// launches.  HJB_LOOP=graph|coop selects it.
+// Convergence loop driver: 0 = a CUDA-graph WHILE loop of one-sweep
+// launches (default), 1 = one cooperative launch running every sweep with
+// grid barriers.  HJB_LOOP=graph|coop selects it.
 int loop_mode() {
     const char *e = std::getenv("HJB_LOOP");
-    if (e && std::strcmp(e, "graph") == 0) return 0;
-    return 1;
+    if (e && std::strcmp(e, "coop") == 0) return 1;
+    return 0;
 }
 
 double default_tol(const hjb_problem *P, double h) {
