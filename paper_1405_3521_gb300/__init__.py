@@ -11,6 +11,7 @@ runs in the sm_103a CUDA library, which must be built first):
     solve_batch([p, ...], ...)      hjb_solve_batch
     backward(p, v, grad_v, wrt)     hjb_backward         (adjoint, pi frozen)
     point_values(p, v, pts)         hjb_point_values
+    solve_static(p, ...)            hjb_solve_static     (no device allocation)
     HJBSolve.apply(theta, spec)     autograd: V(theta) for s = exp(theta)
 
 Arrays may be CUDA torch tensors or host numpy arrays.  Outputs follow the
@@ -28,7 +29,7 @@ from ._capi import (HJB_DYN_DUBINS, HJB_DYN_SPEED_CURRENT, HJBError, NotConverge
                     hjb_ra_opts, hjb_solve_opts, hjb_stats)
 
 __all__ = ["Problem", "solve", "subdomains", "solve_decomposed", "solve_batch", "backward",
-           "point_values", "HJBSolve", "point_loss", "HJBError", "NotConverged", "library_path",
+           "point_values", "solve_static", "HJBSolve", "point_loss", "HJBError", "NotConverged", "library_path",
            "version"]
 
 
@@ -153,6 +154,7 @@ class Problem:
         tg.n_targets = self.n_targets
         tg.value_out = float(value_out)
         self._grid = g
+        self._desc = (g, dy, co, di, ct, tg)  # kept for hjb_solve_static
         self._handle = C.c_void_p()
         check(L.hjb_create(C.byref(g), C.byref(dy), C.byref(co), C.byref(di), C.byref(ct),
                            C.byref(tg), C.byref(self._handle)))
@@ -189,6 +191,20 @@ def solve(p: Problem, tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_p
     o = _opts(tol, max_iters, use_w_form, v_init, sweeps_per_check)
     rc = _capi.lib().hjb_solve(p.handle, C.byref(o), _ptr(out), C.byref(st), _stream(stream))
     check(rc, allow_not_converged)
+    return out, st.as_dict()
+
+
+def solve_static(p: Problem, tol=0.0, max_iters=0, v_init=None, out=None, stream=None):
+    """hjb_solve_static on the problem's descriptors: the full-domain solve
+    without any device allocation (device arrays only, bounded grid size).
+    Returns (V, stats dict)."""
+    out = p.empty(p.N) if out is None else out
+    st = hjb_stats()
+    o = _opts(tol, max_iters, -1, v_init, 0)
+    g, dy, co, di, ct, tg = p._desc
+    check(_capi.lib().hjb_solve_static(C.byref(g), C.byref(dy), C.byref(co), C.byref(di),
+                                       C.byref(ct), C.byref(tg), C.byref(o), _ptr(out),
+                                       C.byref(st), _stream(stream)))
     return out, st.as_dict()
 
 

@@ -27,8 +27,8 @@ HJB_DYN_SPEED_CURRENT = 0
 HJB_DYN_DUBINS = 1
 
 EXPORTS = ["hjb_create", "hjb_destroy", "hjb_solve", "hjb_subdomains", "hjb_solve_decomposed",
-           "hjb_solve_batch", "hjb_backward", "hjb_point_values", "hjb_last_error",
-           "hjb_version"]
+           "hjb_solve_batch", "hjb_backward", "hjb_point_values", "hjb_solve_static",
+           "hjb_last_error", "hjb_version"]
 
 
 class HJBError(RuntimeError):
@@ -113,6 +113,10 @@ def lib():
         L.hjb_backward.argtypes = [P, vp, vp, i, C.POINTER(hjb_solve_opts), vp,
                                    C.POINTER(hjb_stats), vp]
         L.hjb_point_values.argtypes = [P, vp, vp, i, vp, vp, vp]
+        L.hjb_solve_static.argtypes = [C.POINTER(hjb_grid), C.POINTER(hjb_dynamics),
+                                       C.POINTER(hjb_cost), C.POINTER(hjb_discount),
+                                       C.POINTER(hjb_controls), C.POINTER(hjb_target),
+                                       C.POINTER(hjb_solve_opts), vp, C.POINTER(hjb_stats), vp]
         L.hjb_last_error.restype = C.c_char_p
         L.hjb_version.restype = C.c_char_p
         for name in EXPORTS:

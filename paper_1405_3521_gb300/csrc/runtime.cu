@@ -1533,3 +1533,248 @@ int hjb_point_values(hjb_problem *P, const float *v, const float *points, int np
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free full-domain solve (hjb_solve_static).
+//
+// For callers that may not allocate device memory -- code running inside a
+// stream capture that must not add allocation nodes, real-time loops that
+// forbid cudaMalloc after start-up, plug-ins whose host application owns
+// every allocation -- this entry point keeps all of its working memory in
+// one file-scope device array.  The array is a fixed 4 MiB on every GPU that
+// loads the library, for as long as the process lives; it bounds the grid to
+// STATIC_MAX_NODES nodes.  Each call re-initialises everything it reads, so
+// no state carries over, but all calls share the array: calls that can
+// overlap on the GPU (different streams, different host threads) race.
+
+namespace {
+
+constexpr size_t STATIC_SCRATCH_BYTES = size_t(4) << 20;
+constexpr long long STATIC_MAX_NODES = 256LL * 1024;
+constexpr int STATIC_MAX_DEVICES = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+void *g_static_addr[STATIC_MAX_DEVICES];
+
+// Device address of the scratch array for the current device.  The host
+// name of a __device__ array is only a stand-in, so its address is looked up
+// once per device, with that device current.
+int static_scratch(unsigned char **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES)
+        return fail(HJB_ERR_UNSUPPORTED, "device ordinal %d beyond %d", dev, STATIC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(HJB_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                        cudaGetErrorString(e));
+        g_static_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_static_addr[dev]);
+    return HJB_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *cost,
+                                const hjb_discount *disc, const hjb_controls *controls,
+                                const hjb_target *target, const hjb_solve_opts *opts, float *v_out,
+                                hjb_stats *stats, void *stream) {
+    g_err.clear();
+    if (!grid || !dyn || !cost || !disc || !controls || !target || !v_out)
+        return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (grid->ndim != 2 || dyn->kind != HJB_DYN_SPEED_CURRENT || grid->periodic[0] ||
+        grid->periodic[1])
+        return fail(HJB_ERR_UNSUPPORTED, "the static solve handles 2D speed/current problems");
+    if (grid->n[0] < 2 || grid->n[1] < 2 || !(grid->hi[0] > grid->lo[0]) ||
+        !(grid->hi[1] > grid->lo[1]))
+        return fail(HJB_ERR_INVALID_ARG, "bad grid");
+    const long long N = static_cast<long long>(grid->n[0]) * grid->n[1];
+    if (N > STATIC_MAX_NODES)
+        return fail(HJB_ERR_INVALID_ARG,
+                    "grid of %lld nodes exceeds the static solve's maximum of %lld nodes", N,
+                    STATIC_MAX_NODES);
+    if (controls->count < 1 || controls->count > HJB_MAX_CONTROLS || controls->dim != 2 ||
+        !controls->a)
+        return fail(HJB_ERR_INVALID_ARG, "controls must be 1..%d 2D vectors", HJB_MAX_CONTROLS);
+    for (int j = 0; j < 2 * controls->count; ++j)
+        if (!std::isfinite(controls->a[j])) return fail(HJB_ERR_INVALID_ARG, "non-finite control");
+    if (!(disc->h > 0) || !(disc->lambda > 0) || !std::isfinite(disc->h) ||
+        !std::isfinite(disc->lambda))
+        return fail(HJB_ERR_INVALID_ARG, "h and lambda must be positive");
+    if (!target->labels || target->n_targets < 1 || target->n_targets > HJB_MAX_TARGETS)
+        return fail(HJB_ERR_INVALID_ARG, "bad target description");
+    if (!cost->l && !(cost->l_const > 0))
+        return fail(HJB_ERR_INVALID_ARG, "constant running cost must be positive");
+    if (dyn->speed && dyn->log_speed) return fail(HJB_ERR_INVALID_ARG, "give speed or log_speed");
+    if (opts && opts->max_iters < 0) return fail(HJB_ERR_INVALID_ARG, "max_iters < 0");
+    // every array must already be device memory: staging host data would allocate
+    const void *ptrs[6] = {dyn->speed, dyn->current, dyn->log_speed, cost->l, target->labels, v_out};
+    for (const void *q : ptrs)
+        if (q && !is_device_ptr(q))
+            return fail(HJB_ERR_INVALID_ARG, "the static solve takes device arrays only");
+    if (opts && opts->v_init && !is_device_ptr(opts->v_init))
+        return fail(HJB_ERR_INVALID_ARG, "the static solve takes device arrays only");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char *base = nullptr;
+    TRY(static_scratch(&base));
+
+    // layout of the scratch array
+    const int rows = hjbk::TY;
+    const int nx = grid->n[0], ny = grid->n[1];
+    const int pitch = (nx + 31) / 32 * 32;
+    const int tiles = ((nx + hjbk::TX - 1) / hjbk::TX) * ((ny + rows - 1) / rows);
+    size_t off = 0;
+    const size_t o_ctl = off;
+    off = align256(off + sizeof(Ctl));
+    const size_t o_state = off;
+    off = align256(off + sizeof(SlotState));
+    const size_t o_slot = off;
+    off = align256(off + sizeof(SlotDesc));
+    const size_t o_red = off;
+    off = align256(off + 64);
+    const size_t o_qlist = off;
+    off = align256(off + 2 * static_cast<size_t>(tiles) * sizeof(int));
+    const size_t o_qflag = off;
+    const size_t fb = (static_cast<size_t>(tiles) + 3) / 4 * 4;
+    off = align256(off + 2 * fb);
+    const size_t o_sexp = off;
+    if (dyn->log_speed) off = align256(off + N * sizeof(float));
+    const size_t vbytes = align256(static_cast<size_t>(pitch) * ny * sizeof(float));
+    const size_t o_v0 = off;
+    off += vbytes;
+    const size_t o_v1 = off;
+    off += vbytes;
+    if (off > STATIC_SCRATCH_BYTES)
+        return fail(HJB_ERR_INVALID_ARG, "grid %d x %d needs %zu bytes of the %zu-byte static scratch",
+                    nx, ny, off, STATIC_SCRATCH_BYTES);
+    Ctl *d_ctl = reinterpret_cast<Ctl *>(base + o_ctl);
+    SlotState *d_state = reinterpret_cast<SlotState *>(base + o_state);
+    SlotDesc *d_slot = reinterpret_cast<SlotDesc *>(base + o_slot);
+    unsigned *d_red = reinterpret_cast<unsigned *>(base + o_red);
+
+    // speed (exp of the log-speed field when given) and the largest foot
+    // displacement, which selects the interpolation halo
+    const float *speed = dyn->speed;
+    if (dyn->log_speed) {
+        float *sexp = reinterpret_cast<float *>(base + o_sexp);
+        hjbh::launch_exp(dyn->log_speed, sexp, N, st);
+        speed = sexp;
+    }
+    double dx[3] = {(grid->hi[0] - grid->lo[0]) / (nx - 1), (grid->hi[1] - grid->lo[1]) / (ny - 1),
+                    1.0};
+    double amax_x = 0, amax_y = 0;
+    for (int j = 0; j < controls->count; ++j) {
+        amax_x = std::fmax(amax_x, std::fabs(controls->a[2 * j]));
+        amax_y = std::fmax(amax_y, std::fabs(controls->a[2 * j + 1]));
+    }
+    unsigned hm[3] = {0u, 0u, 0u};
+    CK(cudaMemsetAsync(d_red, 0, 3 * sizeof(unsigned), st));
+    if (speed) hjbh::launch_absmax(speed, N, 1, 0, d_red, st);
+    if (dyn->current) {
+        hjbh::launch_absmax(dyn->current, N, 2, 0, d_red + 1, st);
+        hjbh::launch_absmax(dyn->current, N, 2, 1, d_red + 2, st);
+    }
+    CK(cudaMemcpyAsync(hm, d_red, sizeof hm, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float fm[3];
+    std::memcpy(fm, hm, sizeof fm);
+    const double smax = speed ? fm[0] : 1.0;
+    const double moff = std::fmax((smax * amax_x + fm[1]) * disc->h / dx[0],
+                                  (smax * amax_y + fm[2]) * disc->h / dx[1]);
+    if (!std::isfinite(moff)) return fail(HJB_ERR_INVALID_ARG, "a field is not finite");
+    const int need = static_cast<int>(std::floor(moff)) + 1;
+    if (need > 4) return fail(HJB_ERR_UNSUPPORTED, "feet move %.3f cells per step (< 4 supported)", moff);
+    const int halo = need <= 2 ? 2 : 4;
+
+    // the slot: the whole grid, W form when the running cost is constant
+    const bool wform = cost->l == nullptr;
+    const double lconst = cost->l ? 1.0 : cost->l_const;
+    const double beta = std::exp(-disc->lambda * disc->h);
+    const double gamma = -std::expm1(-disc->lambda * disc->h) / disc->lambda;
+    const double c = lconst / disc->lambda;
+    SlotDesc S;
+    std::memset(&S, 0, sizeof S);
+    S.V[0] = reinterpret_cast<float *>(base + o_v0);
+    S.V[1] = reinterpret_cast<float *>(base + o_v1);
+    S.speed = speed;
+    S.current = dyn->current;
+    S.cost = wform ? nullptr : cost->l;
+    S.labels = target->labels;
+    S.nx = nx;
+    S.ny = ny;
+    S.nz = 1;
+    S.pitch = pitch;
+    S.zstride = static_cast<long long>(pitch) * ny;
+    S.tiles_x = (nx + hjbk::TX - 1) / hjbk::TX;
+    S.tiles_y = (ny + rows - 1) / rows;
+    S.tiles_z = 1;
+    S.ntiles = tiles;
+    S.halo = halo;
+    S.hx = static_cast<float>(disc->h / dx[0]);
+    S.hy = static_cast<float>(disc->h / dx[1]);
+    S.beta = static_cast<float>(beta);
+    S.gamma = static_cast<float>(gamma);
+    S.gl = static_cast<float>(gamma * lconst);
+    S.vout = static_cast<float>(wform ? c - target->value_out : target->value_out);
+    S.vtarget = static_cast<float>(wform ? c : 0.0);
+    S.tol = static_cast<float>((opts && opts->tol > 0) ? opts->tol : 0.5e-4 * (1.0 - beta));
+    S.max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
+    TRY(encode_maps(S, 2, halo, rows));
+    CK(cudaMemcpyAsync(d_slot, &S, sizeof S, cudaMemcpyHostToDevice, st));
+    hjbk::ControlTable ctrl;
+    std::memset(&ctrl, 0, sizeof ctrl);
+    ctrl.count = controls->count;
+    for (int j = 0; j < controls->count; ++j) {
+        ctrl.ax[j] = controls->a[2 * j];
+        ctrl.ay[j] = controls->a[2 * j + 1];
+        ctrl.a2[j] = make_float2(ctrl.ax[j], ctrl.ay[j]);
+    }
+    const float c_over = static_cast<float>(c);
+    hjbh::launch_init_values(d_slot, 1, static_cast<int>(N), wform ? 1 : 0, c_over,
+                             opts ? opts->v_init : nullptr, st);
+    hjbh::launch_loop_init(d_slot, d_state, d_ctl, 1, st);
+    hjbk::SweepArgs args;
+    std::memset(&args, 0, sizeof args);
+    args.slots = d_slot;
+    args.state = d_state;
+    args.ctl = d_ctl;
+    args.qlist[0] = reinterpret_cast<int *>(base + o_qlist);
+    args.qlist[1] = args.qlist[0] + tiles;
+    args.qflag[0] = base + o_qflag;
+    args.qflag[1] = base + o_qflag + fb;
+    args.nslots = 1;
+    args.use_handle = 0;
+    args.stall_tol = 8.0f * 1.1920929e-7f;
+    args.ctrl = ctrl;
+    hjbh::launch_queue_init(d_slot, 1, tiles, d_ctl, args.qlist[0], args.qflag[0], args.qflag[1], st);
+    const hjbh::SweepKey key{0, wform ? 1 : 0, controls->count, halo, rows, 1, 1};
+    const void *fn = hjbh::sweep_kernel(key, nullptr);
+    if (!fn) return fail(HJB_ERR_UNSUPPORTED, "no sweep kernel for this configuration");
+    const int gridsz = hjbh::sweep_grid(key);
+    void *argv[1] = {&args};
+    CK(cudaLaunchCooperativeKernel(fn, dim3(gridsz), dim3(hjbk::THREADS), argv, 0, st));
+    hjbh::launch_extract(d_slot, d_state, 0, v_out, wform ? 1 : 0, c_over, st);
+    SlotState hs;
+    int herr[2] = {0, 0};
+    CK(cudaMemcpyAsync(&hs, d_state, sizeof hs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(herr, &d_ctl->error, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (stats) {
+        fill_stats(stats, hs);
+        stats->launches = (dyn->log_speed ? 1 : 0) + (speed ? 1 : 0) + (dyn->current ? 2 : 0) + 5;
+    }
+    if (herr[0]) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (!hs.converged)
+        return fail(HJB_ERR_NOT_CONVERGED, "not converged after %d iterations (residual %g)", hs.iters,
+                    hs.final_res);
+    return HJB_OK;
+}
