@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1025, help="grid side (default: the 1025^2 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="zermelo", choices=["zermelo", "dubins", "batch", "adjoint"],
+                    help="zermelo: the 1025^2 Zermelo problem (default, the headline line); "
+                         "dubins, batch, adjoint: the other hot-path rows, each printing its own line")
     ap.add_argument("--profile", choices=["full", "decomposed", "ra"], default=None,
                     help="run one solve of that path (after one warm-up) for a profiler; "
                          "prints per-solve statistics instead of the JSON line")
@@ -208,10 +211,185 @@ def run_reference(args):
     }))
 
 
+def _timed_steps(step, steps, warmup, flush, local):
+    """Run `warmup` untimed steps, then `steps` steps each between CUDA events
+    on the current stream (L2 flushed before each, outside the events), with
+    the clocks sampled meanwhile.  Returns (mean ms, last result, clocks)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    sampler.start()
+    res = None
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        res = step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps, res, clocks
+
+
+def _line(args, metric, value, unit, ms, config, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config}
+    line.update(extra)
+    print(json.dumps(line))
+
+
+def run_dubins(args, hjb, S, dev, flush, local):
+    """3D Dubins car, 256 x 256 x 128, reconstruction (stride 5, 5, 8) and the
+    decomposed solve against the full-domain solve."""
+    import numpy as np
+    d = S.c3()
+    nfree = int((d["labels"] == 0).sum())
+    p = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8), d["h"],
+                    dyn=hjb.HJB_DYN_DUBINS, periodic=(0, 0, 1), n_targets=d["ntargets"])
+    Vf, fst = hjb.solve(p)
+    iters_full = fst["iterations"]
+    ms_full, (Vf, fst), _ = _timed_steps(lambda: hjb.solve(p), args.steps, 1, flush, local)
+
+    def step():
+        fine, _, _, rst = hjb.subdomains(p, d["stride"], delta=-1.0, C_=0.0, M=-1.0)
+        Vb, per, tot = hjb.solve_decomposed(p, fine)
+        return Vb, rst, tot
+
+    ms, (Vb, rst, tot), clocks = _timed_steps(step, args.steps, args.warmup, flush, local)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6660.0)
+    ach = tot["node_updates"] * 9 / (tot["ms"] / 1e3) / 1e9  # V read+write 8 B, labels 1 B
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as orc
+        po = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"], dyn=1,
+                         periodic=(0, 0, 1), ntargets=d["ntargets"])
+        cores = os.cpu_count() or 1
+        V = orc.initial(po)
+        t0, sw = time.perf_counter(), 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            V, _ = orc.apply(po, V, nthreads=cores)
+            sw += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": nfree * sw / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d Jacobi sweeps of the FP64 oracle over the 256x256x128 grid in %.1f s"
+                         % (sw, el)}
+    _line(args, "node-updates/s to convergence, decomposed vs full-domain GPU (3D Dubins)",
+          nfree * iters_full / (ms / 1e3), UNIT, ms,
+          {"workload": "dubins-256x256x128-u3-8targets", "coarse_stride": list(d["stride"])},
+          full_domain={"iterations": iters_full, "ms": ms_full,
+                       "node_updates_per_s": nfree * iters_full / (ms_full / 1e3)},
+          decomposed={"ms_ra": rst["ms"], "ms_fine": tot["ms"], "max_subdomain_iters": tot["iterations"],
+                      "labelled_fraction": rst["labelled"] / d["labels"].size,
+                      "max_abs_diff_vs_full": float((Vb - Vf).abs().max().item())},
+          raw_node_updates_per_s=(rst["node_updates"] + tot["node_updates"]) / (ms / 1e3),
+          roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "kernel": "sweep3d_kernel (decomposed fine solve)",
+                    "bytes_per_node_update": 9},
+          cpu_baseline=cpu, gpu_launches=rst["launches"] + tot["launches"], clocks=clocks)
+
+
+def run_batch(args, hjb, S, dev, flush, local):
+    """512 independent square problems, sides ~ U{64..512}, one launch."""
+    import numpy as np
+    sides = S.c4_sides()
+    ds = [S.c4_problem(i, int(n)) for i, n in enumerate(sides)]
+    ps = [hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8),
+                      d["h"], speed=dev(d["speed"]), n_targets=d["ntargets"]) for d in ds]
+    nfree = [int((d["labels"] == 0).sum()) for d in ds]
+    ms, (Vs, sts), clocks = _timed_steps(lambda: hjb.solve_batch(ps), args.steps, args.warmup,
+                                         flush, local)
+    equiv = sum(nf * st["iterations"] for nf, st in zip(nfree, sts))
+    upd = sum(st["node_updates"] for st in sts)
+    peak = torch_sms(local) * 128 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
+    ach = upd * 32 * OPS_PER_CONTROL / (sts[0]["ms"] / 1e3)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as orc
+        cores = os.cpu_count() or 1
+        t0, done = time.perf_counter(), 0
+        idx = np.argsort(sides)[:: len(sides) // 16]  # a stratified sample over the sizes
+        for i in idx:
+            d = ds[i]
+            po = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"],
+                             speed=d["speed"], ntargets=d["ntargets"])
+            V = orc.initial(po)
+            for _ in range(3):
+                V, _ = orc.apply(po, V, nthreads=cores)
+            done += 3 * nfree[i]
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "3 Jacobi sweeps of the FP64 oracle on a size-stratified sample of the "
+                         "batch (%d node-updates in %.1f s)" % (done, el)}
+    _line(args, "node-updates/s to convergence, batch of 512 uneven problems in one launch",
+          equiv / (ms / 1e3), UNIT, ms,
+          {"workload": "batch-512-sides64to512-A32", "problems": len(ps),
+           "nodes": int(sum(int(n) ** 2 for n in sides))},
+          raw_node_updates_per_s=upd / (ms / 1e3),
+          max_iterations=max(st["iterations"] for st in sts),
+          roofline={"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s",
+                    "frac": ach / peak, "traffic": None, "kernel": "sweep2d_kernel<32,W,2>"},
+          cpu_baseline=cpu, gpu_launches=sts[0]["launches"], clocks=clocks)
+
+
+def run_adjoint(args, hjb, S, dev, flush, local):
+    """Gradient of the mean of V at 4096 points w.r.t. a 1025^2 log-speed field."""
+    import numpy as np
+    import torch
+    d = S.c5()
+    theta = dev(d["log_speed"])
+    p = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8), d["h"],
+                    log_speed=theta, n_targets=d["ntargets"])
+    V, fst = hjb.solve(p)
+    pts = dev(d["points"])
+    _, gV = hjb.point_values(p, V, pts)
+    ms, (g, st), clocks = _timed_steps(lambda: hjb.backward(p, V, gV, wrt=0), args.steps,
+                                       args.warmup, flush, local)
+    N = d["labels"].size
+    upd = N * st["iterations"]
+    hbm = measured_peaks().get("hbm_gbs", 6660.0)
+    # per node and iteration: lambda read 4 B, policy 1 B, s 4 B, 4 scattered
+    # atomics 16 B, residual pass (two lambda reads, g read, lambda write) 16 B
+    ach = upd * 41 / (st["ms"] / 1e3) / 1e9
+    _line(args, "adjoint node-updates/s to convergence (transposed fixed point, policy frozen)",
+          upd / (ms / 1e3), UNIT, ms, {"workload": "adjoint-1025x1025-A32-4096points"},
+          iterations=st["iterations"], forward_iterations=fst["iterations"],
+          roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None, "kernel": "adj_scatter + adj_resid",
+                    "bytes_per_node_iteration": 41},
+          cpu_baseline=None, gpu_launches=st["launches"], clocks=clocks)
+
+
+def torch_sms(local):
+    import torch
+    return torch.cuda.get_device_properties(local).multi_processor_count
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "zermelo":
+        import numpy as np
+        import torch
+        rank, world, local = env_rank()
+        torch.cuda.set_device(local)
+        import paper_1405_3521_gb300 as hjb
+        import synthetic as S
+        hjb._capi.lib()
+        dev = lambda a, dt=np.float32: torch.as_tensor(np.ascontiguousarray(np.asarray(a).astype(dt))).cuda()  # noqa
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        {"dubins": run_dubins, "batch": run_batch, "adjoint": run_adjoint}[args.workload](
+            args, hjb, S, dev, flush, local)
         return
     import numpy as np
     import torch
