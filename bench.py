@@ -80,6 +80,35 @@ def aggregate(step_ms, units_per_rank, dist=None, device="cuda"):
     return ms, float(u.item()) / (ms / 1e3)
 
 
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sweep2d_zermelo1025_dram_traffic.md")
+KERNEL_SOURCES = ("paper_1405_3521_gb300/csrc/sweep.cu", "paper_1405_3521_gb300/csrc/hjb_internal.cuh")
+
+
+def kernel_sources_sha256():
+    """Digest of the sources the 2D sweep kernel is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def sweep_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, or None
+    when the kernel sources changed after the counters were taken."""
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            kv = dict(line.strip("- \n").split(": ", 1) for line in f
+                      if line.startswith("- ") and ": " in line)
+        if kv.get("sources_sha256") != kernel_sources_sha256():
+            return None
+        return {"bytes_per_launch": float(kv["traffic_bytes_per_launch"]),
+                "node_updates_per_launch": float(kv["node_updates_per_launch"])}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -259,9 +288,9 @@ def run_dubins(args, hjb, S, dev, flush, local):
     def step():
         fine, _, _, rst = hjb.subdomains(p, d["stride"], delta=-1.0, C_=0.0, M=-1.0)
         Vb, per, tot = hjb.solve_decomposed(p, fine)
-        return Vb, rst, tot
+        return Vb, rst, tot, per
 
-    ms, (Vb, rst, tot), clocks = _timed_steps(step, args.steps, args.warmup, flush, local)
+    ms, (Vb, rst, tot, per), clocks = _timed_steps(step, args.steps, args.warmup, flush, local)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6660.0)
     ach = tot["node_updates"] * 9 / (tot["ms"] / 1e3) / 1e9  # V read+write 8 B, labels 1 B
@@ -287,7 +316,8 @@ def run_dubins(args, hjb, S, dev, flush, local):
                        "node_updates_per_s": nfree * iters_full / (ms_full / 1e3)},
           decomposed={"ms_ra": rst["ms"], "ms_fine": tot["ms"], "max_subdomain_iters": tot["iterations"],
                       "labelled_fraction": rst["labelled"] / d["labels"].size,
-                      "max_abs_diff_vs_full": float((Vb - Vf).abs().max().item())},
+                      "max_abs_diff_vs_full": float((Vb - Vf).abs().max().item()),
+                      "solved_subdomains": sum(1 for s in per if s["node_updates"] > 0)},
           raw_node_updates_per_s=(rst["node_updates"] + tot["node_updates"]) / (ms / 1e3),
           roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "traffic": None, "kernel": "sweep3d_kernel (decomposed fine solve)",
@@ -303,9 +333,11 @@ def run_batch(args, hjb, S, dev, flush, local):
     ps = [hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8),
                       d["h"], speed=dev(d["speed"]), n_targets=d["ntargets"]) for d in ds]
     nfree = [int((d["labels"] == 0).sum()) for d in ds]
+    # work unit: the sweeps plain (Jacobi) value iteration needs per problem
+    _, sts_j = hjb.solve_batch(ps, local_iters=1)
     ms, (Vs, sts), clocks = _timed_steps(lambda: hjb.solve_batch(ps), args.steps, args.warmup,
                                          flush, local)
-    equiv = sum(nf * st["iterations"] for nf, st in zip(nfree, sts))
+    equiv = sum(nf * st["iterations"] for nf, st in zip(nfree, sts_j))
     upd = sum(st["node_updates"] for st in sts)
     peak = torch_sms(local) * 128 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
     ach = upd * 32 * OPS_PER_CONTROL / (sts[0]["ms"] / 1e3)
@@ -335,6 +367,7 @@ def run_batch(args, hjb, S, dev, flush, local):
            "nodes": int(sum(int(n) ** 2 for n in sides))},
           raw_node_updates_per_s=upd / (ms / 1e3),
           max_iterations=max(st["iterations"] for st in sts),
+          max_iterations_jacobi=max(st["iterations"] for st in sts_j),
           roofline={"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s",
                     "frac": ach / peak, "traffic": None, "kernel": "sweep2d_kernel<32,W,2>"},
           cpu_baseline=cpu, gpu_launches=sts[0]["launches"], clocks=clocks)
@@ -441,16 +474,23 @@ def main():
         print(json.dumps(info))
         return
 
-    # full-domain reference solve on the same GPU (sweeps to the same stopping rule)
-    for _ in range(max(1, args.warmup)):
-        Vfull, fst = hjb.solve(p)
-    iters_full = fst["iterations"]
-    full_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        Vfull, fst = hjb.solve(p)
-        full_ms.append(fst["ms"])
+    # full-domain reference solves on the same GPU (same stopping rule): plain
+    # value iteration (Jacobi sweeps), whose sweep count fixes the work unit
+    # N_free x iters_full of every rate below, and the default solve
+    def full_times(local_iters):
+        for _ in range(max(1, args.warmup)):
+            V, st = hjb.solve(p, local_iters=local_iters)
+        t = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            V, st = hjb.solve(p, local_iters=local_iters)
+            t.append(st["ms"])
+        return V, st, statistics.median(t)
+
+    _, fst_j, full_ms_j = full_times(1)
+    iters_full = fst_j["iterations"]
+    Vfull, fst, full_ms = full_times(0)
 
     for _ in range(args.warmup):
         step(p)
@@ -504,6 +544,7 @@ def main():
     fmax = peaks.get("sm_max_mhz", 2070.0) * 1e6
     peak_ops = sms * 128 * fmax
     achieved = (tot["node_updates"] * 64 * OPS_PER_CONTROL) / (tot["ms"] / 1e3)
+    traffic = sweep_traffic()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle  # noqa: F401
@@ -518,14 +559,20 @@ def main():
                    "l2": "flushed between steps (256 MB write outside the event-timed region)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "raw_node_updates_per_s": raw * world,
-        "full_domain": {"iterations": iters_full, "ms": statistics.median(full_ms),
-                        "node_updates_per_s": nfree * iters_full / (statistics.median(full_ms) / 1e3)},
+        "full_domain": {"sweeps": fst["iterations"], "ms": full_ms,
+                        "node_updates_per_s": nfree * iters_full / (full_ms / 1e3)},
+        "full_domain_jacobi": {"sweeps": iters_full, "ms": full_ms_j,
+                               "node_updates_per_s": nfree * iters_full / (full_ms_j / 1e3)},
         "decomposed": {"ms_ra": ra_ms / args.steps, "ms_fine": loop_ms / args.steps,
                        "max_subdomain_iters": tot["iterations"],
                        "labelled_fraction": rst["labelled"] / N, "ra_iters": rst["iterations"],
                        "max_abs_diff_vs_full": check},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Top/s", "frac": achieved / peak_ops, "traffic": None,
+                     "unit": "Top/s", "frac": achieved / peak_ops,
+                     "traffic": traffic["bytes_per_launch"] if traffic else None,
+                     "traffic_unit": "DRAM bytes per sweep launch (ncu, warm L2)",
+                     "algorithmic_bytes_per_launch": (
+                         9 * traffic["node_updates_per_launch"] if traffic else None),
                      "kernel": "sweep2d_kernel<64,W,2> (decomposed fine solve)",
                      "peak_source": "SMs x 128 FP32 lanes x max SM clock (derived)"},
         "cpu_baseline": cpu,

@@ -138,27 +138,36 @@ int hjb_destroy(hjb_problem *p);
  *       Sec. 3); by the contraction bound the distance to the fixed point is
  *       then at most beta/(1-beta) tol.  tol <= 0 selects 0.5e-4 (1 - beta),
  *       which guarantees 1e-4 in exact arithmetic.
- *  max_iters: cap on applications of T (<= 0: 100,000).
+ *  max_iters: cap on sweeps (<= 0: 100,000).
  *  use_w_form: 1 = iterate on W = l/lambda - V (constant cost only),
  *       0 = iterate on V, -1 = automatic (W form when the cost is constant).
  *  v_init: optional warm start [N] (a previous solution), NULL = start from
  *       value_out on free nodes and 0 on targets (a supersolution).
  *  sweeps_per_check: sweeps between two convergence tests in the device loop
- *       (<= 0: library default). */
+ *       (<= 0: library default).
+ *  local_iters: applications of T to each staged tile per sweep (2D
+ *       problems; <= 0: default 4, 16 at most).  The first reads the previous
+ *       sweep's values; each further one reads the tile's own latest values
+ *       with the halo held (block Gauss-Seidel inside the tile).  Every
+ *       ordering of the updates has the same fixed point, and a sweep is still
+ *       a beta-contraction, so tol keeps its meaning.  1 is plain value
+ *       iteration (Jacobi).  Not used by the 3D kernel. */
 typedef struct {
     double tol;
     int max_iters;
     int use_w_form;
     const float *v_init;
     int sweeps_per_check;
+    int local_iters;
 } hjb_solve_opts;
 
 /* Statistics of one solve (per problem or per sub-domain). */
 typedef struct {
-    int iterations;        /* applications of T */
+    int iterations;        /* sweeps (with local_iters 1: applications of T) */
     int converged;         /* 1: the residual reached tol; 2: it stopped decreasing at the
                               FP32 rounding floor (accepted); 0: not converged */
-    long long node_updates;/* evaluations of T at free nodes (all controls) */
+    long long node_updates;/* evaluations of T at free nodes (all controls), every
+                              application inside a tile counted */
     double final_residual; /* last ||V^{n+1} - V^n||_inf */
     double ms;             /* device time of the call, milliseconds */
     long long ties;        /* label decisions within 1e-6 of the threshold */
@@ -228,7 +237,10 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
  *           HJB_DYN_SPEED_CURRENT):  lambda_i beta h s_i grad I[V](y_i) . a_pi(i)
  *  wrt = 1: grad_out = dL/dl for the cost field: lambda_i gamma.
  *  v [N]: the converged solution; grad_v [N]: dL/dV.  opts->tol bounds
- *  ||lambda^{n+1} - lambda^n||_inf.  stats (optional). */
+ *  ||lambda^{n+1} - lambda^n||_inf (default 1e-7); the iteration also stops
+ *  (stats->converged = 2) once that change is within 256 FP32 ulp of
+ *  max|lambda|, the summation-order floor of the scattered accumulation.
+ *  Otherwise HJB_ERR_NOT_CONVERGED after opts->max_iters.  stats (optional). */
 int hjb_backward(hjb_problem *p, const float *v, const float *grad_v, int wrt,
                  const hjb_solve_opts *opts, float *grad_out, hjb_stats *stats, void *stream);
 

@@ -82,13 +82,14 @@ def _stream(stream):
     return None
 
 
-def _opts(tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_per_check=0):
+def _opts(tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_per_check=0, local_iters=0):
     o = hjb_solve_opts()
     o.tol = float(tol)
     o.max_iters = int(max_iters)
     o.use_w_form = int(use_w_form)
     o.v_init = _ptr(v_init)
     o.sweeps_per_check = int(sweeps_per_check)
+    o.local_iters = int(local_iters)
     return o
 
 
@@ -184,23 +185,26 @@ class Problem:
 
 
 def solve(p: Problem, tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_per_check=0,
-          out=None, stream=None, allow_not_converged=False):
-    """Value iteration (Sec. 3).  Returns (V, stats dict)."""
+          out=None, stream=None, allow_not_converged=False, local_iters=0):
+    """Value iteration (Sec. 3).  Returns (V, stats dict).  local_iters:
+    applications of T per staged tile and sweep (1 = plain Jacobi value
+    iteration, 0 = library default)."""
     out = p.empty(p.N) if out is None else out
     st = hjb_stats()
-    o = _opts(tol, max_iters, use_w_form, v_init, sweeps_per_check)
+    o = _opts(tol, max_iters, use_w_form, v_init, sweeps_per_check, local_iters)
     rc = _capi.lib().hjb_solve(p.handle, C.byref(o), _ptr(out), C.byref(st), _stream(stream))
     check(rc, allow_not_converged)
     return out, st.as_dict()
 
 
-def solve_static(p: Problem, tol=0.0, max_iters=0, v_init=None, out=None, stream=None):
+def solve_static(p: Problem, tol=0.0, max_iters=0, v_init=None, out=None, stream=None,
+                 local_iters=0):
     """hjb_solve_static on the problem's descriptors: the full-domain solve
     without any device allocation (device arrays only, bounded grid size).
     Returns (V, stats dict)."""
     out = p.empty(p.N) if out is None else out
     st = hjb_stats()
-    o = _opts(tol, max_iters, -1, v_init, 0)
+    o = _opts(tol, max_iters, -1, v_init, 0, local_iters)
     g, dy, co, di, ct, tg = p._desc
     check(_capi.lib().hjb_solve_static(C.byref(g), C.byref(dy), C.byref(co), C.byref(di),
                                        C.byref(ct), C.byref(tg), C.byref(o), _ptr(out),
@@ -237,26 +241,26 @@ def subdomains(p: Problem, stride, delta=-1.0, C_=0.0, M=-1.0, q=1.0, h_coarse=0
 
 
 def solve_decomposed(p: Problem, fine_mask, tol=0.0, max_iters=0, use_w_form=-1,
-                     sweeps_per_check=0, out=None, stream=None):
+                     sweeps_per_check=0, out=None, stream=None, local_iters=0):
     """ISA steps 3-4 (Sec. 4).  Returns (Vbar, per-sub-domain stats, total stats)."""
     out = p.empty(p.N) if out is None else out
     per = (hjb_stats * p.n_targets)()
     tot = hjb_stats()
-    o = _opts(tol, max_iters, use_w_form, None, sweeps_per_check)
+    o = _opts(tol, max_iters, use_w_form, None, sweeps_per_check, local_iters)
     check(_capi.lib().hjb_solve_decomposed(p.handle, _ptr(fine_mask), C.byref(o), _ptr(out), per,
                                            C.byref(tot), _stream(stream)))
     return out, [s.as_dict() for s in per], tot.as_dict()
 
 
 def solve_batch(problems, tol=0.0, max_iters=0, use_w_form=-1, sweeps_per_check=0, outs=None,
-                stream=None):
+                stream=None, local_iters=0):
     """Many problems in one persistent launch.  Returns (list of V, list of stats)."""
     n = len(problems)
     outs = [p.empty(p.N) for p in problems] if outs is None else outs
     hs = (C.c_void_p * n)(*[p.handle.value for p in problems])
     os_ = (C.c_void_p * n)(*[_ptr(o) for o in outs])
     per = (hjb_stats * n)()
-    o = _opts(tol, max_iters, use_w_form, None, sweeps_per_check)
+    o = _opts(tol, max_iters, use_w_form, None, sweeps_per_check, local_iters)
     check(_capi.lib().hjb_solve_batch(hs, n, C.byref(o), os_, per, _stream(stream)))
     return outs, [s.as_dict() for s in per]
 

@@ -69,7 +69,8 @@ class hjb_target(C.Structure):
 
 class hjb_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("use_w_form", C.c_int),
-                ("v_init", C.c_void_p), ("sweeps_per_check", C.c_int)]
+                ("v_init", C.c_void_p), ("sweeps_per_check", C.c_int),
+                ("local_iters", C.c_int)]
 
 
 class hjb_stats(C.Structure):

@@ -158,21 +158,34 @@ __global__ void adj_resid(const __grid_constant__ AdjArgs A) {
     float *src = A.L[par];
     const float *dst = A.L[par ^ 1];
     const long long N = static_cast<long long>(A.ap.nx) * A.ap.ny;
-    float r = 0.0f;
+    float r = 0.0f, a = 0.0f;
     GRID_STRIDE(i, N) {
-        r = fmaxf(r, fabsf(dst[i] - src[i]));
+        const float d = dst[i];
+        r = fmaxf(r, fabsf(d - src[i]));
+        a = fmaxf(a, fabsf(d));
         src[i] = A.g[i];
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-    __shared__ float s_r[THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    }
+    __shared__ float s_r[THREADS / 32], s_a[THREADS / 32];
     __shared__ int s_last;
-    if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = r;
+    if ((threadIdx.x & 31) == 0) {
+        s_r[threadIdx.x >> 5] = r;
+        s_a[threadIdx.x >> 5] = a;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float m = s_r[0];
-        for (int w = 1; w < THREADS / 32; ++w) m = fmaxf(m, s_r[w]);
+        float m = s_r[0], ma = s_a[0];
+        for (int w = 1; w < THREADS / 32; ++w) {
+            m = fmaxf(m, s_r[w]);
+            ma = fmaxf(ma, s_a[w]);
+        }
+        // non-negative floats order like their bit patterns
         atomicMax(&ctl->res_bits, __float_as_uint(m));
+        atomicMax(&ctl->lam_bits, __float_as_uint(ma));
         __threadfence();
         s_last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1 : 0;
     }
@@ -180,27 +193,26 @@ __global__ void adj_resid(const __grid_constant__ AdjArgs A) {
     if (s_last && threadIdx.x == 0) {
         __threadfence();
         const float res = __uint_as_float(ctl->res_bits);
+        const float lam_max = __uint_as_float(ctl->lam_bits);
         ctl->res_bits = 0u;
+        ctl->lam_bits = 0u;
         ctl->iters += 1;
         ctl->final_res = res;
+        ctl->lam_max = lam_max;
         ctl->parity = par ^ 1;
         ctl->done_ctas = 0u;
-        // stopping: residual <= tol (1); or no decrease over 64 iterations,
-        // i.e. the FP32 rounding floor of the atomic accumulation, after at
-        // least a 1e3-fold reduction (2); otherwise the iteration cap (3)
-        if (ctl->iters == 1) ctl->first_res = res;
-        if (res < ctl->best_res) {
-            ctl->best_res = res;
-            ctl->stall = 0;
-        } else {
-            ctl->stall += 1;
-        }
+        // stopping: residual <= tol (1); or residual within the FP32 rounding
+        // floor of the atomic accumulation, 256 ulp of max|lambda| (2): there
+        // the sweep-to-sweep change is summation order alone; otherwise the
+        // iteration cap (3). The residual does not decrease monotonically
+        // (adjoint mass travels along the optimal trajectories to the target
+        // before it leaves), so no stagnation test is used.
         int go = 1;
         if (res <= ctl->tol) {
             ctl->converged = 1;
             go = 0;
-        } else if (ctl->stall >= 64) {
-            ctl->converged = ctl->best_res <= 1e-3f * ctl->first_res ? 2 : 3;
+        } else if (res <= 256.0f * 1.1920929e-7f * lam_max) {
+            ctl->converged = 2;
             go = 0;
         } else if (ctl->iters >= ctl->max_iters) {
             ctl->converged = 3;
@@ -234,9 +246,8 @@ __global__ void adj_init_kernel(const float *g, float *L0, float *L1, long long 
         ctl->tol = tol;
         ctl->max_iters = max_iters;
         ctl->error = 0;
-        ctl->best_res = INFINITY;
-        ctl->first_res = INFINITY;
-        ctl->stall = 0;
+        ctl->lam_bits = 0u;
+        ctl->lam_max = 0.0f;
     }
 }
 

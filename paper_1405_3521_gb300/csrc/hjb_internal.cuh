@@ -79,7 +79,8 @@ struct SlotState {
     float best_res;
     float final_res;
     unsigned long long updates;  // free-node evaluations of T
-    unsigned long long changed;  // (reserved)
+    int twin;                    // lower slot with the same node set (not solved), else -1
+    int pad_s;
 };
 
 // Launch-wide control block.
@@ -94,6 +95,7 @@ struct Ctl {
     int nactive;
     int error;           // non-zero: a bounded wait gave up
     unsigned launches;   // sweep kernels run (including empty ones at the loop's end)
+    unsigned twin_mask;  // slots (< 32) that duplicate a lower slot's node set
     int act_slot[MAX_SLOTS];
 };
 
@@ -109,6 +111,7 @@ struct SweepArgs {
     int use_handle;
     cudaGraphConditionalHandle handle;
     float stall_tol;
+    int local_iters;  // applications of T per tile and sweep (2D; >= 1)
     ControlTable ctrl;
 };
 
@@ -135,8 +138,11 @@ const void *sweep_kernel(const SweepKey &k, size_t *smem);
 int sweep_grid(const SweepKey &k);
 
 // Kernels used around the loop (see their definitions for the contracts).
+// diff (optional, decomposed solve): bit j of diff[k] is set iff the node
+// sets of sub-domains k and j differ somewhere.  A slot whose node set equals
+// that of a lower slot is marked as its twin and left out of the loop.
 void launch_loop_init(const hjbk::SlotDesc *slots, hjbk::SlotState *state, hjbk::Ctl *ctl,
-                      int nslots, cudaStream_t st);
+                      int nslots, cudaStream_t st, const uint32_t *diff = nullptr);
 // Queue of the first sweep: every tile of every slot that holds a node of it
 // (for masked slots: tile_bits carries the slot's bit); both flag arrays set.
 void launch_queue_init(const hjbk::SlotDesc *slots, int nslots, int max_tiles, hjbk::Ctl *ctl,
@@ -174,13 +180,17 @@ void launch_grad_max(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, 
 // ISA step 2: fine bitmask from coarse labels through the Kuhn simplices.
 void launch_project(const GridDims &fine, const GridDims &coarse, const int stride[3],
                     const uint32_t *coarse_labels, uint32_t *fine_mask, cudaStream_t st);
-// Per-tile OR of the sub-domain bits of the decomposed solve.
+// Per-tile OR of the sub-domain bits of the decomposed solve.  diff
+// (optional, [32], zeroed by the caller): bit j of diff[k] is OR-ed in where
+// the node sets of sub-domains k and j differ (m sub-domains, m <= 32).
 void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty,
-                      const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st);
-// ISA step 4: Vbar = min over the sub-domains containing each node.
+                      const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st,
+                      uint32_t *diff = nullptr, int m = 0);
+// ISA step 4: Vbar = min over the sub-domains containing each node.  Slots
+// in ctl->twin_mask (ctl optional) are skipped: their twin holds the same V.
 void launch_assemble(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int m,
                      const GridDims &fine, const uint32_t *mask, int wform, float c_over,
-                     float vout_v, float *out, cudaStream_t st);
+                     float vout_v, float *out, cudaStream_t st, const hjbk::Ctl *ctl = nullptr);
 // Largest |value| of a node field (float bits, atomicMax) -- used for the
 // interpolation halo.
 void launch_absmax(const float *x, long long n, int stride, int offset, unsigned *out,
@@ -214,10 +224,9 @@ struct AdjCtl {
     float tol;
     int max_iters;
     int error;
-    float best_res;
-    float first_res;
-    int stall;
-    int pad_[4];
+    unsigned lam_bits;
+    float lam_max;
+    int pad_[5];
 };
 
 // pi_i = argmin_j I[V](foot_j) (lowest index on ties), -1 on targets, -2

@@ -160,6 +160,9 @@ struct RunCtx {
     cudaGraphExec_t exec = nullptr;
     hjbh::SweepKey key{-1, -1, -1, -1, -1, -1, -1};
     int last_loop = 0;  // the last run used the cooperative loop kernel
+    const uint32_t *diff = nullptr;  // decomposed solve: membership differences (twins)
+    int local_iters = 1;             // applications of T per tile and sweep (2D)
+    int li_in_graph = -1;
     int spb = 0;
     const void *graph_slots = nullptr;
     const void *graph_q = nullptr;
@@ -502,7 +505,19 @@ int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows) {
     return HJB_OK;
 }
 
+// Applications of T per tile and sweep in the 2D kernels: opts->local_iters
+// when positive, else HJB_LOCAL_ITERS, else 4 (clamped to 1..16).
+int local_iters(const hjb_solve_opts *o) {
+    static const int dflt = [] {
+        const char *e = std::getenv("HJB_LOCAL_ITERS");
+        return e ? std::atoi(e) : 4;
+    }();
+    const int v = (o && o->local_iters > 0) ? o->local_iters : dflt;
+    return v < 1 ? 1 : (v > 16 ? 16 : v);
+}
+
 void set_queue_args(const RunCtx &R, hjbk::SweepArgs &a) {
+    a.local_iters = R.local_iters;
     const size_t fb = (static_cast<size_t>(R.qtiles) + 3) / 4 * 4;
     a.qlist[0] = R.qlist.as<int>();
     a.qlist[1] = R.qlist.as<int>() + R.qtiles;
@@ -517,7 +532,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     const int n = static_cast<int>(R.slots.size());
     if (R.exec && R.key.dubins == key.dubins && R.key.wform == key.wform && R.key.na == key.na &&
         R.key.halo == key.halo && R.key.ty == key.ty && R.key.groups == key.groups &&
-        R.key.loop == key.loop &&
+        R.key.loop == key.loop && R.li_in_graph == R.local_iters &&
         R.spb == spb && R.graph_slots == R.d_slots.p &&
         R.graph_q == R.qlist.p && R.graph_f == R.qflag.p &&
         R.graph_nslots == n && std::memcmp(&R.ctrl_in_graph, &ctrl, sizeof ctrl) == 0)
@@ -571,6 +586,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     CK(cudaGraphInstantiate(&R.exec, R.graph, 0));
     R.key = key;
     R.spb = spb;
+    R.li_in_graph = R.local_iters;
     R.graph_slots = R.d_slots.p;
     R.graph_q = R.qlist.p;
     R.graph_f = R.qflag.p;
@@ -601,10 +617,11 @@ int upload_slots(RunCtx &R, cudaStream_t st) {
 
 // Run the convergence loop (graph), after init values and loop init.
 int run_loop(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlTable &ctrl,
-             cudaStream_t st) {
+             cudaStream_t st, int local = 1) {
     const int n = static_cast<int>(R.slots.size());
+    R.local_iters = key.dubins ? 1 : local;
     hjbh::launch_loop_init(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), R.d_ctl.as<Ctl>(),
-                           n, st);
+                           n, st, R.diff);
     {
         hjbk::SweepArgs qa;
         set_queue_args(R, qa);
@@ -932,7 +949,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_ou
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
                              8 / rows, loop_mode()};
     const hjbk::ControlTable ctrl = control_table(P);
-    TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st));
+    TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, local_iters(opts)));
     hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
                          static_cast<float *>(out.dev()), wform, c_over, st);
     CK(cudaEventRecord(R.ev1, st));
@@ -1050,7 +1067,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
                              8 / rows, loop_mode()};
-    TRY(run_loop(R, key, 8, control_table(P), st));
+    TRY(run_loop(R, key, 8, control_table(P), st, local_iters(nullptr)));
     // threshold of eq. (rep)
     double delta = ra->delta;
     TRY(P->scratch_u64.ensure(64));
@@ -1167,7 +1184,9 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     const int tiles_y = (g.ny + rows - 1) / rows;
     const int tiles_z = nd > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
     const int nt = tiles_x * tiles_y * tiles_z;
-    TRY(P->tile_bits.ensure(nt * sizeof(uint32_t)));
+    // tile bits, then 32 words of pairwise membership differences
+    TRY(P->tile_bits.ensure((nt + 32) * sizeof(uint32_t)));
+    uint32_t *diff = P->tile_bits.as<uint32_t>() + nt;
     for (int k = 0; k < m; ++k) {
         fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows);
         R.slots[k].mask = mask;
@@ -1181,16 +1200,22 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     TRY(out.init(v_out, P->N * sizeof(float), &P->out_stage));
     const float c_over = static_cast<float>(P->l_const / P->lambda);
     CK(cudaEventRecord(R.ev0, st));
+    CK(cudaMemsetAsync(diff, 0, 32 * sizeof(uint32_t), st));
     hjbh::launch_tile_bits(fine, tiles_x, tiles_y, tiles_z, rows, mask,
-                           P->tile_bits.as<uint32_t>(), st);
+                           P->tile_bits.as<uint32_t>(), st, diff, m);
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
                              8 / rows, loop_mode()};
-    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P), st));
+    // sub-domains with equal node sets are solved once (V_k depends on the
+    // node set alone: its targets are the target nodes inside it)
+    R.diff = diff;
+    const int lrc = run_loop(R, key, sweeps_per_body(opts), control_table(P), st, local_iters(opts));
+    R.diff = nullptr;
+    TRY(lrc);
     hjbh::launch_assemble(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, fine, mask,
                           wform ? 1 : 0, c_over, static_cast<float>(P->value_out),
-                          static_cast<float *>(out.dev()), st);
+                          static_cast<float *>(out.dev()), st, R.d_ctl.as<Ctl>());
     CK(cudaEventRecord(R.ev1, st));
     TRY(out.finish(st));
     int err = 0;
@@ -1203,7 +1228,15 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     hjb_stats tot;
     std::memset(&tot, 0, sizeof tot);
     for (int k = 0; k < m; ++k) {
-        const SlotState &s = R.h_state[k];
+        SlotState s = R.h_state[k];
+        if (s.twin >= 0 && s.twin < k) {
+            // solved as its twin: same iterate, no node-updates of its own
+            const SlotState &t = R.h_state[s.twin];
+            s.iters = t.iters;
+            s.converged = t.converged;
+            s.final_res = t.final_res;
+            s.updates = 0ull;
+        }
         if (per_subdomain) {
             fill_stats(&per_subdomain[k], s);
             per_subdomain[k].ms = ms;
@@ -1300,7 +1333,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
                              nullptr, st);
     const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P0->na, halo, rows,
                              8 / rows, loop_mode()};
-    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st));
+    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st, local_iters(opts)));
     for (int i = 0; i < count; ++i) {
         TRY(outs[i].init(v_out[i], problems[i]->N * sizeof(float), &problems[i]->out_stage));
         hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), i,
@@ -1753,6 +1786,7 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     args.nslots = 1;
     args.use_handle = 0;
     args.stall_tol = 8.0f * 1.1920929e-7f;
+    args.local_iters = local_iters(opts);
     args.ctrl = ctrl;
     hjbh::launch_queue_init(d_slot, 1, tiles, d_ctl, args.qlist[0], args.qflag[0], args.qflag[1], st);
     const hjbh::SweepKey key{0, wform ? 1 : 0, controls->count, halo, rows, 1, 1};

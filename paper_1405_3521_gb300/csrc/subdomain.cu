@@ -204,27 +204,55 @@ __global__ void project_kernel(hjbh::GridDims fine, hjbh::GridDims coarse, int r
 // OR of the sub-domain bits over the nodes of each tile (one block per tile;
 // tiles are 32 x ty (x TZ in 3D) nodes).
 __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int ty_rows,
-                                 const uint32_t *mask, uint32_t *tile_bits) {
+                                 const uint32_t *mask, uint32_t *tile_bits, uint32_t *diff,
+                                 int m) {
     const int t = blockIdx.x;
     const int txy = tiles_x * tiles_y;
     const int tz = t / txy, rem = t - tz * txy;
     const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
     const int x = tx * TX + (threadIdx.x & 31);
+    const uint32_t mbits = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
     uint32_t bits = 0u;
+    // dk[k]: sub-domains whose membership differs from k's at a node seen here
+    uint32_t dk[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) dk[k] = 0u;
     const int zn = g.ndim > 2 ? TZ : 1;
     for (int r = threadIdx.x >> 5; r < ty_rows * zn; r += THREADS / 32) {
         const int y = ty * ty_rows + r % ty_rows;
         const int z = g.ndim > 2 ? tz * TZ + r / ty_rows : 0;
-        if (x < g.n[0] && y < g.n[1] && (g.ndim < 3 || z < g.n[2])) bits |= mask[flat(g, x, y, z)];
+        if (x < g.n[0] && y < g.n[1] && (g.ndim < 3 || z < g.n[2])) {
+            const uint32_t v = mask[flat(g, x, y, z)];
+            bits |= v;
+            if (diff) {
+                const uint32_t b = v & mbits;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) dk[k] |= ((b >> k) & 1u) ? (~b & mbits) : b;
+            }
+        }
     }
     bits = __reduce_or_sync(0xffffffffu, bits);
     __shared__ uint32_t s[THREADS / 32];
+    __shared__ uint32_t s_d[THREADS / 32][32];
     if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = bits;
+    if (diff) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t w = __reduce_or_sync(0xffffffffu, dk[k]);
+            if ((threadIdx.x & 31) == 0) s_d[threadIdx.x >> 5][k] = w;
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t b = 0u;
         for (int w = 0; w < THREADS / 32; ++w) b |= s[w];
         tile_bits[t] = b;
+    }
+    if (diff && threadIdx.x < 32) {
+        uint32_t w = 0u;
+        for (int q = 0; q < THREADS / 32; ++q) w |= s_d[q][threadIdx.x];
+        // most words saturate early: skip the atomic when it adds nothing
+        if (w & ~__ldcg(&diff[threadIdx.x])) atomicOr(&diff[threadIdx.x], w);
     }
 }
 
@@ -232,12 +260,13 @@ __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int
 // W form), value_out on nodes that belong to no sub-domain.
 __global__ void assemble_kernel(const SlotDesc *slots, const SlotState *state, int m,
                                 hjbh::GridDims g, const uint32_t *mask, int wform, float c_over,
-                                float vout_v, float *out) {
+                                float vout_v, float *out, const Ctl *ctl) {
     const long long N = count(g);
+    const uint32_t skip = ctl ? ctl->twin_mask : 0u;
     GRID_STRIDE(i, N) {
         int c[3];
         unflat(g, i, c);
-        uint32_t bits = mask[i];
+        uint32_t bits = mask[i] & ~skip;
         if (m < 32) bits &= (1u << m) - 1u;
         float best = wform ? -INFINITY : INFINITY;
         while (bits) {
@@ -327,17 +356,18 @@ void launch_project(const GridDims &fine, const GridDims &coarse, const int stri
 }
 
 void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty,
-                      const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st) {
+                      const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st, uint32_t *diff,
+                      int m) {
     const int nt = tiles_x * tiles_y * tiles_z;
-    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, ty, mask, tile_bits);
+    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, ty, mask, tile_bits, diff, m);
 }
 
 void launch_assemble(const SlotDesc *slots, const SlotState *state, int m, const GridDims &fine,
                      const uint32_t *mask, int wform, float c_over, float vout_v, float *out,
-                     cudaStream_t st) {
+                     cudaStream_t st, const Ctl *ctl) {
     long long N = static_cast<long long>(fine.n[0]) * fine.n[1] * (fine.ndim > 2 ? fine.n[2] : 1);
     assemble_kernel<<<blocks_for(N), THREADS, 0, st>>>(slots, state, m, fine, mask, wform, c_over,
-                                                      vout_v, out);
+                                                      vout_v, out, ctl);
 }
 
 void launch_absmax(const float *x, long long n, int stride, int offset, unsigned *out,

@@ -53,6 +53,12 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Orders this thread's generic-proxy shared-memory writes before later
+// async-proxy (TMA) writes to the same buffer.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
@@ -552,7 +558,7 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
             break;
         }
         // pair layout: (raw[r][c], raw[r][c+1]) for the TW-1 columns a foot can use
-        const float *T = sm.tile[b];
+        float *T = sm.tile[b];
         for (int i = tid; i < ROWS * (TW - 1); i += THREADS) {
             const int r = i / (TW - 1), c = i - r * (TW - 1);
             sm.pair[r * PW + c] = make_float2(T[r * TW + c], T[r * TW + c + 1]);
@@ -563,8 +569,9 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
         const float vold = T[(ly + H) * TW + lx + XPAD];
         const long long gi = static_cast<long long>(gy) * nx + gx;
         const bool isfree = (gx < nx) && (gy < ny) && node_class(S, gi) == CLS_FREE;
-        __syncthreads();
-        float best = WFORM ? -INFINITY : INFINITY;
+        const bool mine = isfree && grp == 0;  // group 0 owns the node's result
+        float2 S2 = make_float2(0.0f, 0.0f), O02 = S2;
+        float add = S.gl;
         if (isfree) {
             const float s = S.speed ? S.speed[gi] : 1.0f;
             float cx = 0.0f, cy = 0.0f;
@@ -573,42 +580,61 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
                 cx = c.x;
                 cy = c.y;
             }
-            const float2 S2 = make_float2(s * S.hx, s * S.hy);
-            const float2 O02 = make_float2(cx * S.hx, cy * S.hy);
-            const float2 BASE2 = make_float2(static_cast<float>(lx + XPAD),
-                                             static_cast<float>(ly + H + 1));
-            const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
-                                  (ty * TYT >= H) && (ty * TYT + TYT - 1 + H <= ny - 1);
-            if (interior) {
-                best = controls_interior<NA, G, WFORM>(grp, args.ctrl, K, S2,
-                                                      __fadd2_rn(BASE2, O02), best);
-            } else {
-                EdgeBounds eb;
-                eb.lox = -static_cast<float>(gx);
-                eb.hix = static_cast<float>(nx - 1 - gx);
-                eb.loy = -static_cast<float>(gy);
-                eb.hiy = static_cast<float>(ny - 1 - gy);
-                best = controls_edge<NA, G, WFORM>(grp, args.ctrl, K, S2, O02, eb, BASE2, S.vout,
-                                                  best);
-            }
+            S2 = make_float2(s * S.hx, s * S.hy);
+            O02 = make_float2(cx * S.hx, cy * S.hy);
+            if (!WFORM && S.cost) add = S.gamma * S.cost[gi];
         }
-        if constexpr (G > 1) {
-            sm.part[grp][ly][lx] = best;
-            __syncthreads();
-            if (grp == 0) {
-#pragma unroll
-                for (int q = 1; q < G; ++q) best = pick<WFORM>(best, sm.part[q][ly][lx]);
-            }
-        }
-        const bool mine = isfree && grp == 0;  // group 0 owns the node's result
+        const float2 BASE2 = make_float2(static_cast<float>(lx + XPAD),
+                                         static_cast<float>(ly + H + 1));
+        const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
+                              (ty * TYT >= H) && (ty * TYT + TYT - 1 + H <= ny - 1);
+        __syncthreads();
+        // args.local_iters applications of T to the tile's nodes, the halo
+        // held at the previous sweep's values: each application reads the
+        // tile's latest values (a block Gauss-Seidel step; same fixed point)
         float vnew = vold;
-        if (mine) {
-            if (WFORM)
-                vnew = S.beta * best;
-            else
-                vnew = fmaf(S.beta, best, S.cost ? S.gamma * S.cost[gi] : S.gl);
-            S.V[dst][static_cast<long long>(gy) * S.pitch + gx] = vnew;
+        int li = 0;  // applications done
+        for (;;) {
+            float best = WFORM ? -INFINITY : INFINITY;
+            if (isfree) {
+                if (interior) {
+                    best = controls_interior<NA, G, WFORM>(grp, args.ctrl, K, S2,
+                                                          __fadd2_rn(BASE2, O02), best);
+                } else {
+                    EdgeBounds eb;
+                    eb.lox = -static_cast<float>(gx);
+                    eb.hix = static_cast<float>(nx - 1 - gx);
+                    eb.loy = -static_cast<float>(gy);
+                    eb.hiy = static_cast<float>(ny - 1 - gy);
+                    best = controls_edge<NA, G, WFORM>(grp, args.ctrl, K, S2, O02, eb, BASE2,
+                                                      S.vout, best);
+                }
+            }
+            if constexpr (G > 1) {
+                sm.part[grp][ly][lx] = best;
+                __syncthreads();
+                if (grp == 0) {
+#pragma unroll
+                    for (int q = 1; q < G; ++q) best = pick<WFORM>(best, sm.part[q][ly][lx]);
+                }
+            }
+            const float vprev = vnew;
+            if (mine) vnew = WFORM ? S.beta * best : fmaf(S.beta, best, add);
+            if (++li >= args.local_iters) break;
+            // all reads of the pairs done; stop early once the tile is stable
+            if (!__syncthreads_or(mine && vnew != vprev)) break;
+            if (mine) {
+                T[(ly + H) * TW + lx + XPAD] = vnew;
+                fence_proxy_async_smem();  // the buffer takes a later TMA copy
+            }
+            __syncthreads();
+            for (int i = tid; i < TYT * (TX + 1); i += THREADS) {
+                const int r = H + i / (TX + 1), c = XPAD - 1 + i % (TX + 1);
+                sm.pair[r * PW + c] = make_float2(T[r * TW + c], T[r * TW + c + 1]);
+            }
+            __syncthreads();
         }
+        if (mine) S.V[dst][static_cast<long long>(gy) * S.pitch + gx] = vnew;
         const float r = warp_max(mine ? fabsf(vnew - vold) : 0.0f);
         const unsigned fm = __ballot_sync(0xffffffffu, mine);
         const unsigned cm = __ballot_sync(0xffffffffu, mine && (vnew != vold));
@@ -628,7 +654,7 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
             }
             if (tid == 0) {
                 if (m > 0.0f) atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
-                atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot));
+                atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot) * li);
                 unflag(args, S, tile, p);
             }
             if (chg) enqueue_neighbours<1, RY, 0>(args, S, slot, tx, ty, 0, p);
@@ -900,7 +926,7 @@ __global__ void __launch_bounds__(THREADS) loop3d_kernel(const __grid_constant__
 // --------------------------------------------------------------------------
 // Helpers around the loop.
 
-__global__ void loop_init_kernel(SlotState *state, Ctl *ctl, int nslots) {
+__global__ void loop_init_kernel(SlotState *state, Ctl *ctl, int nslots, const uint32_t *diff) {
     for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
         SlotState &st = state[i];
         st.res_bits = 0u;
@@ -912,11 +938,28 @@ __global__ void loop_init_kernel(SlotState *state, Ctl *ctl, int nslots) {
         st.best_res = INFINITY;
         st.final_res = 0.0f;
         st.updates = 0ull;
-        st.changed = 0ull;
-        ctl->act_slot[i] = i;
+        // a sub-domain with the node set of a lower one has the same V
+        int twin = -1;
+        if (diff && i < 32)
+            for (int j = 0; j < i; ++j)
+                if (!((diff[j] >> i) & 1u)) {
+                    twin = j;
+                    break;
+                }
+        st.twin = twin;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        ctl->nactive = nslots;
+        int na = 0;
+        unsigned tm = 0u;
+        for (int i = 0; i < nslots; ++i) {
+            if (state[i].twin >= 0)
+                tm |= 1u << i;
+            else
+                ctl->act_slot[na++] = i;
+        }
+        ctl->twin_mask = tm;
+        ctl->nactive = na;
         ctl->sweep = 0u;
         ctl->done_ctas = 0u;
         ctl->error = 0;
@@ -934,11 +977,12 @@ __global__ void queue_init_kernel(const SlotDesc *slots, Ctl *ctl, int *qlist0, 
     const int slot = blockIdx.y;
     const SlotDesc &S = slots[slot];
     const int lane = threadIdx.x & 31;
+    const bool twin = slot < 32 && ((ctl->twin_mask >> slot) & 1u);
     for (int t0 = blockIdx.x * blockDim.x; t0 < S.ntiles; t0 += gridDim.x * blockDim.x) {
         const int t = t0 + threadIdx.x;
         bool member = false;
         if (t < S.ntiles) {
-            member = S.tile_bits == nullptr || ((S.tile_bits[t] >> S.mask_bit) & 1u);
+            member = !twin && (S.tile_bits == nullptr || ((S.tile_bits[t] >> S.mask_bit) & 1u));
             qflag0[S.qbase + t] = member ? 1 : 0;
             qflag1[S.qbase + t] = 0;
         }
@@ -1057,8 +1101,8 @@ int sweep_grid(const SweepKey &k) {
 }
 
 void launch_loop_init(const SlotDesc * /*slots*/, SlotState *state, Ctl *ctl, int nslots,
-                      cudaStream_t st) {
-    loop_init_kernel<<<1, THREADS, 0, st>>>(state, ctl, nslots);
+                      cudaStream_t st, const uint32_t *diff) {
+    loop_init_kernel<<<1, THREADS, 0, st>>>(state, ctl, nslots, diff);
 }
 
 void launch_queue_init(const SlotDesc *slots, int nslots, int max_tiles, Ctl *ctl, int *qlist0,

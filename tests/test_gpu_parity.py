@@ -38,9 +38,10 @@ def test_c1_full_solve(hjb, orc, wform):
     err = np.abs(to_np(V) - Vo).max()
     assert st["converged"] == 1
     assert err < TOL_V, err
-    # quiescent tiles are skipped (exactly), so at most every free node per sweep
+    # quiescent tiles are skipped (exactly), so at most every free node per
+    # application, with 4 applications per staged tile and sweep by default
     nfree = int((d["labels"] == 0).sum())
-    assert 0 < st["node_updates"] <= st["iterations"] * nfree
+    assert 0 < st["node_updates"] <= st["iterations"] * nfree * 4
 
 
 @pytest.mark.parametrize("nx,ny,A,cur", [(67, 45, 16, True), (33, 97, 7, False),
@@ -196,6 +197,44 @@ def test_decomposed_matches_oracle_isa(hjb, orc, which):
     assert np.array_equal(to_np(Vbar_h), to_np(Vbar))
 
 
+def test_decomposed_equal_subdomains_solved_once(hjb, orc):
+    """Sub-domains with equal node sets share one solve (their V_k is the same
+    function of the node set); Vbar still matches the oracle's ISA, which
+    solves every copy."""
+    d = S.c1(n=81)
+    stride = (4, 4)
+    po = oracle_problem(orc, d)
+    _, lab_o, _ = orc.ra(po, stride, 0.15, tol=1e-11)
+    fine = orc.project(po, stride, lab_o).astype(np.uint32)
+    b0 = fine & np.uint32(1)
+    fine = (fine & ~np.uint32(0b1100)) | (b0 << np.uint32(2)) | (b0 << np.uint32(3))
+    Vbar_o, _, its_o, _ = orc.isa(po, fine, tol=1e-11, nthreads=8)
+    p = gpu_problem(hjb, d)
+    Vbar, per, tot = hjb.solve_decomposed(p, fine)
+    assert np.abs(to_np(Vbar) - Vbar_o).max() < TOL_V
+    assert tot["converged"] == 1
+    assert per[2]["node_updates"] == 0 and per[3]["node_updates"] == 0
+    assert per[2]["iterations"] == per[0]["iterations"] == per[3]["iterations"]
+    assert per[0]["node_updates"] > 0 and per[1]["node_updates"] > 0
+    assert all(s["converged"] == 1 for s in per)
+
+
+def test_dubins_whole_domain_subdomains(hjb, orc):
+    """3D Dubins with every node in every sub-domain (the safe threshold of a
+    discontinuous value function): one solve, equal to the full solve."""
+    d = S.c3(nxy=40, nth=16, stride=(3, 3, 4))
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-11, nthreads=8)
+    p = gpu_problem(hjb, d)
+    fine, _, _, rst = hjb.subdomains(p, d["stride"], delta=4.0)
+    assert rst["labelled"] == d["ntargets"] * d["labels"].size
+    Vbar, per, tot = hjb.solve_decomposed(p, fine)
+    assert np.abs(to_np(Vbar) - Vo).max() < TOL_V
+    assert sum(s["node_updates"] > 0 for s in per) == 1
+    V, st = hjb.solve(p)
+    assert np.abs(to_np(V) - to_np(Vbar)).max() < 1e-6
+
+
 def test_batch_uneven(hjb, orc):
     sides = [64, 97, 130, 71]
     ds = [S.c4_problem(i, n) for i, n in enumerate(sides)]
@@ -289,10 +328,10 @@ def test_tile_shapes_agree_bitwise(hjb, orc, monkeypatch):
         monkeypatch.setenv("HJB_LOOP", loop)
         for rows in ("8", "4", "2"):
             monkeypatch.setenv("HJB_TILE_ROWS", rows)
-            V, st = hjb.solve(p)
+            V, st = hjb.solve(p, local_iters=1)
             outs.append(to_np(V))
             fine, _, _, _ = hjb.subdomains(p, (16, 16), delta=0.2)
-            Vb, _, _ = hjb.solve_decomposed(p, fine)
+            Vb, _, _ = hjb.solve_decomposed(p, fine, local_iters=1)
             outs.append(to_np(Vb))
     for k in range(2, len(outs), 2):
         assert np.abs(outs[0] - outs[k]).max() < 1e-5
@@ -304,3 +343,36 @@ def test_tile_shapes_agree_bitwise(hjb, orc, monkeypatch):
     po = oracle_problem(orc, d)
     Tv, r = orc.apply(po, outs[0].astype(np.float64), nthreads=8)
     assert r / (1 - po.beta) < TOL_V
+
+
+def test_local_iterations_same_fixed_point(hjb, orc):
+    """Several applications of T per staged tile (the halo held) reach the
+    fixed point of plain value iteration in fewer sweeps: each GPU result is
+    within 1e-4 of the oracle's fixed point by the FP64 residual bound, for
+    the full-domain, decomposed and batched solves."""
+    n, A = 321, 32
+    X, Y = S.mesh2(n, n)
+    g = S.rng("misc", 32)
+    lab = S.disk_labels(X, Y, S.disk_centers(g, 4, 0.1), 0.1)
+    d = dict(shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=S.f32(S.circle_controls(A)), labels=lab, ntargets=4,
+             speed=S.f32(S.speed_field(g, X, Y)), current=S.f32(S.current_field(g, X, Y)),
+             h=2.0 / (n - 1), lam=1.0, v_out=1.0)
+    p = gpu_problem(hjb, d)
+    p2 = gpu_problem(hjb, d)
+    po = oracle_problem(orc, d)
+    fine, _, _, _ = hjb.subdomains(p, (16, 16), delta=0.2)
+    Vb_o, _, _, _ = orc.isa(po, to_np(fine).astype(np.uint32), tol=1e-11, nthreads=8)
+    sweeps = {}
+    for L in (1, 2, 4, 16):
+        V, st = hjb.solve(p, local_iters=L)
+        assert st["converged"] == 1
+        sweeps[L] = st["iterations"]
+        _, r = orc.apply(po, to_np(V).astype(np.float64), nthreads=8)
+        assert r / (1 - po.beta) < TOL_V
+        Vb, per, tot = hjb.solve_decomposed(p, fine, local_iters=L)
+        assert tot["converged"] == 1
+        assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V
+        Vs, sts = hjb.solve_batch([p, p2], local_iters=L)
+        assert np.abs(to_np(Vs[0]) - to_np(V)).max() < 1e-6
+    assert sweeps[4] < sweeps[2] < sweeps[1]
