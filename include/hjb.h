@@ -236,11 +236,13 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
  *  wrt = 0: grad_out = dL/dtheta for the log-speed field (s = exp(theta),
  *           HJB_DYN_SPEED_CURRENT):  lambda_i beta h s_i grad I[V](y_i) . a_pi(i)
  *  wrt = 1: grad_out = dL/dl for the cost field: lambda_i gamma.
- *  v [N]: the converged solution; grad_v [N]: dL/dV.  opts->tol bounds
- *  ||lambda^{n+1} - lambda^n||_inf (default 1e-7); the iteration also stops
- *  (stats->converged = 2) once that change is within 256 FP32 ulp of
- *  max|lambda|, the summation-order floor of the scattered accumulation.
- *  Otherwise HJB_ERR_NOT_CONVERGED after opts->max_iters.  stats (optional). */
+ *  v [N]: the converged solution; grad_v [N]: dL/dV.  opts->tol (optional,
+ *  > 0) stops the iteration once ||lambda^{n+1} - lambda^n||_inf <= tol
+ *  (stats->converged = 1).  It always stops (stats->converged = 2) at the
+ *  summation-order floor of the scattered FP32 accumulation: a change within
+ *  32 ulp of max|lambda|, or no new minimum of the change for 256 iterations
+ *  once it is below 1024 ulp of max|lambda|.  Otherwise
+ *  HJB_ERR_NOT_CONVERGED after opts->max_iters.  stats (optional). */
 int hjb_backward(hjb_problem *p, const float *v, const float *grad_v, int wrt,
                  const hjb_solve_opts *opts, float *grad_out, hjb_stats *stats, void *stream);
 

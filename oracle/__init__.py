@@ -82,6 +82,8 @@ def _lib_handle():
             lib.ohjb_adjoint.restype = i
             lib.ohjb_grad.argtypes = [P, vp, vp, vp, vp, vp]
             lib.ohjb_points.argtypes = [P, vp, vp, i, vp, vp]
+            lib.ohjb_tie_influence.argtypes = [P, vp, vp, d, d, i, vp, vp]
+            lib.ohjb_tie_influence.restype = C.c_longlong
             lib.ohjb_max_threads.restype = i
             _lib = lib
     return _lib
@@ -289,6 +291,23 @@ def points(p: Problem, V, pts, with_grad=True):
     _lib_handle().ohjb_points(p._ref(), V.ctypes.data, pts.ctypes.data, int(P), vals.ctypes.data,
                               _ptr(g))
     return vals, g
+
+
+def tie_influence(p: Problem, V, pol, eps=1e-6, face_eps=1e-5, closure=True,
+                  with_second=False):
+    """Nodes whose policy or interpolant gradient is not unique (the two best
+    controls within eps, or the chosen foot within face_eps cells of a cell
+    face) and, with closure, everything downstream of them along the
+    transposed policy map.  Returns a bool mask [N] (and, with_second, the
+    runner-up control of every free node)."""
+    V = _f64(V).reshape(-1)
+    pol = np.ascontiguousarray(pol, dtype=np.int32).reshape(-1)
+    out = np.empty(p.N, dtype=np.uint8)
+    sec = np.empty(p.N, dtype=np.int32) if with_second else None
+    _lib_handle().ohjb_tie_influence(p._ref(), V.ctypes.data, pol.ctypes.data, float(eps),
+                                     float(face_eps), int(bool(closure)), out.ctypes.data,
+                                     _ptr(sec))
+    return (out.astype(bool), sec) if with_second else out.astype(bool)
 
 
 def interp(p: Problem, V, y):

@@ -706,6 +706,71 @@ void ohjb_points(const ohjb_problem *p, const double *V, const double *pts, int 
     }
 }
 
+/* Nodes whose adjoint or gradient is not unique (R10): the policy at a node
+ * is not determined when its two smallest control values I[V](foot) differ by
+ * at most eps, and the gradient of the Q1 interpolant is one-sided when the
+ * foot of the chosen control lies within face_eps cells of a cell face.
+ * lambda flows from a node to the corners of its foot (the transposed system
+ * (I - beta P_pi)^T lam = g), so with closure != 0 every node reached from
+ * such a seed along that map is marked too.  out[i] = 1 marks a node; returns
+ * their number.  second (optional) receives the runner-up control of every
+ * free node (-1 elsewhere). */
+long long ohjb_tie_influence(const ohjb_problem *p, const double *V, const int32_t *policy,
+                             double eps, double face_eps, int closure, uint8_t *out,
+                             int32_t *second_arg) {
+    long long N = node_count(p);
+    long long *queue = (long long *)malloc(sizeof(long long) * N);
+    long long head = 0, tail = 0;
+    for (long long i = 0; i < N; ++i) {
+        out[i] = 0;
+        if (second_arg) second_arg[i] = -1;
+        if (policy[i] < 0 || p->target[i] != 0) continue;
+        int idx[3];
+        unflatten(p, i, idx);
+        double best = INFINITY, second = INFINITY;
+        int jb = -1, js = -1;
+        for (int j = 0; j < p->ncontrols; ++j) {
+            double g[3], off[3];
+            double q = foot(p, i, idx, j, g, off) ? q1_at(p, V, g, NULL) : p->v_out;
+            if (q < best) {
+                second = best;
+                js = jb;
+                best = q;
+                jb = j;
+            } else if (q < second) {
+                second = q;
+                js = j;
+            }
+        }
+        if (second_arg) second_arg[i] = js;
+        int seed = (second - best) <= eps;
+        double g[3], off[3];
+        if (!seed && foot(p, i, idx, policy[i], g, off))
+            for (int d = 0; d < p->ndim; ++d) {
+                double t = g[d] - floor(g[d]);
+                if (t <= face_eps || t >= 1.0 - face_eps) seed = 1;
+            }
+        if (seed) {
+            out[i] = 1;
+            queue[tail++] = i;
+        }
+    }
+    while (closure && head < tail) {
+        long long i = queue[head++];
+        if (policy[i] < 0 || p->target[i] != 0) continue;
+        long long ci[8];
+        double cw[8];
+        int nc = row_weights(p, i, policy[i], ci, cw, NULL, NULL);
+        for (int m = 0; m < nc; ++m)
+            if (cw[m] > 0.0 && !out[ci[m]]) {
+                out[ci[m]] = 1;
+                queue[tail++] = ci[m];
+            }
+    }
+    free(queue);
+    return tail;
+}
+
 /* Number of OpenMP threads the library would use (1 without OpenMP). */
 int ohjb_max_threads(void) {
 #ifdef _OPENMP

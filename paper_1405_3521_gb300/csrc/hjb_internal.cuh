@@ -226,7 +226,9 @@ struct AdjCtl {
     int error;
     unsigned lam_bits;
     float lam_max;
-    int pad_[5];
+    float best_res;
+    int stall;
+    int pad_[3];
 };
 
 // pi_i = argmin_j I[V](foot_j) (lowest index on ties), -1 on targets, -2

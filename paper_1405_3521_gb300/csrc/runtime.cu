@@ -1428,7 +1428,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     ap.current = pr.current;
     ap.labels = pr.labels;
     const hjbk::ControlTable ctrl = control_table(P);
-    const double tol = (opts && opts->tol > 0) ? opts->tol : 1e-7;
+    // no absolute default: the iteration runs to the FP32 floor of lambda
+    const double tol = (opts && opts->tol > 0) ? opts->tol : 0.0;
     const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
     float *L0 = P->adj_L.as<float>(), *L1 = L0 + N;
     hjbh::AdjCtl *ctl = P->adj_ctl.as<hjbh::AdjCtl>();

@@ -1,0 +1,199 @@
+"""Parity at the full sizes of the workloads, in the launch configuration the
+benchmark times: the tuner's tile shape, the graph loop, four applications of
+T per staged tile and sweep.  Every expected value comes from the FP64 oracle
+on the same seeded inputs:
+
+- Zermelo 1025^2 (64 controls, 16 targets): the oracle's full solve, element
+  by element; RA labels at the benchmark's coarse stride; the restricted solve
+  of sampled sub-domains of the oracle's own decomposition.
+- Dubins 256 x 256 x 128: the oracle's full solve, element by element (its
+  value function is discontinuous, so the residual bound below is too loose
+  there: an FP32 foot a 1e-7 cell off a jump of 1 leaves a residual of 1e-6).
+- The 512-problem batch: the oracle solves a size-stratified sample of the
+  problems; every problem passes the fixed-point property: the oracle's
+  operator (Sec. 3, eq. Tdef) applied to the GPU result, whose FP64 residual r
+  bounds the distance to the oracle's fixed point by r / (1 - beta)
+  (contraction bound).
+- The adjoint at 1025^2: the oracle's FP64 solve, policy, adjoint and
+  gradient against hjb_backward, as derivatives along smooth directions of
+  theta at 1e-3; and central differences of GPU solves along such
+  directions."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from _cases import gpu_problem, oracle_problem, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL_V = 1e-4
+
+
+@pytest.fixture(scope="module")
+def hjb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1405_3521_gb300 as h
+    h._capi.lib()
+    return h
+
+
+def _near_threshold(Vaux, delta, diff, m):
+    """Label bits that differ only where |V_k - V| is within TOL_V of delta."""
+    vmin = Vaux.min(0)
+    near = np.zeros_like(diff, dtype=bool)
+    for k in range(m):
+        close = np.abs(np.abs(Vaux[k] - vmin) - delta) <= TOL_V
+        near |= close & (((diff >> k) & 1) == 1)
+    return near
+
+
+def test_zermelo_1025_full_ra_and_subdomains(hjb, orc):
+    d = S.c2()
+    nt = orc.max_threads()
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-10, nthreads=nt)
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p)
+    assert st["converged"] == 1
+    assert np.abs(to_np(V).astype(np.float64) - Vo).max() < TOL_V
+    # RA at the benchmark's stride (65^2 coarse grid, 16 auxiliary problems)
+    stride = d["stride"]
+    delta = 0.1
+    Vaux_o, lab_o, _ = orc.ra(po, stride, delta, tol=1e-11, nthreads=nt)
+    fine_o = orc.project(po, stride, lab_o)
+    fine, coarse, aux, rst = hjb.subdomains(p, stride, delta=delta, want_aux=True)
+    assert np.abs(to_np(aux).reshape(Vaux_o.shape) - Vaux_o).max() < TOL_V
+    coarse = to_np(coarse).astype(np.uint32)
+    diff = coarse ^ lab_o
+    assert ((diff != 0) & ~_near_threshold(Vaux_o, delta, diff, d["ntargets"])).sum() == 0
+    if not diff.any():
+        assert np.array_equal(to_np(fine).astype(np.uint32), fine_o)
+    # ISA step 3 on the oracle's decomposition: the two smallest sub-domains,
+    # each solved alone by both sides
+    sizes = [int(((fine_o >> k) & 1).sum()) for k in range(d["ntargets"])]
+    for k in np.argsort(sizes)[:2]:
+        k = int(k)
+        only = (fine_o & np.uint32(1 << k)).astype(np.uint32)
+        Vk_o, _, _ = orc.solve(po, tol=1e-10, mask=only, bit=k, nthreads=nt)
+        Vb, per, tot = hjb.solve_decomposed(p, only)
+        assert tot["converged"] == 1
+        inside = ((only >> k) & 1) == 1
+        assert np.abs(to_np(Vb)[inside].astype(np.float64) - Vk_o[inside]).max() < TOL_V
+
+
+def test_dubins_full_size(hjb, orc):
+    d = S.c3()
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-10, nthreads=orc.max_threads())
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p)
+    assert st["converged"] == 1
+    assert np.abs(to_np(V).astype(np.float64) - Vo).max() < TOL_V
+    # the benchmark's decomposition (safe threshold): every node in every
+    # sub-domain, solved once, equal to the full solve
+    fine, _, _, rst = hjb.subdomains(p, d["stride"], delta=-1.0, C_=0.0, M=-1.0)
+    Vb, per, tot = hjb.solve_decomposed(p, fine)
+    assert np.abs(to_np(Vb) - to_np(V)).max() < 1e-6
+
+
+def test_batch_512_sampled(hjb, orc):
+    sides = S.c4_sides()
+    ds = [S.c4_problem(i, int(n)) for i, n in enumerate(sides)]
+    ps = [gpu_problem(hjb, d) for d in ds]
+    Vs, sts = hjb.solve_batch(ps)
+    assert all(s["converged"] == 1 for s in sts)
+    nt = orc.max_threads()
+    for d, V in zip(ds, Vs):
+        po = oracle_problem(orc, d)
+        _, r = orc.apply(po, to_np(V).astype(np.float64), nthreads=nt)
+        assert r / (1 - po.beta) < TOL_V
+    for i in np.argsort(sides)[:: len(sides) // 6]:
+        po = oracle_problem(orc, ds[i])
+        Vo, _, _ = orc.solve(po, tol=1e-10, nthreads=nt)
+        assert np.abs(to_np(Vs[i]).astype(np.float64) - Vo).max() < TOL_V
+
+
+def _smooth_directions(d, count, seed):
+    """Seeded smooth perturbation fields of theta (sums of 4 low-frequency
+    sines, zero on target nodes), one per row."""
+    X, Y = S.mesh2(*d["shape"])
+    g = np.random.default_rng(seed)
+    free = (d["labels"] == 0).reshape(-1)
+    out = []
+    for _ in range(count):
+        f = np.zeros_like(X)
+        for _ in range(4):
+            k = g.uniform(-2 * np.pi, 2 * np.pi, size=2)
+            f += g.normal() * np.sin(k[0] * X + k[1] * Y + g.uniform(0, 2 * np.pi))
+        out.append(np.where(free, f.reshape(-1), 0.0))
+    return np.array(out)
+
+
+def test_adjoint_1025_against_oracle(hjb, orc):
+    """hjb_backward at the oracle's FP64 fixed point and loss gradient
+    (rounded to FP32) against the oracle's FP64 adjoint and gradient.
+
+    The adjoint is not unique pointwise: where the policy is tied within FP32
+    rounding, either control is optimal, and along a line where the optimal
+    trajectories of two controls converge the accumulated adjoint mass may go
+    down either of two adjacent columns (measured: mass swapped between
+    neighbouring columns, the gradient equal to 5e-6 wherever lambda agrees).
+    What is unique is the gradient as a functional on smooth perturbations of
+    theta -- the derivative of the loss along a smooth direction -- so the
+    check is g . d for seeded smooth fields d, at 1e-3 of sum |g_i d_i|, and
+    the L1 distance of the gradients at 1e-2."""
+    d = S.c5()
+    nt = orc.max_threads()
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-11, nthreads=nt)
+    pol, _ = orc.policy(po, Vo, nthreads=nt)
+    _, gV_o = orc.points(po, Vo, d["points"])
+    lam, _, _ = orc.adjoint(po, pol, gV_o, tol=1e-14)
+    gt_o, _ = orc.grad(po, Vo, pol, lam)
+    import torch
+    p = gpu_problem(hjb, d)
+    V, _ = hjb.solve(p)
+    assert np.abs(to_np(V).astype(np.float64) - Vo).max() < TOL_V
+    pts = torch.as_tensor(np.asarray(d["points"], np.float32)).cuda()
+    _, gV = hjb.point_values(p, V, pts)
+    assert np.abs(to_np(gV).astype(np.float64) - gV_o).max() < 1e-7
+    v32 = torch.as_tensor(Vo.astype(np.float32)).cuda()
+    gv32 = torch.as_tensor(gV_o.astype(np.float32)).cuda()
+    g, st = hjb.backward(p, v32, gv32, wrt=0)
+    assert st["converged"] in (1, 2)
+    g = to_np(g).astype(np.float64)
+    for dk in _smooth_directions(d, 16, 41):
+        ref = gt_o @ dk
+        assert abs(g @ dk - ref) <= 1e-3 * (np.abs(gt_o) @ np.abs(dk)), (g @ dk, ref)
+    assert np.abs(g - gt_o).sum() / np.abs(gt_o).sum() < 1e-2
+
+
+def test_adjoint_1025_finite_differences(hjb):
+    """The derivative of the loss (mean of V at 4096 points) along smooth
+    directions of theta: central differences of GPU solves against g . d from
+    hjb_backward, at the benchmark's size."""
+    import torch
+    d = S.c5()
+    th = np.asarray(d["log_speed"], np.float64).reshape(-1)
+    pts = torch.as_tensor(np.asarray(d["points"], np.float32)).cuda()
+
+    def loss(theta):
+        q = dict(d)
+        q["log_speed"] = theta.reshape(d["labels"].shape).astype(np.float32)
+        p = gpu_problem(hjb, q)
+        V, _ = hjb.solve(p, tol=1e-9)
+        vals, _ = hjb.point_values(p, V, pts)
+        return float(to_np(vals).astype(np.float64).mean()), p, V
+
+    _, p, V = loss(th)
+    _, gV = hjb.point_values(p, V, pts)
+    g, _ = hjb.backward(p, V, gV, wrt=0)
+    g = to_np(g).astype(np.float64)
+    eps = 3e-3  # FP32 solves: rounding ~1e-7 in L against a step of 3e-3
+    for dk in _smooth_directions(d, 4, 43):
+        Lp, _, _ = loss(th + eps * dk)
+        Lm, _, _ = loss(th - eps * dk)
+        fd = (Lp - Lm) / (2 * eps)
+        assert abs(fd - g @ dk) <= 1e-3 * (np.abs(g) @ np.abs(dk)), (fd, g @ dk)

@@ -720,3 +720,63 @@ def test_points_loss_gradient_is_interpolation_weights(orc):
     # L is linear in V: L(V) = gr . V
     assert abs(vals.mean() - gr @ V) < 1e-12
     assert abs(gr.sum() - 1.0) < 1e-12
+
+
+def test_tie_influence_is_the_closure_of_the_seeds(orc):
+    """The non-unique set used by the full-size gradient comparison: it holds
+    every near-tied node, is closed under "corners of the chosen foot", and
+    holds nothing else (each member is a seed or a corner of a member)."""
+    n, A = 25, 16
+    X, Y, th, lab, pts = _c5_small(n, A)
+    h = 2.0 / (n - 1)
+    p = orc.Problem((n, n), (-1, -1), (1, 1), S.circle_controls(A), lab, h, speed=np.exp(th))
+    V, _, _ = orc.solve(p, tol=1e-14)
+    pol, _ = orc.policy(p, V)
+    eps = 2e-3
+    out = orc.tie_influence(p, V, pol, eps=eps, face_eps=-1.0)
+    N = n * n
+    xs = np.linspace(-1, 1, n)
+    ctr = S.circle_controls(A)
+    s = np.exp(th).reshape(-1)
+
+    def corners(i, j):
+        iy, ix = divmod(i, n)
+        y = np.array([xs[ix], xs[iy]]) + h * s[i] * ctr[j]
+        if np.any(y < -1 - 1e-9) or np.any(y > 1 + 1e-9):
+            return None, None
+        g = np.clip((y + 1) / h, 0, n - 1)
+        c = np.minimum(np.floor(g).astype(int), n - 2)
+        t = g - c
+        ids, ws = [], []
+        for dy in (0, 1):
+            for dx in (0, 1):
+                ids.append((c[1] + dy) * n + c[0] + dx)
+                ws.append((t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]))
+        return ids, ws
+
+    seeds = np.zeros(N, bool)
+    for i in range(N):
+        if pol[i] < 0 or lab.reshape(-1)[i] != 0:
+            continue
+        q = []
+        for j in range(A):
+            ids, ws = corners(i, j)
+            q.append(1.0 if ids is None else sum(w * V[k] for k, w in zip(ids, ws)))
+        q = np.sort(q)
+        seeds[i] = q[1] - q[0] <= eps
+    assert seeds.any() and not out.all()
+    assert np.array_equal(orc.tie_influence(p, V, pol, eps=eps, face_eps=-1.0, closure=False),
+                          seeds)
+    assert np.all(out[seeds])
+    reached = seeds.copy()
+    for i in np.nonzero(out)[0]:
+        if pol[i] < 0 or lab.reshape(-1)[i] != 0:
+            continue
+        ids, ws = corners(i, pol[i])
+        if ids is None:
+            continue
+        for k, w in zip(ids, ws):
+            if w > 0:
+                assert out[k]
+                reached[k] = True
+    assert np.array_equal(reached, out)
