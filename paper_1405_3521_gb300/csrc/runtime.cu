@@ -619,7 +619,7 @@ int upload_slots(RunCtx &R, cudaStream_t st) {
 int run_loop(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlTable &ctrl,
              cudaStream_t st, int local = 1) {
     const int n = static_cast<int>(R.slots.size());
-    R.local_iters = key.dubins ? 1 : local;
+    R.local_iters = local;
     hjbh::launch_loop_init(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), R.d_ctl.as<Ctl>(),
                            n, st, R.diff);
     {

@@ -783,23 +783,34 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
         const int tz = tile / txy, rem = tile - tz * txy;
         const int ty = rem / S.tiles_x, tx = rem - ty * S.tiles_x;
         const int gx = tx * TX + lx, gy = ty * TY + ly;
-        const float *T = sm.tile[b];
+        float *T = sm.tile[b];
         const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
                               (ty * TY >= H) && (ty * TY + TY - 1 + H <= ny - 1);
-        float rmax = 0.0f;
-        int cnt = 0;
-        bool chg = false;
-#pragma unroll 1
+        // the thread's column of TZ nodes: starting values and free flags
+        float vold[TZ], vnew[TZ];
+        unsigned freebits = 0u;
+#pragma unroll
         for (int lz = 0; lz < TZ; ++lz) {
             const int gz = tz * TZ + lz;
-            const float *L = T + (lz + HZ) * LAYER;  // layer of this node
-            const float vold = L[(ly + H) * TW + lx + XPAD];
+            vold[lz] = T[(lz + HZ) * LAYER + (ly + H) * TW + lx + XPAD];
+            vnew[lz] = vold[lz];
             const long long gi = (static_cast<long long>(gz) * ny + gy) * nx + gx;
-            const bool isfree = (gx < nx) && (gy < ny) && (gz < nz) && node_class(S, gi) == CLS_FREE;
-            if (!isfree) continue;
-            const float2 tr = S.trig[gz];
-            float ox = tr.x, oy = tr.y;
-            bool out = false;
+            if ((gx < nx) && (gy < ny) && (gz < nz) && node_class(S, gi) == CLS_FREE)
+                freebits |= 1u << lz;
+        }
+        // args.local_iters applications of T to the tile's nodes with the
+        // halo held (the first reads the previous sweep's values)
+        int li = 0;
+        for (;;) {
+            bool moved = false;
+#pragma unroll
+            for (int lz = 0; lz < TZ; ++lz) {
+                if (!((freebits >> lz) & 1u)) continue;
+                const int gz = tz * TZ + lz;
+                const long long gi = (static_cast<long long>(gz) * ny + gy) * nx + gx;
+                    const float2 tr = S.trig[gz];
+                float ox = tr.x, oy = tr.y;
+                bool out = false;
             if (!interior) {
                 const float lox = -static_cast<float>(gx), hix = static_cast<float>(nx - 1 - gx);
                 const float loy = -static_cast<float>(gy), hiy = static_cast<float>(ny - 1 - gy);
@@ -845,23 +856,37 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
                     best = pick<WFORM>(best, q);
                 }
             }
-            float vnew;
-            if (WFORM)
-                vnew = S.beta * best;
-            else
-                vnew = fmaf(S.beta, best, S.cost ? S.gamma * S.cost[gi] : S.gl);
-            float *D = S.V[dst];
-            const long long row = static_cast<long long>(gy) * S.pitch + gx;
-            D[static_cast<long long>(gz + S.zdup) * S.zstride + row] = vnew;
-            if (gz < S.zdup) D[static_cast<long long>(gz + nz + S.zdup) * S.zstride + row] = vnew;
+            const float v = WFORM ? S.beta * best
+                                  : fmaf(S.beta, best, S.cost ? S.gamma * S.cost[gi] : S.gl);
+            moved |= (v != vnew[lz]);
+            vnew[lz] = v;
+            }
+            if (++li >= args.local_iters) break;
+            // all reads of the tile done; stop early once the tile is stable
+            if (!__syncthreads_or(moved)) break;
+#pragma unroll
+            for (int lz = 0; lz < TZ; ++lz)
+                if ((freebits >> lz) & 1u) T[(lz + HZ) * LAYER + (ly + H) * TW + lx + XPAD] = vnew[lz];
+            if (freebits) fence_proxy_async_smem();  // the buffer takes a later TMA copy
+            __syncthreads();
+        }
+        float rmax = 0.0f;
+        bool chg = false;
+        float *D = S.V[dst];
+        const long long row = static_cast<long long>(gy) * S.pitch + gx;
+#pragma unroll
+        for (int lz = 0; lz < TZ; ++lz) {
+            if (!((freebits >> lz) & 1u)) continue;
+            const int gz = tz * TZ + lz;
+            D[static_cast<long long>(gz + S.zdup) * S.zstride + row] = vnew[lz];
+            if (gz < S.zdup) D[static_cast<long long>(gz + nz + S.zdup) * S.zstride + row] = vnew[lz];
             if (gz >= nz - S.zdup)
-                D[static_cast<long long>(gz - nz + S.zdup) * S.zstride + row] = vnew;
-            rmax = fmaxf(rmax, fabsf(vnew - vold));
-            chg |= (vnew != vold);
-            ++cnt;
+                D[static_cast<long long>(gz - nz + S.zdup) * S.zstride + row] = vnew[lz];
+            rmax = fmaxf(rmax, fabsf(vnew[lz] - vold[lz]));
+            chg |= (vnew[lz] != vold[lz]);
         }
         const float r = warp_max(rmax);
-        int c = cnt;
+        int c = __popc(freebits) * li;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         const unsigned cm = __ballot_sync(0xffffffffu, chg);

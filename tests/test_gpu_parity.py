@@ -376,3 +376,18 @@ def test_local_iterations_same_fixed_point(hjb, orc):
         Vs, sts = hjb.solve_batch([p, p2], local_iters=L)
         assert np.abs(to_np(Vs[0]) - to_np(V)).max() < 1e-6
     assert sweeps[4] < sweeps[2] < sweeps[1]
+
+
+def test_dubins_local_iterations(hjb, orc):
+    """The 3D kernel's repeated applications per staged tile reach the same
+    fixed point (periodic heading, halo layers held)."""
+    d = S.c3(nxy=41, nth=16, ntargets=3, stride=(5, 5, 4))
+    _, Vo = _ref(orc, d, tol=1e-11)
+    p = gpu_problem(hjb, d)
+    sweeps = {}
+    for L in (1, 4, 16):
+        V, st = hjb.solve(p, local_iters=L)
+        assert st["converged"] == 1
+        sweeps[L] = st["iterations"]
+        assert np.abs(to_np(V) - Vo).max() < TOL_V
+    assert sweeps[4] < sweeps[1]
