@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1025, help="grid side (default: the 1025^2 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="zermelo", choices=["zermelo", "dubins", "batch", "adjoint"],
+    ap.add_argument("--workload", default="zermelo", choices=["zermelo", "dubins", "batch", "adjoint", "vdp"],
                     help="zermelo: the 1025^2 Zermelo problem (default, the headline line); "
                          "dubins, batch, adjoint: the other hot-path rows, each printing its own line")
     ap.add_argument("--profile", choices=["full", "decomposed", "ra"], default=None,
@@ -326,6 +326,45 @@ def run_dubins(args, hjb, S, dev, flush, local):
           cpu_baseline=cpu, gpu_launches=rst["launches"] + tot["launches"], clocks=clocks)
 
 
+def run_vdp(args, hjb, S, dev, flush, local):
+    """Van der Pol oscillator (Sec. 5, Example ex3) on 1025^2, 21 controls,
+    running cost |x|, target disk in 4 cake slices: reconstruction at stride
+    16 with delta = 0.1 and the decomposed solve against the full solve."""
+    import numpy as np
+    d = S.vdp(n=args.n, slices=4)
+    nfree = int((d["labels"] == 0).sum())
+    p = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8), d["h"],
+                    current=dev(d["current"]), cost=dev(d["cost"]), n_targets=d["ntargets"],
+                    value_out=d["v_out"])
+    _, fst_j = hjb.solve(p, local_iters=1)
+    iters_full = fst_j["iterations"]
+    ms_full, (Vf, fst), _ = _timed_steps(lambda: hjb.solve(p), args.steps, 1, flush, local)
+    delta = 0.1
+
+    def step():
+        fine, _, _, rst = hjb.subdomains(p, d["stride"], delta=delta)
+        Vb, per, tot = hjb.solve_decomposed(p, fine)
+        return Vb, rst, tot, per
+
+    ms, (Vb, rst, tot, per), clocks = _timed_steps(step, args.steps, args.warmup, flush, local)
+    peak = torch_sms(local) * 128 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
+    ach = tot["node_updates"] * d["controls"].shape[0] * OPS_PER_CONTROL / (tot["ms"] / 1e3)
+    _line(args, "node-updates/s to convergence, decomposed vs full-domain GPU (Van der Pol)",
+          nfree * iters_full / (ms / 1e3), UNIT, ms,
+          {"workload": "vdp-%dx%d-A21-4slices" % (args.n, args.n), "coarse_stride": list(d["stride"]),
+           "delta": delta},
+          full_domain={"sweeps": fst["iterations"], "jacobi_sweeps": iters_full, "ms": ms_full,
+                       "node_updates_per_s": nfree * iters_full / (ms_full / 1e3)},
+          decomposed={"ms_ra": rst["ms"], "ms_fine": tot["ms"], "max_subdomain_iters": tot["iterations"],
+                      "labelled_fraction": rst["labelled"] / d["labels"].size,
+                      "max_abs_diff_vs_full": float((Vb - Vf).abs().max().item()),
+                      "solved_subdomains": sum(1 for s in per if s["node_updates"] > 0)},
+          raw_node_updates_per_s=(rst["node_updates"] + tot["node_updates"]) / (ms / 1e3),
+          roofline={"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s",
+                    "frac": ach / peak, "traffic": None, "kernel": "sweep2d_kernel<0,V,4>"},
+          cpu_baseline=None, gpu_launches=rst["launches"] + tot["launches"], clocks=clocks)
+
+
 def run_batch(args, hjb, S, dev, flush, local):
     """512 independent square problems, sides ~ U{64..512}, one launch."""
     import numpy as np
@@ -425,7 +464,8 @@ def main():
         hjb._capi.lib()
         dev = lambda a, dt=np.float32: torch.as_tensor(np.ascontiguousarray(np.asarray(a).astype(dt))).cuda()  # noqa
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-        {"dubins": run_dubins, "batch": run_batch, "adjoint": run_adjoint}[args.workload](
+        {"dubins": run_dubins, "batch": run_batch, "adjoint": run_adjoint,
+         "vdp": run_vdp}[args.workload](
             args, hjb, S, dev, flush, local)
         return
     import numpy as np

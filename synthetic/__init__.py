@@ -20,6 +20,8 @@ families this library is benchmarked on:
   c4  batch of 512 square problems, sides ~ U{64..512}, 1-8 disks, 32 controls
   c5  2D f = exp(theta) a on 1025^2, theta a Gaussian random field, 4 disks,
       4096 loss points
+  vdp the Van der Pol oscillator of Sec. 5 (Example ex3) as a target problem:
+      running cost |x|, target B(0, 0.2) split into angular "cake slices"
 """
 from __future__ import annotations
 
@@ -223,3 +225,30 @@ def c5(n=1025, A=32, ntargets=4, P=4096):
     d["speed"] = None
     d["points"] = f32(uniform_points(rng("points", 5), P))
     return d
+
+
+def vdp(n=101, A=21, slices=4, rho=0.2, stride=None):
+    """Van der Pol oscillator as a target problem (Sec. 5, Example ex3):
+    f(x, a) = (x2, (1 - x1^2) x2 - x1 + a) on (-1, 1)^2 with a in [-1, 1]
+    sampled at A equispaced points, running cost l(x) = |x|, lambda = 1,
+    g = 0, target the closed disk B(0, rho) split into `slices` equal angular
+    sectors (label k + 1 for angles in [2 pi k / slices, 2 pi (k + 1) / slices)),
+    h = dx.  The state-dependent part of f is the node field `current`, the
+    control part the control vectors (0, a_j).  Trajectories that must leave
+    the box take value_out = sup l / lambda = sqrt(2), the discounted cost of
+    never arriving bounded from above."""
+    X, Y = mesh2(n, n)
+    r = np.hypot(X, Y)
+    ang = np.mod(np.arctan2(Y, X), 2 * np.pi)
+    k = np.minimum((ang / (2 * np.pi / slices)).astype(np.int64), slices - 1) + 1
+    lab = np.where(r <= rho + 1e-12, k, 0).astype(np.uint8)
+    drift = np.stack([Y, (1.0 - X * X) * Y - X], axis=-1)
+    a = np.linspace(-1.0, 1.0, A)
+    controls = np.stack([np.zeros_like(a), a], axis=-1)
+    if stride is None:
+        stride = next((s for s in (16, 10, 8, 5, 4, 2) if (n - 1) % s == 0), 1)
+    return dict(
+        shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+        controls=f32(controls), labels=lab, ntargets=slices, speed=None,
+        current=f32(drift), cost=f32(r), log_speed=None, h=2.0 / (n - 1), lam=1.0,
+        v_out=float(np.float32(math.sqrt(2.0))), stride=(stride, stride))

@@ -391,3 +391,30 @@ def test_dubins_local_iterations(hjb, orc):
         sweeps[L] = st["iterations"]
         assert np.abs(to_np(V) - Vo).max() < TOL_V
     assert sweeps[4] < sweeps[1]
+
+
+def test_vdp_full_and_decomposed(hjb, orc):
+    """Van der Pol (Sec. 5, Example ex3): drift as a node field, running cost
+    |x| (V form), target disk in 4 cake slices; full solve, RA labels and the
+    decomposed solve against the oracle."""
+    d = S.vdp(n=129, slices=4)
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-11, nthreads=8)
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p)
+    assert st["converged"] == 1
+    assert np.abs(to_np(V) - Vo).max() < TOL_V
+    stride, delta = d["stride"], 0.1
+    Vaux_o, lab_o, _ = orc.ra(po, stride, delta, tol=1e-11, nthreads=8)
+    fine_o = orc.project(po, stride, lab_o)
+    fine, coarse, aux, _ = hjb.subdomains(p, stride, delta=delta, want_aux=True)
+    assert np.abs(to_np(aux).reshape(Vaux_o.shape) - Vaux_o).max() < TOL_V
+    diff = to_np(coarse).astype(np.uint32) ^ lab_o
+    vmin = Vaux_o.min(0)
+    for k in range(d["ntargets"]):
+        bad = ((diff >> k) & 1) == 1
+        assert np.all(np.abs(np.abs(Vaux_o[k][bad] - vmin[bad]) - delta) <= TOL_V)
+    Vb_o, unc, _, _ = orc.isa(po, fine_o, tol=1e-11, nthreads=8)
+    Vb, per, tot = hjb.solve_decomposed(p, fine_o)
+    assert tot["converged"] == 1
+    assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V

@@ -780,3 +780,49 @@ def test_tie_influence_is_the_closure_of_the_seeds(orc):
                 assert out[k]
                 reached[k] = True
     assert np.array_equal(reached, out)
+
+
+def test_vdp_decomposition_keeps_the_error(orc):
+    """Table 5 (Sec. 5, Van der Pol): the ISA error against a finer reference
+    equals the original problem's error for 2, 4 and 8 cake slices, and both
+    fall as the grid is refined.  The reference is the oracle on a 201^2
+    grid (the paper uses 400^2); the grids are nested, so errors are taken
+    at common nodes.  The paper's absolute numbers depend on its unstated
+    control sampling and time step, so the magnitude is only checked loosely."""
+    import json
+    gold = json.load(open(os.path.join(GOLDEN, "paper_table5_vdp.json")))
+    assert all(gold["rows"][k] == gold["rows"]["original"]
+               for k in ("2-subsets", "4-subsets", "8-subsets"))
+    ref = S.vdp(n=201, slices=1)
+    Vr, _, _ = orc.solve(_vdp_problem(orc, ref), tol=1e-10, nthreads=orc.max_threads())
+    Vr = Vr.reshape(201, 201)
+    errs = {}
+    for n in (51, 101):
+        sub = Vr[:: 200 // (n - 1), :: 200 // (n - 1)].reshape(-1)
+        V0, _, _ = orc.solve(_vdp_problem(orc, S.vdp(n=n, slices=1)), tol=1e-10,
+                             nthreads=orc.max_threads())
+        e0 = np.abs(V0 - sub)
+        errs[n] = (e0.max(), e0.mean())
+        if n != 101:
+            continue
+        for slices in (2, 4, 8):
+            d = S.vdp(n=n, slices=slices)
+            po = _vdp_problem(orc, d)
+            _, lab, _ = orc.ra(po, (5, 5), 0.1, tol=1e-10, nthreads=orc.max_threads())
+            fm = orc.project(po, (5, 5), lab)
+            Vb, unc, _, _ = orc.isa(po, fm, tol=1e-10, nthreads=orc.max_threads())
+            assert unc == 0
+            e = np.abs(Vb - sub)
+            assert abs(e.max() - e0.max()) <= 1e-3 * e0.max()
+            assert abs(e.mean() - e0.mean()) <= 2e-2 * e0.mean()
+            # the sub-domains are proper subsets
+            assert all(((fm >> k) & 1).mean() < 1.0 for k in range(slices))
+    assert errs[101][0] < errs[51][0] and errs[101][1] < errs[51][1]
+    # the same order of magnitude as the paper's 100^2 row
+    assert 0.2 * gold["rows"]["original"][1][1] < errs[101][1] < 5 * gold["rows"]["original"][1][1]
+
+
+def _vdp_problem(orc, d):
+    return orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"],
+                       current=d["current"], cost=d["cost"], lam=d["lam"], v_out=d["v_out"],
+                       ntargets=d["ntargets"])
