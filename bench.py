@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1025, help="grid side (default: the 1025^2 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="zermelo", choices=["zermelo", "dubins", "batch", "adjoint", "vdp"],
+    ap.add_argument("--workload", default="zermelo", choices=["zermelo", "dubins", "batch", "adjoint", "vdp", "game"],
                     help="zermelo: the 1025^2 Zermelo problem (default, the headline line); "
                          "dubins, batch, adjoint: the other hot-path rows, each printing its own line")
     ap.add_argument("--profile", choices=["full", "decomposed", "ra"], default=None,
@@ -365,6 +365,48 @@ def run_vdp(args, hjb, S, dev, flush, local):
           cpu_baseline=None, gpu_launches=rst["launches"] + tot["launches"], clocks=clocks)
 
 
+def run_game(args, hjb, S, dev, flush, local):
+    """The pursuit-evasion game (Sec. 5, Example ex4) on 1025^2: 16 pursuer
+    by 8 evader directions (128 pairs per node), per-axis scale field,
+    running cost x1^2 + 0.1, capture disk in 4 slices; reconstruction at
+    stride 16 (delta = 0.1) and the decomposed solve against the full solve."""
+    import numpy as np
+    d = S.pursuit_evasion(n=args.n, slices=4)
+    nfree = int((d["labels"] == 0).sum())
+    p = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8), d["h"],
+                    scale=dev(d["scale"]), cost=dev(d["cost"]), n_targets=d["ntargets"],
+                    value_out=d["v_out"], controls_b=d["controls_b"])
+    _, fst_j = hjb.solve(p, local_iters=1)
+    iters_full = fst_j["iterations"]
+    ms_full, (Vf, fst), _ = _timed_steps(lambda: hjb.solve(p), args.steps, 1, flush, local)
+    delta = 0.1
+
+    def step():
+        fine, _, _, rst = hjb.subdomains(p, d["stride"], delta=delta)
+        Vb, per, tot = hjb.solve_decomposed(p, fine)
+        return Vb, rst, tot, per
+
+    ms, (Vb, rst, tot, per), clocks = _timed_steps(step, args.steps, args.warmup, flush, local)
+    pairs = d["controls"].shape[0] * d["controls_b"].shape[0]
+    peak = torch_sms(local) * 128 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
+    ach = tot["node_updates"] * pairs * OPS_PER_CONTROL / (tot["ms"] / 1e3)
+    _line(args, "node-updates/s to convergence, decomposed vs full-domain GPU (pursuit-evasion game)",
+          nfree * iters_full / (ms / 1e3), UNIT, ms,
+          {"workload": "game-%dx%d-A16xB8-4slices" % (args.n, args.n),
+           "coarse_stride": list(d["stride"]), "delta": delta},
+          full_domain={"sweeps": fst["iterations"], "jacobi_sweeps": iters_full, "ms": ms_full,
+                       "node_updates_per_s": nfree * iters_full / (ms_full / 1e3)},
+          decomposed={"ms_ra": rst["ms"], "ms_fine": tot["ms"], "max_subdomain_iters": tot["iterations"],
+                      "labelled_fraction": rst["labelled"] / d["labels"].size,
+                      "max_abs_diff_vs_full": float((Vb - Vf).abs().max().item()),
+                      "solved_subdomains": sum(1 for s in per if s["node_updates"] > 0)},
+          raw_node_updates_per_s=(rst["node_updates"] + tot["node_updates"]) / (ms / 1e3),
+          roofline={"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s",
+                    "frac": ach / peak, "traffic": None, "kernel": "sweep2d_kernel<0,V,2> (game)",
+                    "evaluations_per_node_update": pairs},
+          cpu_baseline=None, gpu_launches=rst["launches"] + tot["launches"], clocks=clocks)
+
+
 def run_batch(args, hjb, S, dev, flush, local):
     """512 independent square problems, sides ~ U{64..512}, one launch."""
     import numpy as np
@@ -465,7 +507,7 @@ def main():
         dev = lambda a, dt=np.float32: torch.as_tensor(np.ascontiguousarray(np.asarray(a).astype(dt))).cuda()  # noqa
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         {"dubins": run_dubins, "batch": run_batch, "adjoint": run_adjoint,
-         "vdp": run_vdp}[args.workload](
+         "vdp": run_vdp, "game": run_game}[args.workload](
             args, hjb, S, dev, flush, local)
         return
     import numpy as np

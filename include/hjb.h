@@ -71,7 +71,11 @@ typedef struct {
  *  HJB_DYN_SPEED_CURRENT (2D): f = s(x) a + c(x), a in R^2 a control.
  *     speed: node field s [N] (device or host), NULL means s = 1;
  *     log_speed: node field theta [N] with s = exp(theta) (use one of the two);
+ *     scale: node field D [N][2] of per-axis factors, f = diag(D(x)) a + c(x)
+ *            (instead of speed / log_speed; Sec. 5, Example ex4);
  *     current: node field c [N][2], NULL means c = 0.
+ *     With a second player (hjb_controls.count_b > 0) the control enters
+ *     as a - b: f = D(x) (a - b) + c(x).
  *  HJB_DYN_DUBINS (3D, dimension 2 is the heading theta, periodic):
  *     f = (v cos theta, v sin theta, u), u a scalar control; v = dubins_v. */
 #define HJB_DYN_SPEED_CURRENT 0
@@ -82,6 +86,7 @@ typedef struct {
     const float *current;
     const float *log_speed;
     double dubins_v;
+    const float *scale;
 } hjb_dynamics;
 
 /* Running cost l > 0 (hypothesis H0): a node field [N], or the constant
@@ -100,11 +105,19 @@ typedef struct {
 
 /* Discrete control set A (Sec. 3: "a discrete version of the control
  * space"), host memory [count][dim], copied at hjb_create.  dim = 2 for
- * HJB_DYN_SPEED_CURRENT, 1 for HJB_DYN_DUBINS.  count <= HJB_MAX_CONTROLS. */
+ * HJB_DYN_SPEED_CURRENT, 1 for HJB_DYN_DUBINS.  count <= HJB_MAX_CONTROLS.
+ * Differential games (Sec. 2, the max over b of the min over a; Example
+ * ex4): count_b > 0 gives the second player's set B, host [count_b][dim],
+ * and T(V)_i = beta max_b min_a I[V](x_i + h f(x_i, a, b)) + gamma l_i.
+ * 2D speed/current dynamics only; count * count_b <= HJB_MAX_CONTROLS; not
+ * supported by hjb_backward and hjb_solve_static.  count_b = 0: no second
+ * player. */
 typedef struct {
     int count;
     int dim;
     const float *a;
+    int count_b;
+    const float *b;
 } hjb_controls;
 
 /* Target (the boundary set Gamma / dG of Sec. 3, with exit cost g = 0),

@@ -47,6 +47,7 @@ class _Prob(C.Structure):
         ("h", C.c_double), ("lam", C.c_double),
         ("ncontrols", C.c_int), ("cdim", C.c_int), ("controls", C.c_void_p),
         ("target", C.c_void_p), ("ntargets", C.c_int), ("v_out", C.c_double),
+        ("scale", C.c_void_p), ("nb", C.c_int), ("controls_b", C.c_void_p),
     ]
 
 
@@ -108,7 +109,7 @@ class Problem:
 
     def __init__(self, shape, lo, hi, controls, target, h, lam=1.0, periodic=None,
                  dyn=0, speed=None, current=None, dubins_v=1.0, cost=None,
-                 cost_const=1.0, v_out=1.0, ntargets=None):
+                 cost_const=1.0, v_out=1.0, ntargets=None, scale=None, controls_b=None):
         self.ndim = len(shape)
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
@@ -118,6 +119,9 @@ class Problem:
         self.speed = _f64(None if speed is None else np.asarray(speed).reshape(-1))
         self.current = _f64(None if current is None else np.asarray(current).reshape(-1, 2))
         self.cost = _f64(None if cost is None else np.asarray(cost).reshape(-1))
+        self.scale = _f64(None if scale is None else np.asarray(scale).reshape(-1, 2))
+        self.controls_b = None if controls_b is None else _f64(
+            np.asarray(controls_b, dtype=np.float64).reshape(len(controls_b), -1))
         self.ntargets = int(self.target.max()) if ntargets is None else int(ntargets)
         per = [0, 0, 0] if periodic is None else list(periodic) + [0] * (3 - len(periodic))
         s = _Prob()
@@ -141,6 +145,9 @@ class Problem:
         s.target = _ptr(self.target)
         s.ntargets = self.ntargets
         s.v_out = float(v_out)
+        s.scale = _ptr(self.scale)
+        s.nb = 0 if self.controls_b is None else self.controls_b.shape[0]
+        s.controls_b = _ptr(self.controls_b)
         self._s = s
         self.h, self.lam, self.v_out = float(h), float(lam), float(v_out)
         self.lo, self.hi, self.periodic = list(lo), list(hi), per[: self.ndim]

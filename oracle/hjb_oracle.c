@@ -24,6 +24,10 @@
  *       fine node belongs to sub-domain k iff every vertex carrying a
  *       non-zero barycentric weight is labelled k.
  *   R10 ties in the control minimum go to the lowest control index.
+ *   Games (Sec. 2 "max_b min_a", Example ex4): with a second control set B
+ *       the operator is beta * max_b min_a I[V](x_i + h f(x_i, a, b)) +
+ *       gamma * l_i, f = D(x)(a - b) + c(x); D(x) = diag(scale) per node, or
+ *       s(x) I, or I.
  *
  * Parity unpinned: none of the functions below is unpinned; the pins live in
  * tests/test_oracle_pins.py (brute force, BFS graph case, closed forms,
@@ -59,6 +63,9 @@ typedef struct {
     const int32_t *target; /* [N] 0 free, k >= 1 target component k */
     int ntargets;
     double v_out;          /* value of ghost nodes / feet outside the box */
+    const double *scale;   /* [N][2] per-axis factors D(x) of f, or NULL (dyn 0) */
+    int nb;                /* size of the second player's set B (0: none) */
+    const double *controls_b; /* [nb][cdim] */
 } ohjb_problem;
 
 static long long node_count(const ohjb_problem *p) {
@@ -151,16 +158,29 @@ double ohjb_interp(const ohjb_problem *p, const double *V, const double *y) {
     return q1_at(p, V, g, NULL);
 }
 
-/* Dynamics f(x_i, a_j) of Sec. 2 for the two families. */
-static void dynamics(const ohjb_problem *p, long long i, const int idx[3], int j,
+/* Dynamics f(x_i, a_j) of Sec. 2 for the two families; with a second
+ * player (k >= 0) the control enters as a_j - b_k (Example ex4). */
+static void dynamics(const ohjb_problem *p, long long i, const int idx[3], int j, int k,
                      double f[3]) {
     const double *a = p->controls + (long long)j * p->cdim;
     if (p->dyn == 0) {
-        double s = p->speed ? p->speed[i] : 1.0;
+        double ux = a[0], uy = a[1];
+        if (k >= 0) {
+            const double *b = p->controls_b + (long long)k * p->cdim;
+            ux -= b[0];
+            uy -= b[1];
+        }
+        double sx = 1.0, sy = 1.0;
+        if (p->scale) {
+            sx = p->scale[2 * i];
+            sy = p->scale[2 * i + 1];
+        } else if (p->speed) {
+            sx = sy = p->speed[i];
+        }
         double cx = p->current ? p->current[2 * i] : 0.0;
         double cy = p->current ? p->current[2 * i + 1] : 0.0;
-        f[0] = s * a[0] + cx;
-        f[1] = s * a[1] + cy;
+        f[0] = sx * ux + cx;
+        f[1] = sy * uy + cy;
         f[2] = 0.0;
     } else {
         double th = p->lo[2] + idx[2] * spacing(p, 2);
@@ -170,12 +190,13 @@ static void dynamics(const ohjb_problem *p, long long i, const int idx[3], int j
     }
 }
 
-/* Foot of the characteristic y = x_i + h f(x_i, a_j) in grid coordinates.
- * Returns 0 when the foot is strictly outside the closed box (reading R2). */
-static int foot(const ohjb_problem *p, long long i, const int idx[3], int j,
-                double g[3], double off[3]) {
+/* Foot of the characteristic y = x_i + h f(x_i, a_j[, b_k]) in grid
+ * coordinates.  Returns 0 when the foot is strictly outside the closed box
+ * (reading R2). */
+static int foot_game(const ohjb_problem *p, long long i, const int idx[3], int j, int k,
+                     double g[3], double off[3]) {
     double f[3];
-    dynamics(p, i, idx, j, f);
+    dynamics(p, i, idx, j, k, f);
     int inside = 1;
     for (int d = 0; d < p->ndim; ++d) {
         double o = p->h * f[d] / spacing(p, d);
@@ -190,6 +211,11 @@ static int foot(const ohjb_problem *p, long long i, const int idx[3], int j,
         }
     }
     return inside;
+}
+
+static int foot(const ohjb_problem *p, long long i, const int idx[3], int j, double g[3],
+                double off[3]) {
+    return foot_game(p, i, idx, j, -1, g, off);
 }
 
 /* Node classes of Sec. 3: ghost (Phi), boundary/target (dG), interior (G).
@@ -222,6 +248,30 @@ static double apply_node(const ohjb_problem *p, const double *V, long long i,
     unflatten(p, i, idx);
     double best = INFINITY;
     int32_t barg = -1;
+    if (p->nb > 0) {
+        /* max over the second player's b of the min over a (Example ex4);
+         * arg: the minimising a under the maximising b */
+        best = -INFINITY;
+        for (int k = 0; k < p->nb; ++k) {
+            double inner = INFINITY;
+            int32_t ja = -1;
+            for (int j = 0; j < p->ncontrols; ++j) {
+                double g[3], off[3];
+                double q = foot_game(p, i, idx, j, k, g, off) ? q1_at(p, V, g, NULL) : p->v_out;
+                if (q < inner) {
+                    inner = q;
+                    ja = j;
+                }
+            }
+            if (inner > best) {
+                best = inner;
+                barg = ja;
+            }
+        }
+        if (arg) *arg = barg;
+        double l = p->cost ? p->cost[i] : p->cost_const;
+        return beta_of(p) * best + gamma_of(p) * l;
+    }
     for (int j = 0; j < p->ncontrols; ++j) {
         double g[3], off[3];
         double q = foot(p, i, idx, j, g, off) ? q1_at(p, V, g, NULL) : p->v_out;
@@ -361,6 +411,7 @@ static int make_coarse(const ohjb_problem *p, const int stride[3], double h_coar
     double *sp = p->speed ? (double *)malloc(sizeof(double) * NK) : NULL;
     double *cu = p->current ? (double *)malloc(sizeof(double) * 2 * NK) : NULL;
     double *co = p->cost ? (double *)malloc(sizeof(double) * NK) : NULL;
+    double *sc = p->scale ? (double *)malloc(sizeof(double) * 2 * NK) : NULL;
     int32_t *ta = (int32_t *)malloc(sizeof(int32_t) * NK);
     for (long long k = 0; k < NK; ++k) {
         int ik[3], ifn[3] = {0, 0, 0};
@@ -373,11 +424,16 @@ static int make_coarse(const ohjb_problem *p, const int stride[3], double h_coar
             cu[2 * k + 1] = p->current[2 * i + 1];
         }
         if (co) co[k] = p->cost[i];
+        if (sc) {
+            sc[2 * k] = p->scale[2 * i];
+            sc[2 * k + 1] = p->scale[2 * i + 1];
+        }
         ta[k] = p->target[i];
     }
     q->speed = sp;
     q->current = cu;
     q->cost = co;
+    q->scale = sc;
     q->target = ta;
     return 0;
 }
@@ -386,6 +442,7 @@ static void free_coarse(ohjb_problem *q) {
     free((void *)q->speed);
     free((void *)q->current);
     free((void *)q->cost);
+    free((void *)q->scale);
     free((void *)q->target);
 }
 

@@ -99,14 +99,17 @@ class Problem:
     shape: nodes per dimension (x first); lo/hi: the box (period for the
     periodic heading of the Dubins car); controls: [A, 2] vectors (speed /
     current dynamics) or [A, 1] turn rates (Dubins); labels: target labels
-    per node (0 free, k target component k); speed / log_speed / current /
-    cost: optional node fields; h, lam: time step and discount rate.
+    per node (0 free, k target component k); speed / log_speed / scale
+    (per-axis factors [N, 2]) / current / cost: optional node fields; h, lam:
+    time step and discount rate; controls_b: the second player's set of a
+    differential game ([B, 2], f = D (a - b) + c).
     Node arrays are in (z,) y, x order with x fastest.
     """
 
     def __init__(self, shape, lo, hi, controls, labels, h, lam=1.0, n_targets=None,
                  dyn=HJB_DYN_SPEED_CURRENT, speed=None, current=None, log_speed=None,
-                 dubins_v=1.0, cost=None, cost_const=1.0, value_out=1.0, periodic=None):
+                 dubins_v=1.0, cost=None, cost_const=1.0, value_out=1.0, periodic=None,
+                 scale=None, controls_b=None):
         L = _capi.lib()
         nd = len(shape)
         self.shape = tuple(int(s) for s in shape)
@@ -117,6 +120,9 @@ class Problem:
         self.current = None if current is None else _as_dtype(current, np.float32).reshape(-1)
         self.log_speed = None if log_speed is None else _as_dtype(log_speed, np.float32).reshape(-1)
         self.cost = None if cost is None else _as_dtype(cost, np.float32).reshape(-1)
+        self.scale = None if scale is None else _as_dtype(scale, np.float32).reshape(-1)
+        self.controls_b = None if controls_b is None else np.ascontiguousarray(
+            np.asarray(controls_b, dtype=np.float32).reshape(len(controls_b), -1))
         self.controls = np.ascontiguousarray(np.asarray(controls, dtype=np.float32).reshape(
             len(controls), -1))
         self.on_gpu = _is_torch(self.labels) and self.labels.is_cuda
@@ -140,6 +146,7 @@ class Problem:
         dy.current = _ptr(self.current)
         dy.log_speed = _ptr(self.log_speed)
         dy.dubins_v = float(dubins_v)
+        dy.scale = _ptr(self.scale)
         co = _capi.hjb_cost()
         co.l = _ptr(self.cost)
         co.l_const = float(cost_const)
@@ -150,6 +157,9 @@ class Problem:
         ct.count = self.controls.shape[0]
         ct.dim = self.controls.shape[1]
         ct.a = self.controls.ctypes.data
+        if self.controls_b is not None:
+            ct.count_b = self.controls_b.shape[0]
+            ct.b = self.controls_b.ctypes.data
         tg = _capi.hjb_target()
         tg.labels = _ptr(self.labels)
         tg.n_targets = self.n_targets

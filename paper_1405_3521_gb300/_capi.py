@@ -48,7 +48,7 @@ class hjb_grid(C.Structure):
 
 class hjb_dynamics(C.Structure):
     _fields_ = [("kind", C.c_int), ("speed", C.c_void_p), ("current", C.c_void_p),
-                ("log_speed", C.c_void_p), ("dubins_v", C.c_double)]
+                ("log_speed", C.c_void_p), ("dubins_v", C.c_double), ("scale", C.c_void_p)]
 
 
 class hjb_cost(C.Structure):
@@ -60,7 +60,8 @@ class hjb_discount(C.Structure):
 
 
 class hjb_controls(C.Structure):
-    _fields_ = [("count", C.c_int), ("dim", C.c_int), ("a", C.c_void_p)]
+    _fields_ = [("count", C.c_int), ("dim", C.c_int), ("a", C.c_void_p), ("count_b", C.c_int),
+                ("b", C.c_void_p)]
 
 
 class hjb_target(C.Structure):

@@ -32,6 +32,7 @@ struct ControlTable {
     float ax[MAX_CTRL];
     float ay[MAX_CTRL];
     int count;
+    int nb;  // games: count = na * nb pairs a_j - b_k at k * na + j; else 1
 };
 // Shared-memory pair layout of the 2D sweep: row r, column c holds
 // (V[r][c], V[r][c+1]) as a float2; rows are PW float2 (512 bytes) apart.
@@ -44,6 +45,7 @@ struct alignas(128) SlotDesc {
     CUtensorMap tmap[2];        // TMA maps of the two iteration buffers
     float *V[2];                // pitched iteration buffers [nzl][ny][pitch]
     const float *speed;         // node field s (or null: s = 1)
+    const float2 *scale2;       // node field of per-axis factors (or null; replaces speed)
     const float *current;       // node field c [N][2] (or null)
     const float *cost;          // node field l (or null: constant)
     const uint8_t *labels;      // target labels [N]
@@ -163,8 +165,9 @@ struct GridDims {
 // be null).
 void launch_gather_coarse(const GridDims &fine, const GridDims &coarse, const int stride[3],
                           const float *speed, const float *current, const float *cost,
-                          const uint8_t *labels, float *c_speed, float *c_current,
-                          float *c_cost, uint8_t *c_labels, cudaStream_t st);
+                          const uint8_t *labels, const float *scale, float *c_speed,
+                          float *c_current, float *c_cost, uint8_t *c_labels, float *c_scale,
+                          cudaStream_t st);
 // RA steps 2-3: labels of the coarse nodes from the m auxiliary solutions
 // held by slots[0..m) (min property + threshold of eq. rep).  ties_out is an
 // unsigned long long counter (accumulated); vmin_out optional.

@@ -196,16 +196,18 @@ struct hjb_problem {
     hjb_grid grid;
     int kind;
     double dubins_v;
-    Field speed, current, log_speed, cost, labels;
+    Field speed, current, log_speed, cost, labels, scale;
     double l_const, h, lambda, value_out;
     int na, cdim;
     float ax[hjbk::MAX_CTRL], ay[hjbk::MAX_CTRL];
+    int nb = 0;  // second player's set B (games), 0: none
+    float bx[hjbk::MAX_CTRL], by[hjbk::MAX_CTRL];
     int ntargets;
     long long N;
     double dx[3];
     DevBuf speed_exp, trig;
     // coarse problem of the reconstruction
-    DevBuf c_speed, c_current, c_cost, c_labels, c_trig, c_mask, c_vstage, c_grad;
+    DevBuf c_speed, c_current, c_cost, c_labels, c_trig, c_mask, c_vstage, c_grad, c_scale;
     DevBuf tile_bits, fine_mask_dev, scratch_u64;
     DevBuf out_stage, out_stage2, out_stage3, in_stage;
     RunCtx full, ra, dec;
@@ -278,6 +280,7 @@ int encode_maps(SlotDesc &S, int ndim, int halo, int rows) {
 // largest foot displacement in cells (which selects the halo).
 struct Prep {
     const float *speed = nullptr;
+    const float *scale = nullptr;  // per-axis factors [N][2]
     const float *current = nullptr;
     const float *cost = nullptr;
     const uint8_t *labels = nullptr;
@@ -292,6 +295,8 @@ int prepare(hjb_problem *P, cudaStream_t st, Prep &out) {
     TRY(P->log_speed.refresh(st));
     TRY(P->cost.refresh(st));
     TRY(P->labels.refresh(st));
+    TRY(P->scale.refresh(st));
+    out.scale = static_cast<const float *>(P->scale.dev());
     out.labels = static_cast<const uint8_t *>(P->labels.dev());
     out.cost = static_cast<const float *>(P->cost.dev());
     out.current = static_cast<const float *>(P->current.dev());
@@ -305,36 +310,47 @@ int prepare(hjb_problem *P, cudaStream_t st, Prep &out) {
         out.speed = static_cast<const float *>(P->speed.dev());
     }
     if (P->kind == HJB_DYN_SPEED_CURRENT) {
+        // largest control components, over the pairs a - b in a game
         double amax_x = 0, amax_y = 0;
-        for (int j = 0; j < P->na; ++j) {
-            amax_x = std::fmax(amax_x, std::fabs(P->ax[j]));
-            amax_y = std::fmax(amax_y, std::fabs(P->ay[j]));
-        }
-        double smax = 1.0, cx = 0.0, cy = 0.0;
-        if (out.speed || out.current) {
+        for (int k = 0; k < (P->nb ? P->nb : 1); ++k)
+            for (int j = 0; j < P->na; ++j) {
+                amax_x = std::fmax(amax_x, std::fabs(P->ax[j] - (P->nb ? P->bx[k] : 0.0f)));
+                amax_y = std::fmax(amax_y, std::fabs(P->ay[j] - (P->nb ? P->by[k] : 0.0f)));
+            }
+        double sxmax = 1.0, symax = 1.0, cx = 0.0, cy = 0.0;
+        if (out.speed || out.scale || out.current) {
             TRY(P->scratch_u64.ensure(64));
             unsigned *d = P->scratch_u64.as<unsigned>();
-            CK(cudaMemsetAsync(d, 0, 3 * sizeof(unsigned), st));
+            CK(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned), st));
             if (out.speed) {
                 hjbh::launch_absmax(out.speed, P->N, 1, 0, d, st);
                 out.launches += 1;
+            }
+            if (out.scale) {
+                hjbh::launch_absmax(out.scale, P->N, 2, 0, d, st);
+                hjbh::launch_absmax(out.scale, P->N, 2, 1, d + 3, st);
+                out.launches += 2;
             }
             if (out.current) {
                 hjbh::launch_absmax(out.current, P->N, 2, 0, d + 1, st);
                 hjbh::launch_absmax(out.current, P->N, 2, 1, d + 2, st);
                 out.launches += 2;
             }
-            unsigned h[3];
+            unsigned h[4];
             CK(cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            float f[3];
+            float f[4];
             std::memcpy(f, h, sizeof f);
-            if (out.speed) smax = f[0];
+            if (out.speed) sxmax = symax = f[0];
+            if (out.scale) {
+                sxmax = f[0];
+                symax = f[3];
+            }
             cx = f[1];
             cy = f[2];
         }
-        const double ox = (smax * amax_x + cx) * P->h / P->dx[0];
-        const double oy = (smax * amax_y + cy) * P->h / P->dx[1];
+        const double ox = (sxmax * amax_x + cx) * P->h / P->dx[0];
+        const double oy = (symax * amax_y + cy) * P->h / P->dx[1];
         out.max_off_xy = std::fmax(ox, oy);
     } else {
         out.max_off_xy = std::fabs(P->dubins_v) * P->h / std::fmin(P->dx[0], P->dx[1]);
@@ -397,6 +413,7 @@ void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &
     S.gamma = static_cast<float>(gamma);
     S.gl = static_cast<float>(gamma * P->l_const);
     S.speed = pr.speed;
+    S.scale2 = reinterpret_cast<const float2 *>(pr.scale);
     S.current = pr.current;
     S.cost = wform ? nullptr : pr.cost;
     S.labels = pr.labels;
@@ -457,17 +474,30 @@ int dubins_trig(const hjb_problem *P, DevBuf &buf, int nz, double h, const doubl
     return HJB_OK;
 }
 
+// The control vectors of the kernels.  In a game the entry k * na + j is
+// the pair a_j - b_k, and the kernel takes the max over the nb blocks of the
+// min within a block (the min over a for each b).
 hjbk::ControlTable control_table(const hjb_problem *P) {
     hjbk::ControlTable c;
     std::memset(&c, 0, sizeof c);
-    c.count = P->na;
-    for (int j = 0; j < P->na; ++j) {
-        c.ax[j] = P->ax[j];
-        c.ay[j] = P->ay[j];
-        c.a2[j] = make_float2(P->ax[j], P->ay[j]);
-    }
+    const int nb = P->nb ? P->nb : 1;
+    c.count = P->na * nb;
+    c.nb = nb;
+    for (int k = 0; k < nb; ++k)
+        for (int j = 0; j < P->na; ++j) {
+            const float x = P->ax[j] - (P->nb ? P->bx[k] : 0.0f);
+            const float y = P->ay[j] - (P->nb ? P->by[k] : 0.0f);
+            c.ax[k * P->na + j] = x;
+            c.ay[k * P->na + j] = y;
+            c.a2[k * P->na + j] = make_float2(x, y);
+        }
     return c;
 }
+
+// Kernel family for a problem: compile-time control counts (32, 64) only
+// without a second player; a game runs the generic kernel with one control
+// group (all pairs of a node in one thread) and 8-row tiles.
+int key_na(const hjb_problem *P) { return P->nb ? 0 : P->na; }
 
 // Allocate iteration buffers for the slots (laid out back to back, each
 // 256-byte aligned) and encode their TMA maps.
@@ -813,14 +843,16 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
         if (grid->periodic[0] || grid->periodic[1])
             return fail(HJB_ERR_UNSUPPORTED, "periodic dimensions are supported for theta (Dubins) only");
         if (controls->dim != 2) return fail(HJB_ERR_INVALID_ARG, "controls must be 2D vectors");
-        if (dyn->speed && dyn->log_speed)
-            return fail(HJB_ERR_INVALID_ARG, "give either speed or log_speed");
+        if ((dyn->speed ? 1 : 0) + (dyn->log_speed ? 1 : 0) + (dyn->scale ? 1 : 0) > 1)
+            return fail(HJB_ERR_INVALID_ARG, "give one of speed, log_speed and scale");
     } else if (dyn->kind == HJB_DYN_DUBINS) {
         if (grid->ndim != 3 || !grid->periodic[2] || grid->periodic[0] || grid->periodic[1])
             return fail(HJB_ERR_INVALID_ARG, "Dubins needs a 3D grid, periodic in dimension 2 only");
         if (controls->dim != 1) return fail(HJB_ERR_INVALID_ARG, "Dubins controls are scalars");
-        if (dyn->speed || dyn->current || dyn->log_speed)
+        if (dyn->speed || dyn->current || dyn->log_speed || dyn->scale)
             return fail(HJB_ERR_UNSUPPORTED, "Dubins takes no node fields");
+        if (controls->count_b)
+            return fail(HJB_ERR_UNSUPPORTED, "games are supported for 2D speed/current dynamics");
     } else {
         return fail(HJB_ERR_INVALID_ARG, "unknown dynamics kind %d", dyn->kind);
     }
@@ -829,6 +861,14 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
     for (int j = 0; j < controls->count * controls->dim; ++j)
         if (!std::isfinite(controls->a[j]) || std::fabs(controls->a[j]) > 1e6f)
             return fail(HJB_ERR_INVALID_ARG, "control component %d is not a finite value", j);
+    if (controls->count_b < 0 || (controls->count_b > 0 && !controls->b) ||
+        controls->count * (controls->count_b > 0 ? controls->count_b : 1) > HJB_MAX_CONTROLS)
+        return fail(HJB_ERR_INVALID_ARG,
+                    "the second player's set needs count_b >= 0 vectors and count * count_b <= %d",
+                    HJB_MAX_CONTROLS);
+    for (int j = 0; j < controls->count_b * controls->dim; ++j)
+        if (!std::isfinite(controls->b[j]) || std::fabs(controls->b[j]) > 1e6f)
+            return fail(HJB_ERR_INVALID_ARG, "component %d of the second player's set is not finite", j);
     if (!std::isfinite(dyn->dubins_v) || !std::isfinite(disc->h) || !std::isfinite(disc->lambda) ||
         !std::isfinite(target->value_out) || !std::isfinite(cost->l_const))
         return fail(HJB_ERR_INVALID_ARG, "non-finite scalar parameter");
@@ -853,6 +893,7 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
     P->speed.set(dyn->speed, N * sizeof(float));
     P->current.set(dyn->current, 2 * N * sizeof(float));
     P->log_speed.set(dyn->log_speed, N * sizeof(float));
+    P->scale.set(dyn->scale, 2 * N * sizeof(float));
     P->cost.set(cost->l, N * sizeof(float));
     P->labels.set(target->labels, N);
     P->l_const = cost->l ? 1.0 : cost->l_const;
@@ -865,6 +906,11 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
     for (int j = 0; j < P->na; ++j) {
         P->ax[j] = controls->a[j * controls->dim];
         P->ay[j] = controls->dim > 1 ? controls->a[j * controls->dim + 1] : 0.0f;
+    }
+    P->nb = controls->count_b;
+    for (int k = 0; k < P->nb; ++k) {
+        P->bx[k] = controls->b[k * controls->dim];
+        P->by[k] = controls->dim > 1 ? controls->b[k * controls->dim + 1] : 0.0f;
     }
     for (int d = 0; d < 3; ++d)
         P->dx[d] = P->grid.periodic[d] ? (P->grid.hi[d] - P->grid.lo[d]) / P->grid.n[d]
@@ -891,7 +937,7 @@ int hjb_destroy(hjb_problem *P) {
     P->adj_v.release();
     DevBuf *bufs[] = {&P->speed_exp, &P->trig,     &P->c_speed,      &P->c_current,
                       &P->c_cost,    &P->c_labels, &P->c_trig,       &P->c_mask,
-                      &P->c_vstage,  &P->c_grad,   &P->tile_bits,
+                      &P->c_vstage,  &P->c_grad,   &P->tile_bits, &P->c_scale,
                       &P->fine_mask_dev, &P->scratch_u64, &P->out_stage, &P->out_stage2,
                       &P->out_stage3, &P->in_stage};
     for (DevBuf *b : bufs) b->release();
@@ -900,6 +946,7 @@ int hjb_destroy(hjb_problem *P) {
     P->log_speed.release();
     P->cost.release();
     P->labels.release();
+    P->scale.release();
     delete P;
     return HJB_OK;
 }
@@ -946,7 +993,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_ou
     CK(cudaEventRecord(R.ev0, st));
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), 1, static_cast<int>(P->N), wform, c_over,
                              vinit, st);
-    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
                              8 / rows, loop_mode()};
     const hjbk::ControlTable ctrl = control_table(P);
     TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, local_iters(opts)));
@@ -982,7 +1029,7 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
     if (!P || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL problem or output");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (P->kind == HJB_DYN_DUBINS) return solve_full(P, opts, hjbk::TY, v_out, stats, st);
+    if (P->kind == HJB_DYN_DUBINS || P->nb) return solve_full(P, opts, hjbk::TY, v_out, stats, st);
     const std::vector<long long> key = {0, P->kind, P->grid.n[0], P->grid.n[1], P->na,
                                         P->cost.user ? 1 : 0};
     return tuned_call(key, [&](int rows, double *ms) {
@@ -1030,11 +1077,14 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     if (pr.speed) TRY(P->c_speed.ensure(NK * sizeof(float)));
     if (pr.current) TRY(P->c_current.ensure(2 * NK * sizeof(float)));
     if (pr.cost) TRY(P->c_cost.ensure(NK * sizeof(float)));
+    if (pr.scale) TRY(P->c_scale.ensure(2 * NK * sizeof(float)));
     hjbh::launch_gather_coarse(fine, coarse, stride, pr.speed, pr.current, pr.cost, pr.labels,
-                               P->c_speed.as<float>(), P->c_current.as<float>(),
-                               P->c_cost.as<float>(), P->c_labels.as<uint8_t>(), st);
+                               pr.scale, P->c_speed.as<float>(), P->c_current.as<float>(),
+                               P->c_cost.as<float>(), P->c_labels.as<uint8_t>(),
+                               P->c_scale.as<float>(), st);
     Prep cp = pr;
     cp.speed = pr.speed ? P->c_speed.as<float>() : nullptr;
+    cp.scale = pr.scale ? P->c_scale.as<float>() : nullptr;
     cp.current = pr.current ? P->c_current.as<float>() : nullptr;
     cp.cost = pr.cost ? P->c_cost.as<float>() : nullptr;
     cp.labels = P->c_labels.as<uint8_t>();
@@ -1053,7 +1103,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     std::memset(R.slots.data(), 0, m * sizeof(SlotDesc));
     if (P->kind == HJB_DYN_DUBINS)
         TRY(dubins_trig(P, P->c_trig, g.nz, hK, dxK, P->grid.lo[2], dxK[2], st));
-    const int rows = P->kind == HJB_DYN_DUBINS ? hjbk::TY : 2;
+    const int rows = (P->kind == HJB_DYN_DUBINS || P->nb) ? hjbk::TY : 2;
     for (int k = 0; k < m; ++k) {
         fill_slot(R.slots[k], P, g, cp, wform, hK, dxK, halo, tol, max_iters, rows);
         R.slots[k].only_target = k + 1;  // RA step 1: dG := X_k
@@ -1065,7 +1115,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     CK(cudaEventRecord(R.ev0, st));
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform, c_over,
                              nullptr, st);
-    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
                              8 / rows, loop_mode()};
     TRY(run_loop(R, key, 8, control_table(P), st, local_iters(nullptr)));
     // threshold of eq. (rep)
@@ -1205,7 +1255,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
                            P->tile_bits.as<uint32_t>(), st, diff, m);
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
                              nullptr, st);
-    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P->na, halo, rows,
+    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
                              8 / rows, loop_mode()};
     // sub-domains with equal node sets are solved once (V_k depends on the
     // node set alone: its targets are the target nodes inside it)
@@ -1265,7 +1315,7 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     if (!P || !fine_mask || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (P->kind == HJB_DYN_DUBINS)
+    if (P->kind == HJB_DYN_DUBINS || P->nb)
         return solve_dec(P, fine_mask, opts, hjbk::TY, v_out, per_subdomain, total, st);
     const std::vector<long long> key = {1, P->kind, P->grid.n[0], P->grid.n[1], P->na,
                                         P->cost.user ? 1 : 0, P->ntargets};
@@ -1297,6 +1347,8 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
             (P->cost.user == nullptr) != (P0->cost.user == nullptr) ||
             std::memcmp(P->ax, P0->ax, P->na * sizeof(float)) ||
             std::memcmp(P->ay, P0->ay, P->na * sizeof(float)) || P->l_const != P0->l_const ||
+            P->nb != P0->nb || std::memcmp(P->bx, P0->bx, P->nb * sizeof(float)) ||
+            std::memcmp(P->by, P0->by, P->nb * sizeof(float)) ||
             P->lambda != P0->lambda)
             return fail(HJB_ERR_INVALID_ARG,
                         "problem %d differs from problem 0 in dynamics kind, controls, cost form "
@@ -1331,7 +1383,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
     CK(cudaEventRecord(R.ev0, st));
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), count, static_cast<int>(maxN), wform, c_over,
                              nullptr, st);
-    const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, P0->na, halo, rows,
+    const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P0), halo, rows,
                              8 / rows, loop_mode()};
     TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st, local_iters(opts)));
     for (int i = 0; i < count; ++i) {
@@ -1376,7 +1428,7 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
     TRY(check_opts(opts));
     if (!problems[0]) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (problems[0]->kind == HJB_DYN_DUBINS)
+    if (problems[0]->kind == HJB_DYN_DUBINS || problems[0]->nb)
         return solve_batch_impl(problems, count, opts, hjbk::TY, v_out, per_problem, st);
     long long nodes = 0;
     for (int i = 0; i < count; ++i) nodes += problems[i] ? problems[i]->N : 0;
@@ -1397,6 +1449,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     if (wrt != 0 && wrt != 1) return fail(HJB_ERR_INVALID_ARG, "wrt must be 0 (log-speed) or 1 (cost)");
     if (P->kind != HJB_DYN_SPEED_CURRENT)
         return fail(HJB_ERR_UNSUPPORTED, "the adjoint is implemented for 2D speed/current dynamics");
+    if (P->nb || P->scale.user)
+        return fail(HJB_ERR_UNSUPPORTED, "the adjoint does not handle games or per-axis scale fields");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Prep pr;
@@ -1648,6 +1702,8 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     if (!cost->l && !(cost->l_const > 0))
         return fail(HJB_ERR_INVALID_ARG, "constant running cost must be positive");
     if (dyn->speed && dyn->log_speed) return fail(HJB_ERR_INVALID_ARG, "give speed or log_speed");
+    if (dyn->scale || controls->count_b)
+        return fail(HJB_ERR_UNSUPPORTED, "the static solve takes no scale field and no second player");
     if (opts && opts->max_iters < 0) return fail(HJB_ERR_INVALID_ARG, "max_iters < 0");
     // every array must already be device memory: staging host data would allocate
     const void *ptrs[6] = {dyn->speed, dyn->current, dyn->log_speed, cost->l, target->labels, v_out};

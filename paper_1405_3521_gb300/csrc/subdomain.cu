@@ -32,8 +32,9 @@ __device__ __forceinline__ long long count(const hjbh::GridDims &g) {
 
 __global__ void gather_coarse_kernel(hjbh::GridDims fine, hjbh::GridDims coarse, int r0, int r1,
                                      int r2, const float *speed, const float *current,
-                                     const float *cost, const uint8_t *labels, float *c_speed,
-                                     float *c_current, float *c_cost, uint8_t *c_labels) {
+                                     const float *cost, const uint8_t *labels, const float *scale,
+                                     float *c_speed, float *c_current, float *c_cost,
+                                     uint8_t *c_labels, float *c_scale) {
     const long long NK = count(coarse);
     GRID_STRIDE(k, NK) {
         int c[3];
@@ -45,6 +46,10 @@ __global__ void gather_coarse_kernel(hjbh::GridDims fine, hjbh::GridDims coarse,
             c_current[2 * k + 1] = current[2 * i + 1];
         }
         if (c_cost) c_cost[k] = cost[i];
+        if (c_scale) {
+            c_scale[2 * k] = scale[2 * i];
+            c_scale[2 * k + 1] = scale[2 * i + 1];
+        }
         c_labels[k] = labels[i];
     }
 }
@@ -323,13 +328,14 @@ namespace hjbh {
 
 void launch_gather_coarse(const GridDims &fine, const GridDims &coarse, const int stride[3],
                           const float *speed, const float *current, const float *cost,
-                          const uint8_t *labels, float *c_speed, float *c_current, float *c_cost,
-                          uint8_t *c_labels, cudaStream_t st) {
+                          const uint8_t *labels, const float *scale, float *c_speed,
+                          float *c_current, float *c_cost, uint8_t *c_labels, float *c_scale,
+                          cudaStream_t st) {
     long long NK = static_cast<long long>(coarse.n[0]) * coarse.n[1] * (coarse.ndim > 2 ? coarse.n[2] : 1);
     gather_coarse_kernel<<<blocks_for(NK), THREADS, 0, st>>>(
         fine, coarse, stride[0], stride[1], coarse.ndim > 2 ? stride[2] : 1, speed, current, cost,
-        labels, speed ? c_speed : nullptr, current ? c_current : nullptr, cost ? c_cost : nullptr,
-        c_labels);
+        labels, scale, speed ? c_speed : nullptr, current ? c_current : nullptr,
+        cost ? c_cost : nullptr, c_labels, scale ? c_scale : nullptr);
 }
 
 void launch_label(const SlotDesc *slots, const SlotState *state, int m, const GridDims &coarse,

@@ -222,6 +222,20 @@ __device__ __forceinline__ float controls_interior(int g, const ControlTable &C,
         return best;
     } else {
         const int na = C.count;
+        if (C.nb > 1) {
+            // game (one control group): the max over b of the min over a, in
+            // the W form the min over b of the max over a
+            const int nA = na / C.nb;
+            float outer = WFORM ? INFINITY : -INFINITY;
+            for (int k = 0; k < na; k += nA) {
+                float inner = WFORM ? -INFINITY : INFINITY;
+#pragma unroll 4
+                for (int j = k; j < k + nA; ++j)
+                    inner = pick<WFORM>(inner, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
+                outer = WFORM ? fminf(outer, inner) : fmaxf(outer, inner);
+            }
+            return pick<WFORM>(best, outer);
+        }
 #pragma unroll 4
         for (int j = g; j < na; j += G)
             best = pick<WFORM>(best, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
@@ -245,6 +259,19 @@ __device__ __forceinline__ float controls_edge(int g, const ControlTable &C, uin
         return best;
     } else {
         const int na = C.count;
+        if (C.nb > 1) {
+            const int nA = na / C.nb;
+            float outer = WFORM ? INFINITY : -INFINITY;
+            for (int k = 0; k < na; k += nA) {
+                float inner = WFORM ? -INFINITY : INFINITY;
+#pragma unroll 4
+                for (int j = k; j < k + nA; ++j)
+                    inner = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2,
+                                                    vout, inner);
+                outer = WFORM ? fminf(outer, inner) : fmaxf(outer, inner);
+            }
+            return pick<WFORM>(best, outer);
+        }
 #pragma unroll 4
         for (int j = g; j < na; j += G)
             best = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2, vout, best);
@@ -573,14 +600,21 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
         float2 S2 = make_float2(0.0f, 0.0f), O02 = S2;
         float add = S.gl;
         if (isfree) {
-            const float s = S.speed ? S.speed[gi] : 1.0f;
+            float sx = 1.0f, sy = 1.0f;
+            if (S.scale2) {
+                const float2 d = S.scale2[gi];
+                sx = d.x;
+                sy = d.y;
+            } else if (S.speed) {
+                sx = sy = S.speed[gi];
+            }
             float cx = 0.0f, cy = 0.0f;
             if (S.current) {
                 const float2 c = reinterpret_cast<const float2 *>(S.current)[gi];
                 cx = c.x;
                 cy = c.y;
             }
-            S2 = make_float2(s * S.hx, s * S.hy);
+            S2 = make_float2(sx * S.hx, sy * S.hy);
             O02 = make_float2(cx * S.hx, cy * S.hy);
             if (!WFORM && S.cost) add = S.gamma * S.cost[gi];
         }

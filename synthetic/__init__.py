@@ -252,3 +252,31 @@ def vdp(n=101, A=21, slices=4, rho=0.2, stride=None):
         controls=f32(controls), labels=lab, ntargets=slices, speed=None,
         current=f32(drift), cost=f32(r), log_speed=None, h=2.0 / (n - 1), lam=1.0,
         v_out=float(np.float32(math.sqrt(2.0))), stride=(stride, stride))
+
+
+def pursuit_evasion(n=129, A=16, B=8, slices=4, rho=0.2, stride=None):
+    """The pursuit-evasion game of Sec. 5 (Example ex4): f(x, a, b) =
+    D(x) (a - b) with D(x) = diag(x2 + 1, 1), the pursuer's a on the unit
+    circle (A directions), the evader's b on the circle of radius 1/2 (B
+    directions), running cost l(x) = x1^2 + 0.1 (the printed "x1 + 0.1" is
+    negative on part of the box, against hypothesis H0; the Hamiltonian the
+    example states carries x1^2 + 0.1), lambda = 1, capture on the closed
+    disk B(0, rho) split into `slices` angular sectors, h = dx, value_out =
+    sup l / lambda = 1.1."""
+    X, Y = mesh2(n, n)
+    r = np.hypot(X, Y)
+    ang = np.mod(np.arctan2(Y, X), 2 * np.pi)
+    k = np.minimum((ang / (2 * np.pi / slices)).astype(np.int64), slices - 1) + 1
+    lab = np.where(r <= rho + 1e-12, k, 0).astype(np.uint8)
+    scale = np.stack([Y + 1.0, np.ones_like(Y)], axis=-1)
+    ta = 2 * np.pi * np.arange(A) / A
+    tb = 2 * np.pi * (np.arange(B) + 0.5) / B
+    if stride is None:
+        stride = next((s for s in (16, 10, 8, 5, 4, 2) if (n - 1) % s == 0), 1)
+    return dict(
+        shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+        controls=f32(np.stack([np.cos(ta), np.sin(ta)], -1)),
+        controls_b=f32(0.5 * np.stack([np.cos(tb), np.sin(tb)], -1)),
+        labels=lab, ntargets=slices, speed=None, current=None, scale=f32(scale),
+        cost=f32(X * X + 0.1), log_speed=None, h=2.0 / (n - 1), lam=1.0,
+        v_out=float(np.float32(1.1)), stride=(stride, stride))

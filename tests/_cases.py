@@ -7,7 +7,8 @@ def oracle_problem(orc, d, **over):
     kw = dict(speed=d.get("speed"), current=d.get("current"), cost=d.get("cost"),
               h=d["h"], lam=d.get("lam", 1.0), v_out=d.get("v_out", 1.0),
               ntargets=d["ntargets"], periodic=d.get("periodic"), dyn=d.get("dyn", 0),
-              dubins_v=d.get("dubins_v", 1.0))
+              dubins_v=d.get("dubins_v", 1.0), scale=d.get("scale"),
+              controls_b=d.get("controls_b"))
     if d.get("log_speed") is not None:
         kw["speed"] = np.exp(np.asarray(d["log_speed"], dtype=np.float32).astype(np.float64))
     kw.update(over)
@@ -29,7 +30,8 @@ def gpu_problem(hjb, d, device="cuda", host=False, **over):
     kw = dict(speed=t(d.get("speed")), current=t(d.get("current")), cost=t(d.get("cost")),
               log_speed=t(d.get("log_speed")), h=d["h"], lam=d.get("lam", 1.0),
               value_out=d.get("v_out", 1.0), n_targets=d["ntargets"],
-              periodic=d.get("periodic"), dyn=d.get("dyn", 0), dubins_v=d.get("dubins_v", 1.0))
+              periodic=d.get("periodic"), dyn=d.get("dyn", 0), dubins_v=d.get("dubins_v", 1.0),
+              scale=t(d.get("scale")), controls_b=d.get("controls_b"))
     kw.update(over)
     return hjb.Problem(d["shape"], d["lo"], d["hi"], np.asarray(d["controls"], np.float32),
                        t(d["labels"], torch.uint8), **kw)

@@ -418,3 +418,44 @@ def test_vdp_full_and_decomposed(hjb, orc):
     Vb, per, tot = hjb.solve_decomposed(p, fine_o)
     assert tot["converged"] == 1
     assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V
+
+
+def test_game_silent_second_player(hjb, orc):
+    """A second player whose only control is b = 0 leaves the control
+    problem unchanged (the game kernel path against the plain one)."""
+    d = S.c2(n=97, A=16, ntargets=3, stride=8)
+    p = gpu_problem(hjb, d)
+    V, _ = hjb.solve(p, local_iters=1)
+    g = dict(d)
+    g["controls_b"] = np.zeros((1, 2), np.float32)
+    Vg, st = hjb.solve(gpu_problem(hjb, g), local_iters=1)
+    assert st["converged"] == 1
+    assert np.abs(to_np(Vg) - to_np(V)).max() < 1e-6
+
+
+def test_pursuit_evasion_game(hjb, orc):
+    """The pursuit-evasion game (Sec. 5, Example ex4): per-axis scale field,
+    the max over the evader's b of the min over the pursuer's a, running cost
+    field; full solve, RA labels and the decomposed solve against the
+    oracle."""
+    d = S.pursuit_evasion(n=129, slices=4)
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-11, nthreads=8)
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p)
+    assert st["converged"] == 1
+    assert np.abs(to_np(V) - Vo).max() < TOL_V
+    stride, delta = d["stride"], 0.1
+    Vaux_o, lab_o, _ = orc.ra(po, stride, delta, tol=1e-11, nthreads=8)
+    fine_o = orc.project(po, stride, lab_o)
+    fine, coarse, aux, _ = hjb.subdomains(p, stride, delta=delta, want_aux=True)
+    assert np.abs(to_np(aux).reshape(Vaux_o.shape) - Vaux_o).max() < TOL_V
+    diff = to_np(coarse).astype(np.uint32) ^ lab_o
+    vmin = Vaux_o.min(0)
+    for k in range(d["ntargets"]):
+        bad = ((diff >> k) & 1) == 1
+        assert np.all(np.abs(np.abs(Vaux_o[k][bad] - vmin[bad]) - delta) <= TOL_V)
+    Vb_o, _, _, _ = orc.isa(po, fine_o, tol=1e-11, nthreads=8)
+    Vb, per, tot = hjb.solve_decomposed(p, fine_o)
+    assert tot["converged"] == 1
+    assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V

@@ -826,3 +826,97 @@ def _vdp_problem(orc, d):
     return orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"],
                        current=d["current"], cost=d["cost"], lam=d["lam"], v_out=d["v_out"],
                        ntargets=d["ntargets"])
+
+
+# --------------------------------------------------------------------------
+# Games (Sec. 2, "max_b min_a"; Example ex4): the second player's control b
+# enters as f = D(x)(a - b) + c(x).
+
+def test_game_with_a_silent_second_player_is_the_control_problem(orc):
+    d = S.c2(n=41, A=16, ntargets=3, stride=8)
+    base = dict(h=d["h"], speed=d["speed"], current=d["current"], ntargets=3)
+    p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], **base)
+    g = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"],
+                    controls_b=np.zeros((1, 2)), **base)
+    V, _, _ = orc.solve(p, tol=1e-13)
+    W, _, _ = orc.solve(g, tol=1e-13)
+    assert np.array_equal(V, W)
+
+
+def test_brute_force_game(orc):
+    """The game's fixed point is the best over the second player's
+    stationary strategies sigma of the first player's optimal value against
+    sigma: V = max_sigma V_sigma, node by node (T_sigma <= T with equality
+    at the maximising sigma, and both are monotone contractions).  V_sigma is
+    the minimum over every first-player policy of the dense linear solve."""
+    g = np.random.default_rng(11)
+    shape = (3, 2)
+    lo, hi = (0.0, 0.0), (2.0, 1.0)
+    N = 6
+    target = np.zeros(N, dtype=np.int32)
+    target[0] = 1
+    angA = 0.2 + 2 * np.pi / 3 * np.arange(3)
+    A = np.stack([np.cos(angA), np.sin(angA)], 1)
+    angB = 1.0 + np.pi * np.arange(2)
+    B = 0.5 * np.stack([np.cos(angB), np.sin(angB)], 1)
+    D = g.uniform(0.5, 1.5, (N, 2))
+    cur = g.uniform(-0.2, 0.2, (N, 2))
+    cost = g.uniform(0.5, 2.0, N)
+    lam, h, v_out = 0.8, 0.7, 3.0
+    free = [i for i in range(N) if target[i] == 0]
+    best = None
+    for sigma in itertools.product(range(len(B)), repeat=len(free)):
+        sg = dict(zip(free, sigma))
+        feet = [[h * (D[i] * (A[j] - B[sg.get(i, 0)]) + cur[i]) for j in range(len(A))]
+                for i in range(N)]
+        Vs = _brute_force(shape, (1.0, 1.0), (0, 0), target, feet, cost, lam, h, v_out)
+        best = Vs if best is None else np.maximum(best, Vs)
+    p = orc.Problem(shape, lo, hi, A, target, h=h, lam=lam, current=cur, cost=cost, v_out=v_out,
+                    scale=D, controls_b=B)
+    V, _, _ = orc.solve(p, tol=1e-15, max_iters=100000)
+    assert np.abs(V - best).max() < 1e-12
+
+
+def test_pursuit_evasion_strip_exact(orc):
+    """f = D (a - b), D = diag(d, 1), a in {+-e1, +-e2}, b in 1/2 {+-e1, +-e2},
+    target the strip |x1| <= 0.2, y periodic (V does not depend on y).  Away
+    from the strip the evader's best answer is b = -e1/2 (moving away), the
+    pursuer's a = -e1, so the foot lies o = d h / (2 dx) cells closer and the
+    scheme reduces to the recursion V_i = (beta o V_{i-1} + gamma) /
+    (1 - beta (1 - o)) from V = 0 on the strip (lambda = 1, l = 1): every
+    other pair of answers gives a smaller value."""
+    n, ny, d = 41, 4, 1.3
+    x = np.linspace(-1, 1, n)
+    h = 2.0 / (n - 1)
+    E = np.array([[1.0, 0.0], [-1.0, 0.0], [0.0, 1.0], [0.0, -1.0]])
+    lab = np.tile((np.abs(x) <= 0.2 + 1e-12).astype(np.uint8), (ny, 1))
+    D = np.tile([d, 1.0], (n * ny, 1))
+    p = orc.Problem((n, ny), (-1.0, 0.0), (1.0, 1.0), E, lab, h, periodic=(0, 1), scale=D,
+                    controls_b=0.5 * E)
+    V, _, _ = orc.solve(p, tol=1e-15, max_iters=100000)
+    V = V.reshape(ny, n)
+    beta = math.exp(-h)
+    gam = 1 - beta
+    o = 0.5 * d
+    ref = np.zeros(n)
+    c = n // 2
+    for i in range(c, n):
+        if abs(x[i]) > 0.2 + 1e-12:
+            ref[i] = (beta * o * ref[i - 1] + gam) / (1 - beta * (1 - o))
+    ref[:c] = ref[c + 1:][::-1]
+    assert np.abs(V - ref[None, :]).max() < 1e-12
+
+
+def test_scale_field_with_equal_axes_is_the_speed_field(orc):
+    """f = diag(D) a with D = (s, s) is f = s a: the full solve and the
+    coarse auxiliary solves of RA (which sample every node field at the
+    coarse stride) agree exactly."""
+    d = S.c2(n=49, A=16, ntargets=3, stride=8)
+    kw = dict(h=d["h"], current=d["current"], ntargets=3)
+    p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], speed=d["speed"], **kw)
+    D = np.repeat(np.asarray(d["speed"]).reshape(-1, 1), 2, axis=1)
+    q = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], scale=D, **kw)
+    assert np.array_equal(orc.solve(p, tol=1e-12)[0], orc.solve(q, tol=1e-12)[0])
+    Va, la, _ = orc.ra(p, (8, 8), 0.1, tol=1e-12)
+    Vb, lb, _ = orc.ra(q, (8, 8), 0.1, tol=1e-12)
+    assert np.array_equal(Va, Vb) and np.array_equal(la, lb)
