@@ -97,10 +97,18 @@ typedef struct {
     double l_const;
 } hjb_cost;
 
-/* Fictitious time step h and discount rate lambda > 0 (Sec. 3). */
+/* Fictitious time step h and discount rate lambda > 0 (Sec. 3).
+ *  weights: HJB_WEIGHTS_EXP (0): beta = exp(-lambda h), gamma = (1 - beta) /
+ *           lambda, the exact discount over one step;
+ *           HJB_WEIGHTS_IMPLICIT (1): beta = 1 / (1 + lambda h), gamma =
+ *           h / (1 + lambda h), the weights printed in the scheme of Sec. 3.
+ *  Both give the value l / lambda for a constant cost l. */
+#define HJB_WEIGHTS_EXP 0
+#define HJB_WEIGHTS_IMPLICIT 1
 typedef struct {
     double h;
     double lambda;
+    int weights;
 } hjb_discount;
 
 /* Discrete control set A (Sec. 3: "a discrete version of the control

@@ -48,6 +48,7 @@ class _Prob(C.Structure):
         ("ncontrols", C.c_int), ("cdim", C.c_int), ("controls", C.c_void_p),
         ("target", C.c_void_p), ("ntargets", C.c_int), ("v_out", C.c_double),
         ("scale", C.c_void_p), ("nb", C.c_int), ("controls_b", C.c_void_p),
+        ("weights", C.c_int),
     ]
 
 
@@ -109,7 +110,8 @@ class Problem:
 
     def __init__(self, shape, lo, hi, controls, target, h, lam=1.0, periodic=None,
                  dyn=0, speed=None, current=None, dubins_v=1.0, cost=None,
-                 cost_const=1.0, v_out=1.0, ntargets=None, scale=None, controls_b=None):
+                 cost_const=1.0, v_out=1.0, ntargets=None, scale=None, controls_b=None,
+                 weights=0):
         self.ndim = len(shape)
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
@@ -148,12 +150,15 @@ class Problem:
         s.scale = _ptr(self.scale)
         s.nb = 0 if self.controls_b is None else self.controls_b.shape[0]
         s.controls_b = _ptr(self.controls_b)
+        s.weights = int(weights)
         self._s = s
         self.h, self.lam, self.v_out = float(h), float(lam), float(v_out)
         self.lo, self.hi, self.periodic = list(lo), list(hi), per[: self.ndim]
 
     @property
     def beta(self):
+        if self._s.weights == 1:
+            return 1.0 / (1.0 + self.lam * self.h)
         return float(np.exp(-self.lam * self.h))
 
     def spacing(self, d):

@@ -66,6 +66,7 @@ typedef struct {
     const double *scale;   /* [N][2] per-axis factors D(x) of f, or NULL (dyn 0) */
     int nb;                /* size of the second player's set B (0: none) */
     const double *controls_b; /* [nb][cdim] */
+    int weights;           /* 0: beta = exp(-lambda h); 1: beta = 1/(1 + lambda h) */
 } ohjb_problem;
 
 static long long node_count(const ohjb_problem *p) {
@@ -230,8 +231,15 @@ static int node_class(const ohjb_problem *p, long long i, const uint32_t *mask,
     return NODE_FREE;
 }
 
-static double beta_of(const ohjb_problem *p) { return exp(-p->lambda * p->h); }
+/* Step weights (R1): beta = e^{-lambda h}, gamma = (1 - beta) / lambda; or
+ * the weights printed in the scheme of Sec. 3, beta = 1/(1 + lambda h) and
+ * gamma = h/(1 + lambda h). */
+static double beta_of(const ohjb_problem *p) {
+    if (p->weights == 1) return 1.0 / (1.0 + p->lambda * p->h);
+    return exp(-p->lambda * p->h);
+}
 static double gamma_of(const ohjb_problem *p) {
+    if (p->weights == 1) return p->h / (1.0 + p->lambda * p->h);
     return (1.0 - exp(-p->lambda * p->h)) / p->lambda;
 }
 

@@ -198,6 +198,7 @@ struct hjb_problem {
     double dubins_v;
     Field speed, current, log_speed, cost, labels, scale;
     double l_const, h, lambda, value_out;
+    int weights = HJB_WEIGHTS_EXP;
     int na, cdim;
     float ax[hjbk::MAX_CTRL], ay[hjbk::MAX_CTRL];
     int nb = 0;  // second player's set B (games), 0: none
@@ -221,6 +222,15 @@ struct hjb_problem {
 };
 
 namespace {
+
+// Step weights of the operator, beta I[V] + gamma l (hjb_discount.weights).
+double beta_w(int weights, double lambda, double h) {
+    return weights == HJB_WEIGHTS_IMPLICIT ? 1.0 / (1.0 + lambda * h) : std::exp(-lambda * h);
+}
+double gamma_w(int weights, double lambda, double h) {
+    return weights == HJB_WEIGHTS_IMPLICIT ? h / (1.0 + lambda * h)
+                                           : -std::expm1(-lambda * h) / lambda;
+}
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -390,8 +400,8 @@ int halo_for(const hjb_problem *P, double max_off, double max_off_z, int *halo) 
 // Fill the fields of a slot that depend on the problem statement.
 void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &pr, bool wform,
                double h, const double dx[3], int halo, double tol, int max_iters, int rows) {
-    const double beta = std::exp(-P->lambda * h);
-    const double gamma = -std::expm1(-P->lambda * h) / P->lambda;
+    const double beta = beta_w(P->weights, P->lambda, h);
+    const double gamma = gamma_w(P->weights, P->lambda, h);
     const double c = P->l_const / P->lambda;
     S.nx = g.nx;
     S.ny = g.ny;
@@ -455,7 +465,7 @@ int loop_mode() {
 }
 
 double default_tol(const hjb_problem *P, double h) {
-    return 0.5e-4 * (-std::expm1(-P->lambda * h));
+    return 0.5e-4 * (1.0 - beta_w(P->weights, P->lambda, h));
 }
 
 // Dubins per-layer foot offsets (v h cos(th)/dx, v h sin(th)/dy) in FP64.
@@ -874,6 +884,8 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
         return fail(HJB_ERR_INVALID_ARG, "non-finite scalar parameter");
     if (!(disc->h > 0) || !(disc->lambda > 0))
         return fail(HJB_ERR_INVALID_ARG, "h and lambda must be positive");
+    if (disc->weights != HJB_WEIGHTS_EXP && disc->weights != HJB_WEIGHTS_IMPLICIT)
+        return fail(HJB_ERR_INVALID_ARG, "unknown step weights %d", disc->weights);
     if (!target->labels) return fail(HJB_ERR_INVALID_ARG, "target labels are required");
     if (target->n_targets < 1 || target->n_targets > HJB_MAX_TARGETS)
         return fail(HJB_ERR_INVALID_ARG, "n_targets must be in [1, %d]", HJB_MAX_TARGETS);
@@ -899,6 +911,7 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
     P->l_const = cost->l ? 1.0 : cost->l_const;
     P->h = disc->h;
     P->lambda = disc->lambda;
+    P->weights = disc->weights;
     P->value_out = target->value_out;
     P->ntargets = target->n_targets;
     P->na = controls->count;
@@ -1474,8 +1487,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     ap.hy = static_cast<float>(P->h / P->dx[1]);
     ap.dx = static_cast<float>(P->dx[0]);
     ap.dy = static_cast<float>(P->dx[1]);
-    ap.beta = static_cast<float>(std::exp(-P->lambda * P->h));
-    ap.gamma = static_cast<float>(-std::expm1(-P->lambda * P->h) / P->lambda);
+    ap.beta = static_cast<float>(beta_w(P->weights, P->lambda, P->h));
+    ap.gamma = static_cast<float>(gamma_w(P->weights, P->lambda, P->h));
     ap.h = static_cast<float>(P->h);
     ap.vout = static_cast<float>(P->value_out);
     ap.speed = pr.speed;
@@ -1697,6 +1710,8 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     if (!(disc->h > 0) || !(disc->lambda > 0) || !std::isfinite(disc->h) ||
         !std::isfinite(disc->lambda))
         return fail(HJB_ERR_INVALID_ARG, "h and lambda must be positive");
+    if (disc->weights != HJB_WEIGHTS_EXP && disc->weights != HJB_WEIGHTS_IMPLICIT)
+        return fail(HJB_ERR_INVALID_ARG, "unknown step weights %d", disc->weights);
     if (!target->labels || target->n_targets < 1 || target->n_targets > HJB_MAX_TARGETS)
         return fail(HJB_ERR_INVALID_ARG, "bad target description");
     if (!cost->l && !(cost->l_const > 0))
@@ -1787,8 +1802,8 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     // the slot: the whole grid, W form when the running cost is constant
     const bool wform = cost->l == nullptr;
     const double lconst = cost->l ? 1.0 : cost->l_const;
-    const double beta = std::exp(-disc->lambda * disc->h);
-    const double gamma = -std::expm1(-disc->lambda * disc->h) / disc->lambda;
+    const double beta = beta_w(disc->weights, disc->lambda, disc->h);
+    const double gamma = gamma_w(disc->weights, disc->lambda, disc->h);
     const double c = lconst / disc->lambda;
     SlotDesc S;
     std::memset(&S, 0, sizeof S);

@@ -459,3 +459,25 @@ def test_pursuit_evasion_game(hjb, orc):
     Vb, per, tot = hjb.solve_decomposed(p, fine_o)
     assert tot["converged"] == 1
     assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V
+
+
+@pytest.mark.parametrize("which", ["c1", "vdp"])
+def test_implicit_step_weights(hjb, orc, which):
+    """The 1/(1 + lambda h) weights of the printed scheme (Sec. 3), W form
+    (constant cost) and V form (cost field), full and decomposed solves."""
+    d = S.c1(n=81) if which == "c1" else S.vdp(n=97, slices=4)
+    d = dict(d, weights=1)
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-11, nthreads=8)
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p)
+    assert st["converged"] == 1
+    assert np.abs(to_np(V) - Vo).max() < TOL_V
+    q = gpu_problem(hjb, dict(d, weights=0))
+    assert np.abs(to_np(hjb.solve(q)[0]) - Vo).max() > 10 * TOL_V
+    stride = (4, 4) if which == "c1" else d["stride"]
+    _, lab_o, _ = orc.ra(po, stride, 0.15, tol=1e-11)
+    fine = orc.project(po, stride, lab_o)
+    Vb_o, _, _, _ = orc.isa(po, fine, tol=1e-11, nthreads=8)
+    Vb, _, tot = hjb.solve_decomposed(p, fine)
+    assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V

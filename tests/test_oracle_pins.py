@@ -116,11 +116,16 @@ def _stencil(shape, spacing, periodic, idx, off):
     return out
 
 
-def _brute_force(shape, spacing, periodic, target, feet, cost, lam, h, v_out):
-    """feet[i][j] = physical offset h f(x_i, a_j).  Returns the optimal V."""
+def _brute_force(shape, spacing, periodic, target, feet, cost, lam, h, v_out, implicit=False):
+    """feet[i][j] = physical offset h f(x_i, a_j).  Returns the optimal V.
+    Step weights: e^{-lam h} and (1 - e^{-lam h}) / lam, or with implicit the
+    1 / (1 + lam h) and h / (1 + lam h) of the printed scheme."""
     N = int(np.prod(shape))
-    beta = math.exp(-lam * h)
-    gam = (1 - beta) / lam
+    if implicit:
+        beta, gam = 1.0 / (1.0 + lam * h), h / (1.0 + lam * h)
+    else:
+        beta = math.exp(-lam * h)
+        gam = (1 - beta) / lam
     free = [i for i in range(N) if target[i] == 0]
     pos = {i: k for k, i in enumerate(free)}
     F, A = len(free), len(feet[free[0]])
@@ -174,6 +179,30 @@ def test_brute_force_speed_current_cost(orc):
                     v_out=v_out)
     V, it, r = orc.solve(p, tol=1e-15, max_iters=100000)
     assert np.abs(V - Vb).max() < 1e-12
+
+
+def test_brute_force_implicit_weights(orc):
+    """The weights printed in the scheme of Sec. 3, 1/(1 + lambda h) and
+    h/(1 + lambda h), against the brute-force solve with the same weights."""
+    g = np.random.default_rng(5)
+    shape = (4, 3)
+    lo, hi = (0.0, 0.0), (3.0, 1.0)
+    N = 12
+    target = np.zeros(N, dtype=np.int32)
+    target[[0, 7, 10]] = [1, 2, 1]
+    ang = 0.4 + np.pi / 2 * np.arange(4)
+    ctr = np.stack([np.cos(ang), np.sin(ang)], 1)
+    s = g.uniform(0.5, 1.5, N)
+    cost = g.uniform(0.5, 2.0, N)
+    lam, h, v_out = 1.3, 0.6, 2.0
+    feet = [[h * s[i] * ctr[j] for j in range(4)] for i in range(N)]
+    Vb = _brute_force(shape, (1.0, 0.5), (0, 0), target, feet, cost, lam, h, v_out, implicit=True)
+    p = orc.Problem(shape, lo, hi, ctr, target, h=h, lam=lam, speed=s, cost=cost, v_out=v_out,
+                    weights=1)
+    V, _, _ = orc.solve(p, tol=1e-15, max_iters=100000)
+    assert np.abs(V - Vb).max() < 1e-12
+    q = orc.Problem(shape, lo, hi, ctr, target, h=h, lam=lam, speed=s, cost=cost, v_out=v_out)
+    assert np.abs(orc.solve(q, tol=1e-15, max_iters=100000)[0] - Vb).max() > 1e-3
 
 
 def test_brute_force_long_feet_constant_drift(orc):
