@@ -97,18 +97,28 @@ typedef struct {
     double l_const;
 } hjb_cost;
 
-/* Fictitious time step h and discount rate lambda > 0 (Sec. 3).
+/* Scheme parameters (Sec. 3): fictitious time step h, discount rate
+ * lambda > 0, step weights and interpolation.
  *  weights: HJB_WEIGHTS_EXP (0): beta = exp(-lambda h), gamma = (1 - beta) /
  *           lambda, the exact discount over one step;
  *           HJB_WEIGHTS_IMPLICIT (1): beta = 1 / (1 + lambda h), gamma =
  *           h / (1 + lambda h), the weights printed in the scheme of Sec. 3.
- *  Both give the value l / lambda for a constant cost l. */
+ *           Both give the value l / lambda for a constant cost l.
+ *  interp:  HJB_INTERP_Q1 (0): multilinear on the cell;
+ *           HJB_INTERP_P1 (1, 2D only): linear on the triangle of the cell's
+ *           split along its (0,0)-(1,1) diagonal that holds the foot (the
+ *           "linear n-dimensional interpolation" of Sec. 3).  P1 problems
+ *           run the generic-count kernel; hjb_backward and hjb_solve_static
+ *           take Q1 only. */
 #define HJB_WEIGHTS_EXP 0
 #define HJB_WEIGHTS_IMPLICIT 1
+#define HJB_INTERP_Q1 0
+#define HJB_INTERP_P1 1
 typedef struct {
     double h;
     double lambda;
     int weights;
+    int interp;
 } hjb_discount;
 
 /* Discrete control set A (Sec. 3: "a discrete version of the control

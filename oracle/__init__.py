@@ -48,7 +48,7 @@ class _Prob(C.Structure):
         ("ncontrols", C.c_int), ("cdim", C.c_int), ("controls", C.c_void_p),
         ("target", C.c_void_p), ("ntargets", C.c_int), ("v_out", C.c_double),
         ("scale", C.c_void_p), ("nb", C.c_int), ("controls_b", C.c_void_p),
-        ("weights", C.c_int),
+        ("weights", C.c_int), ("interp", C.c_int),
     ]
 
 
@@ -111,7 +111,7 @@ class Problem:
     def __init__(self, shape, lo, hi, controls, target, h, lam=1.0, periodic=None,
                  dyn=0, speed=None, current=None, dubins_v=1.0, cost=None,
                  cost_const=1.0, v_out=1.0, ntargets=None, scale=None, controls_b=None,
-                 weights=0):
+                 weights=0, interp=0):
         self.ndim = len(shape)
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
@@ -151,6 +151,7 @@ class Problem:
         s.nb = 0 if self.controls_b is None else self.controls_b.shape[0]
         s.controls_b = _ptr(self.controls_b)
         s.weights = int(weights)
+        s.interp = int(interp)
         self._s = s
         self.h, self.lam, self.v_out = float(h), float(lam), float(v_out)
         self.lo, self.hi, self.periodic = list(lo), list(hi), per[: self.ndim]

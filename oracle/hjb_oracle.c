@@ -24,6 +24,10 @@
  *       fine node belongs to sub-domain k iff every vertex carrying a
  *       non-zero barycentric weight is labelled k.
  *   R10 ties in the control minimum go to the lowest control index.
+ *   P1 (Sec. 3, "linear n-dimensional interpolation"; 2D, interp = 1): the
+ *       linear interpolant on the triangle of the Kuhn split of the cell that
+ *       holds the point; Q1 (multilinear) otherwise.  The adjoint functions
+ *       assume Q1.
  *   Games (Sec. 2 "max_b min_a", Example ex4): with a second control set B
  *       the operator is beta * max_b min_a I[V](x_i + h f(x_i, a, b)) +
  *       gamma * l_i, f = D(x)(a - b) + c(x); D(x) = diag(scale) per node, or
@@ -67,6 +71,7 @@ typedef struct {
     int nb;                /* size of the second player's set B (0: none) */
     const double *controls_b; /* [nb][cdim] */
     int weights;           /* 0: beta = exp(-lambda h); 1: beta = 1/(1 + lambda h) */
+    int interp;            /* 0: Q1 multilinear; 1: P1 on the Kuhn triangles (2D) */
 } ohjb_problem;
 
 static long long node_count(const ohjb_problem *p) {
@@ -121,6 +126,29 @@ static double q1_at(const ohjb_problem *p, const double *V, const double *g,
             c0[d] = c;
             c1[d] = c + 1;
         }
+    }
+    if (p->interp == 1 && p->ndim == 2) {
+        /* P1: the linear interpolant on the triangle of the Kuhn split of
+         * the cell (diagonal from corner (0,0) to (1,1)) holding the point */
+        double v00 = V[flatten(p, (int[3]){c0[0], c0[1], 0})];
+        double v10 = V[flatten(p, (int[3]){c1[0], c0[1], 0})];
+        double v01 = V[flatten(p, (int[3]){c0[0], c1[1], 0})];
+        double v11 = V[flatten(p, (int[3]){c1[0], c1[1], 0})];
+        double val;
+        if (t[0] >= t[1]) {
+            val = (1.0 - t[0]) * v00 + (t[0] - t[1]) * v10 + t[1] * v11;
+            if (grad) {
+                grad[0] = v10 - v00;
+                grad[1] = v11 - v10;
+            }
+        } else {
+            val = (1.0 - t[1]) * v00 + (t[1] - t[0]) * v01 + t[0] * v11;
+            if (grad) {
+                grad[0] = v11 - v01;
+                grad[1] = v01 - v00;
+            }
+        }
+        return val;
     }
     double acc = 0.0;
     double gacc[3] = {0, 0, 0};

@@ -26,6 +26,7 @@ import numpy as np
 
 from . import _capi
 from ._capi import (HJB_DYN_DUBINS, HJB_DYN_SPEED_CURRENT, HJB_WEIGHTS_EXP, HJB_WEIGHTS_IMPLICIT,
+                    HJB_INTERP_Q1, HJB_INTERP_P1,
                     HJBError, NotConverged, check,
                     hjb_ra_opts, hjb_solve_opts, hjb_stats)
 
@@ -103,7 +104,8 @@ class Problem:
     per node (0 free, k target component k); speed / log_speed / scale
     (per-axis factors [N, 2]) / current / cost: optional node fields; h, lam:
     time step and discount rate; weights: 0 = exp(-lam h) step weights, 1 = the
-    1 / (1 + lam h) weights of the printed scheme; controls_b: the second
+    1 / (1 + lam h) weights of the printed scheme; interp: 0 = Q1, 1 = P1 on
+    the Kuhn triangles of each cell (2D); controls_b: the second
     player's set of a differential game ([B, 2], f = D (a - b) + c).
     Node arrays are in (z,) y, x order with x fastest.
     """
@@ -111,7 +113,7 @@ class Problem:
     def __init__(self, shape, lo, hi, controls, labels, h, lam=1.0, n_targets=None,
                  dyn=HJB_DYN_SPEED_CURRENT, speed=None, current=None, log_speed=None,
                  dubins_v=1.0, cost=None, cost_const=1.0, value_out=1.0, periodic=None,
-                 scale=None, controls_b=None, weights=0):
+                 scale=None, controls_b=None, weights=0, interp=0):
         L = _capi.lib()
         nd = len(shape)
         self.shape = tuple(int(s) for s in shape)
@@ -156,6 +158,7 @@ class Problem:
         di.h = float(h)
         di.lam = float(lam)
         di.weights = int(weights)
+        di.interp = int(interp)
         ct = _capi.hjb_controls()
         ct.count = self.controls.shape[0]
         ct.dim = self.controls.shape[1]

@@ -27,6 +27,8 @@ HJB_DYN_SPEED_CURRENT = 0
 HJB_DYN_DUBINS = 1
 HJB_WEIGHTS_EXP = 0
 HJB_WEIGHTS_IMPLICIT = 1
+HJB_INTERP_Q1 = 0
+HJB_INTERP_P1 = 1
 
 EXPORTS = ["hjb_create", "hjb_destroy", "hjb_solve", "hjb_subdomains", "hjb_solve_decomposed",
            "hjb_solve_batch", "hjb_backward", "hjb_point_values", "hjb_solve_static",
@@ -58,7 +60,7 @@ class hjb_cost(C.Structure):
 
 
 class hjb_discount(C.Structure):
-    _fields_ = [("h", C.c_double), ("lam", C.c_double), ("weights", C.c_int)]
+    _fields_ = [("h", C.c_double), ("lam", C.c_double), ("weights", C.c_int), ("interp", C.c_int)]
 
 
 class hjb_controls(C.Structure):

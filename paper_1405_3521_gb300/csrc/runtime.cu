@@ -199,6 +199,7 @@ struct hjb_problem {
     Field speed, current, log_speed, cost, labels, scale;
     double l_const, h, lambda, value_out;
     int weights = HJB_WEIGHTS_EXP;
+    int interp = HJB_INTERP_Q1;
     int na, cdim;
     float ax[hjbk::MAX_CTRL], ay[hjbk::MAX_CTRL];
     int nb = 0;  // second player's set B (games), 0: none
@@ -507,7 +508,14 @@ hjbk::ControlTable control_table(const hjb_problem *P) {
 // Kernel family for a problem: compile-time control counts (32, 64) only
 // without a second player; a game runs the generic kernel with one control
 // group (all pairs of a node in one thread) and 8-row tiles.
-int key_na(const hjb_problem *P) { return P->nb ? 0 : P->na; }
+int key_na(const hjb_problem *P) {
+    if (P->interp == HJB_INTERP_P1) return -1;  // generic count, P1 interpolation
+    return P->nb ? 0 : P->na;
+}
+// Problems that run one control group in 8-row tiles (no tile-shape tuning).
+bool fixed_shape(const hjb_problem *P) {
+    return P->kind == HJB_DYN_DUBINS || P->nb || P->interp == HJB_INTERP_P1;
+}
 
 // Allocate iteration buffers for the slots (laid out back to back, each
 // 256-byte aligned) and encode their TMA maps.
@@ -886,6 +894,10 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
         return fail(HJB_ERR_INVALID_ARG, "h and lambda must be positive");
     if (disc->weights != HJB_WEIGHTS_EXP && disc->weights != HJB_WEIGHTS_IMPLICIT)
         return fail(HJB_ERR_INVALID_ARG, "unknown step weights %d", disc->weights);
+    if (disc->interp != HJB_INTERP_Q1 && disc->interp != HJB_INTERP_P1)
+        return fail(HJB_ERR_INVALID_ARG, "unknown interpolation %d", disc->interp);
+    if (disc->interp == HJB_INTERP_P1 && dyn->kind != HJB_DYN_SPEED_CURRENT)
+        return fail(HJB_ERR_UNSUPPORTED, "P1 interpolation is implemented for 2D problems");
     if (!target->labels) return fail(HJB_ERR_INVALID_ARG, "target labels are required");
     if (target->n_targets < 1 || target->n_targets > HJB_MAX_TARGETS)
         return fail(HJB_ERR_INVALID_ARG, "n_targets must be in [1, %d]", HJB_MAX_TARGETS);
@@ -912,6 +924,7 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
     P->h = disc->h;
     P->lambda = disc->lambda;
     P->weights = disc->weights;
+    P->interp = disc->interp;
     P->value_out = target->value_out;
     P->ntargets = target->n_targets;
     P->na = controls->count;
@@ -1042,7 +1055,7 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
     if (!P || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL problem or output");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (P->kind == HJB_DYN_DUBINS || P->nb) return solve_full(P, opts, hjbk::TY, v_out, stats, st);
+    if (fixed_shape(P)) return solve_full(P, opts, hjbk::TY, v_out, stats, st);
     const std::vector<long long> key = {0, P->kind, P->grid.n[0], P->grid.n[1], P->na,
                                         P->cost.user ? 1 : 0};
     return tuned_call(key, [&](int rows, double *ms) {
@@ -1116,7 +1129,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     std::memset(R.slots.data(), 0, m * sizeof(SlotDesc));
     if (P->kind == HJB_DYN_DUBINS)
         TRY(dubins_trig(P, P->c_trig, g.nz, hK, dxK, P->grid.lo[2], dxK[2], st));
-    const int rows = (P->kind == HJB_DYN_DUBINS || P->nb) ? hjbk::TY : 2;
+    const int rows = fixed_shape(P) ? hjbk::TY : 2;
     for (int k = 0; k < m; ++k) {
         fill_slot(R.slots[k], P, g, cp, wform, hK, dxK, halo, tol, max_iters, rows);
         R.slots[k].only_target = k + 1;  // RA step 1: dG := X_k
@@ -1328,7 +1341,7 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     if (!P || !fine_mask || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (P->kind == HJB_DYN_DUBINS || P->nb)
+    if (fixed_shape(P))
         return solve_dec(P, fine_mask, opts, hjbk::TY, v_out, per_subdomain, total, st);
     const std::vector<long long> key = {1, P->kind, P->grid.n[0], P->grid.n[1], P->na,
                                         P->cost.user ? 1 : 0, P->ntargets};
@@ -1360,7 +1373,8 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
             (P->cost.user == nullptr) != (P0->cost.user == nullptr) ||
             std::memcmp(P->ax, P0->ax, P->na * sizeof(float)) ||
             std::memcmp(P->ay, P0->ay, P->na * sizeof(float)) || P->l_const != P0->l_const ||
-            P->nb != P0->nb || std::memcmp(P->bx, P0->bx, P->nb * sizeof(float)) ||
+            P->nb != P0->nb || P->interp != P0->interp ||
+            std::memcmp(P->bx, P0->bx, P->nb * sizeof(float)) ||
             std::memcmp(P->by, P0->by, P->nb * sizeof(float)) ||
             P->lambda != P0->lambda)
             return fail(HJB_ERR_INVALID_ARG,
@@ -1441,7 +1455,7 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
     TRY(check_opts(opts));
     if (!problems[0]) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (problems[0]->kind == HJB_DYN_DUBINS || problems[0]->nb)
+    if (fixed_shape(problems[0]))
         return solve_batch_impl(problems, count, opts, hjbk::TY, v_out, per_problem, st);
     long long nodes = 0;
     for (int i = 0; i < count; ++i) nodes += problems[i] ? problems[i]->N : 0;
@@ -1462,8 +1476,9 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     if (wrt != 0 && wrt != 1) return fail(HJB_ERR_INVALID_ARG, "wrt must be 0 (log-speed) or 1 (cost)");
     if (P->kind != HJB_DYN_SPEED_CURRENT)
         return fail(HJB_ERR_UNSUPPORTED, "the adjoint is implemented for 2D speed/current dynamics");
-    if (P->nb || P->scale.user)
-        return fail(HJB_ERR_UNSUPPORTED, "the adjoint does not handle games or per-axis scale fields");
+    if (P->nb || P->scale.user || P->interp != HJB_INTERP_Q1)
+        return fail(HJB_ERR_UNSUPPORTED,
+                    "the adjoint handles Q1 interpolation without games or per-axis scale fields");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Prep pr;
@@ -1712,6 +1727,8 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
         return fail(HJB_ERR_INVALID_ARG, "h and lambda must be positive");
     if (disc->weights != HJB_WEIGHTS_EXP && disc->weights != HJB_WEIGHTS_IMPLICIT)
         return fail(HJB_ERR_INVALID_ARG, "unknown step weights %d", disc->weights);
+    if (disc->interp != HJB_INTERP_Q1)
+        return fail(HJB_ERR_UNSUPPORTED, "the static solve uses Q1 interpolation");
     if (!target->labels || target->n_targets < 1 || target->n_targets > HJB_MAX_TARGETS)
         return fail(HJB_ERR_INVALID_ARG, "bad target description");
     if (!cost->l && !(cost->l_const > 0))

@@ -157,6 +157,34 @@ __device__ __forceinline__ float q1_pairs(float2 P2, uint32_t K) {
     return fmaf(F2.x, b, E2.x * a);
 }
 
+// P1 variant ("linear n-dimensional interpolation" on the Kuhn triangles of
+// each cell, split along the (0,0)-(1,1) diagonal): the same loads, the
+// barycentric weights (1 - t1, t1 - t2, t2) with t1 = max(fx, fy), t2 =
+// min(fx, fy) on the corners (0,0), (1,0) or (0,1), (1,1).  Non-negative
+// weights in fused multiply-adds keep the value monotone in the data.
+__device__ __forceinline__ float p1_pairs(float2 P2, uint32_t K) {
+    const float2 M2 = __fadd2_rn(P2, make_float2(MAGIC, MAGIC));
+    const float2 Kn = __ffma2_rn(M2, make_float2(-1.0f, -1.0f), make_float2(TWO23, TWO23));
+    const float2 F2 = __fadd2_rn(P2, Kn);
+    const uint32_t addr = (__float_as_uint(M2.y) << 9) + (__float_as_uint(M2.x) << 3) + K;
+    float lo0, lo1, hi0, hi1;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(lo0), "=f"(lo1) : "r"(addr));
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+512];" : "=f"(hi0), "=f"(hi1) : "r"(addr));
+    const bool lower = F2.x >= F2.y;  // the triangle (0,0), (1,0), (1,1)
+    const float t1 = lower ? F2.x : F2.y, t2 = lower ? F2.y : F2.x;
+    const float mid = lower ? lo1 : hi0;
+    return fmaf(t2, hi1, fmaf(t1 - t2, mid, (1.0f - t1) * lo0));
+}
+
+// Interpolation of a kernel family: NA < 0 selects P1, otherwise Q1.
+template <int NA>
+__device__ __forceinline__ float interp_pairs(float2 P2, uint32_t K) {
+    if constexpr (NA < 0)
+        return p1_pairs(P2, K);
+    else
+        return q1_pairs(P2, K);
+}
+
 template <bool WFORM>
 __device__ __forceinline__ float pick(float best, float q) {
     return WFORM ? fmaxf(best, q) : fminf(best, q);
@@ -182,14 +210,14 @@ struct EdgeBounds {
     float lox, hix, loy, hiy;
 };
 
-template <bool WFORM>
+template <bool WFORM, int NA = 0>
 __device__ __forceinline__ float one_control_edge(uint32_t K, float2 O2, const EdgeBounds &eb,
                                                   float2 BASE2, float vout, float best) {
     const bool out = (O2.x < eb.lox - 1e-6f) | (O2.x > eb.hix + 1e-6f) | (O2.y < eb.loy - 1e-6f) |
                      (O2.y > eb.hiy + 1e-6f);
     O2.x = fminf(fmaxf(O2.x, eb.lox), eb.hix);
     O2.y = fminf(fmaxf(O2.y, eb.loy), eb.hiy);
-    const float q = q1_pairs(__fadd2_rn(O2, BASE2), K);
+    const float q = interp_pairs<NA>(__fadd2_rn(O2, BASE2), K);
     return pick<WFORM>(best, out ? vout : q);
 }
 
@@ -231,14 +259,14 @@ __device__ __forceinline__ float controls_interior(int g, const ControlTable &C,
                 float inner = WFORM ? -INFINITY : INFINITY;
 #pragma unroll 4
                 for (int j = k; j < k + nA; ++j)
-                    inner = pick<WFORM>(inner, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
+                    inner = pick<WFORM>(inner, interp_pairs<NA>(__ffma2_rn(S2, C.a2[j], B2), K));
                 outer = WFORM ? fminf(outer, inner) : fmaxf(outer, inner);
             }
             return pick<WFORM>(best, outer);
         }
 #pragma unroll 4
         for (int j = g; j < na; j += G)
-            best = pick<WFORM>(best, q1_pairs(__ffma2_rn(S2, C.a2[j], B2), K));
+            best = pick<WFORM>(best, interp_pairs<NA>(__ffma2_rn(S2, C.a2[j], B2), K));
         return best;
     }
 }
@@ -266,15 +294,16 @@ __device__ __forceinline__ float controls_edge(int g, const ControlTable &C, uin
                 float inner = WFORM ? -INFINITY : INFINITY;
 #pragma unroll 4
                 for (int j = k; j < k + nA; ++j)
-                    inner = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2,
-                                                    vout, inner);
+                    inner = one_control_edge<WFORM, NA>(K, __ffma2_rn(S2, C.a2[j], O02), eb,
+                                                        BASE2, vout, inner);
                 outer = WFORM ? fminf(outer, inner) : fmaxf(outer, inner);
             }
             return pick<WFORM>(best, outer);
         }
 #pragma unroll 4
         for (int j = g; j < na; j += G)
-            best = one_control_edge<WFORM>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2, vout, best);
+            best = one_control_edge<WFORM, NA>(K, __ffma2_rn(S2, C.a2[j], O02), eb, BASE2, vout,
+                                               best);
         return best;
     }
 }
@@ -1137,6 +1166,10 @@ const void *sweep_kernel(const SweepKey &k, size_t *smem) {
         case 32:
             HJB_PICK_SHAPES(32, 2)
             HJB_PICK_SHAPES(32, 4)
+            break;
+        case -1:  // generic count, P1 interpolation: one control group, 8-row tiles
+            HJB_PICK(-1, 2, 8, 1)
+            HJB_PICK(-1, 4, 8, 1)
             break;
         default:
             HJB_PICK_SHAPES(0, 2)

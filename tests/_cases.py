@@ -8,7 +8,8 @@ def oracle_problem(orc, d, **over):
               h=d["h"], lam=d.get("lam", 1.0), v_out=d.get("v_out", 1.0),
               ntargets=d["ntargets"], periodic=d.get("periodic"), dyn=d.get("dyn", 0),
               dubins_v=d.get("dubins_v", 1.0), scale=d.get("scale"),
-              controls_b=d.get("controls_b"), weights=d.get("weights", 0))
+              controls_b=d.get("controls_b"), weights=d.get("weights", 0),
+              interp=d.get("interp", 0))
     if d.get("log_speed") is not None:
         kw["speed"] = np.exp(np.asarray(d["log_speed"], dtype=np.float32).astype(np.float64))
     kw.update(over)
@@ -32,7 +33,7 @@ def gpu_problem(hjb, d, device="cuda", host=False, **over):
               value_out=d.get("v_out", 1.0), n_targets=d["ntargets"],
               periodic=d.get("periodic"), dyn=d.get("dyn", 0), dubins_v=d.get("dubins_v", 1.0),
               scale=t(d.get("scale")), controls_b=d.get("controls_b"),
-              weights=d.get("weights", 0))
+              weights=d.get("weights", 0), interp=d.get("interp", 0))
     kw.update(over)
     return hjb.Problem(d["shape"], d["lo"], d["hi"], np.asarray(d["controls"], np.float32),
                        t(d["labels"], torch.uint8), **kw)

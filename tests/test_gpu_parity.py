@@ -481,3 +481,27 @@ def test_implicit_step_weights(hjb, orc, which):
     Vb_o, _, _, _ = orc.isa(po, fine, tol=1e-11, nthreads=8)
     Vb, _, tot = hjb.solve_decomposed(p, fine)
     assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_p1_interpolation(hjb, orc, which):
+    """P1 interpolation on the Kuhn triangles (Sec. 3): W form (c1) and a
+    speed/current problem (c2, 61 controls: the generic-count kernel), full
+    and decomposed solves against the oracle; P1 and Q1 results differ."""
+    d = S.c1(n=81) if which == "c1" else S.c2(n=129, A=61, ntargets=5, stride=8)
+    d = dict(d, interp=1)
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-11, nthreads=8)
+    p = gpu_problem(hjb, d)
+    V, st = hjb.solve(p)
+    assert st["converged"] == 1
+    assert np.abs(to_np(V) - Vo).max() < TOL_V
+    q = gpu_problem(hjb, dict(d, interp=0))
+    assert np.abs(to_np(hjb.solve(q)[0]) - Vo).max() > 10 * TOL_V
+    stride = (4, 4) if which == "c1" else d["stride"]
+    _, lab_o, _ = orc.ra(po, stride, 0.15, tol=1e-11)
+    fine = orc.project(po, stride, lab_o)
+    Vb_o, _, _, _ = orc.isa(po, fine, tol=1e-11, nthreads=8)
+    Vb, _, tot = hjb.solve_decomposed(p, fine)
+    assert tot["converged"] == 1
+    assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V

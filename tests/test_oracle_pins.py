@@ -86,9 +86,11 @@ def _grid_index(shape, idx):
     return out
 
 
-def _stencil(shape, spacing, periodic, idx, off):
+def _stencil(shape, spacing, periodic, idx, off, p1=False):
     """Independent restatement of the foot rule: returns None when the foot
-    is outside the closed box (beyond 1e-6 cells), else [(flat, weight)]."""
+    is outside the closed box (beyond 1e-6 cells), else [(flat, weight)].
+    p1 (2D): the barycentric weights of the triangle of the cell's split
+    along its (0,0)-(1,1) diagonal that holds the foot."""
     nd = len(shape)
     cells = []
     for d in range(nd):
@@ -105,6 +107,13 @@ def _stencil(shape, spacing, periodic, idx, off):
             gd = min(max(gd, 0.0), n - 1.0)
             c = min(max(int(math.floor(gd)), 0), n - 2)
             cells.append((c, c + 1, gd - c))
+    if p1:
+        (x0, x1, tx), (y0, y1, ty) = cells
+        if tx >= ty:
+            corners = [((x0, y0), 1 - tx), ((x1, y0), tx - ty), ((x1, y1), ty)]
+        else:
+            corners = [((x0, y0), 1 - ty), ((x0, y1), ty - tx), ((x1, y1), tx)]
+        return [(_grid_index(shape, list(c)), w) for c, w in corners]
     out = []
     for bits in itertools.product((0, 1), repeat=nd):
         w, ii = 1.0, []
@@ -116,7 +125,8 @@ def _stencil(shape, spacing, periodic, idx, off):
     return out
 
 
-def _brute_force(shape, spacing, periodic, target, feet, cost, lam, h, v_out, implicit=False):
+def _brute_force(shape, spacing, periodic, target, feet, cost, lam, h, v_out, implicit=False,
+                 p1=False):
     """feet[i][j] = physical offset h f(x_i, a_j).  Returns the optimal V.
     Step weights: e^{-lam h} and (1 - e^{-lam h}) / lam, or with implicit the
     1 / (1 + lam h) and h / (1 + lam h) of the printed scheme."""
@@ -138,7 +148,7 @@ def _brute_force(shape, spacing, periodic, target, feet, cost, lam, h, v_out, im
             idx.append(r % shape[d])
             r //= shape[d]
         for j in range(A):
-            st = _stencil(shape, spacing, periodic, idx, feet[i][j])
+            st = _stencil(shape, spacing, periodic, idx, feet[i][j], p1=p1)
             b[k, j] = gam * cost[i]
             if st is None:
                 b[k, j] += beta * v_out
@@ -203,6 +213,52 @@ def test_brute_force_implicit_weights(orc):
     assert np.abs(V - Vb).max() < 1e-12
     q = orc.Problem(shape, lo, hi, ctr, target, h=h, lam=lam, speed=s, cost=cost, v_out=v_out)
     assert np.abs(orc.solve(q, tol=1e-15, max_iters=100000)[0] - Vb).max() > 1e-3
+
+
+def test_p1_interpolation_closed_forms(orc):
+    """P1 on the Kuhn triangles (Sec. 3, "linear n-dimensional
+    interpolation"): exact on affine data; on the corner data (0, 0, 0, 1) of
+    one cell (the function xy) it is min(t_x, t_y), where Q1 gives t_x t_y."""
+    g = np.random.default_rng(21)
+    lab = np.zeros((3, 4), np.uint8)
+    lab[0, 0] = 1
+    ctr = np.array([[1.0, 0.0]])
+    p = orc.Problem((4, 3), (0.0, 0.0), (3.0, 2.0), ctr, lab, 0.5, interp=1)
+    q = orc.Problem((4, 3), (0.0, 0.0), (3.0, 2.0), ctr, lab, 0.5)
+    X, Y = np.meshgrid(np.arange(4.0), np.arange(3.0))
+    a, b, c = g.normal(size=3)
+    V = (a + b * X + c * Y).reshape(-1)
+    for y in g.uniform([0, 0], [3, 2], size=(50, 2)):
+        assert abs(orc.interp(p, V, y) - (a + b * y[0] + c * y[1])) < 1e-12
+    e = np.zeros(12)
+    e[1 * 4 + 2] = 1.0  # node (2, 1): the (1,1) corner of cell (1, 0)
+    for t in g.uniform(0, 1, size=(50, 2)):
+        y = np.array([1.0 + t[0], 0.0 + t[1]])
+        assert abs(orc.interp(p, e, y) - min(t[0], t[1])) < 1e-12
+        assert abs(orc.interp(q, e, y) - t[0] * t[1]) < 1e-12
+
+
+def test_brute_force_p1(orc):
+    g = np.random.default_rng(9)
+    shape = (4, 3)
+    lo, hi = (0.0, 0.0), (3.0, 1.0)
+    N = 12
+    target = np.zeros(N, dtype=np.int32)
+    target[[0, 7, 9]] = [1, 2, 1]
+    ang = 0.3 + np.pi / 2 * np.arange(4)
+    ctr = np.stack([np.cos(ang), np.sin(ang)], 1)
+    s = g.uniform(0.5, 1.5, N)
+    cur = g.uniform(-0.2, 0.2, (N, 2))
+    cost = g.uniform(0.5, 2.0, N)
+    lam, h, v_out = 0.7, 0.8, 3.0
+    feet = [[h * (s[i] * ctr[j] + cur[i]) for j in range(4)] for i in range(N)]
+    Vb = _brute_force(shape, (1.0, 0.5), (0, 0), target, feet, cost, lam, h, v_out, p1=True)
+    p = orc.Problem(shape, lo, hi, ctr, target, h=h, lam=lam, speed=s, current=cur, cost=cost,
+                    v_out=v_out, interp=1)
+    V, _, _ = orc.solve(p, tol=1e-15, max_iters=100000)
+    assert np.abs(V - Vb).max() < 1e-12
+    Vq = _brute_force(shape, (1.0, 0.5), (0, 0), target, feet, cost, lam, h, v_out)
+    assert np.abs(Vq - Vb).max() > 1e-4
 
 
 def test_brute_force_long_feet_constant_drift(orc):
