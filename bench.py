@@ -54,7 +54,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="zermelo", choices=["zermelo", "dubins", "batch", "adjoint", "vdp", "game"],
                     help="zermelo: the 1025^2 Zermelo problem (default, the headline line); "
-                         "dubins, batch, adjoint: the other hot-path rows, each printing its own line")
+                         "dubins, batch, adjoint, vdp, game: the other rows, each printing its own line")
+    ap.add_argument("--small", action="store_true",
+                    help="dubins / adjoint: a reduced size (126x126x64 / 257^2) for detailed "
+                         "profiler captures; not a benchmark configuration")
     ap.add_argument("--profile", choices=["full", "decomposed", "ra"], default=None,
                     help="run one solve of that path (after one warm-up) for a profiler; "
                          "prints per-solve statistics instead of the JSON line")
@@ -277,7 +280,7 @@ def run_dubins(args, hjb, S, dev, flush, local):
     """3D Dubins car, 256 x 256 x 128, reconstruction (stride 5, 5, 8) and the
     decomposed solve against the full-domain solve."""
     import numpy as np
-    d = S.c3()
+    d = S.c3(nxy=126, nth=64, stride=(5, 5, 8)) if args.small else S.c3()
     nfree = int((d["labels"] == 0).sum())
     p = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8), d["h"],
                     dyn=hjb.HJB_DYN_DUBINS, periodic=(0, 0, 1), n_targets=d["ntargets"])
@@ -312,7 +315,7 @@ def run_dubins(args, hjb, S, dev, flush, local):
                          % (sw, el)}
     _line(args, "node-updates/s to convergence, decomposed vs full-domain GPU (3D Dubins)",
           nfree * iters_full / (ms / 1e3), UNIT, ms,
-          {"workload": "dubins-256x256x128-u3-8targets", "coarse_stride": list(d["stride"])},
+          {"workload": "dubins-%dx%dx%d-u3-8targets" % tuple(d["shape"]), "coarse_stride": list(d["stride"])},
           full_domain={"sweeps": fst["iterations"], "jacobi_sweeps": iters_full, "ms": ms_full,
                        "node_updates_per_s": nfree * iters_full / (ms_full / 1e3)},
           decomposed={"ms_ra": rst["ms"], "ms_fine": tot["ms"], "max_subdomain_iters": tot["iterations"],
@@ -462,7 +465,7 @@ def run_adjoint(args, hjb, S, dev, flush, local):
     """Gradient of the mean of V at 4096 points w.r.t. a 1025^2 log-speed field."""
     import numpy as np
     import torch
-    d = S.c5()
+    d = S.c5(n=257) if args.small else S.c5()
     theta = dev(d["log_speed"])
     p = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8), d["h"],
                     log_speed=theta, n_targets=d["ntargets"])
@@ -478,7 +481,7 @@ def run_adjoint(args, hjb, S, dev, flush, local):
     # atomics 16 B, residual pass (two lambda reads, g read, lambda write) 16 B
     ach = upd * 41 / (st["ms"] / 1e3) / 1e9
     _line(args, "adjoint node-updates/s to convergence (transposed fixed point, policy frozen)",
-          upd / (ms / 1e3), UNIT, ms, {"workload": "adjoint-1025x1025-A32-4096points"},
+          upd / (ms / 1e3), UNIT, ms, {"workload": "adjoint-%dx%d-A32-4096points" % tuple(d["shape"])},
           iterations=st["iterations"], forward_iterations=fst["iterations"],
           roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                     "frac": ach / hbm, "traffic": None, "kernel": "adj_scatter + adj_resid",

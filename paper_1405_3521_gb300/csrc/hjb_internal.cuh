@@ -51,6 +51,7 @@ struct alignas(128) SlotDesc {
     const uint8_t *labels;      // target labels [N]
     const uint32_t *mask;       // sub-domain bitmask [N] (or null)
     const uint32_t *tile_bits;  // per-tile OR of the sub-domain bits (masked slots), or null
+    const uint32_t *tile_full;  // per-tile AND of the sub-domain bits (tiles inside a sub-domain)
     const float2 *trig;         // Dubins: per heading layer (v h cos/dx, v h sin/dy)
     long long zstride;          // floats between layers of V
     int nx, ny, nz, pitch;
@@ -183,12 +184,13 @@ void launch_grad_max(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, 
 // ISA step 2: fine bitmask from coarse labels through the Kuhn simplices.
 void launch_project(const GridDims &fine, const GridDims &coarse, const int stride[3],
                     const uint32_t *coarse_labels, uint32_t *fine_mask, cudaStream_t st);
-// Per-tile OR of the sub-domain bits of the decomposed solve.  diff
+// Per-tile OR (and, optionally, AND: tile_full) of the sub-domain bits of
+// the decomposed solve.  diff
 // (optional, [32], zeroed by the caller): bit j of diff[k] is OR-ed in where
 // the node sets of sub-domains k and j differ (m sub-domains, m <= 32).
 void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty,
                       const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st,
-                      uint32_t *diff = nullptr, int m = 0);
+                      uint32_t *diff = nullptr, int m = 0, uint32_t *tile_full = nullptr);
 // ISA step 4: Vbar = min over the sub-domains containing each node.  Slots
 // in ctl->twin_mask (ctl optional) are skipped: their twin holds the same V.
 void launch_assemble(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int m,

@@ -415,6 +415,7 @@ void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &
     S.tiles_z = P->grid.ndim > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
     S.ntiles = S.tiles_x * S.tiles_y * S.tiles_z;
     S.tile_bits = nullptr;
+    S.tile_full = nullptr;
     S.qbase = 0;
     S.halo = halo;
     S.hx = static_cast<float>(h / dx[0]);
@@ -1260,14 +1261,17 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     const int tiles_y = (g.ny + rows - 1) / rows;
     const int tiles_z = nd > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
     const int nt = tiles_x * tiles_y * tiles_z;
-    // tile bits, then 32 words of pairwise membership differences
-    TRY(P->tile_bits.ensure((nt + 32) * sizeof(uint32_t)));
-    uint32_t *diff = P->tile_bits.as<uint32_t>() + nt;
+    // per-tile OR and AND of the sub-domain bits, then 32 words of pairwise
+    // membership differences
+    TRY(P->tile_bits.ensure((2 * nt + 32) * sizeof(uint32_t)));
+    uint32_t *tile_full = P->tile_bits.as<uint32_t>() + nt;
+    uint32_t *diff = P->tile_bits.as<uint32_t>() + 2 * nt;
     for (int k = 0; k < m; ++k) {
         fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows);
         R.slots[k].mask = mask;
         R.slots[k].mask_bit = k;
         R.slots[k].tile_bits = P->tile_bits.as<uint32_t>();
+        R.slots[k].tile_full = tile_full;
         if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->trig.as<float2>();
     }
     TRY(alloc_slot_buffers(R, nd, halo, rows));
@@ -1278,7 +1282,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     CK(cudaEventRecord(R.ev0, st));
     CK(cudaMemsetAsync(diff, 0, 32 * sizeof(uint32_t), st));
     hjbh::launch_tile_bits(fine, tiles_x, tiles_y, tiles_z, rows, mask,
-                           P->tile_bits.as<uint32_t>(), st, diff, m);
+                           P->tile_bits.as<uint32_t>(), st, diff, m, tile_full);
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,

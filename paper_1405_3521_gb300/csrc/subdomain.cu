@@ -210,14 +210,14 @@ __global__ void project_kernel(hjbh::GridDims fine, hjbh::GridDims coarse, int r
 // tiles are 32 x ty (x TZ in 3D) nodes).
 __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int ty_rows,
                                  const uint32_t *mask, uint32_t *tile_bits, uint32_t *diff,
-                                 int m) {
+                                 int m, uint32_t *tile_full) {
     const int t = blockIdx.x;
     const int txy = tiles_x * tiles_y;
     const int tz = t / txy, rem = t - tz * txy;
     const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
     const int x = tx * TX + (threadIdx.x & 31);
     const uint32_t mbits = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
-    uint32_t bits = 0u;
+    uint32_t bits = 0u, all = 0xffffffffu;
     // dk[k]: sub-domains whose membership differs from k's at a node seen here
     uint32_t dk[32];
 #pragma unroll
@@ -229,6 +229,7 @@ __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int
         if (x < g.n[0] && y < g.n[1] && (g.ndim < 3 || z < g.n[2])) {
             const uint32_t v = mask[flat(g, x, y, z)];
             bits |= v;
+            all &= v;
             if (diff) {
                 const uint32_t b = v & mbits;
 #pragma unroll
@@ -237,9 +238,13 @@ __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int
         }
     }
     bits = __reduce_or_sync(0xffffffffu, bits);
-    __shared__ uint32_t s[THREADS / 32];
+    all = __reduce_and_sync(0xffffffffu, all);
+    __shared__ uint32_t s[THREADS / 32], s_all[THREADS / 32];
     __shared__ uint32_t s_d[THREADS / 32][32];
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = bits;
+    if ((threadIdx.x & 31) == 0) {
+        s[threadIdx.x >> 5] = bits;
+        s_all[threadIdx.x >> 5] = all;
+    }
     if (diff) {
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
@@ -249,9 +254,13 @@ __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t b = 0u;
-        for (int w = 0; w < THREADS / 32; ++w) b |= s[w];
+        uint32_t b = 0u, a = 0xffffffffu;
+        for (int w = 0; w < THREADS / 32; ++w) {
+            b |= s[w];
+            a &= s_all[w];
+        }
         tile_bits[t] = b;
+        if (tile_full) tile_full[t] = a;  // every node of the tile in these sub-domains
     }
     if (diff && threadIdx.x < 32) {
         uint32_t w = 0u;
@@ -363,9 +372,10 @@ void launch_project(const GridDims &fine, const GridDims &coarse, const int stri
 
 void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty,
                       const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st, uint32_t *diff,
-                      int m) {
+                      int m, uint32_t *tile_full) {
     const int nt = tiles_x * tiles_y * tiles_z;
-    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, ty, mask, tile_bits, diff, m);
+    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, ty, mask, tile_bits, diff, m,
+                                             tile_full);
 }
 
 void launch_assemble(const SlotDesc *slots, const SlotState *state, int m, const GridDims &fine,

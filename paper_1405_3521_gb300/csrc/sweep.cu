@@ -121,8 +121,10 @@ __device__ __forceinline__ float warp_max(float v) {
 // Node classes of Sec. 3 for one slot: ghost (outside a restricted
 // sub-domain), target (the slot's part of dG) or free (G).
 enum { CLS_FREE = 0, CLS_TARGET = 1, CLS_GHOST = 2 };
-__device__ __forceinline__ int node_class(const SlotDesc &S, long long gi) {
-    if (S.mask != nullptr && !((S.mask[gi] >> S.mask_bit) & 1u)) return CLS_GHOST;
+// inside: the node's tile lies wholly inside the slot's sub-domain (no mask
+// read needed).
+__device__ __forceinline__ int node_class(const SlotDesc &S, long long gi, bool inside = false) {
+    if (!inside && S.mask != nullptr && !((S.mask[gi] >> S.mask_bit) & 1u)) return CLS_GHOST;
     const int lab = S.labels[gi];
     if (lab != 0 && (S.only_target == 0 || lab == S.only_target)) return CLS_TARGET;
     return CLS_FREE;
@@ -624,7 +626,8 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
         const int gx = tx * TX + lx, gy = ty * TYT + ly;
         const float vold = T[(ly + H) * TW + lx + XPAD];
         const long long gi = static_cast<long long>(gy) * nx + gx;
-        const bool isfree = (gx < nx) && (gy < ny) && node_class(S, gi) == CLS_FREE;
+        const bool inside = S.tile_full != nullptr && ((S.tile_full[tile] >> S.mask_bit) & 1u);
+        const bool isfree = (gx < nx) && (gy < ny) && node_class(S, gi, inside) == CLS_FREE;
         const bool mine = isfree && grp == 0;  // group 0 owns the node's result
         float2 S2 = make_float2(0.0f, 0.0f), O02 = S2;
         float add = S.gl;
@@ -852,13 +855,14 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
         // the thread's column of TZ nodes: starting values and free flags
         float vold[TZ], vnew[TZ];
         unsigned freebits = 0u;
+        const bool inside = S.tile_full != nullptr && ((S.tile_full[tile] >> S.mask_bit) & 1u);
 #pragma unroll
         for (int lz = 0; lz < TZ; ++lz) {
             const int gz = tz * TZ + lz;
             vold[lz] = T[(lz + HZ) * LAYER + (ly + H) * TW + lx + XPAD];
             vnew[lz] = vold[lz];
             const long long gi = (static_cast<long long>(gz) * ny + gy) * nx + gx;
-            if ((gx < nx) && (gy < ny) && (gz < nz) && node_class(S, gi) == CLS_FREE)
+            if ((gx < nx) && (gy < ny) && (gz < nz) && node_class(S, gi, inside) == CLS_FREE)
                 freebits |= 1u << lz;
         }
         // args.local_iters applications of T to the tile's nodes with the
