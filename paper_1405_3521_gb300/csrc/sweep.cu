@@ -37,6 +37,10 @@ using namespace hjbk;
 #ifndef HJB_SWEEP2D_MINB
 #define HJB_SWEEP2D_MINB 8
 #endif
+// Resident CTAs per SM the 3D sweep is compiled for (register budget).
+#ifndef HJB_SWEEP3D_MINB
+#define HJB_SWEEP3D_MINB 4
+#endif
 
 namespace {
 
@@ -992,7 +996,7 @@ __device__ __forceinline__ void init_bars3(Smem3d &sm) {
 }
 
 template <bool WFORM>
-__global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant__ SweepArgs args) {
+__global__ void __launch_bounds__(THREADS, HJB_SWEEP3D_MINB) sweep3d_kernel(const __grid_constant__ SweepArgs args) {
     __shared__ alignas(128) Smem3d sm;
     const int p = static_cast<int>(args.ctl->sweep & 1u);
     const int nitems = args.ctl->qcount[p];
@@ -1005,7 +1009,7 @@ __global__ void __launch_bounds__(THREADS) sweep3d_kernel(const __grid_constant_
 }
 
 template <bool WFORM>
-__global__ void __launch_bounds__(THREADS) loop3d_kernel(const __grid_constant__ SweepArgs args) {
+__global__ void __launch_bounds__(THREADS, HJB_SWEEP3D_MINB) loop3d_kernel(const __grid_constant__ SweepArgs args) {
     __shared__ alignas(128) Smem3d sm;
     init_bars3(sm);
     unsigned uses[2] = {0u, 0u};
