@@ -97,17 +97,19 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def sweep_traffic():
-    """DRAM bytes per sweep launch from the committed ncu summary, or None
+def sweep_traffic(path=TRAFFIC_PROFILE):
+    """DRAM bytes per sweep launch from a committed ncu summary, or None
     when the kernel sources changed after the counters were taken."""
     try:
-        with open(TRAFFIC_PROFILE) as f:
+        with open(path) as f:
             kv = dict(line.strip("- \n").split(": ", 1) for line in f
                       if line.startswith("- ") and ": " in line)
         if kv.get("sources_sha256") != kernel_sources_sha256():
             return None
-        return {"bytes_per_launch": float(kv["traffic_bytes_per_launch"]),
-                "node_updates_per_launch": float(kv["node_updates_per_launch"])}
+        out = {"bytes_per_launch": float(kv["traffic_bytes_per_launch"])}
+        if "node_updates_per_launch" in kv:
+            out["node_updates_per_launch"] = float(kv["node_updates_per_launch"])
+        return out
     except (OSError, KeyError, ValueError):
         return None
 
@@ -298,6 +300,7 @@ def run_dubins(args, hjb, S, dev, flush, local):
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6660.0)
     ach = tot["node_updates"] * 9 / (tot["ms"] / 1e3) / 1e9  # V read+write 8 B, labels 1 B
+    traffic = sweep_traffic(os.path.join(ROOT, "profiles", "sweep3d_dubins256_launch_list_traffic.md"))
     cpu = None
     if not args.no_cpu_baseline:
         import oracle as orc
@@ -324,7 +327,10 @@ def run_dubins(args, hjb, S, dev, flush, local):
                       "solved_subdomains": sum(1 for s in per if s["node_updates"] > 0)},
           raw_node_updates_per_s=(rst["node_updates"] + tot["node_updates"]) / (ms / 1e3),
           roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": None, "kernel": "sweep3d_kernel (decomposed fine solve)",
+                    "traffic": traffic["bytes_per_launch"] if traffic else None,
+                    "traffic_unit": "DRAM bytes per sweep launch (ncu, warm L2)",
+                    "algorithmic_bytes_per_launch": 9 * tot["node_updates"] / max(1, tot["launches"]),
+                    "kernel": "sweep3d_kernel (decomposed fine solve)",
                     "bytes_per_node_update": 9},
           cpu_baseline=cpu, gpu_launches=rst["launches"] + tot["launches"], clocks=clocks)
 
