@@ -75,6 +75,39 @@ def test_create_validates_without_touching_the_gpu(libpath):
     assert L.hjb_destroy(None) == 0
 
 
+def test_create_validates_scheme_and_game_options(libpath):
+    """The options of the step weights, the interpolation, the per-axis scale
+    field and the second player are checked at creation (no GPU needed)."""
+    import paper_1405_3521_gb300 as hjb
+    lab = np.zeros(16, dtype=np.uint8)
+    A = S.circle_controls(4).astype(np.float32)
+    ok = dict(n_targets=1)
+    for bad in (dict(weights=2), dict(interp=3), dict(interp=-1)):
+        with pytest.raises(hjb.HJBError):
+            hjb.Problem((4, 4), (0, 0), (1, 1), A, lab, 0.1, **ok, **bad)
+    # speed and scale are exclusive
+    with pytest.raises(hjb.HJBError):
+        hjb.Problem((4, 4), (0, 0), (1, 1), A, lab, 0.1, speed=np.ones(16, np.float32),
+                    scale=np.ones((16, 2), np.float32), **ok)
+    # second player: count * count_b <= 128, finite components
+    with pytest.raises(hjb.HJBError):
+        hjb.Problem((4, 4), (0, 0), (1, 1), S.circle_controls(16), lab, 0.1,
+                    controls_b=np.zeros((9, 2), np.float32), **ok)
+    with pytest.raises(hjb.HJBError):
+        hjb.Problem((4, 4), (0, 0), (1, 1), A, lab, 0.1,
+                    controls_b=np.full((2, 2), np.inf, np.float32), **ok)
+    # P1 and games are 2D speed/current features
+    lab3 = np.zeros(4 * 4 * 4, dtype=np.uint8)
+    u = np.array([[-1.0], [0.0], [1.0]], np.float32)
+    with pytest.raises(hjb.HJBError):
+        hjb.Problem((4, 4, 4), (0, 0, 0), (1, 1, 6.28), u, lab3, 0.1, dyn=hjb.HJB_DYN_DUBINS,
+                    periodic=(0, 0, 1), interp=1, **ok)
+    # valid combinations are accepted
+    for good in (dict(weights=1), dict(interp=1), dict(scale=np.ones((16, 2), np.float32)),
+                 dict(controls_b=0.5 * A)):
+        hjb.Problem((4, 4), (0, 0), (1, 1), A, lab, 0.1, **ok, **good).close()
+
+
 def test_package_never_reaches_the_oracle():
     """The library path and the oracle share no code and the package never
     imports, loads or runs anything under oracle/."""
