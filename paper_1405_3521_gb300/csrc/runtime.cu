@@ -1541,7 +1541,26 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     args.L[1] = L1;
     args.ctl = ctl;
     args.use_handle = 1;
-    if (!P->adj_exec || std::memcmp(&P->adj_args_in_graph.ap, &args.ap, sizeof args.ap) ||
+    const char *ng = std::getenv("HJB_NO_GRAPH");
+    if (ng && ng[0] == '1') {
+        // host-driven loop (profiling aid): the same kernels, 8 iterations
+        // between reads of the convergence flag
+        args.use_handle = 0;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const void *fns[2] = {hjbh::adj_scatter_kernel(), hjbh::adj_resid_kernel()};
+        void *argv[1] = {&args};
+        for (;;) {
+            for (int rep = 0; rep < 8; ++rep)
+                for (int k = 0; k < 2; ++k)
+                    CK(cudaLaunchKernel(fns[k], dim3(sms * 8), dim3(hjbk::THREADS), argv, 0, st));
+            int conv = 0;
+            CK(cudaMemcpyAsync(&conv, &ctl->converged, sizeof conv, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (conv) break;
+        }
+    } else if (!P->adj_exec || std::memcmp(&P->adj_args_in_graph.ap, &args.ap, sizeof args.ap) ||
         std::memcmp(&P->adj_args_in_graph.ctrl, &args.ctrl, sizeof args.ctrl) ||
         P->adj_args_in_graph.L[0] != L0 || P->adj_args_in_graph.policy != args.policy ||
         P->adj_args_in_graph.g != args.g || P->adj_args_in_graph.ctl != ctl) {
@@ -1584,7 +1603,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
         CK(cudaGraphInstantiate(&P->adj_exec, P->adj_graph, 0));
         P->adj_args_in_graph = args;
     }
-    CK(cudaGraphLaunch(P->adj_exec, st));
+    if (args.use_handle) CK(cudaGraphLaunch(P->adj_exec, st));
     hjbh::AdjCtl hc;
     CK(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
