@@ -176,6 +176,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_cpu():
+    """The host processor as /proc/cpuinfo names it (model name on x86, the
+    implementer/part codes on Arm), with the machine type."""
+    import platform
+    name = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = {}
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    info.setdefault(k.strip().lower(), v.strip())
+        name = info.get("model name") or (
+            "implementer %s part %s" % (info.get("cpu implementer"), info.get("cpu part"))
+            if "cpu part" in info else None)
+    except OSError:
+        pass
+    return "%s (%s)" % (name or "unknown", platform.machine())
+
+
 def cpu_baseline(seconds, n):
     """The FP64 oracle as it stands (OpenMP Jacobi applications of T) on the
     host cores, on a bounded sample of the workload: whole sweeps over the
@@ -201,7 +221,7 @@ def cpu_baseline(seconds, n):
             break
     el = time.perf_counter() - t0
     return {"value": nfree * sweeps / el, "unit": UNIT, "cores": orc.max_threads() if cores < 1
-            else cores, "kind": "oracle",
+            else cores, "kind": "oracle", "cpu": host_cpu(),
             "sample": "%d Jacobi sweeps of the FP64 oracle over the %dx%d grid (%d free nodes, "
                       "64 controls) in %.1f s" % (sweeps, n, n, nfree, el)}
 
@@ -239,7 +259,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [args.n, args.n],
                                         "controls": 64, "targets": 16},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -313,7 +333,7 @@ def run_dubins(args, hjb, S, dev, flush, local):
             V, _ = orc.apply(po, V, nthreads=cores)
             sw += 1
         el = time.perf_counter() - t0
-        cpu = {"value": nfree * sw / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+        cpu = {"value": nfree * sw / el, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                "sample": "%d Jacobi sweeps of the FP64 oracle over the 256x256x128 grid in %.1f s"
                          % (sw, el)}
     _line(args, "node-updates/s to convergence, decomposed vs full-domain GPU (3D Dubins)",
@@ -451,7 +471,7 @@ def run_batch(args, hjb, S, dev, flush, local):
                 done += 3 * nfree[i]
             rounds += 1
         el = time.perf_counter() - t0
-        cpu = {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+        cpu = {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                "sample": "%d rounds of 3 Jacobi sweeps of the FP64 oracle on a size-stratified "
                          "sample of 16 batch problems (%d node-updates in %.1f s)"
                          % (rounds, done, el)}
