@@ -176,13 +176,14 @@ int hjb_destroy(hjb_problem *p);
  *       value_out on free nodes and 0 on targets (a supersolution).
  *  sweeps_per_check: sweeps between two convergence tests in the device loop
  *       (<= 0: library default).
- *  local_iters: applications of T to each staged tile per sweep (2D
- *       problems; <= 0: default 4, 16 at most).  The first reads the previous
- *       sweep's values; each further one reads the tile's own latest values
- *       with the halo held (block Gauss-Seidel inside the tile).  Every
- *       ordering of the updates has the same fixed point, and a sweep is still
- *       a beta-contraction, so tol keeps its meaning.  1 is plain value
- *       iteration (Jacobi).  Not used by the 3D kernel. */
+ *  local_iters: applications of T to each staged tile per sweep (<= 0:
+ *       default 4, 16 at most).  The first reads the previous sweep's
+ *       values; each further one reads the tile's own latest values with the
+ *       halo held (block Gauss-Seidel inside the tile), and a tile stops early
+ *       once an application changes none of its nodes.  Every ordering of the
+ *       updates has the same fixed point, and a sweep is still a
+ *       beta-contraction, so tol keeps its meaning.  1 is plain value
+ *       iteration (Jacobi). */
 typedef struct {
     double tol;
     int max_iters;

@@ -1,19 +1,24 @@
-// sweep.cu -- the value-iteration sweep: one Jacobi application of the
+// sweep.cu -- the value-iteration sweep: applications of the
 // semi-Lagrangian operator T of Festa (arXiv:1405.3521), Sec. 3, eq. (Tdef),
 //
 //   [T(V)]_i = beta * min_a I[V](x_i + h f(x_i, a)) + gamma * l_i   (free node)
 //
 // to every free node of every active problem ("slot") of a launch, with the
-// L-infinity residual ||T(V) - V|| of the stopping remark of Sec. 3 fused
-// into the same kernel, and the convergence decision taken by the last CTA
-// to finish (which also drives the CUDA-graph WHILE loop around the sweep).
+// L-infinity change over the sweep (the residual of the stopping remark of
+// Sec. 3) fused into the same kernel, and the convergence decision taken by
+// the last CTA to finish (which also drives the CUDA-graph WHILE loop around
+// the sweep).  A sweep applies T up to args.local_iters times to each staged
+// tile: the first application reads the previous sweep's values (with one,
+// the sweep is exactly one Jacobi application), each further one the
+// tile's own latest values with the halo held -- the same fixed point, and
+// still a beta-contraction per sweep.
 //
 // Design for sm_103a:
 //  * persistent grid (SMs x resident CTAs) over a device work queue of
 //    (slot, tile) items: a tile is queued for the next sweep only when a tile
 //    of its 3x3 (3x3x3) neighbourhood changed bitwise in this sweep, since
 //    otherwise its inputs, and hence its outputs, are those of the previous
-//    sweep -- the iteration stays exactly Jacobi while quiescent regions
+//    sweep -- skipping it changes no iterate, while quiescent regions
 //    (ahead of the front, and behind it once converged) cost nothing; tiles
 //    of converged slots drop out of the queue;
 //  * each tile of V plus its interpolation halo is staged in shared memory by
@@ -790,6 +795,7 @@ struct Smem3d {
     int item[2][3];
     float red[THREADS / 32];
     int cnt[THREADS / 32];
+    float2 trig[TZ];  // heading offsets of the item's layers
 };
 
 template <bool WFORM>
@@ -840,6 +846,12 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
             __syncthreads();
             continue;
         }
+        // the item's heading offsets, read once into shared memory (visible
+        // after the barrier below)
+        if (tid < TZ) {
+            const int gz = (tile / (S.tiles_x * S.tiles_y)) * TZ + tid;
+            sm.trig[tid] = gz < S.nz ? S.trig[gz] : make_float2(0.0f, 0.0f);
+        }
         const bool ok = mbar_wait_bounded(&sm.bar[b], uses[b] & 1u);
         uses[b] += 1u;
         if (!__syncthreads_and(ok)) {
@@ -879,7 +891,7 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
                 if (!((freebits >> lz) & 1u)) continue;
                 const int gz = tz * TZ + lz;
                 const long long gi = (static_cast<long long>(gz) * ny + gy) * nx + gx;
-                    const float2 tr = S.trig[gz];
+                    const float2 tr = sm.trig[lz];
                 float ox = tr.x, oy = tr.y;
                 bool out = false;
             if (!interior) {
