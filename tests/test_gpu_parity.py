@@ -505,3 +505,45 @@ def test_p1_interpolation(hjb, orc, which):
     Vb, _, tot = hjb.solve_decomposed(p, fine)
     assert tot["converged"] == 1
     assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V
+
+
+def test_decomposed_with_32_targets(hjb, orc):
+    """The largest label set (32 target components, bit 31 of the masks):
+    RA labels, the decomposed solve against the oracle's ISA, and equal
+    sub-domains (two components given the same node set) solved once."""
+    n = 129
+    X, Y = S.mesh2(n, n)
+    lab = np.zeros((n, n), np.uint8)
+    k = 0
+    for cy in np.linspace(-0.8, 0.8, 6):
+        for cx in np.linspace(-0.8, 0.8, 6):
+            if k == 32:
+                break
+            lab[np.hypot(X - cx, Y - cy) <= 0.07] = k + 1
+            k += 1
+    g = S.rng("misc", 33)
+    d = dict(shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=S.f32(S.circle_controls(16)), labels=lab, ntargets=32,
+             speed=S.f32(S.speed_field(g, X, Y)), current=None, h=2.0 / (n - 1), lam=1.0,
+             v_out=1.0)
+    po = oracle_problem(orc, d)
+    stride, delta = (4, 4), 0.05
+    Vaux_o, lab_o, _ = orc.ra(po, stride, delta, tol=1e-11)
+    p = gpu_problem(hjb, d)
+    fine, coarse, aux, _ = hjb.subdomains(p, stride, delta=delta, want_aux=True)
+    assert np.abs(to_np(aux).reshape(Vaux_o.shape) - Vaux_o).max() < TOL_V
+    diff = to_np(coarse).astype(np.uint32) ^ lab_o
+    vmin = Vaux_o.min(0)
+    for b in range(32):
+        bad = ((diff >> b) & 1) == 1
+        assert np.all(np.abs(np.abs(Vaux_o[b][bad] - vmin[bad]) - delta) <= TOL_V)
+    fine_o = orc.project(po, stride, lab_o).astype(np.uint32)
+    # components 30 and 31 get the node set of component 0
+    b0 = fine_o & np.uint32(1)
+    fine_o = (fine_o & ~np.uint32(0xC0000000)) | (b0 << np.uint32(30)) | (b0 << np.uint32(31))
+    Vb_o, _, _, _ = orc.isa(po, fine_o, tol=1e-11, nthreads=8)
+    Vb, per, tot = hjb.solve_decomposed(p, fine_o)
+    assert tot["converged"] == 1
+    assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V
+    assert per[30]["node_updates"] == 0 and per[31]["node_updates"] == 0
+    assert per[0]["node_updates"] > 0
