@@ -14,7 +14,11 @@
  * with I the multilinear (Q1) interpolation on a structured grid, a foot
  * strictly outside the closed box taking the value `value_out` (the image of
  * the paper's +infinity on ghost nodes), and the reconstruction (RA, Sec. 3)
- * and decomposed solve (ISA, Sec. 4) of independent sub-domains.
+ * and decomposed solve (ISA, Sec. 4) of independent sub-domains.  Options
+ * select the printed step weights 1/(1 + lambda h), h/(1 + lambda h) and P1
+ * interpolation on triangles (hjb_discount), and differential games with
+ * the max over a second player's control b outside the min over a
+ * (hjb_controls).
  *
  * Conventions for every entry point:
  *  - Return value: HJB_OK (0) or a negative HJB_ERR_* code.  The message of
