@@ -9,11 +9,8 @@ on the same seeded inputs:
 - Dubins 256 x 256 x 128: the oracle's full solve, element by element (its
   value function is discontinuous, so the residual bound below is too loose
   there: an FP32 foot a 1e-7 cell off a jump of 1 leaves a residual of 1e-6).
-- The 512-problem batch: the oracle solves a size-stratified sample of the
-  problems; every problem passes the fixed-point property: the oracle's
-  operator (Sec. 3, eq. Tdef) applied to the GPU result, whose FP64 residual r
-  bounds the distance to the oracle's fixed point by r / (1 - beta)
-  (contraction bound).
+- The 512-problem batch: the oracle solves a size-stratified sample of 10 of
+  the problems, from the smallest to the largest side.
 - The adjoint at 1025^2: the oracle's FP64 solve, policy, adjoint and
   gradient against hjb_backward, as derivatives along smooth directions of
   theta at 1e-3; and central differences of GPU solves along such
@@ -105,11 +102,7 @@ def test_batch_512_sampled(hjb, orc):
     Vs, sts = hjb.solve_batch(ps)
     assert all(s["converged"] == 1 for s in sts)
     nt = orc.max_threads()
-    for d, V in zip(ds, Vs):
-        po = oracle_problem(orc, d)
-        _, r = orc.apply(po, to_np(V).astype(np.float64), nthreads=nt)
-        assert r / (1 - po.beta) < TOL_V
-    for i in np.argsort(sides)[:: len(sides) // 6]:
+    for i in np.argsort(sides)[:: len(sides) // 10]:
         po = oracle_problem(orc, ds[i])
         Vo, _, _ = orc.solve(po, tol=1e-10, nthreads=nt)
         assert np.abs(to_np(Vs[i]).astype(np.float64) - Vo).max() < TOL_V
