@@ -162,10 +162,11 @@ __device__ __forceinline__ float q1_pairs(float2 P2, uint32_t K) {
     float lo0, lo1, hi0, hi1;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(lo0), "=f"(lo1) : "r"(addr));
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+512];" : "=f"(hi0), "=f"(hi1) : "r"(addr));
-    // lo = (v00, v10), hi = (v01, v11): lerp in y, then in x
-    const float a = fmaf(F2.y, hi0, E2.y * lo0);
-    const float b = fmaf(F2.y, hi1, E2.y * lo1);
-    return fmaf(F2.x, b, E2.x * a);
+    // lo = (v00, v10), hi = (v01, v11): the two lerps in y as one packed
+    // pair (the same roundings as two scalar ones), then the lerp in x
+    const float2 ab = __ffma2_rn(make_float2(F2.y, F2.y), make_float2(hi0, hi1),
+                                 __fmul2_rn(make_float2(E2.y, E2.y), make_float2(lo0, lo1)));
+    return fmaf(F2.x, ab.y, E2.x * ab.x);
 }
 
 // P1 variant ("linear n-dimensional interpolation" on the Kuhn triangles of
