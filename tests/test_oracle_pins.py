@@ -2,14 +2,16 @@
 
 Each test checks the oracle against what the paper or the mathematics fixes:
 exactness of Q1 interpolation on multilinear functions, brute-force policy
-enumeration with exact linear solves, graph shortest paths where every foot
+enumeration with exact linear solves, policy iteration (Howard) with sparse
+exact solves on 41^2 and Dubins grids, graph shortest paths where every foot
 lands on a node, closed-form solutions (distance to disks, constant drift,
 the strip of Example 3.1, the box-boundary distance of Sec. 4.1), the
 invariants of the iteration and of the reconstruction (Sec. 3), the defining
 property of independent sub-domains (a restricted solve reproduces the full
 values on policy-closed sets), the concave-hull projection against a direct
-enumeration of labelled simplices, Table 1 of the paper, and central finite
-differences for the adjoint gradient.
+enumeration of labelled simplices, Table 1 of the paper, and for the adjoint
+gradient central finite differences and the dot product with the
+tangent-linear model.
 """
 import itertools
 import json
@@ -295,6 +297,135 @@ def test_brute_force_dubins_periodic(orc):
     p = orc.Problem(shape, lo, hi, ctr, target, h=h, dyn=1, periodic=(0, 0, 1))
     V, _, _ = orc.solve(p, tol=1e-15)
     assert np.abs(V - Vb).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Policy iteration (Howard): an exact solver of the same discrete problem by
+# alternating exact policy evaluation (a sparse linear solve) and greedy
+# improvement.  It stops when no node's control can improve, which for a
+# discounted problem happens after finitely many steps at the optimal value,
+# so it pins the value iteration at sizes brute force cannot reach.
+
+def _transitions(shape, spacing, periodic, target, feet, cost, lam, h, v_out, implicit=False,
+                 p1=False):
+    """(R, b, free, beta): R sparse [F * A, F], row k * A + j the interpolation
+    weights of the foot of free node k under control j on the free nodes
+    (target nodes hold 0); b [F, A] the running cost plus beta v_out for a
+    foot outside the box."""
+    import scipy.sparse as sp
+    N = int(np.prod(shape))
+    if implicit:
+        beta, gam = 1.0 / (1.0 + lam * h), h / (1.0 + lam * h)
+    else:
+        beta = math.exp(-lam * h)
+        gam = (1 - beta) / lam
+    free = np.nonzero(np.asarray(target) == 0)[0]
+    pos = np.full(N, -1)
+    pos[free] = np.arange(len(free))
+    A = len(feet[free[0]])
+    rows, cols, vals = [], [], []
+    b = np.zeros((len(free), A))
+    for k, i in enumerate(free):
+        idx, r = [], int(i)
+        for d in range(len(shape)):
+            idx.append(r % shape[d])
+            r //= shape[d]
+        for j in range(A):
+            st = _stencil(shape, spacing, periodic, idx, feet[i][j], p1=p1)
+            b[k, j] = gam * cost[i]
+            if st is None:
+                b[k, j] += beta * v_out
+                continue
+            for flat, w in st:
+                if pos[flat] >= 0 and w != 0.0:
+                    rows.append(k * A + j)
+                    cols.append(pos[flat])
+                    vals.append(w)
+    R = sp.csr_matrix((vals, (rows, cols)), shape=(len(free) * A, len(free)))
+    return R, b, free, beta
+
+
+def _howard(R, b, beta, max_steps=2000):
+    """Policy iteration from the all-zero policy; a control is replaced only
+    by a strictly better one (1e-13), so the iteration cannot cycle."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    F, A = b.shape
+    ar = np.arange(F)
+    pol = np.zeros(F, dtype=np.int64)
+    eye = sp.identity(F, format="csr")
+    for step in range(max_steps):
+        V = spl.spsolve((eye - beta * R[ar * A + pol]).tocsc(), b[ar, pol])
+        Q = b + beta * (R @ V).reshape(F, A)
+        best = Q.argmin(axis=1)
+        better = Q[ar, best] < Q[ar, pol] - 1e-13
+        if not better.any():
+            return V, step
+        pol = np.where(better, best, pol)
+    raise AssertionError("policy iteration did not terminate")
+
+
+def _zermelo_fields(n, A, seed):
+    X, Y = S.mesh2(n, n)
+    g = np.random.default_rng(seed)
+    s = S.speed_field(g, X, Y).reshape(-1)
+    cur = S.current_field(g, X, Y).reshape(-1, 2)
+    cost = g.uniform(0.5, 2.0, n * n)
+    cen = S.disk_centers(g, 3, radius=0.15)
+    lab = S.disk_labels(X, Y, cen, 0.15).reshape(-1)
+    return s, cur, cost, lab
+
+
+@pytest.mark.parametrize("variant", ["q1", "implicit", "p1"])
+def test_policy_iteration_zermelo(orc, variant):
+    """41^2 grid, 16 controls, speed, divergence-free current, cost field,
+    lambda = 0.8, three target disks: the value iteration's fixed point equals
+    Howard's exact solution, with the exponential or the printed implicit step
+    weights, with Q1 or P1 interpolation."""
+    n, A = 41, 16
+    s, cur, cost, lab = _zermelo_fields(n, A, 21)
+    ctr = S.circle_controls(A)
+    h, lam, v_out = 2.0 / (n - 1), 0.8, 2.5
+    dx = 2.0 / (n - 1)
+    feet = [[h * (s[i] * ctr[j] + cur[i]) for j in range(A)] for i in range(n * n)]
+    implicit, p1 = variant == "implicit", variant == "p1"
+    R, b, free, beta = _transitions((n, n), (dx, dx), (0, 0), lab, feet, cost, lam, h, v_out,
+                                    implicit=implicit, p1=p1)
+    Vh, steps = _howard(R, b, beta)
+    assert steps >= 2
+    p = orc.Problem((n, n), (-1, -1), (1, 1), ctr, lab, h, lam=lam, speed=s, current=cur,
+                    cost=cost, v_out=v_out, weights=int(implicit), interp=int(p1))
+    V, _, _ = orc.solve(p, tol=1e-14, max_iters=1_000_000)
+    assert np.abs(V[free] - Vh).max() < 1e-11
+    assert np.abs(V[lab != 0]).max() == 0.0
+
+
+def test_policy_iteration_dubins(orc):
+    """Dubins car on 16 x 16 x 12 with periodic heading, three turn rates,
+    two target disks: value iteration equals Howard's exact solution."""
+    nx, nth = 16, 12
+    shape = (nx, nx, nth)
+    dx, dth = 2.0 / (nx - 1), 2 * np.pi / nth
+    h = dx
+    x = np.linspace(-1, 1, nx)
+    lab = np.zeros(shape[::-1], dtype=np.int32)
+    for k, (cx, cy) in enumerate([(-0.4, 0.3), (0.5, -0.5)]):
+        inside = (x[None, :] - cx) ** 2 + (x[:, None] - cy) ** 2 <= 0.3 ** 2
+        lab[:, inside] = k + 1
+    lab = lab.reshape(-1)
+    N = lab.size
+    feet = []
+    for i in range(N):
+        th = (i // (nx * nx)) * dth
+        feet.append([np.array([h * np.cos(th), h * np.sin(th), h * u]) for u in (-1.0, 0.0, 1.0)])
+    R, b, free, beta = _transitions(shape, (dx, dx, dth), (0, 0, 1), lab, feet, np.ones(N), 1.0,
+                                    h, 1.0)
+    Vh, steps = _howard(R, b, beta)
+    assert steps >= 2
+    p = orc.Problem(shape, (-1, -1, 0), (1, 1, 2 * np.pi), [[-1.0], [0.0], [1.0]], lab, h,
+                    dyn=1, periodic=(0, 0, 1))
+    V, _, _ = orc.solve(p, tol=1e-14, max_iters=1_000_000)
+    assert np.abs(V[free] - Vh).max() < 1e-11
 
 
 # --------------------------------------------------------------------------
@@ -793,6 +924,94 @@ def test_adjoint_matches_finite_differences(orc):
         if (pp != pol).any():
             continue
         assert abs((Lp - L0) / 1e-3 - gc[i]) < 1e-8 + 1e-6 * abs(gc[i])
+
+
+def _q1_gradient(shape, spacing, idx, off):
+    """d/dy of the bilinear interpolant at the foot x_idx + off, as
+    [(flat, d weight / dy_x, d weight / dy_y)], in the cell the foot rule
+    picks (the last cell on the upper face)."""
+    cells = []
+    for d in range(2):
+        gd = min(max(idx[d] + off[d] / spacing[d], 0.0), shape[d] - 1.0)
+        c = min(max(int(math.floor(gd)), 0), shape[d] - 2)
+        cells.append((c, gd - c))
+    (cx, tx), (cy, ty) = cells
+    out = []
+    for bx, by in itertools.product((0, 1), repeat=2):
+        wx = tx if bx else 1.0 - tx
+        wy = ty if by else 1.0 - ty
+        sx = 1.0 if bx else -1.0
+        sy = 1.0 if by else -1.0
+        out.append((_grid_index(shape, (cx + bx, cy + by)), sx * wy / spacing[0],
+                    sy * wx / spacing[1]))
+    return out
+
+
+def test_adjoint_tangent_linear_dot_product(orc):
+    """The adjoint against the tangent-linear model (exact linear solves, no
+    oracle code): with the optimal policy frozen, a perturbation d of
+    theta = log s moves V by dV solving (I - beta P) dV = beta c d, where c_i
+    is the derivative of I[V] at the foot along h s_i a_pi(i).  The loss
+    derivative g . dV must equal (dL/dtheta) . d to rounding, for several
+    random directions; and dV agrees with central differences of full oracle
+    solves along a smooth direction."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    n, A = 21, 16
+    X, Y, th, lab, pts = _c5_small(n, A)
+    lab = lab.reshape(-1)
+    ctr = S.circle_controls(A)
+    h = dx = 2.0 / (n - 1)
+    s = np.exp(th.reshape(-1))
+
+    def prob(theta):
+        return orc.Problem((n, n), (-1, -1), (1, 1), ctr, lab, h, speed=np.exp(theta))
+
+    p = prob(th.reshape(-1))
+    V, _, _ = orc.solve(p, tol=1e-15, max_iters=200000)
+    pol, _ = orc.policy(p, V)
+    _, gV = orc.points(p, V, pts)
+    lam, _, _ = orc.adjoint(p, pol, gV, tol=1e-15)
+    gt, _ = orc.grad(p, V, pol, lam)
+    feet = [[h * s[i] * ctr[j] for j in range(A)] for i in range(n * n)]
+    R, b, free, beta = _transitions((n, n), (dx, dx), (0, 0), lab, feet, np.ones(n * n), 1.0, h,
+                                    1.0)
+    F = len(free)
+    ar = np.arange(F)
+    # the oracle's policy is optimal for the independently built problem
+    Q = b + beta * (R @ V[free]).reshape(F, A)
+    assert np.abs(Q[ar, pol[free]] - Q.min(axis=1)).max() < 1e-12
+    assert np.abs(Q[ar, pol[free]] - V[free]).max() < 1e-12
+    c = np.zeros(F)
+    inside = np.zeros(F, dtype=bool)
+    for k, i in enumerate(free):
+        idx = (i % n, i // n)
+        off = feet[i][pol[i]]
+        if _stencil((n, n), (dx, dx), (0, 0), idx, off) is None:
+            continue
+        inside[k] = True
+        direc = h * s[i] * ctr[pol[i]]
+        for flat, gx, gy in _q1_gradient((n, n), (dx, dx), idx, off):
+            c[k] += V[flat] * (gx * direc[0] + gy * direc[1])
+    assert inside.sum() > 0.9 * F
+    M = (sp.identity(F, format="csr") - beta * R[ar * A + pol[free]]).tocsc()
+    lu = spl.splu(M)
+    g = np.random.default_rng(17)
+    for _ in range(4):
+        d = np.zeros(n * n)
+        d[free] = g.normal(size=F)
+        dV = lu.solve(beta * c * d[free])
+        lhs = gV[free] @ dV
+        rhs = gt @ d
+        assert abs(lhs - rhs) <= 1e-10 * (np.abs(gt) @ np.abs(d)), (lhs, rhs)
+    # tangent-linear model against central differences along a smooth field
+    d = np.where(lab == 0, (np.sin(1.7 * X + 0.4) * np.cos(0.9 * Y)).reshape(-1), 0.0)
+    dV = lu.solve(beta * c * d[free])
+    eps = 1e-6
+    Vp, _, _ = orc.solve(prob(th.reshape(-1) + eps * d), tol=1e-15, max_iters=200000)
+    Vm, _, _ = orc.solve(prob(th.reshape(-1) - eps * d), tol=1e-15, max_iters=200000)
+    fd = (Vp[free] - Vm[free]) / (2 * eps)
+    assert np.abs(fd - dV).max() <= 1e-5 * np.abs(dV).max()
 
 
 def test_points_loss_gradient_is_interpolation_weights(orc):
