@@ -59,7 +59,8 @@ def parse():
                     help="dubins / adjoint: a reduced size (126x126x64 / 257^2) for detailed "
                          "profiler captures; not a benchmark configuration")
     ap.add_argument("--profile", choices=["full", "decomposed", "ra"], default=None,
-                    help="run one solve of that path (after one warm-up) for a profiler; "
+                    help="run one solve of that path (after one warm-up; decomposed: once per 2D "
+                         "tile shape) for a profiler; "
                          "prints per-solve statistics instead of the JSON line")
     return ap.parse_args()
 
@@ -97,18 +98,20 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def sweep_traffic(path=TRAFFIC_PROFILE):
-    """DRAM bytes per sweep launch from a committed ncu summary, or None
-    when the kernel sources changed after the counters were taken."""
+def sweep_traffic(path=TRAFFIC_PROFILE, rows=None):
+    """DRAM bytes per sweep launch from a committed ncu summary (for the 2D
+    tile shape with `rows` rows when the summary lists shapes), or None when
+    the kernel sources changed after the counters were taken."""
     try:
         with open(path) as f:
             kv = dict(line.strip("- \n").split(": ", 1) for line in f
                       if line.startswith("- ") and ": " in line)
         if kv.get("sources_sha256") != kernel_sources_sha256():
             return None
-        out = {"bytes_per_launch": float(kv["traffic_bytes_per_launch"])}
-        if "node_updates_per_launch" in kv:
-            out["node_updates_per_launch"] = float(kv["node_updates_per_launch"])
+        sfx = "_rows%d" % rows if rows and ("traffic_bytes_per_launch_rows%d" % rows) in kv else ""
+        out = {"bytes_per_launch": float(kv["traffic_bytes_per_launch" + sfx])}
+        if "node_updates_per_launch" + sfx in kv:
+            out["node_updates_per_launch"] = float(kv["node_updates_per_launch" + sfx])
         return out
     except (OSError, KeyError, ValueError):
         return None
@@ -577,14 +580,23 @@ def main():
             if args.profile == "full":
                 _, st = hjb.solve(p)
                 info = st
-            else:
+            elif args.profile == "ra":
                 fine, _, _, rst = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
                 info = rst
-                if args.profile == "decomposed":
+            else:
+                # the decomposed fine solve once per 2D tile shape, in the
+                # order 32 x 8, 32 x 4, 32 x 2 (the RA coarse solve first)
+                fine, _, _, rst = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
+                f = fine.cpu().numpy().astype(np.uint32)
+                info = {}
+                for r in (8, 4, 2):
+                    os.environ["HJB_TILE_ROWS"] = str(r)
                     _, per, tot = hjb.solve_decomposed(p, fine)
-                    f = fine.cpu().numpy().astype(np.uint32)
-                    info = {"total": tot, "per": [(s_["iterations"], int(((f >> k) & 1).sum()))
-                                                  for k, s_ in enumerate(per)]}
+                    info[r] = {"total": tot, "per": [(s_["iterations"], int(((f >> k) & 1).sum()))
+                                                     for k, s_ in enumerate(per)]}
+                del os.environ["HJB_TILE_ROWS"]
+                torch.cuda.synchronize()
+                break
             torch.cuda.synchronize()
         print(json.dumps(info))
         return
@@ -659,7 +671,8 @@ def main():
     fmax = peaks.get("sm_max_mhz", 2070.0) * 1e6
     peak_ops = sms * 128 * fmax
     achieved = (tot["node_updates"] * 64 * OPS_PER_CONTROL) / (tot["ms"] / 1e3)
-    traffic = sweep_traffic()
+    rows = tot.get("tile_rows") or None
+    traffic = sweep_traffic(rows=rows)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle  # noqa: F401
@@ -688,7 +701,8 @@ def main():
                      "traffic_unit": "DRAM bytes per sweep launch (ncu, warm L2)",
                      "algorithmic_bytes_per_launch": (
                          9 * traffic["node_updates_per_launch"] if traffic else None),
-                     "kernel": "sweep2d_kernel<64,W,2> (decomposed fine solve)",
+                     "kernel": "sweep2d_kernel<64,W,2> 32x%s tiles (decomposed fine solve)"
+                               % (rows or "?"),
                      "peak_source": "SMs x 128 FP32 lanes x max SM clock (derived)"},
         "cpu_baseline": cpu,
         "e2e": {"value": nfree * iters_full / e2e_s * world, "unit": UNIT,

@@ -209,6 +209,8 @@ typedef struct {
     long long ties;        /* label decisions within 1e-6 of the threshold */
     long long labelled;    /* sum over sub-domains of their node counts */
     long long launches;    /* CUDA kernels the call launched */
+    int tile_rows;         /* rows of the 2D tiles the sweeps ran on (32 x 8, 4 or 2 nodes:
+                              the autotuner's choice or HJB_TILE_ROWS); 0 for 3D */
 } hjb_stats;
 
 /* Full-domain solve of V = T(V) by value iteration V^{n+1} = T(V^n)

@@ -81,7 +81,7 @@ class hjb_solve_opts(C.Structure):
 class hjb_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("node_updates", C.c_longlong),
                 ("final_residual", C.c_double), ("ms", C.c_double), ("ties", C.c_longlong),
-                ("labelled", C.c_longlong), ("launches", C.c_longlong)]
+                ("labelled", C.c_longlong), ("launches", C.c_longlong), ("tile_rows", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -94,6 +94,8 @@ struct Ctl {
     alignas(128) unsigned done_ctas;
     alignas(128) unsigned gen;  // generation of the cooperative loop's grid barrier
     alignas(128) int qcount[2];  // entries of the two tile queues (parity = sweep parity)
+    // queue entries handed out past each CTA's first one (dynamic scheduling)
+    alignas(128) int qhead[2];
     alignas(128) unsigned sweep;  // number of sweeps so far (parity of the source buffer)
     int nactive;
     int error;           // non-zero: a bounded wait gave up
@@ -115,6 +117,10 @@ struct SweepArgs {
     cudaGraphConditionalHandle handle;
     float stall_tol;
     int local_iters;  // applications of T per tile and sweep (2D; >= 1)
+    // 1: a CTA takes its items after the first from a shared counter, so
+    // CTAs that drew cheap tiles take more; 0: CTA b takes entries b,
+    // b + grid, b + 2 grid, ...  The iterates do not depend on the order.
+    int dyn_queue;
     ControlTable ctrl;
 };
 

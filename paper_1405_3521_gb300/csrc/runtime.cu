@@ -163,6 +163,8 @@ struct RunCtx {
     const uint32_t *diff = nullptr;  // decomposed solve: membership differences (twins)
     int local_iters = 1;             // applications of T per tile and sweep (2D)
     int li_in_graph = -1;
+    int dyn_queue = 0;               // tile-queue sharing of this run (SweepArgs::dyn_queue)
+    int dq_in_graph = -1;
     int spb = 0;
     const void *graph_slots = nullptr;
     const void *graph_q = nullptr;
@@ -565,8 +567,18 @@ int local_iters(const hjb_solve_opts *o) {
     return v < 1 ? 1 : (v > 16 ? 16 : v);
 }
 
+// How the CTAs of a sweep share its tile queue: by default the entries past
+// each CTA's first one are handed out by a counter (items cost 1 to
+// local_iters applications, so CTAs that drew cheap ones take more);
+// HJB_QUEUE=static strides by the grid size instead.  Read at each solve.
+int queue_mode() {
+    const char *e = std::getenv("HJB_QUEUE");
+    return (e && std::strcmp(e, "static") == 0) ? 0 : 1;
+}
+
 void set_queue_args(const RunCtx &R, hjbk::SweepArgs &a) {
     a.local_iters = R.local_iters;
+    a.dyn_queue = R.dyn_queue;
     const size_t fb = (static_cast<size_t>(R.qtiles) + 3) / 4 * 4;
     a.qlist[0] = R.qlist.as<int>();
     a.qlist[1] = R.qlist.as<int>() + R.qtiles;
@@ -582,6 +594,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     if (R.exec && R.key.dubins == key.dubins && R.key.wform == key.wform && R.key.na == key.na &&
         R.key.halo == key.halo && R.key.ty == key.ty && R.key.groups == key.groups &&
         R.key.loop == key.loop && R.li_in_graph == R.local_iters &&
+        R.dq_in_graph == R.dyn_queue &&
         R.spb == spb && R.graph_slots == R.d_slots.p &&
         R.graph_q == R.qlist.p && R.graph_f == R.qflag.p &&
         R.graph_nslots == n && std::memcmp(&R.ctrl_in_graph, &ctrl, sizeof ctrl) == 0)
@@ -636,6 +649,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     R.key = key;
     R.spb = spb;
     R.li_in_graph = R.local_iters;
+    R.dq_in_graph = R.dyn_queue;
     R.graph_slots = R.d_slots.p;
     R.graph_q = R.qlist.p;
     R.graph_f = R.qflag.p;
@@ -669,6 +683,7 @@ int run_loop(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlT
              cudaStream_t st, int local = 1) {
     const int n = static_cast<int>(R.slots.size());
     R.local_iters = local;
+    R.dyn_queue = queue_mode();
     hjbh::launch_loop_init(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), R.d_ctl.as<Ctl>(),
                            n, st, R.diff);
     {
@@ -1038,6 +1053,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_ou
         fill_stats(stats, R.h_state[0]);
         stats->ms = ms;
         stats->launches = pr.launches + 4 + sweeps;
+        stats->tile_rows = P->grid.ndim == 2 ? rows : 0;
     }
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
     if (!R.h_state[0].converged)
@@ -1320,6 +1336,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
         if (per_subdomain) {
             fill_stats(&per_subdomain[k], s);
             per_subdomain[k].ms = ms;
+            per_subdomain[k].tile_rows = P->grid.ndim == 2 ? rows : 0;
         }
         tot.iterations = s.iters > tot.iterations ? s.iters : tot.iterations;
         tot.node_updates += static_cast<long long>(s.updates);
@@ -1329,6 +1346,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     tot.converged = conv;
     tot.ms = ms;
     tot.launches = pr.launches + 5 + sweeps;
+    tot.tile_rows = P->grid.ndim == 2 ? rows : 0;
     if (total) *total = tot;
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
     if (!conv) return fail(HJB_ERR_NOT_CONVERGED, "a sub-domain did not converge");
@@ -1438,6 +1456,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
             fill_stats(&per_problem[i], R.h_state[i]);
             per_problem[i].ms = ms;
             per_problem[i].launches = nl;
+            per_problem[i].tile_rows = P0->grid.ndim == 2 ? rows : 0;
         }
         conv &= R.h_state[i].converged ? 1 : 0;
     }
@@ -1899,6 +1918,7 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     args.use_handle = 0;
     args.stall_tol = 8.0f * 1.1920929e-7f;
     args.local_iters = local_iters(opts);
+    args.dyn_queue = queue_mode();
     args.ctrl = ctrl;
     hjbh::launch_queue_init(d_slot, 1, tiles, d_ctl, args.qlist[0], args.qflag[0], args.qflag[1], st);
     const hjbh::SweepKey key{0, wform ? 1 : 0, controls->count, halo, rows, 1, 1};
@@ -1917,6 +1937,7 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     if (stats) {
         fill_stats(stats, hs);
         stats->launches = (dyn->log_speed ? 1 : 0) + (speed ? 1 : 0) + (dyn->current ? 2 : 0) + 5;
+        stats->tile_rows = rows;
     }
     if (herr[0]) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up");
     if (!hs.converged)

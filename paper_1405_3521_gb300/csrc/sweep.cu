@@ -413,6 +413,7 @@ __device__ void finish_sweep(const SweepArgs &args) {
     if (threadIdx.x == 0) {
         ctl->nactive = tc;
         ctl->qcount[p] = 0;  // every entry of this sweep's queue was consumed
+        ctl->qhead[p] = 0;
         if (n > 0) ctl->sweep = __ldcg(&ctl->sweep) + 1u;
         ctl->launches = __ldcg(&ctl->launches) + 1u;
         ctl->done_ctas = 0u;
@@ -439,6 +440,22 @@ __device__ __forceinline__ void cta_done(const SweepArgs &args, bool failed, int
         __threadfence();
         finish_sweep(args);
     }
+}
+
+// Queue entry of a CTA's next item, taken by thread 0 and published in
+// `next` (the other threads read it after the loop body's barriers; the
+// value they get back here is unused).  Static: entry v + grid.  Dynamic:
+// entries past the first grid-size ones are handed out in order by one
+// counter, so a CTA whose items were cheap takes more of them.
+__device__ __forceinline__ int next_entry(const SweepArgs &args, int &next, int v, int p,
+                                          int nitems) {
+    int vn = nitems;
+    if (threadIdx.x == 0) {
+        vn = args.dyn_queue ? static_cast<int>(gridDim.x) + atomicAdd(&args.ctl->qhead[p], 1)
+                            : v + static_cast<int>(gridDim.x);
+        next = vn;
+    }
+    return vn;
 }
 
 // Tile queue of the next sweep: called by warp 0 of a CTA whose tile changed
@@ -555,6 +572,7 @@ struct Smem2d {
     float2 pair[ROWS * PW];
     uint64_t bar[2];
     int item[2][3];
+    int next;  // queue entry of the CTA's next item
     float red[THREADS / 32];
     int cnt[THREADS / 32];
     float part[G][TYT][32];
@@ -604,16 +622,18 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
     if (tid == 0 && v < nitems) issue(v, b0);
     __syncthreads();
     bool failed = false;
-    for (int it = 0; v < nitems; ++it, v += gridDim.x) {
+    for (int it = 0; v < nitems; ++it, v = sm.next) {
         const int b = (b0 + it) & 1;
-        const int vn = v + gridDim.x;
         const int slot = sm.item[b][0], tile = sm.item[b][1], live = sm.item[b][2];
-        __syncthreads();  // everyone has read sm.item[b]; buffer b ^ 1 is free
-        if (tid == 0 && vn < nitems) issue(vn, b ^ 1);
+        __syncthreads();  // everyone has read sm.item[b] and sm.next; buffer b ^ 1 is free
+        if (tid == 0) {
+            const int vn = next_entry(args, sm.next, v, p, nitems);
+            if (vn < nitems) issue(vn, b ^ 1);
+        }
         const SlotDesc &S = args.slots[slot];
         if (!live) {
             if (tid == 0) unflag(args, S, tile, p);
-            __syncthreads();  // sm.item[b ^ 1] written by the issue above
+            __syncthreads();  // sm.item[b ^ 1] and sm.next written above
             continue;
         }
         const bool ok = mbar_wait_bounded(&sm.bar[b], uses[b] & 1u);
@@ -621,7 +641,7 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
         if (!__syncthreads_and(ok)) {
             failed = true;
             // let the prefetch of the next item (if any) land before leaving
-            if (tid == 0 && vn < nitems && sm.item[b ^ 1][2])
+            if (tid == 0 && sm.next < nitems && sm.item[b ^ 1][2])
                 mbar_wait_bounded(&sm.bar[b ^ 1], uses[b ^ 1] & 1u);
             break;
         }
@@ -794,6 +814,7 @@ struct Smem3d {
     float tile[2][TILE_STRIDE];
     uint64_t bar[2];
     int item[2][3];
+    int next;  // queue entry of the CTA's next item
     float red[THREADS / 32];
     int cnt[THREADS / 32];
     float2 trig[TZ];  // heading offsets of the item's layers
@@ -835,16 +856,18 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
     if (tid == 0 && v < nitems) issue(v, b0);
     __syncthreads();
     bool failed = false;
-    for (int it = 0; v < nitems; ++it, v += gridDim.x) {
+    for (int it = 0; v < nitems; ++it, v = sm.next) {
         const int b = (b0 + it) & 1;
-        const int vn = v + gridDim.x;
         const int slot = sm.item[b][0], tile = sm.item[b][1], live = sm.item[b][2];
-        __syncthreads();
-        if (tid == 0 && vn < nitems) issue(vn, b ^ 1);
+        __syncthreads();  // everyone has read sm.item[b] and sm.next; buffer b ^ 1 is free
+        if (tid == 0) {
+            const int vn = next_entry(args, sm.next, v, p, nitems);
+            if (vn < nitems) issue(vn, b ^ 1);
+        }
         const SlotDesc &S = args.slots[slot];
         if (!live) {
             if (tid == 0) unflag(args, S, tile, p);
-            __syncthreads();
+            __syncthreads();  // sm.item[b ^ 1] and sm.next written above
             continue;
         }
         // the item's heading offsets, read once into shared memory (visible
@@ -857,7 +880,7 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
         uses[b] += 1u;
         if (!__syncthreads_and(ok)) {
             failed = true;
-            if (tid == 0 && vn < nitems && sm.item[b ^ 1][2])
+            if (tid == 0 && sm.next < nitems && sm.item[b ^ 1][2])
                 mbar_wait_bounded(&sm.bar[b ^ 1], uses[b ^ 1] & 1u);
             break;
         }
@@ -1076,6 +1099,8 @@ __global__ void loop_init_kernel(SlotState *state, Ctl *ctl, int nslots, const u
         ctl->gen = 0u;
         ctl->qcount[0] = 0;
         ctl->qcount[1] = 0;
+        ctl->qhead[0] = 0;
+        ctl->qhead[1] = 0;
     }
 }
 

@@ -346,6 +346,45 @@ def test_tile_shapes_agree_bitwise(hjb, orc, monkeypatch):
     assert np.abs(outs[0] - Vo).max() < TOL_V
 
 
+@pytest.mark.parametrize("loop", ["graph", "coop"])
+def test_queue_schedules_agree_bitwise(hjb, monkeypatch, loop):
+    """Static and dynamic sharing of a sweep's tile queue among the CTAs run
+    the identical iteration: a tile's new values depend only on the previous
+    sweep's values and its own staged tile, so V, the sweep count and the
+    node-update count agree bitwise.  2D full, decomposed and batched solves
+    with four applications per tile (more tiles than resident CTAs, items of
+    unequal cost), and the 3D Dubins solve."""
+    monkeypatch.setenv("HJB_LOOP", loop)
+    n, A = 577, 16
+    X, Y = S.mesh2(n, n)
+    g = S.rng("misc", 31)
+    lab = S.disk_labels(X, Y, S.disk_centers(g, 5, 0.1), 0.1)
+    d = dict(shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=S.f32(S.circle_controls(A)), labels=lab, ntargets=5,
+             speed=S.f32(S.speed_field(g, X, Y)), current=S.f32(S.current_field(g, X, Y)),
+             h=2.0 / (n - 1), lam=1.0, v_out=1.0)
+    p = gpu_problem(hjb, d)
+    batch = [gpu_problem(hjb, S.c4_problem(i, m)) for i, m in ((0, 200), (1, 333), (2, 150))]
+    p3 = gpu_problem(hjb, S.c3(nxy=64, nth=32, ntargets=3, stride=(3, 3, 4)))
+    runs = {}
+    for mode in ("static", "dynamic"):
+        monkeypatch.setenv("HJB_QUEUE", mode)
+        out = []
+        V, st = hjb.solve(p, local_iters=4)
+        out.append((to_np(V), st["iterations"], st["node_updates"]))
+        fine, _, _, _ = hjb.subdomains(p, (16, 16), delta=0.2)
+        Vb, _, tot = hjb.solve_decomposed(p, fine, local_iters=4)
+        out.append((to_np(Vb), tot["iterations"], tot["node_updates"]))
+        Vs, sts = hjb.solve_batch(batch, local_iters=4)
+        out += [(to_np(v), s["iterations"], s["node_updates"]) for v, s in zip(Vs, sts)]
+        V3, st3 = hjb.solve(p3)
+        out.append((to_np(V3), st3["iterations"], st3["node_updates"]))
+        runs[mode] = out
+    for (va, ia, ua), (vb, ib, ub) in zip(runs["static"], runs["dynamic"]):
+        assert np.array_equal(va, vb)
+        assert (ia, ua) == (ib, ub)
+
+
 def test_local_iterations_same_fixed_point(hjb, orc):
     """Several applications of T per staged tile (the halo held) reach the
     fixed point of plain value iteration in fewer sweeps: each GPU result is
