@@ -585,16 +585,21 @@ def main():
                 info = rst
             else:
                 # the decomposed fine solve once per 2D tile shape, in the
-                # order 32 x 8, 32 x 4, 32 x 2 (the RA coarse solve first)
+                # order 32 x 8, 32 x 4, 32 x 2 (the RA coarse solve first), or
+                # only the shape HJB_TILE_ROWS forces
                 fine, _, _, rst = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
                 f = fine.cpu().numpy().astype(np.uint32)
                 info = {}
-                for r in (8, 4, 2):
+                forced = os.environ.get("HJB_TILE_ROWS")
+                for r in ((int(forced),) if forced else (8, 4, 2)):
                     os.environ["HJB_TILE_ROWS"] = str(r)
                     _, per, tot = hjb.solve_decomposed(p, fine)
                     info[r] = {"total": tot, "per": [(s_["iterations"], int(((f >> k) & 1).sum()))
                                                      for k, s_ in enumerate(per)]}
-                del os.environ["HJB_TILE_ROWS"]
+                if forced:
+                    os.environ["HJB_TILE_ROWS"] = forced
+                else:
+                    del os.environ["HJB_TILE_ROWS"]
                 torch.cuda.synchronize()
                 break
             torch.cuda.synchronize()
