@@ -557,11 +557,11 @@ int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows) {
 }
 
 // Applications of T per tile and sweep in the 2D kernels: opts->local_iters
-// when positive, else HJB_LOCAL_ITERS, else 4 (clamped to 1..16).
+// when positive, else HJB_LOCAL_ITERS, else 6 (clamped to 1..16).
 int local_iters(const hjb_solve_opts *o) {
     static const int dflt = [] {
         const char *e = std::getenv("HJB_LOCAL_ITERS");
-        return e ? std::atoi(e) : 4;
+        return e ? std::atoi(e) : 6;
     }();
     const int v = (o && o->local_iters > 0) ? o->local_iters : dflt;
     return v < 1 ? 1 : (v > 16 ? 16 : v);

@@ -1,5 +1,5 @@
 """Parity at the full sizes of the workloads, in the launch configuration the
-benchmark times: the tuner's tile shape, the graph loop, four applications of
+benchmark times: the tuner's tile shape, the graph loop, six applications of
 T per staged tile and sweep.  Every expected value comes from the FP64 oracle
 on the same seeded inputs:
 
