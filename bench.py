@@ -98,6 +98,18 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
+# Applications of T per staged tile and sweep the library uses when the
+# caller passes none (hjb_solve_opts.local_iters <= 0), unless HJB_LOCAL_ITERS
+# overrides it.
+LIBRARY_LOCAL_ITERS = 6
+
+
+def run_local_iters():
+    e = os.environ.get("HJB_LOCAL_ITERS")
+    v = int(e) if e else LIBRARY_LOCAL_ITERS
+    return min(max(v, 1), 16)
+
+
 def sweep_traffic(path=TRAFFIC_PROFILE, rows=None):
     """DRAM bytes per sweep launch from a committed ncu summary (for the 2D
     tile shape with `rows` rows when the summary lists shapes), or None when
@@ -107,6 +119,8 @@ def sweep_traffic(path=TRAFFIC_PROFILE, rows=None):
             kv = dict(line.strip("- \n").split(": ", 1) for line in f
                       if line.startswith("- ") and ": " in line)
         if kv.get("sources_sha256") != kernel_sources_sha256():
+            return None
+        if "local_iters" in kv and int(kv["local_iters"]) != run_local_iters():
             return None
         sfx = "_rows%d" % rows if rows and ("traffic_bytes_per_launch_rows%d" % rows) in kv else ""
         out = {"bytes_per_launch": float(kv["traffic_bytes_per_launch" + sfx])}

@@ -181,7 +181,7 @@ int hjb_destroy(hjb_problem *p);
  *  sweeps_per_check: sweeps between two convergence tests in the device loop
  *       (<= 0: library default).
  *  local_iters: applications of T to each staged tile per sweep (<= 0:
- *       default 6, 16 at most).  The first reads the previous sweep's
+ *       default 6, 4 for a game, 16 at most).  The first reads the previous sweep's
  *       values; each further one reads the tile's own latest values with the
  *       halo held (block Gauss-Seidel inside the tile), and a tile stops early
  *       once an application changes none of its nodes.  Every ordering of the

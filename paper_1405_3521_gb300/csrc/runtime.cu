@@ -556,13 +556,15 @@ int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows) {
     return HJB_OK;
 }
 
-// Applications of T per tile and sweep in the 2D kernels: opts->local_iters
-// when positive, else HJB_LOCAL_ITERS, else 6 (clamped to 1..16).
-int local_iters(const hjb_solve_opts *o) {
-    static const int dflt = [] {
+// Applications of T per tile and sweep: opts->local_iters when positive,
+// else HJB_LOCAL_ITERS, else 6, or 4 for a game, whose 8-16x costlier
+// applications make a longer stay on a tile slower (clamped to 1..16).
+int local_iters(const hjb_solve_opts *o, const hjb_problem *P) {
+    static const int env = [] {
         const char *e = std::getenv("HJB_LOCAL_ITERS");
-        return e ? std::atoi(e) : 6;
+        return e ? std::atoi(e) : 0;
     }();
+    const int dflt = env > 0 ? env : ((P && P->nb > 1) ? 4 : 6);
     const int v = (o && o->local_iters > 0) ? o->local_iters : dflt;
     return v < 1 ? 1 : (v > 16 ? 16 : v);
 }
@@ -1038,7 +1040,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_ou
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
                              8 / rows, loop_mode()};
     const hjbk::ControlTable ctrl = control_table(P);
-    TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, local_iters(opts)));
+    TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, local_iters(opts, P)));
     hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
                          static_cast<float *>(out.dev()), wform, c_over, st);
     CK(cudaEventRecord(R.ev1, st));
@@ -1160,7 +1162,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
                              8 / rows, loop_mode()};
-    TRY(run_loop(R, key, 8, control_table(P), st, local_iters(nullptr)));
+    TRY(run_loop(R, key, 8, control_table(P), st, local_iters(nullptr, P)));
     // threshold of eq. (rep)
     double delta = ra->delta;
     TRY(P->scratch_u64.ensure(64));
@@ -1306,7 +1308,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     // sub-domains with equal node sets are solved once (V_k depends on the
     // node set alone: its targets are the target nodes inside it)
     R.diff = diff;
-    const int lrc = run_loop(R, key, sweeps_per_body(opts), control_table(P), st, local_iters(opts));
+    const int lrc = run_loop(R, key, sweeps_per_body(opts), control_table(P), st, local_iters(opts, P));
     R.diff = nullptr;
     TRY(lrc);
     hjbh::launch_assemble(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, fine, mask,
@@ -1434,7 +1436,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
                              nullptr, st);
     const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P0), halo, rows,
                              8 / rows, loop_mode()};
-    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st, local_iters(opts)));
+    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st, local_iters(opts, P0)));
     for (int i = 0; i < count; ++i) {
         TRY(outs[i].init(v_out[i], problems[i]->N * sizeof(float), &problems[i]->out_stage));
         hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), i,
@@ -1917,7 +1919,7 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     args.nslots = 1;
     args.use_handle = 0;
     args.stall_tol = 8.0f * 1.1920929e-7f;
-    args.local_iters = local_iters(opts);
+    args.local_iters = local_iters(opts, nullptr);
     args.dyn_queue = queue_mode();
     args.ctrl = ctrl;
     hjbh::launch_queue_init(d_slot, 1, tiles, d_ctl, args.qlist[0], args.qflag[0], args.qflag[1], st);
