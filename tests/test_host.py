@@ -171,3 +171,37 @@ def test_bench_aggregation_two_ranks():
     for rank, ms, total in res:
         assert ms == 11.0  # the slowest rank sets the time
         assert abs(total - 2000.0 / 11.0e-3) < 1e-6 * total  # units of all ranks / that time
+
+
+def test_bench_traffic_lookup(tmp_path, monkeypatch):
+    """roofline.traffic comes from a committed ncu summary only for the kernel
+    sources, tile shape and applications per tile the summary was taken on."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.delenv("HJB_LOCAL_ITERS", raising=False)
+    h = bench.kernel_sources_sha256()
+    f = tmp_path / "t.md"
+    f.write_text("- traffic_bytes_per_launch_rows8: 100\n- node_updates_per_launch_rows8: 10\n"
+                 "- traffic_bytes_per_launch_rows4: 200\n- node_updates_per_launch_rows4: 20\n"
+                 "- traffic_bytes_per_launch: 5\n- local_iters: %d\n- sources_sha256: %s\n"
+                 % (bench.LIBRARY_LOCAL_ITERS, h))
+    assert bench.sweep_traffic(str(f), rows=4) == {"bytes_per_launch": 200.0,
+                                                   "node_updates_per_launch": 20.0}
+    assert bench.sweep_traffic(str(f), rows=8)["bytes_per_launch"] == 100.0
+    assert bench.sweep_traffic(str(f), rows=2) == {"bytes_per_launch": 5.0}
+    monkeypatch.setenv("HJB_LOCAL_ITERS", str(bench.LIBRARY_LOCAL_ITERS + 1))
+    assert bench.sweep_traffic(str(f), rows=4) is None
+    monkeypatch.delenv("HJB_LOCAL_ITERS")
+    f.write_text(f.read_text().replace(h, "0" * 64))
+    assert bench.sweep_traffic(str(f), rows=4) is None
+    # the committed summaries parse and match the current sources
+    assert bench.sweep_traffic(rows=4) is not None
+
+
+def test_library_default_applications_match_bench():
+    """bench.py's copy of the library's default applications per tile (used
+    to match ncu summaries to the timed configuration) is the runtime's."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "paper_1405_3521_gb300", "csrc", "runtime.cu")).read()
+    assert "? 4 : %d)" % bench.LIBRARY_LOCAL_ITERS in src

@@ -686,6 +686,36 @@ def test_nesting_in_threshold(orc):
     assert np.allclose(vmin, Vaux.min(0))
 
 
+def test_exact_sets_inside_reconstructed_sets(orc):
+    """Sec. 3 (the reconstruction contains the set it approximates): the set
+    Sigma_k where target k alone gives the value (V_k = V within 1e-9, from
+    full solves on the fine grid) lies inside the projected RA set of the
+    coarse grid four times coarser, once the threshold is 2 dx_K (the rule
+    2 M dx_K with the distance's gradient bound M = 1).  The reconstructed
+    sets are not trivial (1.14 N in total), and half that threshold already
+    misses a few nodes, so the check has teeth."""
+    n, stride = 201, 4
+    d = S.c1(n=n, A=32)
+    p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"])
+    nt = orc.max_threads()
+    V, _, _ = orc.solve(p, tol=1e-11, nthreads=nt)
+    m = d["ntargets"]
+    sig = np.array([np.abs(orc.solve(p, tol=1e-11, only_target=k + 1, nthreads=nt)[0] - V) <= 1e-9
+                    for k in range(m)])
+    assert sig.any(axis=0).mean() > 0.99
+    dxk = stride * 2.0 / (n - 1)
+    missed = {}
+    for delta in (dxk, 2 * dxk):
+        _, lab, _ = orc.ra(p, (stride, stride), delta, tol=1e-11, nthreads=nt)
+        fine = orc.project(p, (stride, stride), lab)
+        sbar = np.array([((fine >> k) & 1) == 1 for k in range(m)])
+        missed[delta] = int((sig & ~sbar).sum())
+        total = sbar.sum() / V.size
+    assert missed[2 * dxk] == 0
+    assert missed[dxk] > 0
+    assert total < 1.2
+
+
 # --------------------------------------------------------------------------
 # Defining property of independent sub-domains (Def. and Prop. 2.1; Prop. 4.1)
 
