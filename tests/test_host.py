@@ -205,3 +205,20 @@ def test_library_default_applications_match_bench():
     import bench
     src = open(os.path.join(ROOT, "paper_1405_3521_gb300", "csrc", "runtime.cu")).read()
     assert "? 4 : %d)" % bench.LIBRARY_LOCAL_ITERS in src
+
+
+def test_missing_library_fails_loudly():
+    """With no built library the package raises instead of computing
+    anything another way (there is no CPU path)."""
+    code = ("import paper_1405_3521_gb300 as h\n"
+            "try:\n"
+            "    h._capi.lib()\n"
+            "except ImportError as e:\n"
+            "    print('raised:', e)\n"
+            "else:\n"
+            "    print('loaded')\n")
+    env = dict(os.environ, HJB_LIBRARY=os.path.join(ROOT, "_no_such_dir", "libhjb.so"))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.startswith("raised: libhjb.so is not built"), r.stdout
