@@ -675,6 +675,53 @@ def test_table1_shape(orc):
             assert abs(f - paper) < 0.05, (n, f, paper)
 
 
+@pytest.mark.parametrize("case", ["scale_current_cost", "dubins"])
+def test_ra_auxiliary_solves_are_the_coarse_problems(orc, case):
+    """RA step 1 (Sec. 3): auxiliary problem k lives on the grid of every
+    stride-th node, with every node field sampled there, time step
+    h_K = stride h, and only target component k as its target.  Each
+    auxiliary solution equals a direct solve of that coarse problem, built
+    here by slicing the fields: per-axis factors that differ on the two axes,
+    a current and a cost field, lambda != 1; and the Dubins car with a
+    periodic heading (every second heading kept)."""
+    g = np.random.default_rng(12)
+    if case == "dubins":
+        d = S.c3(nxy=33, nth=16, ntargets=3, stride=(4, 4, 2))
+        stride = (4, 4, 2)
+        p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"], dyn=1,
+                        periodic=d["periodic"], ntargets=3)
+        lab = np.asarray(d["labels"])
+        labc = lab[::2, ::4, ::4]
+        q = orc.Problem(labc.shape[::-1], d["lo"], d["hi"], d["controls"], labc, d["h"] * 4,
+                        dyn=1, periodic=d["periodic"], ntargets=3)
+    else:
+        n, m = 49, 3
+        X, Y = S.mesh2(n, n)
+        lab = S.disk_labels(X, Y, S.disk_centers(g, m, 0.15), 0.15)
+        D = np.stack([g.uniform(0.5, 1.5, X.shape), g.uniform(0.2, 0.8, X.shape)], -1)
+        cur = S.current_field(g, X, Y, cmax=0.3)
+        cost = g.uniform(0.5, 2.0, X.shape)
+        h = 2.0 / (n - 1)
+        stride = (4, 4)
+        ctr = S.circle_controls(16)
+        p = orc.Problem((n, n), (-1, -1), (1, 1), ctr, lab, h, lam=0.7, scale=D, current=cur,
+                        cost=cost, v_out=2.0, ntargets=m)
+        sl = (slice(None, None, 4), slice(None, None, 4))
+        labc = lab[sl]
+        q = orc.Problem(labc.shape[::-1], (-1, -1), (1, 1), ctr, labc, h * 4, lam=0.7,
+                        scale=D[sl], current=cur[sl], cost=cost[sl], v_out=2.0, ntargets=m)
+    Vaux, _, _ = orc.ra(p, stride, 0.1, tol=1e-13)
+    for k in range(Vaux.shape[0]):
+        Vk, _, _ = orc.solve(q, tol=1e-13, only_target=k + 1)
+        assert np.abs(Vaux[k] - Vk).max() < 1e-11
+    # a swap of the two factors changes the coarse problem
+    if case != "dubins":
+        qs = orc.Problem(labc.shape[::-1], (-1, -1), (1, 1), ctr, labc, h * 4, lam=0.7,
+                         scale=D[sl][..., ::-1], current=cur[sl], cost=cost[sl], v_out=2.0,
+                         ntargets=m)
+        assert np.abs(Vaux[0] - orc.solve(qs, tol=1e-13, only_target=1)[0]).max() > 1e-3
+
+
 def test_nesting_in_threshold(orc):
     d = S.c1(n=41)
     p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"])
