@@ -1024,14 +1024,17 @@ def _q1_gradient(shape, spacing, idx, off):
     return out
 
 
-def test_adjoint_tangent_linear_dot_product(orc):
+@pytest.mark.parametrize("variant", ["speed", "current_cost", "implicit"])
+def test_adjoint_tangent_linear_dot_product(orc, variant):
     """The adjoint against the tangent-linear model (exact linear solves, no
     oracle code): with the optimal policy frozen, a perturbation d of
     theta = log s moves V by dV solving (I - beta P) dV = beta c d, where c_i
     is the derivative of I[V] at the foot along h s_i a_pi(i).  The loss
     derivative g . dV must equal (dL/dtheta) . d to rounding, for several
     random directions; and dV agrees with central differences of full oracle
-    solves along a smooth direction."""
+    solves along a smooth direction.  Variants: speed only; with a current,
+    a cost field and lambda = 0.7 (the foot moves with the current, the
+    derivative does not); with the implicit step weights 1/(1 + lambda h)."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spl
     n, A = 21, 16
@@ -1040,9 +1043,18 @@ def test_adjoint_tangent_linear_dot_product(orc):
     ctr = S.circle_controls(A)
     h = dx = 2.0 / (n - 1)
     s = np.exp(th.reshape(-1))
+    g0 = np.random.default_rng(23)
+    cur = S.current_field(g0, X, Y, cmax=0.3).reshape(-1, 2) if variant == "current_cost" \
+        else np.zeros((n * n, 2))
+    cost = g0.uniform(0.5, 2.0, n * n) if variant == "current_cost" else np.ones(n * n)
+    lam_ = 0.7 if variant == "current_cost" else 1.0
+    implicit = variant == "implicit"
+    kw = dict(lam=lam_, weights=int(implicit))
+    if variant == "current_cost":
+        kw.update(current=cur, cost=cost)
 
     def prob(theta):
-        return orc.Problem((n, n), (-1, -1), (1, 1), ctr, lab, h, speed=np.exp(theta))
+        return orc.Problem((n, n), (-1, -1), (1, 1), ctr, lab, h, speed=np.exp(theta), **kw)
 
     p = prob(th.reshape(-1))
     V, _, _ = orc.solve(p, tol=1e-15, max_iters=200000)
@@ -1050,9 +1062,9 @@ def test_adjoint_tangent_linear_dot_product(orc):
     _, gV = orc.points(p, V, pts)
     lam, _, _ = orc.adjoint(p, pol, gV, tol=1e-15)
     gt, _ = orc.grad(p, V, pol, lam)
-    feet = [[h * s[i] * ctr[j] for j in range(A)] for i in range(n * n)]
-    R, b, free, beta = _transitions((n, n), (dx, dx), (0, 0), lab, feet, np.ones(n * n), 1.0, h,
-                                    1.0)
+    feet = [[h * (s[i] * ctr[j] + cur[i]) for j in range(A)] for i in range(n * n)]
+    R, b, free, beta = _transitions((n, n), (dx, dx), (0, 0), lab, feet, cost, lam_, h,
+                                    1.0, implicit=implicit)
     F = len(free)
     ar = np.arange(F)
     # the oracle's policy is optimal for the independently built problem
