@@ -59,6 +59,12 @@ extern "C" {
 
 #define HJB_MAX_CONTROLS 128
 #define HJB_MAX_TARGETS 32
+/* Problems per hjb_solve_batch call, and tiles per grid: the sweep's work
+ * queue addresses a tile of a problem in one 31-bit word (9 bits of problem,
+ * 22 bits of tile).  A tile is 32 x 2 nodes at the smallest 2D shape and
+ * 32 x 8 x 4 in 3D, so a 2D grid holds up to about 2.7e8 nodes. */
+#define HJB_MAX_BATCH 512
+#define HJB_MAX_TILES (1 << 22)
 
 /* Structured grid of Sec. 3 (the "regular mesh" case).  Non-periodic
  * dimension d has n[d] >= 2 nodes x = lo + i (hi-lo)/(n-1); a periodic
@@ -160,7 +166,8 @@ typedef struct hjb_problem hjb_problem;
  * pointers, copies the control set, and sizes (but does not yet allocate)
  * the workspaces.  On success *out receives the handle.
  * Errors: HJB_ERR_INVALID_ARG (bad sizes, NULL required pointers, controls
- * whose feet move more than 3 cells per step), HJB_ERR_UNSUPPORTED. */
+ * whose feet move more than 3 cells per step), HJB_ERR_UNSUPPORTED (among
+ * others: a grid of more than HJB_MAX_TILES tiles). */
 int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *cost,
                const hjb_discount *disc, const hjb_controls *controls,
                const hjb_target *target, hjb_problem **out);
@@ -262,7 +269,8 @@ int hjb_solve_decomposed(hjb_problem *p, const uint32_t *fine_mask, const hjb_so
 
 /* Many independent problems (uneven grids allowed) in one persistent,
  * graph-captured launch with per-problem convergence.  All problems must use
- * the same dynamics kind, control set size and cost form.
+ * the same dynamics kind, control set size and cost form; count <=
+ * HJB_MAX_BATCH (HJB_ERR_INVALID_ARG otherwise).
  *  v_out[i] [N_i] receives problem i's V; per_problem (optional) [count]. */
 int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opts *opts,
                     float *const *v_out, hjb_stats *per_problem, void *stream);

@@ -874,6 +874,18 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
     if (grid->n[0] > 65536 || grid->n[1] > 65536 || (grid->ndim > 2 && grid->n[2] > 65536))
         return fail(HJB_ERR_INVALID_ARG, "grid too large");
     if (N > (1LL << 31)) return fail(HJB_ERR_INVALID_ARG, "more than 2^31 nodes");
+    {
+        // tiles at the smallest shape the sweep may run (32 x 2 in 2D, 32 x 8 x 4 in 3D):
+        // a work-queue entry holds a tile index in 22 bits
+        const long long tx = (grid->n[0] + hjbk::TX - 1) / hjbk::TX;
+        const long long tiles = grid->ndim == 2
+                                    ? tx * ((grid->n[1] + 1) / 2)
+                                    : tx * ((grid->n[1] + hjbk::TY - 1) / hjbk::TY) *
+                                          ((grid->n[2] + hjbk::TZ - 1) / hjbk::TZ);
+        if (tiles > HJB_MAX_TILES)
+            return fail(HJB_ERR_UNSUPPORTED, "the grid has %lld tiles, more than the %d a problem "
+                        "may hold", tiles, HJB_MAX_TILES);
+    }
     if (dyn->kind == HJB_DYN_SPEED_CURRENT) {
         if (grid->ndim != 2) return fail(HJB_ERR_UNSUPPORTED, "speed/current dynamics are 2D");
         if (grid->periodic[0] || grid->periodic[1])
@@ -1475,8 +1487,8 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
                     float *const *v_out, hjb_stats *per_problem, void *stream) {
     g_err.clear();
     if (!problems || count < 1 || !v_out) return fail(HJB_ERR_INVALID_ARG, "empty batch");
-    if (count > hjbk::MAX_SLOTS)
-        return fail(HJB_ERR_INVALID_ARG, "at most %d problems per batch", hjbk::MAX_SLOTS);
+    if (count > HJB_MAX_BATCH)
+        return fail(HJB_ERR_INVALID_ARG, "at most %d problems per batch", HJB_MAX_BATCH);
     TRY(check_opts(opts));
     if (!problems[0]) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
     cudaStream_t st = static_cast<cudaStream_t>(stream);

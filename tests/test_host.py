@@ -222,3 +222,45 @@ def test_missing_library_fails_loudly():
                        text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.startswith("raised: libhjb.so is not built"), r.stdout
+
+
+def test_work_queue_limits_are_enforced_on_the_host(libpath):
+    """A work-queue entry holds a problem index in 9 bits and a tile index in
+    22: a batch of more than 512 problems, or a grid of more than 2^22 tiles
+    of 32 x 2 nodes, is refused before anything reaches the GPU."""
+    from paper_1405_3521_gb300 import _capi
+    L = _capi.lib()
+    count = 513
+    probs = (C.c_void_p * count)()
+    outs = (C.c_void_p * count)()
+    rc = L.hjb_solve_batch(probs, count, None, outs, None, None)
+    assert rc == _capi.HJB_ERR_INVALID_ARG
+    assert b"at most 512 problems" in L.hjb_last_error()
+    lab = np.zeros(16, dtype=np.uint8)
+    A = np.asarray(S.circle_controls(4), np.float32)
+
+    def create(n0, n1):
+        g = _capi.hjb_grid()
+        g.ndim = 2
+        g.n[0], g.n[1] = n0, n1
+        g.lo[0] = g.lo[1] = -1.0
+        g.hi[0] = g.hi[1] = 1.0
+        dy, co, di, ct, tg = (_capi.hjb_dynamics(), _capi.hjb_cost(), _capi.hjb_discount(),
+                              _capi.hjb_controls(), _capi.hjb_target())
+        co.l_const = 1.0
+        di.h, di.lam = 1e-4, 1.0
+        ct.count, ct.dim = 4, 2
+        ct.a = A.ctypes.data
+        tg.labels = lab.ctypes.data
+        tg.n_targets, tg.value_out = 1, 1.0
+        h = C.c_void_p()
+        rc = L.hjb_create(C.byref(g), C.byref(dy), C.byref(co), C.byref(di), C.byref(ct),
+                          C.byref(tg), C.byref(h))
+        if rc == 0:
+            L.hjb_destroy(h)
+        return rc
+
+    # 16384 x 16384 nodes: exactly 2^22 tiles of 32 x 2; one more row of tiles is refused
+    assert create(16384, 16384) == 0
+    assert create(16384, 16386) == _capi.HJB_ERR_UNSUPPORTED
+    assert b"tiles" in L.hjb_last_error()
