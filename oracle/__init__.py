@@ -76,7 +76,7 @@ def _lib_handle():
             lib.ohjb_ra.argtypes = [P, vp, d, d, d, i, vp, vp, i]
             lib.ohjb_ra.restype = C.c_longlong
             lib.ohjb_project.argtypes = [P, vp, vp, vp]
-            lib.ohjb_isa.argtypes = [P, vp, d, i, i, vp, vp, vp, i]
+            lib.ohjb_isa.argtypes = [P, vp, d, i, i, vp, vp, vp, i, i]
             lib.ohjb_isa.restype = C.c_longlong
             lib.ohjb_policy.argtypes = [P, vp, vp, i]
             lib.ohjb_policy.restype = d
@@ -254,14 +254,17 @@ def project(p: Problem, stride, coarse_labels):
 
 
 def isa(p: Problem, fine_mask, tol=1e-12, max_iters=1_000_000, gs=False, keep_vk=False,
-        nthreads=1):
-    """ISA steps 3-4 (Sec. 4).  Returns (Vbar, uncovered, iters[m], Vk or None)."""
+        nthreads=1, own_targets=False):
+    """ISA steps 3-4 (Sec. 4).  Returns (Vbar, uncovered, iters[m], Vk or None).
+    own_targets: sub-problem k keeps only target component k (the target
+    choice of RA step 1, Sec. 3) instead of every target node inside it."""
     fm = np.ascontiguousarray(fine_mask, dtype=np.uint32).reshape(-1)
     Vbar = np.empty(p.N)
     Vk = np.empty((p.ntargets, p.N)) if keep_vk else None
     its = np.zeros(p.ntargets, dtype=np.int32)
     unc = _lib_handle().ohjb_isa(p._ref(), fm.ctypes.data, float(tol), int(max_iters), int(gs),
-                                 _ptr(Vk), Vbar.ctypes.data, its.ctypes.data, int(nthreads))
+                                 _ptr(Vk), Vbar.ctypes.data, its.ctypes.data, int(nthreads),
+                                 int(bool(own_targets)))
     return Vbar, int(unc), its, Vk
 
 

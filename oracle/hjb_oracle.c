@@ -607,23 +607,27 @@ void ohjb_project(const ohjb_problem *p, const int stride[3], const uint32_t *co
 }
 
 /* ISA steps 3-4 (Sec. 4): restricted solves on every sub-domain given by
- * fine_mask (reading R3), then Vbar(j) = min{ V_k(j) : j in Sigma_k }.
+ * fine_mask, then Vbar(j) = min{ V_k(j) : j in Sigma_k }.  The targets of
+ * sub-problem k are every target node inside it (own_targets = 0: the
+ * operator of Sec. 4 step 3 as written, reading R3), or only component k
+ * (own_targets = 1: the target choice of RA step 1, dG := X_k, in Sec. 3).
  * Vk (optional) receives [m][N].  Returns the number of uncovered nodes
  * (nodes in no sub-domain; they receive v_out). */
 long long ohjb_isa(const ohjb_problem *p, const uint32_t *fine_mask, double tol,
                    int max_iters, int use_gs, double *Vk, double *Vbar,
-                   int *iters, int nthreads) {
+                   int *iters, int nthreads, int own_targets) {
     long long N = node_count(p);
     int m = p->ntargets;
     double *tmp = (double *)malloc(sizeof(double) * N);
     for (long long i = 0; i < N; ++i) Vbar[i] = INFINITY;
     for (int k = 0; k < m; ++k) {
-        ohjb_initial(p, tmp, fine_mask, k, 0);
+        const int only = own_targets ? k + 1 : 0;
+        ohjb_initial(p, tmp, fine_mask, k, only);
         int it;
         if (use_gs)
-            it = ohjb_solve_gs(p, tol, max_iters, tmp, fine_mask, k, 0, NULL);
+            it = ohjb_solve_gs(p, tol, max_iters, tmp, fine_mask, k, only, NULL);
         else
-            it = ohjb_solve(p, tol, max_iters, tmp, fine_mask, k, 0, nthreads, NULL);
+            it = ohjb_solve(p, tol, max_iters, tmp, fine_mask, k, only, nthreads, NULL);
         if (iters) iters[k] = it;
         if (Vk) memcpy(Vk + (long long)k * N, tmp, sizeof(double) * N);
         for (long long i = 0; i < N; ++i)

@@ -307,11 +307,12 @@ def test_brute_force_dubins_periodic(orc):
 # so it pins the value iteration at sizes brute force cannot reach.
 
 def _transitions(shape, spacing, periodic, target, feet, cost, lam, h, v_out, implicit=False,
-                 p1=False):
+                 p1=False, ghost=None):
     """(R, b, free, beta): R sparse [F * A, F], row k * A + j the interpolation
     weights of the foot of free node k under control j on the free nodes
     (target nodes hold 0); b [F, A] the running cost plus beta v_out for a
-    foot outside the box."""
+    foot outside the box, and beta w v_out for each stencil weight w on a
+    ghost node (ghost: bool [N], nodes outside a restricted problem)."""
     import scipy.sparse as sp
     N = int(np.prod(shape))
     if implicit:
@@ -319,7 +320,8 @@ def _transitions(shape, spacing, periodic, target, feet, cost, lam, h, v_out, im
     else:
         beta = math.exp(-lam * h)
         gam = (1 - beta) / lam
-    free = np.nonzero(np.asarray(target) == 0)[0]
+    gh = np.zeros(N, dtype=bool) if ghost is None else np.asarray(ghost, dtype=bool)
+    free = np.nonzero((np.asarray(target) == 0) & ~gh)[0]
     pos = np.full(N, -1)
     pos[free] = np.arange(len(free))
     A = len(feet[free[0]])
@@ -337,7 +339,9 @@ def _transitions(shape, spacing, periodic, target, feet, cost, lam, h, v_out, im
                 b[k, j] += beta * v_out
                 continue
             for flat, w in st:
-                if pos[flat] >= 0 and w != 0.0:
+                if gh[flat]:
+                    b[k, j] += beta * w * v_out
+                elif pos[flat] >= 0 and w != 0.0:
                     rows.append(k * A + j)
                     cols.append(pos[flat])
                     vals.append(w)
@@ -398,6 +402,48 @@ def test_policy_iteration_zermelo(orc, variant):
     V, _, _ = orc.solve(p, tol=1e-14, max_iters=1_000_000)
     assert np.abs(V[free] - Vh).max() < 1e-11
     assert np.abs(V[lab != 0]).max() == 0.0
+
+
+@pytest.mark.parametrize("own", [False, True])
+def test_policy_iteration_restricted_subproblems(orc, own):
+    """ISA step 3 (Sec. 4) on the oracle's own decomposition of a 33^2 problem
+    with three targets (threshold 0.5, so that sub-domains reach into other
+    components): each restricted solve equals Howard's exact solution
+    of the problem on that sub-domain (nodes outside it are ghosts carrying
+    value_out), with every target node inside the sub-domain as a target
+    (the operator of Sec. 4 as written), or only target component k (the
+    target choice of RA step 1, Sec. 3)."""
+    n, A = 33, 16
+    s, cur, cost, lab = _zermelo_fields(n, A, 22)
+    ctr = S.circle_controls(A)
+    h = dx = 2.0 / (n - 1)
+    p = orc.Problem((n, n), (-1, -1), (1, 1), ctr, lab, h, lam=0.8, speed=s, current=cur,
+                    cost=cost, v_out=2.5)
+    _, lab_c, _ = orc.ra(p, (4, 4), 0.5, tol=1e-13)
+    fine = orc.project(p, (4, 4), lab_c)
+    Vbar, unc, _, Vk = orc.isa(p, fine, tol=1e-14, keep_vk=True, own_targets=own)
+    feet = [[h * (s[i] * ctr[j] + cur[i]) for j in range(A)] for i in range(n * n)]
+    m = int(lab.max())
+    assert m == 3
+    for k in range(m):
+        inside = ((fine >> k) & 1) == 1
+        assert 0 < inside.sum() < n * n
+        tk = np.where(inside & ((lab == k + 1) if own else (lab != 0)), lab, 0)
+        R, b, free, beta = _transitions((n, n), (dx, dx), (0, 0), tk, feet, cost, 0.8, h, 2.5,
+                                        ghost=~inside)
+        Vh, _ = _howard(R, b, beta)
+        assert np.abs(Vk[k][free] - Vh).max() < 1e-11
+    # the assembly: the minimum over the sub-domains holding a node
+    ref = np.where(fine != 0, np.min(np.where(((fine[None, :] >> np.arange(m)[:, None]) & 1) == 1,
+                                              Vk, np.inf), axis=0), 2.5)
+    assert np.array_equal(Vbar, ref)
+    # at this threshold sub-domains 1 and 3 hold nodes of other components,
+    # so the two choices of targets are different problems
+    other = [int(np.sum(((fine >> k) & 1)[(lab != 0) & (lab != k + 1)])) for k in range(m)]
+    assert max(other) > 0
+    if own:
+        _, _, _, Vk3 = orc.isa(p, fine, tol=1e-14, keep_vk=True)
+        assert np.abs(Vk - Vk3).max() > 0.1
 
 
 def test_policy_iteration_dubins(orc):
