@@ -194,7 +194,15 @@ int hjb_destroy(hjb_problem *p);
  *       once an application changes none of its nodes.  Every ordering of the
  *       updates has the same fixed point, and a sweep is still a
  *       beta-contraction, so tol keeps its meaning.  1 is plain value
- *       iteration (Jacobi). */
+ *       iteration (Jacobi).
+ *  subdomain_targets (hjb_solve_decomposed only): the targets of sub-problem
+ *       k.  HJB_SUBDOMAIN_TARGETS_ALL (0, default): every target node inside
+ *       the sub-domain (the operator of Sec. 4 step 3 as written); equal
+ *       sub-domains are then solved once.  HJB_SUBDOMAIN_TARGETS_OWN (1):
+ *       only component k, the target choice of the auxiliary problems of RA
+ *       step 1 (Sec. 3); nodes of other components inside it are free. */
+#define HJB_SUBDOMAIN_TARGETS_ALL 0
+#define HJB_SUBDOMAIN_TARGETS_OWN 1
 typedef struct {
     double tol;
     int max_iters;
@@ -202,6 +210,7 @@ typedef struct {
     const float *v_init;
     int sweeps_per_check;
     int local_iters;
+    int subdomain_targets;
 } hjb_solve_opts;
 
 /* Statistics of one solve (per problem or per sub-domain). */

@@ -26,8 +26,8 @@ import numpy as np
 
 from . import _capi
 from ._capi import (HJB_DYN_DUBINS, HJB_DYN_SPEED_CURRENT, HJB_WEIGHTS_EXP, HJB_WEIGHTS_IMPLICIT,
-                    HJB_INTERP_Q1, HJB_INTERP_P1,
-                    HJBError, NotConverged, check,
+                    HJB_INTERP_Q1, HJB_INTERP_P1, HJB_SUBDOMAIN_TARGETS_ALL,
+                    HJB_SUBDOMAIN_TARGETS_OWN, HJBError, NotConverged, check,
                     hjb_ra_opts, hjb_solve_opts, hjb_stats)
 
 __all__ = ["Problem", "solve", "subdomains", "solve_decomposed", "solve_batch", "backward",
@@ -84,7 +84,8 @@ def _stream(stream):
     return None
 
 
-def _opts(tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_per_check=0, local_iters=0):
+def _opts(tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_per_check=0, local_iters=0,
+          subdomain_targets=0):
     o = hjb_solve_opts()
     o.tol = float(tol)
     o.max_iters = int(max_iters)
@@ -92,6 +93,7 @@ def _opts(tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_per_check=0, 
     o.v_init = _ptr(v_init)
     o.sweeps_per_check = int(sweeps_per_check)
     o.local_iters = int(local_iters)
+    o.subdomain_targets = int(subdomain_targets)
     return o
 
 
@@ -257,12 +259,16 @@ def subdomains(p: Problem, stride, delta=-1.0, C_=0.0, M=-1.0, q=1.0, h_coarse=0
 
 
 def solve_decomposed(p: Problem, fine_mask, tol=0.0, max_iters=0, use_w_form=-1,
-                     sweeps_per_check=0, out=None, stream=None, local_iters=0):
-    """ISA steps 3-4 (Sec. 4).  Returns (Vbar, per-sub-domain stats, total stats)."""
+                     sweeps_per_check=0, out=None, stream=None, local_iters=0,
+                     subdomain_targets=0):
+    """ISA steps 3-4 (Sec. 4).  Returns (Vbar, per-sub-domain stats, total stats).
+    subdomain_targets: 0 = every target node inside a sub-domain is its
+    target (Sec. 4 step 3 as written), 1 = only its own component (the
+    target choice of RA step 1, Sec. 3)."""
     out = p.empty(p.N) if out is None else out
     per = (hjb_stats * p.n_targets)()
     tot = hjb_stats()
-    o = _opts(tol, max_iters, use_w_form, None, sweeps_per_check, local_iters)
+    o = _opts(tol, max_iters, use_w_form, None, sweeps_per_check, local_iters, subdomain_targets)
     check(_capi.lib().hjb_solve_decomposed(p.handle, _ptr(fine_mask), C.byref(o), _ptr(out), per,
                                            C.byref(tot), _stream(stream)))
     return out, [s.as_dict() for s in per], tot.as_dict()

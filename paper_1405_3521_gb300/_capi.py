@@ -29,6 +29,8 @@ HJB_WEIGHTS_EXP = 0
 HJB_WEIGHTS_IMPLICIT = 1
 HJB_INTERP_Q1 = 0
 HJB_INTERP_P1 = 1
+HJB_SUBDOMAIN_TARGETS_ALL = 0
+HJB_SUBDOMAIN_TARGETS_OWN = 1
 
 EXPORTS = ["hjb_create", "hjb_destroy", "hjb_solve", "hjb_subdomains", "hjb_solve_decomposed",
            "hjb_solve_batch", "hjb_backward", "hjb_point_values", "hjb_solve_static",
@@ -75,7 +77,7 @@ class hjb_target(C.Structure):
 class hjb_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("use_w_form", C.c_int),
                 ("v_init", C.c_void_p), ("sweeps_per_check", C.c_int),
-                ("local_iters", C.c_int)]
+                ("local_iters", C.c_int), ("subdomain_targets", C.c_int)]
 
 
 class hjb_stats(C.Structure):

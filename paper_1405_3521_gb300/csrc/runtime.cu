@@ -793,6 +793,9 @@ hjbh::GridDims dims_of(const hjb_problem *P) {
 
 int check_opts(const hjb_solve_opts *o) {
     if (o && o->max_iters < 0) return fail(HJB_ERR_INVALID_ARG, "max_iters < 0");
+    if (o && o->subdomain_targets != HJB_SUBDOMAIN_TARGETS_ALL &&
+        o->subdomain_targets != HJB_SUBDOMAIN_TARGETS_OWN)
+        return fail(HJB_ERR_INVALID_ARG, "unknown subdomain_targets %d", o->subdomain_targets);
     return HJB_OK;
 }
 
@@ -1296,10 +1299,12 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     TRY(P->tile_bits.ensure((2 * nt + 32) * sizeof(uint32_t)));
     uint32_t *tile_full = P->tile_bits.as<uint32_t>() + nt;
     uint32_t *diff = P->tile_bits.as<uint32_t>() + 2 * nt;
+    const bool own = opts && opts->subdomain_targets == HJB_SUBDOMAIN_TARGETS_OWN;
     for (int k = 0; k < m; ++k) {
         fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows);
         R.slots[k].mask = mask;
         R.slots[k].mask_bit = k;
+        R.slots[k].only_target = own ? k + 1 : 0;
         R.slots[k].tile_bits = P->tile_bits.as<uint32_t>();
         R.slots[k].tile_full = tile_full;
         if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->trig.as<float2>();
@@ -1318,8 +1323,9 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
                              8 / rows, loop_mode()};
     // sub-domains with equal node sets are solved once (V_k depends on the
-    // node set alone: its targets are the target nodes inside it)
-    R.diff = diff;
+    // node set alone when its targets are the target nodes inside it; not so
+    // with one target component per sub-domain)
+    R.diff = own ? nullptr : diff;
     const int lrc = run_loop(R, key, sweeps_per_body(opts), control_table(P), st, local_iters(opts, P));
     R.diff = nullptr;
     TRY(lrc);

@@ -385,6 +385,31 @@ def test_queue_schedules_agree_bitwise(hjb, monkeypatch, loop):
         assert (ia, ua) == (ib, ub)
 
 
+def test_decomposed_own_targets_against_oracle(hjb, orc):
+    """ISA with sub-problems that keep only their own target component (the
+    target choice of RA step 1, Sec. 3, as the alternative reading of Sec. 4
+    step 3): the GPU decomposed solve on the oracle's own decomposition
+    against the oracle's ISA with the same choice, node by node.  At this
+    threshold sub-domains reach into other components, where the two
+    readings differ by more than the tolerance."""
+    d = S.c2(n=129, A=16, ntargets=4, stride=4)
+    nt = orc.max_threads()
+    po = oracle_problem(orc, d)
+    _, lab_o, _ = orc.ra(po, (4, 4), 0.5, tol=1e-11, nthreads=nt)
+    fine = orc.project(po, (4, 4), lab_o)
+    lab = np.asarray(d["labels"]).reshape(-1)
+    assert sum(int(np.sum(((fine >> k) & 1)[(lab != 0) & (lab != k + 1)])) for k in range(4)) > 0
+    Vo, unc, _, _ = orc.isa(po, fine, tol=1e-11, nthreads=nt, own_targets=True)
+    Vr, _, _, _ = orc.isa(po, fine, tol=1e-11, nthreads=nt)
+    assert unc == 0 and np.abs(Vo - Vr).max() > 10 * TOL_V
+    p = gpu_problem(hjb, d)
+    Vb, per, tot = hjb.solve_decomposed(p, fine, subdomain_targets=hjb.HJB_SUBDOMAIN_TARGETS_OWN)
+    assert tot["converged"] == 1
+    assert np.abs(to_np(Vb).astype(np.float64) - Vo).max() < TOL_V
+    Vb3, _, _ = hjb.solve_decomposed(p, fine)
+    assert np.abs(to_np(Vb3).astype(np.float64) - Vr).max() < TOL_V
+
+
 def test_local_iterations_same_fixed_point(hjb, orc):
     """Several applications of T per staged tile (the halo held) reach the
     fixed point of plain value iteration in fewer sweeps: each GPU result is

@@ -264,3 +264,20 @@ def test_work_queue_limits_are_enforced_on_the_host(libpath):
     assert create(16384, 16384) == 0
     assert create(16384, 16386) == _capi.HJB_ERR_UNSUPPORTED
     assert b"tiles" in L.hjb_last_error()
+
+
+def test_solve_options_are_validated_on_the_host(libpath):
+    """An unknown choice of sub-problem targets is refused before anything
+    reaches the GPU."""
+    import paper_1405_3521_gb300 as hjb
+    from paper_1405_3521_gb300 import _capi
+    L = _capi.lib()
+    lab = np.zeros(16, dtype=np.uint8)
+    lab[0] = 1
+    p = hjb.Problem((4, 4), (0, 0), (1, 1), S.circle_controls(4), lab, 0.1, n_targets=1)
+    o = hjb._opts(subdomain_targets=2)
+    out = np.zeros(16, np.float32)
+    rc = L.hjb_solve(p.handle, C.byref(o), out.ctypes.data, None, None)
+    assert rc == _capi.HJB_ERR_INVALID_ARG
+    assert b"subdomain_targets" in L.hjb_last_error()
+    p.close()
