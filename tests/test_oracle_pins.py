@@ -785,10 +785,10 @@ def test_exact_sets_inside_reconstructed_sets(orc):
     full solves on the fine grid) lies inside the projected RA set of the
     coarse grid four times coarser, once the threshold is 2 dx_K (the rule
     2 M dx_K with the distance's gradient bound M = 1).  The reconstructed
-    sets are not trivial (1.14 N in total), and half that threshold already
+    sets are not trivial (1.18 N in total), and half that threshold already
     misses a few nodes, so the check has teeth."""
-    n, stride = 201, 4
-    d = S.c1(n=n, A=32)
+    n, stride = 161, 4
+    d = S.c1(n=n, A=16)
     p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"])
     nt = orc.max_threads()
     V, _, _ = orc.solve(p, tol=1e-11, nthreads=nt)
