@@ -281,3 +281,20 @@ def test_solve_options_are_validated_on_the_host(libpath):
     assert rc == _capi.HJB_ERR_INVALID_ARG
     assert b"subdomain_targets" in L.hjb_last_error()
     p.close()
+
+
+def test_bench_reference_arm_line():
+    """bench.py --impl reference times the oracle on the host cores and prints
+    one JSON line with the contract's keys (no GPU involved)."""
+    import json
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--n", "65"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    for key in ("metric", "unit", "n_gpus", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
