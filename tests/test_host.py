@@ -298,3 +298,44 @@ def test_bench_reference_arm_line():
         assert key in line, key
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_entry_points_validate_arguments_on_the_host(libpath):
+    """Argument errors of the solve, reconstruction, adjoint and point-value
+    entry points are refused before any CUDA call (so also without a GPU)."""
+    import paper_1405_3521_gb300 as hjb
+    from paper_1405_3521_gb300 import _capi
+    L = _capi.lib()
+    n = 9
+    lab = np.zeros(n * n, dtype=np.uint8)
+    lab[0] = 1
+    p = hjb.Problem((n, n), (0, 0), (1, 1), S.circle_controls(4), lab, 0.1, n_targets=1)
+    buf = np.zeros(n * n, np.float32)
+    mask = np.zeros(n * n, np.uint32)
+    ptr = buf.ctypes.data
+
+    def err(rc, code, text):
+        assert rc == code, (rc, L.hjb_last_error())
+        assert text in L.hjb_last_error(), L.hjb_last_error()
+
+    ra = _capi.hjb_ra_opts()
+    for stride, text in (((0, 2), b"< 1"), ((3, 2), b"does not divide")):
+        ra.coarse_stride[0], ra.coarse_stride[1] = stride
+        err(L.hjb_subdomains(p.handle, C.byref(ra), mask.ctypes.data, None, None, None, None),
+            _capi.HJB_ERR_INVALID_ARG, text)
+    err(L.hjb_backward(p.handle, ptr, ptr, 2, None, ptr, None, None),
+        _capi.HJB_ERR_INVALID_ARG, b"wrt")
+    o = hjb._opts(max_iters=-1)
+    err(L.hjb_backward(p.handle, ptr, ptr, 0, C.byref(o), ptr, None, None),
+        _capi.HJB_ERR_INVALID_ARG, b"max_iters")
+    err(L.hjb_solve_decomposed(p.handle, mask.ctypes.data, C.byref(o), ptr, None, None, None),
+        _capi.HJB_ERR_INVALID_ARG, b"max_iters")
+    err(L.hjb_point_values(p.handle, ptr, ptr, -1, None, None, None),
+        _capi.HJB_ERR_INVALID_ARG, b"bad argument")
+    # games have no adjoint
+    g = hjb.Problem((n, n), (0, 0), (1, 1), S.circle_controls(4), lab, 0.1, n_targets=1,
+                    controls_b=0.5 * np.asarray(S.circle_controls(2), np.float32))
+    err(L.hjb_backward(g.handle, ptr, ptr, 0, None, ptr, None, None),
+        _capi.HJB_ERR_UNSUPPORTED, b"without games")
+    g.close()
+    p.close()
