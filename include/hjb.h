@@ -117,7 +117,7 @@ typedef struct {
  *  interp:  HJB_INTERP_Q1 (0): multilinear on the cell;
  *           HJB_INTERP_P1 (1, 2D only): linear on the triangle of the cell's
  *           split along its (0,0)-(1,1) diagonal that holds the foot (the
- *           "linear n-dimensional interpolation" of Sec. 3).  P1 problems
+ *           linear interpolation in n dimensions the scheme of Sec. 3 names).  P1 problems
  *           run the generic-count kernel; hjb_backward and hjb_solve_static
  *           take Q1 only. */
 #define HJB_WEIGHTS_EXP 0

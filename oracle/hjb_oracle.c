@@ -24,7 +24,7 @@
  *       fine node belongs to sub-domain k iff every vertex carrying a
  *       non-zero barycentric weight is labelled k.
  *   R10 ties in the control minimum go to the lowest control index.
- *   P1 (Sec. 3, "linear n-dimensional interpolation"; 2D, interp = 1): the
+ *   P1 (Sec. 3: linear interpolation in n dimensions; 2D, interp = 1): the
  *       linear interpolant on the triangle of the Kuhn split of the cell that
  *       holds the point; Q1 (multilinear) otherwise.  The adjoint functions
  *       assume Q1.
@@ -100,7 +100,7 @@ static long long flatten(const ohjb_problem *p, const int idx[3]) {
 }
 
 /* Q1 (multilinear) interpolation I[V] at grid coordinate g (Sec. 3, the
- * "linear n-dimensional interpolation" of the scheme).  Non-periodic
+ * interpolation the scheme applies at the feet).  Non-periodic
  * coordinates must already lie in [0, n-1]; the cell is floor(g) clamped to
  * [0, n-2].  Periodic coordinates wrap modulo n.  If grad != NULL the
  * gradient with respect to the grid coordinates is written there. */

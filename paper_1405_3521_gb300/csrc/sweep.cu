@@ -169,8 +169,8 @@ __device__ __forceinline__ float q1_pairs(float2 P2, uint32_t K) {
     return fmaf(F2.x, ab.y, E2.x * ab.x);
 }
 
-// P1 variant ("linear n-dimensional interpolation" on the Kuhn triangles of
-// each cell, split along the (0,0)-(1,1) diagonal): the same loads, the
+// P1 variant (the linear interpolant on the Kuhn triangles of each
+// cell, split along the (0,0)-(1,1) diagonal): the same loads, the
 // barycentric weights (1 - t1, t1 - t2, t2) with t1 = max(fx, fy), t2 =
 // min(fx, fy) on the corners (0,0), (1,0) or (0,1), (1,1).  Non-negative
 // weights in fused multiply-adds keep the value monotone in the data.

@@ -28,7 +28,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 # --------------------------------------------------------------------------
-# Q1 interpolation (Sec. 3, linear n-dimensional interpolation)
+# Q1 interpolation (Sec. 3, the interpolation at the feet)
 
 def test_q1_exact_on_bilinear(orc):
     g = np.random.default_rng(1)
@@ -218,8 +218,8 @@ def test_brute_force_implicit_weights(orc):
 
 
 def test_p1_interpolation_closed_forms(orc):
-    """P1 on the Kuhn triangles (Sec. 3, "linear n-dimensional
-    interpolation"): exact on affine data; on the corner data (0, 0, 0, 1) of
+    """P1 on the Kuhn triangles (Sec. 3: linear interpolation in n
+    dimensions): exact on affine data; on the corner data (0, 0, 0, 1) of
     one cell (the function xy) it is min(t_x, t_y), where Q1 gives t_x t_y."""
     g = np.random.default_rng(21)
     lab = np.zeros((3, 4), np.uint8)
