@@ -557,8 +557,9 @@ int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows) {
 }
 
 // Applications of T per tile and sweep: opts->local_iters when positive,
-// else HJB_LOCAL_ITERS, else 6, or 4 for a game, whose 8-16x costlier
-// applications make a longer stay on a tile slower (clamped to 1..16).
+// else HJB_LOCAL_ITERS, else 6, or 4 for a game, whose applications
+// evaluate every (a, b) pair of controls, so that a longer stay on a tile
+// costs more than the sweeps it saves (measured; clamped to 1..16).
 int local_iters(const hjb_solve_opts *o, const hjb_problem *P) {
     static const int env = [] {
         const char *e = std::getenv("HJB_LOCAL_ITERS");
