@@ -339,3 +339,48 @@ def test_entry_points_validate_arguments_on_the_host(libpath):
         _capi.HJB_ERR_UNSUPPORTED, b"without games")
     g.close()
     p.close()
+
+
+C_CLIENT = r"""
+#include "hjb.h"
+#include <stdio.h>
+
+/* A C client of the library: builds a problem descriptor and checks that a
+ * bad grid is refused with a message; never reaches the GPU. */
+int main(void) {
+    hjb_grid grid = {0};
+    hjb_dynamics dyn = {0};
+    hjb_cost cost = {0};
+    hjb_discount disc = {0};
+    hjb_controls controls = {0};
+    hjb_target target = {0};
+    hjb_solve_opts opts = {0};
+    hjb_stats stats = {0};
+    hjb_problem *p = NULL;
+    grid.ndim = 5;
+    opts.subdomain_targets = HJB_SUBDOMAIN_TARGETS_OWN;
+    int rc = hjb_create(&grid, &dyn, &cost, &disc, &controls, &target, &p);
+    printf("%d %s %d %d\n", rc, hjb_last_error(), (int)sizeof opts, stats.tile_rows);
+    return rc == HJB_ERR_INVALID_ARG && p == NULL ? 0 : 1;
+}
+"""
+
+
+@pytest.mark.parametrize("lang", ["c99", "c++17"])
+def test_header_serves_a_c_client(libpath, tmp_path, lang):
+    """include/hjb.h compiles as C99 and as C++ on its own (no CUDA headers),
+    and a C program links against libhjb.so and runs its host-side checks."""
+    cc = "gcc" if lang == "c99" else "g++"
+    if shutil.which(cc) is None:
+        pytest.skip(cc + " not available")
+    src = tmp_path / ("client.c" if lang == "c99" else "client.cpp")
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(libpath)
+    r = subprocess.run([cc, "-std=" + lang, "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", libdir, "-lhjb", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "ndim" in r.stdout
