@@ -165,9 +165,12 @@ typedef struct hjb_problem hjb_problem;
 /* Create a problem.  Validates every descriptor, classifies the field
  * pointers, copies the control set, and sizes (but does not yet allocate)
  * the workspaces.  On success *out receives the handle.
- * Errors: HJB_ERR_INVALID_ARG (bad sizes, NULL required pointers, controls
- * whose feet move more than 3 cells per step), HJB_ERR_UNSUPPORTED (among
- * others: a grid of more than HJB_MAX_TILES tiles). */
+ * Errors: HJB_ERR_INVALID_ARG (bad sizes, NULL required pointers, non-finite
+ * controls or scalars), HJB_ERR_UNSUPPORTED (among others: a grid of more
+ * than HJB_MAX_TILES tiles).  The foot displacement is checked by the solve
+ * calls, which need the fields: HJB_ERR_UNSUPPORTED when a foot moves 4 or
+ * more cells per step (2D), or 2 or more in (x, y) or 1 or more in theta
+ * (Dubins). */
 int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *cost,
                const hjb_discount *disc, const hjb_controls *controls,
                const hjb_target *target, hjb_problem **out);
