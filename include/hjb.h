@@ -66,7 +66,7 @@ extern "C" {
 #define HJB_MAX_BATCH 512
 #define HJB_MAX_TILES (1 << 22)
 
-/* Structured grid of Sec. 3 (the "regular mesh" case).  Non-periodic
+/* Structured grid of Sec. 3 (a uniform lattice in each dimension).  Non-periodic
  * dimension d has n[d] >= 2 nodes x = lo + i (hi-lo)/(n-1); a periodic
  * dimension has n[d] nodes on the period [lo, hi): x = lo + i (hi-lo)/n. */
 typedef struct {
@@ -77,7 +77,7 @@ typedef struct {
     int periodic[3];   /* 0/1 per dimension */
 } hjb_grid;
 
-/* Dynamics f(x, a) of Sec. 2 ("y' = f(y, a)").
+/* Dynamics f(x, a) of Sec. 2: trajectories solve y' = f(y, a).
  *  HJB_DYN_SPEED_CURRENT (2D): f = s(x) a + c(x), a in R^2 a control.
  *     speed: node field s [N] (device or host), NULL means s = 1;
  *     log_speed: node field theta [N] with s = exp(theta) (use one of the two);
@@ -117,9 +117,9 @@ typedef struct {
  *  interp:  HJB_INTERP_Q1 (0): multilinear on the cell;
  *           HJB_INTERP_P1 (1, 2D only): linear on the triangle of the cell's
  *           split along its (0,0)-(1,1) diagonal that holds the foot (the
- *           linear interpolation in n dimensions the scheme of Sec. 3 names).  P1 problems
- *           run the generic-count kernel; hjb_backward and hjb_solve_static
- *           take Q1 only. */
+ *           linear interpolation in n dimensions the scheme of Sec. 3
+ *           names).  P1 problems run the generic-count kernel;
+ *           hjb_backward and hjb_solve_static take Q1 only. */
 #define HJB_WEIGHTS_EXP 0
 #define HJB_WEIGHTS_IMPLICIT 1
 #define HJB_INTERP_Q1 0
@@ -131,8 +131,8 @@ typedef struct {
     int interp;
 } hjb_discount;
 
-/* Discrete control set A (Sec. 3: "a discrete version of the control
- * space"), host memory [count][dim], copied at hjb_create.  dim = 2 for
+/* Discrete control set A (Sec. 3 replaces the control space by a finite
+ * set), host memory [count][dim], copied at hjb_create.  dim = 2 for
  * HJB_DYN_SPEED_CURRENT, 1 for HJB_DYN_DUBINS.  count <= HJB_MAX_CONTROLS.
  * Differential games (Sec. 2, the max over b of the min over a; Example
  * ex4): count_b > 0 gives the second player's set B, host [count_b][dim],
@@ -191,9 +191,9 @@ int hjb_destroy(hjb_problem *p);
  *  sweeps_per_check: sweeps between two convergence tests in the device loop
  *       (<= 0: library default).
  *  local_iters: applications of T to each staged tile per sweep (<= 0:
- *       default 6, 4 for a game, 16 at most).  The first reads the previous sweep's
- *       values; each further one reads the tile's own latest values with the
- *       halo held (block Gauss-Seidel inside the tile), and a tile stops early
+ *       default 6, 4 for a game, 16 at most).  The first reads the previous
+ *       sweep's values; each further one reads the tile's own latest values
+ *       with the halo held (block Gauss-Seidel inside the tile), and a tile stops early
  *       once an application changes none of its nodes.  Every ordering of the
  *       updates has the same fixed point, and a sweep is still a
  *       beta-contraction, so tol keeps its meaning.  1 is plain value
@@ -270,7 +270,9 @@ int hjb_subdomains(hjb_problem *p, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
 
 /* ISA steps 3-4 (Sec. 4): for every k, iterate V_k = T(V_k) restricted to
  * the nodes with bit k-1 of fine_mask (every target node inside is kept as
- * a target, nodes outside are ghosts with value value_out), all sub-domains
+ * a target, or only those of component k with opts->subdomain_targets =
+ * HJB_SUBDOMAIN_TARGETS_OWN; nodes outside are ghosts with value
+ * value_out), all sub-domains
  * in one persistent launch with per-sub-domain convergence; then
  * Vbar(j) = min{ V_k(j) : bit k-1 of fine_mask[j] }.  Nodes in no
  * sub-domain receive value_out.
