@@ -28,7 +28,7 @@
  *       linear interpolant on the triangle of the Kuhn split of the cell that
  *       holds the point; Q1 (multilinear) otherwise.  The adjoint functions
  *       assume Q1.
- *   Games (Sec. 2 "max_b min_a", Example ex4): with a second control set B
+ *   Games (Sec. 2, max over b of min over a; Example ex4): with a second control set B
  *       the operator is beta * max_b min_a I[V](x_i + h f(x_i, a, b)) +
  *       gamma * l_i, f = D(x)(a - b) + c(x); D(x) = diag(scale) per node, or
  *       s(x) I, or I.

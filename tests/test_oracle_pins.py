@@ -1268,7 +1268,7 @@ def _vdp_problem(orc, d):
 
 
 # --------------------------------------------------------------------------
-# Games (Sec. 2, "max_b min_a"; Example ex4): the second player's control b
+# Games (Sec. 2, max over b of min over a; Example ex4): the second player's control b
 # enters as f = D(x)(a - b) + c(x).
 
 def test_game_with_a_silent_second_player_is_the_control_problem(orc):
