@@ -659,6 +659,68 @@ def test_box_boundary_distance_exact(orc):
 # --------------------------------------------------------------------------
 # Invariants (Sec. 3)
 
+def _sym_problem(orc, shape, lo, hi, ctr, lab, **kw):
+    p = orc.Problem(shape, lo, hi, ctr, lab, 0.08, lam=0.8, v_out=2.0, **kw)
+    return orc.solve(p, tol=1e-14)[0].reshape(shape[1], shape[0])
+
+
+@pytest.mark.parametrize("fields", ["speed", "scale", "p1"])
+def test_symmetries_of_the_scheme(orc, fields):
+    """The discrete problem (Sec. 3) on a non-square grid with an asymmetric
+    control set, speed or per-axis factors, a current and a cost field:
+    mirroring x (controls, current x-component, every field and the targets)
+    mirrors V, and exchanging x and y (grid, box, fields, vector components)
+    transposes V, to rounding.  This catches what a single case cannot:
+    lower and upper faces handled differently, the two spacings or strides
+    mixed up.  The P1 split along the (0,0)-(1,1) diagonal is invariant under
+    the exchange of x and y but not under the mirror, which maps it to the
+    other diagonal (a different scheme), so P1 is checked under the exchange
+    only."""
+    g = np.random.default_rng(5)
+    nx, ny = 23, 17
+    lo, hi = (-1.0, -0.7), (1.0, 0.9)
+    X, Y = S.mesh2(nx, ny, lo=lo, hi=hi)
+    lab = S.disk_labels(X, Y, np.array([[-0.4, 0.2], [0.5, -0.3]]), 0.2)
+    cur = g.uniform(-0.3, 0.3, X.shape + (2,))
+    cost = g.uniform(0.5, 2.0, X.shape)
+    F = g.uniform(0.4, 1.4, X.shape + (2,)) if fields == "scale" else g.uniform(0.5, 1.5, X.shape)
+    ctr = S.circle_controls(12) @ np.array([[1.0, 0.2], [0.1, 0.9]])
+    key = "scale" if fields == "scale" else "speed"
+    extra = dict(interp=1) if fields == "p1" else {}
+    c = np.ascontiguousarray
+    V = _sym_problem(orc, (nx, ny), lo, hi, ctr, lab, current=cur, cost=cost, **{key: F}, **extra)
+    if fields != "p1":
+        Vm = _sym_problem(orc, (nx, ny), lo, hi, ctr * [-1, 1], c(lab[:, ::-1]),
+                          current=c(cur[:, ::-1] * [-1, 1]), cost=c(cost[:, ::-1]),
+                          **{key: c(F[:, ::-1])}, **extra)
+        assert np.abs(Vm[:, ::-1] - V).max() < 1e-12
+    Ft = c(F.transpose(1, 0, 2)[..., ::-1]) if fields == "scale" else c(F.T)
+    Vt = _sym_problem(orc, (ny, nx), lo[::-1], hi[::-1], c(ctr[:, ::-1]), c(lab.T),
+                      current=c(cur.transpose(1, 0, 2)[..., ::-1]), cost=c(cost.T),
+                      **{key: Ft}, **extra)
+    assert np.abs(Vt.T - V).max() < 1e-12
+
+
+def test_symmetry_of_the_dubins_scheme(orc):
+    """Dubins car (Sec. 5 setting, heading periodic on [-pi, pi)): mirroring
+    y together with the heading (theta -> -theta, node k -> n - k) and the
+    turn rate (u -> -u) mirrors V, to rounding."""
+    n, nth = 21, 16
+    x = np.linspace(-1, 1, n)
+    lab = np.zeros((nth, n, n), dtype=np.int32)
+    lab[:, (x[None, :] - 0.3) ** 2 + (x[:, None] - 0.35) ** 2 <= 0.25 ** 2] = 1
+    h = 2.0 / (n - 1)
+    box = ((-1, -1, -np.pi), (1, 1, np.pi))
+
+    def solve(u, labels):
+        p = orc.Problem((n, n, nth), *box, u, labels, h, dyn=1, periodic=(0, 0, 1))
+        return orc.solve(p, tol=1e-14)[0].reshape(nth, n, n)
+
+    V = solve([[-1.0], [0.0], [1.0]], lab)
+    Vm = solve([[1.0], [0.0], [-1.0]], np.ascontiguousarray(lab[:, ::-1, :]))
+    assert np.abs(Vm[(-np.arange(nth)) % nth][:, ::-1, :] - V).max() < 1e-12
+
+
 def test_iteration_invariants(orc):
     d = S.c2(n=65)
     p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"],
