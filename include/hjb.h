@@ -313,13 +313,14 @@ int hjb_point_values(hjb_problem *p, const float *v, const float *points, int P,
                      float *grad_v, void *stream);
 
 /* Allocation-free full-domain solve.  The paper has no counterpart: this is
- * a deployment variant of hjb_solve for callers that must not allocate
- * device memory -- code recorded into a CUDA graph by stream capture (an
- * allocation there would become a graph allocation node or fail), real-time
- * control loops that forbid cudaMalloc/cudaFree after start-up, and plug-ins
- * whose host application owns every device allocation.  It takes the
- * descriptors of hjb_create directly (no problem object) and runs the same
- * sweep kernel as hjb_solve in one cooperative launch.
+ * a deployment variant of hjb_solve for callers that cannot allocate device
+ * memory while they run: real-time control loops, where cudaMalloc and
+ * cudaFree may synchronise the device and take unbounded time, so they are
+ * forbidden after start-up; and plug-ins or embedded solvers whose host
+ * application owns every device allocation (its own pool and memory
+ * budget), so the library may not add allocations of its own.  It takes
+ * the descriptors of hjb_create directly (no problem object) and runs the
+ * same sweep kernel as hjb_solve in one cooperative launch.
  *
  * Its working memory (iteration buffers, work queue, control block) lives in
  * a single 4 MiB file-scope device array that every GPU loading the library
@@ -329,14 +330,17 @@ int hjb_point_values(hjb_problem *p, const float *v, const float *points, int P,
  * rejected with HJB_ERR_INVALID_ARG and a message saying so.
  * Every array argument must be device memory (host arrays would need
  * staging buffers): host pointers are rejected with HJB_ERR_INVALID_ARG.
- * No cudaMalloc, cudaFree or allocating library call is made.
+ * No cudaMalloc, cudaFree or allocating library call is made.  The call
+ * reads the largest field magnitudes back to the host (to pick the
+ * interpolation halo) and synchronises the stream before it returns.
  *
  * The array's device address is looked up (cudaGetSymbolAddress) by the
- * first call on each device, with that device current: make one call on
- * each device before any stream capture.  All calls share the array, so
- * calls that may overlap on the GPU (other streams, other host threads)
- * race; serialise them.  Each call re-initialises every part of the array
- * it reads.  Outputs and statistics as for hjb_solve. */
+ * first call on each device, with that device current; that first call
+ * should come before any stream capture.  All calls share the array, which
+ * keeps the last call's contents, so calls that may overlap on the GPU
+ * (other streams, other host threads) race: serialise them.  Each call
+ * re-initialises every part of the array it reads.  Outputs and statistics
+ * as for hjb_solve. */
 int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *cost,
                      const hjb_discount *disc, const hjb_controls *controls,
                      const hjb_target *target, const hjb_solve_opts *opts, float *v_out,

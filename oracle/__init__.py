@@ -73,6 +73,8 @@ def _lib_handle():
             lib.ohjb_coarse_shape.restype = i
             lib.ohjb_label.argtypes = [C.c_longlong, i, vp, vp, d, d, vp, vp]
             lib.ohjb_label.restype = C.c_longlong
+            lib.ohjb_delta.argtypes = [P, vp, vp, d, d, d, C.POINTER(d)]
+            lib.ohjb_delta.restype = d
             lib.ohjb_ra.argtypes = [P, vp, d, d, d, i, vp, vp, i]
             lib.ohjb_ra.restype = C.c_longlong
             lib.ohjb_project.argtypes = [P, vp, vp, vp]
@@ -242,6 +244,22 @@ def ra(p: Problem, stride, delta, h_coarse=None, tol=1e-12, max_iters=1_000_000,
     if ties < 0:
         raise ValueError("bad stride")
     return Vaux, lab, int(ties)
+
+
+def delta(p: Problem, stride, Vaux, C_=0.0, q=1.0, M=-1.0):
+    """Threshold of RA step 3, 2 (C dx_K^q + M dx_K) (eq. rep, Prop. 3.1); M < 0
+    estimates M by the largest discrete gradient norm of min_k V_k on the
+    coarse grid (reading R5).  Returns (delta, M)."""
+    st = (C.c_int * 3)(*(list(stride) + [1] * (3 - len(stride))))
+    Va = _f64(Vaux)
+    if Va.shape != (p.ntargets, int(np.prod(coarse_shape(p, stride)))):
+        raise ValueError("Vaux must be [ntargets, coarse nodes]")
+    Mo = C.c_double(0.0)
+    dl = _lib_handle().ohjb_delta(p._ref(), st, Va.ctypes.data, float(C_), float(q), float(M),
+                                  C.byref(Mo))
+    if dl < 0:
+        raise ValueError("stride does not divide the grid")
+    return float(dl), float(Mo.value)
 
 
 def project(p: Problem, stride, coarse_labels):

@@ -514,6 +514,64 @@ long long ohjb_label(long long NK, int m, const double *Vaux, const int32_t *tar
     return ties;
 }
 
+/* Threshold of RA step 3 (eq. rep of Prop. 3.1): delta = 2 (C dx^q + M dx)
+ * on the coarse grid K of the given stride, dx = dx_K the spacing of its
+ * first dimension.  M is the Lipschitz constant of the value function
+ * (hypothesis lip); M < 0 selects the estimate of reading R5, the largest
+ * norm over the nodes of K of the discrete gradient of V = min_k V_k:
+ * per dimension the centred difference (V(j + e_d) - V(j - e_d)) / (2 dx_d),
+ * one-sided (V(j + e_d) - V(j)) / dx_d or (V(j) - V(j - e_d)) / dx_d on the
+ * first and last node of a non-periodic dimension, wrapping on a periodic
+ * one.  Vaux is [m][NK] as returned by RA step 1; M_out (optional) receives
+ * the M used.  Returns delta, or -1 when the stride does not fit the grid. */
+double ohjb_delta(const ohjb_problem *p, const int stride[3], const double *Vaux, double C,
+                  double q, double M, double *M_out) {
+    ohjb_problem K;
+    if (make_coarse(p, stride, p->h, &K)) return -1.0;
+    long long NK = node_count(&K);
+    int m = p->ntargets;
+    if (M < 0.0) {
+        double *V = (double *)malloc(sizeof(double) * NK);
+        for (long long j = 0; j < NK; ++j) {
+            V[j] = INFINITY;
+            for (int k = 0; k < m; ++k)
+                if (Vaux[(long long)k * NK + j] < V[j]) V[j] = Vaux[(long long)k * NK + j];
+        }
+        M = 0.0;
+        for (long long j = 0; j < NK; ++j) {
+            int idx[3];
+            unflatten(&K, j, idx);
+            double norm2 = 0.0;
+            for (int d = 0; d < K.ndim; ++d) {
+                int lo[3] = {idx[0], idx[1], idx[2]}, hi[3] = {idx[0], idx[1], idx[2]};
+                double span = 2.0 * spacing(&K, d);
+                if (K.periodic[d]) {
+                    lo[d] = (idx[d] + K.n[d] - 1) % K.n[d];
+                    hi[d] = (idx[d] + 1) % K.n[d];
+                } else if (idx[d] == 0) {
+                    hi[d] = 1;
+                    span = spacing(&K, d);
+                } else if (idx[d] == K.n[d] - 1) {
+                    lo[d] = K.n[d] - 2;
+                    span = spacing(&K, d);
+                } else {
+                    lo[d] = idx[d] - 1;
+                    hi[d] = idx[d] + 1;
+                }
+                double g = (V[flatten(&K, hi)] - V[flatten(&K, lo)]) / span;
+                norm2 += g * g;
+            }
+            if (sqrt(norm2) > M) M = sqrt(norm2);
+        }
+        free(V);
+    }
+    if (M_out) *M_out = M;
+    double dx = spacing(&K, 0);
+    double delta = 2.0 * ((C > 0.0 ? C * pow(dx, q) : 0.0) + M * dx);
+    free_coarse(&K);
+    return delta;
+}
+
 /* RA (all three steps) on the coarse grid of the given stride.
  * Step 1 solves the m auxiliary problems V_k = T_k(V_k) whose target is
  * component k only (dG := X_k); Vaux receives them as [m][NK].  labels

@@ -1716,11 +1716,11 @@ int hjb_point_values(hjb_problem *P, const float *v, const float *points, int np
 // ===========================================================================
 // Allocation-free full-domain solve (hjb_solve_static).
 //
-// For callers that may not allocate device memory -- code running inside a
-// stream capture that must not add allocation nodes, real-time loops that
-// forbid cudaMalloc after start-up, plug-ins whose host application owns
-// every allocation -- this entry point keeps all of its working memory in
-// one file-scope device array.  The array is a fixed 4 MiB on every GPU that
+// For callers that cannot allocate device memory while they run --
+// real-time loops that forbid cudaMalloc/cudaFree after start-up (both may
+// synchronise the device), plug-ins whose host application owns every
+// allocation -- this entry point keeps all of its working memory in one
+// file-scope device array.  The array is a fixed 4 MiB on every GPU that
 // loads the library, for as long as the process lives; it bounds the grid to
 // STATIC_MAX_NODES nodes.  Each call re-initialises everything it reads, so
 // no state carries over, but all calls share the array: calls that can

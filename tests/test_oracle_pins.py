@@ -899,6 +899,66 @@ def _policy_closed(p, pol, member, shape):
     return keep
 
 
+def test_threshold_estimate_exact_cases(orc):
+    """The threshold of eq. (rep), delta = 2 (C dx_K^q + M dx_K), with M
+    estimated by the largest discrete gradient norm of min_k V_k on the
+    coarse grid (reading R5).  Fixed by mathematics, not by a retyped
+    formula: differences of an affine field are its gradient exactly
+    (anisotropic spacings, so transposed axes or spacings fail); the
+    estimate takes the minimum over the auxiliary solutions (a min switching
+    between two affine fields has the larger slope); on V = x^2 on [-1, 1]
+    centred differences give 2|x| and the one-sided edge difference 2 - dx,
+    the maximum; a periodic dimension wraps (sin over a full period); and
+    the C dx^q term adds 2 C dx^q."""
+    nx, ny = 9, 5  # fine grid; stride 2 gives a 5 x 3 coarse grid on [-1,1] x [-1,1]
+    lab = np.zeros((ny, nx), dtype=np.int32)
+    lab[0, 0] = 1
+    lab[-1, -1] = 2
+    p = orc.Problem((nx, ny), (-1, -1), (1, 1), S.circle_controls(4), lab, 0.25)
+    nk = orc.coarse_shape(p, (2, 2))
+    assert nk == (5, 3)
+    Xk, Yk = S.mesh2(5, 3)
+    dxk = 0.5
+    a, b = 0.3, -0.7
+    aff = (a * Xk + b * Yk + 0.2).reshape(1, -1)
+    two = np.concatenate([aff, aff + 5.0])  # the min is the first
+    dl, M = orc.delta(p, (2, 2), two)
+    assert abs(M - math.hypot(a, b)) < 1e-14
+    assert abs(dl - 2 * M * dxk) < 1e-14
+    sw = np.concatenate([(0.5 * Xk).reshape(1, -1), (-2.0 * Xk).reshape(1, -1)])
+    assert abs(orc.delta(p, (2, 2), sw)[1] - 2.0) < 1e-14
+    quad = np.concatenate([(Xk ** 2).reshape(1, -1)] * 2)
+    assert abs(orc.delta(p, (2, 2), quad)[1] - (2 - dxk)) < 1e-14
+    dl_c, _ = orc.delta(p, (2, 2), two, C_=0.7, q=0.5)
+    assert abs(dl_c - (dl + 2 * 0.7 * math.sqrt(dxk))) < 1e-14
+    assert abs(orc.delta(p, (2, 2), two, M=3.0)[0] - 2 * 3.0 * dxk) < 1e-14
+    # periodic third dimension: 8 layers on [0, 2 pi), stride 2 keeps 4; the
+    # wrapped centred difference of sin at the layer theta = 0 is
+    # (sin(pi/2) - sin(-pi/2)) / pi = 2 / pi, the largest over the layers
+    lab3 = np.zeros((8, ny, nx), dtype=np.int32)
+    lab3[:, 0, 0] = 1
+    p3 = orc.Problem((nx, ny, 8), (-1, -1, 0), (1, 1, 2 * np.pi), [[-1.0], [1.0]], lab3, 0.25,
+                     periodic=(0, 0, 1), dyn=1)
+    th = np.arange(4) * (np.pi / 2)
+    V3 = np.broadcast_to(np.sin(th)[:, None, None], (4, 3, 5)).reshape(1, -1).copy()
+    assert abs(orc.delta(p3, (2, 2, 2), V3)[1] - 2 / np.pi) < 1e-14
+
+
+def test_threshold_estimate_on_the_box_distance(orc):
+    """On the distance to the boundary of (-1,1)^2 (Sec. 4.1; RA with the box
+    sides as the four target components) the discrete value is the closed
+    form 1 - exp(-(1 - max|x|)) and its gradient norm exp(-d) <= 1 peaks at
+    the boundary; the estimate is the one-sided edge difference there,
+    (1 - exp(-dx_K)) / dx_K."""
+    n, st = 81, 8
+    p = orc.Problem((n, n), (-1, -1), (1, 1), S.circle_controls(32), _box_labels(n), 2 / (n - 1))
+    Vaux, _, _ = orc.ra(p, (st, st), 0.1, tol=1e-14)
+    dl, M = orc.delta(p, (st, st), Vaux)
+    dxk = 2.0 / ((n - 1) // st)
+    assert abs(M - (1 - math.exp(-dxk)) / dxk) < 1e-10
+    assert abs(dl - 2 * M * dxk) < 1e-14
+
+
 @pytest.mark.parametrize("which", ["c1", "c2"])
 def test_restricted_solve_reproduces_full(orc, which):
     """Prop. 2.1 / Prop. 4.1: a solve restricted to a reconstructed
@@ -920,10 +980,7 @@ def test_restricted_solve_reproduces_full(orc, which):
     # threshold of eq. (rep) with the Lipschitz constant M estimated by the
     # largest discrete gradient of the coarse V = min_k V_k (C dx^q dropped)
     Vaux, _, _ = orc.ra(p, stride, 0.0, tol=1e-13)
-    nk = orc.coarse_shape(p, stride)
-    dxk = 2.0 / (nk[0] - 1)
-    gy, gx = np.gradient(Vaux.min(0).reshape(nk[1], nk[0]), dxk)
-    delta = 2 * np.sqrt(gx ** 2 + gy ** 2).max() * dxk
+    delta, _ = orc.delta(p, stride, Vaux)
     vmin, lab, _ = orc.label(Vaux, p.target.reshape(n, n)[::stride[1], ::stride[0]], delta)
     fine = orc.project(p, stride, lab)
     Vbar, unc, its, Vk = orc.isa(p, fine, tol=1e-13, keep_vk=True)

@@ -1,11 +1,12 @@
 """The allocation-free solve (hjb_solve_static) against the ordinary solve.
 
-Callers that cannot allocate device memory -- work recorded by stream
-capture, real-time loops that forbid cudaMalloc after start-up, plug-ins
-whose host owns every allocation -- use hjb_solve_static, which keeps its
-working memory in one static device array.  This file is collected last so
-that a run stopping at the first failure has already run every other test;
-it also passes on its own in a fresh process.
+Some callers cannot allocate device memory while they run: real-time
+control loops that forbid cudaMalloc/cudaFree after start-up (both may
+synchronise the device), and plug-ins whose host application owns every
+device allocation.  They use hjb_solve_static, which keeps its working
+memory in one static device array.  This file is collected last so that a
+run stopping at the first failure has already run every other test; it also
+passes on its own in a fresh process.
 """
 import ctypes as C
 
