@@ -98,37 +98,59 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-# Applications of T per staged tile and sweep the library uses when the
-# caller passes none (hjb_solve_opts.local_iters <= 0), unless HJB_LOCAL_ITERS
-# overrides it.
-LIBRARY_LOCAL_ITERS = 6
-
-
-def run_local_iters():
-    e = os.environ.get("HJB_LOCAL_ITERS")
-    v = int(e) if e else LIBRARY_LOCAL_ITERS
-    return min(max(v, 1), 16)
-
-
-def sweep_traffic(path=TRAFFIC_PROFILE, rows=None):
-    """DRAM bytes per sweep launch from a committed ncu summary (for the 2D
-    tile shape with `rows` rows when the summary lists shapes), or None when
-    the kernel sources changed after the counters were taken."""
+def sweep_traffic(path=TRAFFIC_PROFILE, rows=None, local_iters=None):
+    """DRAM bytes per sweep launch from a committed ncu summary, for the tile
+    shape (`rows`) and applications per tile (`local_iters`) the timed run
+    used, or None when the summary has no line for them or the kernel
+    sources changed after the counters were taken.  Lines are
+    `- traffic_bytes_per_launch_rows<R>_li<L>: <bytes>` and
+    `- node_updates_per_launch_rows<R>_li<L>: <count>` (3D: rows 8)."""
     try:
         with open(path) as f:
             kv = dict(line.strip("- \n").split(": ", 1) for line in f
                       if line.startswith("- ") and ": " in line)
         if kv.get("sources_sha256") != kernel_sources_sha256():
             return None
-        if "local_iters" in kv and int(kv["local_iters"]) != run_local_iters():
+        sfx = "_rows%d_li%d" % (rows or 8, local_iters or 6)
+        if "traffic_bytes_per_launch" + sfx not in kv:
             return None
-        sfx = "_rows%d" % rows if rows and ("traffic_bytes_per_launch_rows%d" % rows) in kv else ""
         out = {"bytes_per_launch": float(kv["traffic_bytes_per_launch" + sfx])}
         if "node_updates_per_launch" + sfx in kv:
             out["node_updates_per_launch"] = float(kv["node_updates_per_launch" + sfx])
         return out
     except (OSError, KeyError, ValueError):
         return None
+
+
+def oracle_gap(n, stride):
+    """The oracle's max |Vbar - V| at the benchmark's threshold, from the
+    committed golden file, when it was written for this grid and stride."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "c2_decomposed_%d.json" % n)) as f:
+            g = json.load(f)
+        if list(g["stride"]) != list(stride):
+            return None
+        return {"max_abs_isa_minus_full": g["max_abs_isa_minus_full"], "delta": g["delta"]}
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def breakdown(ms_ra, ms_fine, tot, rst, fst, full_ms, nfree):
+    """Where the decomposed step's time goes against the full-domain solve:
+    the reconstruction, then the fine solve as sweeps x time per sweep, with
+    the node-updates it performs relative to the full solve's."""
+    return {
+        "ra_ms": ms_ra,
+        "fine_ms": ms_fine,
+        "fine_sweeps": tot["iterations"],
+        "fine_us_per_sweep": 1e3 * ms_fine / max(1, tot["iterations"]),
+        "full_sweeps": fst["iterations"],
+        "full_us_per_sweep": 1e3 * full_ms / max(1, fst["iterations"]),
+        "fine_node_updates": tot["node_updates"],
+        "full_node_updates": fst["node_updates"],
+        "node_update_ratio": tot["node_updates"] / max(1, fst["node_updates"]),
+        "labelled_over_free": rst["labelled"] / max(1, nfree),
+    }
 
 
 def measured_peaks():
@@ -337,7 +359,8 @@ def run_dubins(args, hjb, S, dev, flush, local):
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6660.0)
     ach = tot["node_updates"] * 9 / (tot["ms"] / 1e3) / 1e9  # V read+write 8 B, labels 1 B
-    traffic = sweep_traffic(os.path.join(ROOT, "profiles", "sweep3d_dubins256_launch_list_traffic.md"))
+    traffic = sweep_traffic(os.path.join(ROOT, "profiles", "sweep3d_dubins256_dram_traffic.md"),
+                            rows=8, local_iters=tot.get("local_iters"))
     cpu = None
     if not args.no_cpu_baseline:
         import oracle as orc
@@ -691,12 +714,13 @@ def main():
     peak_ops = sms * 128 * fmax
     achieved = (tot["node_updates"] * 64 * OPS_PER_CONTROL) / (tot["ms"] / 1e3)
     rows = tot.get("tile_rows") or None
-    traffic = sweep_traffic(rows=rows)
+    traffic = sweep_traffic(rows=rows, local_iters=tot.get("local_iters"))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle  # noqa: F401
         cpu = cpu_baseline(args.cpu_seconds, n)
     check = float((Vbar - Vfull).abs().max().item())
+    gold = oracle_gap(n, stride)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -713,7 +737,17 @@ def main():
         "decomposed": {"ms_ra": ra_ms / args.steps, "ms_fine": loop_ms / args.steps,
                        "max_subdomain_iters": tot["iterations"],
                        "labelled_fraction": rst["labelled"] / N, "ra_iters": rst["iterations"],
-                       "max_abs_diff_vs_full": check},
+                       "delta": rst["delta"], "lipschitz": rst["lipschitz"],
+                       "max_abs_diff_vs_full": check,
+                       # the method's own difference between the assembled ISA value and the
+                       # full-domain value at this threshold, from the FP64 oracle
+                       # (tests/golden/c2_decomposed_1025.json); the GPU must reproduce it
+                       "oracle_max_abs_isa_minus_full": gold["max_abs_isa_minus_full"] if gold else None,
+                       "oracle_delta": gold["delta"] if gold else None,
+                       "gap_matches_oracle": (abs(check - gold["max_abs_isa_minus_full"]) < 1e-4)
+                       if gold else None,
+                       "breakdown": breakdown(ra_ms / args.steps, loop_ms / args.steps, tot, rst,
+                                              fst, full_ms, nfree)},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Top/s", "frac": achieved / peak_ops,
                      "traffic": traffic["bytes_per_launch"] if traffic else None,

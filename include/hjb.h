@@ -230,6 +230,12 @@ typedef struct {
     long long launches;    /* CUDA kernels the call launched */
     int tile_rows;         /* rows of the 2D tiles the sweeps ran on (32 x 8, 4 or 2 nodes:
                               the autotuner's choice or HJB_TILE_ROWS); 0 for 3D */
+    double delta;          /* hjb_subdomains: the threshold of RA step 3 it applied */
+    double lipschitz;      /* hjb_subdomains: the M of that threshold (estimated when
+                              hjb_ra_opts.M < 0 and delta < 0; 0 when delta was given) */
+    int local_iters;       /* applications of T per staged tile and sweep that ran */
+    long long tile_visits; /* tiles staged and processed by the sweeps (each visit applies T
+                              1 to local_iters times to the tile's nodes) */
 } hjb_stats;
 
 /* Full-domain solve of V = T(V) by value iteration V^{n+1} = T(V^n)
@@ -345,6 +351,38 @@ int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_co
                      const hjb_discount *disc, const hjb_controls *controls,
                      const hjb_target *target, const hjb_solve_opts *opts, float *v_out,
                      hjb_stats *stats, void *stream);
+
+/* Autotuner table (not in the paper: a property of this implementation).
+ * hjb_solve, hjb_solve_decomposed and hjb_solve_batch run the sweep with a
+ * tile shape (tile_rows: 2D tiles of 32 x 8, 32 x 4 or 32 x 2 nodes, with
+ * 1, 2 or 4 control groups per node; fixed at 8 for Dubins, games and P1)
+ * and a number of applications of T per staged tile and sweep
+ * (local_iters).  The first call for a problem class on a device runs the
+ * whole call once per candidate on the caller's data and keeps the fastest
+ * (ms: its device time) in a table keyed by
+ *     "<device name>/<SM count>|<full|decomposed|batch>|<class fields>".
+ * The table is also filled, at the first call that needs it, from the file
+ * tune_cache.json of the package directory (one level above the directory
+ * holding libhjb.so; read only) and then from the file named by the
+ * environment variable HJB_TUNE_CACHE (read, and rewritten after every
+ * tuning).  HJB_TUNE=off never times a call: it takes the table's choice or
+ * the default (tile_rows 8, local_iters 6, 4 for a game), so that repeated
+ * runs are bit for bit reproducible; HJB_TUNE=force times even when the
+ * table holds a choice.  HJB_TILE_ROWS and HJB_LOCAL_ITERS (or
+ * hjb_solve_opts.local_iters) pin their axis.  The file is a JSON array of
+ * {"key": ..., "rows": ..., "local_iters": ..., "ms": ...} objects, one per
+ * line.  Errors: HJB_ERR_INVALID_ARG (NULL argument, unknown key, a choice
+ * out of range, a file that cannot be opened). */
+typedef struct {
+    int tile_rows;
+    int local_iters;
+    double ms;
+} hjb_tune_choice;
+int hjb_tune_get(const char *key, hjb_tune_choice *out);
+int hjb_tune_set(const char *key, const hjb_tune_choice *choice);
+int hjb_tune_load(const char *path, int *entries); /* merges the file's entries (they win) */
+int hjb_tune_save(const char *path);               /* writes every entry of the table */
+int hjb_tune_clear(void);                           /* empties the table (files not re-read) */
 
 /* Message of the last failure on this thread ("" if none). */
 const char *hjb_last_error(void);

@@ -34,6 +34,7 @@ HJB_SUBDOMAIN_TARGETS_OWN = 1
 
 EXPORTS = ["hjb_create", "hjb_destroy", "hjb_solve", "hjb_subdomains", "hjb_solve_decomposed",
            "hjb_solve_batch", "hjb_backward", "hjb_point_values", "hjb_solve_static",
+           "hjb_tune_get", "hjb_tune_set", "hjb_tune_load", "hjb_tune_save", "hjb_tune_clear",
            "hjb_last_error", "hjb_version"]
 
 
@@ -83,10 +84,16 @@ class hjb_solve_opts(C.Structure):
 class hjb_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("node_updates", C.c_longlong),
                 ("final_residual", C.c_double), ("ms", C.c_double), ("ties", C.c_longlong),
-                ("labelled", C.c_longlong), ("launches", C.c_longlong), ("tile_rows", C.c_int)]
+                ("labelled", C.c_longlong), ("launches", C.c_longlong), ("tile_rows", C.c_int),
+                ("delta", C.c_double), ("lipschitz", C.c_double), ("local_iters", C.c_int),
+                ("tile_visits", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hjb_tune_choice(C.Structure):
+    _fields_ = [("tile_rows", C.c_int), ("local_iters", C.c_int), ("ms", C.c_double)]
 
 
 class hjb_ra_opts(C.Structure):
@@ -125,6 +132,11 @@ def lib():
                                        C.POINTER(hjb_cost), C.POINTER(hjb_discount),
                                        C.POINTER(hjb_controls), C.POINTER(hjb_target),
                                        C.POINTER(hjb_solve_opts), vp, C.POINTER(hjb_stats), vp]
+        L.hjb_tune_get.argtypes = [C.c_char_p, C.POINTER(hjb_tune_choice)]
+        L.hjb_tune_set.argtypes = [C.c_char_p, C.POINTER(hjb_tune_choice)]
+        L.hjb_tune_load.argtypes = [C.c_char_p, C.POINTER(C.c_int)]
+        L.hjb_tune_save.argtypes = [C.c_char_p]
+        L.hjb_tune_clear.argtypes = []
         L.hjb_last_error.restype = C.c_char_p
         L.hjb_version.restype = C.c_char_p
         for name in EXPORTS:

@@ -83,7 +83,7 @@ struct SlotState {
     float final_res;
     unsigned long long updates;  // free-node evaluations of T
     int twin;                    // lower slot with the same node set (not solved), else -1
-    int pad_s;
+    unsigned visits;             // staged tile items processed (sum over sweeps)
 };
 
 // Launch-wide control block.

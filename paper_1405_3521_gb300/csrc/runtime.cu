@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <dlfcn.h>
 #include <map>
 #include <mutex>
 #include <string>
@@ -556,18 +557,27 @@ int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows) {
     return HJB_OK;
 }
 
-// Applications of T per tile and sweep: opts->local_iters when positive,
-// else HJB_LOCAL_ITERS, else 6, or 4 for a game, whose applications
-// evaluate every (a, b) pair of controls, so that a longer stay on a tile
-// costs more than the sweeps it saves (measured; clamped to 1..16).
-int local_iters(const hjb_solve_opts *o, const hjb_problem *P) {
+// Applications of T per tile and sweep pinned by the caller:
+// opts->local_iters when positive, else HJB_LOCAL_ITERS, else 0 (not pinned:
+// the autotuner's choice).  Clamped to 1..16.
+int pinned_local_iters(const hjb_solve_opts *o) {
     static const int env = [] {
         const char *e = std::getenv("HJB_LOCAL_ITERS");
         return e ? std::atoi(e) : 0;
     }();
-    const int dflt = env > 0 ? env : ((P && P->nb > 1) ? 4 : 6);
-    const int v = (o && o->local_iters > 0) ? o->local_iters : dflt;
-    return v < 1 ? 1 : (v > 16 ? 16 : v);
+    const int v = (o && o->local_iters > 0) ? o->local_iters : (env > 0 ? env : 0);
+    if (v <= 0) return 0;
+    return v > 16 ? 16 : v;
+}
+
+// Applications of T per tile and sweep without a tuned choice: the pinned
+// value, else 6, or 4 for a game, whose applications evaluate every (a, b)
+// pair of controls, so that a longer stay on a tile costs more than the
+// sweeps it saves (measured).
+int local_iters(const hjb_solve_opts *o, const hjb_problem *P) {
+    const int v = pinned_local_iters(o);
+    if (v) return v;
+    return (P && P->nb > 1) ? 4 : 6;
 }
 
 // How the CTAs of a sweep share its tile queue: by default the entries past
@@ -780,6 +790,7 @@ void fill_stats(hjb_stats *s, const SlotState &st) {
     s->converged = st.converged;
     s->node_updates = static_cast<long long>(st.updates);
     s->final_residual = st.final_res;
+    s->tile_visits = static_cast<long long>(st.visits);
 }
 
 hjbh::GridDims dims_of(const hjb_problem *P) {
@@ -801,15 +812,35 @@ int check_opts(const hjb_solve_opts *o) {
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner of the 2D tile shape: 32 x rows nodes with 8 / rows control groups
-// per node.  Small tiles follow a narrow active front with less wasted work
-// and finish an item sooner; large tiles amortise the halo.  The first call
-// for a problem class runs the whole call once per candidate on the caller's
-// data and keeps the fastest; the choice is cached for the process.
-// HJB_TILE_ROWS=8|4|2 forces a shape.
+// Autotuner.  A choice is a point of the search space of the sweep:
+//  - rows: 2D tile rows (tiles of 32 x 8, 32 x 4 or 32 x 2 nodes with 1, 2
+//    or 4 control groups per node); fixed at 8 for the fixed-shape kernels
+//    (Dubins, games, P1);
+//  - li: applications of T per staged tile and sweep (small tiles follow a
+//    narrow active front with less wasted work and finish an item sooner;
+//    more applications per staging cross more of a tile per sweep but keep
+//    a CTA longer on one item).
+// The first call for a problem class runs the whole call once per candidate
+// on the caller's data and keeps the fastest.  Choices live in a table keyed
+// by the device and the problem class; the table is filled from the file
+// HJB_TUNE_CACHE names (read and written) and from the tuning file shipped
+// beside the library (read only; the choices measured for this library on
+// its target GPU), and can be read and written through hjb_tune_get /
+// hjb_tune_set / hjb_tune_load / hjb_tune_save.  HJB_TUNE=off never times:
+// a call takes the table's choice or the fixed default, so repeated runs are
+// bit-reproducible; HJB_TUNE=force times even when the table has a choice.
+// HJB_TILE_ROWS=8|4|2 and HJB_LOCAL_ITERS (or hjb_solve_opts.local_iters)
+// pin their axis.
+
+struct Choice {
+    int rows = 8;
+    int li = 6;
+    double ms = 0.0;
+};
 
 std::mutex g_tune_mu;
-std::map<std::vector<long long>, int> g_tuned;
+std::map<std::string, Choice> g_tuned;
+bool g_tune_files_read = false;
 
 int forced_rows() {
     const char *e = std::getenv("HJB_TILE_ROWS");
@@ -818,35 +849,183 @@ int forced_rows() {
     return (r == 8 || r == 4 || r == 2) ? r : 0;
 }
 
+int tune_mode() {  // 0 off, 1 on (default), 2 force
+    const char *e = std::getenv("HJB_TUNE");
+    if (!e) return 1;
+    if (std::strcmp(e, "off") == 0) return 0;
+    if (std::strcmp(e, "force") == 0) return 2;
+    return 1;
+}
+
+// Parse one cache line: {"key": "...", "rows": R, "local_iters": L, "ms": M}.
+bool parse_tune_line(const std::string &line, std::string *key, Choice *c) {
+    const size_t k0 = line.find("\"key\"");
+    if (k0 == std::string::npos) return false;
+    const size_t q0 = line.find('"', line.find(':', k0) + 1);
+    const size_t q1 = q0 == std::string::npos ? q0 : line.find('"', q0 + 1);
+    if (q1 == std::string::npos) return false;
+    *key = line.substr(q0 + 1, q1 - q0 - 1);
+    auto num = [&](const char *name, double *v) {
+        const size_t a = line.find(name, q1);
+        if (a == std::string::npos) return false;
+        const size_t b = line.find(':', a);
+        if (b == std::string::npos) return false;
+        char *end = nullptr;
+        *v = std::strtod(line.c_str() + b + 1, &end);
+        return end != line.c_str() + b + 1;
+    };
+    double r = 0, l = 0, ms = 0;
+    if (!num("\"rows\"", &r) || !num("\"local_iters\"", &l)) return false;
+    num("\"ms\"", &ms);
+    if (!(r == 8 || r == 4 || r == 2) || l < 1 || l > 16) return false;
+    c->rows = static_cast<int>(r);
+    c->li = static_cast<int>(l);
+    c->ms = ms;
+    return true;
+}
+
+// Merge the entries of a cache file into the table (caller holds the lock).
+// Returns the number of entries read, or -1 if the file cannot be opened.
+int load_tune_file(const char *path, bool overwrite) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return -1;
+    int n = 0;
+    char buf[1024];
+    while (std::fgets(buf, sizeof buf, f)) {
+        std::string key;
+        Choice c;
+        if (!parse_tune_line(buf, &key, &c)) continue;
+        if (overwrite || !g_tuned.count(key)) g_tuned[key] = c;
+        ++n;
+    }
+    std::fclose(f);
+    return n;
+}
+
+int save_tune_file(const char *path) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return -1;
+    std::fprintf(f, "[\n");
+    size_t i = 0;
+    for (const auto &kv : g_tuned) {
+        std::fprintf(f, "{\"key\": \"%s\", \"rows\": %d, \"local_iters\": %d, \"ms\": %.4f}%s\n",
+                     kv.first.c_str(), kv.second.rows, kv.second.li, kv.second.ms,
+                     ++i < g_tuned.size() ? "," : "");
+    }
+    std::fprintf(f, "]\n");
+    std::fclose(f);
+    return std::rename(tmp.c_str(), path) == 0 ? 0 : -1;
+}
+
+// The tuning file shipped beside the library: <package>/tune_cache.json, one
+// directory above the build directory that holds libhjb.so.
+std::string shipped_tune_file() {
+    Dl_info info;
+    if (!dladdr(reinterpret_cast<void *>(&hjb_version), &info) || !info.dli_fname) return "";
+    std::string so = info.dli_fname;
+    const size_t a = so.rfind('/');
+    if (a == std::string::npos) return "";
+    const size_t b = so.rfind('/', a - 1);
+    if (b == std::string::npos) return "";
+    return so.substr(0, b) + "/tune_cache.json";
+}
+
+void read_tune_files() {  // caller holds the lock
+    if (g_tune_files_read) return;
+    g_tune_files_read = true;
+    const std::string shipped = shipped_tune_file();
+    if (!shipped.empty()) load_tune_file(shipped.c_str(), false);
+    if (const char *e = std::getenv("HJB_TUNE_CACHE")) load_tune_file(e, true);
+}
+
+// Key of a problem class on the current device.
+std::string tune_key(const char *op, const std::vector<long long> &cls) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    char name[256] = "unknown";
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) std::snprintf(name, sizeof name, "%s", prop.name);
+    for (char *c = name; *c; ++c)
+        if (*c == '"' || *c == '\\' || *c == '|') *c = '_';
+    std::string k = std::string(name) + "/" + std::to_string(sms) + "|" + op;
+    for (long long v : cls) k += "|" + std::to_string(v);
+    return k;
+}
+
+// Default choice when nothing is tuned: 32 x 8 tiles (the fixed shape of the
+// 3D and generic kernels), the measured default applications per tile.
+Choice default_choice(const hjb_problem *P) {
+    Choice c;
+    c.rows = hjbk::TY;
+    c.li = local_iters(nullptr, P);
+    return c;
+}
+
+// Run `run(choice, &ms)` with the tuned choice for `key`, tuning it first
+// when needed.  fixed_rows: the kernel family has one tile shape; li_fixed:
+// the caller (opts or HJB_LOCAL_ITERS) pinned the applications per tile.
 template <typename Run>
-int tuned_call(const std::vector<long long> &key, Run run) {
-    int rows = forced_rows();
-    if (rows) return run(rows, nullptr);
+int tuned_call(const std::string &key, const hjb_problem *P, bool fixed_rows, int li_pinned, Run run) {
+    const int mode = tune_mode();
+    const int frows = fixed_rows ? hjbk::TY : forced_rows();
+    Choice c = default_choice(P);
+    bool have = false;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        read_tune_files();
         auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) rows = it->second;
+        if (it != g_tuned.end()) {
+            c = it->second;
+            have = true;
+        }
     }
-    if (rows) return run(rows, nullptr);
-    const int cand[3] = {8, 4, 2};
+    if (frows) c.rows = frows;
+    if (li_pinned) c.li = li_pinned;
+    const bool all_pinned = frows && li_pinned;
+    if (mode == 0 || all_pinned || (have && mode == 1)) return run(c, nullptr);
+    std::vector<Choice> cand;
+    const int rows_c[3] = {8, 4, 2};
+    const bool game = P && P->nb > 1;
+    const int li_c[3] = {game ? 2 : 4, game ? 4 : 6, game ? 6 : 8};
+    for (int r : rows_c) {
+        if (frows && r != frows) continue;
+        for (int l : li_c) {
+            if (li_pinned && l != li_pinned) continue;
+            Choice x;
+            x.rows = r;
+            x.li = l;
+            cand.push_back(x);
+        }
+        if (li_pinned && cand.empty()) {
+            Choice x;
+            x.rows = r;
+            x.li = li_pinned;
+            cand.push_back(x);
+        }
+    }
     double best_ms = 1e300;
-    int best = 2, last_rc = HJB_OK;
-    for (int c : cand) {
+    size_t best = 0;
+    int last_rc = HJB_OK;
+    for (size_t i = 0; i < cand.size(); ++i) {
         double ms = 0;
-        const int rc = run(c, &ms);
+        const int rc = run(cand[i], &ms);
         if (rc != HJB_OK && rc != HJB_ERR_NOT_CONVERGED) return rc;
         last_rc = rc;
+        cand[i].ms = ms;
         if (ms < best_ms) {
             best_ms = ms;
-            best = c;
+            best = i;
         }
     }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = best;
+        g_tuned[key] = cand[best];
+        if (const char *e = std::getenv("HJB_TUNE_CACHE")) save_tune_file(e);
     }
     // the outputs of the last candidate are in place when it won
-    return best == cand[2] ? last_rc : run(best, nullptr);
+    return best + 1 == cand.size() ? last_rc : run(cand[best], nullptr);
 }
 
 }  // namespace
@@ -859,6 +1038,65 @@ extern "C" {
 const char *hjb_last_error(void) { return g_err.c_str(); }
 
 const char *hjb_version(void) { return "hjb-gb300 0.1 (sm_103a)"; }
+
+int hjb_tune_get(const char *key, hjb_tune_choice *out) {
+    g_err.clear();
+    if (!key || !out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    read_tune_files();
+    auto it = g_tuned.find(key);
+    if (it == g_tuned.end()) return fail(HJB_ERR_INVALID_ARG, "no tuned choice for this key");
+    out->tile_rows = it->second.rows;
+    out->local_iters = it->second.li;
+    out->ms = it->second.ms;
+    return HJB_OK;
+}
+
+int hjb_tune_set(const char *key, const hjb_tune_choice *c) {
+    g_err.clear();
+    if (!key || !c) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (!(c->tile_rows == 8 || c->tile_rows == 4 || c->tile_rows == 2) || c->local_iters < 1 ||
+        c->local_iters > 16)
+        return fail(HJB_ERR_INVALID_ARG, "tile_rows must be 8, 4 or 2 and local_iters 1..16");
+    if (std::strchr(key, '"') || std::strchr(key, '\\') || std::strchr(key, '\n'))
+        return fail(HJB_ERR_INVALID_ARG, "a key may not hold quotes, backslashes or newlines");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    read_tune_files();
+    Choice x;
+    x.rows = c->tile_rows;
+    x.li = c->local_iters;
+    x.ms = c->ms;
+    g_tuned[key] = x;
+    return HJB_OK;
+}
+
+int hjb_tune_load(const char *path, int *entries) {
+    g_err.clear();
+    if (!path) return fail(HJB_ERR_INVALID_ARG, "NULL path");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    read_tune_files();
+    const int n = load_tune_file(path, true);
+    if (n < 0) return fail(HJB_ERR_INVALID_ARG, "cannot open %s", path);
+    if (entries) *entries = n;
+    return HJB_OK;
+}
+
+int hjb_tune_save(const char *path) {
+    g_err.clear();
+    if (!path) return fail(HJB_ERR_INVALID_ARG, "NULL path");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    read_tune_files();
+    if (save_tune_file(path) != 0) return fail(HJB_ERR_INVALID_ARG, "cannot write %s", path);
+    return HJB_OK;
+}
+
+int hjb_tune_clear(void) {
+    g_err.clear();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+    g_tune_files_read = true;  // an explicit clear also drops the files' entries
+    return HJB_OK;
+}
 
 int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *cost,
                const hjb_discount *disc, const hjb_controls *controls, const hjb_target *target,
@@ -1015,8 +1253,8 @@ int hjb_destroy(hjb_problem *P) {
 
 namespace {
 
-int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_out, hjb_stats *stats,
-               cudaStream_t st) {
+int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, int li, float *v_out,
+               hjb_stats *stats, cudaStream_t st) {
     bool wform;
     TRY(resolve_form(P, opts ? opts->use_w_form : -1, &wform));
     Prep pr;
@@ -1056,7 +1294,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_ou
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
                              8 / rows, loop_mode()};
     const hjbk::ControlTable ctrl = control_table(P);
-    TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, local_iters(opts, P)));
+    TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, li));
     hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
                          static_cast<float *>(out.dev()), wform, c_over, st);
     CK(cudaEventRecord(R.ev1, st));
@@ -1072,6 +1310,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, float *v_ou
         stats->ms = ms;
         stats->launches = pr.launches + 4 + sweeps;
         stats->tile_rows = P->grid.ndim == 2 ? rows : 0;
+        stats->local_iters = R.local_iters;
     }
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
     if (!R.h_state[0].converged)
@@ -1090,13 +1329,12 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
     if (!P || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL problem or output");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (fixed_shape(P)) return solve_full(P, opts, hjbk::TY, v_out, stats, st);
-    const std::vector<long long> key = {0, P->kind, P->grid.n[0], P->grid.n[1], P->na,
-                                        P->cost.user ? 1 : 0};
-    return tuned_call(key, [&](int rows, double *ms) {
+    const std::string key = tune_key("full", {P->kind, P->grid.n[0], P->grid.n[1], P->grid.n[2],
+                                              P->na, P->nb, P->interp, P->cost.user ? 1 : 0});
+    return tuned_call(key, P, fixed_shape(P), pinned_local_iters(opts), [&](Choice c, double *ms) {
         hjb_stats tmp;
         hjb_stats *sp = stats ? stats : &tmp;
-        const int rc = solve_full(P, opts, rows, v_out, sp, st);
+        const int rc = solve_full(P, opts, c.rows, c.li, v_out, sp, st);
         if (ms) *ms = sp->ms;
         return rc;
     });
@@ -1181,6 +1419,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     TRY(run_loop(R, key, 8, control_table(P), st, local_iters(nullptr, P)));
     // threshold of eq. (rep)
     double delta = ra->delta;
+    double lipschitz = 0.0;
     TRY(P->scratch_u64.ensure(64));
     unsigned long long *d_u64 = P->scratch_u64.as<unsigned long long>();
     CK(cudaMemsetAsync(d_u64, 0, 64, st));
@@ -1202,6 +1441,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
         const double C = ra->C > 0 ? ra->C : 0.0;
         const double q = ra->q > 0 ? ra->q : 1.0;
         delta = 2.0 * (C * std::pow(dxK[0], q) + M * dxK[0]);
+        lipschitz = M;
     }
     OutArr cl;
     TRY(cl.init(coarse_labels_out, NK * sizeof(uint32_t), &P->c_mask));
@@ -1242,12 +1482,16 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
             const SlotState &s = R.h_state[k];
             stats->iterations = s.iters > stats->iterations ? s.iters : stats->iterations;
             stats->node_updates += static_cast<long long>(s.updates);
+            stats->tile_visits += static_cast<long long>(s.visits);
             stats->final_residual = std::fmax(stats->final_residual, s.final_res);
             conv &= s.converged ? 1 : 0;
         }
         stats->converged = conv;
         stats->ties = static_cast<long long>(hc[0]);
         stats->labelled = static_cast<long long>(hc[1]);
+        stats->delta = delta;
+        stats->lipschitz = lipschitz;
+        stats->local_iters = R.local_iters;
         stats->launches = pr.launches + 8 + sweeps + (ra->delta < 0 && ra->M < 0 ? 1 : 0) +
                           (v_aux_out ? m : 0);
         float ms = 0;
@@ -1266,7 +1510,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
 namespace {
 
 int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *opts, int rows,
-              float *v_out, hjb_stats *per_subdomain, hjb_stats *total, cudaStream_t st) {
+              int li, float *v_out, hjb_stats *per_subdomain, hjb_stats *total, cudaStream_t st) {
     bool wform;
     TRY(resolve_form(P, opts ? opts->use_w_form : -1, &wform));
     Prep pr;
@@ -1327,7 +1571,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     // node set alone when its targets are the target nodes inside it; not so
     // with one target component per sub-domain)
     R.diff = own ? nullptr : diff;
-    const int lrc = run_loop(R, key, sweeps_per_body(opts), control_table(P), st, local_iters(opts, P));
+    const int lrc = run_loop(R, key, sweeps_per_body(opts), control_table(P), st, li);
     R.diff = nullptr;
     TRY(lrc);
     hjbh::launch_assemble(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, fine, mask,
@@ -1353,14 +1597,17 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
             s.converged = t.converged;
             s.final_res = t.final_res;
             s.updates = 0ull;
+            s.visits = 0u;
         }
         if (per_subdomain) {
             fill_stats(&per_subdomain[k], s);
             per_subdomain[k].ms = ms;
             per_subdomain[k].tile_rows = P->grid.ndim == 2 ? rows : 0;
+            per_subdomain[k].local_iters = R.local_iters;
         }
         tot.iterations = s.iters > tot.iterations ? s.iters : tot.iterations;
         tot.node_updates += static_cast<long long>(s.updates);
+        tot.tile_visits += static_cast<long long>(s.visits);
         tot.final_residual = std::fmax(tot.final_residual, s.final_res);
         conv &= s.converged ? 1 : 0;
     }
@@ -1368,6 +1615,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     tot.ms = ms;
     tot.launches = pr.launches + 5 + sweeps;
     tot.tile_rows = P->grid.ndim == 2 ? rows : 0;
+    tot.local_iters = R.local_iters;
     if (total) *total = tot;
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
     if (!conv) return fail(HJB_ERR_NOT_CONVERGED, "a sub-domain did not converge");
@@ -1384,14 +1632,14 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     if (!P || !fine_mask || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     TRY(check_opts(opts));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (fixed_shape(P))
-        return solve_dec(P, fine_mask, opts, hjbk::TY, v_out, per_subdomain, total, st);
-    const std::vector<long long> key = {1, P->kind, P->grid.n[0], P->grid.n[1], P->na,
-                                        P->cost.user ? 1 : 0, P->ntargets};
-    return tuned_call(key, [&](int rows, double *ms) {
+    const std::string key = tune_key("decomposed",
+                                     {P->kind, P->grid.n[0], P->grid.n[1], P->grid.n[2], P->na, P->nb,
+                                      P->interp, P->cost.user ? 1 : 0, P->ntargets,
+                                      opts ? opts->subdomain_targets : 0});
+    return tuned_call(key, P, fixed_shape(P), pinned_local_iters(opts), [&](Choice c, double *ms) {
         hjb_stats tmp;
         hjb_stats *tp = total ? total : &tmp;
-        const int rc = solve_dec(P, fine_mask, opts, rows, v_out, per_subdomain, tp, st);
+        const int rc = solve_dec(P, fine_mask, opts, c.rows, c.li, v_out, per_subdomain, tp, st);
         if (ms) *ms = tp->ms;
         return rc;
     });
@@ -1402,7 +1650,7 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
 namespace {
 
 int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_opts *opts, int rows,
-                     float *const *v_out, hjb_stats *per_problem, cudaStream_t st) {
+                     int li, float *const *v_out, hjb_stats *per_problem, cudaStream_t st) {
     hjb_problem *P0 = problems[0];
     if (!P0) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
     bool wform;
@@ -1455,7 +1703,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
                              nullptr, st);
     const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P0), halo, rows,
                              8 / rows, loop_mode()};
-    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st, local_iters(opts, P0)));
+    TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st, li));
     for (int i = 0; i < count; ++i) {
         TRY(outs[i].init(v_out[i], problems[i]->N * sizeof(float), &problems[i]->out_stage));
         hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), i,
@@ -1478,6 +1726,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
             per_problem[i].ms = ms;
             per_problem[i].launches = nl;
             per_problem[i].tile_rows = P0->grid.ndim == 2 ? rows : 0;
+            per_problem[i].local_iters = R.local_iters;
         }
         conv &= R.h_state[i].converged ? 1 : 0;
     }
@@ -1499,15 +1748,15 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
     TRY(check_opts(opts));
     if (!problems[0]) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (fixed_shape(problems[0]))
-        return solve_batch_impl(problems, count, opts, hjbk::TY, v_out, per_problem, st);
     long long nodes = 0;
     for (int i = 0; i < count; ++i) nodes += problems[i] ? problems[i]->N : 0;
-    const std::vector<long long> key = {2, problems[0]->kind, count, nodes, problems[0]->na};
+    const hjb_problem *P0 = problems[0];
+    const std::string key = tune_key("batch", {P0->kind, count, nodes, P0->na, P0->nb, P0->interp,
+                                               P0->cost.user ? 1 : 0});
     std::vector<hjb_stats> tmp(count);
-    return tuned_call(key, [&](int rows, double *ms) {
+    return tuned_call(key, P0, fixed_shape(P0), pinned_local_iters(opts), [&](Choice c, double *ms) {
         hjb_stats *pp = per_problem ? per_problem : tmp.data();
-        const int rc = solve_batch_impl(problems, count, opts, rows, v_out, pp, st);
+        const int rc = solve_batch_impl(problems, count, opts, c.rows, c.li, v_out, pp, st);
         if (ms) *ms = pp[0].ms;
         return rc;
     });
@@ -1959,6 +2208,7 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
         fill_stats(stats, hs);
         stats->launches = (dyn->log_speed ? 1 : 0) + (speed ? 1 : 0) + (dyn->current ? 2 : 0) + 5;
         stats->tile_rows = rows;
+        stats->local_iters = args.local_iters;
     }
     if (herr[0]) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up");
     if (!hs.converged)

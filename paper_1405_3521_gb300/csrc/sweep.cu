@@ -751,6 +751,7 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
             if (tid == 0) {
                 if (m > 0.0f) atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
                 atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot) * li);
+                atomicAdd(&args.state[slot].visits, 1u);
                 unflag(args, S, tile, p);
             }
             if (chg) enqueue_neighbours<1, RY, 0>(args, S, slot, tx, ty, 0, p);
@@ -1014,6 +1015,7 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
             if (tid == 0) {
                 if (m > 0.0f) atomicMax(&args.state[slot].res_bits, __float_as_uint(m));
                 atomicAdd(&args.state[slot].updates, static_cast<unsigned long long>(tot));
+                atomicAdd(&args.state[slot].visits, 1u);
                 unflag(args, S, tile, p);
             }
             if (any) enqueue_neighbours<1, 1, 1>(args, S, slot, tx, ty, tz, p);
@@ -1070,6 +1072,7 @@ __global__ void loop_init_kernel(SlotState *state, Ctl *ctl, int nslots, const u
         st.best_res = INFINITY;
         st.final_res = 0.0f;
         st.updates = 0ull;
+        st.visits = 0u;
         // a sub-domain with the node set of a lower one has the same V
         int twin = -1;
         if (diff && i < 32)

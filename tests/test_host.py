@@ -173,38 +173,24 @@ def test_bench_aggregation_two_ranks():
         assert abs(total - 2000.0 / 11.0e-3) < 1e-6 * total  # units of all ranks / that time
 
 
-def test_bench_traffic_lookup(tmp_path, monkeypatch):
+def test_bench_traffic_lookup(tmp_path):
     """roofline.traffic comes from a committed ncu summary only for the kernel
     sources, tile shape and applications per tile the summary was taken on."""
     sys.path.insert(0, ROOT)
     import bench
-    monkeypatch.delenv("HJB_LOCAL_ITERS", raising=False)
     h = bench.kernel_sources_sha256()
     f = tmp_path / "t.md"
-    f.write_text("- traffic_bytes_per_launch_rows8: 100\n- node_updates_per_launch_rows8: 10\n"
-                 "- traffic_bytes_per_launch_rows4: 200\n- node_updates_per_launch_rows4: 20\n"
-                 "- traffic_bytes_per_launch: 5\n- local_iters: %d\n- sources_sha256: %s\n"
-                 % (bench.LIBRARY_LOCAL_ITERS, h))
-    assert bench.sweep_traffic(str(f), rows=4) == {"bytes_per_launch": 200.0,
-                                                   "node_updates_per_launch": 20.0}
-    assert bench.sweep_traffic(str(f), rows=8)["bytes_per_launch"] == 100.0
-    assert bench.sweep_traffic(str(f), rows=2) == {"bytes_per_launch": 5.0}
-    monkeypatch.setenv("HJB_LOCAL_ITERS", str(bench.LIBRARY_LOCAL_ITERS + 1))
-    assert bench.sweep_traffic(str(f), rows=4) is None
-    monkeypatch.delenv("HJB_LOCAL_ITERS")
+    f.write_text("- traffic_bytes_per_launch_rows8_li6: 100\n- node_updates_per_launch_rows8_li6: 10\n"
+                 "- traffic_bytes_per_launch_rows4_li6: 200\n- node_updates_per_launch_rows4_li6: 20\n"
+                 "- traffic_bytes_per_launch_rows4_li8: 5\n- sources_sha256: %s\n" % h)
+    assert bench.sweep_traffic(str(f), rows=4, local_iters=6) == {
+        "bytes_per_launch": 200.0, "node_updates_per_launch": 20.0}
+    assert bench.sweep_traffic(str(f), rows=8, local_iters=6)["bytes_per_launch"] == 100.0
+    assert bench.sweep_traffic(str(f), rows=4, local_iters=8) == {"bytes_per_launch": 5.0}
+    assert bench.sweep_traffic(str(f), rows=2, local_iters=6) is None
+    assert bench.sweep_traffic(str(f), rows=4, local_iters=4) is None
     f.write_text(f.read_text().replace(h, "0" * 64))
-    assert bench.sweep_traffic(str(f), rows=4) is None
-    # the committed summaries parse and match the current sources
-    assert bench.sweep_traffic(rows=4) is not None
-
-
-def test_library_default_applications_match_bench():
-    """bench.py's copy of the library's default applications per tile (used
-    to match ncu summaries to the timed configuration) is the runtime's."""
-    sys.path.insert(0, ROOT)
-    import bench
-    src = open(os.path.join(ROOT, "paper_1405_3521_gb300", "csrc", "runtime.cu")).read()
-    assert "? 4 : %d)" % bench.LIBRARY_LOCAL_ITERS in src
+    assert bench.sweep_traffic(str(f), rows=4, local_iters=6) is None
 
 
 def test_missing_library_fails_loudly():
@@ -384,3 +370,76 @@ def test_header_serves_a_c_client(libpath, tmp_path, lang):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "ndim" in r.stdout
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every descriptor the Python binding marshals has the size and field
+    offsets that include/hjb.h gives it (a C program prints them)."""
+    import ctypes as C
+
+    from paper_1405_3521_gb300 import _capi
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc not available")
+    structs = {"hjb_grid": _capi.hjb_grid, "hjb_dynamics": _capi.hjb_dynamics,
+               "hjb_cost": _capi.hjb_cost, "hjb_discount": _capi.hjb_discount,
+               "hjb_controls": _capi.hjb_controls, "hjb_target": _capi.hjb_target,
+               "hjb_solve_opts": _capi.hjb_solve_opts, "hjb_stats": _capi.hjb_stats,
+               "hjb_ra_opts": _capi.hjb_ra_opts, "hjb_tune_choice": _capi.hjb_tune_choice}
+    # the binding renames one field (lambda is a Python keyword)
+    cname = {("hjb_discount", "lam"): "lambda"}
+    lines = []
+    for sname, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (sname, sname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));'
+                         % (sname, f, sname, cname.get((sname, f), f)))
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "hjb.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for sname, cls in structs.items():
+        assert int(got[sname]) == C.sizeof(cls), sname
+        for f, _ in cls._fields_:
+            assert int(got[sname + "." + f]) == getattr(cls, f).offset, (sname, f)
+
+
+TUNE_ROUND_TRIP = r"""
+import ctypes as C, json, sys
+from paper_1405_3521_gb300 import _capi
+L = _capi.lib()
+path = sys.argv[1]
+assert L.hjb_tune_clear() == 0
+keys = [b"NVIDIA GB300/152|decomposed|0|1025|1025|1|64|0|0|0|16|0", b"NVIDIA GB300/152|batch|0|512"]
+want = [(4, 6, 13.9), (2, 8, 150.25)]
+for k, (r, l, ms) in zip(keys, want):
+    assert L.hjb_tune_set(k, C.byref(_capi.hjb_tune_choice(r, l, ms))) == 0
+assert L.hjb_tune_set(b"x", C.byref(_capi.hjb_tune_choice(3, 6, 0.0))) == _capi.HJB_ERR_INVALID_ARG
+assert L.hjb_tune_set(b'a"b', C.byref(_capi.hjb_tune_choice(4, 6, 0.0))) == _capi.HJB_ERR_INVALID_ARG
+assert L.hjb_tune_save(path.encode()) == 0
+entries = json.load(open(path))
+assert sorted(e["key"] for e in entries) == sorted(k.decode() for k in keys)
+assert L.hjb_tune_clear() == 0
+out = _capi.hjb_tune_choice()
+assert L.hjb_tune_get(keys[0], C.byref(out)) == _capi.HJB_ERR_INVALID_ARG
+n = C.c_int(0)
+assert L.hjb_tune_load(path.encode(), C.byref(n)) == 0 and n.value == 2
+for k, (r, l, ms) in zip(keys, want):
+    assert L.hjb_tune_get(k, C.byref(out)) == 0
+    assert (out.tile_rows, out.local_iters) == (r, l) and abs(out.ms - ms) < 1e-3
+assert L.hjb_tune_load(b"/nonexistent/tune.json", None) == _capi.HJB_ERR_INVALID_ARG
+print("ok")
+"""
+
+
+def test_tuning_table_round_trips_through_a_file(libpath, tmp_path):
+    """The autotuner's table survives a save and a load through the C ABI
+    (no GPU: the table is host state), and the file is valid JSON."""
+    r = subprocess.run([sys.executable, "-c", TUNE_ROUND_TRIP, str(tmp_path / "tune.json")],
+                       cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
