@@ -230,6 +230,7 @@ typedef struct {
     long long launches;    /* CUDA kernels the call launched */
     int tile_rows;         /* rows of the 2D tiles the sweeps ran on (32 x 8, 4 or 2 nodes:
                               the autotuner's choice or HJB_TILE_ROWS); 0 for 3D */
+    int tile_lanes;        /* lanes per node of those tiles (1, or 2: a_j and -a_j) */
     double delta;          /* hjb_subdomains: the threshold of RA step 3 it applied */
     double lipschitz;      /* hjb_subdomains: the M of that threshold (estimated when
                               hjb_ra_opts.M < 0 and delta < 0; 0 when delta was given) */
@@ -355,9 +356,9 @@ int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_co
 /* Autotuner table (not in the paper: a property of this implementation).
  * hjb_solve, hjb_solve_decomposed and hjb_solve_batch run the sweep with a
  * tile shape (tile_rows: 2D tiles of 32 x 8, 32 x 4 or 32 x 2 nodes, with
- * 1, 2 or 4 control groups per node; fixed at 8 for Dubins, games and P1)
- * and a number of applications of T per staged tile and sweep
- * (local_iters).  The first call for a problem class on a device runs the
+ * 1, 2 or 4 warp groups splitting the controls of a node, or for 32 x 4
+ * tiles lanes = 2 lanes per node; fixed at 8 for Dubins, games and P1) and
+ * a number of applications of T per staged tile and sweep (local_iters).  The first call for a problem class on a device runs the
  * whole call once per candidate on the caller's data and keeps the fastest
  * (ms: its device time) in a table keyed by
  *     "<device name>/<SM count>|<full|decomposed|batch>|<class fields>".
@@ -370,11 +371,13 @@ int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_co
  * runs are bit for bit reproducible; HJB_TUNE=force times even when the
  * table holds a choice.  HJB_TILE_ROWS and HJB_LOCAL_ITERS (or
  * hjb_solve_opts.local_iters) pin their axis.  The file is a JSON array of
- * {"key": ..., "rows": ..., "local_iters": ..., "ms": ...} objects, one per
- * line.  Errors: HJB_ERR_INVALID_ARG (NULL argument, unknown key, a choice
+ * {"key": ..., "rows": ..., "lanes": ..., "local_iters": ..., "ms": ...}
+ * objects, one per line.  HJB_TILE_LANES=1|2 pins the lanes.  Errors: HJB_ERR_INVALID_ARG (NULL argument, unknown key, a choice
  * out of range, a file that cannot be opened). */
 typedef struct {
     int tile_rows;
+    int lanes;         /* 1, or 2 (32 x 4 tiles): two lanes per node taking a_j and -a_j, for
+                          control sets whose second half is the negated first half */
     int local_iters;
     double ms;
 } hjb_tune_choice;

@@ -85,6 +85,7 @@ class hjb_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("node_updates", C.c_longlong),
                 ("final_residual", C.c_double), ("ms", C.c_double), ("ties", C.c_longlong),
                 ("labelled", C.c_longlong), ("launches", C.c_longlong), ("tile_rows", C.c_int),
+                ("tile_lanes", C.c_int),
                 ("delta", C.c_double), ("lipschitz", C.c_double), ("local_iters", C.c_int),
                 ("tile_visits", C.c_longlong)]
 
@@ -93,7 +94,8 @@ class hjb_stats(C.Structure):
 
 
 class hjb_tune_choice(C.Structure):
-    _fields_ = [("tile_rows", C.c_int), ("local_iters", C.c_int), ("ms", C.c_double)]
+    _fields_ = [("tile_rows", C.c_int), ("lanes", C.c_int), ("local_iters", C.c_int),
+                ("ms", C.c_double)]
 
 
 class hjb_ra_opts(C.Structure):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhjb.so")
-SOURCES = ["sweep.cu", "subdomain.cu", "adjoint.cu", "runtime.cu"]
+SOURCES = ["sweep.cu", "subdomain.cu", "adjoint.cu", "coarse.cu", "runtime.cu"]
 HEADERS = ["hjb_internal.cuh", os.path.join("..", "..", "include", "hjb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

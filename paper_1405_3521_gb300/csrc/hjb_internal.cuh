@@ -136,8 +136,9 @@ struct SweepKey {
     int na;      // number of controls
     int halo;    // 2 or 4 (2D), 2 (3D)
     int ty;      // tile rows: 8, 4 or 2 (2D); 8 (3D)
-    int groups;  // control groups per node: 256 / (32 ty)
+    int groups;  // warp groups splitting the controls of a node: 256 / (32 ty lanes)
     int loop;    // 1: the cooperative whole-loop kernel, 0: one sweep per launch
+    int lanes;   // 2D: 1, or 2 lanes per node taking a_j and -a_j (32 x 4 tiles)
 };
 
 // Returns the kernel function for a key (nullptr if unsupported) and the
@@ -160,6 +161,17 @@ void launch_init_values(const hjbk::SlotDesc *slots, int nslots, int max_nodes, 
                         float c_over, const float *v_init, cudaStream_t st);
 void launch_extract(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int slot,
                     float *out, int wform, float c_over, cudaStream_t st);
+
+// RA step 1 on chip (coarse.cu): whether an nx x ny coarse grid with the
+// given interpolation halo fits the cluster kernel's shared memory (and its
+// layout), and the launch solving the m auxiliary problems of slots[0..m)
+// to convergence, one thread-block cluster per problem; the result goes to
+// each slot's buffer 0 and its state (iters, converged, updates).  Returns 0
+// on success.
+int coarse_fits(int nx, int ny, int halo, size_t *smem_bytes, int *nbands, int *band_max);
+int launch_coarse_solve(const hjbk::SlotDesc *slots, hjbk::SlotState *state, int m, int nx, int ny,
+                        int halo, int interp, int wform, const hjbk::ControlTable &ctrl,
+                        float stall_tol, cudaStream_t st);
 
 // Grid geometry shared by the reconstruction kernels.
 struct GridDims {

@@ -159,7 +159,7 @@ struct RunCtx {
     SlotState *h_state = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    hjbh::SweepKey key{-1, -1, -1, -1, -1, -1, -1};
+    hjbh::SweepKey key{-1, -1, -1, -1, -1, -1, -1, -1};
     int last_loop = 0;  // the last run used the cooperative loop kernel
     const uint32_t *diff = nullptr;  // decomposed solve: membership differences (twins)
     int local_iters = 1;             // applications of T per tile and sweep (2D)
@@ -606,6 +606,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     const int n = static_cast<int>(R.slots.size());
     if (R.exec && R.key.dubins == key.dubins && R.key.wform == key.wform && R.key.na == key.na &&
         R.key.halo == key.halo && R.key.ty == key.ty && R.key.groups == key.groups &&
+        R.key.lanes == key.lanes &&
         R.key.loop == key.loop && R.li_in_graph == R.local_iters &&
         R.dq_in_graph == R.dyn_queue &&
         R.spb == spb && R.graph_slots == R.d_slots.p &&
@@ -834,6 +835,7 @@ int check_opts(const hjb_solve_opts *o) {
 
 struct Choice {
     int rows = 8;
+    int lanes = 1;
     int li = 6;
     double ms = 0.0;
 };
@@ -847,6 +849,25 @@ int forced_rows() {
     if (!e) return 0;
     const int r = std::atoi(e);
     return (r == 8 || r == 4 || r == 2) ? r : 0;
+}
+
+int forced_lanes() {
+    const char *e = std::getenv("HJB_TILE_LANES");
+    if (!e) return 0;
+    const int l = std::atoi(e);
+    return (l == 1 || l == 2) ? l : 0;
+}
+
+// The lane split (two lanes per node taking a_j and -a_j, 32 x 4 tiles)
+// needs a control set whose second half is exactly the negated first half,
+// one of the specialised control counts, Q1 and no second player.
+bool lane_split_ok(const hjb_problem *P) {
+    if (!P || P->nb || P->interp != HJB_INTERP_Q1 || P->kind != HJB_DYN_SPEED_CURRENT) return false;
+    if (P->na != 32 && P->na != 64) return false;
+    const int h = P->na / 2;
+    for (int j = 0; j < h; ++j)
+        if (P->ax[j + h] != -P->ax[j] || P->ay[j + h] != -P->ay[j]) return false;
+    return true;
 }
 
 int tune_mode() {  // 0 off, 1 on (default), 2 force
@@ -874,11 +895,14 @@ bool parse_tune_line(const std::string &line, std::string *key, Choice *c) {
         *v = std::strtod(line.c_str() + b + 1, &end);
         return end != line.c_str() + b + 1;
     };
-    double r = 0, l = 0, ms = 0;
+    double r = 0, l = 0, ms = 0, ln = 1;
     if (!num("\"rows\"", &r) || !num("\"local_iters\"", &l)) return false;
     num("\"ms\"", &ms);
-    if (!(r == 8 || r == 4 || r == 2) || l < 1 || l > 16) return false;
+    num("\"lanes\"", &ln);
+    if (!(r == 8 || r == 4 || r == 2) || l < 1 || l > 16 || !(ln == 1 || (ln == 2 && r == 4)))
+        return false;
     c->rows = static_cast<int>(r);
+    c->lanes = static_cast<int>(ln);
     c->li = static_cast<int>(l);
     c->ms = ms;
     return true;
@@ -909,8 +933,10 @@ int save_tune_file(const char *path) {
     std::fprintf(f, "[\n");
     size_t i = 0;
     for (const auto &kv : g_tuned) {
-        std::fprintf(f, "{\"key\": \"%s\", \"rows\": %d, \"local_iters\": %d, \"ms\": %.4f}%s\n",
-                     kv.first.c_str(), kv.second.rows, kv.second.li, kv.second.ms,
+        std::fprintf(f,
+                     "{\"key\": \"%s\", \"rows\": %d, \"lanes\": %d, \"local_iters\": %d, "
+                     "\"ms\": %.4f}%s\n",
+                     kv.first.c_str(), kv.second.rows, kv.second.lanes, kv.second.li, kv.second.ms,
                      ++i < g_tuned.size() ? "," : "");
     }
     std::fprintf(f, "]\n");
@@ -970,6 +996,7 @@ template <typename Run>
 int tuned_call(const std::string &key, const hjb_problem *P, bool fixed_rows, int li_pinned, Run run) {
     const int mode = tune_mode();
     const int frows = fixed_rows ? hjbk::TY : forced_rows();
+    const int flanes = fixed_rows ? 1 : forced_lanes();
     Choice c = default_choice(P);
     bool have = false;
     {
@@ -982,29 +1009,37 @@ int tuned_call(const std::string &key, const hjb_problem *P, bool fixed_rows, in
         }
     }
     if (frows) c.rows = frows;
+    if (flanes) c.lanes = flanes;
     if (li_pinned) c.li = li_pinned;
-    const bool all_pinned = frows && li_pinned;
+    if (c.lanes == 2 && (c.rows != 4 || !lane_split_ok(P))) c.lanes = 1;
+    const bool all_pinned = frows && flanes && li_pinned;
     if (mode == 0 || all_pinned || (have && mode == 1)) return run(c, nullptr);
     std::vector<Choice> cand;
-    const int rows_c[3] = {8, 4, 2};
+    // tile shapes (rows, lanes) x applications per tile
+    const int shapes[4][2] = {{8, 1}, {4, 1}, {4, 2}, {2, 1}};
     const bool game = P && P->nb > 1;
     const int li_c[3] = {game ? 2 : 4, game ? 4 : 6, game ? 6 : 8};
-    for (int r : rows_c) {
-        if (frows && r != frows) continue;
+    for (const auto &sh : shapes) {
+        if (frows && sh[0] != frows) continue;
+        if (flanes && sh[1] != flanes) continue;
+        if (sh[1] == 2 && !lane_split_ok(P)) continue;
         for (int l : li_c) {
             if (li_pinned && l != li_pinned) continue;
             Choice x;
-            x.rows = r;
+            x.rows = sh[0];
+            x.lanes = sh[1];
             x.li = l;
             cand.push_back(x);
         }
-        if (li_pinned && cand.empty()) {
+        if (li_pinned && (cand.empty() || cand.back().rows != sh[0] || cand.back().lanes != sh[1])) {
             Choice x;
-            x.rows = r;
+            x.rows = sh[0];
+            x.lanes = sh[1];
             x.li = li_pinned;
             cand.push_back(x);
         }
     }
+    if (cand.empty()) return run(c, nullptr);
     double best_ms = 1e300;
     size_t best = 0;
     int last_rc = HJB_OK;
@@ -1047,6 +1082,7 @@ int hjb_tune_get(const char *key, hjb_tune_choice *out) {
     auto it = g_tuned.find(key);
     if (it == g_tuned.end()) return fail(HJB_ERR_INVALID_ARG, "no tuned choice for this key");
     out->tile_rows = it->second.rows;
+    out->lanes = it->second.lanes;
     out->local_iters = it->second.li;
     out->ms = it->second.ms;
     return HJB_OK;
@@ -1056,14 +1092,16 @@ int hjb_tune_set(const char *key, const hjb_tune_choice *c) {
     g_err.clear();
     if (!key || !c) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     if (!(c->tile_rows == 8 || c->tile_rows == 4 || c->tile_rows == 2) || c->local_iters < 1 ||
-        c->local_iters > 16)
-        return fail(HJB_ERR_INVALID_ARG, "tile_rows must be 8, 4 or 2 and local_iters 1..16");
+        c->local_iters > 16 || !(c->lanes == 1 || (c->lanes == 2 && c->tile_rows == 4)))
+        return fail(HJB_ERR_INVALID_ARG,
+                    "tile_rows must be 8, 4 or 2, lanes 1 (or 2 with 4 rows) and local_iters 1..16");
     if (std::strchr(key, '"') || std::strchr(key, '\\') || std::strchr(key, '\n'))
         return fail(HJB_ERR_INVALID_ARG, "a key may not hold quotes, backslashes or newlines");
     std::lock_guard<std::mutex> lk(g_tune_mu);
     read_tune_files();
     Choice x;
     x.rows = c->tile_rows;
+    x.lanes = c->lanes;
     x.li = c->local_iters;
     x.ms = c->ms;
     g_tuned[key] = x;
@@ -1253,8 +1291,9 @@ int hjb_destroy(hjb_problem *P) {
 
 namespace {
 
-int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, int li, float *v_out,
+int solve_full(hjb_problem *P, const hjb_solve_opts *opts, const Choice &ch, float *v_out,
                hjb_stats *stats, cudaStream_t st) {
+    const int rows = ch.rows, li = ch.li;
     bool wform;
     TRY(resolve_form(P, opts ? opts->use_w_form : -1, &wform));
     Prep pr;
@@ -1292,7 +1331,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, int li, flo
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), 1, static_cast<int>(P->N), wform, c_over,
                              vinit, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
-                             8 / rows, loop_mode()};
+                             8 / rows / ch.lanes, loop_mode(), ch.lanes};
     const hjbk::ControlTable ctrl = control_table(P);
     TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, li));
     hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
@@ -1310,6 +1349,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, int rows, int li, flo
         stats->ms = ms;
         stats->launches = pr.launches + 4 + sweeps;
         stats->tile_rows = P->grid.ndim == 2 ? rows : 0;
+        stats->tile_lanes = ch.lanes;
         stats->local_iters = R.local_iters;
     }
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
@@ -1334,7 +1374,7 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
     return tuned_call(key, P, fixed_shape(P), pinned_local_iters(opts), [&](Choice c, double *ms) {
         hjb_stats tmp;
         hjb_stats *sp = stats ? stats : &tmp;
-        const int rc = solve_full(P, opts, c.rows, c.li, v_out, sp, st);
+        const int rc = solve_full(P, opts, c, v_out, sp, st);
         if (ms) *ms = sp->ms;
         return rc;
     });
@@ -1412,11 +1452,30 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     TRY(upload_slots(R, st));
     const float c_over = static_cast<float>(P->l_const / P->lambda);
     CK(cudaEventRecord(R.ev0, st));
-    hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform, c_over,
-                             nullptr, st);
-    const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
-                             8 / rows, loop_mode()};
-    TRY(run_loop(R, key, 8, control_table(P), st, local_iters(nullptr, P)));
+    // 2D coarse grids that fit on chip: one thread-block cluster per
+    // auxiliary problem solves it to convergence in shared memory
+    // (HJB_RA=tiles keeps the tile-queue sweep for every grid)
+    const char *ra_env = std::getenv("HJB_RA");
+    const bool on_chip = nd == 2 && !(ra_env && std::strcmp(ra_env, "tiles") == 0) &&
+                         hjbh::coarse_fits(coarse.n[0], coarse.n[1], halo, nullptr, nullptr, nullptr);
+    if (on_chip) {
+        hjbh::launch_loop_init(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), R.d_ctl.as<Ctl>(),
+                               m, st);
+        const int crc = hjbh::launch_coarse_solve(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(),
+                                                  m, coarse.n[0], coarse.n[1], halo, P->interp,
+                                                  wform ? 1 : 0, control_table(P),
+                                                  8.0f * 1.1920929e-7f, st);
+        if (crc) return fail(HJB_ERR_CUDA, "launch of the on-chip coarse solve failed: %s",
+                             cudaGetErrorString(cudaGetLastError()));
+        R.last_loop = 1;
+        R.local_iters = 1;
+    } else {
+        hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform, c_over,
+                                 nullptr, st);
+        const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo,
+                                 rows, 8 / rows, loop_mode(), 1};
+        TRY(run_loop(R, key, 8, control_table(P), st, local_iters(nullptr, P)));
+    }
     // threshold of eq. (rep)
     double delta = ra->delta;
     double lipschitz = 0.0;
@@ -1492,8 +1551,8 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
         stats->delta = delta;
         stats->lipschitz = lipschitz;
         stats->local_iters = R.local_iters;
-        stats->launches = pr.launches + 8 + sweeps + (ra->delta < 0 && ra->M < 0 ? 1 : 0) +
-                          (v_aux_out ? m : 0);
+        stats->launches = pr.launches + (on_chip ? 7 : 8) + sweeps +
+                          (ra->delta < 0 && ra->M < 0 ? 1 : 0) + (v_aux_out ? m : 0);
         float ms = 0;
         cudaEventElapsedTime(&ms, R.ev0, R.ev1);
         stats->ms = ms;
@@ -1509,8 +1568,10 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
 
 namespace {
 
-int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *opts, int rows,
-              int li, float *v_out, hjb_stats *per_subdomain, hjb_stats *total, cudaStream_t st) {
+int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *opts,
+              const Choice &ch, float *v_out, hjb_stats *per_subdomain, hjb_stats *total,
+              cudaStream_t st) {
+    const int rows = ch.rows, li = ch.li;
     bool wform;
     TRY(resolve_form(P, opts ? opts->use_w_form : -1, &wform));
     Prep pr;
@@ -1566,7 +1627,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
-                             8 / rows, loop_mode()};
+                             8 / rows / ch.lanes, loop_mode(), ch.lanes};
     // sub-domains with equal node sets are solved once (V_k depends on the
     // node set alone when its targets are the target nodes inside it; not so
     // with one target component per sub-domain)
@@ -1603,6 +1664,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
             fill_stats(&per_subdomain[k], s);
             per_subdomain[k].ms = ms;
             per_subdomain[k].tile_rows = P->grid.ndim == 2 ? rows : 0;
+            per_subdomain[k].tile_lanes = ch.lanes;
             per_subdomain[k].local_iters = R.local_iters;
         }
         tot.iterations = s.iters > tot.iterations ? s.iters : tot.iterations;
@@ -1615,6 +1677,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     tot.ms = ms;
     tot.launches = pr.launches + 5 + sweeps;
     tot.tile_rows = P->grid.ndim == 2 ? rows : 0;
+    tot.tile_lanes = ch.lanes;
     tot.local_iters = R.local_iters;
     if (total) *total = tot;
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
@@ -1639,7 +1702,7 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     return tuned_call(key, P, fixed_shape(P), pinned_local_iters(opts), [&](Choice c, double *ms) {
         hjb_stats tmp;
         hjb_stats *tp = total ? total : &tmp;
-        const int rc = solve_dec(P, fine_mask, opts, c.rows, c.li, v_out, per_subdomain, tp, st);
+        const int rc = solve_dec(P, fine_mask, opts, c, v_out, per_subdomain, tp, st);
         if (ms) *ms = tp->ms;
         return rc;
     });
@@ -1649,8 +1712,10 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
 
 namespace {
 
-int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_opts *opts, int rows,
-                     int li, float *const *v_out, hjb_stats *per_problem, cudaStream_t st) {
+int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_opts *opts,
+                     const Choice &ch, float *const *v_out, hjb_stats *per_problem,
+                     cudaStream_t st) {
+    const int rows = ch.rows, li = ch.li;
     hjb_problem *P0 = problems[0];
     if (!P0) return fail(HJB_ERR_INVALID_ARG, "NULL problem");
     bool wform;
@@ -1702,7 +1767,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), count, static_cast<int>(maxN), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P0), halo, rows,
-                             8 / rows, loop_mode()};
+                             8 / rows / ch.lanes, loop_mode(), ch.lanes};
     TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st, li));
     for (int i = 0; i < count; ++i) {
         TRY(outs[i].init(v_out[i], problems[i]->N * sizeof(float), &problems[i]->out_stage));
@@ -1726,6 +1791,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
             per_problem[i].ms = ms;
             per_problem[i].launches = nl;
             per_problem[i].tile_rows = P0->grid.ndim == 2 ? rows : 0;
+            per_problem[i].tile_lanes = ch.lanes;
             per_problem[i].local_iters = R.local_iters;
         }
         conv &= R.h_state[i].converged ? 1 : 0;
@@ -1756,7 +1822,7 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
     std::vector<hjb_stats> tmp(count);
     return tuned_call(key, P0, fixed_shape(P0), pinned_local_iters(opts), [&](Choice c, double *ms) {
         hjb_stats *pp = per_problem ? per_problem : tmp.data();
-        const int rc = solve_batch_impl(problems, count, opts, c.rows, c.li, v_out, pp, st);
+        const int rc = solve_batch_impl(problems, count, opts, c, v_out, pp, st);
         if (ms) *ms = pp[0].ms;
         return rc;
     });
@@ -2191,7 +2257,7 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     args.dyn_queue = queue_mode();
     args.ctrl = ctrl;
     hjbh::launch_queue_init(d_slot, 1, tiles, d_ctl, args.qlist[0], args.qflag[0], args.qflag[1], st);
-    const hjbh::SweepKey key{0, wform ? 1 : 0, controls->count, halo, rows, 1, 1};
+    const hjbh::SweepKey key{0, wform ? 1 : 0, controls->count, halo, rows, 1, 1, 1};
     const void *fn = hjbh::sweep_kernel(key, nullptr);
     if (!fn) return fail(HJB_ERR_UNSUPPORTED, "no sweep kernel for this configuration");
     const int gridsz = hjbh::sweep_grid(key);
@@ -2208,6 +2274,7 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
         fill_stats(stats, hs);
         stats->launches = (dyn->log_speed ? 1 : 0) + (speed ? 1 : 0) + (dyn->current ? 2 : 0) + 5;
         stats->tile_rows = rows;
+        stats->tile_lanes = 1;
         stats->local_iters = args.local_iters;
     }
     if (herr[0]) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up");

@@ -558,9 +558,19 @@ __device__ bool grid_barrier_finish(const SweepArgs &args, bool failed) {
 
 // --------------------------------------------------------------------------
 // 2D sweep: f = s(x) a + c(x).  Tile 32 x TYT nodes, halo H (cells) in x
-// and y; the 256 threads form G control groups per node: warp w handles row
-// w / G of the tile for the controls of group w % G, and the groups' partial
-// extrema are combined through shared memory.
+// and y; the 256 threads split the controls of a node in one of two ways:
+//  * LANES = 1: G warp groups -- warp w handles row w / G of the tile for the
+//    controls of group w % G, and the groups' partial extrema are combined
+//    through shared memory;
+//  * LANES = 2 (TYT = 4, G = 1; control sets with a_{j + A/2} = -a_j): the
+//    two lanes 2n, 2n + 1 of a warp handle node n of a 16-node half row, the
+//    even lane with the controls a_j and the odd one with -a_j (j < A/2),
+//    through the same instruction stream with the node's speed factors
+//    negated, and one shuffle combines them.
+// The tile's values are read through a pair layout that is double-buffered
+// across the applications of T to the staged tile: application li reads
+// buffer li & 1 and writes its new values into the other, so one barrier
+// per application (which also takes the early-exit vote) suffices.
 
 template <int H, int TYT, int G>
 struct Smem2d {
@@ -569,36 +579,42 @@ struct Smem2d {
     // each staging buffer starts on a 128-byte boundary (TMA destination rule)
     static constexpr int TILE_STRIDE = (TILE + 31) / 32 * 32;
     float tile[2][TILE_STRIDE];
-    float2 pair[ROWS * PW];
+    float2 pair[2][ROWS * PW];
     uint64_t bar[2];
     int item[2][3];
     int next;  // queue entry of the CTA's next item
     float red[THREADS / 32];
     int cnt[THREADS / 32];
-    float part[G][TYT][32];
+    float part[G > 1 ? G : 1][G > 1 ? TYT : 1][32];
 };
 
 // One sweep over this launch's tile queue by one CTA.  `uses` counts the
 // TMA phases consumed per staging buffer and persists across sweeps.
-template <int NA, bool WFORM, int H, int TYT, int G>
+template <int NA, bool WFORM, int H, int TYT, int G, int LANES>
 __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> &sm,
                                        unsigned uses[2]) {
     using SM = Smem2d<H, TYT, G>;
     constexpr int ROWS = SM::ROWS;
     constexpr int TILE = SM::TILE;
     constexpr int RY = (H + TYT - 1) / TYT;  // tile neighbourhood reached by the halo
+    constexpr uint32_t PAIR_BYTES = ROWS * PW * 8;
+    static_assert(LANES == 1 || (LANES == 2 && G == 1 && TYT == 4 && NA > 0),
+                  "the lane split pairs a_j with -a_j in 32 x 4 tiles");
     const Ctl *ctl = args.ctl;
     const int tid = threadIdx.x;
-    const int lx = tid & 31, warp = tid >> 5;
-    const int grp = warp % G, ly = warp / G;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int grp = LANES == 2 ? (lane & 1) : warp % G;
+    const int ly = LANES == 2 ? (warp >> 1) : warp / G;
+    const int lx = LANES == 2 ? ((warp & 1) << 4) + (lane >> 1) : lane;
     const int p = static_cast<int>(*reinterpret_cast<const volatile unsigned *>(&ctl->sweep) & 1u);
     const int src = p, dst = p ^ 1;
     const int nitems = *reinterpret_cast<const volatile int *>(&ctl->qcount[p]);
     const int *qlist = args.qlist[p];
-    // pair (ky, kx) sits at byte (ky - 1) * 512 + kx * 8 of sm.pair, with
-    // kx = bits(mx) - 2^23 bits and ky = bits(my) - 2^23 bits (see q1_pairs)
-    const uint32_t K = smem_u32(sm.pair) - (static_cast<uint32_t>(TWO23_BITS) << 9) -
-                       (static_cast<uint32_t>(TWO23_BITS) << 3) - 512u;
+    // pair (ky, kx) of buffer c sits at byte c * PAIR_BYTES + (ky - 1) * 512 +
+    // kx * 8 of sm.pair, with kx = bits(mx) - 2^23 bits and ky = bits(my) -
+    // 2^23 bits (see q1_pairs)
+    const uint32_t K0 = smem_u32(sm.pair[0]) - (static_cast<uint32_t>(TWO23_BITS) << 9) -
+                        (static_cast<uint32_t>(TWO23_BITS) << 3) - 512u;
 
     // thread 0: stage item v into buffer b (no copy for a finished slot)
     auto issue = [&](int v, int b) {
@@ -645,11 +661,14 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
                 mbar_wait_bounded(&sm.bar[b ^ 1], uses[b ^ 1] & 1u);
             break;
         }
-        // pair layout: (raw[r][c], raw[r][c+1]) for the TW-1 columns a foot can use
-        float *T = sm.tile[b];
+        // both pair buffers: (raw[r][c], raw[r][c+1]) for the TW-1 columns a
+        // foot can use (the halo is the same in both and never rewritten)
+        const float *T = sm.tile[b];
         for (int i = tid; i < ROWS * (TW - 1); i += THREADS) {
             const int r = i / (TW - 1), c = i - r * (TW - 1);
-            sm.pair[r * PW + c] = make_float2(T[r * TW + c], T[r * TW + c + 1]);
+            const float2 q = make_float2(T[r * TW + c], T[r * TW + c + 1]);
+            sm.pair[0][r * PW + c] = q;
+            sm.pair[1][r * PW + c] = q;
         }
         const int nx = S.nx, ny = S.ny;
         const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
@@ -676,7 +695,8 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
                 cx = c.x;
                 cy = c.y;
             }
-            S2 = make_float2(sx * S.hx, sy * S.hy);
+            const float sg = (LANES == 2 && grp) ? -1.0f : 1.0f;  // the odd lane takes -a_j
+            S2 = make_float2(sg * sx * S.hx, sg * sy * S.hy);
             O02 = make_float2(cx * S.hx, cy * S.hy);
             if (!WFORM && S.cost) add = S.gamma * S.cost[gi];
         }
@@ -684,6 +704,8 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
                                          static_cast<float>(ly + H + 1));
         const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
                               (ty * TYT >= H) && (ty * TYT + TYT - 1 + H <= ny - 1);
+        // this node's two entries in the pair layout: (v, right) and (left, v)
+        const int pr = (ly + H) * PW + lx + XPAD;
         __syncthreads();
         // args.local_iters applications of T to the tile's nodes, the halo
         // held at the previous sweep's values: each application reads the
@@ -691,22 +713,25 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
         float vnew = vold;
         int li = 0;  // applications done
         for (;;) {
+            const uint32_t K = K0 + static_cast<uint32_t>(li & 1) * PAIR_BYTES;
             float best = WFORM ? -INFINITY : INFINITY;
             if (isfree) {
                 if (interior) {
-                    best = controls_interior<NA, G, WFORM>(grp, args.ctrl, K, S2,
-                                                          __fadd2_rn(BASE2, O02), best);
+                    best = controls_interior<NA, LANES == 2 ? 2 : G, WFORM>(
+                        LANES == 2 ? 0 : grp, args.ctrl, K, S2, __fadd2_rn(BASE2, O02), best);
                 } else {
                     EdgeBounds eb;
                     eb.lox = -static_cast<float>(gx);
                     eb.hix = static_cast<float>(nx - 1 - gx);
                     eb.loy = -static_cast<float>(gy);
                     eb.hiy = static_cast<float>(ny - 1 - gy);
-                    best = controls_edge<NA, G, WFORM>(grp, args.ctrl, K, S2, O02, eb, BASE2,
-                                                      S.vout, best);
+                    best = controls_edge<NA, LANES == 2 ? 2 : G, WFORM>(
+                        LANES == 2 ? 0 : grp, args.ctrl, K, S2, O02, eb, BASE2, S.vout, best);
                 }
             }
-            if constexpr (G > 1) {
+            if constexpr (LANES == 2) {
+                best = pick<WFORM>(best, __shfl_xor_sync(0xffffffffu, best, 1));
+            } else if constexpr (G > 1) {
                 sm.part[grp][ly][lx] = best;
                 __syncthreads();
                 if (grp == 0) {
@@ -717,24 +742,19 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
             const float vprev = vnew;
             if (mine) vnew = WFORM ? S.beta * best : fmaf(S.beta, best, add);
             if (++li >= args.local_iters) break;
-            // all reads of the pairs done; stop early once the tile is stable
-            if (!__syncthreads_or(mine && vnew != vprev)) break;
             if (mine) {
-                T[(ly + H) * TW + lx + XPAD] = vnew;
-                fence_proxy_async_smem();  // the buffer takes a later TMA copy
+                float2 *P = sm.pair[li & 1];
+                P[pr].x = vnew;
+                P[pr - 1].y = vnew;
             }
-            __syncthreads();
-            for (int i = tid; i < TYT * (TX + 1); i += THREADS) {
-                const int r = H + i / (TX + 1), c = XPAD - 1 + i % (TX + 1);
-                sm.pair[r * PW + c] = make_float2(T[r * TW + c], T[r * TW + c + 1]);
-            }
-            __syncthreads();
+            // the new values are visible; stop early once the tile is stable
+            if (!__syncthreads_or(mine && vnew != vprev)) break;
         }
         if (mine) S.V[dst][static_cast<long long>(gy) * S.pitch + gx] = vnew;
         const float r = warp_max(mine ? fabsf(vnew - vold) : 0.0f);
         const unsigned fm = __ballot_sync(0xffffffffu, mine);
         const unsigned cm = __ballot_sync(0xffffffffu, mine && (vnew != vold));
-        if (lx == 0) {
+        if (lane == 0) {
             sm.red[warp] = r;
             sm.cnt[warp] = __popc(fm) | (cm ? 0x10000 : 0);
         }
@@ -771,9 +791,9 @@ __device__ __forceinline__ void init_bars(Smem2d<H, TYT, G> &sm) {
 }
 
 // One sweep per launch (the body of the CUDA-graph WHILE loop).
-template <int NA, bool WFORM, int H, int TYT, int G>
+template <int NA, bool WFORM, int H, int TYT, int G, int LANES>
 __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(const __grid_constant__ SweepArgs args) {
-    static_assert(TYT * G * 32 == THREADS, "tile rows x control groups must fill the CTA");
+    static_assert(TYT * G * LANES * 32 == THREADS, "tile rows x control groups must fill the CTA");
     __shared__ alignas(128) Smem2d<H, TYT, G> sm;
     const int p = static_cast<int>(args.ctl->sweep & 1u);
     const int nitems = args.ctl->qcount[p];
@@ -781,20 +801,20 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) sweep2d_kernel(cons
     if (static_cast<int>(blockIdx.x) >= working) return;
     init_bars(sm);
     unsigned uses[2] = {0u, 0u};
-    const bool failed = pass2d<NA, WFORM, H, TYT, G>(args, sm, uses);
+    const bool failed = pass2d<NA, WFORM, H, TYT, G, LANES>(args, sm, uses);
     cta_done(args, failed, working);
 }
 
 // The whole convergence loop in one cooperative launch: sweeps separated by
 // a grid barrier that also takes the convergence decision.
-template <int NA, bool WFORM, int H, int TYT, int G>
+template <int NA, bool WFORM, int H, int TYT, int G, int LANES>
 __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) loop2d_kernel(const __grid_constant__ SweepArgs args) {
-    static_assert(TYT * G * 32 == THREADS, "tile rows x control groups must fill the CTA");
+    static_assert(TYT * G * LANES * 32 == THREADS, "tile rows x control groups must fill the CTA");
     __shared__ alignas(128) Smem2d<H, TYT, G> sm;
     init_bars(sm);
     unsigned uses[2] = {0u, 0u};
     for (;;) {
-        const bool failed = pass2d<NA, WFORM, H, TYT, G>(args, sm, uses);
+        const bool failed = pass2d<NA, WFORM, H, TYT, G, LANES>(args, sm, uses);
         if (!grid_barrier_finish(args, failed)) break;
     }
 }
@@ -1194,31 +1214,37 @@ const void *sweep_kernel(const SweepKey &k, size_t *smem) {
         return k.wform ? reinterpret_cast<const void *>(&sweep3d_kernel<true>)
                        : reinterpret_cast<const void *>(&sweep3d_kernel<false>);
     }
-#define HJB_PICK(NA_, H_, TY_, G_)                                                              \
-    if (k.halo == H_ && k.ty == TY_ && k.groups == G_) {                                         \
+#define HJB_PICK(NA_, H_, TY_, G_, L_)                                                          \
+    if (k.halo == H_ && k.ty == TY_ && k.groups == G_ && k.lanes == L_) {                        \
         if (k.loop)                                                                              \
-            return k.wform                                                                       \
-                       ? reinterpret_cast<const void *>(&loop2d_kernel<NA_, true, H_, TY_, G_>)  \
-                       : reinterpret_cast<const void *>(&loop2d_kernel<NA_, false, H_, TY_, G_>); \
-        return k.wform ? reinterpret_cast<const void *>(&sweep2d_kernel<NA_, true, H_, TY_, G_>)  \
-                       : reinterpret_cast<const void *>(&sweep2d_kernel<NA_, false, H_, TY_, G_>); \
+            return k.wform ? reinterpret_cast<const void *>(                                     \
+                                 &loop2d_kernel<NA_, true, H_, TY_, G_, L_>)                     \
+                           : reinterpret_cast<const void *>(                                     \
+                                 &loop2d_kernel<NA_, false, H_, TY_, G_, L_>);                   \
+        return k.wform ? reinterpret_cast<const void *>(&sweep2d_kernel<NA_, true, H_, TY_, G_, L_>) \
+                       : reinterpret_cast<const void *>(                                         \
+                             &sweep2d_kernel<NA_, false, H_, TY_, G_, L_>);                       \
     }
 #define HJB_PICK_SHAPES(NA_, H_) \
-    HJB_PICK(NA_, H_, 8, 1)      \
-    HJB_PICK(NA_, H_, 4, 2)      \
-    HJB_PICK(NA_, H_, 2, 4)
+    HJB_PICK(NA_, H_, 8, 1, 1)   \
+    HJB_PICK(NA_, H_, 4, 2, 1)   \
+    HJB_PICK(NA_, H_, 2, 4, 1)
     switch (k.na) {
         case 64:
             HJB_PICK_SHAPES(64, 2)
             HJB_PICK_SHAPES(64, 4)
+            HJB_PICK(64, 2, 4, 1, 2)
+            HJB_PICK(64, 4, 4, 1, 2)
             break;
         case 32:
             HJB_PICK_SHAPES(32, 2)
             HJB_PICK_SHAPES(32, 4)
+            HJB_PICK(32, 2, 4, 1, 2)
+            HJB_PICK(32, 4, 4, 1, 2)
             break;
         case -1:  // generic count, P1 interpolation: one control group, 8-row tiles
-            HJB_PICK(-1, 2, 8, 1)
-            HJB_PICK(-1, 4, 8, 1)
+            HJB_PICK(-1, 2, 8, 1, 1)
+            HJB_PICK(-1, 4, 8, 1, 1)
             break;
         default:
             HJB_PICK_SHAPES(0, 2)

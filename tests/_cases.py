@@ -47,3 +47,17 @@ def to_np(x):
     except ImportError:
         pass
     return np.asarray(x)
+
+
+def projection_reads(nk, r, coarse_nodes, shape):
+    """Fine nodes (2D, grid shape (nx, ny)) whose projection through Con reads
+    one of the given coarse nodes (a bool array over the nk[0] x nk[1] coarse
+    grid): every fine node of a coarse cell that has such a vertex."""
+    nx, ny = shape
+    out = np.zeros((ny, nx), dtype=bool)
+    for jy, jx in zip(*np.nonzero(np.asarray(coarse_nodes).reshape(nk[1], nk[0]))):
+        for cy in (jy - 1, jy):
+            for cx in (jx - 1, jx):
+                if 0 <= cy <= nk[1] - 2 and 0 <= cx <= nk[0] - 2:
+                    out[cy * r:cy * r + r + 1, cx * r:cx * r + r + 1] = True
+    return out.reshape(-1)

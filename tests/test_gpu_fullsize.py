@@ -23,7 +23,7 @@ import numpy as np
 import pytest
 
 import synthetic as S
-from _cases import gpu_problem, oracle_problem, to_np
+from _cases import gpu_problem, oracle_problem, projection_reads, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -89,18 +89,6 @@ def _golden(name):
         return json.load(f)
 
 
-def _projection_reads(nk, r, coarse_nodes, n):
-    """Fine nodes whose projection through Con reads one of the given coarse
-    nodes: every fine node of a coarse cell that has such a vertex."""
-    out = np.zeros((n, n), dtype=bool)
-    for jy, jx in zip(*np.nonzero(coarse_nodes.reshape(nk[1], nk[0]))):
-        for cy in (jy - 1, jy):
-            for cx in (jx - 1, jx):
-                if 0 <= cy <= nk[1] - 2 and 0 <= cx <= nk[0] - 2:
-                    out[cy * r:cy * r + r + 1, cx * r:cx * r + r + 1] = True
-    return out.reshape(-1)
-
-
 def test_zermelo_1025_decomposed_at_the_benchmark_threshold(hjb, orc):
     """The benchmark's step, checked against the oracle at the same
     threshold (c2_decomposed_1025.json, written by oracle/ alone):
@@ -149,7 +137,7 @@ def test_zermelo_1025_decomposed_at_the_benchmark_threshold(hjb, orc):
         close = np.abs(np.abs(Vaux_o[k] - vmin_o) - delta_o) <= band
         near |= close & (((diff >> k) & 1) == 1)
     assert ((diff != 0) & ~near).sum() == 0
-    reads = _projection_reads(nk, r, diff != 0, n)
+    reads = projection_reads(nk, r, diff != 0, (n, n))
     f = to_np(fine).astype(np.uint32)
     assert np.array_equal(f[~reads], fine_o[~reads])
     assert reads.sum() <= 4 * (r + 1) ** 2 * int((diff != 0).sum())
@@ -281,3 +269,33 @@ def test_adjoint_1025_finite_differences(hjb):
         Lm, _, _ = loss(th - eps * dk)
         fd = (Lp - Lm) / (2 * eps)
         assert abs(fd - g @ dk) <= 1e-3 * (np.abs(g) @ np.abs(dk)), (fd, g @ dk)
+
+
+def test_adjoint_1025_per_entry_finite_differences(hjb):
+    """hjb_backward on the GPU's own forward solve against FP64 central
+    finite differences of the loss at 64 seeded non-target entries of theta
+    (c5_fd_1025.json, written by oracle/ alone: eps = 1e-5, Gauss-Seidel
+    solves warm-started from the converged V to 1e-15).  Entries where the
+    optimal policy changes between theta_i +- eps at a node that carries
+    adjoint mass are kinks -- the loss is not differentiable there -- and are
+    counted, not compared.  Every other entry agrees within 1e-3 relative."""
+    import torch
+    gold = _golden("c5_fd_1025.json")
+    d = S.c5()
+    p = gpu_problem(hjb, d)
+    V, _ = hjb.solve(p)
+    pts = torch.as_tensor(np.asarray(d["points"], np.float32)).cuda()
+    _, gV = hjb.point_values(p, V, pts)
+    g, st = hjb.backward(p, V, gV, wrt=0)
+    assert st["converged"] in (1, 2)
+    g = to_np(g).astype(np.float64)
+    checked = 0
+    worst = 0.0
+    for e in gold["entries"]:
+        if e["kink"]:
+            continue
+        rel = abs(g[e["index"]] - e["fd"]) / abs(e["fd"])
+        worst = max(worst, rel)
+        assert rel <= 1e-3, (e["xy"], g[e["index"]], e["fd"])
+        checked += 1
+    assert checked >= 48, (checked, gold["kinks"])

@@ -1,0 +1,62 @@
+"""The autotuner's choice persists across processes (HJB_TUNE_CACHE), and a
+process that reads it reproduces the solve bit for bit.  The iterates do
+not depend on the order in which CTAs take tiles, only on the tile shape and
+the applications per tile, so equal choices give equal bits."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+RUN = r"""
+import json, sys
+sys.path.insert(0, %r)
+sys.path.insert(0, %r)
+import numpy as np
+import torch
+import paper_1405_3521_gb300 as hjb
+import synthetic as S
+from _cases import gpu_problem, to_np
+d = S.c2(n=257, A=64, ntargets=6)
+p = gpu_problem(hjb, d)
+V, st = hjb.solve(p)
+np.save(sys.argv[1], to_np(V))
+print(json.dumps({k: st[k] for k in ("iterations", "tile_rows", "tile_lanes", "local_iters",
+                                     "node_updates")}))
+""" % (ROOT, os.path.join(ROOT, "tests"))
+
+
+def _run(tmp_path, name, **env_over):
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("HJB_TUNE", "HJB_TILE_ROWS", "HJB_TILE_LANES", "HJB_LOCAL_ITERS",
+                        "HJB_TUNE_CACHE")}
+    env["HJB_TUNE_CACHE"] = str(tmp_path / "tune.json")
+    env.update(env_over)
+    out = tmp_path / (name + ".npy")
+    r = subprocess.run([sys.executable, "-c", RUN, str(out)], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return np.load(out), json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_tuned_choice_persists_across_processes(tmp_path):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Va, sa = _run(tmp_path, "a", HJB_TUNE="force")  # times the candidates, writes the file
+    entries = json.load(open(tmp_path / "tune.json"))
+    mine = [e for e in entries if "|full|" in e["key"]]
+    assert len(mine) == 1
+    assert (mine[0]["rows"], mine[0]["lanes"], mine[0]["local_iters"]) == (
+        sa["tile_rows"], sa["tile_lanes"], sa["local_iters"])
+    Vb, sb = _run(tmp_path, "b")                 # reads the file, no timing
+    Vc, sc = _run(tmp_path, "c", HJB_TUNE="off")  # never times
+    assert sa == sb == sc
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert np.array_equal(Vb.view(np.uint32), Vc.view(np.uint32))
