@@ -613,33 +613,19 @@ def main():
         return Vbar, fine, rst, tot
 
     if args.profile:
-        for rep in range(2):
-            if args.profile == "full":
-                _, st = hjb.solve(p)
-                info = st
-            elif args.profile == "ra":
-                fine, _, _, rst = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
-                info = rst
-            else:
-                # the decomposed fine solve once per 2D tile shape, in the
-                # order 32 x 8, 32 x 4, 32 x 2 (the RA coarse solve first), or
-                # only the shape HJB_TILE_ROWS forces
-                fine, _, _, rst = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
-                f = fine.cpu().numpy().astype(np.uint32)
-                info = {}
-                forced = os.environ.get("HJB_TILE_ROWS")
-                for r in ((int(forced),) if forced else (8, 4, 2)):
-                    os.environ["HJB_TILE_ROWS"] = str(r)
-                    _, per, tot = hjb.solve_decomposed(p, fine)
-                    info[r] = {"total": tot, "per": [(s_["iterations"], int(((f >> k) & 1).sum()))
-                                                     for k, s_ in enumerate(per)]}
-                if forced:
-                    os.environ["HJB_TILE_ROWS"] = forced
-                else:
-                    del os.environ["HJB_TILE_ROWS"]
-                torch.cuda.synchronize()
-                break
-            torch.cuda.synchronize()
+        # one solve of the chosen path for a profiler: set HJB_TUNE=off and
+        # pin HJB_TILE_ROWS / HJB_TILE_LANES / HJB_LOCAL_ITERS so that no
+        # tuning runs precede it
+        if args.profile == "full":
+            _, info = hjb.solve(p)
+        elif args.profile == "ra":
+            _, _, _, info = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
+        else:
+            fine, _, _, rst = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
+            _, per, tot = hjb.solve_decomposed(p, fine)
+            info = {"ra": rst, "total": tot,
+                    "per": [(s_["iterations"], s_["node_updates"]) for s_ in per]}
+        torch.cuda.synchronize()
         print(json.dumps(info))
         return
 

@@ -372,7 +372,11 @@ int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_co
  * table holds a choice.  HJB_TILE_ROWS and HJB_LOCAL_ITERS (or
  * hjb_solve_opts.local_iters) pin their axis.  The file is a JSON array of
  * {"key": ..., "rows": ..., "lanes": ..., "local_iters": ..., "ms": ...}
- * objects, one per line.  HJB_TILE_LANES=1|2 pins the lanes.  Errors: HJB_ERR_INVALID_ARG (NULL argument, unknown key, a choice
+ * objects, one per line.  HJB_TILE_LANES=1|2 pins the lanes.  The
+ * reconstruction (hjb_subdomains, key op "ra") tunes its auxiliary solves
+ * the same way; there tile_rows = 1 selects the on-chip solve of a 2D
+ * coarse grid (one thread-block cluster per auxiliary problem, iterating in
+ * shared memory), and HJB_RA=tiles|chip pins the path.  Errors: HJB_ERR_INVALID_ARG (NULL argument, unknown key, a choice
  * out of range, a file that cannot be opened). */
 typedef struct {
     int tile_rows;

@@ -78,6 +78,8 @@ def _lib_handle():
             lib.ohjb_ra.argtypes = [P, vp, d, d, d, i, vp, vp, i]
             lib.ohjb_ra.restype = C.c_longlong
             lib.ohjb_project.argtypes = [P, vp, vp, vp]
+            lib.ohjb_ra_split.argtypes = [P, vp, d, d, d, i, i, d, i, vp, vp, C.POINTER(i)]
+            lib.ohjb_ra_split.restype = C.c_longlong
             lib.ohjb_isa.argtypes = [P, vp, d, i, i, vp, vp, vp, i, i]
             lib.ohjb_isa.restype = C.c_longlong
             lib.ohjb_policy.argtypes = [P, vp, vp, i]
@@ -269,6 +271,27 @@ def project(p: Problem, stride, coarse_labels):
     out = np.empty(p.N, dtype=np.uint32)
     _lib_handle().ohjb_project(p._ref(), st, cl.ctypes.data, out.ctypes.data)
     return out
+
+
+def ra_split(p: Problem, stride, delta, max_splits, min_gain=0.05, h_coarse=None, tol=1e-12,
+             max_iters=1_000_000, nthreads=1):
+    """Recursive re-splitting of the target components (Conclusions; reading
+    R22): the component with the largest sub-domain is split in two, and the
+    split is kept when both parts' sub-domains are smaller than (1 -
+    min_gain) times its own.  Returns (components [N] int32, fine mask [N],
+    m, largest)."""
+    st = (C.c_int * 3)(*(list(stride) + [1] * (3 - len(stride))))
+    hc = p.h * stride[0] if h_coarse is None else float(h_coarse)
+    comp = np.empty(p.N, dtype=np.int32)
+    fine = np.empty(p.N, dtype=np.uint32)
+    m = C.c_int(0)
+    largest = _lib_handle().ohjb_ra_split(p._ref(), st, hc, float(delta), float(tol),
+                                          int(max_iters), int(max_splits), float(min_gain),
+                                          int(nthreads),
+                                          comp.ctypes.data, fine.ctypes.data, C.byref(m))
+    if largest < 0:
+        raise ValueError("bad stride")
+    return comp, fine, int(m.value), int(largest)
 
 
 def isa(p: Problem, fine_mask, tol=1e-12, max_iters=1_000_000, gs=False, keep_vk=False,

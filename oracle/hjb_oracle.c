@@ -702,6 +702,140 @@ long long ohjb_isa(const ohjb_problem *p, const uint32_t *fine_mask, double tol,
 }
 
 /* ---------------------------------------------------------------------- */
+/* Recursive re-splitting of the target components (Conclusions: the       */
+/* unbalanced sub-domains of Example ex3 can be balanced by refining the   */
+/* division of Gamma recursively, in a few steps).  Reading R22: each step */
+/* splits the component whose projected sub-domain is largest (the lowest  */
+/* index on ties) in two, along the x or y grid axis with the larger index */
+/* extent of its fine target nodes (x on ties): the nodes whose index on   */
+/* that axis is at most s keep the component, the others form a new one,  */
+/* with s the smallest index holding at least half of the nodes (the next  */
+/* lower occupied index when that would leave the second part empty).  RA  */
+/* and the projection are re-run on the new division with the same        */
+/* threshold (V = min_k V_k, and hence the estimated M, does not change    */
+/* with the division); the step is kept only when the sub-domains of both  */
+/* parts are smaller than (1 - min_gain) times the split one's, and the    */
+/* refinement stops at the first step that is not (the largest sub-domain  */
+/* no longer shrinks by splitting its component), after max_splits steps,  */
+/* at 32 components, or when the chosen component cannot be split (a       */
+/* single index on the axis).                                              */
+
+/* RA steps 1-3 and the projection for the division `comp` into m
+ * components; returns the largest sub-domain (nodes), sizes[k] its nodes. */
+static long long ra_division(const ohjb_problem *p, const int32_t *comp, int m, const int stride[3],
+                             double h_coarse, double delta, double tol, int max_iters,
+                             int nthreads, uint32_t *fine, long long *sizes) {
+    ohjb_problem q = *p;
+    q.target = comp;
+    q.ntargets = m;
+    int nK[3];
+    if (ohjb_coarse_shape(&q, stride, nK)) return -1;
+    long long NK = (long long)nK[0] * nK[1] * (p->ndim > 2 ? nK[2] : 1);
+    double *Vaux = (double *)malloc(sizeof(double) * m * NK);
+    uint32_t *cl = (uint32_t *)malloc(sizeof(uint32_t) * NK);
+    ohjb_ra(&q, stride, h_coarse, delta, tol, max_iters, Vaux, cl, nthreads);
+    ohjb_project(&q, stride, cl, fine);
+    long long N = node_count(p), largest = 0;
+    for (int k = 0; k < m; ++k) {
+        sizes[k] = 0;
+        for (long long i = 0; i < N; ++i) sizes[k] += (fine[i] >> k) & 1u;
+        if (sizes[k] > largest) largest = sizes[k];
+    }
+    free(Vaux);
+    free(cl);
+    return largest;
+}
+
+/* Split component k (1-based id k + 1) into k and m + 1; returns 0 when it
+ * cannot be split. */
+static int split_component(const ohjb_problem *p, int32_t *comp, int k, int m) {
+    long long N = node_count(p);
+    int lo[2] = {p->n[0], p->n[1]}, hi[2] = {-1, -1};
+    long long cnt = 0;
+    for (long long i = 0; i < N; ++i) {
+        if (comp[i] != k + 1) continue;
+        int idx[3];
+        unflatten(p, i, idx);
+        for (int d = 0; d < 2; ++d) {
+            if (idx[d] < lo[d]) lo[d] = idx[d];
+            if (idx[d] > hi[d]) hi[d] = idx[d];
+        }
+        ++cnt;
+    }
+    if (cnt < 2) return 0;
+    int axis = (hi[0] - lo[0]) >= (hi[1] - lo[1]) ? 0 : 1;
+    int n = p->n[axis];
+    long long *hist = (long long *)calloc(n, sizeof(long long));
+    for (long long i = 0; i < N; ++i) {
+        if (comp[i] != k + 1) continue;
+        int idx[3];
+        unflatten(p, i, idx);
+        hist[idx[axis]] += 1;
+    }
+    long long half = (cnt + 1) / 2, cum = 0;
+    int s = -1;
+    for (int j = 0; j < n; ++j) {
+        cum += hist[j];
+        if (cum >= half) {
+            s = j;
+            break;
+        }
+    }
+    if (cum == cnt) { /* everything at or below s: use the next lower occupied index */
+        int t = s - 1;
+        while (t >= 0 && hist[t] == 0) --t;
+        s = t;
+    }
+    free(hist);
+    if (s < 0) return 0;
+    for (long long i = 0; i < N; ++i) {
+        if (comp[i] != k + 1) continue;
+        int idx[3];
+        unflatten(p, i, idx);
+        if (idx[axis] > s) comp[i] = m + 1;
+    }
+    return 1;
+}
+
+/* Recursive re-splitting; comp_out [N] receives the final division, fine
+ * [N] its projected sub-domains, *m_out its number of components; returns
+ * the largest sub-domain (nodes), or -1 on a bad stride. */
+long long ohjb_ra_split(const ohjb_problem *p, const int stride[3], double h_coarse,
+                        double delta, double tol, int max_iters, int max_splits, double min_gain,
+                        int nthreads, int32_t *comp_out, uint32_t *fine, int *m_out) {
+    long long N = node_count(p);
+    int m = p->ntargets;
+    long long sizes[32];
+    memcpy(comp_out, p->target, sizeof(int32_t) * N);
+    long long largest = ra_division(p, comp_out, m, stride, h_coarse, delta, tol, max_iters,
+                                    nthreads, fine, sizes);
+    if (largest < 0) return -1;
+    int32_t *trial = (int32_t *)malloc(sizeof(int32_t) * N);
+    uint32_t *tfine = (uint32_t *)malloc(sizeof(uint32_t) * N);
+    long long tsizes[32];
+    for (int step = 0; step < max_splits && m < 32; ++step) {
+        int k = 0;
+        for (int j = 1; j < m; ++j)
+            if (sizes[j] > sizes[k]) k = j;
+        memcpy(trial, comp_out, sizeof(int32_t) * N);
+        if (!split_component(p, trial, k, m)) break;
+        long long tl = ra_division(p, trial, m + 1, stride, h_coarse, delta, tol, max_iters,
+                                   nthreads, tfine, tsizes);
+        double lim = (1.0 - min_gain) * (double)sizes[k];
+        if ((double)tsizes[k] > lim || (double)tsizes[m] > lim) break;
+        memcpy(comp_out, trial, sizeof(int32_t) * N);
+        memcpy(fine, tfine, sizeof(uint32_t) * N);
+        memcpy(sizes, tsizes, sizeof tsizes);
+        largest = tl;
+        ++m;
+    }
+    free(trial);
+    free(tfine);
+    *m_out = m;
+    return largest;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Adjoint of the converged fixed point with the optimal policy frozen.    */
 /* (The paper has no adjoint; this is the plain linear algebra of          */
 /* V = beta P_pi V + b: the transposed system (I - beta P_pi)^T lam = g.)  */

@@ -899,7 +899,8 @@ bool parse_tune_line(const std::string &line, std::string *key, Choice *c) {
     if (!num("\"rows\"", &r) || !num("\"local_iters\"", &l)) return false;
     num("\"ms\"", &ms);
     num("\"lanes\"", &ln);
-    if (!(r == 8 || r == 4 || r == 2) || l < 1 || l > 16 || !(ln == 1 || (ln == 2 && r == 4)))
+    if (!(r == 8 || r == 4 || r == 2 || r == 1) || l < 1 || l > 16 ||
+        !(ln == 1 || (ln == 2 && r == 4)))
         return false;
     c->rows = static_cast<int>(r);
     c->lanes = static_cast<int>(ln);
@@ -989,12 +990,61 @@ Choice default_choice(const hjb_problem *P) {
     return c;
 }
 
+// Run `run(choice, &ms)` with the table's choice for `key` when it is one of
+// the candidates, otherwise (tuning on) time every candidate, keep the
+// fastest and leave its outputs in place.  The first candidate is the
+// default when tuning is off and the table has no choice.
+template <typename Run>
+int tuned_candidates(const std::string &key, const std::vector<Choice> &cand, Run run) {
+    if (cand.empty()) return fail(HJB_ERR_UNSUPPORTED, "no candidate configuration");
+    const int mode = tune_mode();
+    Choice c = cand.front();
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        read_tune_files();
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end())
+            for (const Choice &x : cand)
+                if (x.rows == it->second.rows && x.lanes == it->second.lanes && x.li == it->second.li) {
+                    c = it->second;
+                    have = true;
+                }
+    }
+    if (cand.size() == 1 || mode == 0 || (have && mode == 1)) return run(c, nullptr);
+    std::vector<Choice> tried = cand;
+    double best_ms = 1e300;
+    size_t best = 0;
+    int last_rc = HJB_OK;
+    for (size_t i = 0; i < tried.size(); ++i) {
+        double ms = 0;
+        const int rc = run(tried[i], &ms);
+        if (rc != HJB_OK && rc != HJB_ERR_NOT_CONVERGED) return rc;
+        last_rc = rc;
+        tried[i].ms = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = i;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = tried[best];
+        if (const char *e = std::getenv("HJB_TUNE_CACHE")) save_tune_file(e);
+    }
+    return best + 1 == tried.size() ? last_rc : run(tried[best], nullptr);
+}
+
 // Run `run(choice, &ms)` with the tuned choice for `key`, tuning it first
 // when needed.  fixed_rows: the kernel family has one tile shape; li_fixed:
 // the caller (opts or HJB_LOCAL_ITERS) pinned the applications per tile.
 template <typename Run>
-int tuned_call(const std::string &key, const hjb_problem *P, bool fixed_rows, int li_pinned, Run run) {
+int tuned_call(const std::string &key_class, const hjb_problem *P, bool fixed_rows, int li_pinned,
+               Run run) {
     const int mode = tune_mode();
+    // a caller that pins the applications per tile tunes (and finds) the
+    // tile shape for that value only, under a key of its own
+    const std::string key = li_pinned ? key_class + "|li" + std::to_string(li_pinned) : key_class;
     const int frows = fixed_rows ? hjbk::TY : forced_rows();
     const int flanes = fixed_rows ? 1 : forced_lanes();
     Choice c = default_choice(P);
@@ -1091,10 +1141,12 @@ int hjb_tune_get(const char *key, hjb_tune_choice *out) {
 int hjb_tune_set(const char *key, const hjb_tune_choice *c) {
     g_err.clear();
     if (!key || !c) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
-    if (!(c->tile_rows == 8 || c->tile_rows == 4 || c->tile_rows == 2) || c->local_iters < 1 ||
-        c->local_iters > 16 || !(c->lanes == 1 || (c->lanes == 2 && c->tile_rows == 4)))
+    if (!(c->tile_rows == 8 || c->tile_rows == 4 || c->tile_rows == 2 || c->tile_rows == 1) ||
+        c->local_iters < 1 || c->local_iters > 16 ||
+        !(c->lanes == 1 || (c->lanes == 2 && c->tile_rows == 4)))
         return fail(HJB_ERR_INVALID_ARG,
-                    "tile_rows must be 8, 4 or 2, lanes 1 (or 2 with 4 rows) and local_iters 1..16");
+                    "tile_rows must be 8, 4, 2 (or 1: the reconstruction's on-chip solve), lanes "
+                    "1 (or 2 with 4 rows) and local_iters 1..16");
     if (std::strchr(key, '"') || std::strchr(key, '\\') || std::strchr(key, '\n'))
         return fail(HJB_ERR_INVALID_ARG, "a key may not hold quotes, backslashes or newlines");
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1442,39 +1494,75 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     std::memset(R.slots.data(), 0, m * sizeof(SlotDesc));
     if (P->kind == HJB_DYN_DUBINS)
         TRY(dubins_trig(P, P->c_trig, g.nz, hK, dxK, P->grid.lo[2], dxK[2], st));
-    const int rows = fixed_shape(P) ? hjbk::TY : 2;
-    for (int k = 0; k < m; ++k) {
-        fill_slot(R.slots[k], P, g, cp, wform, hK, dxK, halo, tol, max_iters, rows);
-        R.slots[k].only_target = k + 1;  // RA step 1: dG := X_k
-        if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->c_trig.as<float2>();
-    }
-    TRY(alloc_slot_buffers(R, nd, halo, rows));
-    TRY(upload_slots(R, st));
     const float c_over = static_cast<float>(P->l_const / P->lambda);
-    CK(cudaEventRecord(R.ev0, st));
-    // 2D coarse grids that fit on chip: one thread-block cluster per
-    // auxiliary problem solves it to convergence in shared memory
-    // (HJB_RA=tiles keeps the tile-queue sweep for every grid)
+    // RA step 1 on a 2D coarse grid that fits on chip may run as one
+    // thread-block cluster per auxiliary problem, solving it to convergence in
+    // shared memory (tuned choice rows = 1), otherwise as the tile-queue sweep
+    // of every auxiliary problem in one launch.  HJB_RA=tiles|chip pins the
+    // path.
     const char *ra_env = std::getenv("HJB_RA");
-    const bool on_chip = nd == 2 && !(ra_env && std::strcmp(ra_env, "tiles") == 0) &&
-                         hjbh::coarse_fits(coarse.n[0], coarse.n[1], halo, nullptr, nullptr, nullptr);
-    if (on_chip) {
-        hjbh::launch_loop_init(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), R.d_ctl.as<Ctl>(),
-                               m, st);
-        const int crc = hjbh::launch_coarse_solve(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(),
-                                                  m, coarse.n[0], coarse.n[1], halo, P->interp,
-                                                  wform ? 1 : 0, control_table(P),
-                                                  8.0f * 1.1920929e-7f, st);
-        if (crc) return fail(HJB_ERR_CUDA, "launch of the on-chip coarse solve failed: %s",
-                             cudaGetErrorString(cudaGetLastError()));
-        R.last_loop = 1;
-        R.local_iters = 1;
-    } else {
-        hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform, c_over,
-                                 nullptr, st);
-        const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo,
-                                 rows, 8 / rows, loop_mode(), 1};
-        TRY(run_loop(R, key, 8, control_table(P), st, local_iters(nullptr, P)));
+    const bool chip_fits = nd == 2 && hjbh::coarse_fits(coarse.n[0], coarse.n[1], halo, nullptr,
+                                                        nullptr, nullptr);
+    bool on_chip = false;
+    auto coarse_solve = [&](Choice c, double *ms) -> int {
+        on_chip = c.rows == 1;
+        const int rows = on_chip ? 2 : c.rows;
+        R.slots.assign(m, SlotDesc());
+        std::memset(R.slots.data(), 0, m * sizeof(SlotDesc));
+        for (int k = 0; k < m; ++k) {
+            fill_slot(R.slots[k], P, g, cp, wform, hK, dxK, halo, tol, max_iters, rows);
+            R.slots[k].only_target = k + 1;  // RA step 1: dG := X_k
+            if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->c_trig.as<float2>();
+        }
+        TRY(alloc_slot_buffers(R, nd, halo, rows));
+        TRY(upload_slots(R, st));
+        CK(cudaEventRecord(R.ev0, st));
+        if (on_chip) {
+            hjbh::launch_loop_init(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(),
+                                   R.d_ctl.as<Ctl>(), m, st);
+            const int crc = hjbh::launch_coarse_solve(
+                R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, coarse.n[0], coarse.n[1],
+                halo, P->interp, wform ? 1 : 0, control_table(P), 8.0f * 1.1920929e-7f, st);
+            if (crc)
+                return fail(HJB_ERR_CUDA, "launch of the on-chip coarse solve failed: %s",
+                            cudaGetErrorString(cudaGetLastError()));
+            R.last_loop = 1;
+            R.local_iters = 1;
+        } else {
+            hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform,
+                                     c_over, nullptr, st);
+            const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P),
+                                     halo, rows, 8 / rows, loop_mode(), 1};
+            TRY(run_loop(R, key, 8, control_table(P), st, c.li));
+        }
+        if (ms) {
+            CK(cudaEventRecord(R.ev1, st));
+            CK(cudaEventSynchronize(R.ev1));
+            float t = 0;
+            cudaEventElapsedTime(&t, R.ev0, R.ev1);
+            *ms = t;
+        }
+        return HJB_OK;
+    };
+    {
+        const std::string key = tune_key("ra", {P->kind, coarse.n[0], coarse.n[1], coarse.n[2], P->na,
+                                                P->nb, P->interp, P->cost.user ? 1 : 0, m, halo});
+        std::vector<Choice> cand;
+        const int li_c[3] = {2, 4, 6};
+        if (fixed_shape(P)) {
+            for (int l : li_c) cand.push_back(Choice{hjbk::TY, 1, l, 0.0});
+        } else {
+            const bool chip = chip_fits && !(ra_env && std::strcmp(ra_env, "tiles") == 0);
+            const bool tiles = !(chip_fits && ra_env && std::strcmp(ra_env, "chip") == 0);
+            if (tiles) {
+                cand.push_back(Choice{2, 1, 6, 0.0});
+                for (int r : {4, 2})
+                    for (int l : li_c)
+                        if (!(r == 2 && l == 6)) cand.push_back(Choice{r, 1, l, 0.0});
+            }
+            if (chip) cand.push_back(Choice{1, 1, 1, 0.0});
+        }
+        TRY(tuned_candidates(key, cand, coarse_solve));
     }
     // threshold of eq. (rep)
     double delta = ra->delta;

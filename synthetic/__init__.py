@@ -57,9 +57,15 @@ def mesh2(nx: int, ny: int, lo=(-1.0, -1.0), hi=(1.0, 1.0)):
 
 
 def circle_controls(A: int) -> np.ndarray:
-    """A unit vectors at angles 2 pi j / A (the discrete control set of Sec. 3)."""
+    """A unit vectors at angles 2 pi j / A (the discrete control set of Sec. 3).
+    For even A the second half is the exact negation of the first (a_{j + A/2}
+    = -a_j, as on the circle; cos and sin of the shifted angles would differ
+    from it by rounding in components near zero)."""
     t = 2.0 * np.pi * np.arange(A) / A
-    return np.stack([np.cos(t), np.sin(t)], axis=1)
+    a = np.stack([np.cos(t), np.sin(t)], axis=1)
+    if A % 2 == 0:
+        a[A // 2:] = -a[: A // 2]
+    return a
 
 
 def king_controls() -> np.ndarray:

@@ -212,14 +212,12 @@ def _ra_case(which):
 @pytest.mark.parametrize("path", ["on_chip", "tiles"])
 @pytest.mark.parametrize("which", ["c2", "c1", "vdp", "halo4", "ragged"])
 def test_ra_paths_against_oracle(hjb, orc, monkeypatch, path, which):
-    """RA step 1 (Sec. 3) by the on-chip cluster solve (the default for 2D
-    coarse grids that fit) and by the tile-queue sweep (HJB_RA=tiles): the
-    auxiliary solutions against the oracle's at 1e-4, the labels bit for bit
-    except near-threshold decisions."""
-    if path == "tiles":
-        monkeypatch.setenv("HJB_RA", "tiles")
-    else:
-        monkeypatch.delenv("HJB_RA", raising=False)
+    """RA step 1 (Sec. 3) by the on-chip cluster solve (HJB_RA=chip) and by
+    the tile-queue sweep (HJB_RA=tiles), the two paths the tuner chooses
+    between for 2D coarse grids: the auxiliary solutions against the
+    oracle's at 1e-4, the labels bit for bit except near-threshold
+    decisions."""
+    monkeypatch.setenv("HJB_RA", "tiles" if path == "tiles" else "chip")
     d, stride, delta, _ = _ra_case(which)
     po = oracle_problem(orc, d)
     Vaux_o, lab_o, _ = orc.ra(po, stride, delta, tol=1e-11, nthreads=8)

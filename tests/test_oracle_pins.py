@@ -766,6 +766,65 @@ def test_ra_invariants_and_exact_quarters(orc):
     assert 0.25 <= fr[1] < fr[0] <= 0.25 + 1.5 / 41
 
 
+def test_resplitting_reaches_the_four_sides(orc):
+    """Recursive re-splitting of the target components (Conclusions; reading
+    R22).  The box boundary divided into two components (bottom + right,
+    top + left): the first split separates bottom from right, the second top
+    from left -- the same coarse labels and projected sub-domains, up to the
+    numbering of the components, as RA run directly on the four sides.
+    Further splits (of single sides) keep shrinking the largest sub-domain,
+    never growing it."""
+    n, st = 41, 4
+    four = _box_labels(n)
+    two = np.where(four <= 2, np.where(four > 0, 1, 0), 2)
+    p2 = orc.Problem((n, n), (-1, -1), (1, 1), S.circle_controls(32), two, 2 / (n - 1))
+    p4 = orc.Problem((n, n), (-1, -1), (1, 1), S.circle_controls(32), four, 2 / (n - 1))
+    Vaux, _, _ = orc.ra(p2, (st, st), 0.0, tol=1e-13)
+    delta, _ = orc.delta(p2, (st, st), Vaux)  # 2 M dx_K, the same for every division
+    comp, fine, m, largest = orc.ra_split(p2, (st, st), delta, max_splits=2, tol=1e-13)
+    assert m == 4
+    # the split components are the four sides (in the order of the splits)
+    f4 = four.reshape(-1)
+    ren = {}
+    for c in range(1, 5):
+        sides = np.unique(f4[comp == c])
+        assert len(sides) == 1 and sides[0] != 0
+        ren[c] = int(sides[0])
+    assert sorted(ren.values()) == [1, 2, 3, 4]
+    assert np.array_equal((comp != 0), (f4 != 0))
+    _, lab4, _ = orc.ra(p4, (st, st), delta, tol=1e-13)
+    fine4 = orc.project(p4, (st, st), lab4)
+    perm = np.zeros_like(fine)
+    for k_split, k_direct in ren.items():
+        perm |= ((fine >> (k_split - 1)) & 1) << (k_direct - 1)
+    assert np.array_equal(perm, fine4)
+    assert largest == max(int(((fine4 >> k) & 1).sum()) for k in range(4))
+    # without splits the two halves are much larger (the threshold is wide here)
+    _, _, m2, largest2 = orc.ra_split(p2, (st, st), delta, max_splits=0, tol=1e-13)
+    assert m2 == 2 and largest2 > 1.4 * largest
+    prev = largest2
+    for ms in (1, 2, 4, 6):
+        _, f, mm, lg = orc.ra_split(p2, (st, st), delta, max_splits=ms, tol=1e-13)
+        assert mm == 2 + ms and lg <= prev
+        assert (f != 0).all()  # every node stays in some sub-domain
+        prev = lg
+
+
+def test_resplitting_keeps_an_unbalanced_division(orc):
+    """Van der Pol (Sec. 5, Example ex3): every slice of the small target
+    disk costs nearly the same from far away, so splitting the largest
+    slice does not shrink its sub-domain and the refinement keeps the given
+    division (the direct RA's sub-domains)."""
+    d = S.vdp(n=41, slices=4, stride=4)
+    p = orc.Problem(d["shape"], d["lo"], d["hi"], d["controls"], d["labels"], d["h"],
+                    current=d["current"], cost=d["cost"], v_out=d["v_out"], ntargets=4)
+    comp, fine, m, largest = orc.ra_split(p, (4, 4), 0.1, max_splits=4, tol=1e-12)
+    assert m == 4
+    assert np.array_equal(comp, p.target)
+    _, lab, _ = orc.ra(p, (4, 4), 0.1, tol=1e-12)
+    assert np.array_equal(fine, orc.project(p, (4, 4), lab))
+
+
 def test_table1_shape(orc):
     """Table 1 of Sec. 4.1: the largest reconstructed sub-domain shrinks as
     the coarse grid is refined (eq. incap) towards the exact 25 %.  With the
