@@ -187,7 +187,12 @@ int hjb_destroy(hjb_problem *p);
  *  use_w_form: 1 = iterate on W = l/lambda - V (constant cost only),
  *       0 = iterate on V, -1 = automatic (W form when the cost is constant).
  *  v_init: optional warm start [N] (a previous solution), NULL = start from
- *       value_out on free nodes and 0 on targets (a supersolution).
+ *       value_out on free nodes and 0 on targets (a supersolution).  In
+ *       hjb_solve_decomposed every sub-domain starts from it on its own nodes
+ *       (for example a coarse solution interpolated onto the fine grid, the
+ *       coarse-to-fine warm start between ISA steps 2 and 3); from a start
+ *       that is not a supersolution the iteration still converges (T is a
+ *       contraction) but not monotonically.
  *  sweeps_per_check: sweeps between two convergence tests in the device loop
  *       (<= 0: library default).
  *  local_iters: applications of T to each staged tile per sweep (<= 0:
@@ -203,7 +208,17 @@ int hjb_destroy(hjb_problem *p);
  *       the sub-domain (the operator of Sec. 4 step 3 as written); equal
  *       sub-domains are then solved once.  HJB_SUBDOMAIN_TARGETS_OWN (1):
  *       only component k, the target choice of the auxiliary problems of RA
- *       step 1 (Sec. 3); nodes of other components inside it are free. */
+ *       step 1 (Sec. 3); nodes of other components inside it are free.
+ *  n_subdomains (hjb_solve_decomposed only): the sub-domains of fine_mask,
+ *       bits 0 .. n_subdomains - 1 (<= 0: n_targets); more than n_targets
+ *       come from re-split components (hjb_ra_opts.max_splits) and need
+ *       HJB_SUBDOMAIN_TARGETS_ALL.
+ *  warm_start (hjb_solve_decomposed only, 2D): 1 = start sub-domain k from
+ *       the Q1 interpolation onto the fine grid of the coarse auxiliary
+ *       solution V_k of the problem's last hjb_subdomains call (a
+ *       coarse-to-fine warm start between ISA steps 2 and 3; that call must
+ *       have kept the division, and the iterated form must match); 0 = the
+ *       usual start.  The fixed point does not depend on the start. */
 #define HJB_SUBDOMAIN_TARGETS_ALL 0
 #define HJB_SUBDOMAIN_TARGETS_OWN 1
 typedef struct {
@@ -214,6 +229,8 @@ typedef struct {
     int sweeps_per_check;
     int local_iters;
     int subdomain_targets;
+    int n_subdomains;
+    int warm_start;
 } hjb_solve_opts;
 
 /* Statistics of one solve (per problem or per sub-domain). */
@@ -235,6 +252,8 @@ typedef struct {
     double lipschitz;      /* hjb_subdomains: the M of that threshold (estimated when
                               hjb_ra_opts.M < 0 and delta < 0; 0 when delta was given) */
     int local_iters;       /* applications of T per staged tile and sweep that ran */
+    int subdomains;        /* hjb_subdomains: components of the returned division */
+    long long largest;     /* hjb_subdomains: nodes of its largest projected sub-domain */
     long long tile_visits; /* tiles staged and processed by the sweeps (each visit applies T
                               1 to local_iters times to the tile's nodes) */
 } hjb_stats;
@@ -252,7 +271,27 @@ int hjb_solve(hjb_problem *p, const hjb_solve_opts *opts, float *v_out, hjb_stat
  *  h_coarse: time step on K (<= 0: h * coarse_stride[0]).
  *  delta: threshold of eq. (rep), |V_k - V| <= delta (Prop. 3.1);
  *       delta < 0 selects 2 (C dx_K^q + M dx_K) with the C, M, q below.
- *  tol / max_iters: stopping rule of the auxiliary solves (RA step 1). */
+ *  tol / max_iters: stopping rule of the auxiliary solves (RA step 1).
+ *  max_splits, split_gain, split_labels: recursive re-splitting of the
+ *       target components (the Conclusions: the unbalanced sub-domains of
+ *       Example ex3 can be balanced by refining the division of Gamma
+ *       recursively).  Each step splits the component whose projected
+ *       sub-domain is largest (lowest index on ties) in two, along the x or y
+ *       grid axis of larger index extent of its target nodes (x on ties):
+ *       nodes with index at most s keep it, the others become component m + 1,
+ *       s the smallest index holding at least half of its nodes (the next
+ *       lower occupied index when that would leave the second part empty).
+ *       RA and the projection are re-run with the first division's threshold
+ *       (V = min_k V_k, hence the estimated M, does not change); the step is
+ *       kept when both parts' sub-domains are smaller than (1 - split_gain)
+ *       times the split one's, and the refinement stops at the first step
+ *       that is not, after max_splits steps, at HJB_MAX_TARGETS components,
+ *       or at a component that cannot be split.  The fine mask then has
+ *       stats.subdomains bits; solve it with hjb_solve_decomposed and
+ *       hjb_solve_opts.n_subdomains = stats.subdomains (the sub-problems'
+ *       targets are the target nodes inside them, so the original labels
+ *       serve), or pass split_labels to hjb_create.  v_aux_out must then be
+ *       NULL. */
 typedef struct {
     int coarse_stride[3];
     double h_coarse;
@@ -260,6 +299,11 @@ typedef struct {
     double C, M, q;
     double tol;
     int max_iters;
+    int max_splits;         /* recursive re-splitting steps (0: none; at most 32) */
+    double split_gain;      /* a split is kept when both parts' sub-domains are below
+                               (1 - split_gain) times the split one's (0: 0.05) */
+    uint8_t *split_labels;  /* optional output [N]: the target labels of the final
+                               division (device or host memory) */
 } hjb_ra_opts;
 
 /* RA (Sec. 3, steps 1-3) on the coarse grid followed by ISA step 2

@@ -85,8 +85,10 @@ def _stream(stream):
 
 
 def _opts(tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_per_check=0, local_iters=0,
-          subdomain_targets=0):
+          subdomain_targets=0, n_subdomains=0, warm_start=0):
     o = hjb_solve_opts()
+    o.n_subdomains = int(n_subdomains)
+    o.warm_start = int(warm_start)
     o.tol = float(tol)
     o.max_iters = int(max_iters)
     o.use_w_form = int(use_w_form)
@@ -231,11 +233,17 @@ def solve_static(p: Problem, tol=0.0, max_iters=0, v_init=None, out=None, stream
 
 
 def subdomains(p: Problem, stride, delta=-1.0, C_=0.0, M=-1.0, q=1.0, h_coarse=0.0, tol=0.0,
-               max_iters=0, want_aux=False, stream=None):
+               max_iters=0, want_aux=False, stream=None, max_splits=0, split_gain=0.0,
+               split_labels=None):
     """RA (Sec. 3) + projection (ISA step 2).  Returns (fine_mask, coarse_labels,
     v_aux or None, stats).  delta < 0: 2 (C dx_K^q + M dx_K), M < 0 estimated
-    from the coarse solution."""
+    from the coarse solution.  max_splits > 0 re-splits the target components
+    recursively (split_labels, optional [N] uint8 output: the final division;
+    stats["subdomains"] its component count)."""
     ra = hjb_ra_opts()
+    ra.max_splits = int(max_splits)
+    ra.split_gain = float(split_gain)
+    ra.split_labels = _ptr(split_labels)
     for d in range(3):
         ra.coarse_stride[d] = int(stride[d]) if d < len(stride) else 1
     ra.h_coarse = float(h_coarse)
@@ -260,15 +268,19 @@ def subdomains(p: Problem, stride, delta=-1.0, C_=0.0, M=-1.0, q=1.0, h_coarse=0
 
 def solve_decomposed(p: Problem, fine_mask, tol=0.0, max_iters=0, use_w_form=-1,
                      sweeps_per_check=0, out=None, stream=None, local_iters=0,
-                     subdomain_targets=0):
+                     subdomain_targets=0, n_subdomains=0, v_init=None, warm_start=0):
     """ISA steps 3-4 (Sec. 4).  Returns (Vbar, per-sub-domain stats, total stats).
     subdomain_targets: 0 = every target node inside a sub-domain is its
     target (Sec. 4 step 3 as written), 1 = only its own component (the
-    target choice of RA step 1, Sec. 3)."""
+    target choice of RA step 1, Sec. 3).  n_subdomains: bits of fine_mask
+    (0: n_targets; more after re-splitting).  v_init: warm start of every
+    sub-domain; warm_start=1: start from the last reconstruction's coarse
+    auxiliary solutions interpolated onto the fine grid."""
     out = p.empty(p.N) if out is None else out
-    per = (hjb_stats * p.n_targets)()
+    per = (hjb_stats * max(p.n_targets, int(n_subdomains)))()
     tot = hjb_stats()
-    o = _opts(tol, max_iters, use_w_form, None, sweeps_per_check, local_iters, subdomain_targets)
+    o = _opts(tol, max_iters, use_w_form, v_init, sweeps_per_check, local_iters, subdomain_targets,
+              n_subdomains, warm_start)
     check(_capi.lib().hjb_solve_decomposed(p.handle, _ptr(fine_mask), C.byref(o), _ptr(out), per,
                                            C.byref(tot), _stream(stream)))
     return out, [s.as_dict() for s in per], tot.as_dict()

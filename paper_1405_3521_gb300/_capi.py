@@ -78,7 +78,8 @@ class hjb_target(C.Structure):
 class hjb_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("use_w_form", C.c_int),
                 ("v_init", C.c_void_p), ("sweeps_per_check", C.c_int),
-                ("local_iters", C.c_int), ("subdomain_targets", C.c_int)]
+                ("local_iters", C.c_int), ("subdomain_targets", C.c_int),
+                ("n_subdomains", C.c_int), ("warm_start", C.c_int)]
 
 
 class hjb_stats(C.Structure):
@@ -87,7 +88,7 @@ class hjb_stats(C.Structure):
                 ("labelled", C.c_longlong), ("launches", C.c_longlong), ("tile_rows", C.c_int),
                 ("tile_lanes", C.c_int),
                 ("delta", C.c_double), ("lipschitz", C.c_double), ("local_iters", C.c_int),
-                ("tile_visits", C.c_longlong)]
+                ("subdomains", C.c_int), ("largest", C.c_longlong), ("tile_visits", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,7 +102,8 @@ class hjb_tune_choice(C.Structure):
 class hjb_ra_opts(C.Structure):
     _fields_ = [("coarse_stride", C.c_int * 3), ("h_coarse", C.c_double), ("delta", C.c_double),
                 ("C", C.c_double), ("M", C.c_double), ("q", C.c_double), ("tol", C.c_double),
-                ("max_iters", C.c_int)]
+                ("max_iters", C.c_int), ("max_splits", C.c_int), ("split_gain", C.c_double),
+                ("split_labels", C.c_void_p)]
 
 
 _lib = None

@@ -159,6 +159,11 @@ void launch_queue_init(const hjbk::SlotDesc *slots, int nslots, int max_tiles, h
                        int *qlist0, uint8_t *qflag0, uint8_t *qflag1, cudaStream_t st);
 void launch_init_values(const hjbk::SlotDesc *slots, int nslots, int max_nodes, int wform,
                         float c_over, const float *v_init, cudaStream_t st);
+// Coarse-to-fine warm start (2D): slot k starts from the Q1 interpolation of
+// coarse slot k (every (r0, r1)-th fine node is a coarse node).
+void launch_init_from_coarse(const hjbk::SlotDesc *slots, const hjbk::SlotDesc *coarse,
+                             const hjbk::SlotState *cstate, int nslots, int max_nodes, int r0,
+                             int r1, cudaStream_t st);
 void launch_extract(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, int slot,
                     float *out, int wform, float c_over, cudaStream_t st);
 
@@ -220,7 +225,21 @@ void launch_absmax(const float *x, long long n, int stride, int offset, unsigned
                    cudaStream_t st);
 // s = exp(theta) elementwise.
 void launch_exp(const float *theta, float *s, long long n, cudaStream_t st);
-// Count of bits per sub-domain (sum over k of |Sigma_k|) into *out.
+// Nodes of each of the m sub-domains (out[k] += |bit k|; out zeroed by the caller).
+void launch_bitcount(const uint32_t *mask, long long n, int m, unsigned long long *out,
+                     cudaStream_t st);
+// Re-splitting of a target component (label value comp): index extents
+// ext = {x min, x max, y min, y max} (initialised by the caller to
+// {INT_MAX, -1, INT_MAX, -1}) and node count, the histogram of its nodes
+// along a grid axis, and the relabelling of its nodes with index > s on
+// that axis as new_comp.
+void launch_comp_extent(const GridDims &g, const uint8_t *labels, int comp, int *ext,
+                        unsigned *count_out, cudaStream_t st);
+void launch_comp_hist(const GridDims &g, const uint8_t *labels, int comp, int axis, unsigned *hist,
+                      cudaStream_t st);
+void launch_comp_split(const GridDims &g, uint8_t *labels, int comp, int axis, int s, int new_comp,
+                       cudaStream_t st);
+// Count of bits per sub-domain (sum over k of |Sigma_k|) into *out.// Count of bits per sub-domain (sum over k of |Sigma_k|) into *out.
 void launch_popcount(const uint32_t *mask, long long n, unsigned long long *out, cudaStream_t st);
 
 // ----- adjoint (adjoint.cu) -------------------------------------------------

@@ -214,6 +214,12 @@ struct hjb_problem {
     // coarse problem of the reconstruction
     DevBuf c_speed, c_current, c_cost, c_labels, c_trig, c_mask, c_vstage, c_grad, c_scale;
     DevBuf tile_bits, fine_mask_dev, scratch_u64;
+    // re-splitting of the target components: labels (current, trial), the
+    // trial's fine and coarse masks, counters and histograms
+    DevBuf split_lab, split_fine, split_cl, split_small;
+    // the last hjb_subdomains without re-splitting: its coarse auxiliary
+    // solutions stay in `ra` for the coarse-to-fine warm start
+    int ra_m = 0, ra_stride[3] = {1, 1, 1}, ra_wform = -1;
     DevBuf out_stage, out_stage2, out_stage3, in_stage;
     RunCtx full, ra, dec;
     RunCtx *batch = nullptr;
@@ -806,6 +812,8 @@ hjbh::GridDims dims_of(const hjb_problem *P) {
 
 int check_opts(const hjb_solve_opts *o) {
     if (o && o->max_iters < 0) return fail(HJB_ERR_INVALID_ARG, "max_iters < 0");
+    if (o && o->n_subdomains > HJB_MAX_TARGETS)
+        return fail(HJB_ERR_INVALID_ARG, "n_subdomains must be at most %d", HJB_MAX_TARGETS);
     if (o && o->subdomain_targets != HJB_SUBDOMAIN_TARGETS_ALL &&
         o->subdomain_targets != HJB_SUBDOMAIN_TARGETS_OWN)
         return fail(HJB_ERR_INVALID_ARG, "unknown subdomain_targets %d", o->subdomain_targets);
@@ -1327,6 +1335,7 @@ int hjb_destroy(hjb_problem *P) {
                       &P->c_cost,    &P->c_labels, &P->c_trig,       &P->c_mask,
                       &P->c_vstage,  &P->c_grad,   &P->tile_bits, &P->c_scale,
                       &P->fine_mask_dev, &P->scratch_u64, &P->out_stage, &P->out_stage2,
+                      &P->split_lab, &P->split_fine, &P->split_cl, &P->split_small,
                       &P->out_stage3, &P->in_stage};
     for (DevBuf *b : bufs) b->release();
     P->speed.release();
@@ -1432,12 +1441,19 @@ int hjb_solve(hjb_problem *P, const hjb_solve_opts *opts, float *v_out, hjb_stat
     });
 }
 
-int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_out,
-                   uint32_t *coarse_labels_out, float *v_aux_out, hjb_stats *stats,
-                   void *stream) {
-    g_err.clear();
-    if (!P || !ra || !fine_mask_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// RA (Sec. 3, steps 1-3) and the projection (ISA step 2) for a division of
+// the target into m components given by comp_labels (device [N], 0 free,
+// k = component k; NULL: the problem's labels).  delta_in >= 0 is the
+// threshold; < 0 derives it from ra (eq. rep).  fine_dev [N] and cl_dev
+// [N_K] receive the fine and coarse sub-domain bits (device), vaux_dev
+// [m][N_K] (optional) the auxiliary solutions; stats as for hjb_subdomains.
+int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_labels, int m,
+                double delta_in, uint32_t *fine_dev, uint32_t *cl_dev, float *vaux_dev,
+                hjb_stats *stats, cudaStream_t st) {
     const int nd = P->grid.ndim;
     hjbh::GridDims fine = dims_of(P), coarse = fine;
     int stride[3] = {1, 1, 1};
@@ -1469,7 +1485,8 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     if (pr.current) TRY(P->c_current.ensure(2 * NK * sizeof(float)));
     if (pr.cost) TRY(P->c_cost.ensure(NK * sizeof(float)));
     if (pr.scale) TRY(P->c_scale.ensure(2 * NK * sizeof(float)));
-    hjbh::launch_gather_coarse(fine, coarse, stride, pr.speed, pr.current, pr.cost, pr.labels,
+    hjbh::launch_gather_coarse(fine, coarse, stride, pr.speed, pr.current, pr.cost,
+                               comp_labels ? comp_labels : pr.labels,
                                pr.scale, P->c_speed.as<float>(), P->c_current.as<float>(),
                                P->c_cost.as<float>(), P->c_labels.as<uint8_t>(),
                                P->c_scale.as<float>(), st);
@@ -1487,7 +1504,6 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
                  &halo));
     const double tol = ra->tol > 0 ? ra->tol : default_tol(P, hK);
     const int max_iters = ra->max_iters > 0 ? ra->max_iters : 100000;
-    const int m = P->ntargets;
     RunCtx &R = P->ra;
     const SlotGeo g = geo_of(nd, coarse.n, coarse.periodic[2]);
     R.slots.assign(m, SlotDesc());
@@ -1565,7 +1581,7 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
         TRY(tuned_candidates(key, cand, coarse_solve));
     }
     // threshold of eq. (rep)
-    double delta = ra->delta;
+    double delta = delta_in;
     double lipschitz = 0.0;
     TRY(P->scratch_u64.ensure(64));
     unsigned long long *d_u64 = P->scratch_u64.as<unsigned long long>();
@@ -1590,32 +1606,16 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
         delta = 2.0 * (C * std::pow(dxK[0], q) + M * dxK[0]);
         lipschitz = M;
     }
-    OutArr cl;
-    TRY(cl.init(coarse_labels_out, NK * sizeof(uint32_t), &P->c_mask));
-    uint32_t *cl_dev = coarse_labels_out ? static_cast<uint32_t *>(cl.dev()) : nullptr;
-    if (!cl_dev) {
-        TRY(P->c_mask.ensure(NK * sizeof(uint32_t)));
-        cl_dev = P->c_mask.as<uint32_t>();
-    }
     hjbh::launch_label(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), m, coarse,
                        P->c_labels.as<uint8_t>(), static_cast<float>(delta), wform ? 1 : 0, cl_dev,
                        nullptr, d_u64, st);
-    OutArr fm;
-    TRY(fm.init(fine_mask_out, P->N * sizeof(uint32_t), &P->out_stage2));
-    hjbh::launch_project(fine, coarse, stride, cl_dev, static_cast<uint32_t *>(fm.dev()), st);
-    hjbh::launch_popcount(static_cast<const uint32_t *>(fm.dev()), P->N, d_u64 + 1, st);
-    if (v_aux_out) {
-        OutArr va;
-        TRY(va.init(v_aux_out, static_cast<size_t>(m) * NK * sizeof(float), &P->c_vstage));
+    hjbh::launch_project(fine, coarse, stride, cl_dev, fine_dev, st);
+    hjbh::launch_popcount(fine_dev, P->N, d_u64 + 1, st);
+    if (vaux_dev)
         for (int k = 0; k < m; ++k)
             hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), k,
-                                 static_cast<float *>(va.dev()) + static_cast<size_t>(k) * NK,
-                                 wform, c_over, st);
-        TRY(va.finish(st));
-    }
+                                 vaux_dev + static_cast<size_t>(k) * NK, wform, c_over, st);
     CK(cudaEventRecord(R.ev1, st));
-    TRY(cl.finish(st));
-    TRY(fm.finish(st));
     unsigned long long hc[2];
     CK(cudaMemcpyAsync(hc, d_u64, sizeof hc, cudaMemcpyDeviceToHost, st));
     int err = 0;
@@ -1640,7 +1640,8 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
         stats->lipschitz = lipschitz;
         stats->local_iters = R.local_iters;
         stats->launches = pr.launches + (on_chip ? 7 : 8) + sweeps +
-                          (ra->delta < 0 && ra->M < 0 ? 1 : 0) + (v_aux_out ? m : 0);
+                          (delta_in < 0 && ra->M < 0 ? 1 : 0) + (vaux_dev ? m : 0);
+        stats->subdomains = m;
         float ms = 0;
         cudaEventElapsedTime(&ms, R.ev0, R.ev1);
         stats->ms = ms;
@@ -1652,6 +1653,184 @@ int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_ou
     return HJB_OK;
 }
 
+
+}  // namespace
+
+extern "C" {
+
+int hjb_subdomains(hjb_problem *P, const hjb_ra_opts *ra, uint32_t *fine_mask_out,
+                   uint32_t *coarse_labels_out, float *v_aux_out, hjb_stats *stats,
+                   void *stream) {
+    g_err.clear();
+    if (!P || !ra || !fine_mask_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
+    if (ra->max_splits < 0 || ra->max_splits > HJB_MAX_TARGETS ||
+        !(ra->split_gain >= 0.0 && ra->split_gain < 1.0))
+        return fail(HJB_ERR_INVALID_ARG, "max_splits must be in [0, %d] and split_gain in [0, 1)",
+                    HJB_MAX_TARGETS);
+    if (ra->max_splits > 0 && v_aux_out)
+        return fail(HJB_ERR_INVALID_ARG, "v_aux_out must be NULL when components are re-split");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nd = P->grid.ndim;
+    long long NK = 1;
+    for (int d = 0; d < nd; ++d) {
+        const int r = ra->coarse_stride[d], n = P->grid.n[d];
+        if (r < 1) return fail(HJB_ERR_INVALID_ARG, "coarse_stride[%d] < 1", d);
+        if (P->grid.periodic[d] ? n % r : (n - 1) % r)
+            return fail(HJB_ERR_INVALID_ARG, "stride %d does not divide n[%d]%s", r, d,
+                        P->grid.periodic[d] ? "" : "-1");
+        const int nk = P->grid.periodic[d] ? n / r : (n - 1) / r + 1;
+        if (nk < 2) return fail(HJB_ERR_INVALID_ARG, "coarse grid has < 2 nodes in dim %d", d);
+        NK *= nk;
+    }
+    OutArr fm, cl, va;
+    TRY(fm.init(fine_mask_out, P->N * sizeof(uint32_t), &P->out_stage2));
+    TRY(cl.init(coarse_labels_out, NK * sizeof(uint32_t), &P->c_mask));
+    uint32_t *cl_dev = static_cast<uint32_t *>(cl.dev());
+    if (!cl_dev) {
+        TRY(P->c_mask.ensure(NK * sizeof(uint32_t)));
+        cl_dev = P->c_mask.as<uint32_t>();
+    }
+    if (v_aux_out)
+        TRY(va.init(v_aux_out, static_cast<size_t>(P->ntargets) * NK * sizeof(float), &P->c_vstage));
+    uint32_t *fine_dev = static_cast<uint32_t *>(fm.dev());
+    TRY(P->split_small.ensure(64 * sizeof(unsigned long long) + 8 * sizeof(int) +
+                              65536 * sizeof(unsigned)));
+    unsigned long long *d_cnt = P->split_small.as<unsigned long long>();
+    hjb_stats s0;
+    std::memset(&s0, 0, sizeof s0);
+    const int rc0 = ra_division(P, ra, nullptr, P->ntargets, ra->delta, fine_dev, cl_dev,
+                                v_aux_out ? static_cast<float *>(va.dev()) : nullptr, &s0, st);
+    if (rc0 != HJB_OK && rc0 != HJB_ERR_NOT_CONVERGED) return rc0;
+    int m = P->ntargets;
+    long long launches = s0.launches;
+    // recursive re-splitting of the target components (Conclusions): split the
+    // component whose sub-domain is largest in two along the x or y axis of
+    // larger index extent at the median index; keep the split when both parts'
+    // sub-domains are smaller than (1 - split_gain) times the split one's
+    std::vector<unsigned long long> sizes(HJB_MAX_TARGETS, 0ull), tsizes(HJB_MAX_TARGETS, 0ull);
+    const hjbh::GridDims fd = dims_of(P);
+    if (ra->max_splits > 0) {
+        const double gain = ra->split_gain > 0 ? ra->split_gain : 0.05;
+        TRY(P->split_lab.ensure(2 * P->N));
+        TRY(P->split_fine.ensure(P->N * sizeof(uint32_t)));
+        TRY(P->split_cl.ensure(NK * sizeof(uint32_t)));
+        uint8_t *comp = P->split_lab.as<uint8_t>(), *trial = comp + P->N;
+        int *d_ext = reinterpret_cast<int *>(d_cnt + 64);
+        unsigned *d_nodes = reinterpret_cast<unsigned *>(d_ext + 4);
+        unsigned *d_hist = reinterpret_cast<unsigned *>(d_ext + 8);
+        Prep pr;
+        TRY(prepare(P, st, pr));
+        CK(cudaMemcpyAsync(comp, pr.labels, P->N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
+        hjbh::launch_bitcount(fine_dev, P->N, m, d_cnt, st);
+        CK(cudaMemcpyAsync(sizes.data(), d_cnt, 32 * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        launches += pr.launches + 1;
+        for (int step = 0; step < ra->max_splits && m < HJB_MAX_TARGETS; ++step) {
+            int k = 0;
+            for (int j = 1; j < m; ++j)
+                if (sizes[j] > sizes[k]) k = j;
+            // extents of component k + 1, then the histogram along the axis
+            const int init_ext[4] = {1 << 30, -1, 1 << 30, -1};
+            CK(cudaMemcpyAsync(d_ext, init_ext, sizeof init_ext, cudaMemcpyHostToDevice, st));
+            CK(cudaMemsetAsync(d_nodes, 0, sizeof(unsigned), st));
+            hjbh::launch_comp_extent(fd, comp, k + 1, d_ext, d_nodes, st);
+            int ext[4];
+            unsigned cnt = 0;
+            CK(cudaMemcpyAsync(ext, d_ext, sizeof ext, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&cnt, d_nodes, sizeof cnt, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (cnt < 2) break;
+            const int axis = (ext[1] - ext[0]) >= (ext[3] - ext[2]) ? 0 : 1;
+            const int n = fd.n[axis];
+            if (n > 65536) break;
+            CK(cudaMemsetAsync(d_hist, 0, n * sizeof(unsigned), st));
+            hjbh::launch_comp_hist(fd, comp, k + 1, axis, d_hist, st);
+            std::vector<unsigned> hist(n);
+            CK(cudaMemcpyAsync(hist.data(), d_hist, n * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                               st));
+            CK(cudaStreamSynchronize(st));
+            const unsigned long long half = (cnt + 1ull) / 2;
+            unsigned long long cum = 0;
+            int s_split = -1;
+            for (int j = 0; j < n; ++j) {
+                cum += hist[j];
+                if (cum >= half) {
+                    s_split = j;
+                    break;
+                }
+            }
+            if (cum == cnt) {  // everything at or below: the next lower occupied index
+                int t = s_split - 1;
+                while (t >= 0 && hist[t] == 0) --t;
+                s_split = t;
+            }
+            launches += 2;
+            if (s_split < 0) break;
+            CK(cudaMemcpyAsync(trial, comp, P->N, cudaMemcpyDeviceToDevice, st));
+            hjbh::launch_comp_split(fd, trial, k + 1, axis, s_split, m + 1, st);
+            hjb_stats ts;
+            std::memset(&ts, 0, sizeof ts);
+            const int trc = ra_division(P, ra, trial, m + 1, s0.delta, P->split_fine.as<uint32_t>(),
+                                        P->split_cl.as<uint32_t>(), nullptr, &ts, st);
+            if (trc != HJB_OK) return trc;
+            CK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
+            hjbh::launch_bitcount(P->split_fine.as<uint32_t>(), P->N, m + 1, d_cnt, st);
+            CK(cudaMemcpyAsync(tsizes.data(), d_cnt, 32 * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            launches += ts.launches + 2;
+            const double lim = (1.0 - gain) * static_cast<double>(sizes[k]);
+            if (static_cast<double>(tsizes[k]) > lim || static_cast<double>(tsizes[m]) > lim) break;
+            // keep the split
+            CK(cudaMemcpyAsync(comp, trial, P->N, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(fine_dev, P->split_fine.p, P->N * sizeof(uint32_t),
+                               cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(cl_dev, P->split_cl.p, NK * sizeof(uint32_t),
+                               cudaMemcpyDeviceToDevice, st));
+            sizes = tsizes;
+            s0.iterations = ts.iterations;
+            s0.node_updates += ts.node_updates;
+            s0.labelled = ts.labelled;
+            s0.ties = ts.ties;
+            ++m;
+        }
+        if (ra->split_labels) {
+            const bool host = !is_device_ptr(ra->split_labels);
+            CK(cudaMemcpyAsync(ra->split_labels, comp, P->N,
+                               host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+        }
+    } else {
+        CK(cudaMemsetAsync(d_cnt, 0, 32 * sizeof(unsigned long long), st));
+        hjbh::launch_bitcount(fine_dev, P->N, m, d_cnt, st);
+        CK(cudaMemcpyAsync(sizes.data(), d_cnt, 32 * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, st));
+        launches += 1;
+    }
+    TRY(cl.finish(st));
+    TRY(fm.finish(st));
+    if (v_aux_out) TRY(va.finish(st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (stats) {
+        *stats = s0;
+        stats->subdomains = m;
+        stats->launches = launches;
+        unsigned long long big = 0;
+        for (int k = 0; k < m; ++k) big = sizes[k] > big ? sizes[k] : big;
+        stats->largest = static_cast<long long>(big);
+    }
+    // the auxiliary solutions in P->ra belong to the original division only
+    // when no split was kept (the splits re-run RA on other divisions)
+    P->ra_m = (m == P->ntargets && ra->max_splits == 0) ? m : 0;
+    for (int d = 0; d < 3; ++d) P->ra_stride[d] = d < nd ? ra->coarse_stride[d] : 1;
+    {
+        bool wf;
+        P->ra_wform = resolve_form(P, -1, &wf) == HJB_OK ? (wf ? 1 : 0) : -1;
+    }
+    return rc0;
+}
 }  // extern "C"
 
 namespace {
@@ -1668,9 +1847,21 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     TRY(halo_for(P, pr.max_off_xy, pr.max_off_z, &halo));
     const double tol = (opts && opts->tol > 0) ? opts->tol : default_tol(P, P->h);
     const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
-    const int m = P->ntargets;
+    const int m = (opts && opts->n_subdomains > 0) ? opts->n_subdomains : P->ntargets;
     const int nd = P->grid.ndim;
     const hjbh::GridDims fine = dims_of(P);
+    // warm start (the same array for every sub-domain, inside its nodes)
+    const float *vinit = nullptr;
+    if (opts && opts->v_init) {
+        if (is_device_ptr(opts->v_init)) {
+            vinit = opts->v_init;
+        } else {
+            TRY(P->in_stage.ensure(P->N * sizeof(float)));
+            CK(cudaMemcpyAsync(P->in_stage.p, opts->v_init, P->N * sizeof(float),
+                               cudaMemcpyHostToDevice, st));
+            vinit = P->in_stage.as<float>();
+        }
+    }
     const uint32_t *mask = fine_mask;
     if (!is_device_ptr(fine_mask)) {
         TRY(P->fine_mask_dev.ensure(P->N * sizeof(uint32_t)));
@@ -1712,8 +1903,15 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     CK(cudaMemsetAsync(diff, 0, 32 * sizeof(uint32_t), st));
     hjbh::launch_tile_bits(fine, tiles_x, tiles_y, tiles_z, rows, mask,
                            P->tile_bits.as<uint32_t>(), st, diff, m, tile_full);
-    hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
-                             nullptr, st);
+    if (opts && opts->warm_start) {
+        // coarse-to-fine warm start from the reconstruction's auxiliary solutions
+        hjbh::launch_init_from_coarse(R.d_slots.as<SlotDesc>(), P->ra.d_slots.as<SlotDesc>(),
+                                      P->ra.d_state.as<SlotState>(), m, static_cast<int>(P->N),
+                                      P->ra_stride[0], P->ra_stride[1], st);
+    } else {
+        hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(P->N), wform, c_over,
+                                 vinit, st);
+    }
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
                              8 / rows / ch.lanes, loop_mode(), ch.lanes};
     // sub-domains with equal node sets are solved once (V_k depends on the
@@ -1782,11 +1980,29 @@ int hjb_solve_decomposed(hjb_problem *P, const uint32_t *fine_mask, const hjb_so
     g_err.clear();
     if (!P || !fine_mask || !v_out) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     TRY(check_opts(opts));
+    if (opts && opts->warm_start) {
+        bool wf;
+        TRY(resolve_form(P, opts->use_w_form, &wf));
+        if (P->grid.ndim != 2 || P->ra_m != P->ntargets || (opts->n_subdomains > 0 &&
+            opts->n_subdomains != P->ntargets) || opts->v_init || P->ra_wform != (wf ? 1 : 0))
+            return fail(HJB_ERR_INVALID_ARG,
+                        "warm_start needs a 2D problem whose last hjb_subdomains call kept its "
+                        "division (no splits), the same iterated form, and no v_init");
+    }
+    if (opts && opts->n_subdomains > P->ntargets &&
+        opts->subdomain_targets == HJB_SUBDOMAIN_TARGETS_OWN)
+        return fail(HJB_ERR_UNSUPPORTED,
+                    "sub-domains of re-split components take every target node inside them "
+                    "(HJB_SUBDOMAIN_TARGETS_ALL)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const std::string key = tune_key("decomposed",
                                      {P->kind, P->grid.n[0], P->grid.n[1], P->grid.n[2], P->na, P->nb,
-                                      P->interp, P->cost.user ? 1 : 0, P->ntargets,
-                                      opts ? opts->subdomain_targets : 0});
+                                      P->interp, P->cost.user ? 1 : 0,
+                                      (opts && opts->n_subdomains > 0) ? opts->n_subdomains
+                                                                       : P->ntargets,
+                                      opts ? opts->subdomain_targets : 0,
+                                      opts && opts->v_init ? 1 : 0,
+                                      opts ? opts->warm_start : 0});
     return tuned_call(key, P, fixed_shape(P), pinned_local_iters(opts), [&](Choice c, double *ms) {
         hjb_stats tmp;
         hjb_stats *tp = total ? total : &tmp;

@@ -324,6 +324,79 @@ __global__ void popcount_kernel(const uint32_t *mask, long long n, unsigned long
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// Nodes of each of the m sub-domains of a mask (out[k] += |bit k|).
+__global__ void bitcount_kernel(const uint32_t *mask, long long n, int m, unsigned long long *out) {
+    __shared__ unsigned s_cnt[32];
+    if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned c[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) c[k] = 0u;
+    GRID_STRIDE(i, n) {
+        const uint32_t v = mask[i];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) c[k] += (v >> k) & 1u;
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const unsigned w = __reduce_add_sync(0xffffffffu, c[k]);
+        if ((threadIdx.x & 31) == 0 && w && k < m) atomicAdd(&s_cnt[k], w);
+    }
+    __syncthreads();
+    if (threadIdx.x < m && s_cnt[threadIdx.x])
+        atomicAdd(&out[threadIdx.x], static_cast<unsigned long long>(s_cnt[threadIdx.x]));
+}
+
+// Index extents (x min, x max, y min, y max) and node count of target
+// component `comp` (label value) of a label array.
+__global__ void comp_extent_kernel(hjbh::GridDims g, const uint8_t *labels, int comp, int *ext,
+                                   unsigned *nodes) {
+    const long long N = count(g);
+    int lox = 1 << 30, hix = -1, loy = 1 << 30, hiy = -1;
+    unsigned c = 0;
+    GRID_STRIDE(i, N) {
+        if (labels[i] != comp) continue;
+        int idx[3];
+        unflat(g, i, idx);
+        lox = min(lox, idx[0]);
+        hix = max(hix, idx[0]);
+        loy = min(loy, idx[1]);
+        hiy = max(hiy, idx[1]);
+        ++c;
+    }
+    if (c) {
+        atomicMin(&ext[0], lox);
+        atomicMax(&ext[1], hix);
+        atomicMin(&ext[2], loy);
+        atomicMax(&ext[3], hiy);
+        atomicAdd(nodes, c);
+    }
+}
+
+// Histogram of the component's nodes along one grid axis.
+__global__ void comp_hist_kernel(hjbh::GridDims g, const uint8_t *labels, int comp, int axis,
+                                 unsigned *hist) {
+    const long long N = count(g);
+    GRID_STRIDE(i, N) {
+        if (labels[i] != comp) continue;
+        int idx[3];
+        unflat(g, i, idx);
+        atomicAdd(&hist[idx[axis]], 1u);
+    }
+}
+
+// Relabel the component's nodes with index > s on the axis as new_comp.
+__global__ void comp_split_kernel(hjbh::GridDims g, uint8_t *labels, int comp, int axis, int s,
+                                  int new_comp) {
+    const long long N = count(g);
+    GRID_STRIDE(i, N) {
+        if (labels[i] != comp) continue;
+        int idx[3];
+        unflat(g, i, idx);
+        if (idx[axis] > s) labels[i] = static_cast<uint8_t>(new_comp);
+    }
+}
+
 int blocks_for(long long n) {
     long long b = (n + THREADS - 1) / THREADS;
     if (b > 4096) b = 4096;
@@ -393,6 +466,29 @@ void launch_absmax(const float *x, long long n, int stride, int offset, unsigned
 
 void launch_exp(const float *theta, float *s, long long n, cudaStream_t st) {
     exp_kernel<<<blocks_for(n), THREADS, 0, st>>>(theta, s, n);
+}
+
+void launch_bitcount(const uint32_t *mask, long long n, int m, unsigned long long *out,
+                     cudaStream_t st) {
+    bitcount_kernel<<<blocks_for(n), THREADS, 0, st>>>(mask, n, m, out);
+}
+
+void launch_comp_extent(const GridDims &g, const uint8_t *labels, int comp, int *ext,
+                        unsigned *count_out, cudaStream_t st) {
+    const long long N = static_cast<long long>(g.n[0]) * g.n[1] * (g.ndim > 2 ? g.n[2] : 1);
+    comp_extent_kernel<<<blocks_for(N), THREADS, 0, st>>>(g, labels, comp, ext, count_out);
+}
+
+void launch_comp_hist(const GridDims &g, const uint8_t *labels, int comp, int axis, unsigned *hist,
+                      cudaStream_t st) {
+    const long long N = static_cast<long long>(g.n[0]) * g.n[1] * (g.ndim > 2 ? g.n[2] : 1);
+    comp_hist_kernel<<<blocks_for(N), THREADS, 0, st>>>(g, labels, comp, axis, hist);
+}
+
+void launch_comp_split(const GridDims &g, uint8_t *labels, int comp, int axis, int s, int new_comp,
+                       cudaStream_t st) {
+    const long long N = static_cast<long long>(g.n[0]) * g.n[1] * (g.ndim > 2 ? g.n[2] : 1);
+    comp_split_kernel<<<blocks_for(N), THREADS, 0, st>>>(g, labels, comp, axis, s, new_comp);
 }
 
 void launch_popcount(const uint32_t *mask, long long n, unsigned long long *out, cudaStream_t st) {

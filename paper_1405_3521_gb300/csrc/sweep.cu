@@ -1182,6 +1182,44 @@ __global__ void init_values_kernel(const SlotDesc *slots, int wform, float c_ove
     }
 }
 
+// Coarse-to-fine warm start of the decomposed solve (2D): the starting
+// iterate of sub-domain k is the Q1 interpolation, at its free nodes, of the
+// coarse auxiliary solution k of the reconstruction (slot k of `coarse`,
+// iterated in the same variable), on a coarse grid whose nodes are every
+// (r0, r1)-th fine node; targets take vtarget and ghosts vout, as in
+// init_values_kernel.
+__global__ void init_from_coarse_kernel(const SlotDesc *slots, const SlotDesc *coarse,
+                                        const SlotState *cstate, int r0, int r1) {
+    const SlotDesc &S = slots[blockIdx.y];
+    const SlotDesc &K = coarse[blockIdx.y];
+    const float *Vk = K.V[cstate[blockIdx.y].final_parity];
+    const long long N = static_cast<long long>(S.nx) * S.ny;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int cls = node_class(S, i);
+        const int gx = static_cast<int>(i % S.nx), gy = static_cast<int>(i / S.nx);
+        float v;
+        if (cls == CLS_TARGET) {
+            v = S.vtarget;
+        } else if (cls == CLS_GHOST) {
+            v = S.vout;
+        } else {
+            int cx = gx / r0, cy = gy / r1;
+            cx = cx > K.nx - 2 ? K.nx - 2 : cx;
+            cy = cy > K.ny - 2 ? K.ny - 2 : cy;
+            const float fx = static_cast<float>(gx - cx * r0) / static_cast<float>(r0);
+            const float fy = static_cast<float>(gy - cy * r1) / static_cast<float>(r1);
+            const float *q = Vk + static_cast<long long>(cy) * K.pitch + cx;
+            const float a = fmaf(fx, q[1], (1.0f - fx) * q[0]);
+            const float b = fmaf(fx, q[K.pitch + 1], (1.0f - fx) * q[K.pitch]);
+            v = fmaf(fy, b, (1.0f - fy) * a);
+        }
+        const long long row = static_cast<long long>(gy) * S.pitch + gx;
+        S.V[0][row] = v;
+        S.V[1][row] = v;
+    }
+}
+
 // Copy the latest iterate of one slot to a dense [N] array, converting
 // W back to V = c_over - W in the W form.
 __global__ void extract_kernel(const SlotDesc *slots, const SlotState *state, int slot, float *out,
@@ -1287,6 +1325,15 @@ void launch_init_values(const SlotDesc *slots, int nslots, int max_nodes, int wf
     if (bx < 1) bx = 1;
     dim3 grid(bx, nslots);
     init_values_kernel<<<grid, THREADS, 0, st>>>(slots, wform, c_over, v_init);
+}
+
+void launch_init_from_coarse(const SlotDesc *slots, const SlotDesc *coarse,
+                             const SlotState *cstate, int nslots, int max_nodes, int r0, int r1,
+                             cudaStream_t st) {
+    int bx = (max_nodes + THREADS - 1) / THREADS;
+    if (bx > 4096) bx = 4096;
+    if (bx < 1) bx = 1;
+    init_from_coarse_kernel<<<dim3(bx, nslots), THREADS, 0, st>>>(slots, coarse, cstate, r0, r1);
 }
 
 void launch_extract(const SlotDesc *slots, const SlotState *state, int slot, float *out, int wform,

@@ -672,3 +672,84 @@ def test_decomposed_with_32_targets(hjb, orc):
     assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V
     assert per[30]["node_updates"] == 0 and per[31]["node_updates"] == 0
     assert per[0]["node_updates"] > 0
+
+
+def _box_split_case():
+    n = 41
+    lab = np.zeros((n, n), dtype=np.uint8)
+    lab[0, :] = 1
+    lab[:, n - 1] = 2
+    lab[n - 1, :] = 3
+    lab[:, 0] = 4
+    two = np.where(lab <= 2, np.where(lab > 0, 1, 0), 2).astype(np.uint8)
+    d = dict(shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=S.f32(S.circle_controls(32)), labels=two, ntargets=2, speed=None,
+             current=None, h=2.0 / (n - 1), lam=1.0, v_out=1.0)
+    return d, (4, 4)
+
+
+@pytest.mark.parametrize("which", ["box", "vdp"])
+def test_resplitting_against_oracle(hjb, orc, which):
+    """Recursive re-splitting of the target components (Conclusions; reading
+    R22) on the GPU against the oracle's: the same final division (labels
+    bit for bit), the coarse labels of that division (tie-tolerant) and the
+    decomposed solve of its sub-domains against the oracle's ISA.  The box
+    boundary given as two components reaches the four sides; Van der Pol
+    keeps its four slices (splitting a slice does not shrink its
+    sub-domain)."""
+    import torch
+    if which == "box":
+        d, stride = _box_split_case()
+        splits = 2
+    else:
+        d = S.vdp(n=97, slices=4, stride=8)
+        stride, splits = (8, 8), 4
+    po = oracle_problem(orc, d)
+    Vaux0, _, _ = orc.ra(po, stride, 0.0, tol=1e-12)
+    delta, _ = orc.delta(po, stride, Vaux0)
+    comp_o, fine_o, m_o, largest_o = orc.ra_split(po, stride, delta, max_splits=splits,
+                                                  tol=1e-12, nthreads=8)
+    p = gpu_problem(hjb, d)
+    split = torch.zeros(p.N, dtype=torch.uint8, device="cuda")
+    fine, coarse, _, st = hjb.subdomains(p, stride, delta=delta, max_splits=splits,
+                                         split_labels=split)
+    assert st["subdomains"] == m_o
+    assert np.array_equal(to_np(split).astype(np.int32), comp_o)
+    # the coarse labels of the final division against the oracle's RA on it
+    pk = oracle_problem(orc, dict(d, labels=comp_o.reshape(d["labels"].shape), ntargets=m_o))
+    Vaux_o, lab_o, _ = orc.ra(pk, stride, delta, tol=1e-12)
+    diff = to_np(coarse).astype(np.uint32) ^ lab_o
+    vmin = Vaux_o.min(0)
+    for k in range(m_o):
+        bad = ((diff >> k) & 1) == 1
+        assert np.all(np.abs(np.abs(Vaux_o[k][bad] - vmin[bad]) - delta) <= TOL_V)
+    reads = projection_reads(orc.coarse_shape(po, stride), stride[0], diff != 0, d["shape"])
+    assert np.array_equal(to_np(fine).astype(np.uint32)[~reads], fine_o[~reads])
+    # ISA steps 3-4 on the oracle's final division (targets: every target
+    # node inside a sub-domain, the same set whatever the division)
+    Vb_o, unc, _, _ = orc.isa(pk, fine_o, tol=1e-12, nthreads=8)
+    fm = torch.as_tensor(fine_o.astype(np.int32)).cuda()
+    Vb, per, tot = hjb.solve_decomposed(p, fm, n_subdomains=m_o)
+    assert tot["converged"] == 1
+    assert np.abs(to_np(Vb) - Vb_o).max() < TOL_V
+
+
+def test_coarse_to_fine_warm_start(hjb, orc):
+    """The decomposed solve started from the reconstruction's coarse
+    auxiliary solutions interpolated onto the fine grid (a warm start
+    between ISA steps 2 and 3) reaches the same fixed point: the oracle's
+    ISA on the same decomposition within 1e-4."""
+    import torch
+    d = S.c2(n=129, ntargets=6, stride=8)
+    po = oracle_problem(orc, d)
+    _, lab_o, _ = orc.ra(po, (8, 8), 0.15, tol=1e-12)
+    fine_o = orc.project(po, (8, 8), lab_o)
+    Vb_o, _, _, _ = orc.isa(po, fine_o, tol=1e-12, nthreads=8)
+    p = gpu_problem(hjb, d)
+    hjb.subdomains(p, (8, 8), delta=0.15)  # the coarse auxiliary solutions of the start
+    fine = torch.as_tensor(fine_o.astype(np.int32)).cuda()
+    Vw, _, totw = hjb.solve_decomposed(p, fine, warm_start=1)
+    assert totw["converged"] in (1, 2)
+    assert np.abs(to_np(Vw) - Vb_o).max() < TOL_V
+    Vc, _, totc = hjb.solve_decomposed(p, fine)
+    assert np.abs(to_np(Vc) - Vb_o).max() < TOL_V
