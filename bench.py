@@ -418,6 +418,15 @@ def run_vdp(args, hjb, S, dev, flush, local):
     ms, (Vb, rst, tot, per), clocks = _timed_steps(step, args.steps, args.warmup, flush, local)
     peak = torch_sms(local) * 128 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
     ach = tot["node_updates"] * d["controls"].shape[0] * OPS_PER_CONTROL / (tot["ms"] / 1e3)
+    # recursive re-splitting of the slices (Conclusions remark on Example ex3)
+    fine_s, _, _, sst = hjb.subdomains(p, d["stride"], delta=delta, max_splits=4)
+    Vs, _, tot_s = hjb.solve_decomposed(p, fine_s, n_subdomains=sst["subdomains"])
+    resplit = {"max_splits": 4, "subdomains": sst["subdomains"],
+               "labelled_fraction": sst["labelled"] / d["labels"].size,
+               "largest_fraction": sst["largest"] / d["labels"].size,
+               "unsplit_largest_fraction": rst["largest"] / d["labels"].size,
+               "ms_ra_with_splits": sst["ms"], "ms_fine": tot_s["ms"],
+               "max_abs_diff_vs_unsplit": float((Vs - Vb).abs().max().item())}
     _line(args, "node-updates/s to convergence, decomposed vs full-domain GPU (Van der Pol)",
           nfree * iters_full / (ms / 1e3), UNIT, ms,
           {"workload": "vdp-%dx%d-A21-4slices" % (args.n, args.n), "coarse_stride": list(d["stride"]),
@@ -431,6 +440,7 @@ def run_vdp(args, hjb, S, dev, flush, local):
           raw_node_updates_per_s=(rst["node_updates"] + tot["node_updates"]) / (ms / 1e3),
           roofline={"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s",
                     "frac": ach / peak, "traffic": None, "kernel": "sweep2d_kernel<0,V,4>"},
+          resplit=resplit,
           cpu_baseline=None, gpu_launches=rst["launches"] + tot["launches"], clocks=clocks)
 
 
@@ -692,6 +702,17 @@ def main():
     h2d = 2 * (N * 4 + N * 8 + N) + N * 4  # fields per call (2 calls) + the fine mask
     d2h = N * 4 + len(coarse_h) * 4 + N * 4  # fine mask, coarse labels, V
 
+    # coarse-to-fine warm start of the fine solves (measured once, not the
+    # timed step): each sub-domain starts from its coarse auxiliary solution
+    # interpolated onto the fine grid
+    fine_w, _, _, _ = hjb.subdomains(p, stride, delta=-1.0, C_=0.0, M=-1.0)
+    Vcold, _, tot_c = hjb.solve_decomposed(p, fine_w)
+    Vwarm, _, tot_w = hjb.solve_decomposed(p, fine_w, warm_start=1)
+    warm = {"ms_fine": tot_w["ms"], "sweeps": tot_w["iterations"],
+            "node_updates": tot_w["node_updates"], "cold_ms_fine": tot_c["ms"],
+            "cold_sweeps": tot_c["iterations"], "cold_node_updates": tot_c["node_updates"],
+            "max_abs_diff_vs_cold": float((Vwarm - Vcold).abs().max().item())}
+
     raw = upd / args.steps / (step_ms / 1e3)
     # roofline of the dominant kernel (the 2D sweep, 64 controls, W form)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -748,6 +769,11 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
+        "warm_start": warm,
+        "tuned": {"fine_tile_rows": tot.get("tile_rows"), "fine_tile_lanes": tot.get("tile_lanes"),
+                  "fine_local_iters": tot.get("local_iters"), "ra_local_iters": rst.get("local_iters"),
+                  "full_tile_rows": fst.get("tile_rows"), "full_tile_lanes": fst.get("tile_lanes"),
+                  "full_local_iters": fst.get("local_iters")},
     }
     if rank == 0:
         print(json.dumps(line))

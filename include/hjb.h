@@ -62,7 +62,7 @@ extern "C" {
 /* Problems per hjb_solve_batch call, and tiles per grid: the sweep's work
  * queue addresses a tile of a problem in one 31-bit word (9 bits of problem,
  * 22 bits of tile).  A tile is 32 x 2 nodes at the smallest 2D shape and
- * 32 x 8 x 4 in 3D, so a 2D grid holds up to about 2.7e8 nodes. */
+ * 32 x 8 x 2 in 3D, so a 2D grid holds up to about 2.7e8 nodes. */
 #define HJB_MAX_BATCH 512
 #define HJB_MAX_TILES (1 << 22)
 
@@ -401,8 +401,9 @@ int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_co
  * hjb_solve, hjb_solve_decomposed and hjb_solve_batch run the sweep with a
  * tile shape (tile_rows: 2D tiles of 32 x 8, 32 x 4 or 32 x 2 nodes, with
  * 1, 2 or 4 warp groups splitting the controls of a node, or for 32 x 4
- * tiles lanes = 2 lanes per node; fixed at 8 for Dubins, games and P1) and
- * a number of applications of T per staged tile and sweep (local_iters).  The first call for a problem class on a device runs the
+ * tiles lanes = 2 lanes per node; fixed at 8 for Dubins, games and P1; for
+ * Dubins 32 x 8 tiles of 4 or 2 heading layers) and a number of
+ * applications of T per staged tile and sweep (local_iters).  The first call for a problem class on a device runs the
  * whole call once per candidate on the caller's data and keeps the fastest
  * (ms: its device time) in a table keyed by
  *     "<device name>/<SM count>|<full|decomposed|batch>|<class fields>".
@@ -415,8 +416,8 @@ int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_co
  * runs are bit for bit reproducible; HJB_TUNE=force times even when the
  * table holds a choice.  HJB_TILE_ROWS and HJB_LOCAL_ITERS (or
  * hjb_solve_opts.local_iters) pin their axis.  The file is a JSON array of
- * {"key": ..., "rows": ..., "lanes": ..., "local_iters": ..., "ms": ...}
- * objects, one per line.  HJB_TILE_LANES=1|2 pins the lanes.  The
+ * {"key": ..., "rows": ..., "lanes": ..., "layers": ..., "local_iters": ...,
+ * "ms": ...} objects, one per line.  HJB_TILE_LANES=1|2 pins the lanes.  The
  * reconstruction (hjb_subdomains, key op "ra") tunes its auxiliary solves
  * the same way; there tile_rows = 1 selects the on-chip solve of a 2D
  * coarse grid (one thread-block cluster per auxiliary problem, iterating in
@@ -428,6 +429,7 @@ typedef struct {
                           control sets whose second half is the negated first half */
     int local_iters;
     double ms;
+    int layers;        /* 3D (Dubins): heading layers per 32 x 8 tile, 4 or 2 */
 } hjb_tune_choice;
 int hjb_tune_get(const char *key, hjb_tune_choice *out);
 int hjb_tune_set(const char *key, const hjb_tune_choice *choice);

@@ -96,7 +96,7 @@ class hjb_stats(C.Structure):
 
 class hjb_tune_choice(C.Structure):
     _fields_ = [("tile_rows", C.c_int), ("lanes", C.c_int), ("local_iters", C.c_int),
-                ("ms", C.c_double)]
+                ("ms", C.c_double), ("layers", C.c_int)]
 
 
 class hjb_ra_opts(C.Structure):

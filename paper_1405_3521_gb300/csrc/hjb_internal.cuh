@@ -11,7 +11,8 @@ namespace hjbk {
 // 2D tile: 32 x 8 nodes, one node per thread (256 threads).
 constexpr int TX = 32;
 constexpr int TY = 8;
-// 3D tile: 32 x 8 x TZ nodes, each thread walks TZ layers.
+// 3D tile: 32 x 8 x TZ nodes, each thread walks TZ layers (the default; the
+// sweep also has tiles of 2 layers).
 constexpr int TZ = 4;
 // x halo padding in shared memory: TMA boxes must start at x coordinates
 // whose byte offset is a multiple of 16, so the x halo is widened to 4 floats.
@@ -139,6 +140,7 @@ struct SweepKey {
     int groups;  // warp groups splitting the controls of a node: 256 / (32 ty lanes)
     int loop;    // 1: the cooperative whole-loop kernel, 0: one sweep per launch
     int lanes;   // 2D: 1, or 2 lanes per node taking a_j and -a_j (32 x 4 tiles)
+    int layers;  // 3D: heading layers per tile (4 or 2); 1 in 2D
 };
 
 // Returns the kernel function for a key (nullptr if unsupported) and the
@@ -211,7 +213,7 @@ void launch_project(const GridDims &fine, const GridDims &coarse, const int stri
 // the decomposed solve.  diff
 // (optional, [32], zeroed by the caller): bit j of diff[k] is OR-ed in where
 // the node sets of sub-domains k and j differ (m sub-domains, m <= 32).
-void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty,
+void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty, int tz,
                       const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st,
                       uint32_t *diff = nullptr, int m = 0, uint32_t *tile_full = nullptr);
 // ISA step 4: Vbar = min over the sub-domains containing each node.  Slots

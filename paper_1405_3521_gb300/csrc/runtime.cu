@@ -159,7 +159,7 @@ struct RunCtx {
     SlotState *h_state = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    hjbh::SweepKey key{-1, -1, -1, -1, -1, -1, -1, -1};
+    hjbh::SweepKey key{-1, -1, -1, -1, -1, -1, -1, -1, -1};
     int last_loop = 0;  // the last run used the cooperative loop kernel
     const uint32_t *diff = nullptr;  // decomposed solve: membership differences (twins)
     int local_iters = 1;             // applications of T per tile and sweep (2D)
@@ -264,7 +264,7 @@ SlotGeo geo_of(int ndim, const int n[3], int periodic_z) {
     return g;
 }
 
-int encode_maps(SlotDesc &S, int ndim, int halo, int rows) {
+int encode_maps(SlotDesc &S, int ndim, int halo, int rows, int layers = hjbk::TZ) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(HJB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     for (int b = 0; b < 2; ++b) {
@@ -285,7 +285,7 @@ int encode_maps(SlotDesc &S, int ndim, int halo, int rows) {
                                      static_cast<cuuint64_t>(S.zstride) * 4};
             cuuint32_t box[3] = {static_cast<cuuint32_t>(hjbk::TW),
                                  static_cast<cuuint32_t>(hjbk::TY + 2 * halo),
-                                 static_cast<cuuint32_t>(hjbk::TZ + 2)};
+                                 static_cast<cuuint32_t>(layers + 2)};
             cuuint32_t es[3] = {1, 1, 1};
             r = enc(&S.tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S.V[b], dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -409,7 +409,7 @@ int halo_for(const hjb_problem *P, double max_off, double max_off_z, int *halo) 
 
 // Fill the fields of a slot that depend on the problem statement.
 void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &pr, bool wform,
-               double h, const double dx[3], int halo, double tol, int max_iters, int rows) {
+               double h, const double dx[3], int halo, double tol, int max_iters, int rows, int layers = hjbk::TZ) {
     const double beta = beta_w(P->weights, P->lambda, h);
     const double gamma = gamma_w(P->weights, P->lambda, h);
     const double c = P->l_const / P->lambda;
@@ -421,7 +421,7 @@ void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &
     S.zstride = g.zstride;
     S.tiles_x = (g.nx + hjbk::TX - 1) / hjbk::TX;
     S.tiles_y = (g.ny + rows - 1) / rows;
-    S.tiles_z = P->grid.ndim > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
+    S.tiles_z = P->grid.ndim > 2 ? (g.nz + layers - 1) / layers : 1;
     S.ntiles = S.tiles_x * S.tiles_y * S.tiles_z;
     S.tile_bits = nullptr;
     S.tile_full = nullptr;
@@ -529,7 +529,7 @@ bool fixed_shape(const hjb_problem *P) {
 
 // Allocate iteration buffers for the slots (laid out back to back, each
 // 256-byte aligned) and encode their TMA maps.
-int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows) {
+int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows, int layers = hjbk::TZ) {
     // tile queues: one flag byte per tile per parity, lists of packed items
     int qt = 0, mt = 0;
     for (SlotDesc &S : R.slots) {
@@ -558,7 +558,7 @@ int alloc_slot_buffers(RunCtx &R, int ndim, int halo, int rows) {
         const size_t fl64 = (fl + 63) / 64 * 64;
         S.V[0] = R.vbuf.as<float>() + off[i];
         S.V[1] = R.vbuf.as<float>() + off[i] + fl64;
-        TRY(encode_maps(S, ndim, halo, rows));
+        TRY(encode_maps(S, ndim, halo, rows, layers));
     }
     return HJB_OK;
 }
@@ -612,7 +612,7 @@ int ensure_graph(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::Cont
     const int n = static_cast<int>(R.slots.size());
     if (R.exec && R.key.dubins == key.dubins && R.key.wform == key.wform && R.key.na == key.na &&
         R.key.halo == key.halo && R.key.ty == key.ty && R.key.groups == key.groups &&
-        R.key.lanes == key.lanes &&
+        R.key.lanes == key.lanes && R.key.layers == key.layers &&
         R.key.loop == key.loop && R.li_in_graph == R.local_iters &&
         R.dq_in_graph == R.dyn_queue &&
         R.spb == spb && R.graph_slots == R.d_slots.p &&
@@ -846,6 +846,7 @@ struct Choice {
     int lanes = 1;
     int li = 6;
     double ms = 0.0;
+    int layers = hjbk::TZ;  // 3D: heading layers per tile (4 or 2)
 };
 
 std::mutex g_tune_mu;
@@ -903,15 +904,18 @@ bool parse_tune_line(const std::string &line, std::string *key, Choice *c) {
         *v = std::strtod(line.c_str() + b + 1, &end);
         return end != line.c_str() + b + 1;
     };
-    double r = 0, l = 0, ms = 0, ln = 1;
+    double r = 0, l = 0, ms = 0, ln = 1, ly = hjbk::TZ;
     if (!num("\"rows\"", &r) || !num("\"local_iters\"", &l)) return false;
     num("\"ms\"", &ms);
     num("\"lanes\"", &ln);
+    num("\"layers\"", &ly);
+    if (!(ly == 4 || ly == 2)) return false;
     if (!(r == 8 || r == 4 || r == 2 || r == 1) || l < 1 || l > 16 ||
         !(ln == 1 || (ln == 2 && r == 4)))
         return false;
     c->rows = static_cast<int>(r);
     c->lanes = static_cast<int>(ln);
+    c->layers = static_cast<int>(ly);
     c->li = static_cast<int>(l);
     c->ms = ms;
     return true;
@@ -943,10 +947,10 @@ int save_tune_file(const char *path) {
     size_t i = 0;
     for (const auto &kv : g_tuned) {
         std::fprintf(f,
-                     "{\"key\": \"%s\", \"rows\": %d, \"lanes\": %d, \"local_iters\": %d, "
-                     "\"ms\": %.4f}%s\n",
-                     kv.first.c_str(), kv.second.rows, kv.second.lanes, kv.second.li, kv.second.ms,
-                     ++i < g_tuned.size() ? "," : "");
+                     "{\"key\": \"%s\", \"rows\": %d, \"lanes\": %d, \"layers\": %d, "
+                     "\"local_iters\": %d, \"ms\": %.4f}%s\n",
+                     kv.first.c_str(), kv.second.rows, kv.second.lanes, kv.second.layers,
+                     kv.second.li, kv.second.ms, ++i < g_tuned.size() ? "," : "");
     }
     std::fprintf(f, "]\n");
     std::fclose(f);
@@ -1014,7 +1018,8 @@ int tuned_candidates(const std::string &key, const std::vector<Choice> &cand, Ru
         auto it = g_tuned.find(key);
         if (it != g_tuned.end())
             for (const Choice &x : cand)
-                if (x.rows == it->second.rows && x.lanes == it->second.lanes && x.li == it->second.li) {
+                if (x.rows == it->second.rows && x.lanes == it->second.lanes &&
+                    x.li == it->second.li && x.layers == it->second.layers) {
                     c = it->second;
                     have = true;
                 }
@@ -1070,14 +1075,25 @@ int tuned_call(const std::string &key_class, const hjb_problem *P, bool fixed_ro
     if (flanes) c.lanes = flanes;
     if (li_pinned) c.li = li_pinned;
     if (c.lanes == 2 && (c.rows != 4 || !lane_split_ok(P))) c.lanes = 1;
-    const bool all_pinned = frows && flanes && li_pinned;
+    const bool all_pinned = frows && flanes && li_pinned && !(P && P->kind == HJB_DYN_DUBINS);
     if (mode == 0 || all_pinned || (have && mode == 1)) return run(c, nullptr);
     std::vector<Choice> cand;
-    // tile shapes (rows, lanes) x applications per tile
-    const int shapes[4][2] = {{8, 1}, {4, 1}, {4, 2}, {2, 1}};
     const bool game = P && P->nb > 1;
     const int li_c[3] = {game ? 2 : 4, game ? 4 : 6, game ? 6 : 8};
+    if (P && P->kind == HJB_DYN_DUBINS) {
+        // 3D: tiles of 4 or 2 heading layers x applications per tile
+        for (int ly : {4, 2})
+            for (int l : li_c) {
+                if (li_pinned && l != li_pinned) continue;
+                cand.push_back(Choice{hjbk::TY, 1, l, 0.0, ly});
+            }
+        if (li_pinned && cand.empty())
+            for (int ly : {4, 2}) cand.push_back(Choice{hjbk::TY, 1, li_pinned, 0.0, ly});
+    }
+    // tile shapes (rows, lanes) x applications per tile
+    const int shapes[4][2] = {{8, 1}, {4, 1}, {4, 2}, {2, 1}};
     for (const auto &sh : shapes) {
+        if (P && P->kind == HJB_DYN_DUBINS) break;
         if (frows && sh[0] != frows) continue;
         if (flanes && sh[1] != flanes) continue;
         if (sh[1] == 2 && !lane_split_ok(P)) continue;
@@ -1141,6 +1157,7 @@ int hjb_tune_get(const char *key, hjb_tune_choice *out) {
     if (it == g_tuned.end()) return fail(HJB_ERR_INVALID_ARG, "no tuned choice for this key");
     out->tile_rows = it->second.rows;
     out->lanes = it->second.lanes;
+    out->layers = it->second.layers;
     out->local_iters = it->second.li;
     out->ms = it->second.ms;
     return HJB_OK;
@@ -1151,10 +1168,11 @@ int hjb_tune_set(const char *key, const hjb_tune_choice *c) {
     if (!key || !c) return fail(HJB_ERR_INVALID_ARG, "NULL argument");
     if (!(c->tile_rows == 8 || c->tile_rows == 4 || c->tile_rows == 2 || c->tile_rows == 1) ||
         c->local_iters < 1 || c->local_iters > 16 ||
-        !(c->lanes == 1 || (c->lanes == 2 && c->tile_rows == 4)))
+        !(c->lanes == 1 || (c->lanes == 2 && c->tile_rows == 4)) ||
+        !(c->layers == 4 || c->layers == 2))
         return fail(HJB_ERR_INVALID_ARG,
                     "tile_rows must be 8, 4, 2 (or 1: the reconstruction's on-chip solve), lanes "
-                    "1 (or 2 with 4 rows) and local_iters 1..16");
+                    "1 (or 2 with 4 rows), layers 4 or 2 and local_iters 1..16");
     if (std::strchr(key, '"') || std::strchr(key, '\\') || std::strchr(key, '\n'))
         return fail(HJB_ERR_INVALID_ARG, "a key may not hold quotes, backslashes or newlines");
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1162,6 +1180,7 @@ int hjb_tune_set(const char *key, const hjb_tune_choice *c) {
     Choice x;
     x.rows = c->tile_rows;
     x.lanes = c->lanes;
+    x.layers = c->layers;
     x.li = c->local_iters;
     x.ms = c->ms;
     g_tuned[key] = x;
@@ -1215,13 +1234,13 @@ int hjb_create(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_cost *co
         return fail(HJB_ERR_INVALID_ARG, "grid too large");
     if (N > (1LL << 31)) return fail(HJB_ERR_INVALID_ARG, "more than 2^31 nodes");
     {
-        // tiles at the smallest shape the sweep may run (32 x 2 in 2D, 32 x 8 x 4 in 3D):
+        // tiles at the smallest shape the sweep may run (32 x 2 in 2D, 32 x 8 x 2 in 3D):
         // a work-queue entry holds a tile index in 22 bits
         const long long tx = (grid->n[0] + hjbk::TX - 1) / hjbk::TX;
         const long long tiles = grid->ndim == 2
                                     ? tx * ((grid->n[1] + 1) / 2)
                                     : tx * ((grid->n[1] + hjbk::TY - 1) / hjbk::TY) *
-                                          ((grid->n[2] + hjbk::TZ - 1) / hjbk::TZ);
+                                          ((grid->n[2] + 1) / 2);
         if (tiles > HJB_MAX_TILES)
             return fail(HJB_ERR_UNSUPPORTED, "the grid has %lld tiles, more than the %d a problem "
                         "may hold", tiles, HJB_MAX_TILES);
@@ -1367,12 +1386,12 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, const Choice &ch, flo
     const SlotGeo g = geo_of(P->grid.ndim, P->grid.n, P->grid.periodic[2]);
     R.slots.assign(1, SlotDesc());
     std::memset(R.slots.data(), 0, sizeof(SlotDesc));
-    fill_slot(R.slots[0], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows);
+    fill_slot(R.slots[0], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows, ch.layers);
     if (P->kind == HJB_DYN_DUBINS) {
         TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
         R.slots[0].trig = P->trig.as<float2>();
     }
-    TRY(alloc_slot_buffers(R, P->grid.ndim, halo, rows));
+    TRY(alloc_slot_buffers(R, P->grid.ndim, halo, rows, ch.layers));
     TRY(upload_slots(R, st));
     OutArr out;
     TRY(out.init(v_out, P->N * sizeof(float), &P->out_stage));
@@ -1392,7 +1411,8 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, const Choice &ch, flo
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), 1, static_cast<int>(P->N), wform, c_over,
                              vinit, st);
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
-                             8 / rows / ch.lanes, loop_mode(), ch.lanes};
+                             8 / rows / ch.lanes, loop_mode(), ch.lanes,
+                             P->grid.ndim > 2 ? ch.layers : 1};
     const hjbk::ControlTable ctrl = control_table(P);
     TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, li));
     hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
@@ -1548,7 +1568,8 @@ int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_label
             hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform,
                                      c_over, nullptr, st);
             const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P),
-                                     halo, rows, 8 / rows, loop_mode(), 1};
+                                     halo, rows, 8 / rows, loop_mode(), 1,
+                                     nd > 2 ? hjbk::TZ : 1};
             TRY(run_loop(R, key, 8, control_table(P), st, c.li));
         }
         if (ms) {
@@ -1566,17 +1587,17 @@ int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_label
         std::vector<Choice> cand;
         const int li_c[3] = {2, 4, 6};
         if (fixed_shape(P)) {
-            for (int l : li_c) cand.push_back(Choice{hjbk::TY, 1, l, 0.0});
+            for (int l : li_c) cand.push_back(Choice{hjbk::TY, 1, l, 0.0, hjbk::TZ});
         } else {
             const bool chip = chip_fits && !(ra_env && std::strcmp(ra_env, "tiles") == 0);
             const bool tiles = !(chip_fits && ra_env && std::strcmp(ra_env, "chip") == 0);
             if (tiles) {
-                cand.push_back(Choice{2, 1, 6, 0.0});
+                cand.push_back(Choice{2, 1, 6, 0.0, 1});
                 for (int r : {4, 2})
                     for (int l : li_c)
-                        if (!(r == 2 && l == 6)) cand.push_back(Choice{r, 1, l, 0.0});
+                        if (!(r == 2 && l == 6)) cand.push_back(Choice{r, 1, l, 0.0, 1});
             }
-            if (chip) cand.push_back(Choice{1, 1, 1, 0.0});
+            if (chip) cand.push_back(Choice{1, 1, 1, 0.0, 1});
         }
         TRY(tuned_candidates(key, cand, coarse_solve));
     }
@@ -1877,7 +1898,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
         TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
     const int tiles_x = (g.nx + hjbk::TX - 1) / hjbk::TX;
     const int tiles_y = (g.ny + rows - 1) / rows;
-    const int tiles_z = nd > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
+    const int tiles_z = nd > 2 ? (g.nz + ch.layers - 1) / ch.layers : 1;
     const int nt = tiles_x * tiles_y * tiles_z;
     // per-tile OR and AND of the sub-domain bits, then 32 words of pairwise
     // membership differences
@@ -1886,7 +1907,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     uint32_t *diff = P->tile_bits.as<uint32_t>() + 2 * nt;
     const bool own = opts && opts->subdomain_targets == HJB_SUBDOMAIN_TARGETS_OWN;
     for (int k = 0; k < m; ++k) {
-        fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows);
+        fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows, ch.layers);
         R.slots[k].mask = mask;
         R.slots[k].mask_bit = k;
         R.slots[k].only_target = own ? k + 1 : 0;
@@ -1894,14 +1915,14 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
         R.slots[k].tile_full = tile_full;
         if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->trig.as<float2>();
     }
-    TRY(alloc_slot_buffers(R, nd, halo, rows));
+    TRY(alloc_slot_buffers(R, nd, halo, rows, ch.layers));
     TRY(upload_slots(R, st));
     OutArr out;
     TRY(out.init(v_out, P->N * sizeof(float), &P->out_stage));
     const float c_over = static_cast<float>(P->l_const / P->lambda);
     CK(cudaEventRecord(R.ev0, st));
     CK(cudaMemsetAsync(diff, 0, 32 * sizeof(uint32_t), st));
-    hjbh::launch_tile_bits(fine, tiles_x, tiles_y, tiles_z, rows, mask,
+    hjbh::launch_tile_bits(fine, tiles_x, tiles_y, tiles_z, rows, ch.layers, mask,
                            P->tile_bits.as<uint32_t>(), st, diff, m, tile_full);
     if (opts && opts->warm_start) {
         // coarse-to-fine warm start from the reconstruction's auxiliary solutions
@@ -1913,7 +1934,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
                                  vinit, st);
     }
     const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P), halo, rows,
-                             8 / rows / ch.lanes, loop_mode(), ch.lanes};
+                             8 / rows / ch.lanes, loop_mode(), ch.lanes, nd > 2 ? ch.layers : 1};
     // sub-domains with equal node sets are solved once (V_k depends on the
     // node set alone when its targets are the target nodes inside it; not so
     // with one target component per sub-domain)
@@ -2056,14 +2077,15 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
         const SlotGeo g = geo_of(P->grid.ndim, P->grid.n, P->grid.periodic[2]);
         const double tol = (opts && opts->tol > 0) ? opts->tol : default_tol(P, P->h);
         const int max_iters = (opts && opts->max_iters > 0) ? opts->max_iters : 100000;
-        fill_slot(R.slots[i], P, g, preps[i], wform, P->h, P->dx, halo, tol, max_iters, rows);
+        fill_slot(R.slots[i], P, g, preps[i], wform, P->h, P->dx, halo, tol, max_iters, rows,
+                  ch.layers);
         if (P->kind == HJB_DYN_DUBINS) {
             TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
             R.slots[i].trig = P->trig.as<float2>();
         }
         maxN = P->N > maxN ? P->N : maxN;
     }
-    TRY(alloc_slot_buffers(R, P0->grid.ndim, halo, rows));
+    TRY(alloc_slot_buffers(R, P0->grid.ndim, halo, rows, ch.layers));
     TRY(upload_slots(R, st));
     const float c_over = static_cast<float>(P0->l_const / P0->lambda);
     std::vector<OutArr> outs(count);
@@ -2071,7 +2093,8 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
     hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), count, static_cast<int>(maxN), wform, c_over,
                              nullptr, st);
     const hjbh::SweepKey key{P0->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P0), halo, rows,
-                             8 / rows / ch.lanes, loop_mode(), ch.lanes};
+                             8 / rows / ch.lanes, loop_mode(), ch.lanes,
+                             P0->grid.ndim > 2 ? ch.layers : 1};
     TRY(run_loop(R, key, sweeps_per_body(opts), control_table(P0), st, li));
     for (int i = 0; i < count; ++i) {
         TRY(outs[i].init(v_out[i], problems[i]->N * sizeof(float), &problems[i]->out_stage));
@@ -2561,7 +2584,7 @@ extern "C" int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, c
     args.dyn_queue = queue_mode();
     args.ctrl = ctrl;
     hjbh::launch_queue_init(d_slot, 1, tiles, d_ctl, args.qlist[0], args.qflag[0], args.qflag[1], st);
-    const hjbh::SweepKey key{0, wform ? 1 : 0, controls->count, halo, rows, 1, 1, 1};
+    const hjbh::SweepKey key{0, wform ? 1 : 0, controls->count, halo, rows, 1, 1, 1, 1};
     const void *fn = hjbh::sweep_kernel(key, nullptr);
     if (!fn) return fail(HJB_ERR_UNSUPPORTED, "no sweep kernel for this configuration");
     const int gridsz = hjbh::sweep_grid(key);

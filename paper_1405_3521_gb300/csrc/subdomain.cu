@@ -209,8 +209,8 @@ __global__ void project_kernel(hjbh::GridDims fine, hjbh::GridDims coarse, int r
 // OR of the sub-domain bits over the nodes of each tile (one block per tile;
 // tiles are 32 x ty (x TZ in 3D) nodes).
 __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int ty_rows,
-                                 const uint32_t *mask, uint32_t *tile_bits, uint32_t *diff,
-                                 int m, uint32_t *tile_full) {
+                                 int tz_layers, const uint32_t *mask, uint32_t *tile_bits,
+                                 uint32_t *diff, int m, uint32_t *tile_full) {
     const int t = blockIdx.x;
     const int txy = tiles_x * tiles_y;
     const int tz = t / txy, rem = t - tz * txy;
@@ -222,10 +222,10 @@ __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int
     uint32_t dk[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) dk[k] = 0u;
-    const int zn = g.ndim > 2 ? TZ : 1;
+    const int zn = g.ndim > 2 ? tz_layers : 1;
     for (int r = threadIdx.x >> 5; r < ty_rows * zn; r += THREADS / 32) {
         const int y = ty * ty_rows + r % ty_rows;
-        const int z = g.ndim > 2 ? tz * TZ + r / ty_rows : 0;
+        const int z = g.ndim > 2 ? tz * tz_layers + r / ty_rows : 0;
         if (x < g.n[0] && y < g.n[1] && (g.ndim < 3 || z < g.n[2])) {
             const uint32_t v = mask[flat(g, x, y, z)];
             bits |= v;
@@ -443,12 +443,12 @@ void launch_project(const GridDims &fine, const GridDims &coarse, const int stri
                                                      fine_mask);
 }
 
-void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty,
+void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_z, int ty, int tz,
                       const uint32_t *mask, uint32_t *tile_bits, cudaStream_t st, uint32_t *diff,
                       int m, uint32_t *tile_full) {
     const int nt = tiles_x * tiles_y * tiles_z;
-    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, ty, mask, tile_bits, diff, m,
-                                             tile_full);
+    tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, ty, tz, mask, tile_bits, diff,
+                                             m, tile_full);
 }
 
 void launch_assemble(const SlotDesc *slots, const SlotState *state, int m, const GridDims &fine,

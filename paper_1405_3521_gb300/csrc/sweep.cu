@@ -42,9 +42,13 @@ using namespace hjbk;
 #ifndef HJB_SWEEP2D_MINB
 #define HJB_SWEEP2D_MINB 8
 #endif
-// Resident CTAs per SM the 3D sweep is compiled for (register budget).
+// Resident CTAs per SM the 3D sweep is compiled for (register budget), for
+// tiles of 4 and of 2 heading layers.
 #ifndef HJB_SWEEP3D_MINB
 #define HJB_SWEEP3D_MINB 4
+#endif
+#ifndef HJB_SWEEP3D_MINB2
+#define HJB_SWEEP3D_MINB2 6
 #endif
 
 namespace {
@@ -675,13 +679,11 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
         const int gx = tx * TX + lx, gy = ty * TYT + ly;
         const float vold = T[(ly + H) * TW + lx + XPAD];
         const long long gi = static_cast<long long>(gy) * nx + gx;
-        const bool inside = S.tile_full != nullptr && ((S.tile_full[tile] >> S.mask_bit) & 1u);
-        const bool isfree = (gx < nx) && (gy < ny) && node_class(S, gi, inside) == CLS_FREE;
-        const bool mine = isfree && grp == 0;  // group 0 owns the node's result
-        float2 S2 = make_float2(0.0f, 0.0f), O02 = S2;
-        float add = S.gl;
-        if (isfree) {
-            float sx = 1.0f, sy = 1.0f;
+        const bool inb = (gx < nx) && (gy < ny);
+        // the node's fields are read before its class is known, so that their
+        // loads and the label (and mask) loads are in flight together
+        float sx = 1.0f, sy = 1.0f, cx = 0.0f, cy = 0.0f, lc = 0.0f;
+        if (inb) {
             if (S.scale2) {
                 const float2 d = S.scale2[gi];
                 sx = d.x;
@@ -689,16 +691,23 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
             } else if (S.speed) {
                 sx = sy = S.speed[gi];
             }
-            float cx = 0.0f, cy = 0.0f;
             if (S.current) {
                 const float2 c = reinterpret_cast<const float2 *>(S.current)[gi];
                 cx = c.x;
                 cy = c.y;
             }
+            if (!WFORM && S.cost) lc = S.cost[gi];
+        }
+        const bool inside = S.tile_full != nullptr && ((S.tile_full[tile] >> S.mask_bit) & 1u);
+        const bool isfree = inb && node_class(S, gi, inside) == CLS_FREE;
+        const bool mine = isfree && grp == 0;  // group 0 owns the node's result
+        float2 S2 = make_float2(0.0f, 0.0f), O02 = S2;
+        float add = S.gl;
+        if (isfree) {
             const float sg = (LANES == 2 && grp) ? -1.0f : 1.0f;  // the odd lane takes -a_j
             S2 = make_float2(sg * sx * S.hx, sg * sy * S.hy);
             O02 = make_float2(cx * S.hx, cy * S.hy);
-            if (!WFORM && S.cost) add = S.gamma * S.cost[gi];
+            if (!WFORM && S.cost) add = S.gamma * lc;
         }
         const float2 BASE2 = make_float2(static_cast<float>(lx + XPAD),
                                          static_cast<float>(ly + H + 1));
@@ -826,11 +835,12 @@ __global__ void __launch_bounds__(THREADS, HJB_SWEEP2D_MINB) loop2d_kernel(const
 // heading layers a foot can reach are computed once per node and each
 // control only interpolates in th.
 
+template <int TZ3>
 struct Smem3d {
     static constexpr int H = 2, HZ = 1;
     static constexpr int ROWS = TY + 2 * H;
     static constexpr int LAYER = ROWS * TW;
-    static constexpr int TILE = (TZ + 2 * HZ) * LAYER;
+    static constexpr int TILE = (TZ3 + 2 * HZ) * LAYER;
     static constexpr int TILE_STRIDE = (TILE + 31) / 32 * 32;  // 128-byte aligned buffers
     float tile[2][TILE_STRIDE];
     uint64_t bar[2];
@@ -838,14 +848,15 @@ struct Smem3d {
     int next;  // queue entry of the CTA's next item
     float red[THREADS / 32];
     int cnt[THREADS / 32];
-    float2 trig[TZ];  // heading offsets of the item's layers
+    float2 trig[TZ3];  // heading offsets of the item's layers
 };
 
-template <bool WFORM>
-__device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsigned uses[2]) {
-    constexpr int H = Smem3d::H, HZ = Smem3d::HZ;
-    constexpr int LAYER = Smem3d::LAYER;
-    constexpr int TILE = Smem3d::TILE;
+template <bool WFORM, int TZ3>
+__device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d<TZ3> &sm, unsigned uses[2]) {
+    using SM = Smem3d<TZ3>;
+    constexpr int H = SM::H, HZ = SM::HZ;
+    constexpr int LAYER = SM::LAYER;
+    constexpr int TILE = SM::TILE;
     const Ctl *ctl = args.ctl;
     const int tid = threadIdx.x;
     const int lx = tid & 31, ly = tid >> 5;
@@ -868,7 +879,7 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
             const int ty = rem / S->tiles_x, tx = rem - ty * S->tiles_x;
             mbar_expect_tx(&sm.bar[b], TILE * 4);
             tma_load_3d(sm.tile[b], &S->tmap[src], tx * TX - XPAD, ty * TY - H,
-                        tz * TZ - HZ + S->zdup, &sm.bar[b]);
+                        tz * TZ3 - HZ + S->zdup, &sm.bar[b]);
         }
     };
 
@@ -893,8 +904,8 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
         }
         // the item's heading offsets, read once into shared memory (visible
         // after the barrier below)
-        if (tid < TZ) {
-            const int gz = (tile / (S.tiles_x * S.tiles_y)) * TZ + tid;
+        if (tid < TZ3) {
+            const int gz = (tile / (S.tiles_x * S.tiles_y)) * TZ3 + tid;
             sm.trig[tid] = gz < S.nz ? S.trig[gz] : make_float2(0.0f, 0.0f);
         }
         const bool ok = mbar_wait_bounded(&sm.bar[b], uses[b] & 1u);
@@ -913,13 +924,13 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
         float *T = sm.tile[b];
         const bool interior = (tx * TX >= H) && (tx * TX + TX - 1 + H <= nx - 1) &&
                               (ty * TY >= H) && (ty * TY + TY - 1 + H <= ny - 1);
-        // the thread's column of TZ nodes: starting values and free flags
-        float vold[TZ], vnew[TZ];
+        // the thread's column of TZ3 nodes: starting values and free flags
+        float vold[TZ3], vnew[TZ3];
         unsigned freebits = 0u;
         const bool inside = S.tile_full != nullptr && ((S.tile_full[tile] >> S.mask_bit) & 1u);
 #pragma unroll
-        for (int lz = 0; lz < TZ; ++lz) {
-            const int gz = tz * TZ + lz;
+        for (int lz = 0; lz < TZ3; ++lz) {
+            const int gz = tz * TZ3 + lz;
             vold[lz] = T[(lz + HZ) * LAYER + (ly + H) * TW + lx + XPAD];
             vnew[lz] = vold[lz];
             const long long gi = (static_cast<long long>(gz) * ny + gy) * nx + gx;
@@ -932,9 +943,9 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
         for (;;) {
             bool moved = false;
 #pragma unroll
-            for (int lz = 0; lz < TZ; ++lz) {
+            for (int lz = 0; lz < TZ3; ++lz) {
                 if (!((freebits >> lz) & 1u)) continue;
-                const int gz = tz * TZ + lz;
+                const int gz = tz * TZ3 + lz;
                 const long long gi = (static_cast<long long>(gz) * ny + gy) * nx + gx;
                     const float2 tr = sm.trig[lz];
                 float ox = tr.x, oy = tr.y;
@@ -993,7 +1004,7 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
             // all reads of the tile done; stop early once the tile is stable
             if (!__syncthreads_or(moved)) break;
 #pragma unroll
-            for (int lz = 0; lz < TZ; ++lz)
+            for (int lz = 0; lz < TZ3; ++lz)
                 if ((freebits >> lz) & 1u) T[(lz + HZ) * LAYER + (ly + H) * TW + lx + XPAD] = vnew[lz];
             if (freebits) fence_proxy_async_smem();  // the buffer takes a later TMA copy
             __syncthreads();
@@ -1003,9 +1014,9 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
         float *D = S.V[dst];
         const long long row = static_cast<long long>(gy) * S.pitch + gx;
 #pragma unroll
-        for (int lz = 0; lz < TZ; ++lz) {
+        for (int lz = 0; lz < TZ3; ++lz) {
             if (!((freebits >> lz) & 1u)) continue;
-            const int gz = tz * TZ + lz;
+            const int gz = tz * TZ3 + lz;
             D[static_cast<long long>(gz + S.zdup) * S.zstride + row] = vnew[lz];
             if (gz < S.zdup) D[static_cast<long long>(gz + nz + S.zdup) * S.zstride + row] = vnew[lz];
             if (gz >= nz - S.zdup)
@@ -1044,7 +1055,8 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d &sm, unsign
     return failed;
 }
 
-__device__ __forceinline__ void init_bars3(Smem3d &sm) {
+template <int TZ3>
+__device__ __forceinline__ void init_bars3(Smem3d<TZ3> &sm) {
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
@@ -1053,26 +1065,28 @@ __device__ __forceinline__ void init_bars3(Smem3d &sm) {
     __syncthreads();
 }
 
-template <bool WFORM>
-__global__ void __launch_bounds__(THREADS, HJB_SWEEP3D_MINB) sweep3d_kernel(const __grid_constant__ SweepArgs args) {
-    __shared__ alignas(128) Smem3d sm;
+template <bool WFORM, int TZ3>
+__global__ void __launch_bounds__(THREADS, TZ3 == 2 ? HJB_SWEEP3D_MINB2 : HJB_SWEEP3D_MINB)
+    sweep3d_kernel(const __grid_constant__ SweepArgs args) {
+    __shared__ alignas(128) Smem3d<TZ3> sm;
     const int p = static_cast<int>(args.ctl->sweep & 1u);
     const int nitems = args.ctl->qcount[p];
     const int working = nitems < 1 ? 1 : (nitems < static_cast<int>(gridDim.x) ? nitems : gridDim.x);
     if (static_cast<int>(blockIdx.x) >= working) return;
     init_bars3(sm);
     unsigned uses[2] = {0u, 0u};
-    const bool failed = pass3d<WFORM>(args, sm, uses);
+    const bool failed = pass3d<WFORM, TZ3>(args, sm, uses);
     cta_done(args, failed, working);
 }
 
-template <bool WFORM>
-__global__ void __launch_bounds__(THREADS, HJB_SWEEP3D_MINB) loop3d_kernel(const __grid_constant__ SweepArgs args) {
-    __shared__ alignas(128) Smem3d sm;
+template <bool WFORM, int TZ3>
+__global__ void __launch_bounds__(THREADS, TZ3 == 2 ? HJB_SWEEP3D_MINB2 : HJB_SWEEP3D_MINB)
+    loop3d_kernel(const __grid_constant__ SweepArgs args) {
+    __shared__ alignas(128) Smem3d<TZ3> sm;
     init_bars3(sm);
     unsigned uses[2] = {0u, 0u};
     for (;;) {
-        const bool failed = pass3d<WFORM>(args, sm, uses);
+        const bool failed = pass3d<WFORM, TZ3>(args, sm, uses);
         if (!grid_barrier_finish(args, failed)) break;
     }
 }
@@ -1245,12 +1259,22 @@ namespace hjbh {
 const void *sweep_kernel(const SweepKey &k, size_t *smem) {
     if (smem) *smem = 0;
     if (k.dubins) {
-        if (k.halo != 2 || k.ty != TY || k.groups != 1) return nullptr;
-        if (k.loop)
-            return k.wform ? reinterpret_cast<const void *>(&loop3d_kernel<true>)
-                           : reinterpret_cast<const void *>(&loop3d_kernel<false>);
-        return k.wform ? reinterpret_cast<const void *>(&sweep3d_kernel<true>)
-                       : reinterpret_cast<const void *>(&sweep3d_kernel<false>);
+        if (k.halo != 2 || k.ty != TY || k.groups != 1 || k.lanes != 1) return nullptr;
+        if (k.layers == 4) {
+            if (k.loop)
+                return k.wform ? reinterpret_cast<const void *>(&loop3d_kernel<true, 4>)
+                               : reinterpret_cast<const void *>(&loop3d_kernel<false, 4>);
+            return k.wform ? reinterpret_cast<const void *>(&sweep3d_kernel<true, 4>)
+                           : reinterpret_cast<const void *>(&sweep3d_kernel<false, 4>);
+        }
+        if (k.layers == 2) {
+            if (k.loop)
+                return k.wform ? reinterpret_cast<const void *>(&loop3d_kernel<true, 2>)
+                               : reinterpret_cast<const void *>(&loop3d_kernel<false, 2>);
+            return k.wform ? reinterpret_cast<const void *>(&sweep3d_kernel<true, 2>)
+                           : reinterpret_cast<const void *>(&sweep3d_kernel<false, 2>);
+        }
+        return nullptr;
     }
 #define HJB_PICK(NA_, H_, TY_, G_, L_)                                                          \
     if (k.halo == H_ && k.ty == TY_ && k.groups == G_ && k.lanes == L_) {                        \

@@ -416,13 +416,14 @@ L = _capi.lib()
 path = sys.argv[1]
 assert L.hjb_tune_clear() == 0
 keys = [b"NVIDIA GB300/152|decomposed|0|1025|1025|1|64|0|0|0|16|0", b"NVIDIA GB300/152|batch|0|512"]
-want = [(4, 2, 6, 13.9), (2, 1, 8, 150.25)]
-for k, (r, ln, l, ms) in zip(keys, want):
-    assert L.hjb_tune_set(k, C.byref(_capi.hjb_tune_choice(r, ln, l, ms))) == 0
+want = [(4, 2, 6, 13.9, 4), (8, 1, 8, 150.25, 2)]
+for k, (r, ln, l, ms, ly) in zip(keys, want):
+    assert L.hjb_tune_set(k, C.byref(_capi.hjb_tune_choice(r, ln, l, ms, ly))) == 0
 bad = _capi.HJB_ERR_INVALID_ARG
-assert L.hjb_tune_set(b"x", C.byref(_capi.hjb_tune_choice(3, 1, 6, 0.0))) == bad
-assert L.hjb_tune_set(b"x", C.byref(_capi.hjb_tune_choice(8, 2, 6, 0.0))) == bad
-assert L.hjb_tune_set(b'a"b', C.byref(_capi.hjb_tune_choice(4, 1, 6, 0.0))) == bad
+assert L.hjb_tune_set(b"x", C.byref(_capi.hjb_tune_choice(3, 1, 6, 0.0, 4))) == bad
+assert L.hjb_tune_set(b"x", C.byref(_capi.hjb_tune_choice(8, 2, 6, 0.0, 4))) == bad
+assert L.hjb_tune_set(b"x", C.byref(_capi.hjb_tune_choice(8, 1, 6, 0.0, 3))) == bad
+assert L.hjb_tune_set(b'a"b', C.byref(_capi.hjb_tune_choice(4, 1, 6, 0.0, 4))) == bad
 assert L.hjb_tune_save(path.encode()) == 0
 entries = json.load(open(path))
 assert sorted(e["key"] for e in entries) == sorted(k.decode() for k in keys)
@@ -431,9 +432,10 @@ out = _capi.hjb_tune_choice()
 assert L.hjb_tune_get(keys[0], C.byref(out)) == _capi.HJB_ERR_INVALID_ARG
 n = C.c_int(0)
 assert L.hjb_tune_load(path.encode(), C.byref(n)) == 0 and n.value == 2
-for k, (r, ln, l, ms) in zip(keys, want):
+for k, (r, ln, l, ms, ly) in zip(keys, want):
     assert L.hjb_tune_get(k, C.byref(out)) == 0
-    assert (out.tile_rows, out.lanes, out.local_iters) == (r, ln, l) and abs(out.ms - ms) < 1e-3
+    assert (out.tile_rows, out.lanes, out.local_iters, out.layers) == (r, ln, l, ly)
+    assert abs(out.ms - ms) < 1e-3
 assert L.hjb_tune_load(b"/nonexistent/tune.json", None) == _capi.HJB_ERR_INVALID_ARG
 print("ok")
 """
