@@ -611,7 +611,9 @@ def main():
     p = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], torch.uint8),
                     d["h"], speed=dev(d["speed"]), current=dev(d["current"]),
                     n_targets=d["ntargets"])
-    host = lambda a, dt=np.float32: np.ascontiguousarray(np.asarray(a).astype(dt))  # noqa
+    # the end-to-end leg's host buffers are page-locked, like the outputs the
+    # package allocates for host problems
+    host = lambda a, dt=np.float32: hjb.pinned_copy(a, dt)  # noqa
     ph = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], host(d["labels"], np.uint8),
                      d["h"], speed=host(d["speed"]), current=host(d["current"]),
                      n_targets=d["ntargets"])

@@ -32,7 +32,7 @@ from ._capi import (HJB_DYN_DUBINS, HJB_DYN_SPEED_CURRENT, HJB_WEIGHTS_EXP, HJB_
 
 __all__ = ["Problem", "solve", "subdomains", "solve_decomposed", "solve_batch", "backward",
            "point_values", "solve_static", "HJBSolve", "point_loss", "HJBError", "NotConverged", "library_path",
-           "version"]
+           "version", "pinned_empty", "pinned_copy"]
 
 
 def library_path():
@@ -196,12 +196,36 @@ class Problem:
             pass
 
     def empty(self, n, dtype=np.float32):
-        """Output array of n elements on the problem's side (GPU or host)."""
+        """Output array of n elements on the problem's side: a CUDA tensor, or
+        for host problems a numpy array in page-locked memory (so that the
+        library's device-to-host copies run at full speed) when torch can
+        allocate it, else an ordinary numpy array."""
         if self.on_gpu:
             import torch
             tdt = {np.float32: torch.float32, np.uint32: torch.int32}[dtype]
             return torch.empty(n, dtype=tdt, device=self.labels.device)
-        return np.empty(n, dtype=dtype)
+        return pinned_empty(n, dtype)
+
+
+def pinned_empty(n, dtype=np.float32):
+    """numpy array of n elements in page-locked host memory (ordinary memory
+    when CUDA is not available)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            tdt = {np.float32: torch.float32, np.uint32: torch.int32, np.uint8: torch.uint8}[dtype]
+            return torch.empty(n, dtype=tdt, pin_memory=True).numpy().view(dtype)
+    except (ImportError, RuntimeError, KeyError):
+        pass
+    return np.empty(n, dtype=dtype)
+
+
+def pinned_copy(a, dtype=np.float32):
+    """Copy of an array in page-locked host memory (see pinned_empty)."""
+    a = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+    out = pinned_empty(a.size, dtype).reshape(a.shape)
+    out[...] = a
+    return out
 
 
 def solve(p: Problem, tol=0.0, max_iters=0, use_w_form=-1, v_init=None, sweeps_per_check=0,

@@ -53,6 +53,7 @@ struct alignas(128) SlotDesc {
     const uint32_t *mask;       // sub-domain bitmask [N] (or null)
     const uint32_t *tile_bits;  // per-tile OR of the sub-domain bits (masked slots), or null
     const uint32_t *tile_full;  // per-tile AND of the sub-domain bits (tiles inside a sub-domain)
+    const uint8_t *tile_clear;  // per tile: 1 = no target node in it (or null)
     const float2 *trig;         // Dubins: per heading layer (v h cos/dx, v h sin/dy)
     long long zstride;          // floats between layers of V
     int nx, ny, nz, pitch;
@@ -71,6 +72,7 @@ struct alignas(128) SlotDesc {
     int max_iters;
     int pad_[2];
 };
+static_assert(sizeof(SlotDesc) % 128 == 0, "slot descriptors are 128-byte aligned");
 
 // Convergence state of a slot.
 struct SlotState {
@@ -209,6 +211,10 @@ void launch_grad_max(const hjbk::SlotDesc *slots, const hjbk::SlotState *state, 
 // ISA step 2: fine bitmask from coarse labels through the Kuhn simplices.
 void launch_project(const GridDims &fine, const GridDims &coarse, const int stride[3],
                     const uint32_t *coarse_labels, uint32_t *fine_mask, cudaStream_t st);
+// Per tile: 1 when none of its nodes is a target node (labels != 0); tiles
+// of 32 x ty (x tz) nodes.
+void launch_tile_clear(const GridDims &g, int tiles_x, int tiles_y, int tiles_z, int ty, int tz,
+                       const uint8_t *labels, uint8_t *clear, cudaStream_t st);
 // Per-tile OR (and, optionally, AND: tile_full) of the sub-domain bits of
 // the decomposed solve.  diff
 // (optional, [32], zeroed by the caller): bit j of diff[k] is OR-ed in where

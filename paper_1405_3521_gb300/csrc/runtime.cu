@@ -214,6 +214,7 @@ struct hjb_problem {
     // coarse problem of the reconstruction
     DevBuf c_speed, c_current, c_cost, c_labels, c_trig, c_mask, c_vstage, c_grad, c_scale;
     DevBuf tile_bits, fine_mask_dev, scratch_u64;
+    DevBuf tile_clear, c_tile_clear;  // per tile: no target node (fine grid, coarse grid)
     // re-splitting of the target components: labels (current, trial), the
     // trial's fine and coarse masks, counters and histograms
     DevBuf split_lab, split_fine, split_cl, split_small;
@@ -425,6 +426,7 @@ void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &
     S.ntiles = S.tiles_x * S.tiles_y * S.tiles_z;
     S.tile_bits = nullptr;
     S.tile_full = nullptr;
+    S.tile_clear = nullptr;
     S.qbase = 0;
     S.halo = halo;
     S.hx = static_cast<float>(h / dx[0]);
@@ -1355,6 +1357,7 @@ int hjb_destroy(hjb_problem *P) {
                       &P->c_vstage,  &P->c_grad,   &P->tile_bits, &P->c_scale,
                       &P->fine_mask_dev, &P->scratch_u64, &P->out_stage, &P->out_stage2,
                       &P->split_lab, &P->split_fine, &P->split_cl, &P->split_small,
+                      &P->tile_clear, &P->c_tile_clear,
                       &P->out_stage3, &P->in_stage};
     for (DevBuf *b : bufs) b->release();
     P->speed.release();
@@ -1387,6 +1390,10 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, const Choice &ch, flo
     R.slots.assign(1, SlotDesc());
     std::memset(R.slots.data(), 0, sizeof(SlotDesc));
     fill_slot(R.slots[0], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows, ch.layers);
+    TRY(P->tile_clear.ensure(R.slots[0].ntiles));
+    hjbh::launch_tile_clear(dims_of(P), R.slots[0].tiles_x, R.slots[0].tiles_y, R.slots[0].tiles_z,
+                            rows, ch.layers, pr.labels, P->tile_clear.as<uint8_t>(), st);
+    R.slots[0].tile_clear = P->tile_clear.as<uint8_t>();
     if (P->kind == HJB_DYN_DUBINS) {
         TRY(dubins_trig(P, P->trig, g.nz, P->h, P->dx, P->grid.lo[2], P->dx[2], st));
         R.slots[0].trig = P->trig.as<float2>();
@@ -1428,7 +1435,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, const Choice &ch, flo
     if (stats) {
         fill_stats(stats, R.h_state[0]);
         stats->ms = ms;
-        stats->launches = pr.launches + 4 + sweeps;
+        stats->launches = pr.launches + 5 + sweeps;
         stats->tile_rows = P->grid.ndim == 2 ? rows : 0;
         stats->tile_lanes = ch.lanes;
         stats->local_iters = R.local_iters;
@@ -1545,8 +1552,16 @@ int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_label
         const int rows = on_chip ? 2 : c.rows;
         R.slots.assign(m, SlotDesc());
         std::memset(R.slots.data(), 0, m * sizeof(SlotDesc));
+        if (!on_chip) {
+            const int ctx = (g.nx + hjbk::TX - 1) / hjbk::TX, cty = (g.ny + rows - 1) / rows;
+            const int ctz = nd > 2 ? (g.nz + hjbk::TZ - 1) / hjbk::TZ : 1;
+            TRY(P->c_tile_clear.ensure(static_cast<size_t>(ctx) * cty * ctz));
+            hjbh::launch_tile_clear(coarse, ctx, cty, ctz, rows, hjbk::TZ, P->c_labels.as<uint8_t>(),
+                                    P->c_tile_clear.as<uint8_t>(), st);
+        }
         for (int k = 0; k < m; ++k) {
             fill_slot(R.slots[k], P, g, cp, wform, hK, dxK, halo, tol, max_iters, rows);
+            if (!on_chip) R.slots[k].tile_clear = P->c_tile_clear.as<uint8_t>();
             R.slots[k].only_target = k + 1;  // RA step 1: dG := X_k
             if (P->kind == HJB_DYN_DUBINS) R.slots[k].trig = P->c_trig.as<float2>();
         }
@@ -1660,7 +1675,7 @@ int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_label
         stats->delta = delta;
         stats->lipschitz = lipschitz;
         stats->local_iters = R.local_iters;
-        stats->launches = pr.launches + (on_chip ? 7 : 8) + sweeps +
+        stats->launches = pr.launches + (on_chip ? 7 : 9) + sweeps +
                           (delta_in < 0 && ra->M < 0 ? 1 : 0) + (vaux_dev ? m : 0);
         stats->subdomains = m;
         float ms = 0;
@@ -1903,11 +1918,15 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     // per-tile OR and AND of the sub-domain bits, then 32 words of pairwise
     // membership differences
     TRY(P->tile_bits.ensure((2 * nt + 32) * sizeof(uint32_t)));
+    TRY(P->tile_clear.ensure(nt));
+    hjbh::launch_tile_clear(fine, tiles_x, tiles_y, tiles_z, rows, ch.layers, pr.labels,
+                            P->tile_clear.as<uint8_t>(), st);
     uint32_t *tile_full = P->tile_bits.as<uint32_t>() + nt;
     uint32_t *diff = P->tile_bits.as<uint32_t>() + 2 * nt;
     const bool own = opts && opts->subdomain_targets == HJB_SUBDOMAIN_TARGETS_OWN;
     for (int k = 0; k < m; ++k) {
         fill_slot(R.slots[k], P, g, pr, wform, P->h, P->dx, halo, tol, max_iters, rows, ch.layers);
+        R.slots[k].tile_clear = P->tile_clear.as<uint8_t>();
         R.slots[k].mask = mask;
         R.slots[k].mask_bit = k;
         R.slots[k].only_target = own ? k + 1 : 0;
@@ -1982,7 +2001,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     }
     tot.converged = conv;
     tot.ms = ms;
-    tot.launches = pr.launches + 5 + sweeps;
+    tot.launches = pr.launches + 6 + sweeps;
     tot.tile_rows = P->grid.ndim == 2 ? rows : 0;
     tot.tile_lanes = ch.lanes;
     tot.local_iters = R.local_iters;

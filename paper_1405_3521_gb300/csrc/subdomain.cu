@@ -270,6 +270,26 @@ __global__ void tile_bits_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int
     }
 }
 
+// 1 for tiles without target nodes (one block per tile).
+__global__ void tile_clear_kernel(hjbh::GridDims g, int tiles_x, int tiles_y, int ty_rows,
+                                  int tz_layers, const uint8_t *labels, uint8_t *clear) {
+    const int t = blockIdx.x;
+    const int txy = tiles_x * tiles_y;
+    const int tz = t / txy, rem = t - tz * txy;
+    const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
+    const int x = tx * TX + (threadIdx.x & 31);
+    const int zn = g.ndim > 2 ? tz_layers : 1;
+    int any = 0;
+    for (int r = threadIdx.x >> 5; r < ty_rows * zn; r += THREADS / 32) {
+        const int y = ty * ty_rows + r % ty_rows;
+        const int z = g.ndim > 2 ? tz * tz_layers + r / ty_rows : 0;
+        if (x < g.n[0] && y < g.n[1] && (g.ndim < 3 || z < g.n[2]))
+            any |= labels[flat(g, x, y, z)] != 0;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) clear[t] = any ? 0 : 1;
+}
+
 // ISA step 4: Vbar(j) = min{ V_k(j) : bit k of mask[j] } (max of W in the
 // W form), value_out on nodes that belong to no sub-domain.
 __global__ void assemble_kernel(const SlotDesc *slots, const SlotState *state, int m,
@@ -449,6 +469,12 @@ void launch_tile_bits(const GridDims &fine, int tiles_x, int tiles_y, int tiles_
     const int nt = tiles_x * tiles_y * tiles_z;
     tile_bits_kernel<<<nt, THREADS, 0, st>>>(fine, tiles_x, tiles_y, ty, tz, mask, tile_bits, diff,
                                              m, tile_full);
+}
+
+void launch_tile_clear(const GridDims &g, int tiles_x, int tiles_y, int tiles_z, int ty, int tz,
+                       const uint8_t *labels, uint8_t *clear, cudaStream_t st) {
+    tile_clear_kernel<<<tiles_x * tiles_y * tiles_z, THREADS, 0, st>>>(g, tiles_x, tiles_y, ty, tz,
+                                                                      labels, clear);
 }
 
 void launch_assemble(const SlotDesc *slots, const SlotState *state, int m, const GridDims &fine,

@@ -699,7 +699,11 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
             if (!WFORM && S.cost) lc = S.cost[gi];
         }
         const bool inside = S.tile_full != nullptr && ((S.tile_full[tile] >> S.mask_bit) & 1u);
-        const bool isfree = inb && node_class(S, gi, inside) == CLS_FREE;
+        // a tile without target nodes, in no sub-domain or wholly inside one,
+        // holds free nodes only: no label or mask reads
+        const bool clear = S.tile_clear != nullptr && S.tile_clear[tile] &&
+                           (S.mask == nullptr || inside);
+        const bool isfree = inb && (clear || node_class(S, gi, inside) == CLS_FREE);
         const bool mine = isfree && grp == 0;  // group 0 owns the node's result
         float2 S2 = make_float2(0.0f, 0.0f), O02 = S2;
         float add = S.gl;
@@ -928,13 +932,18 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d<TZ3> &sm, u
         float vold[TZ3], vnew[TZ3];
         unsigned freebits = 0u;
         const bool inside = S.tile_full != nullptr && ((S.tile_full[tile] >> S.mask_bit) & 1u);
+        // a tile without target nodes, in no sub-domain or wholly inside one,
+        // holds free nodes only: no label or mask reads
+        const bool clear = S.tile_clear != nullptr && S.tile_clear[tile] &&
+                           (S.mask == nullptr || inside);
 #pragma unroll
         for (int lz = 0; lz < TZ3; ++lz) {
             const int gz = tz * TZ3 + lz;
             vold[lz] = T[(lz + HZ) * LAYER + (ly + H) * TW + lx + XPAD];
             vnew[lz] = vold[lz];
             const long long gi = (static_cast<long long>(gz) * ny + gy) * nx + gx;
-            if ((gx < nx) && (gy < ny) && (gz < nz) && node_class(S, gi, inside) == CLS_FREE)
+            if ((gx < nx) && (gy < ny) && (gz < nz) &&
+                (clear || node_class(S, gi, inside) == CLS_FREE))
                 freebits |= 1u << lz;
         }
         // args.local_iters applications of T to the tile's nodes with the
