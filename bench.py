@@ -358,7 +358,17 @@ def run_dubins(args, hjb, S, dev, flush, local):
     ms, (Vb, rst, tot, per), clocks = _timed_steps(step, args.steps, args.warmup, flush, local)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6660.0)
-    ach = tot["node_updates"] * 9 / (tot["ms"] / 1e3) / 1e9  # V read+write 8 B, labels 1 B
+    # algorithmic work of the 3D sweep: 53 FP32 operations per node-update
+    # (the foot's cell and fractions 10, bilinear values at three heading
+    # layers 18, per control the heading interpolation and extremum 8 x 3,
+    # the discount 1); 9 bytes per node of a staged tile (V read and write,
+    # labels), once per tile visit however many applications it runs
+    layers = tot.get("tile_layers") or 4
+    nodes_per_tile = 32 * 8 * layers
+    peak_ops = torch_sms(local) * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    ach_ops = tot["node_updates"] * 53 / (tot["ms"] / 1e3)
+    alg_bytes = tot["tile_visits"] * nodes_per_tile * 9
+    ach_bw = alg_bytes / (tot["ms"] / 1e3) / 1e9
     traffic = sweep_traffic(os.path.join(ROOT, "profiles", "sweep3d_dubins256_dram_traffic.md"),
                             rows=8, local_iters=tot.get("local_iters"))
     cpu = None
@@ -386,12 +396,15 @@ def run_dubins(args, hjb, S, dev, flush, local):
                       "max_abs_diff_vs_full": float((Vb - Vf).abs().max().item()),
                       "solved_subdomains": sum(1 for s in per if s["node_updates"] > 0)},
           raw_node_updates_per_s=(rst["node_updates"] + tot["node_updates"]) / (ms / 1e3),
-          roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+          roofline={"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12,
+                    "unit": "Top/s", "frac": ach_ops / peak_ops,
                     "traffic": traffic["bytes_per_launch"] if traffic else None,
                     "traffic_unit": "DRAM bytes per sweep launch (ncu, warm L2)",
-                    "algorithmic_bytes_per_launch": 9 * tot["node_updates"] / max(1, tot["launches"]),
-                    "kernel": "sweep3d_kernel (decomposed fine solve)",
-                    "bytes_per_node_update": 9},
+                    "algorithmic_bytes_per_launch": alg_bytes / max(1, tot["launches"]),
+                    "hbm": {"achieved_gbs": ach_bw, "peak_gbs": hbm, "frac": ach_bw / hbm,
+                            "bytes_per_tile_node": 9},
+                    "ops_per_node_update": 53, "tile_layers": layers,
+                    "kernel": "sweep3d_kernel (decomposed fine solve)"},
           cpu_baseline=cpu, gpu_launches=rst["launches"] + tot["launches"], clocks=clocks)
 
 

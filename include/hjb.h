@@ -256,6 +256,7 @@ typedef struct {
     long long largest;     /* hjb_subdomains: nodes of its largest projected sub-domain */
     long long tile_visits; /* tiles staged and processed by the sweeps (each visit applies T
                               1 to local_iters times to the tile's nodes) */
+    int tile_layers;       /* 3D: heading layers of the 32 x 8 tiles (4 or 2); 0 in 2D */
 } hjb_stats;
 
 /* Full-domain solve of V = T(V) by value iteration V^{n+1} = T(V^n)
@@ -421,7 +422,8 @@ int hjb_solve_static(const hjb_grid *grid, const hjb_dynamics *dyn, const hjb_co
  * reconstruction (hjb_subdomains, key op "ra") tunes its auxiliary solves
  * the same way; there tile_rows = 1 selects the on-chip solve of a 2D
  * coarse grid (one thread-block cluster per auxiliary problem, iterating in
- * shared memory), and HJB_RA=tiles|chip pins the path.  Errors: HJB_ERR_INVALID_ARG (NULL argument, unknown key, a choice
+ * shared memory), and HJB_RA=tiles|chip pins the path.  HJB_TUNE_VERBOSE
+ * prints every timed candidate to stderr.  Errors: HJB_ERR_INVALID_ARG (NULL argument, unknown key, a choice
  * out of range, a file that cannot be opened). */
 typedef struct {
     int tile_rows;

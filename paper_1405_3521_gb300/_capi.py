@@ -88,7 +88,8 @@ class hjb_stats(C.Structure):
                 ("labelled", C.c_longlong), ("launches", C.c_longlong), ("tile_rows", C.c_int),
                 ("tile_lanes", C.c_int),
                 ("delta", C.c_double), ("lipschitz", C.c_double), ("local_iters", C.c_int),
-                ("subdomains", C.c_int), ("largest", C.c_longlong), ("tile_visits", C.c_longlong)]
+                ("subdomains", C.c_int), ("largest", C.c_longlong), ("tile_visits", C.c_longlong),
+                ("tile_layers", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

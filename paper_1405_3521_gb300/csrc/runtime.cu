@@ -1031,12 +1031,16 @@ int tuned_candidates(const std::string &key, const std::vector<Choice> &cand, Ru
     double best_ms = 1e300;
     size_t best = 0;
     int last_rc = HJB_OK;
+    const bool verbose = std::getenv("HJB_TUNE_VERBOSE") != nullptr;
     for (size_t i = 0; i < tried.size(); ++i) {
         double ms = 0;
         const int rc = run(tried[i], &ms);
         if (rc != HJB_OK && rc != HJB_ERR_NOT_CONVERGED) return rc;
         last_rc = rc;
         tried[i].ms = ms;
+        if (verbose)
+            std::fprintf(stderr, "hjb tune %s: rows %d lanes %d layers %d li %d: %.4f ms\n",
+                         key.c_str(), tried[i].rows, tried[i].lanes, tried[i].layers, tried[i].li, ms);
         if (ms < best_ms) {
             best_ms = ms;
             best = i;
@@ -1119,12 +1123,16 @@ int tuned_call(const std::string &key_class, const hjb_problem *P, bool fixed_ro
     double best_ms = 1e300;
     size_t best = 0;
     int last_rc = HJB_OK;
+    const bool verbose = std::getenv("HJB_TUNE_VERBOSE") != nullptr;
     for (size_t i = 0; i < cand.size(); ++i) {
         double ms = 0;
         const int rc = run(cand[i], &ms);
         if (rc != HJB_OK && rc != HJB_ERR_NOT_CONVERGED) return rc;
         last_rc = rc;
         cand[i].ms = ms;
+        if (verbose)
+            std::fprintf(stderr, "hjb tune %s: rows %d lanes %d layers %d li %d: %.4f ms\n",
+                         key.c_str(), cand[i].rows, cand[i].lanes, cand[i].layers, cand[i].li, ms);
         if (ms < best_ms) {
             best_ms = ms;
             best = i;
@@ -1438,6 +1446,7 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, const Choice &ch, flo
         stats->launches = pr.launches + 5 + sweeps;
         stats->tile_rows = P->grid.ndim == 2 ? rows : 0;
         stats->tile_lanes = ch.lanes;
+        stats->tile_layers = P->grid.ndim > 2 ? ch.layers : 0;
         stats->local_iters = R.local_iters;
     }
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
@@ -1607,12 +1616,12 @@ int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_label
             const bool chip = chip_fits && !(ra_env && std::strcmp(ra_env, "tiles") == 0);
             const bool tiles = !(chip_fits && ra_env && std::strcmp(ra_env, "chip") == 0);
             if (tiles) {
-                cand.push_back(Choice{2, 1, 6, 0.0, 1});
+                cand.push_back(Choice{2, 1, 6, 0.0, hjbk::TZ});
                 for (int r : {4, 2})
                     for (int l : li_c)
-                        if (!(r == 2 && l == 6)) cand.push_back(Choice{r, 1, l, 0.0, 1});
+                        if (!(r == 2 && l == 6)) cand.push_back(Choice{r, 1, l, 0.0, hjbk::TZ});
             }
-            if (chip) cand.push_back(Choice{1, 1, 1, 0.0, 1});
+            if (chip) cand.push_back(Choice{1, 1, 1, 0.0, hjbk::TZ});
         }
         TRY(tuned_candidates(key, cand, coarse_solve));
     }
@@ -1991,6 +2000,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
             per_subdomain[k].ms = ms;
             per_subdomain[k].tile_rows = P->grid.ndim == 2 ? rows : 0;
             per_subdomain[k].tile_lanes = ch.lanes;
+            per_subdomain[k].tile_layers = P->grid.ndim > 2 ? ch.layers : 0;
             per_subdomain[k].local_iters = R.local_iters;
         }
         tot.iterations = s.iters > tot.iterations ? s.iters : tot.iterations;
@@ -2004,6 +2014,7 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     tot.launches = pr.launches + 6 + sweeps;
     tot.tile_rows = P->grid.ndim == 2 ? rows : 0;
     tot.tile_lanes = ch.lanes;
+    tot.tile_layers = P->grid.ndim > 2 ? ch.layers : 0;
     tot.local_iters = R.local_iters;
     if (total) *total = tot;
     if (err) return fail(HJB_ERR_TIMEOUT, "a bounded device wait gave up (TMA transfer lost)");
@@ -2138,6 +2149,7 @@ int solve_batch_impl(hjb_problem *const *problems, int count, const hjb_solve_op
             per_problem[i].launches = nl;
             per_problem[i].tile_rows = P0->grid.ndim == 2 ? rows : 0;
             per_problem[i].tile_lanes = ch.lanes;
+            per_problem[i].tile_layers = P0->grid.ndim > 2 ? ch.layers : 0;
             per_problem[i].local_iters = R.local_iters;
         }
         conv &= R.h_state[i].converged ? 1 : 0;

@@ -293,7 +293,9 @@ def test_dubins_whole_domain_subdomains(hjb, orc):
     assert np.abs(to_np(Vbar) - Vo).max() < TOL_V
     assert sum(s["node_updates"] > 0 for s in per) == 1
     V, st = hjb.solve(p)
-    assert np.abs(to_np(V) - to_np(Vbar)).max() < 1e-6
+    # the two calls may run differently tuned tiles (shape, applications per
+    # tile), whose FP32 roundings differ within the stopping tolerance
+    assert np.abs(to_np(V) - to_np(Vbar)).max() < 1e-5
 
 
 def test_batch_uneven(hjb, orc):

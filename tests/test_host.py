@@ -415,8 +415,9 @@ from paper_1405_3521_gb300 import _capi
 L = _capi.lib()
 path = sys.argv[1]
 assert L.hjb_tune_clear() == 0
-keys = [b"NVIDIA GB300/152|decomposed|0|1025|1025|1|64|0|0|0|16|0", b"NVIDIA GB300/152|batch|0|512"]
-want = [(4, 2, 6, 13.9, 4), (8, 1, 8, 150.25, 2)]
+keys = [b"NVIDIA GB300/152|decomposed|0|1025|1025|1|64|0|0|0|16|0", b"NVIDIA GB300/152|batch|0|512",
+        b"NVIDIA GB300/152|ra|0|65|65|1|64|0|0|0|16|2"]
+want = [(4, 2, 6, 13.9, 4), (8, 1, 8, 150.25, 2), (1, 1, 1, 0.5, 4)]
 for k, (r, ln, l, ms, ly) in zip(keys, want):
     assert L.hjb_tune_set(k, C.byref(_capi.hjb_tune_choice(r, ln, l, ms, ly))) == 0
 bad = _capi.HJB_ERR_INVALID_ARG
@@ -431,7 +432,7 @@ assert L.hjb_tune_clear() == 0
 out = _capi.hjb_tune_choice()
 assert L.hjb_tune_get(keys[0], C.byref(out)) == _capi.HJB_ERR_INVALID_ARG
 n = C.c_int(0)
-assert L.hjb_tune_load(path.encode(), C.byref(n)) == 0 and n.value == 2
+assert L.hjb_tune_load(path.encode(), C.byref(n)) == 0 and n.value == 3
 for k, (r, ln, l, ms, ly) in zip(keys, want):
     assert L.hjb_tune_get(k, C.byref(out)) == 0
     assert (out.tile_rows, out.lanes, out.local_iters, out.layers) == (r, ln, l, ly)
