@@ -70,7 +70,8 @@ struct alignas(128) SlotDesc {
     float vtarget;              // target value in the iterated variable
     float tol;
     int max_iters;
-    int pad_[2];
+    int trows;                  // tile rows (2D 8, 4 or 2; 3D 8)
+    int tlayers;                // tile heading layers (3D), 1 in 2D
 };
 static_assert(sizeof(SlotDesc) % 128 == 0, "slot descriptors are 128-byte aligned");
 
@@ -159,8 +160,12 @@ void launch_loop_init(const hjbk::SlotDesc *slots, hjbk::SlotState *state, hjbk:
                       int nslots, cudaStream_t st, const uint32_t *diff = nullptr);
 // Queue of the first sweep: every tile of every slot that holds a node of it
 // (for masked slots: tile_bits carries the slot's bit); both flag arrays set.
+// near_only: queue only tiles whose neighbourhood (the tiles a halo
+// reaches) holds a target node -- exact when the start is a fixed point of T
+// away from targets (the W form from W = 0 with a zero outside value).
 void launch_queue_init(const hjbk::SlotDesc *slots, int nslots, int max_tiles, hjbk::Ctl *ctl,
-                       int *qlist0, uint8_t *qflag0, uint8_t *qflag1, cudaStream_t st);
+                       int *qlist0, uint8_t *qflag0, uint8_t *qflag1, cudaStream_t st,
+                       int near_only = 0);
 void launch_init_values(const hjbk::SlotDesc *slots, int nslots, int max_nodes, int wform,
                         float c_over, const float *v_init, cudaStream_t st);
 // Coarse-to-fine warm start (2D): slot k starts from the Q1 interpolation of

@@ -163,6 +163,7 @@ struct RunCtx {
     int last_loop = 0;  // the last run used the cooperative loop kernel
     const uint32_t *diff = nullptr;  // decomposed solve: membership differences (twins)
     int local_iters = 1;             // applications of T per tile and sweep (2D)
+    int near_start = 0;              // first queue: only tiles near a target (see queue_init)
     int li_in_graph = -1;
     int dyn_queue = 0;               // tile-queue sharing of this run (SweepArgs::dyn_queue)
     int dq_in_graph = -1;
@@ -423,6 +424,8 @@ void fill_slot(SlotDesc &S, const hjb_problem *P, const SlotGeo &g, const Prep &
     S.tiles_x = (g.nx + hjbk::TX - 1) / hjbk::TX;
     S.tiles_y = (g.ny + rows - 1) / rows;
     S.tiles_z = P->grid.ndim > 2 ? (g.nz + layers - 1) / layers : 1;
+    S.trows = rows;
+    S.tlayers = P->grid.ndim > 2 ? layers : 1;
     S.ntiles = S.tiles_x * S.tiles_y * S.tiles_z;
     S.tile_bits = nullptr;
     S.tile_full = nullptr;
@@ -712,7 +715,8 @@ int run_loop(RunCtx &R, const hjbh::SweepKey &key, int spb, const hjbk::ControlT
         hjbk::SweepArgs qa;
         set_queue_args(R, qa);
         hjbh::launch_queue_init(R.d_slots.as<SlotDesc>(), n, R.max_tiles, R.d_ctl.as<Ctl>(),
-                                qa.qlist[0], qa.qflag[0], qa.qflag[1], st);
+                                qa.qlist[0], qa.qflag[0], qa.qflag[1], st, R.near_start);
+        R.near_start = 0;
     }
     CK(cudaGetLastError());
     const float stall_tol = 8.0f * 1.1920929e-7f;
@@ -1429,6 +1433,9 @@ int solve_full(hjb_problem *P, const hjb_solve_opts *opts, const Choice &ch, flo
                              8 / rows / ch.lanes, loop_mode(), ch.lanes,
                              P->grid.ndim > 2 ? ch.layers : 1};
     const hjbk::ControlTable ctrl = control_table(P);
+    // from W = 0 with a zero outside value only tiles near a target change in
+    // the first sweep (T(0) = 0 elsewhere): queue just those
+    R.near_start = wform && !vinit && R.slots[0].vout == 0.0f;
     TRY(run_loop(R, key, sweeps_per_body(opts), ctrl, st, li));
     hjbh::launch_extract(R.d_slots.as<SlotDesc>(), R.d_state.as<SlotState>(), 0,
                          static_cast<float *>(out.dev()), wform, c_over, st);
@@ -1594,6 +1601,7 @@ int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_label
             const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P),
                                      halo, rows, 8 / rows, loop_mode(), 1,
                                      nd > 2 ? hjbk::TZ : 1};
+            R.near_start = wform && R.slots[0].vout == 0.0f;  // see solve_full
             TRY(run_loop(R, key, 8, control_table(P), st, c.li));
         }
         if (ms) {
@@ -1967,6 +1975,8 @@ int solve_dec(hjb_problem *P, const uint32_t *fine_mask, const hjb_solve_opts *o
     // node set alone when its targets are the target nodes inside it; not so
     // with one target component per sub-domain)
     R.diff = own ? nullptr : diff;
+    R.near_start = wform && !vinit && !(opts && opts->warm_start) &&
+                   R.slots[0].vout == 0.0f;  // see solve_full
     const int lrc = run_loop(R, key, sweeps_per_body(opts), control_table(P), st, li);
     R.diff = nullptr;
     TRY(lrc);

@@ -1150,10 +1150,31 @@ __global__ void loop_init_kernel(SlotState *state, Ctl *ctl, int nslots, const u
     }
 }
 
-// First queue: every member tile of every slot, both flag arrays written
-// (blockIdx.y = slot, threads over the slot's tiles).
+// Whether a tile's neighbourhood (the tiles its halo reaches: one tile in x
+// and z, ceil(halo / rows) in y) holds a target node.
+__device__ __forceinline__ bool near_target(const SlotDesc &S, int t) {
+    const int txy = S.tiles_x * S.tiles_y;
+    const int tz = t / txy, rem = t - tz * txy;
+    const int ty = rem / S.tiles_x, tx = rem - ty * S.tiles_x;
+    const int ry = (S.halo + S.trows - 1) / S.trows;
+    const int rz = S.tiles_z > 1 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; ++dz) {
+        const int z = ((tz + dz) % S.tiles_z + S.tiles_z) % S.tiles_z;  // periodic heading
+        for (int dy = -ry; dy <= ry; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = tx + dx, y = ty + dy;
+                if (x < 0 || x >= S.tiles_x || y < 0 || y >= S.tiles_y) continue;
+                if (!S.tile_clear[(z * S.tiles_y + y) * S.tiles_x + x]) return true;
+            }
+    }
+    return false;
+}
+
+// First queue: every member tile of every slot (with near_only, only those
+// near a target), both flag arrays written (blockIdx.y = slot, threads over
+// the slot's tiles).
 __global__ void queue_init_kernel(const SlotDesc *slots, Ctl *ctl, int *qlist0, uint8_t *qflag0,
-                                  uint8_t *qflag1) {
+                                  uint8_t *qflag1, int near_only) {
     const int slot = blockIdx.y;
     const SlotDesc &S = slots[slot];
     const int lane = threadIdx.x & 31;
@@ -1163,6 +1184,7 @@ __global__ void queue_init_kernel(const SlotDesc *slots, Ctl *ctl, int *qlist0, 
         bool member = false;
         if (t < S.ntiles) {
             member = !twin && (S.tile_bits == nullptr || ((S.tile_bits[t] >> S.mask_bit) & 1u));
+            if (member && near_only && S.tile_clear != nullptr) member = near_target(S, t);
             qflag0[S.qbase + t] = member ? 1 : 0;
             qflag1[S.qbase + t] = 0;
         }
@@ -1344,11 +1366,12 @@ void launch_loop_init(const SlotDesc * /*slots*/, SlotState *state, Ctl *ctl, in
 }
 
 void launch_queue_init(const SlotDesc *slots, int nslots, int max_tiles, Ctl *ctl, int *qlist0,
-                       uint8_t *qflag0, uint8_t *qflag1, cudaStream_t st) {
+                       uint8_t *qflag0, uint8_t *qflag1, cudaStream_t st, int near_only) {
     int bx = (max_tiles + THREADS - 1) / THREADS;
     if (bx > 1024) bx = 1024;
     if (bx < 1) bx = 1;
-    queue_init_kernel<<<dim3(bx, nslots), THREADS, 0, st>>>(slots, ctl, qlist0, qflag0, qflag1);
+    queue_init_kernel<<<dim3(bx, nslots), THREADS, 0, st>>>(slots, ctl, qlist0, qflag0, qflag1,
+                                                            near_only);
 }
 
 void launch_init_values(const SlotDesc *slots, int nslots, int max_nodes, int wform, float c_over,
