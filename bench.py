@@ -345,6 +345,14 @@ def run_dubins(args, hjb, S, dev, flush, local):
     nfree = int((d["labels"] == 0).sum())
     p = hjb.Problem(d["shape"], d["lo"], d["hi"], d["controls"], dev(d["labels"], np.uint8), d["h"],
                     dyn=hjb.HJB_DYN_DUBINS, periodic=(0, 0, 1), n_targets=d["ntargets"])
+    if args.profile:
+        # one step (reconstruction + decomposed solve) for a profiler
+        fine, _, _, rst = hjb.subdomains(p, d["stride"], delta=-1.0, C_=0.0, M=-1.0)
+        _, _, tot = hjb.solve_decomposed(p, fine)
+        import torch
+        torch.cuda.synchronize()
+        print(json.dumps({"ra": rst, "total": tot}))
+        return
     # work unit: the sweeps of plain (Jacobi) value iteration on the full grid
     _, fst_j = hjb.solve(p, local_iters=1)
     iters_full = fst_j["iterations"]
