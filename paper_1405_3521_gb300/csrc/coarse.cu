@@ -28,6 +28,8 @@
 // the box only at nodes near it.
 #include <cooperative_groups.h>
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include "hjb_internal.cuh"
 
@@ -390,6 +392,24 @@ int launch_coarse_solve(const SlotDesc *slots, SlotState *state, int m, int nx, 
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
         return -2;
+    if (std::getenv("HJB_TUNE_VERBOSE")) {
+        // how many of the m clusters the GPU holds at once
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(m * CL);
+        cfg.blockDim = dim3(CT);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = CL;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int clusters = -1;
+        cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+        std::fprintf(stderr, "hjb coarse solve: %d clusters of %d CTAs, %d resident at once, %zu B "
+                     "shared memory per CTA\n", m, CL, clusters, smem);
+    }
     void *argv[1] = {&a};
     if (cudaLaunchKernel(fn, dim3(m * CL), dim3(CT), argv, smem, st) != cudaSuccess) return -2;
     return 0;
