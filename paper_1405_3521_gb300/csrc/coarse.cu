@@ -81,14 +81,15 @@ __device__ __forceinline__ float q1c(float2 P2, uint32_t K) {
     const float2 M2 = __fadd2_rn(P2, make_float2(MAGIC, MAGIC));
     const float2 Kn = __ffma2_rn(M2, make_float2(-1.0f, -1.0f), make_float2(TWO23, TWO23));
     const float2 F2 = __fadd2_rn(P2, Kn);  // (fx, fy) = p - k
-    const float2 E2 = __ffma2_rn(F2, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
     const uint32_t addr = (__float_as_uint(M2.y) << 10) + (__float_as_uint(M2.x) << 3) + K;
     float lo0, lo1, hi0, hi1;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(lo0), "=f"(lo1) : "r"(addr));
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+1024];" : "=f"(hi0), "=f"(hi1) : "r"(addr));
+    // (1-f) a as fma(-f, a, a): a (1-f) rounded once
+    const float2 lo = make_float2(lo0, lo1);
     const float2 ab = __ffma2_rn(make_float2(F2.y, F2.y), make_float2(hi0, hi1),
-                                 __fmul2_rn(make_float2(E2.y, E2.y), make_float2(lo0, lo1)));
-    return fmaf(F2.x, ab.y, E2.x * ab.x);
+                                 __ffma2_rn(make_float2(-F2.y, -F2.y), lo, lo));
+    return fmaf(F2.x, ab.y, fmaf(-F2.x, ab.x, ab.x));
 }
 
 // P1 variant: the triangle of the cell's split along its (0,0)-(1,1) diagonal.
@@ -103,7 +104,7 @@ __device__ __forceinline__ float p1c(float2 P2, uint32_t K) {
     const bool lower = F2.x >= F2.y;
     const float t1 = lower ? F2.x : F2.y, t2 = lower ? F2.y : F2.x;
     const float mid = lower ? lo1 : hi0;
-    return fmaf(t2, hi1, fmaf(t1 - t2, mid, (1.0f - t1) * lo0));
+    return fmaf(t2, hi1, fmaf(t1 - t2, mid, fmaf(-t1, lo0, lo0)));
 }
 
 template <bool P1>

@@ -156,21 +156,24 @@ constexpr int TWO23_BITS = 0x4B000000;
 // address of the pair array minus the magic-constant bias, so that the byte
 // address of pair (ky, kx) is (bits(my) << 9) + (bits(mx) << 3) + K.  The
 // lerps use the two-product form (1-f) a + f b, which is monotone in a and b
-// under FP32 rounding.
+// under FP32 rounding.  Its first product is taken as fma(-f, a, a), the
+// exact a (1-f) rounded once, so no separate 1-f is computed; that is the
+// rounded product of a and 1-f whenever 1-f is exact, as it is for the
+// fraction of any coordinate >= 1/2 (a multiple of 2^-24 in [0, 1)).
 __device__ __forceinline__ float q1_pairs(float2 P2, uint32_t K) {
     const float2 M2 = __fadd2_rn(P2, make_float2(MAGIC, MAGIC));
     const float2 Kn = __ffma2_rn(M2, make_float2(-1.0f, -1.0f), make_float2(TWO23, TWO23));
     const float2 F2 = __fadd2_rn(P2, Kn);  // (fx, fy) = p - k
-    const float2 E2 = __ffma2_rn(F2, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
     const uint32_t addr = (__float_as_uint(M2.y) << 9) + (__float_as_uint(M2.x) << 3) + K;
     float lo0, lo1, hi0, hi1;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(lo0), "=f"(lo1) : "r"(addr));
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+512];" : "=f"(hi0), "=f"(hi1) : "r"(addr));
     // lo = (v00, v10), hi = (v01, v11): the two lerps in y as one packed
     // pair (the same roundings as two scalar ones), then the lerp in x
+    const float2 lo = make_float2(lo0, lo1);
     const float2 ab = __ffma2_rn(make_float2(F2.y, F2.y), make_float2(hi0, hi1),
-                                 __fmul2_rn(make_float2(E2.y, E2.y), make_float2(lo0, lo1)));
-    return fmaf(F2.x, ab.y, E2.x * ab.x);
+                                 __ffma2_rn(make_float2(-F2.y, -F2.y), lo, lo));
+    return fmaf(F2.x, ab.y, fmaf(-F2.x, ab.x, ab.x));
 }
 
 // P1 variant (the linear interpolant on the Kuhn triangles of each
@@ -189,7 +192,7 @@ __device__ __forceinline__ float p1_pairs(float2 P2, uint32_t K) {
     const bool lower = F2.x >= F2.y;  // the triangle (0,0), (1,0), (1,1)
     const float t1 = lower ? F2.x : F2.y, t2 = lower ? F2.y : F2.x;
     const float mid = lower ? lo1 : hi0;
-    return fmaf(t2, hi1, fmaf(t1 - t2, mid, (1.0f - t1) * lo0));
+    return fmaf(t2, hi1, fmaf(t1 - t2, mid, fmaf(-t1, lo0, lo0)));
 }
 
 // Interpolation of a kernel family: NA < 0 selects P1, otherwise Q1.
@@ -567,10 +570,12 @@ __device__ bool grid_barrier_finish(const SweepArgs &args, bool failed) {
 //    controls of group w % G, and the groups' partial extrema are combined
 //    through shared memory;
 //  * LANES = 2 (TYT = 4, G = 1; control sets with a_{j + A/2} = -a_j): the
-//    two lanes 2n, 2n + 1 of a warp handle node n of a 16-node half row, the
-//    even lane with the controls a_j and the odd one with -a_j (j < A/2),
-//    through the same instruction stream with the node's speed factors
-//    negated, and one shuffle combines them.
+//    lanes n and n + 16 of a warp handle node n of a 16-node half row, the
+//    low half-warp with the controls a_j and the high one with -a_j
+//    (j < A/2), through the same instruction stream with the node's speed
+//    factors negated, and one shuffle combines them.  Each half-warp reads
+//    16 neighbouring pairs per control, so its 64-bit shared loads stay free
+//    of bank conflicts.
 // The tile's values are read through a pair layout that is double-buffered
 // across the applications of T to the staged tile: application li reads
 // buffer li & 1 and writes its new values into the other, so one barrier
@@ -607,9 +612,9 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
     const Ctl *ctl = args.ctl;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int grp = LANES == 2 ? (lane & 1) : warp % G;
+    const int grp = LANES == 2 ? (lane >> 4) : warp % G;
     const int ly = LANES == 2 ? (warp >> 1) : warp / G;
-    const int lx = LANES == 2 ? ((warp & 1) << 4) + (lane >> 1) : lane;
+    const int lx = LANES == 2 ? ((warp & 1) << 4) + (lane & 15) : lane;
     const int p = static_cast<int>(*reinterpret_cast<const volatile unsigned *>(&ctl->sweep) & 1u);
     const int src = p, dst = p ^ 1;
     const int nitems = *reinterpret_cast<const volatile int *>(&ctl->qcount[p]);
@@ -708,7 +713,7 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
         float2 S2 = make_float2(0.0f, 0.0f), O02 = S2;
         float add = S.gl;
         if (isfree) {
-            const float sg = (LANES == 2 && grp) ? -1.0f : 1.0f;  // the odd lane takes -a_j
+            const float sg = (LANES == 2 && grp) ? -1.0f : 1.0f;  // the high half takes -a_j
             S2 = make_float2(sg * sx * S.hx, sg * sy * S.hy);
             O02 = make_float2(cx * S.hx, cy * S.hy);
             if (!WFORM && S.cost) add = S.gamma * lc;
@@ -743,7 +748,7 @@ __device__ __forceinline__ bool pass2d(const SweepArgs &args, Smem2d<H, TYT, G> 
                 }
             }
             if constexpr (LANES == 2) {
-                best = pick<WFORM>(best, __shfl_xor_sync(0xffffffffu, best, 1));
+                best = pick<WFORM>(best, __shfl_xor_sync(0xffffffffu, best, 16));
             } else if constexpr (G > 1) {
                 sm.part[grp][ly][lx] = best;
                 __syncthreads();
@@ -976,16 +981,15 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d<TZ3> &sm, u
                 const float py = static_cast<float>(ly + H + 1) + oy;
                 const float mx = px + MAGIC, my = py + MAGIC;
                 const float fx = px - (mx - TWO23), fy = py - (my - TWO23);
-                const float ex = 1.0f - fx, ey = 1.0f - fy;
                 const int idx = (__float_as_int(my) - (TWO23_BITS + 1)) * TW +
                                 (__float_as_int(mx) - TWO23_BITS);
                 float B[3];
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     const float *P = T + (lz + HZ - 1 + t) * LAYER + idx;
-                    const float a = fmaf(fx, P[1], ex * P[0]);
-                    const float c = fmaf(fx, P[TW + 1], ex * P[TW]);
-                    B[t] = fmaf(fy, c, ey * a);
+                    const float a = fmaf(fx, P[1], fmaf(-fx, P[0], P[0]));
+                    const float c = fmaf(fx, P[TW + 1], fmaf(-fx, P[TW], P[TW]));
+                    B[t] = fmaf(fy, c, fmaf(-fy, a, a));
                 }
                 // heading: local coordinate of the node is lz + HZ + 1 (+1 shift)
                 const float bz = static_cast<float>(lz + HZ + 1);
@@ -1000,7 +1004,7 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d<TZ3> &sm, u
                     const int d = (__float_as_int(mz) - TWO23_BITS) - kz0;  // -1 or 0
                     const float lo = d < 0 ? B[0] : B[1];
                     const float hi = d < 0 ? B[1] : B[2];
-                    const float q = fmaf(fz, hi, (1.0f - fz) * lo);
+                    const float q = fmaf(fz, hi, fmaf(-fz, lo, lo));
                     best = pick<WFORM>(best, q);
                 }
             }

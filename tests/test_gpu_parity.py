@@ -407,6 +407,43 @@ def test_tile_shapes_agree_bitwise(hjb, orc, monkeypatch):
     assert np.abs(outs[0] - Vo).max() < TOL_V
 
 
+@pytest.mark.parametrize("A", [32, 64])
+def test_lane_split_agrees_bitwise(hjb, monkeypatch, A):
+    """The lane split of 32 x 4 tiles (lanes n and n + 16 of a warp take a_j
+    and -a_j of node n) evaluates the same foot products as the two control
+    groups (a_{j + A/2} = -a_j exactly, and negation is exact), and the
+    extremum does not depend on the order: V, the sweep counts and the
+    node-update counts are identical, with one and with six applications
+    per staged tile, for the full and the decomposed solve."""
+    n = 577
+    X, Y = S.mesh2(n, n)
+    g = S.rng("misc", 37)
+    lab = S.disk_labels(X, Y, S.disk_centers(g, 5, 0.1), 0.1)
+    ctrl = S.f32(S.circle_controls(A))
+    assert np.array_equal(ctrl[A // 2:], -ctrl[:A // 2])
+    d = dict(shape=(n, n), lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=(0, 0), dyn=0,
+             controls=ctrl, labels=lab, ntargets=5,
+             speed=S.f32(S.speed_field(g, X, Y)), current=S.f32(S.current_field(g, X, Y)),
+             h=2.0 / (n - 1), lam=1.0, v_out=1.0)
+    p = gpu_problem(hjb, d)
+    monkeypatch.setenv("HJB_TUNE", "off")
+    monkeypatch.setenv("HJB_TILE_ROWS", "4")
+    fine, _, _, _ = hjb.subdomains(p, (16, 16), delta=0.2)
+    runs = {}
+    for lanes in ("1", "2"):
+        monkeypatch.setenv("HJB_TILE_LANES", lanes)
+        for li in (1, 6):
+            V, st = hjb.solve(p, local_iters=li)
+            Vb, _, tot = hjb.solve_decomposed(p, fine, local_iters=li)
+            assert st["tile_lanes"] == int(lanes) and tot["tile_lanes"] == int(lanes)
+            runs[lanes, li] = (to_np(V), st["iterations"], st["node_updates"],
+                               to_np(Vb), tot["iterations"], tot["node_updates"])
+    for li in (1, 6):
+        a, b = runs["1", li], runs["2", li]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[3], b[3])
+        assert a[1:3] == b[1:3] and a[4:6] == b[4:6]
+
+
 @pytest.mark.parametrize("loop", ["graph", "coop"])
 def test_queue_schedules_agree_bitwise(hjb, monkeypatch, loop):
     """Static and dynamic sharing of a sweep's tile queue among the CTAs run
