@@ -278,9 +278,14 @@ def test_adjoint_1025_per_entry_finite_differences(hjb):
     solves warm-started from the converged V to 1e-15).  Entries where the
     optimal policy changes between theta_i +- eps at a node that carries
     adjoint mass are kinks -- the loss is not differentiable there -- and are
-    counted, not compared.  Every other entry agrees within 1e-3 relative."""
+    counted, not compared.  An entry whose difference quotient is at least
+    1e-3 of the largest one agrees within 1e-3 relative.  Below that the
+    quotient is at its own resolution (the loss is resolved to about 1e-15,
+    so a quotient to about 1e-10; eight entries are exactly 0), and the
+    entry is held to the absolute form of the bound, 1e-5 of the largest."""
     import torch
     gold = _golden("c5_fd_1025.json")
+    scale = max(abs(e["fd"]) for e in gold["entries"])
     d = S.c5()
     p = gpu_problem(hjb, d)
     V, _ = hjb.solve(p)
@@ -289,13 +294,20 @@ def test_adjoint_1025_per_entry_finite_differences(hjb):
     g, st = hjb.backward(p, V, gV, wrt=0)
     assert st["converged"] in (1, 2)
     g = to_np(g).astype(np.float64)
-    checked = 0
+    checked = small = 0
     worst = 0.0
     for e in gold["entries"]:
         if e["kink"]:
             continue
-        rel = abs(g[e["index"]] - e["fd"]) / abs(e["fd"])
-        worst = max(worst, rel)
-        assert rel <= 1e-3, (e["xy"], g[e["index"]], e["fd"])
-        checked += 1
-    assert checked >= 48, (checked, gold["kinks"])
+        err = abs(g[e["index"]] - e["fd"])
+        if abs(e["fd"]) >= 1e-3 * scale:
+            rel = err / abs(e["fd"])
+            worst = max(worst, rel)
+            assert rel <= 1e-3, (e["xy"], g[e["index"]], e["fd"])
+            checked += 1
+        else:
+            assert err <= 1e-5 * scale, (e["xy"], g[e["index"]], e["fd"])
+            small += 1
+    print("per-entry FD: %d resolved entries, worst relative %.2e; %d below resolution; %d kinks"
+          % (checked, worst, small, gold["kinks"]))
+    assert checked >= 48, (checked, small, gold["kinks"])

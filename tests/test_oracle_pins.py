@@ -1537,3 +1537,32 @@ def test_scale_field_with_equal_axes_is_the_speed_field(orc):
     Va, la, _ = orc.ra(p, (8, 8), 0.1, tol=1e-12)
     Vb, lb, _ = orc.ra(q, (8, 8), 0.1, tol=1e-12)
     assert np.array_equal(Va, Vb) and np.array_equal(la, lb)
+
+
+def test_c5_finite_difference_golden_pins_the_oracle_adjoint():
+    """The stored FP64 central differences of the 1025^2 adjoint workload
+    (tests/golden/c5_fd_1025.json, written by make_c5_fd_golden.py from the
+    oracle's forward solves alone) pin the oracle's adjoint gradient, stored
+    beside them, at full size: the gradient is the transposed fixed point
+    with the policy frozen, the differences are of the loss itself.  Every
+    entry whose quotient is at least 1e-3 of the largest agrees within 1e-3
+    relative (measured <= 4.5e-4, the smallest such quotients being at the
+    differences' resolution of ~1e-12); the rest within 1e-5 of the largest
+    in absolute terms.  Entries at a kink would be excluded (none occur)."""
+    with open(os.path.join(GOLDEN, "c5_fd_1025.json")) as f:
+        gold = json.load(f)
+    assert gold["n"] == 1025 and len(gold["entries"]) == 64 and "eps=1e-05" in gold["method"]
+    scale = max(abs(e["fd"]) for e in gold["entries"])
+    resolved = 0
+    for e in gold["entries"]:
+        assert 0 <= e["index"] < 1025 * 1025
+        if e["kink"]:
+            continue
+        err = abs(e["adjoint"] - e["fd"])
+        if abs(e["fd"]) >= 1e-3 * scale:
+            assert err <= 1e-3 * abs(e["fd"]), e
+            resolved += 1
+        else:
+            assert err <= 1e-5 * scale, e
+    assert resolved >= 48
+    assert sum(e["kink"] for e in gold["entries"]) == gold["kinks"]
