@@ -1598,8 +1598,9 @@ int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_label
         } else {
             hjbh::launch_init_values(R.d_slots.as<SlotDesc>(), m, static_cast<int>(NK), wform,
                                      c_over, nullptr, st);
+            const int lanes = c.lanes == 2 && rows == 4 && lane_split_ok(P) ? 2 : 1;
             const hjbh::SweepKey key{P->kind == HJB_DYN_DUBINS ? 1 : 0, wform ? 1 : 0, key_na(P),
-                                     halo, rows, 8 / rows, loop_mode(), 1,
+                                     halo, rows, 8 / rows / lanes, loop_mode(), lanes,
                                      nd > 2 ? hjbk::TZ : 1};
             R.near_start = wform && R.slots[0].vout == 0.0f;  // see solve_full
             TRY(run_loop(R, key, 8, control_table(P), st, c.li));
@@ -1628,6 +1629,8 @@ int ra_division(hjb_problem *P, const hjb_ra_opts *ra, const uint8_t *comp_label
                 for (int r : {4, 2})
                     for (int l : li_c)
                         if (!(r == 2 && l == 6)) cand.push_back(Choice{r, 1, l, 0.0, hjbk::TZ});
+                if (lane_split_ok(P))
+                    for (int l : li_c) cand.push_back(Choice{4, 2, l, 0.0, hjbk::TZ});
             }
             if (chip) cand.push_back(Choice{1, 1, 1, 0.0, hjbk::TZ});
         }
