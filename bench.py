@@ -572,17 +572,23 @@ def run_adjoint(args, hjb, S, dev, flush, local):
     ms, (g, st), clocks = _timed_steps(lambda: hjb.backward(p, V, gV, wrt=0), args.steps,
                                        args.warmup, flush, local)
     N = d["labels"].size
-    upd = N * st["iterations"]
+    # node-updates of the transposed iteration and of the refinement of the
+    # values the policy is decided on (a policy-frozen forward iteration)
+    ref = st["local_iters"]
+    upd = N * (st["iterations"] + ref)
     hbm = measured_peaks().get("hbm_gbs", 6660.0)
-    # per node and iteration: lambda read 4 B, policy 1 B, s 4 B, 4 scattered
-    # atomics 16 B, residual pass (two lambda reads, g read, lambda write) 16 B
-    ach = upd * 41 / (st["ms"] / 1e3) / 1e9
+    # per node and transposed iteration: lambda read 4 B, policy 1 B, s 4 B,
+    # 4 scattered atomics 16 B, residual pass (two lambda reads, g read,
+    # lambda write) 16 B; per node and refinement iteration: policy 1 B, r 4 B,
+    # s 4 B, the node's own correction read 4 B and write 4 B
+    ach = N * (41 * st["iterations"] + 17 * ref) / (st["ms"] / 1e3) / 1e9
     _line(args, "adjoint node-updates/s to convergence (transposed fixed point, policy frozen)",
           upd / (ms / 1e3), UNIT, ms, {"workload": "adjoint-%dx%d-A32-4096points" % tuple(d["shape"])},
-          iterations=st["iterations"], forward_iterations=fst["iterations"],
+          iterations=st["iterations"], refine_iterations=ref, forward_iterations=fst["iterations"],
           roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": None, "kernel": "adj_scatter + adj_resid",
-                    "bytes_per_node_iteration": 41},
+                    "frac": ach / hbm, "traffic": None,
+                    "kernel": "adj_scatter + adj_resid, refine_iter",
+                    "bytes_per_node_iteration": {"transposed": 41, "refinement": 17}},
           cpu_baseline=None, gpu_launches=st["launches"], clocks=clocks)
 
 

@@ -59,13 +59,6 @@ __device__ __forceinline__ Foot foot_of(const AdjProblem &ap, int gx, int gy, fl
     return f;
 }
 
-__device__ __forceinline__ float interp(const float *V, int nx, const Foot &f) {
-    const long long i = static_cast<long long>(f.cy) * nx + f.cx;
-    const float a = fmaf(f.tx, V[i + 1], (1.0f - f.tx) * V[i]);
-    const float b = fmaf(f.tx, V[i + nx + 1], (1.0f - f.tx) * V[i + nx]);
-    return fmaf(f.ty, b, (1.0f - f.ty) * a);
-}
-
 struct NodeDyn {
     float sx, sy, ox0, oy0, s;
 };
@@ -90,8 +83,48 @@ __device__ __forceinline__ NodeDyn node_dyn(const AdjProblem &ap, long long i) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < (n); \
          i += static_cast<long long>(gridDim.x) * blockDim.x)
 
+__device__ __forceinline__ double value_f64(const float *V, const float *dV, long long c) {
+    return dV ? static_cast<double>(V[c]) + static_cast<double>(dV[c]) : static_cast<double>(V[c]);
+}
+
+// The control value I[V + dV](foot) of one control in FP64: the foot
+// x + h (s a + c) in grid coordinates, outside the box beyond the 1e-6-cell
+// tolerance, clamped onto it otherwise, and the bilinear interpolation of
+// the values with the corner weights products of (1 - t) and t.  dV: the
+// refinement correction, or null.  Returns false for a foot outside the box.
+__device__ __forceinline__ bool control_value_f64(const AdjProblem &ap, const float *V,
+                                                  const float *dV, int gx, int gy, double s,
+                                                  double cx, double cy, float ax, float ay,
+                                                  double &q) {
+    const double ox = ap.hd * (s * static_cast<double>(ax) + cx) / ap.dxd;
+    const double oy = ap.hd * (s * static_cast<double>(ay) + cy) / ap.dyd;
+    if (ox < -static_cast<double>(gx) - 1e-6 || ox > static_cast<double>(ap.nx - 1 - gx) + 1e-6 ||
+        oy < -static_cast<double>(gy) - 1e-6 || oy > static_cast<double>(ap.ny - 1 - gy) + 1e-6)
+        return false;
+    const double px = fmin(fmax(gx + ox, 0.0), static_cast<double>(ap.nx - 1));
+    const double py = fmin(fmax(gy + oy, 0.0), static_cast<double>(ap.ny - 1));
+    int ix = static_cast<int>(floor(px)), iy = static_cast<int>(floor(py));
+    if (ix > ap.nx - 2) ix = ap.nx - 2;
+    if (iy > ap.ny - 2) iy = ap.ny - 2;
+    const double tx = px - ix, ty = py - iy;
+    const double ex = 1.0 - tx, ey = 1.0 - ty;
+    const long long c = static_cast<long long>(iy) * ap.nx + ix;
+    double acc = (ex * ey) * value_f64(V, dV, c);
+    acc += (tx * ey) * value_f64(V, dV, c + 1);
+    acc += (ex * ty) * value_f64(V, dV, c + ap.nx);
+    acc += (tx * ty) * value_f64(V, dV, c + ap.nx + 1);
+    q = acc;
+    return true;
+}
+
+// Optimal policy pi_i = argmin_j I[V](foot_j), lowest index on ties.  The
+// decision is taken in FP64 (the precision of the FP64 reference), on the
+// values V + dV (dV: the refinement correction, or null): in FP32 the
+// control values of neighbouring directions, which often differ by less
+// than their rounding at this step size, would pick another control at many
+// nodes and route adjoint mass differently.
 __global__ void policy_kernel(AdjProblem ap, const __grid_constant__ ControlTable C, const float *V,
-                              int8_t *policy, unsigned *ties) {
+                              const float *dV, int8_t *policy, unsigned *ties) {
     const long long N = static_cast<long long>(ap.nx) * ap.ny;
     unsigned nt = 0;
     GRID_STRIDE(i, N) {
@@ -100,28 +133,155 @@ __global__ void policy_kernel(AdjProblem ap, const __grid_constant__ ControlTabl
             continue;
         }
         const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
-        const NodeDyn d = node_dyn(ap, i);
-        float best = INFINITY, second = INFINITY;
+        const double s = ap.speed ? static_cast<double>(ap.speed[i]) : 1.0;
+        double cx = 0.0, cy = 0.0;
+        if (ap.current) {
+            const float2 c = reinterpret_cast<const float2 *>(ap.current)[i];
+            cx = c.x;
+            cy = c.y;
+        }
+        double best = INFINITY, second = INFINITY;
         int arg = 0;
         bool arg_inside = false;
         for (int j = 0; j < C.count; ++j) {
-            const Foot f = foot_of(ap, gx, gy, d.sx, d.sy, d.ox0, d.oy0, C.ax[j], C.ay[j]);
-            const float q = f.inside ? interp(V, ap.nx, f) : ap.vout;
+            double q = ap.vout;
+            const bool inside =
+                control_value_f64(ap, V, dV, gx, gy, s, cx, cy, C.ax[j], C.ay[j], q);
             if (q < best) {
                 second = best;
                 best = q;
                 arg = j;
-                arg_inside = f.inside;
+                arg_inside = inside;
             } else if (q < second) {
                 second = q;
             }
         }
-        if (second - best <= 1e-6f) ++nt;
+        if (second - best <= 1e-6) ++nt;
         policy[i] = arg_inside ? static_cast<int8_t>(arg) : static_cast<int8_t>(-2);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nt += __shfl_xor_sync(0xffffffffu, nt, o);
     if ((threadIdx.x & 31) == 0 && nt) atomicAdd(ties, nt);
+}
+
+// Iterative refinement (mixed precision) of the values the policy is
+// decided on.  The FP32 fixed point V differs from the FP64 one by the
+// rounding carried along the characteristics (about 1e-6 at 1025^2), enough
+// to pick the runner-up control where two directions are closer than that.
+// With the policy pi frozen, V solves the linear system
+// V = beta P_pi V + gamma l; its residual r is taken in FP64 and the
+// correction dV = r + beta P_pi dV, a small quantity, is iterated in FP32
+// (its own rounding is then ~1e-7 of ~1e-6).  The policy is decided again on
+// V + dV, the exact FP64 values of pi up to that rounding.
+__global__ void refine_residual_kernel(AdjProblem ap, const __grid_constant__ ControlTable C,
+                                       const float *V, const int8_t *policy, float *r) {
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    GRID_STRIDE(i, N) {
+        const int p = policy[i];
+        if (p == -1) {
+            r[i] = 0.0f;  // target (value fixed)
+            continue;
+        }
+        double q = ap.vout;  // p == -2: the best foot leaves the box
+        if (p >= 0) {
+            const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
+            const double s = ap.speed ? static_cast<double>(ap.speed[i]) : 1.0;
+            double cx = 0.0, cy = 0.0;
+            if (ap.current) {
+                const float2 c = reinterpret_cast<const float2 *>(ap.current)[i];
+                cx = c.x;
+                cy = c.y;
+            }
+            control_value_f64(ap, V, nullptr, gx, gy, s, cx, cy, C.ax[p], C.ay[p], q);
+        }
+        const double l = ap.cost ? static_cast<double>(ap.cost[i]) : ap.lconst;
+        r[i] = static_cast<float>(ap.betad * q + ap.gammad * l - static_cast<double>(V[i]));
+    }
+}
+
+// One Jacobi iteration dV_dst = r + beta P_pi dV_src (A.g = r, A.L = dV);
+// the last CTA takes the stopping decision: the change within 4 ulp of
+// max|dV| (the FP32 floor of this iteration), or 256 iterations without a
+// new minimum once below 64 ulp, or the iteration cap.
+__global__ void refine_iter(const __grid_constant__ AdjArgs A) {
+    AdjCtl *ctl = A.ctl;
+    if (ctl->converged) return;
+    const AdjProblem &ap = A.ap;
+    const int par = ctl->parity;
+    const float *src = A.L[par];
+    float *dst = A.L[par ^ 1];
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    float r = 0.0f, a = 0.0f;
+    GRID_STRIDE(i, N) {
+        const int p = A.policy[i];
+        float d = 0.0f;
+        if (p != -1) {
+            d = A.g[i];
+            if (p >= 0) {
+                const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
+                const NodeDyn nd = node_dyn(ap, i);
+                const Foot f = foot_of(ap, gx, gy, nd.sx, nd.sy, nd.ox0, nd.oy0, A.ctrl.ax[p],
+                                       A.ctrl.ay[p]);
+                const long long c = static_cast<long long>(f.cy) * ap.nx + f.cx;
+                const float lo = fmaf(f.tx, src[c + 1], fmaf(-f.tx, src[c], src[c]));
+                const float hi =
+                    fmaf(f.tx, src[c + ap.nx + 1], fmaf(-f.tx, src[c + ap.nx], src[c + ap.nx]));
+                d = fmaf(ap.beta, fmaf(f.ty, hi, fmaf(-f.ty, lo, lo)), d);
+            }
+        }
+        dst[i] = d;
+        r = fmaxf(r, fabsf(d - src[i]));
+        a = fmaxf(a, fabsf(d));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    }
+    __shared__ float s_r[THREADS / 32], s_a[THREADS / 32];
+    __shared__ int s_last;
+    if ((threadIdx.x & 31) == 0) {
+        s_r[threadIdx.x >> 5] = r;
+        s_a[threadIdx.x >> 5] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = s_r[0], ma = s_a[0];
+        for (int w = 1; w < THREADS / 32; ++w) {
+            m = fmaxf(m, s_r[w]);
+            ma = fmaxf(ma, s_a[w]);
+        }
+        atomicMax(&ctl->res_bits, __float_as_uint(m));
+        atomicMax(&ctl->lam_bits, __float_as_uint(ma));
+        __threadfence();
+        s_last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const float res = __uint_as_float(ctl->res_bits);
+        const float amax = __uint_as_float(ctl->lam_bits);
+        ctl->res_bits = 0u;
+        ctl->lam_bits = 0u;
+        ctl->iters += 1;
+        ctl->final_res = res;
+        ctl->lam_max = amax;
+        ctl->parity = par ^ 1;
+        ctl->done_ctas = 0u;
+        constexpr float EPS = 1.1920929e-7f;
+        if (res < ctl->best_res) {
+            ctl->best_res = res;
+            ctl->stall = 0;
+        } else {
+            ctl->stall += 1;
+        }
+        if (res <= 4.0f * EPS * amax ||
+            (ctl->stall >= 256 && ctl->best_res <= 64.0f * EPS * amax))
+            ctl->converged = 2;
+        else if (ctl->iters >= ctl->max_iters)
+            ctl->converged = 3;
+        __threadfence();
+    }
 }
 
 // lambda_dst += beta P_pi^T lambda_src (dst pre-armed with g).
@@ -323,11 +483,19 @@ int blocks_for(long long n) {
 
 namespace hjbh {
 
-void launch_policy(const AdjProblem &ap, const ControlTable &C, const float *V, int8_t *policy,
-                   unsigned *ties_out, cudaStream_t st) {
+void launch_policy(const AdjProblem &ap, const ControlTable &C, const float *V, const float *dV,
+                   int8_t *policy, unsigned *ties_out, cudaStream_t st) {
     const long long N = static_cast<long long>(ap.nx) * ap.ny;
-    policy_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, policy, ties_out);
+    policy_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, dV, policy, ties_out);
 }
+
+void launch_refine_residual(const AdjProblem &ap, const ControlTable &C, const float *V,
+                            const int8_t *policy, float *r, cudaStream_t st) {
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    refine_residual_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, policy, r);
+}
+
+const void *refine_iter_kernel() { return reinterpret_cast<const void *>(&refine_iter); }
 
 const void *adj_scatter_kernel() { return reinterpret_cast<const void *>(&adj_scatter_guarded); }
 const void *adj_resid_kernel() { return reinterpret_cast<const void *>(&adj_resid); }

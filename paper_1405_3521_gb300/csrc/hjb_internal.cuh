@@ -261,6 +261,9 @@ void launch_popcount(const uint32_t *mask, long long n, unsigned long long *out,
 struct AdjProblem {
     int nx, ny;
     float hx, hy;        // h / dx, h / dy
+    double hd, dxd, dyd; // h, dx, dy in FP64 (the policy decision)
+    double betad, gammad, lconst;  // step weights and constant cost in FP64
+    const float *cost;   // running cost field l (or null: lconst)
     float dx, dy;
     float beta, gamma, h;
     float vout;          // value of feet outside the box (V form)
@@ -289,7 +292,14 @@ struct AdjCtl {
 // pi_i = argmin_j I[V](foot_j) (lowest index on ties), -1 on targets, -2
 // when the minimising foot is outside the box (a zero row of P_pi).
 void launch_policy(const AdjProblem &ap, const hjbk::ControlTable &C, const float *V,
-                   int8_t *policy, unsigned *ties_out, cudaStream_t st);
+                   const float *dV, int8_t *policy, unsigned *ties_out, cudaStream_t st);
+// Iterative refinement of the values the policy is decided on: r = the FP64
+// residual (beta I[V](foot_pi) + gamma l) - V of the policy-frozen equation,
+// and one Jacobi iteration dV <- r + beta P_pi dV (FP32) per launch of the
+// refinement kernel (AdjArgs: g = r, L = the two dV buffers).
+void launch_refine_residual(const AdjProblem &ap, const hjbk::ControlTable &C, const float *V,
+                            const int8_t *policy, float *r, cudaStream_t st);
+const void *refine_iter_kernel();
 // Graph-able adjoint iteration kernels.
 const void *adj_scatter_kernel();
 const void *adj_resid_kernel();

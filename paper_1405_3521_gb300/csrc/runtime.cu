@@ -226,7 +226,7 @@ struct hjb_problem {
     RunCtx full, ra, dec;
     RunCtx *batch = nullptr;
     // adjoint workspaces
-    DevBuf adj_policy, adj_g, adj_L, adj_ctl, adj_v;
+    DevBuf adj_policy, adj_g, adj_L, adj_ctl, adj_v, adj_ref;
     cudaGraph_t adj_graph = nullptr;
     cudaGraphExec_t adj_exec = nullptr;
     hjbh::AdjArgs adj_args_in_graph;
@@ -1363,6 +1363,7 @@ int hjb_destroy(hjb_problem *P) {
     P->adj_g.release();
     P->adj_L.release();
     P->adj_ctl.release();
+    P->adj_ref.release();
     P->adj_v.release();
     DevBuf *bufs[] = {&P->speed_exp, &P->trig,     &P->c_speed,      &P->c_current,
                       &P->c_cost,    &P->c_labels, &P->c_trig,       &P->c_mask,
@@ -2230,10 +2231,17 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     ap.ny = P->grid.n[1];
     ap.hx = static_cast<float>(P->h / P->dx[0]);
     ap.hy = static_cast<float>(P->h / P->dx[1]);
+    ap.hd = P->h;
+    ap.dxd = P->dx[0];
+    ap.dyd = P->dx[1];
     ap.dx = static_cast<float>(P->dx[0]);
     ap.dy = static_cast<float>(P->dx[1]);
-    ap.beta = static_cast<float>(beta_w(P->weights, P->lambda, P->h));
-    ap.gamma = static_cast<float>(gamma_w(P->weights, P->lambda, P->h));
+    ap.betad = beta_w(P->weights, P->lambda, P->h);
+    ap.gammad = gamma_w(P->weights, P->lambda, P->h);
+    ap.lconst = P->l_const;
+    ap.cost = pr.cost;
+    ap.beta = static_cast<float>(ap.betad);
+    ap.gamma = static_cast<float>(ap.gammad);
     ap.h = static_cast<float>(P->h);
     ap.vout = static_cast<float>(P->value_out);
     ap.speed = pr.speed;
@@ -2253,7 +2261,56 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     OutArr out;
     TRY(out.init(grad_out, N * sizeof(float), &P->out_stage));
     CK(cudaEventRecord(R.ev0, st));
-    hjbh::launch_policy(ap, ctrl, P->adj_v.as<float>(), P->adj_policy.as<int8_t>(), d_ties, st);
+    hjbh::launch_policy(ap, ctrl, P->adj_v.as<float>(), nullptr, P->adj_policy.as<int8_t>(), d_ties,
+                        st);
+    long long ref_launches = 0;
+    int ref_iters = 0;
+    {
+        // iterative refinement of the values the policy is decided on (see
+        // refine_residual_kernel): HJB_ADJ_REFINE rounds, default 1, 0 = none
+        const char *e = std::getenv("HJB_ADJ_REFINE");
+        const int rounds = e ? std::max(0, std::min(4, std::atoi(e))) : 1;
+        if (rounds > 0) TRY(P->adj_ref.ensure(3 * N * sizeof(float)));
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int round = 0; round < rounds; ++round) {
+            float *r = P->adj_ref.as<float>(), *D0 = r + N, *D1 = D0 + N;
+            hjbh::launch_refine_residual(ap, ctrl, P->adj_v.as<float>(), P->adj_policy.as<int8_t>(),
+                                         r, st);
+            hjbh::launch_adj_init(r, D0, D1, N, ctl, 0.0f, 20000, st);
+            hjbh::AdjArgs ra;
+            std::memset(&ra, 0, sizeof ra);
+            ra.ap = ap;
+            ra.ctrl = ctrl;
+            ra.policy = P->adj_policy.as<int8_t>();
+            ra.g = r;
+            ra.L[0] = D0;
+            ra.L[1] = D1;
+            ra.ctl = ctl;
+            void *argv[1] = {&ra};
+            hjbh::AdjCtl hr;
+            // 32 iterations between reads of the stopping flag (at most 20000)
+            for (;;) {
+                for (int k = 0; k < 32; ++k)
+                    CK(cudaLaunchKernel(hjbh::refine_iter_kernel(), dim3(sms * 8),
+                                        dim3(hjbk::THREADS), argv, 0, st));
+                ref_launches += 32;
+                CK(cudaMemcpyAsync(&hr, ctl, sizeof hr, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (hr.converged) break;
+            }
+            if (hr.converged != 2)
+                return fail(HJB_ERR_NOT_CONVERGED,
+                            "refinement of the policy values not converged after %d iterations",
+                            hr.iters);
+            ref_iters += hr.iters;
+            CK(cudaMemsetAsync(d_ties, 0, sizeof(unsigned), st));
+            hjbh::launch_policy(ap, ctrl, P->adj_v.as<float>(), hr.parity ? D1 : D0,
+                                P->adj_policy.as<int8_t>(), d_ties, st);
+            ref_launches += 3;
+        }
+    }
     hjbh::launch_adj_init(P->adj_g.as<float>(), L0, L1, N, ctl, static_cast<float>(tol), max_iters,
                           st);
     // graph: WHILE { scatter; residual } x 2
@@ -2349,7 +2406,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
         stats->final_residual = hc.final_res;
         stats->node_updates = static_cast<long long>(hc.iters) * N;
         stats->ties = ties;
-        stats->launches = pr.launches + 3 + 4LL * ((hc.iters + 1) / 2);
+        stats->launches = pr.launches + 3 + 4LL * ((hc.iters + 1) / 2) + ref_launches;
+        stats->local_iters = ref_iters;  // iterations of the policy-value refinement
         float ms = 0;
         cudaEventElapsedTime(&ms, R.ev0, R.ev1);
         stats->ms = ms;
