@@ -59,9 +59,10 @@ def parse():
                     help="dubins / adjoint: a reduced size (126x126x64 / 257^2) for detailed "
                          "profiler captures; not a benchmark configuration")
     ap.add_argument("--profile", choices=["full", "decomposed", "ra"], default=None,
-                    help="run one solve of that path (after one warm-up; decomposed: once per 2D "
-                         "tile shape) for a profiler; "
-                         "prints per-solve statistics instead of the JSON line")
+                    help="run one solve of that path (zermelo: the full solve, the reconstruction, "
+                         "or the reconstruction and the decomposed solve; dubins: one step; "
+                         "adjoint: the forward solve and one backward) for a profiler; prints "
+                         "per-solve statistics instead of the JSON line")
     return ap.parse_args()
 
 
@@ -569,6 +570,11 @@ def run_adjoint(args, hjb, S, dev, flush, local):
     V, fst = hjb.solve(p)
     pts = dev(d["points"])
     _, gV = hjb.point_values(p, V, pts)
+    if args.profile:
+        _, st = hjb.backward(p, V, gV, wrt=0)
+        torch.cuda.synchronize()
+        print(json.dumps({"forward": fst, "backward": st}))
+        return
     ms, (g, st), clocks = _timed_steps(lambda: hjb.backward(p, V, gV, wrt=0), args.steps,
                                        args.warmup, flush, local)
     N = d["labels"].size
