@@ -117,14 +117,39 @@ __device__ __forceinline__ bool control_value_f64(const AdjProblem &ap, const fl
     return true;
 }
 
+// FP32 value of one control for the prefilter of the policy decision: the
+// bilinear interpolation of V at the clamped foot, v_out outside the box;
+// where the foot lies within 1e-4 cells of the box tolerance (so that the
+// FP64 test may decide the other way) the smaller of the two.
+__device__ __forceinline__ float control_value_f32(const AdjProblem &ap, const float *V, int gx,
+                                                   int gy, float sx, float sy, float ox0,
+                                                   float oy0, float ax, float ay) {
+    const float ox = fmaf(sx, ax, ox0), oy = fmaf(sy, ay, oy0);
+    const float lox = -static_cast<float>(gx), hix = static_cast<float>(ap.nx - 1 - gx);
+    const float loy = -static_cast<float>(gy), hiy = static_cast<float>(ap.ny - 1 - gy);
+    const bool out = (ox < lox - 1e-6f) | (ox > hix + 1e-6f) | (oy < loy - 1e-6f) |
+                     (oy > hiy + 1e-6f);
+    const bool amb = fabsf(ox - lox) < 1e-4f || fabsf(ox - hix) < 1e-4f ||
+                     fabsf(oy - loy) < 1e-4f || fabsf(oy - hiy) < 1e-4f;
+    if (out && !amb) return ap.vout;
+    const Foot f = foot_of(ap, gx, gy, sx, sy, ox0, oy0, ax, ay);
+    const long long c = static_cast<long long>(f.cy) * ap.nx + f.cx;
+    const float lo = fmaf(f.tx, V[c + 1], fmaf(-f.tx, V[c], V[c]));
+    const float hi = fmaf(f.tx, V[c + ap.nx + 1], fmaf(-f.tx, V[c + ap.nx], V[c + ap.nx]));
+    const float q = fmaf(f.ty, hi, fmaf(-f.ty, lo, lo));
+    return amb ? fminf(q, ap.vout) : q;
+}
+
 // Optimal policy pi_i = argmin_j I[V](foot_j), lowest index on ties.  The
 // decision is taken in FP64 (the precision of the FP64 reference), on the
 // values V + dV (dV: the refinement correction, or null): in FP32 the
 // control values of neighbouring directions, which often differ by less
 // than their rounding at this step size, would pick another control at many
-// nodes and route adjoint mass differently.
+// nodes and route adjoint mass differently.  An FP32 pass over every control
+// finds the best FP32 value; only controls within `margin` of it (above the
+// FP32 error of a control value plus twice max|dV|) are evaluated in FP64.
 __global__ void policy_kernel(AdjProblem ap, const __grid_constant__ ControlTable C, const float *V,
-                              const float *dV, int8_t *policy, unsigned *ties) {
+                              const float *dV, float margin, int8_t *policy, unsigned *ties) {
     const long long N = static_cast<long long>(ap.nx) * ap.ny;
     unsigned nt = 0;
     GRID_STRIDE(i, N) {
@@ -133,6 +158,12 @@ __global__ void policy_kernel(AdjProblem ap, const __grid_constant__ ControlTabl
             continue;
         }
         const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
+        const NodeDyn nd = node_dyn(ap, i);
+        float best32 = INFINITY;
+        for (int j = 0; j < C.count; ++j)
+            best32 = fminf(best32, control_value_f32(ap, V, gx, gy, nd.sx, nd.sy, nd.ox0, nd.oy0,
+                                                     C.ax[j], C.ay[j]));
+        const float cut = best32 + margin * fmaxf(1.0f, fabsf(best32));
         const double s = ap.speed ? static_cast<double>(ap.speed[i]) : 1.0;
         double cx = 0.0, cy = 0.0;
         if (ap.current) {
@@ -144,6 +175,9 @@ __global__ void policy_kernel(AdjProblem ap, const __grid_constant__ ControlTabl
         int arg = 0;
         bool arg_inside = false;
         for (int j = 0; j < C.count; ++j) {
+            if (control_value_f32(ap, V, gx, gy, nd.sx, nd.sy, nd.ox0, nd.oy0, C.ax[j],
+                                  C.ay[j]) > cut)
+                continue;
             double q = ap.vout;
             const bool inside =
                 control_value_f64(ap, V, dV, gx, gy, s, cx, cy, C.ax[j], C.ay[j], q);
@@ -162,6 +196,27 @@ __global__ void policy_kernel(AdjProblem ap, const __grid_constant__ ControlTabl
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nt += __shfl_xor_sync(0xffffffffu, nt, o);
     if ((threadIdx.x & 31) == 0 && nt) atomicAdd(ties, nt);
+}
+
+// The foot of each node's policy control (FP32, the arithmetic of the
+// sweep's boundary path): corner cell index and fractions; -1 for targets,
+// -2 for a foot outside the box.
+__global__ void feet_kernel(AdjProblem ap, const __grid_constant__ ControlTable C,
+                            const int8_t *policy, int *cell, float2 *frac) {
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    GRID_STRIDE(i, N) {
+        const int p = policy[i];
+        if (p < 0) {
+            cell[i] = p == -1 ? -1 : -2;
+            frac[i] = make_float2(0.0f, 0.0f);
+            continue;
+        }
+        const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
+        const NodeDyn d = node_dyn(ap, i);
+        const Foot f = foot_of(ap, gx, gy, d.sx, d.sy, d.ox0, d.oy0, C.ax[p], C.ay[p]);
+        cell[i] = f.cy * ap.nx + f.cx;
+        frac[i] = make_float2(f.tx, f.ty);
+    }
 }
 
 // Iterative refinement (mixed precision) of the values the policy is
@@ -213,20 +268,16 @@ __global__ void refine_iter(const __grid_constant__ AdjArgs A) {
     const long long N = static_cast<long long>(ap.nx) * ap.ny;
     float r = 0.0f, a = 0.0f;
     GRID_STRIDE(i, N) {
-        const int p = A.policy[i];
+        const int c = A.cell[i];
         float d = 0.0f;
-        if (p != -1) {
+        if (c != -1) {
             d = A.g[i];
-            if (p >= 0) {
-                const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
-                const NodeDyn nd = node_dyn(ap, i);
-                const Foot f = foot_of(ap, gx, gy, nd.sx, nd.sy, nd.ox0, nd.oy0, A.ctrl.ax[p],
-                                       A.ctrl.ay[p]);
-                const long long c = static_cast<long long>(f.cy) * ap.nx + f.cx;
-                const float lo = fmaf(f.tx, src[c + 1], fmaf(-f.tx, src[c], src[c]));
+            if (c >= 0) {
+                const float2 t = A.frac[i];
+                const float lo = fmaf(t.x, src[c + 1], fmaf(-t.x, src[c], src[c]));
                 const float hi =
-                    fmaf(f.tx, src[c + ap.nx + 1], fmaf(-f.tx, src[c + ap.nx], src[c + ap.nx]));
-                d = fmaf(ap.beta, fmaf(f.ty, hi, fmaf(-f.ty, lo, lo)), d);
+                    fmaf(t.x, src[c + ap.nx + 1], fmaf(-t.x, src[c + ap.nx], src[c + ap.nx]));
+                d = fmaf(ap.beta, fmaf(t.y, hi, fmaf(-t.y, lo, lo)), d);
             }
         }
         dst[i] = d;
@@ -292,19 +343,16 @@ __device__ __forceinline__ void scatter_body(const AdjArgs &A) {
     float *dst = A.L[par ^ 1];
     const long long N = static_cast<long long>(ap.nx) * ap.ny;
     GRID_STRIDE(i, N) {
-        const int p = A.policy[i];
-        if (p < 0) continue;
+        const int c = A.cell[i];
+        if (c < 0) continue;
         const float lam = src[i];
         if (lam == 0.0f) continue;
-        const int gx = static_cast<int>(i % ap.nx), gy = static_cast<int>(i / ap.nx);
-        const NodeDyn d = node_dyn(ap, i);
-        const Foot f = foot_of(ap, gx, gy, d.sx, d.sy, d.ox0, d.oy0, A.ctrl.ax[p], A.ctrl.ay[p]);
+        const float2 t = A.frac[i];
         const float bl = ap.beta * lam;
-        const long long c = static_cast<long long>(f.cy) * ap.nx + f.cx;
-        atomicAdd(dst + c, bl * (1.0f - f.tx) * (1.0f - f.ty));
-        atomicAdd(dst + c + 1, bl * f.tx * (1.0f - f.ty));
-        atomicAdd(dst + c + ap.nx, bl * (1.0f - f.tx) * f.ty);
-        atomicAdd(dst + c + ap.nx + 1, bl * f.tx * f.ty);
+        atomicAdd(dst + c, bl * (1.0f - t.x) * (1.0f - t.y));
+        atomicAdd(dst + c + 1, bl * t.x * (1.0f - t.y));
+        atomicAdd(dst + c + ap.nx, bl * (1.0f - t.x) * t.y);
+        atomicAdd(dst + c + ap.nx + 1, bl * t.x * t.y);
     }
 }
 
@@ -484,9 +532,15 @@ int blocks_for(long long n) {
 namespace hjbh {
 
 void launch_policy(const AdjProblem &ap, const ControlTable &C, const float *V, const float *dV,
-                   int8_t *policy, unsigned *ties_out, cudaStream_t st) {
+                   float margin, int8_t *policy, unsigned *ties_out, cudaStream_t st) {
     const long long N = static_cast<long long>(ap.nx) * ap.ny;
-    policy_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, dV, policy, ties_out);
+    policy_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, dV, margin, policy, ties_out);
+}
+
+void launch_feet(const AdjProblem &ap, const ControlTable &C, const int8_t *policy, int *cell,
+                 float2 *frac, cudaStream_t st) {
+    const long long N = static_cast<long long>(ap.nx) * ap.ny;
+    feet_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, policy, cell, frac);
 }
 
 void launch_refine_residual(const AdjProblem &ap, const ControlTable &C, const float *V,

@@ -292,7 +292,12 @@ struct AdjCtl {
 // pi_i = argmin_j I[V](foot_j) (lowest index on ties), -1 on targets, -2
 // when the minimising foot is outside the box (a zero row of P_pi).
 void launch_policy(const AdjProblem &ap, const hjbk::ControlTable &C, const float *V,
-                   const float *dV, int8_t *policy, unsigned *ties_out, cudaStream_t st);
+                   const float *dV, float margin, int8_t *policy, unsigned *ties_out,
+                   cudaStream_t st);
+// The foot of every node's policy control in FP32 (cell index and fractions,
+// see AdjArgs::cell), once per policy decision.
+void launch_feet(const AdjProblem &ap, const hjbk::ControlTable &C, const int8_t *policy, int *cell,
+                 float2 *frac, cudaStream_t st);
 // Iterative refinement of the values the policy is decided on: r = the FP64
 // residual (beta I[V](foot_pi) + gamma l) - V of the policy-frozen equation,
 // and one Jacobi iteration dV <- r + beta P_pi dV (FP32) per launch of the
@@ -312,6 +317,10 @@ struct AdjArgs {
     AdjCtl *ctl;
     int use_handle;
     cudaGraphConditionalHandle handle;
+    // the foot of each node's policy control (launch_feet): corner cell
+    // index (-1 target, -2 foot outside the box) and fractions (tx, ty)
+    const int *cell;
+    const float2 *frac;
 };
 void launch_adj_init(const float *g, float *L0, float *L1, long long n, AdjCtl *ctl, float tol,
                      int max_iters, cudaStream_t st);

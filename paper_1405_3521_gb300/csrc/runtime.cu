@@ -19,6 +19,11 @@ using hjbk::Ctl;
 using hjbk::SlotDesc;
 using hjbk::SlotState;
 
+// CTAs per SM of the adjoint's iteration kernels (grid-stride over the nodes).
+#ifndef HJB_ADJ_BLOCKS_PER_SM
+#define HJB_ADJ_BLOCKS_PER_SM 8
+#endif
+
 namespace {
 
 thread_local std::string g_err;
@@ -226,7 +231,7 @@ struct hjb_problem {
     RunCtx full, ra, dec;
     RunCtx *batch = nullptr;
     // adjoint workspaces
-    DevBuf adj_policy, adj_g, adj_L, adj_ctl, adj_v, adj_ref;
+    DevBuf adj_policy, adj_g, adj_L, adj_ctl, adj_v, adj_ref, adj_cell, adj_frac;
     cudaGraph_t adj_graph = nullptr;
     cudaGraphExec_t adj_exec = nullptr;
     hjbh::AdjArgs adj_args_in_graph;
@@ -1364,6 +1369,8 @@ int hjb_destroy(hjb_problem *P) {
     P->adj_L.release();
     P->adj_ctl.release();
     P->adj_ref.release();
+    P->adj_cell.release();
+    P->adj_frac.release();
     P->adj_v.release();
     DevBuf *bufs[] = {&P->speed_exp, &P->trig,     &P->c_speed,      &P->c_current,
                       &P->c_cost,    &P->c_labels, &P->c_trig,       &P->c_mask,
@@ -2221,6 +2228,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     CK(cudaMemcpyAsync(P->adj_v.p, v, N * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaMemcpyAsync(P->adj_g.p, grad_v, N * sizeof(float), cudaMemcpyDefault, st));
     TRY(P->adj_policy.ensure(N));
+    TRY(P->adj_cell.ensure(N * sizeof(int)));
+    TRY(P->adj_frac.ensure(N * sizeof(float2)));
     TRY(P->adj_L.ensure(2 * N * sizeof(float)));
     TRY(P->adj_ctl.ensure(sizeof(hjbh::AdjCtl)));
     TRY(P->scratch_u64.ensure(64));
@@ -2261,8 +2270,13 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     OutArr out;
     TRY(out.init(grad_out, N * sizeof(float), &P->out_stage));
     CK(cudaEventRecord(R.ev0, st));
-    hjbh::launch_policy(ap, ctrl, P->adj_v.as<float>(), nullptr, P->adj_policy.as<int8_t>(), d_ties,
-                        st);
+    // controls within this relative margin of the best FP32 value are decided
+    // in FP64 (the FP32 error of a control value is a few ulp)
+    constexpr float POLICY_MARGIN = 1e-5f;
+    hjbh::launch_policy(ap, ctrl, P->adj_v.as<float>(), nullptr, POLICY_MARGIN,
+                        P->adj_policy.as<int8_t>(), d_ties, st);
+    hjbh::launch_feet(ap, ctrl, P->adj_policy.as<int8_t>(), P->adj_cell.as<int>(),
+                      P->adj_frac.as<float2>(), st);
     long long ref_launches = 0;
     int ref_iters = 0;
     {
@@ -2288,12 +2302,14 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
             ra.L[0] = D0;
             ra.L[1] = D1;
             ra.ctl = ctl;
+            ra.cell = P->adj_cell.as<int>();
+            ra.frac = P->adj_frac.as<float2>();
             void *argv[1] = {&ra};
             hjbh::AdjCtl hr;
             // 32 iterations between reads of the stopping flag (at most 20000)
             for (;;) {
                 for (int k = 0; k < 32; ++k)
-                    CK(cudaLaunchKernel(hjbh::refine_iter_kernel(), dim3(sms * 8),
+                    CK(cudaLaunchKernel(hjbh::refine_iter_kernel(), dim3(sms * HJB_ADJ_BLOCKS_PER_SM),
                                         dim3(hjbk::THREADS), argv, 0, st));
                 ref_launches += 32;
                 CK(cudaMemcpyAsync(&hr, ctl, sizeof hr, cudaMemcpyDeviceToHost, st));
@@ -2307,8 +2323,11 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
             ref_iters += hr.iters;
             CK(cudaMemsetAsync(d_ties, 0, sizeof(unsigned), st));
             hjbh::launch_policy(ap, ctrl, P->adj_v.as<float>(), hr.parity ? D1 : D0,
-                                P->adj_policy.as<int8_t>(), d_ties, st);
-            ref_launches += 3;
+                                POLICY_MARGIN + 2.0f * hr.lam_max, P->adj_policy.as<int8_t>(),
+                                d_ties, st);
+            hjbh::launch_feet(ap, ctrl, P->adj_policy.as<int8_t>(), P->adj_cell.as<int>(),
+                              P->adj_frac.as<float2>(), st);
+            ref_launches += 4;
         }
     }
     hjbh::launch_adj_init(P->adj_g.as<float>(), L0, L1, N, ctl, static_cast<float>(tol), max_iters,
@@ -2324,6 +2343,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     args.L[1] = L1;
     args.ctl = ctl;
     args.use_handle = 1;
+    args.cell = P->adj_cell.as<int>();
+    args.frac = P->adj_frac.as<float2>();
     const char *ng = std::getenv("HJB_NO_GRAPH");
     if (ng && ng[0] == '1') {
         // host-driven loop (profiling aid): the same kernels, 8 iterations
@@ -2337,7 +2358,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
         for (;;) {
             for (int rep = 0; rep < 8; ++rep)
                 for (int k = 0; k < 2; ++k)
-                    CK(cudaLaunchKernel(fns[k], dim3(sms * 8), dim3(hjbk::THREADS), argv, 0, st));
+                    CK(cudaLaunchKernel(fns[k], dim3(sms * HJB_ADJ_BLOCKS_PER_SM),
+                                        dim3(hjbk::THREADS), argv, 0, st));
             int conv = 0;
             CK(cudaMemcpyAsync(&conv, &ctl->converged, sizeof conv, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -2346,7 +2368,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     } else if (!P->adj_exec || std::memcmp(&P->adj_args_in_graph.ap, &args.ap, sizeof args.ap) ||
         std::memcmp(&P->adj_args_in_graph.ctrl, &args.ctrl, sizeof args.ctrl) ||
         P->adj_args_in_graph.L[0] != L0 || P->adj_args_in_graph.policy != args.policy ||
-        P->adj_args_in_graph.g != args.g || P->adj_args_in_graph.ctl != ctl) {
+        P->adj_args_in_graph.g != args.g || P->adj_args_in_graph.ctl != ctl ||
+        P->adj_args_in_graph.cell != args.cell || P->adj_args_in_graph.frac != args.frac) {
         if (P->adj_exec) cudaGraphExecDestroy(P->adj_exec);
         if (P->adj_graph) cudaGraphDestroy(P->adj_graph);
         P->adj_exec = nullptr;
@@ -2375,7 +2398,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
                 cudaKernelNodeParams kp;
                 std::memset(&kp, 0, sizeof kp);
                 kp.func = const_cast<void *>(fns[k]);
-                kp.gridDim = dim3(sms * 8);
+                kp.gridDim = dim3(sms * HJB_ADJ_BLOCKS_PER_SM);
                 kp.blockDim = dim3(hjbk::THREADS);
                 void *argv[1] = {&args};
                 kp.kernelParams = argv;
@@ -2406,7 +2429,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
         stats->final_residual = hc.final_res;
         stats->node_updates = static_cast<long long>(hc.iters) * N;
         stats->ties = ties;
-        stats->launches = pr.launches + 3 + 4LL * ((hc.iters + 1) / 2) + ref_launches;
+        stats->launches = pr.launches + 4 + 4LL * ((hc.iters + 1) / 2) + ref_launches;
         stats->local_iters = ref_iters;  // iterations of the policy-value refinement
         float ms = 0;
         cudaEventElapsedTime(&ms, R.ev0, R.ev1);
