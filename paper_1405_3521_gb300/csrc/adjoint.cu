@@ -332,6 +332,7 @@ __global__ void refine_iter(const __grid_constant__ AdjArgs A) {
         else if (ctl->iters >= ctl->max_iters)
             ctl->converged = 3;
         __threadfence();
+        if (A.use_handle) cudaGraphSetConditional(A.handle, ctl->converged ? 0u : 1u);
     }
 }
 

@@ -19,9 +19,12 @@ using hjbk::Ctl;
 using hjbk::SlotDesc;
 using hjbk::SlotState;
 
-// CTAs per SM of the adjoint's iteration kernels (grid-stride over the nodes).
+// CTAs per SM of the adjoint's iteration kernels (grid-stride over the
+// nodes).  Every iteration ends in one same-address atomic per CTA and a
+// last-CTA decision, so fewer, longer-lived CTAs win: measured at 1025^2
+// (backward, 2 / 3 / 4 / 6 / 8 per SM): 33.4 / 27.6 / 25.7 / 29.9 / 29.9 ms.
 #ifndef HJB_ADJ_BLOCKS_PER_SM
-#define HJB_ADJ_BLOCKS_PER_SM 8
+#define HJB_ADJ_BLOCKS_PER_SM 4
 #endif
 
 namespace {
@@ -234,6 +237,9 @@ struct hjb_problem {
     DevBuf adj_policy, adj_g, adj_L, adj_ctl, adj_v, adj_ref, adj_cell, adj_frac;
     cudaGraph_t adj_graph = nullptr;
     cudaGraphExec_t adj_exec = nullptr;
+    cudaGraph_t ref_graph = nullptr;  // the refinement loop of hjb_backward
+    cudaGraphExec_t ref_exec = nullptr;
+    hjbh::AdjArgs ref_args_in_graph;
     hjbh::AdjArgs adj_args_in_graph;
     std::vector<const hjb_problem *> batch_key;
 };
@@ -1364,6 +1370,8 @@ int hjb_destroy(hjb_problem *P) {
     }
     if (P->adj_exec) cudaGraphExecDestroy(P->adj_exec);
     if (P->adj_graph) cudaGraphDestroy(P->adj_graph);
+    if (P->ref_exec) cudaGraphExecDestroy(P->ref_exec);
+    if (P->ref_graph) cudaGraphDestroy(P->ref_graph);
     P->adj_policy.release();
     P->adj_g.release();
     P->adj_L.release();
@@ -2207,6 +2215,61 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
     });
 }
 
+// The graph of an adjoint loop (WHILE conditional node): `reps` rounds of the
+// kernels fns[0..nf) per body, each on sms x HJB_ADJ_BLOCKS_PER_SM CTAs with
+// `args` (whose handle is set here); the kernels' last CTA sets the
+// condition.
+int build_adj_loop(cudaGraph_t &graph, cudaGraphExec_t &exec, const void *const *fns, int nf,
+                   int reps, hjbh::AdjArgs &args) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof cp_raw);
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    args.handle = handle;
+    args.use_handle = 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGraphNode_t prev = nullptr;
+    for (int rep = 0; rep < reps; ++rep)
+        for (int k = 0; k < nf; ++k) {
+            cudaKernelNodeParams kp;
+            std::memset(&kp, 0, sizeof kp);
+            kp.func = const_cast<void *>(fns[k]);
+            kp.gridDim = dim3(sms * HJB_ADJ_BLOCKS_PER_SM);
+            kp.blockDim = dim3(hjbk::THREADS);
+            void *argv[1] = {&args};
+            kp.kernelParams = argv;
+            cudaGraphNode_t node;
+            CK(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+            prev = node;
+        }
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    return HJB_OK;
+}
+
+// An instantiated loop graph can be reused when its kernels' arguments
+// (other than the condition handle) are the same.
+bool same_adj_args(cudaGraphExec_t exec, const hjbh::AdjArgs &a, const hjbh::AdjArgs &b) {
+    return exec && !std::memcmp(&a.ap, &b.ap, sizeof a.ap) &&
+           !std::memcmp(&a.ctrl, &b.ctrl, sizeof a.ctrl) && a.policy == b.policy && a.g == b.g &&
+           a.L[0] == b.L[0] && a.L[1] == b.L[1] && a.ctl == b.ctl && a.cell == b.cell &&
+           a.frac == b.frac;
+}
+
 int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
                  const hjb_solve_opts *opts, float *grad_out, hjb_stats *stats, void *stream) {
     g_err.clear();
@@ -2304,18 +2367,34 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
             ra.ctl = ctl;
             ra.cell = P->adj_cell.as<int>();
             ra.frac = P->adj_frac.as<float2>();
-            void *argv[1] = {&ra};
             hjbh::AdjCtl hr;
-            // 32 iterations between reads of the stopping flag (at most 20000)
-            for (;;) {
-                for (int k = 0; k < 32; ++k)
-                    CK(cudaLaunchKernel(hjbh::refine_iter_kernel(), dim3(sms * HJB_ADJ_BLOCKS_PER_SM),
-                                        dim3(hjbk::THREADS), argv, 0, st));
-                ref_launches += 32;
+            const char *ng = std::getenv("HJB_NO_GRAPH");
+            if (ng && ng[0] == '1') {
+                // host-driven loop (profiling aid): 32 iterations between reads
+                // of the stopping flag
+                void *argv[1] = {&ra};
+                for (;;) {
+                    for (int k = 0; k < 32; ++k)
+                        CK(cudaLaunchKernel(hjbh::refine_iter_kernel(),
+                                            dim3(sms * HJB_ADJ_BLOCKS_PER_SM), dim3(hjbk::THREADS),
+                                            argv, 0, st));
+                    CK(cudaMemcpyAsync(&hr, ctl, sizeof hr, cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                    if (hr.converged) break;
+                }
+            } else {
+                // graph loop: 4 iterations per body, the last CTA of each
+                // iteration sets the condition
+                if (!same_adj_args(P->ref_exec, P->ref_args_in_graph, ra)) {
+                    const void *fns[1] = {hjbh::refine_iter_kernel()};
+                    TRY(build_adj_loop(P->ref_graph, P->ref_exec, fns, 1, 4, ra));
+                    P->ref_args_in_graph = ra;
+                }
+                CK(cudaGraphLaunch(P->ref_exec, st));
                 CK(cudaMemcpyAsync(&hr, ctl, sizeof hr, cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
-                if (hr.converged) break;
             }
+            ref_launches += (hr.iters + 3) / 4 * 4;
             if (hr.converged != 2)
                 return fail(HJB_ERR_NOT_CONVERGED,
                             "refinement of the policy values not converged after %d iterations",
@@ -2365,48 +2444,9 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
             CK(cudaStreamSynchronize(st));
             if (conv) break;
         }
-    } else if (!P->adj_exec || std::memcmp(&P->adj_args_in_graph.ap, &args.ap, sizeof args.ap) ||
-        std::memcmp(&P->adj_args_in_graph.ctrl, &args.ctrl, sizeof args.ctrl) ||
-        P->adj_args_in_graph.L[0] != L0 || P->adj_args_in_graph.policy != args.policy ||
-        P->adj_args_in_graph.g != args.g || P->adj_args_in_graph.ctl != ctl ||
-        P->adj_args_in_graph.cell != args.cell || P->adj_args_in_graph.frac != args.frac) {
-        if (P->adj_exec) cudaGraphExecDestroy(P->adj_exec);
-        if (P->adj_graph) cudaGraphDestroy(P->adj_graph);
-        P->adj_exec = nullptr;
-        P->adj_graph = nullptr;
-        CK(cudaGraphCreate(&P->adj_graph, 0));
-        cudaGraphConditionalHandle handle;
-        CK(cudaGraphConditionalHandleCreate(&handle, P->adj_graph, 1, cudaGraphCondAssignDefault));
-        alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
-        std::memset(cp_raw, 0, sizeof cp_raw);
-        cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = handle;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t cnode;
-        CK(cudaGraphAddNode(&cnode, P->adj_graph, nullptr, nullptr, 0, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        args.handle = handle;
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    } else if (!same_adj_args(P->adj_exec, P->adj_args_in_graph, args)) {
         const void *fns[2] = {hjbh::adj_scatter_kernel(), hjbh::adj_resid_kernel()};
-        cudaGraphNode_t prev = nullptr;
-        for (int rep = 0; rep < 2; ++rep)
-            for (int k = 0; k < 2; ++k) {
-                cudaKernelNodeParams kp;
-                std::memset(&kp, 0, sizeof kp);
-                kp.func = const_cast<void *>(fns[k]);
-                kp.gridDim = dim3(sms * HJB_ADJ_BLOCKS_PER_SM);
-                kp.blockDim = dim3(hjbk::THREADS);
-                void *argv[1] = {&args};
-                kp.kernelParams = argv;
-                cudaGraphNode_t node;
-                CK(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
-                prev = node;
-            }
-        CK(cudaGraphInstantiate(&P->adj_exec, P->adj_graph, 0));
+        TRY(build_adj_loop(P->adj_graph, P->adj_exec, fns, 2, 2, args));
         P->adj_args_in_graph = args;
     }
     if (args.use_handle) CK(cudaGraphLaunch(P->adj_exec, st));
