@@ -408,8 +408,9 @@ def run_dubins(args, hjb, S, dev, flush, local):
           roofline={"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12,
                     "unit": "Top/s", "frac": ach_ops / peak_ops,
                     "traffic": traffic["bytes_per_launch"] if traffic else None,
-                    "traffic_unit": "DRAM bytes per sweep launch (ncu, warm L2)",
-                    "algorithmic_bytes_per_launch": alg_bytes / max(1, tot["launches"]),
+                    "traffic_unit": "DRAM bytes per sweep launch (ncu, warm L2, three launches "
+                                    "of the fine solve's middle sweeps)",
+                    "algorithmic_bytes_per_launch": alg_bytes / max(1, tot["iterations"]),
                     "hbm": {"achieved_gbs": ach_bw, "peak_gbs": hbm, "frac": ach_bw / hbm,
                             "bytes_per_tile_node": 9},
                     "ops_per_node_update": 53, "tile_layers": layers,
@@ -793,11 +794,13 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Top/s", "frac": achieved / peak_ops,
                      "traffic": traffic["bytes_per_launch"] if traffic else None,
-                     "traffic_unit": "DRAM bytes per sweep launch (ncu, warm L2)",
-                     "algorithmic_bytes_per_launch": (
-                         9 * traffic["node_updates_per_launch"] if traffic else None),
-                     "kernel": "sweep2d_kernel<64,W,2> 32x%s tiles (decomposed fine solve)"
-                               % (rows or "?"),
+                     "traffic_unit": "DRAM bytes per sweep launch (ncu, warm L2, three launches "
+                                     "of the fine solve's busiest phase)",
+                     # 9 B per node-update (V read and write, labels), average sweep
+                     "algorithmic_bytes_per_launch": 9 * tot["node_updates"] / max(1, tot["iterations"]),
+                     "kernel": "sweep2d_kernel<64 controls, W form> 32x%s tiles, %s (decomposed "
+                               "fine solve)" % (rows or "?", "lane split" if tot.get("tile_lanes") == 2
+                                                else "control groups"),
                      "peak_source": "SMs x 128 FP32 lanes x max SM clock (derived)"},
         "cpu_baseline": cpu,
         "e2e": {"value": nfree * iters_full / e2e_s * world, "unit": UNIT,
