@@ -89,11 +89,15 @@ TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sweep2d_zermelo1025_dram_traff
 KERNEL_SOURCES = ("paper_1405_3521_gb300/csrc/sweep.cu", "paper_1405_3521_gb300/csrc/hjb_internal.cuh")
 
 
-def kernel_sources_sha256():
-    """Digest of the sources the 2D sweep kernel is built from."""
+ADJOINT_SOURCES = ("paper_1405_3521_gb300/csrc/adjoint.cu", "paper_1405_3521_gb300/csrc/hjb_internal.cuh")
+ADJOINT_PROFILE = os.path.join(ROOT, "profiles", "adjoint1025_launch_list_traffic.md")
+
+
+def kernel_sources_sha256(sources=KERNEL_SOURCES):
+    """Digest of the sources a kernel is built from (default: the sweeps)."""
     import hashlib
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -120,6 +124,22 @@ def sweep_traffic(path=TRAFFIC_PROFILE, rows=None, local_iters=None):
             out["node_updates_per_launch"] = float(kv["node_updates_per_launch" + sfx])
         return out
     except (OSError, KeyError, ValueError):
+        return None
+
+
+def adjoint_traffic(path=ADJOINT_PROFILE):
+    """DRAM bytes per launch of the adjoint's iteration kernels from a committed
+    ncu summary (`- traffic_bytes_per_launch_<kernel>: <bytes>`), or None when
+    the sources changed after the counters were taken."""
+    try:
+        with open(path) as f:
+            kv = dict(line.strip("- \n").split(": ", 1) for line in f
+                      if line.startswith("- ") and ": " in line)
+        if kv.get("sources_sha256") != kernel_sources_sha256(ADJOINT_SOURCES):
+            return None
+        return {k[len("traffic_bytes_per_launch_"):]: float(v) for k, v in kv.items()
+                if k.startswith("traffic_bytes_per_launch_")}
+    except (OSError, ValueError):
         return None
 
 
@@ -589,11 +609,20 @@ def run_adjoint(args, hjb, S, dev, flush, local):
     # lambda write) 16 B; per node and refinement iteration: policy 1 B, r 4 B,
     # s 4 B, the node's own correction read 4 B and write 4 B
     ach = N * (41 * st["iterations"] + 17 * ref) / (st["ms"] / 1e3) / 1e9
+    # measured DRAM traffic of one backward: the iteration kernels' per-launch
+    # bytes (committed ncu windows) times their launches
+    tr = adjoint_traffic()
+    traffic = None
+    if tr and all(k in tr for k in ("adj_scatter", "adj_resid", "refine_iter")):
+        traffic = (st["iterations"] * (tr["adj_scatter"] + tr["adj_resid"])
+                   + ref * tr["refine_iter"] + 2 * tr.get("policy_kernel", 0.0))
     _line(args, "adjoint node-updates/s to convergence (transposed fixed point, policy frozen)",
           upd / (ms / 1e3), UNIT, ms, {"workload": "adjoint-%dx%d-A32-4096points" % tuple(d["shape"])},
           iterations=st["iterations"], refine_iterations=ref, forward_iterations=fst["iterations"],
           roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": None,
+                    "frac": ach / hbm, "traffic": traffic,
+                    "traffic_unit": "DRAM bytes per backward (ncu, per-launch windows x launches)",
+                    "algorithmic_bytes": N * (41 * st["iterations"] + 17 * ref),
                     "kernel": "adj_scatter + adj_resid, refine_iter",
                     "bytes_per_node_iteration": {"transposed": 41, "refinement": 17}},
           cpu_baseline=None, gpu_launches=st["launches"], clocks=clocks)
