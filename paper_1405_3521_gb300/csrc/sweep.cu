@@ -1001,16 +1001,22 @@ __device__ __forceinline__ bool pass3d(const SweepArgs &args, Smem3d<TZ3> &sm, u
                 const int kz0 = lz + HZ + 1;
                 best = WFORM ? -INFINITY : INFINITY;
                 const int na = args.ctrl.count;
-#pragma unroll 4
-                for (int j = 0; j < na; ++j) {
+                // heading interpolation of control j between the bilinear values
+                auto heading = [&](int j) {
                     const float pz = fmaf(S.hz, args.ctrl.ax[j], bz);
                     const float mz = pz + MAGIC;
                     const float fz = pz - (mz - TWO23);
                     const int d = (__float_as_int(mz) - TWO23_BITS) - kz0;  // -1 or 0
                     const float lo = d < 0 ? B[0] : B[1];
                     const float hi = d < 0 ? B[1] : B[2];
-                    const float q = fmaf(fz, hi, fmaf(-fz, lo, lo));
-                    best = pick<WFORM>(best, q);
+                    return fmaf(fz, hi, fmaf(-fz, lo, lo));
+                };
+                if (na == 3) {
+                    // the three turn rates of the car: straight-line code
+                    best = pick<WFORM>(pick<WFORM>(heading(0), heading(1)), heading(2));
+                } else {
+#pragma unroll 4
+                    for (int j = 0; j < na; ++j) best = pick<WFORM>(best, heading(j));
                 }
             }
             const float v = WFORM ? S.beta * best
