@@ -350,6 +350,43 @@ def test_adjoint_gradient(hjb, orc):
     assert rel_t < 1e-3, rel_t
 
 
+def test_adjoint_policy_refinement(hjb, orc, monkeypatch):
+    """The backward decides the optimal policy in FP64 on values refined from
+    the FP32 solution (the FP64 residual of the policy-frozen system, an FP32
+    correction).  With a current and a running-cost field, both of which
+    enter that residual, the gradients match the oracle's FP64 adjoint within
+    1e-3 relative, no worse (beyond the FP32 accumulation noise) than without the refinement
+    (HJB_ADJ_REFINE=0),
+    and the statistics show the refinement's iterations."""
+    import torch
+    n, A = 129, 32
+    d = S.c5(n=n, A=A, ntargets=3, P=512)
+    X, Y = S.mesh2(n, n)
+    g = S.rng("misc", 41)
+    d["current"] = S.f32(0.5 * S.current_field(g, X, Y))
+    d["cost"] = S.f32(S.speed_field(g, X, Y))
+    po = oracle_problem(orc, d)
+    Vo, _, _ = orc.solve(po, tol=1e-14, nthreads=orc.max_threads())
+    pol, _ = orc.policy(po, Vo)
+    _, gV = orc.points(po, Vo, d["points"])
+    lam, _, _ = orc.adjoint(po, pol, gV, tol=1e-14)
+    gt_o, gc_o = orc.grad(po, Vo, pol, lam)
+    p = gpu_problem(hjb, d)
+    V, _ = hjb.solve(p)
+    pts = torch.as_tensor(d["points"].astype(np.float32)).cuda()
+    _, gV_gpu = hjb.point_values(p, V, pts)
+    errs = {}
+    for refine in ("1", "0"):
+        monkeypatch.setenv("HJB_ADJ_REFINE", refine)
+        gt, st = hjb.backward(p, V, gV_gpu, wrt=0)
+        gc, _ = hjb.backward(p, V, gV_gpu, wrt=1)
+        assert (st["local_iters"] > 0) == (refine == "1"), st
+        errs[refine] = (np.abs(to_np(gt) - gt_o).max() / np.abs(gt_o).max(),
+                        np.abs(to_np(gc) - gc_o).max() / np.abs(gc_o).max())
+    assert errs["1"][0] < 1e-3 and errs["1"][1] < 1e-3, errs
+    assert errs["1"][0] <= errs["0"][0] + 1e-4 and errs["1"][1] <= errs["0"][1] + 1e-4, errs
+
+
 def test_autograd_function(hjb, orc):
     import torch
     n, A = 49, 16
