@@ -355,9 +355,9 @@ def test_adjoint_policy_refinement(hjb, orc, monkeypatch):
     the FP32 solution (the FP64 residual of the policy-frozen system, an FP32
     correction).  With a current and a running-cost field, both of which
     enter that residual, the gradients match the oracle's FP64 adjoint within
-    1e-3 relative, no worse (beyond the FP32 accumulation noise) than without the refinement
-    (HJB_ADJ_REFINE=0),
-    and the statistics show the refinement's iterations."""
+    1e-3 relative, no worse (beyond the FP32 accumulation noise) than without
+    the refinement (HJB_ADJ_REFINE=0), and the statistics show the
+    refinement's iterations."""
     import torch
     n, A = 129, 32
     d = S.c5(n=n, A=A, ntargets=3, P=512)
