@@ -319,8 +319,10 @@ __global__ void assemble_kernel(const SlotDesc *slots, const SlotState *state, i
 }
 
 // Largest |x| over a strided field; a non-finite entry yields +inf so that
-// the caller rejects the field.
+// the caller rejects the field.  One atomic per CTA (per-warp atomics on one
+// address serialised the reduction).
 __global__ void absmax_kernel(const float *x, long long n, int stride, int offset, unsigned *out) {
+    __shared__ float s_m[THREADS / 32];
     float m = 0.0f;
     GRID_STRIDE(i, n) {
         float a = fabsf(x[i * stride + offset]);
@@ -329,7 +331,13 @@ __global__ void absmax_kernel(const float *x, long long n, int stride, int offse
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 1; w < THREADS / 32; ++w) m = fmaxf(m, s_m[w]);
+        atomicMax(out, __float_as_uint(m));
+    }
 }
 
 __global__ void exp_kernel(const float *th, float *s, long long n) {
@@ -337,11 +345,18 @@ __global__ void exp_kernel(const float *th, float *s, long long n) {
 }
 
 __global__ void popcount_kernel(const uint32_t *mask, long long n, unsigned long long *out) {
+    __shared__ unsigned long long s_c[THREADS / 32];
     unsigned long long c = 0;
     GRID_STRIDE(i, n) c += __popc(mask[i]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 1; w < THREADS / 32; ++w) c += s_c[w];
+        if (c) atomicAdd(out, c);
+    }
 }
 
 // Nodes of each of the m sub-domains of a mask (out[k] += |bit k|).
@@ -424,6 +439,13 @@ int blocks_for(long long n) {
     return static_cast<int>(b);
 }
 
+// Reductions to one counter: a grid of at most 4 CTAs per SM of a GB300
+// (608), each thread striding over the field.
+int reduction_blocks(long long n) {
+    const int b = blocks_for(n);
+    return b < 608 ? b : 608;
+}
+
 }  // namespace
 
 namespace hjbh {
@@ -487,7 +509,7 @@ void launch_assemble(const SlotDesc *slots, const SlotState *state, int m, const
 
 void launch_absmax(const float *x, long long n, int stride, int offset, unsigned *out,
                    cudaStream_t st) {
-    absmax_kernel<<<blocks_for(n), THREADS, 0, st>>>(x, n, stride, offset, out);
+    absmax_kernel<<<reduction_blocks(n), THREADS, 0, st>>>(x, n, stride, offset, out);
 }
 
 void launch_exp(const float *theta, float *s, long long n, cudaStream_t st) {
@@ -518,7 +540,7 @@ void launch_comp_split(const GridDims &g, uint8_t *labels, int comp, int axis, i
 }
 
 void launch_popcount(const uint32_t *mask, long long n, unsigned long long *out, cudaStream_t st) {
-    popcount_kernel<<<blocks_for(n), THREADS, 0, st>>>(mask, n, out);
+    popcount_kernel<<<reduction_blocks(n), THREADS, 0, st>>>(mask, n, out);
 }
 
 }  // namespace hjbh
