@@ -352,10 +352,11 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
  *  the FP64 fixed point by the rounding carried along the characteristics,
  *  so the policy taken on v is frozen, the FP64 residual r of its linear
  *  system is formed, the correction dv = r + beta P_pi dv is iterated in FP32
- *  to its rounding floor, and pi is decided again on v + dv (one round; the
- *  environment variable HJB_ADJ_REFINE sets 0-4 rounds).  stats->ties counts
- *  the free nodes whose two best control values differ by at most 1e-6,
- *  stats->local_iters the iterations of the refinement.
+ *  to its rounding floor (block Gauss-Seidel sweeps over staged tiles), and
+ *  pi is decided again on v + dv (one round; the environment variable
+ *  HJB_ADJ_REFINE sets 0-4 rounds).  stats->ties counts the free nodes whose
+ *  two best control values differ by at most 1e-6, stats->local_iters the
+ *  sweeps of the refinement.
  *  wrt = 0: grad_out = dL/dtheta for the log-speed field (s = exp(theta),
  *           HJB_DYN_SPEED_CURRENT):  lambda_i beta h s_i grad I[V](y_i) . a_pi(i)
  *  wrt = 1: grad_out = dL/dl for the cost field: lambda_i gamma.

@@ -20,6 +20,8 @@ using namespace hjbk;
 using hjbh::AdjArgs;
 using hjbh::AdjCtl;
 using hjbh::AdjProblem;
+using hjbh::REFINE_APPS;
+using hjbh::REFINE_ROWS;
 
 namespace {
 
@@ -226,7 +228,7 @@ __global__ void feet_kernel(AdjProblem ap, const __grid_constant__ ControlTable 
 // With the policy pi frozen, V solves the linear system
 // V = beta P_pi V + gamma l; its residual r is taken in FP64 and the
 // correction dV = r + beta P_pi dV, a small quantity, is iterated in FP32
-// (its own rounding is then ~1e-7 of ~1e-6).  The policy is decided again on
+// (its own rounding is then ~1e-7 of ~1e-6) by refine_tiles.  The policy is decided again on
 // V + dV, the exact FP64 values of pi up to that rounding.
 __global__ void refine_residual_kernel(AdjProblem ap, const __grid_constant__ ControlTable C,
                                        const float *V, const int8_t *policy, float *r) {
@@ -254,46 +256,110 @@ __global__ void refine_residual_kernel(AdjProblem ap, const __grid_constant__ Co
     }
 }
 
-// One Jacobi iteration dV_dst = r + beta P_pi dV_src (A.g = r, A.L = dV);
-// the last CTA takes the stopping decision: the change within 4 ulp of
-// max|dV| (the FP32 floor of this iteration), or 256 iterations without a
-// new minimum once below 64 ulp, or the iteration cap.
-__global__ void refine_iter(const __grid_constant__ AdjArgs A) {
+// Block Gauss-Seidel sweep of the refinement iteration dV = r + beta P_pi dV
+// with the policy frozen: each CTA stages a tile of 32 x REFINE_ROWS nodes of
+// dV_src with an hr-cell halo in shared memory, applies the iteration
+// REFINE_APPS times there (the halo held at the previous sweep's values; two
+// buffers, so every application reads only the previous one: the result does
+// not depend on the order of the CTAs), and writes the tile to dV_dst.  The
+// same fixed point as the Jacobi iteration, reached in a fraction of the
+// launches because a correction travels REFINE_APPS steps within a tile per
+// sweep.  The last CTA takes the stopping decision: the sweep's change
+// within 4 ulp of max|dV| (the FP32 floor of the iteration), or 64 sweeps
+// without a new minimum once below 64 ulp, or the sweep cap; a foot beyond
+// the staged halo (which the halo derived from the fields rules out) stops
+// the loop with the error flag set.
+__global__ void refine_tiles(const __grid_constant__ AdjArgs A) {
+    static_assert(TX * REFINE_ROWS == THREADS, "one thread per node of a refinement tile");
+    extern __shared__ float s_buf[];
     AdjCtl *ctl = A.ctl;
     if (ctl->converged) return;
     const AdjProblem &ap = A.ap;
+    const int hr = A.hr;
+    const int W = TX + 2 * hr, HH = REFINE_ROWS + 2 * hr, SZ = W * HH;
+    const int nx = ap.nx, ny = ap.ny;
+    const int tiles_x = (nx + TX - 1) / TX, tiles_y = (ny + REFINE_ROWS - 1) / REFINE_ROWS;
     const int par = ctl->parity;
     const float *src = A.L[par];
     float *dst = A.L[par ^ 1];
-    const long long N = static_cast<long long>(ap.nx) * ap.ny;
-    float r = 0.0f, a = 0.0f;
-    GRID_STRIDE(i, N) {
-        const int c = A.cell[i];
-        float d = 0.0f;
-        if (c != -1) {
-            d = A.g[i];
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    float rmax = 0.0f, amax = 0.0f;
+    bool bad = false;
+    for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        const int x0 = tx * TX - hr, y0 = ty * REFINE_ROWS - hr;
+        __syncthreads();  // the previous tile is done with the buffers
+        for (int k = threadIdx.x; k < SZ; k += THREADS) {
+            const int sy = k / W, sx = k - sy * W;
+            const int gx = x0 + sx, gy = y0 + sy;
+            const float v = (gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+                                ? __ldcg(src + static_cast<long long>(gy) * nx + gx)
+                                : 0.0f;
+            s_buf[k] = v;
+            s_buf[SZ + k] = v;
+        }
+        const int gx = tx * TX + lx, gy = ty * REFINE_ROWS + ly;
+        const bool in = gx < nx && gy < ny;
+        const long long i = static_cast<long long>(gy) * nx + gx;
+        int c = -1;
+        float r = 0.0f;
+        float2 f = make_float2(0.0f, 0.0f);
+        int lc = 0;
+        if (in) {
+            c = A.cell[i];
+            if (c != -1) r = A.g[i];
             if (c >= 0) {
-                const float2 t = A.frac[i];
-                const float lo = fmaf(t.x, src[c + 1], fmaf(-t.x, src[c], src[c]));
-                const float hi =
-                    fmaf(t.x, src[c + ap.nx + 1], fmaf(-t.x, src[c + ap.nx], src[c + ap.nx]));
-                d = fmaf(ap.beta, fmaf(t.y, hi, fmaf(-t.y, lo, lo)), d);
+                f = A.frac[i];
+                const int cy = c / nx, cx = c - cy * nx;
+                const int sx = cx - x0, sy = cy - y0;
+                if (sx < 0 || sx + 1 >= W || sy < 0 || sy + 1 >= HH) {
+                    bad = true;  // a foot beyond the halo: never with hr from the fields
+                    c = -2;
+                } else {
+                    lc = sy * W + sx;
+                }
             }
         }
-        dst[i] = d;
-        r = fmaxf(r, fabsf(d - src[i]));
-        a = fmaxf(a, fabsf(d));
+        const int me = (ly + hr) * W + lx + hr;
+        __syncthreads();
+        const float dold = in ? s_buf[me] : 0.0f;
+        float d = dold;
+#pragma unroll 1
+        for (int a = 0; a < REFINE_APPS; ++a) {
+            const float *cur = s_buf + (a & 1) * SZ;
+            float *nxt = s_buf + ((a + 1) & 1) * SZ;
+            if (in) {
+                d = 0.0f;
+                if (c != -1) {
+                    d = r;
+                    if (c >= 0) {
+                        const float lo = fmaf(f.x, cur[lc + 1], fmaf(-f.x, cur[lc], cur[lc]));
+                        const float hi = fmaf(f.x, cur[lc + W + 1],
+                                              fmaf(-f.x, cur[lc + W], cur[lc + W]));
+                        d = fmaf(ap.beta, fmaf(f.y, hi, fmaf(-f.y, lo, lo)), d);
+                    }
+                }
+                nxt[me] = d;
+            }
+            __syncthreads();
+        }
+        if (in) {
+            dst[i] = d;
+            rmax = fmaxf(rmax, fabsf(d - dold));
+            amax = fmaxf(amax, fabsf(d));
+        }
     }
+    if (bad) atomicExch(&ctl->error, 1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     }
     __shared__ float s_r[THREADS / 32], s_a[THREADS / 32];
     __shared__ int s_last;
-    if ((threadIdx.x & 31) == 0) {
-        s_r[threadIdx.x >> 5] = r;
-        s_a[threadIdx.x >> 5] = a;
+    if (lx == 0) {
+        s_r[ly] = rmax;
+        s_a[ly] = amax;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -311,12 +377,12 @@ __global__ void refine_iter(const __grid_constant__ AdjArgs A) {
     if (s_last && threadIdx.x == 0) {
         __threadfence();
         const float res = __uint_as_float(ctl->res_bits);
-        const float amax = __uint_as_float(ctl->lam_bits);
+        const float am = __uint_as_float(ctl->lam_bits);
         ctl->res_bits = 0u;
         ctl->lam_bits = 0u;
         ctl->iters += 1;
         ctl->final_res = res;
-        ctl->lam_max = amax;
+        ctl->lam_max = am;
         ctl->parity = par ^ 1;
         ctl->done_ctas = 0u;
         constexpr float EPS = 1.1920929e-7f;
@@ -326,8 +392,9 @@ __global__ void refine_iter(const __grid_constant__ AdjArgs A) {
         } else {
             ctl->stall += 1;
         }
-        if (res <= 4.0f * EPS * amax ||
-            (ctl->stall >= 256 && ctl->best_res <= 64.0f * EPS * amax))
+        if (ctl->error)
+            ctl->converged = 3;
+        else if (res <= 4.0f * EPS * am || (ctl->stall >= 64 && ctl->best_res <= 64.0f * EPS * am))
             ctl->converged = 2;
         else if (ctl->iters >= ctl->max_iters)
             ctl->converged = 3;
@@ -550,7 +617,15 @@ void launch_refine_residual(const AdjProblem &ap, const ControlTable &C, const f
     refine_residual_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, policy, r);
 }
 
-const void *refine_iter_kernel() { return reinterpret_cast<const void *>(&refine_iter); }
+const void *refine_tiles_kernel() { return reinterpret_cast<const void *>(&refine_tiles); }
+
+size_t refine_tiles_smem(int hr) {
+    return 2 * sizeof(float) * static_cast<size_t>(TX + 2 * hr) * (REFINE_ROWS + 2 * hr);
+}
+
+int refine_tiles_grid(int nx, int ny) {
+    return ((nx + TX - 1) / TX) * ((ny + REFINE_ROWS - 1) / REFINE_ROWS);
+}
 
 const void *adj_scatter_kernel() { return reinterpret_cast<const void *>(&adj_scatter_guarded); }
 const void *adj_resid_kernel() { return reinterpret_cast<const void *>(&adj_resid); }

@@ -300,11 +300,15 @@ void launch_feet(const AdjProblem &ap, const hjbk::ControlTable &C, const int8_t
                  float2 *frac, cudaStream_t st);
 // Iterative refinement of the values the policy is decided on: r = the FP64
 // residual (beta I[V](foot_pi) + gamma l) - V of the policy-frozen equation,
-// and one Jacobi iteration dV <- r + beta P_pi dV (FP32) per launch of the
-// refinement kernel (AdjArgs: g = r, L = the two dV buffers).
+// then block Gauss-Seidel sweeps of dV <- r + beta P_pi dV (FP32) over staged
+// tiles, one per launch of the refinement kernel (AdjArgs: g = r, L = the
+// two dV buffers, hr the tiles' halo; shared memory refine_tiles_smem(hr)
+// bytes, one CTA per tile: refine_tiles_grid).
 void launch_refine_residual(const AdjProblem &ap, const hjbk::ControlTable &C, const float *V,
                             const int8_t *policy, float *r, cudaStream_t st);
-const void *refine_iter_kernel();
+const void *refine_tiles_kernel();
+size_t refine_tiles_smem(int hr);
+int refine_tiles_grid(int nx, int ny);
 // Graph-able adjoint iteration kernels.
 const void *adj_scatter_kernel();
 const void *adj_resid_kernel();
@@ -321,7 +325,12 @@ struct AdjArgs {
     // index (-1 target, -2 foot outside the box) and fractions (tx, ty)
     const int *cell;
     const float2 *frac;
+    int hr;  // refinement tiles: halo in cells around each 32 x REFINE_ROWS tile
 };
+// Tiles of the refinement's block Gauss-Seidel sweep: 32 x REFINE_ROWS nodes,
+// REFINE_APPS applications of the frozen-policy iteration per staged tile.
+constexpr int REFINE_ROWS = 8;
+constexpr int REFINE_APPS = 8;
 void launch_adj_init(const float *g, float *L0, float *L1, long long n, AdjCtl *ctl, float tol,
                      int max_iters, cudaStream_t st);
 // dL/dtheta (wrt = 0) or dL/dl (wrt = 1) from lambda.

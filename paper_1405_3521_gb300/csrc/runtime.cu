@@ -2216,11 +2216,12 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
 }
 
 // The graph of an adjoint loop (WHILE conditional node): `reps` rounds of the
-// kernels fns[0..nf) per body, each on sms x HJB_ADJ_BLOCKS_PER_SM CTAs with
+// kernels fns[0..nf) per body, each on `grid` CTAs (default sms x
+// HJB_ADJ_BLOCKS_PER_SM) with `smem` bytes of dynamic shared memory and
 // `args` (whose handle is set here); the kernels' last CTA sets the
 // condition.
 int build_adj_loop(cudaGraph_t &graph, cudaGraphExec_t &exec, const void *const *fns, int nf,
-                   int reps, hjbh::AdjArgs &args) {
+                   int reps, hjbh::AdjArgs &args, int grid = 0, size_t smem = 0) {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
@@ -2249,8 +2250,9 @@ int build_adj_loop(cudaGraph_t &graph, cudaGraphExec_t &exec, const void *const 
             cudaKernelNodeParams kp;
             std::memset(&kp, 0, sizeof kp);
             kp.func = const_cast<void *>(fns[k]);
-            kp.gridDim = dim3(sms * HJB_ADJ_BLOCKS_PER_SM);
+            kp.gridDim = dim3(grid > 0 ? grid : sms * HJB_ADJ_BLOCKS_PER_SM);
             kp.blockDim = dim3(hjbk::THREADS);
+            kp.sharedMemBytes = static_cast<unsigned>(smem);
             void *argv[1] = {&args};
             kp.kernelParams = argv;
             cudaGraphNode_t node;
@@ -2355,7 +2357,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
             float *r = P->adj_ref.as<float>(), *D0 = r + N, *D1 = D0 + N;
             hjbh::launch_refine_residual(ap, ctrl, P->adj_v.as<float>(), P->adj_policy.as<int8_t>(),
                                          r, st);
-            hjbh::launch_adj_init(r, D0, D1, N, ctl, 0.0f, 20000, st);
+            hjbh::launch_adj_init(r, D0, D1, N, ctl, 0.0f, 5000, st);
             hjbh::AdjArgs ra;
             std::memset(&ra, 0, sizeof ra);
             ra.ap = ap;
@@ -2367,37 +2369,44 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
             ra.ctl = ctl;
             ra.cell = P->adj_cell.as<int>();
             ra.frac = P->adj_frac.as<float2>();
+            // tiles' halo: every corner of a policy foot (at most ceil of the
+            // largest foot offset, plus the second corner)
+            ra.hr = std::max(2, static_cast<int>(std::ceil(pr.max_off_xy)) + 1);
+            const int rgrid = hjbh::refine_tiles_grid(ap.nx, ap.ny);
+            const size_t rsmem = hjbh::refine_tiles_smem(ra.hr);
             hjbh::AdjCtl hr;
             const char *ng = std::getenv("HJB_NO_GRAPH");
             if (ng && ng[0] == '1') {
-                // host-driven loop (profiling aid): 32 iterations between reads
-                // of the stopping flag
+                // host-driven loop (profiling aid): 8 sweeps between reads of
+                // the stopping flag
                 void *argv[1] = {&ra};
                 for (;;) {
-                    for (int k = 0; k < 32; ++k)
-                        CK(cudaLaunchKernel(hjbh::refine_iter_kernel(),
-                                            dim3(sms * HJB_ADJ_BLOCKS_PER_SM), dim3(hjbk::THREADS),
-                                            argv, 0, st));
+                    for (int k = 0; k < 8; ++k)
+                        CK(cudaLaunchKernel(hjbh::refine_tiles_kernel(), dim3(rgrid),
+                                            dim3(hjbk::THREADS), argv, rsmem, st));
                     CK(cudaMemcpyAsync(&hr, ctl, sizeof hr, cudaMemcpyDeviceToHost, st));
                     CK(cudaStreamSynchronize(st));
                     if (hr.converged) break;
                 }
             } else {
-                // graph loop: 4 iterations per body, the last CTA of each
-                // iteration sets the condition
-                if (!same_adj_args(P->ref_exec, P->ref_args_in_graph, ra)) {
-                    const void *fns[1] = {hjbh::refine_iter_kernel()};
-                    TRY(build_adj_loop(P->ref_graph, P->ref_exec, fns, 1, 4, ra));
+                // graph loop: 2 sweeps per body, the last CTA of each sets the
+                // condition
+                if (!same_adj_args(P->ref_exec, P->ref_args_in_graph, ra) ||
+                    P->ref_args_in_graph.hr != ra.hr) {
+                    const void *fns[1] = {hjbh::refine_tiles_kernel()};
+                    TRY(build_adj_loop(P->ref_graph, P->ref_exec, fns, 1, 2, ra, rgrid, rsmem));
                     P->ref_args_in_graph = ra;
                 }
                 CK(cudaGraphLaunch(P->ref_exec, st));
                 CK(cudaMemcpyAsync(&hr, ctl, sizeof hr, cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
             }
-            ref_launches += (hr.iters + 3) / 4 * 4;
+            ref_launches += (hr.iters + 1) / 2 * 2;
+            if (hr.error)
+                return fail(HJB_ERR_CUDA, "a policy foot lies beyond the refinement tiles' halo");
             if (hr.converged != 2)
                 return fail(HJB_ERR_NOT_CONVERGED,
-                            "refinement of the policy values not converged after %d iterations",
+                            "refinement of the policy values not converged after %d sweeps",
                             hr.iters);
             ref_iters += hr.iters;
             CK(cudaMemsetAsync(d_ties, 0, sizeof(unsigned), st));
