@@ -600,32 +600,30 @@ def run_adjoint(args, hjb, S, dev, flush, local):
                                        args.warmup, flush, local)
     N = d["labels"].size
     # node-updates of the transposed iteration and of the refinement of the
-    # values the policy is decided on (a policy-frozen forward iteration, 8
-    # applications per staged tile and sweep)
+    # values the policy is decided on (a policy-frozen forward iteration):
+    # both run block Gauss-Seidel sweeps, 8 applications per staged tile
     ref = st["local_iters"]
-    upd = N * (st["iterations"] + 8 * ref)
+    upd = N * 8 * (st["iterations"] + ref)
     hbm = measured_peaks().get("hbm_gbs", 6660.0)
-    # per node and transposed iteration: lambda read 4 B, policy 1 B, s 4 B,
-    # 4 scattered atomics 16 B, residual pass (two lambda reads, g read,
-    # lambda write) 16 B; per node and refinement sweep: the foot's cell 4 B
-    # and fractions 8 B, r 4 B, the correction read 4 B and written 4 B
-    ach = N * (41 * st["iterations"] + 24 * ref) / (st["ms"] / 1e3) / 1e9
+    # per node and sweep of either: the policy foot's cell 4 B and fractions
+    # 8 B, g (or r) 4 B, lambda (or the correction) read 4 B and written 4 B
+    ach = N * 24 * (st["iterations"] + ref) / (st["ms"] / 1e3) / 1e9
     # measured DRAM traffic of one backward: the iteration kernels' per-launch
     # bytes (committed ncu windows) times their launches
     tr = adjoint_traffic()
     traffic = None
-    if tr and all(k in tr for k in ("adj_scatter", "adj_resid", "refine_tiles")):
-        traffic = (st["iterations"] * (tr["adj_scatter"] + tr["adj_resid"])
-                   + ref * tr["refine_tiles"] + 2 * tr.get("policy_kernel", 0.0))
+    if tr and all(k in tr for k in ("adj_tiles", "refine_tiles")):
+        traffic = (st["iterations"] * tr["adj_tiles"] + ref * tr["refine_tiles"]
+                   + 2 * tr.get("policy_kernel", 0.0))
     _line(args, "adjoint node-updates/s to convergence (transposed fixed point, policy frozen)",
           upd / (ms / 1e3), UNIT, ms, {"workload": "adjoint-%dx%d-A32-4096points" % tuple(d["shape"])},
-          iterations=st["iterations"], refine_sweeps=ref, forward_iterations=fst["iterations"],
+          sweeps=st["iterations"], refine_sweeps=ref, forward_iterations=fst["iterations"],
           roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                     "frac": ach / hbm, "traffic": traffic,
                     "traffic_unit": "DRAM bytes per backward (ncu, per-launch windows x launches)",
-                    "algorithmic_bytes": N * (41 * st["iterations"] + 24 * ref),
-                    "kernel": "adj_scatter + adj_resid, refine_tiles",
-                    "bytes_per_node_iteration": {"transposed": 41, "refinement_sweep": 24}},
+                    "algorithmic_bytes": N * 24 * (st["iterations"] + ref),
+                    "kernel": "adj_tiles, refine_tiles",
+                    "bytes_per_node_sweep": 24},
           cpu_baseline=None, gpu_launches=st["launches"], clocks=clocks)
 
 

@@ -360,13 +360,17 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
  *  wrt = 0: grad_out = dL/dtheta for the log-speed field (s = exp(theta),
  *           HJB_DYN_SPEED_CURRENT):  lambda_i beta h s_i grad I[V](y_i) . a_pi(i)
  *  wrt = 1: grad_out = dL/dl for the cost field: lambda_i gamma.
- *  v [N]: the converged solution; grad_v [N]: dL/dV.  opts->tol (optional,
- *  > 0) stops the iteration once ||lambda^{n+1} - lambda^n||_inf <= tol
- *  (stats->converged = 1).  It always stops (stats->converged = 2) at the
- *  summation-order floor of the scattered FP32 accumulation: a change within
- *  32 ulp of max|lambda|, or no new minimum of the change for 256 iterations
- *  once it is below 1024 ulp of max|lambda|.  Otherwise
- *  HJB_ERR_NOT_CONVERGED after opts->max_iters.  stats (optional). */
+ *  v [N]: the converged solution; grad_v [N]: dL/dV.  lambda is iterated by
+ *  block Gauss-Seidel sweeps over 32 x 8 tiles (8 applications per staged
+ *  tile and sweep, the halo held); stats->iterations counts the sweeps.
+ *  opts->tol (optional, > 0) stops the iteration once a sweep changes lambda
+ *  by at most tol (stats->converged = 1).  It always stops
+ *  (stats->converged = 2) at the summation-order floor of the FP32
+ *  accumulation: a change within 32 ulp of max|lambda|, or no new minimum of
+ *  the change for 64 sweeps once it is below 1024 ulp of max|lambda|.
+ *  Otherwise HJB_ERR_NOT_CONVERGED after opts->max_iters sweeps.  Feet of
+ *  more than 6 cells (h |f| / dx) are HJB_ERR_UNSUPPORTED.  stats
+ *  (optional). */
 int hjb_backward(hjb_problem *p, const float *v, const float *grad_v, int wrt,
                  const hjb_solve_opts *opts, float *grad_out, hjb_stats *stats, void *stream);
 

@@ -403,54 +403,125 @@ __global__ void refine_tiles(const __grid_constant__ AdjArgs A) {
     }
 }
 
-// lambda_dst += beta P_pi^T lambda_src (dst pre-armed with g).
-__device__ __forceinline__ void scatter_body(const AdjArgs &A) {
+// Block Gauss-Seidel sweep of the transposed iteration lambda = g +
+// beta P_pi^T lambda (dL/dV = g).  Each CTA owns a tile of 32 x REFINE_ROWS
+// nodes.  The mass that the tile's hr-cell halo (the nodes whose policy feet
+// can reach the tile) sends into it, beta times the Q1 weight times lambda,
+// is constant during the sweep (the halo is held at the previous sweep's
+// values): it is added to g once, in shared memory.  Then REFINE_APPS times
+// every tile node's lambda becomes that base plus the mass the tile's own
+// nodes send it (shared-memory atomics), and the tile's lambda is written at
+// the end.  Mass that leaves the tile is gathered by the neighbouring
+// tile, whose halo holds this one.  As with the scattered global atomics
+// this replaces, the order of the additions is not fixed, so lambda is
+// reproducible to its FP32 rounding.  The last CTA takes the stopping
+// decision: the sweep's change within 32 ulp of max|lambda|, or 64 sweeps
+// without a new minimum once below 1024 ulp, or an optional absolute tol,
+// or the sweep cap.
+__global__ void adj_tiles(const __grid_constant__ AdjArgs A) {
+    static_assert(TX * REFINE_ROWS == THREADS, "one thread per node of a tile");
+    __shared__ float s_base[THREADS];  // g plus the halo's mass, per tile node
+    __shared__ float s_acc[THREADS];
+    AdjCtl *ctl = A.ctl;
+    if (ctl->converged) return;
     const AdjProblem &ap = A.ap;
-    const int par = A.ctl->parity;
+    const int hr = A.hr;
+    const int W = TX + 2 * hr, HH = REFINE_ROWS + 2 * hr, SZ = W * HH;
+    const int nx = ap.nx, ny = ap.ny;
+    const int tiles_x = (nx + TX - 1) / TX, tiles_y = (ny + REFINE_ROWS - 1) / REFINE_ROWS;
+    const int par = ctl->parity;
     const float *src = A.L[par];
     float *dst = A.L[par ^ 1];
-    const long long N = static_cast<long long>(ap.nx) * ap.ny;
-    GRID_STRIDE(i, N) {
-        const int c = A.cell[i];
-        if (c < 0) continue;
-        const float lam = src[i];
-        if (lam == 0.0f) continue;
-        const float2 t = A.frac[i];
-        const float bl = ap.beta * lam;
-        atomicAdd(dst + c, bl * (1.0f - t.x) * (1.0f - t.y));
-        atomicAdd(dst + c + 1, bl * t.x * (1.0f - t.y));
-        atomicAdd(dst + c + ap.nx, bl * (1.0f - t.x) * t.y);
-        atomicAdd(dst + c + ap.nx + 1, bl * t.x * t.y);
-    }
-}
-
-// Residual ||lambda_dst - lambda_src||_inf, re-arming src with g for the
-// next iteration; the last CTA decides convergence.
-__global__ void adj_resid(const __grid_constant__ AdjArgs A) {
-    AdjCtl *ctl = A.ctl;
-    // a finished loop may still run the rest of its body: leave the result
-    if (ctl->converged) return;
-    const int par = ctl->parity;
-    float *src = A.L[par];
-    const float *dst = A.L[par ^ 1];
-    const long long N = static_cast<long long>(A.ap.nx) * A.ap.ny;
-    float r = 0.0f, a = 0.0f;
-    GRID_STRIDE(i, N) {
-        const float d = dst[i];
-        r = fmaxf(r, fabsf(d - src[i]));
-        a = fmaxf(a, fabsf(d));
-        src[i] = A.g[i];
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    float rmax = 0.0f, amax = 0.0f;
+    for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        const int x0 = tx * TX - hr, y0 = ty * REFINE_ROWS - hr;
+        const int tx0 = tx * TX, ty0 = ty * REFINE_ROWS;
+        const int gx = tx0 + lx, gy = ty0 + ly;
+        const bool in = gx < nx && gy < ny;
+        const long long i = static_cast<long long>(gy) * nx + gx;
+        __syncthreads();  // the previous tile is done with the shared arrays
+        s_base[threadIdx.x] = in ? A.g[i] : 0.0f;
+        __syncthreads();
+        // the halo's mass is constant during the sweep: scatter it into the
+        // base once (nodes of the tile itself are skipped here)
+        for (int k = threadIdx.x; k < SZ; k += THREADS) {
+            const int sy = k / W, sx = k - sy * W;
+            const int hx = x0 + sx, hy = y0 + sy;
+            const bool own = sx >= hr && sx < hr + TX && sy >= hr && sy < hr + REFINE_ROWS;
+            if (own || hx < 0 || hx >= nx || hy < 0 || hy >= ny) continue;
+            const long long j = static_cast<long long>(hy) * nx + hx;
+            const int c = A.cell[j];
+            if (c < 0) continue;
+            const float bl = ap.beta * __ldcg(src + j);
+            if (bl == 0.0f) continue;
+            const float2 f = A.frac[j];
+            const int cy = c / nx, cx = c - cy * nx;
+            const float w[4] = {(1.0f - f.x) * (1.0f - f.y), f.x * (1.0f - f.y),
+                                (1.0f - f.x) * f.y, f.x * f.y};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int ex = cx + (e & 1) - tx0, ey = cy + (e >> 1) - ty0;
+                if (ex >= 0 && ex < TX && ey >= 0 && ey < REFINE_ROWS)
+                    atomicAdd(&s_base[ey * TX + ex], bl * w[e]);
+            }
+        }
+        // this thread's node of the tile: its lambda and the tile-local
+        // corners (-1 outside the tile) and weights of its policy foot
+        float lam = 0.0f;
+        int cn[4] = {-1, -1, -1, -1};
+        float wt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (in) {
+            lam = __ldcg(src + i);
+            const int c = A.cell[i];
+            if (c >= 0) {
+                const float2 f = A.frac[i];
+                const int cy = c / nx, cx = c - cy * nx;
+                const float w[4] = {(1.0f - f.x) * (1.0f - f.y), f.x * (1.0f - f.y),
+                                    (1.0f - f.x) * f.y, f.x * f.y};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int ex = cx + (e & 1) - tx0, ey = cy + (e >> 1) - ty0;
+                    if (ex >= 0 && ex < TX && ey >= 0 && ey < REFINE_ROWS) {
+                        cn[e] = ey * TX + ex;
+                        wt[e] = ap.beta * w[e];
+                    }
+                }
+            }
+        }
+        const float lold = lam;
+        __syncthreads();  // the base is complete
+        const float base = s_base[threadIdx.x];
+#pragma unroll 1
+        for (int a = 0; a < REFINE_APPS; ++a) {
+            s_acc[threadIdx.x] = base;
+            __syncthreads();
+            if (lam != 0.0f) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (cn[e] >= 0) atomicAdd(&s_acc[cn[e]], lam * wt[e]);
+            }
+            __syncthreads();
+            lam = s_acc[threadIdx.x];
+            __syncthreads();  // read before the next application resets it
+        }
+        if (in) {
+            dst[i] = lam;
+            rmax = fmaxf(rmax, fabsf(lam - lold));
+            amax = fmaxf(amax, fabsf(lam));
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     }
     __shared__ float s_r[THREADS / 32], s_a[THREADS / 32];
     __shared__ int s_last;
-    if ((threadIdx.x & 31) == 0) {
-        s_r[threadIdx.x >> 5] = r;
-        s_a[threadIdx.x >> 5] = a;
+    if (lx == 0) {
+        s_r[ly] = rmax;
+        s_a[ly] = amax;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -459,7 +530,6 @@ __global__ void adj_resid(const __grid_constant__ AdjArgs A) {
             m = fmaxf(m, s_r[w]);
             ma = fmaxf(ma, s_a[w]);
         }
-        // non-negative floats order like their bit patterns
         atomicMax(&ctl->res_bits, __float_as_uint(m));
         atomicMax(&ctl->lam_bits, __float_as_uint(ma));
         __threadfence();
@@ -477,15 +547,6 @@ __global__ void adj_resid(const __grid_constant__ AdjArgs A) {
         ctl->lam_max = lam_max;
         ctl->parity = par ^ 1;
         ctl->done_ctas = 0u;
-        // stopping: residual <= tol (1, tol > 0 only); or the residual is
-        // within the FP32 rounding floor of the atomic accumulation, 32 ulp
-        // of max|lambda| (2): every iteration re-sums each lambda_i from its
-        // few contributions in an arbitrary order, so once the iterate has
-        // converged the change is that order alone.  The residual is not
-        // monotone while adjoint mass travels along the optimal trajectories
-        // to the target, so a stagnation test (2) applies only below 1024
-        // ulp of max|lambda| and after 256 iterations without a new minimum.
-        // Otherwise the iteration cap (3).
         constexpr float EPS = 1.1920929e-7f;
         if (res < ctl->best_res) {
             ctl->best_res = res;
@@ -493,28 +554,16 @@ __global__ void adj_resid(const __grid_constant__ AdjArgs A) {
         } else {
             ctl->stall += 1;
         }
-        int go = 1;
-        if (res <= ctl->tol) {
+        if (res <= ctl->tol)
             ctl->converged = 1;
-            go = 0;
-        } else if (res <= 32.0f * EPS * lam_max ||
-                   (ctl->stall >= 256 && ctl->best_res <= 1024.0f * EPS * lam_max)) {
+        else if (res <= 32.0f * EPS * lam_max ||
+                 (ctl->stall >= 64 && ctl->best_res <= 1024.0f * EPS * lam_max))
             ctl->converged = 2;
-            go = 0;
-        } else if (ctl->iters >= ctl->max_iters) {
+        else if (ctl->iters >= ctl->max_iters)
             ctl->converged = 3;
-            go = 0;
-        }
         __threadfence();
-        if (A.use_handle) cudaGraphSetConditional(A.handle, go ? 1u : 0u);
+        if (A.use_handle) cudaGraphSetConditional(A.handle, ctl->converged ? 0u : 1u);
     }
-}
-
-// A finished loop may still run the rest of its body: the scatter and
-// residual kernels return at once when ctl->converged is set.
-__global__ void adj_scatter_guarded(const __grid_constant__ AdjArgs A) {
-    if (A.ctl->converged) return;
-    scatter_body(A);
 }
 
 __global__ void adj_init_kernel(const float *g, float *L0, float *L1, long long n, AdjCtl *ctl,
@@ -627,8 +676,9 @@ int refine_tiles_grid(int nx, int ny) {
     return ((nx + TX - 1) / TX) * ((ny + REFINE_ROWS - 1) / REFINE_ROWS);
 }
 
-const void *adj_scatter_kernel() { return reinterpret_cast<const void *>(&adj_scatter_guarded); }
-const void *adj_resid_kernel() { return reinterpret_cast<const void *>(&adj_resid); }
+const void *adj_tiles_kernel() { return reinterpret_cast<const void *>(&adj_tiles); }
+
+size_t adj_tiles_smem(int) { return 0; }
 
 void launch_adj_init(const float *g, float *L0, float *L1, long long n, AdjCtl *ctl, float tol,
                      int max_iters, cudaStream_t st) {

@@ -309,9 +309,11 @@ void launch_refine_residual(const AdjProblem &ap, const hjbk::ControlTable &C, c
 const void *refine_tiles_kernel();
 size_t refine_tiles_smem(int hr);
 int refine_tiles_grid(int nx, int ny);
-// Graph-able adjoint iteration kernels.
-const void *adj_scatter_kernel();
-const void *adj_resid_kernel();
+// One block Gauss-Seidel sweep of the transposed iteration over staged
+// tiles (the refinement's tiles and grid; shared memory adj_tiles_smem(hr)
+// bytes).
+const void *adj_tiles_kernel();
+size_t adj_tiles_smem(int hr);
 struct AdjArgs {
     AdjProblem ap;
     hjbk::ControlTable ctrl;

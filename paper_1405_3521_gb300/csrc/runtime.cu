@@ -19,13 +19,6 @@ using hjbk::Ctl;
 using hjbk::SlotDesc;
 using hjbk::SlotState;
 
-// CTAs per SM of the adjoint's iteration kernels (grid-stride over the
-// nodes).  Every iteration ends in one same-address atomic per CTA and a
-// last-CTA decision, so fewer, longer-lived CTAs win: measured at 1025^2
-// (backward, 2 / 3 / 4 / 6 / 8 per SM): 33.4 / 27.6 / 25.7 / 29.9 / 29.9 ms.
-#ifndef HJB_ADJ_BLOCKS_PER_SM
-#define HJB_ADJ_BLOCKS_PER_SM 4
-#endif
 
 namespace {
 
@@ -2216,12 +2209,11 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
 }
 
 // The graph of an adjoint loop (WHILE conditional node): `reps` rounds of the
-// kernels fns[0..nf) per body, each on `grid` CTAs (default sms x
-// HJB_ADJ_BLOCKS_PER_SM) with `smem` bytes of dynamic shared memory and
-// `args` (whose handle is set here); the kernels' last CTA sets the
-// condition.
+// kernels fns[0..nf) per body, each on `grid` CTAs with `smem` bytes of
+// dynamic shared memory and `args` (whose handle is set here); the kernels'
+// last CTA sets the condition.
 int build_adj_loop(cudaGraph_t &graph, cudaGraphExec_t &exec, const void *const *fns, int nf,
-                   int reps, hjbh::AdjArgs &args, int grid = 0, size_t smem = 0) {
+                   int reps, hjbh::AdjArgs &args, int grid, size_t smem) {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
@@ -2241,16 +2233,13 @@ int build_adj_loop(cudaGraph_t &graph, cudaGraphExec_t &exec, const void *const 
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     args.handle = handle;
     args.use_handle = 1;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGraphNode_t prev = nullptr;
     for (int rep = 0; rep < reps; ++rep)
         for (int k = 0; k < nf; ++k) {
             cudaKernelNodeParams kp;
             std::memset(&kp, 0, sizeof kp);
             kp.func = const_cast<void *>(fns[k]);
-            kp.gridDim = dim3(grid > 0 ? grid : sms * HJB_ADJ_BLOCKS_PER_SM);
+            kp.gridDim = dim3(grid);
             kp.blockDim = dim3(hjbk::THREADS);
             kp.sharedMemBytes = static_cast<unsigned>(smem);
             void *argv[1] = {&args};
@@ -2344,15 +2333,19 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
                       P->adj_frac.as<float2>(), st);
     long long ref_launches = 0;
     int ref_iters = 0;
+    // the tiles of the refinement and of the transposed iteration hold every
+    // corner of a policy foot in their halo: the largest foot offset, rounded
+    // up, plus the second corner
+    const int tiles_hr = std::max(2, static_cast<int>(std::ceil(pr.max_off_xy)) + 1);
+    if (tiles_hr > 7)
+        return fail(HJB_ERR_UNSUPPORTED, "the adjoint takes feet of at most 6 cells (h |f| / dx)");
+    const int tiles_grid = hjbh::refine_tiles_grid(ap.nx, ap.ny);
     {
         // iterative refinement of the values the policy is decided on (see
         // refine_residual_kernel): HJB_ADJ_REFINE rounds, default 1, 0 = none
         const char *e = std::getenv("HJB_ADJ_REFINE");
         const int rounds = e ? std::max(0, std::min(4, std::atoi(e))) : 1;
         if (rounds > 0) TRY(P->adj_ref.ensure(3 * N * sizeof(float)));
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         for (int round = 0; round < rounds; ++round) {
             float *r = P->adj_ref.as<float>(), *D0 = r + N, *D1 = D0 + N;
             hjbh::launch_refine_residual(ap, ctrl, P->adj_v.as<float>(), P->adj_policy.as<int8_t>(),
@@ -2371,8 +2364,8 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
             ra.frac = P->adj_frac.as<float2>();
             // tiles' halo: every corner of a policy foot (at most ceil of the
             // largest foot offset, plus the second corner)
-            ra.hr = std::max(2, static_cast<int>(std::ceil(pr.max_off_xy)) + 1);
-            const int rgrid = hjbh::refine_tiles_grid(ap.nx, ap.ny);
+            ra.hr = tiles_hr;
+            const int rgrid = tiles_grid;
             const size_t rsmem = hjbh::refine_tiles_smem(ra.hr);
             hjbh::AdjCtl hr;
             const char *ng = std::getenv("HJB_NO_GRAPH");
@@ -2420,7 +2413,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     }
     hjbh::launch_adj_init(P->adj_g.as<float>(), L0, L1, N, ctl, static_cast<float>(tol), max_iters,
                           st);
-    // graph: WHILE { scatter; residual } x 2
+    // graph: WHILE { sweep } x 2
     hjbh::AdjArgs args;
     std::memset(&args, 0, sizeof args);
     args.ap = ap;
@@ -2433,29 +2426,27 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     args.use_handle = 1;
     args.cell = P->adj_cell.as<int>();
     args.frac = P->adj_frac.as<float2>();
+    args.hr = tiles_hr;
+    const size_t asmem = hjbh::adj_tiles_smem(tiles_hr);
     const char *ng = std::getenv("HJB_NO_GRAPH");
     if (ng && ng[0] == '1') {
-        // host-driven loop (profiling aid): the same kernels, 8 iterations
-        // between reads of the convergence flag
+        // host-driven loop (profiling aid): the same kernel, 8 sweeps between
+        // reads of the convergence flag
         args.use_handle = 0;
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const void *fns[2] = {hjbh::adj_scatter_kernel(), hjbh::adj_resid_kernel()};
         void *argv[1] = {&args};
         for (;;) {
             for (int rep = 0; rep < 8; ++rep)
-                for (int k = 0; k < 2; ++k)
-                    CK(cudaLaunchKernel(fns[k], dim3(sms * HJB_ADJ_BLOCKS_PER_SM),
-                                        dim3(hjbk::THREADS), argv, 0, st));
+                CK(cudaLaunchKernel(hjbh::adj_tiles_kernel(), dim3(tiles_grid),
+                                    dim3(hjbk::THREADS), argv, asmem, st));
             int conv = 0;
             CK(cudaMemcpyAsync(&conv, &ctl->converged, sizeof conv, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             if (conv) break;
         }
-    } else if (!same_adj_args(P->adj_exec, P->adj_args_in_graph, args)) {
-        const void *fns[2] = {hjbh::adj_scatter_kernel(), hjbh::adj_resid_kernel()};
-        TRY(build_adj_loop(P->adj_graph, P->adj_exec, fns, 2, 2, args));
+    } else if (!same_adj_args(P->adj_exec, P->adj_args_in_graph, args) ||
+               P->adj_args_in_graph.hr != args.hr) {
+        const void *fns[1] = {hjbh::adj_tiles_kernel()};
+        TRY(build_adj_loop(P->adj_graph, P->adj_exec, fns, 1, 2, args, tiles_grid, asmem));
         P->adj_args_in_graph = args;
     }
     if (args.use_handle) CK(cudaGraphLaunch(P->adj_exec, st));
@@ -2476,9 +2467,9 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
         stats->iterations = hc.iters;
         stats->converged = (hc.converged == 1 || hc.converged == 2) ? hc.converged : 0;
         stats->final_residual = hc.final_res;
-        stats->node_updates = static_cast<long long>(hc.iters) * N;
+        stats->node_updates = static_cast<long long>(hc.iters) * N * hjbh::REFINE_APPS;
         stats->ties = ties;
-        stats->launches = pr.launches + 4 + 4LL * ((hc.iters + 1) / 2) + ref_launches;
+        stats->launches = pr.launches + 4 + 2LL * ((hc.iters + 1) / 2) + ref_launches;
         stats->local_iters = ref_iters;  // iterations of the policy-value refinement
         float ms = 0;
         cudaEventElapsedTime(&ms, R.ev0, R.ev1);
