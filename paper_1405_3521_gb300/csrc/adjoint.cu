@@ -20,7 +20,6 @@ using namespace hjbk;
 using hjbh::AdjArgs;
 using hjbh::AdjCtl;
 using hjbh::AdjProblem;
-using hjbh::REFINE_APPS;
 using hjbh::REFINE_ROWS;
 
 namespace {
@@ -259,16 +258,17 @@ __global__ void refine_residual_kernel(AdjProblem ap, const __grid_constant__ Co
 // Block Gauss-Seidel sweep of the refinement iteration dV = r + beta P_pi dV
 // with the policy frozen: each CTA stages a tile of 32 x REFINE_ROWS nodes of
 // dV_src with an hr-cell halo in shared memory, applies the iteration
-// REFINE_APPS times there (the halo held at the previous sweep's values; two
+// APPS times there (the halo held at the previous sweep's values; two
 // buffers, so every application reads only the previous one: the result does
 // not depend on the order of the CTAs), and writes the tile to dV_dst.  The
 // same fixed point as the Jacobi iteration, reached in a fraction of the
-// launches because a correction travels REFINE_APPS steps within a tile per
+// launches because a correction travels APPS steps within a tile per
 // sweep.  The last CTA takes the stopping decision: the sweep's change
 // within 4 ulp of max|dV| (the FP32 floor of the iteration), or 64 sweeps
 // without a new minimum once below 64 ulp, or the sweep cap; a foot beyond
 // the staged halo (which the halo derived from the fields rules out) stops
 // the loop with the error flag set.
+template <int APPS>
 __global__ void refine_tiles(const __grid_constant__ AdjArgs A) {
     static_assert(TX * REFINE_ROWS == THREADS, "one thread per node of a refinement tile");
     extern __shared__ float s_buf[];
@@ -325,7 +325,7 @@ __global__ void refine_tiles(const __grid_constant__ AdjArgs A) {
         const float dold = in ? s_buf[me] : 0.0f;
         float d = dold;
 #pragma unroll 1
-        for (int a = 0; a < REFINE_APPS; ++a) {
+        for (int a = 0; a < APPS; ++a) {
             const float *cur = s_buf + (a & 1) * SZ;
             float *nxt = s_buf + ((a + 1) & 1) * SZ;
             if (in) {
@@ -408,7 +408,7 @@ __global__ void refine_tiles(const __grid_constant__ AdjArgs A) {
 // nodes.  The mass that the tile's hr-cell halo (the nodes whose policy feet
 // can reach the tile) sends into it, beta times the Q1 weight times lambda,
 // is constant during the sweep (the halo is held at the previous sweep's
-// values): it is added to g once, in shared memory.  Then REFINE_APPS times
+// values): it is added to g once, in shared memory.  Then APPS times
 // every tile node's lambda becomes that base plus the mass the tile's own
 // nodes send it (shared-memory atomics), and the tile's lambda is written at
 // the end.  Mass that leaves the tile is gathered by the neighbouring
@@ -418,10 +418,11 @@ __global__ void refine_tiles(const __grid_constant__ AdjArgs A) {
 // decision: the sweep's change within 32 ulp of max|lambda|, or 64 sweeps
 // without a new minimum once below 1024 ulp, or an optional absolute tol,
 // or the sweep cap.
+template <int APPS>
 __global__ void adj_tiles(const __grid_constant__ AdjArgs A) {
     static_assert(TX * REFINE_ROWS == THREADS, "one thread per node of a tile");
     __shared__ float s_base[THREADS];  // g plus the halo's mass, per tile node
-    __shared__ float s_acc[THREADS];
+    __shared__ float s_acc[2][THREADS];
     AdjCtl *ctl = A.ctl;
     if (ctl->converged) return;
     const AdjProblem &ap = A.ap;
@@ -494,17 +495,19 @@ __global__ void adj_tiles(const __grid_constant__ AdjArgs A) {
         __syncthreads();  // the base is complete
         const float base = s_base[threadIdx.x];
 #pragma unroll 1
-        for (int a = 0; a < REFINE_APPS; ++a) {
-            s_acc[threadIdx.x] = base;
+        for (int a = 0; a < APPS; ++a) {
+            // two accumulators: this application's is reset while the other
+            // may still be read, so two barriers per application suffice
+            float *acc = s_acc[a & 1];
+            acc[threadIdx.x] = base;
             __syncthreads();
             if (lam != 0.0f) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (cn[e] >= 0) atomicAdd(&s_acc[cn[e]], lam * wt[e]);
+                    if (cn[e] >= 0) atomicAdd(&acc[cn[e]], lam * wt[e]);
             }
             __syncthreads();
-            lam = s_acc[threadIdx.x];
-            __syncthreads();  // read before the next application resets it
+            lam = acc[threadIdx.x];
         }
         if (in) {
             dst[i] = lam;
@@ -666,7 +669,11 @@ void launch_refine_residual(const AdjProblem &ap, const ControlTable &C, const f
     refine_residual_kernel<<<blocks_for(N), THREADS, 0, st>>>(ap, C, V, policy, r);
 }
 
-const void *refine_tiles_kernel() { return reinterpret_cast<const void *>(&refine_tiles); }
+const void *refine_tiles_kernel(int apps) {
+    if (apps == 32) return reinterpret_cast<const void *>(&refine_tiles<32>);
+    if (apps == 8) return reinterpret_cast<const void *>(&refine_tiles<8>);
+    return reinterpret_cast<const void *>(&refine_tiles<16>);
+}
 
 size_t refine_tiles_smem(int hr) {
     return 2 * sizeof(float) * static_cast<size_t>(TX + 2 * hr) * (REFINE_ROWS + 2 * hr);
@@ -676,7 +683,11 @@ int refine_tiles_grid(int nx, int ny) {
     return ((nx + TX - 1) / TX) * ((ny + REFINE_ROWS - 1) / REFINE_ROWS);
 }
 
-const void *adj_tiles_kernel() { return reinterpret_cast<const void *>(&adj_tiles); }
+const void *adj_tiles_kernel(int apps) {
+    if (apps == 32) return reinterpret_cast<const void *>(&adj_tiles<32>);
+    if (apps == 8) return reinterpret_cast<const void *>(&adj_tiles<8>);
+    return reinterpret_cast<const void *>(&adj_tiles<16>);
+}
 
 size_t adj_tiles_smem(int) { return 0; }
 

@@ -306,13 +306,13 @@ void launch_feet(const AdjProblem &ap, const hjbk::ControlTable &C, const int8_t
 // bytes, one CTA per tile: refine_tiles_grid).
 void launch_refine_residual(const AdjProblem &ap, const hjbk::ControlTable &C, const float *V,
                             const int8_t *policy, float *r, cudaStream_t st);
-const void *refine_tiles_kernel();
+const void *refine_tiles_kernel(int apps);
 size_t refine_tiles_smem(int hr);
 int refine_tiles_grid(int nx, int ny);
 // One block Gauss-Seidel sweep of the transposed iteration over staged
 // tiles (the refinement's tiles and grid; shared memory adj_tiles_smem(hr)
 // bytes).
-const void *adj_tiles_kernel();
+const void *adj_tiles_kernel(int apps);
 size_t adj_tiles_smem(int hr);
 struct AdjArgs {
     AdjProblem ap;
@@ -329,10 +329,10 @@ struct AdjArgs {
     const float2 *frac;
     int hr;  // refinement tiles: halo in cells around each 32 x REFINE_ROWS tile
 };
-// Tiles of the refinement's block Gauss-Seidel sweep: 32 x REFINE_ROWS nodes,
-// REFINE_APPS applications of the frozen-policy iteration per staged tile.
+// Tiles of the adjoint's block Gauss-Seidel sweeps: 32 x REFINE_ROWS nodes;
+// the applications per staged tile and sweep are a template parameter of
+// the kernels (8, 16 or 32).
 constexpr int REFINE_ROWS = 8;
-constexpr int REFINE_APPS = 8;
 void launch_adj_init(const float *g, float *L0, float *L1, long long n, AdjCtl *ctl, float tol,
                      int max_iters, cudaStream_t st);
 // dL/dtheta (wrt = 0) or dL/dl (wrt = 1) from lambda.

@@ -233,6 +233,7 @@ struct hjb_problem {
     cudaGraph_t ref_graph = nullptr;  // the refinement loop of hjb_backward
     cudaGraphExec_t ref_exec = nullptr;
     hjbh::AdjArgs ref_args_in_graph;
+    int adj_apps_in_graph = 0, ref_apps_in_graph = 0;  // kernels of the cached loops
     hjbh::AdjArgs adj_args_in_graph;
     std::vector<const hjb_problem *> batch_key;
 };
@@ -2340,6 +2341,11 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
     if (tiles_hr > 7)
         return fail(HJB_ERR_UNSUPPORTED, "the adjoint takes feet of at most 6 cells (h |f| / dx)");
     const int tiles_grid = hjbh::refine_tiles_grid(ap.nx, ap.ny);
+    // applications per staged tile and sweep of both loops (HJB_ADJ_APPS: 8,
+    // 16 or 32; default 16)
+    const char *ea = std::getenv("HJB_ADJ_APPS");
+    const int ea_v = ea ? std::atoi(ea) : 16;
+    const int apps = (ea_v == 8 || ea_v == 32) ? ea_v : 16;
     {
         // iterative refinement of the values the policy is decided on (see
         // refine_residual_kernel): HJB_ADJ_REFINE rounds, default 1, 0 = none
@@ -2375,7 +2381,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
                 void *argv[1] = {&ra};
                 for (;;) {
                     for (int k = 0; k < 8; ++k)
-                        CK(cudaLaunchKernel(hjbh::refine_tiles_kernel(), dim3(rgrid),
+                        CK(cudaLaunchKernel(hjbh::refine_tiles_kernel(apps), dim3(rgrid),
                                             dim3(hjbk::THREADS), argv, rsmem, st));
                     CK(cudaMemcpyAsync(&hr, ctl, sizeof hr, cudaMemcpyDeviceToHost, st));
                     CK(cudaStreamSynchronize(st));
@@ -2385,10 +2391,11 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
                 // graph loop: 2 sweeps per body, the last CTA of each sets the
                 // condition
                 if (!same_adj_args(P->ref_exec, P->ref_args_in_graph, ra) ||
-                    P->ref_args_in_graph.hr != ra.hr) {
-                    const void *fns[1] = {hjbh::refine_tiles_kernel()};
+                    P->ref_args_in_graph.hr != ra.hr || P->ref_apps_in_graph != apps) {
+                    const void *fns[1] = {hjbh::refine_tiles_kernel(apps)};
                     TRY(build_adj_loop(P->ref_graph, P->ref_exec, fns, 1, 2, ra, rgrid, rsmem));
                     P->ref_args_in_graph = ra;
+                    P->ref_apps_in_graph = apps;
                 }
                 CK(cudaGraphLaunch(P->ref_exec, st));
                 CK(cudaMemcpyAsync(&hr, ctl, sizeof hr, cudaMemcpyDeviceToHost, st));
@@ -2436,7 +2443,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
         void *argv[1] = {&args};
         for (;;) {
             for (int rep = 0; rep < 8; ++rep)
-                CK(cudaLaunchKernel(hjbh::adj_tiles_kernel(), dim3(tiles_grid),
+                CK(cudaLaunchKernel(hjbh::adj_tiles_kernel(apps), dim3(tiles_grid),
                                     dim3(hjbk::THREADS), argv, asmem, st));
             int conv = 0;
             CK(cudaMemcpyAsync(&conv, &ctl->converged, sizeof conv, cudaMemcpyDeviceToHost, st));
@@ -2444,10 +2451,11 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
             if (conv) break;
         }
     } else if (!same_adj_args(P->adj_exec, P->adj_args_in_graph, args) ||
-               P->adj_args_in_graph.hr != args.hr) {
-        const void *fns[1] = {hjbh::adj_tiles_kernel()};
+               P->adj_args_in_graph.hr != args.hr || P->adj_apps_in_graph != apps) {
+        const void *fns[1] = {hjbh::adj_tiles_kernel(apps)};
         TRY(build_adj_loop(P->adj_graph, P->adj_exec, fns, 1, 2, args, tiles_grid, asmem));
         P->adj_args_in_graph = args;
+        P->adj_apps_in_graph = apps;
     }
     if (args.use_handle) CK(cudaGraphLaunch(P->adj_exec, st));
     hjbh::AdjCtl hc;
@@ -2467,7 +2475,7 @@ int hjb_backward(hjb_problem *P, const float *v, const float *grad_v, int wrt,
         stats->iterations = hc.iters;
         stats->converged = (hc.converged == 1 || hc.converged == 2) ? hc.converged : 0;
         stats->final_residual = hc.final_res;
-        stats->node_updates = static_cast<long long>(hc.iters) * N * hjbh::REFINE_APPS;
+        stats->node_updates = static_cast<long long>(hc.iters) * N * apps;
         stats->ties = ties;
         stats->launches = pr.launches + 4 + 2LL * ((hc.iters + 1) / 2) + ref_launches;
         stats->local_iters = ref_iters;  // iterations of the policy-value refinement
