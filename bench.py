@@ -601,9 +601,11 @@ def run_adjoint(args, hjb, S, dev, flush, local):
     N = d["labels"].size
     # node-updates of the transposed iteration and of the refinement of the
     # values the policy is decided on (a policy-frozen forward iteration):
-    # both run block Gauss-Seidel sweeps, 8 applications per staged tile
+    # both run block Gauss-Seidel sweeps; node_updates counts the transposed
+    # sweep's applications, the refinement runs as many per tile and sweep
     ref = st["local_iters"]
-    upd = N * 8 * (st["iterations"] + ref)
+    apps = st["node_updates"] // max(1, N * st["iterations"])
+    upd = N * apps * (st["iterations"] + ref)
     hbm = measured_peaks().get("hbm_gbs", 6660.0)
     # per node and sweep of either: the policy foot's cell 4 B and fractions
     # 8 B, g (or r) 4 B, lambda (or the correction) read 4 B and written 4 B

@@ -361,8 +361,9 @@ int hjb_solve_batch(hjb_problem *const *problems, int count, const hjb_solve_opt
  *           HJB_DYN_SPEED_CURRENT):  lambda_i beta h s_i grad I[V](y_i) . a_pi(i)
  *  wrt = 1: grad_out = dL/dl for the cost field: lambda_i gamma.
  *  v [N]: the converged solution; grad_v [N]: dL/dV.  lambda is iterated by
- *  block Gauss-Seidel sweeps over 32 x 8 tiles (8 applications per staged
- *  tile and sweep, the halo held); stats->iterations counts the sweeps.
+ *  block Gauss-Seidel sweeps over 32 x 8 tiles (16 applications per staged
+ *  tile and sweep, the halo held; HJB_ADJ_APPS sets 8, 16 or 32);
+ *  stats->iterations counts the sweeps.
  *  opts->tol (optional, > 0) stops the iteration once a sweep changes lambda
  *  by at most tol (stats->converged = 1).  It always stops
  *  (stats->converged = 2) at the summation-order floor of the FP32
